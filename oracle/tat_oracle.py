@@ -86,7 +86,9 @@ def hybrid_rule(a: int = LOW_A, m: int = LOW_M):
     for p in range(m):
         c = np.zeros(p + 1)
         c[p] = 1.0
-        P = np.polynomial.Legendre(c, domain=[0, a]).convert(kind=np.polynomial.Polynomial)
+        # Evaluated in the Legendre basis on [0, a]: the monomial expansion of
+        # P_p(2x/a - 1) cancels catastrophically at x = a for p near m.
+        P = np.polynomial.Legendre(c, domain=[0, a])
         prim = P.integ()
         mom = prim(a) - prim(0.0) - 0.5 * P(a)
         d = P.deriv()
