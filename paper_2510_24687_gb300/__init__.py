@@ -1,0 +1,18 @@
+"""GB300-native fast forward operator A and adjoint A* for photoacoustic /
+thermoacoustic tomography with detectors on a circle (Hauptmann, Kunyansky,
+Poimala, arXiv 2510.24687, Algorithms 1 and 2).
+
+The operators run as hand-written CUDA kernels for sm_103a inside libtat.so,
+whose C ABI is declared in include/tat.h; this package is its thin binding.
+"""
+from .binding import (TatError, TatOperator, header_symbols, load, tat_adjoint, tat_adjoint_batched,
+                      tat_debug_bessel, tat_debug_low_mode_rule, tat_debug_stencils, tat_forward,
+                      tat_forward_batched, tat_plan_create, tat_plan_create_ex, tat_plan_desc,
+                      tat_plan_desc_default, tat_plan_destroy, tat_plan_get_info, tat_plan_info,
+                      tat_plan_query, tat_status_string, tat_workspace_size)
+
+__all__ = ["TatError", "TatOperator", "header_symbols", "load", "tat_adjoint", "tat_adjoint_batched",
+           "tat_debug_bessel", "tat_debug_low_mode_rule", "tat_debug_stencils", "tat_forward",
+           "tat_forward_batched", "tat_plan_create", "tat_plan_create_ex", "tat_plan_desc",
+           "tat_plan_desc_default", "tat_plan_destroy", "tat_plan_get_info", "tat_plan_info", "tat_plan_query",
+           "tat_status_string", "tat_workspace_size"]

@@ -1,0 +1,264 @@
+"""ctypes binding of libtat (include/tat.h, include/tat_debug.h).
+
+Argument marshalling only: every step of A and A* runs in the CUDA kernels of
+libtat.  Functions keep the C names.  Device buffers are passed as integer
+addresses (``tensor.data_ptr()``); ``TatOperator`` wraps a plan together with
+torch-allocated outputs and workspace for convenience.  There is no CPU
+fallback: if libtat.so is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import re
+
+from ._build import LIB, ROOT
+
+TAT_OK = 0
+_STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported configuration", 3: "out of memory",
+           4: "CUDA error", 5: "device wait timed out", 6: "internal error"}
+
+
+class TatError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {_STATUS.get(status, 'unknown status')} (status {status})")
+        self.status = status
+
+
+class tat_plan_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("n_det", ctypes.c_int), ("n_t", ctypes.c_int),
+                ("c", ctypes.c_double), ("R", ctypes.c_double), ("T", ctypes.c_double),
+                ("support_radius", ctypes.c_double), ("arc_begin", ctypes.c_double),
+                ("arc_len", ctypes.c_double), ("n_phi", ctypes.c_int), ("pad_L", ctypes.c_double),
+                ("low_mode_quadrature", ctypes.c_int)]
+
+
+class tat_plan_info(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int), ("J", ctypes.c_int), ("n_phi", ctypes.c_int),
+                ("K", ctypes.c_int), ("n_low", ctypes.c_int), ("n_points", ctypes.c_int),
+                ("h", ctypes.c_double), ("dt", ctypes.c_double), ("dlam", ctypes.c_double),
+                ("dxi", ctypes.c_double), ("lam_c", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_LL = ctypes.c_longlong
+_D = ctypes.c_double
+
+
+def load() -> ctypes.CDLL:
+    """Loads libtat.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB):
+        raise RuntimeError(f"{LIB} is missing: run __graft_entry__.build() (there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB)
+    sig = {
+        "tat_plan_desc_default": (_I, [ctypes.POINTER(tat_plan_desc), _I, _I, _I, _D, _D, _D]),
+        "tat_plan_query": (_I, [ctypes.POINTER(tat_plan_desc), ctypes.POINTER(tat_plan_info)]),
+        "tat_plan_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _D, _D, _D]),
+        "tat_plan_create_ex": (_I, [ctypes.POINTER(_P), ctypes.POINTER(tat_plan_desc)]),
+        "tat_plan_destroy": (_I, [_P]),
+        "tat_plan_get_info": (_I, [_P, ctypes.POINTER(tat_plan_info)]),
+        "tat_workspace_size": (ctypes.c_size_t, [_P, _I]),
+        "tat_forward": (_I, [_P, _P, _P, _P, _P]),
+        "tat_adjoint": (_I, [_P, _P, _P, _P, _P]),
+        "tat_forward_batched": (_I, [_P, _I, _P, _LL, _P, _LL, _P, _P]),
+        "tat_adjoint_batched": (_I, [_P, _I, _P, _LL, _P, _LL, _P, _P]),
+        "tat_status_string": (ctypes.c_char_p, [_I]),
+        "tat_debug_bessel": (_I, [_D, _I, ctypes.POINTER(_D)]),
+        "tat_debug_low_mode_rule": (_I, [ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+        "tat_debug_stencils": (_I, [ctypes.POINTER(tat_plan_desc), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                                    ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D),
+                                    ctypes.POINTER(_D), _I]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def header_symbols():
+    """Function names declared in include/*.h (for the ABI export test)."""
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            txt = open(os.path.join(inc, h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(tat_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def _check(status: int, what: str):
+    if status != TAT_OK:
+        raise TatError(status, what)
+
+
+# ------------------------------------------------------------------ C names
+
+def tat_plan_desc_default(n, n_det, n_t, c=1.0, R=1.0, T=2.0) -> tat_plan_desc:
+    d = tat_plan_desc()
+    _check(load().tat_plan_desc_default(ctypes.byref(d), n, n_det, n_t, c, R, T), "tat_plan_desc_default")
+    return d
+
+
+def tat_plan_query(desc: tat_plan_desc) -> dict:
+    info = tat_plan_info()
+    _check(load().tat_plan_query(ctypes.byref(desc), ctypes.byref(info)), "tat_plan_query")
+    return info.as_dict()
+
+
+def tat_plan_create(n, n_det, n_t, c=1.0, R=1.0, T=2.0) -> int:
+    h = _P()
+    _check(load().tat_plan_create(ctypes.byref(h), n, n_det, n_t, c, R, T), "tat_plan_create")
+    return h.value
+
+
+def tat_plan_create_ex(desc: tat_plan_desc) -> int:
+    h = _P()
+    _check(load().tat_plan_create_ex(ctypes.byref(h), ctypes.byref(desc)), "tat_plan_create_ex")
+    return h.value
+
+
+def tat_plan_destroy(plan: int):
+    _check(load().tat_plan_destroy(plan), "tat_plan_destroy")
+
+
+def tat_plan_get_info(plan: int) -> dict:
+    info = tat_plan_info()
+    _check(load().tat_plan_get_info(plan, ctypes.byref(info)), "tat_plan_get_info")
+    return info.as_dict()
+
+
+def tat_workspace_size(plan: int, batch: int = 1) -> int:
+    return int(load().tat_workspace_size(plan, batch))
+
+
+def tat_forward(plan, f_ptr, g_ptr, ws_ptr, stream=0):
+    _check(load().tat_forward(plan, f_ptr, g_ptr, ws_ptr, stream or None), "tat_forward")
+
+
+def tat_adjoint(plan, g_ptr, f_ptr, ws_ptr, stream=0):
+    _check(load().tat_adjoint(plan, g_ptr, f_ptr, ws_ptr, stream or None), "tat_adjoint")
+
+
+def tat_forward_batched(plan, batch, f_ptr, f_stride, g_ptr, g_stride, ws_ptr, stream=0):
+    _check(load().tat_forward_batched(plan, batch, f_ptr, f_stride, g_ptr, g_stride, ws_ptr, stream or None),
+           "tat_forward_batched")
+
+
+def tat_adjoint_batched(plan, batch, g_ptr, g_stride, f_ptr, f_stride, ws_ptr, stream=0):
+    _check(load().tat_adjoint_batched(plan, batch, g_ptr, g_stride, f_ptr, f_stride, ws_ptr, stream or None),
+           "tat_adjoint_batched")
+
+
+def tat_status_string(status: int) -> str:
+    return load().tat_status_string(status).decode()
+
+
+def tat_debug_bessel(x: float, kmax: int):
+    out = (_D * (kmax + 1))()
+    _check(load().tat_debug_bessel(x, kmax, out), "tat_debug_bessel")
+    return list(out)
+
+
+def tat_debug_low_mode_rule():
+    cnt = _I(0)
+    _check(load().tat_debug_low_mode_rule(None, None, ctypes.byref(cnt)), "tat_debug_low_mode_rule")
+    x, w = (_D * cnt.value)(), (_D * cnt.value)()
+    _check(load().tat_debug_low_mode_rule(x, w, ctypes.byref(cnt)), "tat_debug_low_mode_rule")
+    return list(x), list(w)
+
+
+def tat_debug_stencils(desc: tat_plan_desc, rings, lps):
+    m = len(rings)
+    r = (_I * m)(*rings)
+    l = (_I * m)(*lps)
+    i0, k0, a, b = (_I * m)(), (_I * m)(), (_D * m)(), (_D * m)()
+    _check(load().tat_debug_stencils(ctypes.byref(desc), r, l, i0, k0, a, b, m), "tat_debug_stencils")
+    return list(i0), list(k0), list(a), list(b)
+
+
+# ------------------------------------------------------------------ torch wrapper
+
+class TatOperator:
+    """A plan plus torch-managed workspace: ``forward(f)`` = A f, ``adjoint(g)`` = A* g.
+
+    f: float32 CUDA tensor (n, n) or (B, n, n); g: (n_det, n_t) or (B, n_det, n_t).
+    All arithmetic runs in libtat's kernels on the current torch stream.
+    """
+
+    def __init__(self, n, n_det, n_t, c=1.0, R=1.0, T=2.0, device=None, **desc_kw):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        desc = tat_plan_desc_default(n, n_det, n_t, c, R, T)
+        for k, v in desc_kw.items():
+            if k == "arc_len" and v is None:
+                v = 2 * math.pi
+            setattr(desc, k, v)
+        self.desc = desc
+        with torch.cuda.device(self.device):
+            self.plan = tat_plan_create_ex(desc)
+        self.info = tat_plan_get_info(self.plan)
+        self.n, self.n_det, self.n_t = n, n_det, n_t
+        self._ws = {}
+
+    def workspace(self, batch):
+        ws = self._ws.get(batch)
+        if ws is None:
+            nbytes = tat_workspace_size(self.plan, batch)
+            ws = self.torch.empty(nbytes // 4 + 64, dtype=self.torch.float32, device=self.device)
+            self._ws = {batch: ws}
+        return ws
+
+    def _stream(self):
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    def forward(self, f, out=None):
+        torch = self.torch
+        single = f.dim() == 2
+        fb = f.reshape(-1, self.n, self.n)
+        if fb.dtype != torch.float32 or not fb.is_cuda or not fb.is_contiguous():
+            raise ValueError("f must be a contiguous float32 CUDA tensor")
+        B = fb.shape[0]
+        g = out if out is not None else torch.empty((B, self.n_det, self.n_t), dtype=torch.float32, device=fb.device)
+        ws = self.workspace(B)
+        with torch.cuda.device(self.device):
+            tat_forward_batched(self.plan, B, fb.data_ptr(), self.n * self.n, g.data_ptr(), self.n_det * self.n_t,
+                                ws.data_ptr(), self._stream())
+        return g[0] if single and out is None else g
+
+    def adjoint(self, g, out=None):
+        torch = self.torch
+        single = g.dim() == 2
+        gb = g.reshape(-1, self.n_det, self.n_t)
+        if gb.dtype != torch.float32 or not gb.is_cuda or not gb.is_contiguous():
+            raise ValueError("g must be a contiguous float32 CUDA tensor")
+        B = gb.shape[0]
+        f = out if out is not None else torch.empty((B, self.n, self.n), dtype=torch.float32, device=gb.device)
+        ws = self.workspace(B)
+        with torch.cuda.device(self.device):
+            tat_adjoint_batched(self.plan, B, gb.data_ptr(), self.n_det * self.n_t, f.data_ptr(), self.n * self.n,
+                                ws.data_ptr(), self._stream())
+        return f[0] if single and out is None else f
+
+    def close(self):
+        if getattr(self, "plan", None):
+            tat_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

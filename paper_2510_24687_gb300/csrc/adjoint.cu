@@ -1,0 +1,42 @@
+// Launcher of the adjoint A* (the stages of Algorithm 2 as the exact transpose
+// of Algorithm 1): five stream-ordered kernels per batch, in reverse order.
+#include "launch.cuh"
+
+namespace tat {
+
+tat_status launch_adjoint(const tat_plan_s* Pl, int batch, const float* g, long long gs, float* f, long long fs,
+                          void* ws, cudaStream_t st) {
+  const DevPlan& P = Pl->d;
+  const LaunchCfg& c = Pl->cfg;
+  const Shapes s = shapes(Pl, batch);
+  float2* X = static_cast<float2*>(ws);
+  float2* Y = X + (size_t)batch * Pl->ws_x;
+  const long long xs = (long long)Pl->ws_x, ys = (long long)Pl->ws_y;
+  const int dev = Pl->device;
+  bool ok = true;
+  dispatch_ang(P.n_det, [&](auto Lc) {
+    constexpr int L = decltype(Lc)::value;
+    ok &= ensure_smem<k_theta_adj<L>>(dev);
+    k_theta_adj<L><<<s.theta_grid, s.theta_block, s.theta_smem, st>>>(P, g, gs, Y, ys, c.t_tile, c.nt_det);
+  });
+  dispatch_2M(2 * P.M, [&](auto Lc) {
+    constexpr int L = decltype(Lc)::value;
+    ok &= ensure_smem<k_modes_adj<L>>(dev);
+    k_modes_adj<L><<<s.modes_grid, s.modes_block, s.modes_smem, st>>>(P, Y, ys, X, xs, c.nt_2M);
+  });
+  dispatch_ang(P.n_phi, [&](auto Lc) {
+    constexpr int L = decltype(Lc)::value;
+    ok &= ensure_smem<k_rings_adj<L>>(dev);
+    k_rings_adj<L><<<s.rings_grid, s.rings_block, s.rings_smem, st>>>(P, X, xs, Y, ys, c.rings_per_cta, c.nt_phi,
+                                                                      s.ntiles);
+  });
+  dispatch_N(P.N, [&](auto Lc) {
+    constexpr int L = decltype(Lc)::value;
+    ok &= ensure_smem<k_cols_adj<L>>(dev) && ensure_smem<k_rows_adj<L>>(dev);
+    k_cols_adj<L><<<s.cols_grid_a, s.cols_block, s.cols_smem_a, st>>>(P, Y, ys, X, xs, c.strip, c.nt_N);
+    k_rows_adj<L><<<s.rows_grid, s.rows_block, s.rows_smem, st>>>(P, X, xs, f, fs, c.rows_pairs, c.nt_N);
+  });
+  return check_launch(ok);
+}
+
+}  // namespace tat

@@ -1,0 +1,60 @@
+// Launcher of the forward operator A (Algorithm 1): five stream-ordered
+// kernels per batch; see kernels.cuh for what each stage computes.
+#include "launch.cuh"
+
+namespace tat {
+
+tat_status configure_kernels() { return TAT_OK; }
+
+// Host-side check of every launch shape against the device limits.
+tat_status validate_shapes(const tat_plan_s* Pl) {
+  const Shapes s = shapes(Pl, 1);
+  const size_t mx = 227 * 1024;
+  const int blocks[] = {s.rows_block, s.cols_block, s.rings_block, s.modes_block, s.theta_block};
+  const size_t smem[] = {s.rows_smem, s.cols_smem_f, s.cols_smem_a, s.rings_smem, s.modes_smem, s.theta_smem};
+  for (int b : blocks)
+    if (b < 32 || b > 1024 || b % 32) return TAT_ERR_UNSUPPORTED;
+  if (s.rings_block < 96) return TAT_ERR_UNSUPPORTED;  // reduction scratch of the low-mode rings
+  if (s.cols_block > 512) return TAT_ERR_UNSUPPORTED;  // launch bound of the column kernels
+  for (size_t m : smem)
+    if (m > mx) return TAT_ERR_UNSUPPORTED;
+  if (Pl->cfg.t_tile % 2 || Pl->cfg.strip < 1 || Pl->cfg.rings_per_cta < 1) return TAT_ERR_INVALID_ARG;
+  return TAT_OK;
+}
+
+tat_status launch_forward(const tat_plan_s* Pl, int batch, const float* f, long long fs, float* g, long long gs,
+                          void* ws, cudaStream_t st) {
+  const DevPlan& P = Pl->d;
+  const LaunchCfg& c = Pl->cfg;
+  const Shapes s = shapes(Pl, batch);
+  float2* X = static_cast<float2*>(ws);
+  float2* Y = X + (size_t)batch * Pl->ws_x;
+  const long long xs = (long long)Pl->ws_x, ys = (long long)Pl->ws_y;
+  const int dev = Pl->device;
+  bool ok = true;
+  dispatch_N(P.N, [&](auto Lc) {
+    constexpr int L = decltype(Lc)::value;
+    ok &= ensure_smem<k_rows_fwd<L>>(dev) && ensure_smem<k_cols_fwd<L>>(dev);
+    k_rows_fwd<L><<<s.rows_grid, s.rows_block, s.rows_smem, st>>>(P, f, fs, X, xs, c.rows_pairs, c.nt_N);
+    k_cols_fwd<L><<<s.cols_grid_f, s.cols_block, s.cols_smem_f, st>>>(P, X, xs, Y, ys, c.strip, c.nt_N);
+  });
+  dispatch_ang(P.n_phi, [&](auto Lc) {
+    constexpr int L = decltype(Lc)::value;
+    ok &= ensure_smem<k_rings_fwd<L>>(dev);
+    k_rings_fwd<L><<<s.rings_grid, s.rings_block, s.rings_smem, st>>>(P, Y, ys, X, xs, c.rings_per_cta, c.nt_phi,
+                                                                      s.ntiles);
+  });
+  dispatch_2M(2 * P.M, [&](auto Lc) {
+    constexpr int L = decltype(Lc)::value;
+    ok &= ensure_smem<k_modes_fwd<L>>(dev);
+    k_modes_fwd<L><<<s.modes_grid, s.modes_block, s.modes_smem, st>>>(P, X, xs, Y, ys, c.nt_2M);
+  });
+  dispatch_ang(P.n_det, [&](auto Lc) {
+    constexpr int L = decltype(Lc)::value;
+    ok &= ensure_smem<k_theta_fwd<L>>(dev);
+    k_theta_fwd<L><<<s.theta_grid, s.theta_block, s.theta_smem, st>>>(P, Y, ys, g, gs, c.t_tile, c.nt_det);
+  });
+  return check_launch(ok);
+}
+
+}  // namespace tat

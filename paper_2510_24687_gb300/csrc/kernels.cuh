@@ -1,0 +1,533 @@
+// CUDA kernels of the fast forward operator A (Algorithm 1) and its exact
+// transpose A* (the stages of Algorithm 2), FP32 on the device.
+//
+// Forward, per image (workspace X, Y are per-image scratch regions):
+//   k_rows_fwd   steps 1-2: zero-extend, row DFT of length N (two real rows
+//                per complex FFT), x (h^2/2pi) e^{i q dxi}  -> X = R[iy][q], q < N/2
+//   k_cols_fwd   steps 2-3: column DFT of length N per half-plane column, kept
+//                in shared memory two columns at a time, x e^{i q dxi}, and the
+//                bilinear gather of every polar sample whose stencil lies in
+//                that column pair  -> Y = F[ring][l']  (the N x N/2 spectrum
+//                never reaches global memory)
+//   k_rings_fwd  steps 4-5a: per ring, length-n_phi DFT (Eq. eq3) and the
+//                per-mode multiplier i^k dlam lam_j J_k(lam_j)/n_phi
+//                -> X = C[k][j]; low-mode rings -> two coefficients per ring
+//   k_modes_fwd  step 5b: per mode, cosine sum over j (DCT-I through a
+//                length-2M FFT of the even extension, Eq. inverse_cos_tr) plus
+//                the clustered low-mode quadrature for k = 0, 1  -> Y = G[k][m]
+//   k_theta_fwd  steps 6-7: per time sample, inverse DFT over the modes
+//                (Eq. FourSerForg; two time samples per complex FFT), arc mask
+//                -> g[d][m]
+// Adjoint: the same five kernels transposed, in reverse order.  Only the
+// half plane q_x >= 0 of the spectrum and the half circle phi in [-pi/2, pi/2)
+// are processed; the other halves follow from Hermitian symmetry (f real).
+#pragma once
+
+#include "fft.cuh"
+#include "plan.hpp"
+
+namespace tat {
+namespace {
+
+__device__ __forceinline__ float2 mul_ipow(float2 v, int k) {  // v * i^k
+  switch (k & 3) {
+    case 1: return make_float2(-v.y, v.x);
+    case 2: return make_float2(-v.x, -v.y);
+    case 3: return make_float2(v.y, -v.x);
+    default: return v;
+  }
+}
+__device__ __forceinline__ float2 mul_mipow(float2 v, int k) {  // v * (-i)^k
+  switch (k & 3) {
+    case 1: return make_float2(v.y, -v.x);
+    case 2: return make_float2(-v.x, -v.y);
+    case 3: return make_float2(-v.y, v.x);
+    default: return v;
+  }
+}
+__device__ __forceinline__ int wrapN(int q, int N) { return q < 0 ? q + N : q; }
+
+// ------------------------------------------------------------------ forward
+
+template <int L>
+__global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __restrict__ f, long long fs, float2* __restrict__ X,
+                           long long xs, int RP, int nt) {
+  extern __shared__ float2 sm[];
+  const int b = blockIdx.y;
+  const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
+  const int SL = spad_len(P.N);
+  float2* buf = sm + g * SL;
+  const int pair = blockIdx.x * RP + g;
+  const int iy1 = 2 * pair, iy2 = 2 * pair + 1;
+  const bool v1 = iy1 < P.n, v2 = iy2 < P.n;
+  const float* fb = f + (size_t)b * fs;
+  const int2 r1 = v1 ? P.rowrange[iy1] : make_int2(0, 0);
+  const int2 r2 = v2 ? P.rowrange[iy2] : make_int2(0, 0);
+  for (int ix = gt; ix < P.N; ix += nt) {
+    float a = 0.f, c = 0.f;
+    if (ix >= r1.x && ix < r1.y) a = fb[(size_t)iy1 * P.n + ix];
+    if (ix >= r2.x && ix < r2.y) c = fb[(size_t)iy2 * P.n + ix];
+    buf[spad(ix)] = make_float2(a, c);
+  }
+  __syncthreads();
+  fft<L, false>(buf, P.fN, gt, nt);
+  float2* Xb = X + (size_t)b * xs;
+  for (int q = gt; q < P.ncol; q += nt) {
+    const float2 Z = buf[spad(q)];
+    const float2 Zc = cconj(buf[spad(q == 0 ? 0 : P.N - q)]);
+    const float2 x1 = cscale(cadd(Z, Zc), 0.5f);
+    const float2 dd = csub(Z, Zc);
+    const float2 x2 = make_float2(0.5f * dd.y, -0.5f * dd.x);
+    const float2 ph = cscale(P.phase[q], P.h2_2pi);
+    if (v1) Xb[(size_t)iy1 * P.ncol + q] = cmul(ph, x1);
+    if (v2) Xb[(size_t)iy2 * P.ncol + q] = cmul(ph, x2);
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(512) k_cols_fwd(DevPlan P, const float2* __restrict__ X, long long xs, float2* __restrict__ Y,
+                           long long ys, int S, int nt) {
+  extern __shared__ float2 sm[];
+  const int b = blockIdx.y;
+  const int SL = spad_len(P.N);
+  float2* slot0 = sm;
+  float2* slot1 = sm + SL;
+  float2* stage = sm + 2 * SL;  // [n][S+1]
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int c0 = blockIdx.x * S;
+  const int c1 = min(c0 + S, P.ncol - 1);  // owned stencil columns i0 in [c0, c1)
+  const int ncols = c1 - c0 + 1;           // spectrum columns c0..c1
+  const float2* Xb = X + (size_t)b * xs;
+  for (int e = tid; e < P.n * ncols; e += NT) {
+    const int iy = e / ncols, cc = e % ncols;
+    stage[iy * (S + 1) + cc] = Xb[(size_t)iy * P.ncol + c0 + cc];
+  }
+  __syncthreads();
+  float2* Yb = Y + (size_t)b * ys;
+  const int N = P.N;
+#pragma unroll 1
+  for (int cc = 0; cc < ncols; ++cc) {
+    float2* buf = (cc & 1) ? slot1 : slot0;
+    for (int q = tid; q < N; q += NT) buf[spad(q)] = q < P.n ? stage[q * (S + 1) + cc] : make_float2(0.f, 0.f);
+    __syncthreads();
+    fft<L, false>(buf, P.fN, tid, nt);
+    if (cc > 0) {
+      const float2* A = (cc & 1) ? slot0 : slot1;  // column c0+cc-1
+      const float2* B = buf;                       // column c0+cc
+      const int ci = c0 + cc - 1;
+      const int e1 = P.coloff[ci + 1];
+      for (int e = P.coloff[ci] + tid; e < e1; e += NT) {
+        const PolarEntry pe = P.pts[e];
+        const int qa = wrapN(pe.k0, N), qb = wrapN(pe.k0 + 1, N);
+        const float a = pe.a, bb = pe.b;
+        const float2 va = cadd(cscale(A[spad(qa)], 1.f - a), cscale(B[spad(qa)], a));
+        const float2 vb = cadd(cscale(A[spad(qb)], 1.f - a), cscale(B[spad(qb)], a));
+        Yb[pe.p] = cadd(cscale(cmul(P.phase[qa], va), 1.f - bb), cscale(cmul(P.phase[qb], vb), bb));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ float block_sum(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  float s = 0.f;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)((blockDim.x + 31) >> 5); ++i) s += red[i];
+  return s;  // valid in thread 0
+}
+
+template <int L>
+__global__ void __launch_bounds__(1024) k_rings_fwd(DevPlan P, const float2* __restrict__ Y, long long ys, float2* __restrict__ X,
+                            long long xs, int RPC, int nt, int ntiles) {
+  extern __shared__ float2 sm[];
+  const int b = blockIdx.y;
+  const float2* Yb = Y + (size_t)b * ys;
+  float2* Xb = X + (size_t)b * xs;
+  const int J1 = P.J + 1;
+  if ((int)blockIdx.x >= ntiles) {
+    // Low-mode ring: only k = 0 and k = 1 are needed.  Over the full circle
+    // (F(phi + pi) = conj F(phi)):  sum_l F_l = 2 sum_half Re F,
+    // sum_l F_l e^{-i phi_l} = 2i sum_half Im F e^{-i phi}.
+    float* red = reinterpret_cast<float*>(sm);
+    const int q = blockIdx.x - ntiles;
+    const int r = P.J + 1 + q;
+    float s0 = 0.f, sx = 0.f, sy = 0.f;
+    for (int l = threadIdx.x; l < P.nh; l += blockDim.x) {
+      const float2 F = Yb[(size_t)r * P.nh + l];
+      const float2 cs = P.cs_half[l];
+      s0 += F.x;
+      sx += F.y * cs.x;
+      sy -= F.y * cs.y;
+    }
+    s0 = block_sum(s0, red);
+    sx = block_sum(sx, red + 32);
+    sy = block_sum(sy, red + 64);
+    if (threadIdx.x == 0) {
+      float2* Ch = Xb + (size_t)(P.K + 1) * J1;
+      const float2 S0 = make_float2(2.f * s0, 0.f);
+      const float2 S1 = make_float2(-2.f * sy, 2.f * sx);  // 2i (sx + i sy)
+      Ch[q] = cscale(S0, P.Bh[q]);
+      Ch[P.n_low + q] = mul_ipow(cscale(S1, P.Bh[P.n_low + q]), 1);
+    }
+    return;
+  }
+  const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
+  const int SL = spad_len(P.n_phi);
+  float2* buf = sm + g * SL;
+  const int rbase = 1 + blockIdx.x * RPC;
+  const int r = rbase + g;
+  const bool valid = r <= P.J;
+  const int q4 = P.n_phi / 4;
+  const float2* Fr = Yb + (size_t)r * P.nh;
+  for (int l = gt; l < P.n_phi; l += nt) {
+    float2 v = make_float2(0.f, 0.f);
+    if (valid) {
+      if (l < q4) v = Fr[l + q4];
+      else if (l < 3 * q4) v = cconj(Fr[l - q4]);
+      else v = Fr[l - 3 * q4];
+    }
+    buf[spad(l)] = v;
+  }
+  __syncthreads();
+  fft<L, false>(buf, P.fphi, gt, nt);
+  for (int e = threadIdx.x; e < (P.K + 1) * RPC; e += blockDim.x) {
+    const int k = e / RPC, gg = e % RPC;
+    const int rr = rbase + gg;
+    if (rr > P.J) continue;
+    const float bt = (P.low_on && k <= 1 && rr < kLowA) ? 0.f : P.Bt[(size_t)k * J1 + rr];
+    Xb[(size_t)k * J1 + rr] = mul_ipow(cscale(sm[gg * SL + spad(k)], bt), k);
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(1024) k_modes_fwd(DevPlan P, const float2* __restrict__ X, long long xs, float2* __restrict__ Y,
+                            long long ys, int nt) {
+  extern __shared__ float2 sm[];
+  const int b = blockIdx.y, k = blockIdx.x;
+  const int J1 = P.J + 1, L2 = 2 * P.M;
+  const float2* Cm = X + (size_t)b * xs + (size_t)k * J1;
+  for (int j = threadIdx.x; j < L2; j += blockDim.x) {
+    float2 v = make_float2(0.f, 0.f);
+    if (j >= 1 && j <= P.J) v = Cm[j];
+    else if (j >= L2 - P.J) v = Cm[L2 - j];
+    sm[spad(j)] = v;
+  }
+  __syncthreads();
+  fft<L, false>(sm, P.f2M, threadIdx.x, nt);
+  float2* G = Y + (size_t)b * ys + (size_t)k * P.n_t;
+  const bool low = P.low_on && k <= 1;
+  const float2* Ch = X + (size_t)b * xs + (size_t)(P.K + 1) * J1 + (size_t)k * P.n_low;
+  for (int m = threadIdx.x; m < P.n_t; m += blockDim.x) {
+    float2 v = cscale(sm[spad(m)], 0.5f);
+    if (low) {
+      for (int q = 0; q < P.n_low; ++q) {
+        const float c = P.Lcos[(size_t)q * P.n_t + m];
+        const float2 ch = Ch[q];
+        v.x += c * ch.x;
+        v.y += c * ch.y;
+      }
+    }
+    G[m] = v;
+  }
+}
+
+// Mode sum folded onto detector bin `bin` for time sample m: sum of g_k over
+// k in [-K, K) with k = bin (mod n_det); g_{-k} = conj(g_k), g_{-K} = G[K].
+__device__ __forceinline__ float2 folded_mode(const DevPlan& P, const float2* G, int bin, int m) {
+  if (P.n_phi == P.n_det) return G[(size_t)bin * P.n_t + m];
+  float2 acc = make_float2(0.f, 0.f);
+  int k = bin;
+  while (k - P.n_det >= -P.K) k -= P.n_det;
+  for (; k < P.K; k += P.n_det) {
+    float2 v;
+    if (k >= 0) v = G[(size_t)k * P.n_t + m];
+    else if (k == -P.K) v = G[(size_t)P.K * P.n_t + m];
+    else v = cconj(G[(size_t)(-k) * P.n_t + m]);
+    acc = cadd(acc, v);
+  }
+  return acc;
+}
+
+template <int L>
+__global__ void __launch_bounds__(1024) k_theta_fwd(DevPlan P, const float2* __restrict__ Y, long long ys, float* __restrict__ g,
+                            long long gs, int TT, int nt) {
+  extern __shared__ float2 sm[];
+  const int b = blockIdx.y;
+  const int m0 = blockIdx.x * TT;
+  const int npair = TT / 2;
+  const int SL = spad_len(P.n_det);
+  const int nd = P.n_det;
+  const float2* G = Y + (size_t)b * ys;
+  for (int e = threadIdx.x; e < (nd / 2 + 1) * npair; e += blockDim.x) {
+    const int bin = e / npair, p = e % npair;
+    const int m1 = m0 + 2 * p, m2 = m1 + 1;
+    float2 x1 = m1 < P.n_t ? folded_mode(P, G, bin, m1) : make_float2(0.f, 0.f);
+    float2 x2 = m2 < P.n_t ? folded_mode(P, G, bin, m2) : make_float2(0.f, 0.f);
+    if (bin == 0 || bin == nd / 2) { x1.y = 0.f; x2.y = 0.f; }
+    float2* z = sm + p * SL;
+    z[spad(bin)] = make_float2(x1.x - x2.y, x1.y + x2.x);
+    if (bin > 0 && bin < nd / 2) z[spad(nd - bin)] = make_float2(x1.x + x2.y, x2.x - x1.y);
+  }
+  __syncthreads();
+  {
+    const int gi = threadIdx.x / nt, gt = threadIdx.x % nt;
+    fft<L, true>(sm + gi * SL, P.fdet, gt, nt);
+  }
+  float* gb = g + (size_t)b * gs;
+  for (int e = threadIdx.x; e < nd * TT; e += blockDim.x) {
+    const int d = e / TT, tt = e % TT;
+    const int m = m0 + tt;
+    if (m >= P.n_t) continue;
+    const float2 z = sm[(tt >> 1) * SL + spad(d)];
+    gb[(size_t)d * P.n_t + m] = P.gamma[d] * ((tt & 1) ? z.y : z.x);
+  }
+}
+
+// ------------------------------------------------------------------ adjoint
+
+template <int L>
+__global__ void __launch_bounds__(1024) k_theta_adj(DevPlan P, const float* __restrict__ g, long long gs, float2* __restrict__ Y,
+                            long long ys, int TT, int nt) {
+  extern __shared__ float2 sm[];
+  const int b = blockIdx.y;
+  const int m0 = blockIdx.x * TT;
+  const int SL = spad_len(P.n_det);
+  const int nd = P.n_det;
+  const float* gb = g + (size_t)b * gs;
+  for (int e = threadIdx.x; e < nd * TT; e += blockDim.x) {
+    const int d = e / TT, tt = e % TT;
+    const int m = m0 + tt;
+    const float v = m < P.n_t ? P.gamma[d] * gb[(size_t)d * P.n_t + m] : 0.f;
+    float* z = reinterpret_cast<float*>(sm + (tt >> 1) * SL + spad(d));
+    z[tt & 1] = v;
+  }
+  __syncthreads();
+  {
+    const int gi = threadIdx.x / nt, gt = threadIdx.x % nt;
+    fft<L, false>(sm + gi * SL, P.fdet, gt, nt);
+  }
+  float2* Gp = Y + (size_t)b * ys;
+  for (int e = threadIdx.x; e < (P.K + 1) * TT; e += blockDim.x) {
+    const int k = e / TT, tt = e % TT;
+    const int m = m0 + tt;
+    if (m >= P.n_t) continue;
+    const int bin = k % nd;
+    const float2* z = sm + (tt >> 1) * SL;
+    const float2 Z = z[spad(bin)];
+    const float2 Zc = cconj(z[spad(bin == 0 ? 0 : nd - bin)]);
+    float2 x;
+    if (tt & 1) {
+      const float2 dd = csub(Z, Zc);
+      x = make_float2(0.5f * dd.y, -0.5f * dd.x);
+    } else {
+      x = cscale(cadd(Z, Zc), 0.5f);
+    }
+    Gp[(size_t)k * P.n_t + m] = x;
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(1024) k_modes_adj(DevPlan P, const float2* __restrict__ Y, long long ys, float2* __restrict__ X,
+                            long long xs, int nt) {
+  extern __shared__ float2 sm[];
+  const int b = blockIdx.y, k = blockIdx.x;
+  const int J1 = P.J + 1, L2 = 2 * P.M;
+  const float2* Gp = Y + (size_t)b * ys + (size_t)k * P.n_t;
+  for (int j = threadIdx.x; j < L2; j += blockDim.x) {
+    float2 v = make_float2(0.f, 0.f);
+    if (j < P.n_t) v = Gp[j];
+    else if (j > L2 - P.n_t) v = Gp[L2 - j];
+    sm[spad(j)] = v;
+  }
+  __syncthreads();
+  const float2 g0 = Gp[0];
+  fft<L, false>(sm, P.f2M, threadIdx.x, nt);
+  float2* Dm = X + (size_t)b * xs + (size_t)k * J1;
+  const bool low = P.low_on && k <= 1;
+  for (int j = threadIdx.x; j < J1; j += blockDim.x) {
+    float2 v = cscale(cadd(sm[spad(j)], g0), 0.5f);
+    if (low && j < kLowA) v = make_float2(0.f, 0.f);
+    Dm[j] = v;
+  }
+  if (low) {
+    // Dh[k][q] = sum_m cos(lam_q t_m) g'_k(t_m): one warp per low-mode node.
+    float2* Dh = X + (size_t)b * xs + (size_t)(P.K + 1) * J1 + (size_t)k * P.n_low;
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int q = w; q < P.n_low; q += nw) {
+      float sx = 0.f, sy = 0.f;
+      for (int m = l; m < P.n_t; m += 32) {
+        const float c = P.Lcos[(size_t)q * P.n_t + m];
+        const float2 v = Gp[m];
+        sx += c * v.x;
+        sy += c * v.y;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      }
+      if (l == 0) Dh[q] = make_float2(sx, sy);
+    }
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __restrict__ X, long long xs, float2* __restrict__ Y,
+                            long long ys, int RPC, int nt, int ntiles) {
+  extern __shared__ float2 sm[];
+  const int b = blockIdx.y;
+  const float2* Xb = X + (size_t)b * xs;
+  float2* Yb = Y + (size_t)b * ys;
+  const int J1 = P.J + 1;
+  if ((int)blockIdx.x >= ntiles) {
+    // Low-mode ring: F'(phi) = c0 + c1 e^{i phi} + c_{-1} e^{-i phi}, c_{-1} = -conj(c1).
+    const int q = blockIdx.x - ntiles;
+    const int r = P.J + 1 + q;
+    const float2* Dh = Xb + (size_t)(P.K + 1) * J1;
+    const float2 c0 = cscale(Dh[q], P.Bh[q]);
+    const float2 c1 = mul_mipow(cscale(Dh[P.n_low + q], P.Bh[P.n_low + q]), 1);
+    const float2 cm = make_float2(-c1.x, c1.y);
+    for (int l = threadIdx.x; l < P.nh; l += blockDim.x) {
+      const float2 cs = P.cs_half[l];
+      const float2 e = cs, ec = cconj(cs);
+      Yb[(size_t)r * P.nh + l] = cadd(c0, cadd(cmul(c1, e), cmul(cm, ec)));
+    }
+    return;
+  }
+  const int SL = spad_len(P.n_phi);
+  const int rbase = 1 + blockIdx.x * RPC;
+  for (int e = threadIdx.x; e < (P.K + 1) * RPC; e += blockDim.x) {
+    const int k = e / RPC, gg = e % RPC;
+    const int rr = rbase + gg;
+    float2 w = make_float2(0.f, 0.f);
+    if (rr <= P.J && !(P.low_on && k <= 1 && rr < kLowA))
+      w = mul_mipow(cscale(Xb[(size_t)k * J1 + rr], P.Bt[(size_t)k * J1 + rr]), k);
+    float2* bg = sm + gg * SL;
+    bg[spad(k)] = w;
+    if (k >= 1 && k < P.K) {
+      const float2 wc = cconj(w);
+      bg[spad(P.n_phi - k)] = (k & 1) ? make_float2(-wc.x, -wc.y) : wc;
+    }
+  }
+  __syncthreads();
+  const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
+  float2* buf = sm + g * SL;
+  fft<L, true>(buf, P.fphi, gt, nt);
+  const int r = rbase + g;
+  if (r <= P.J) {
+    const int q4 = P.n_phi / 4;
+    for (int l = gt; l < P.nh; l += nt) {
+      int s = l - q4;
+      if (s < 0) s += P.n_phi;
+      Yb[(size_t)r * P.nh + l] = buf[spad(s)];
+    }
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(512) k_cols_adj(DevPlan P, const float2* __restrict__ Y, long long ys, float2* __restrict__ X,
+                           long long xs, int S, int nt) {
+  extern __shared__ float2 sm[];
+  const int b = blockIdx.y;
+  const int N = P.N;
+  const int SL = spad_len(N);
+  float2* slot = sm;
+  float2* stage = sm + SL;  // [n][S]
+  const int tid = threadIdx.x, NT = blockDim.x;
+  const int c0 = blockIdx.x * S;
+  const int c1 = min(c0 + S, P.ncol);
+  const float2* Yb = Y + (size_t)b * ys;
+#pragma unroll 1
+  for (int c = c0; c < c1; ++c) {
+    for (int q = tid; q < SL; q += NT) slot[q] = make_float2(0.f, 0.f);
+    __syncthreads();
+    // Transposed bilinear weights: points whose stencil has column c on the
+    // left (i0 = c, weight 1-a) or on the right (i0 = c-1, weight a).
+    for (int side = 0; side < 2; ++side) {
+      const int ci = side == 0 ? c : c - 1;
+      if (ci < 0 || ci > P.ncol - 2) continue;
+      const int e1 = P.coloff[ci + 1];
+      for (int e = P.coloff[ci] + tid; e < e1; e += NT) {
+        const PolarEntry pe = P.pts[e];
+        const float wa = side == 0 ? 1.f - pe.a : pe.a;
+        const float2 val = Yb[pe.p];
+        const int qa = wrapN(pe.k0, N), qb = wrapN(pe.k0 + 1, N);
+        const float2 va = cscale(cmulc(val, P.phase[qa]), wa * (1.f - pe.b));
+        const float2 vb = cscale(cmulc(val, P.phase[qb]), wa * pe.b);
+        atomicAdd(&slot[spad(qa)].x, va.x);
+        atomicAdd(&slot[spad(qa)].y, va.y);
+        atomicAdd(&slot[spad(qb)].x, vb.x);
+        atomicAdd(&slot[spad(qb)].y, vb.y);
+      }
+    }
+    __syncthreads();
+    if (c == 0) {
+      // Column 0 also receives the mirrored samples of the other half circle:
+      // F'(0, q) += conj(F'(0, -q)).
+      for (int q = tid; q <= N / 2 - 1; q += NT) {
+        if (q == 0) {
+          const float2 s = slot[0];
+          slot[0] = make_float2(2.f * s.x, 0.f);
+        } else {
+          const float2 A = slot[spad(q)], B = slot[spad(N - q)];
+          slot[spad(q)] = cadd(A, cconj(B));
+          slot[spad(N - q)] = cadd(B, cconj(A));
+        }
+      }
+      __syncthreads();
+    }
+    fft<L, true>(slot, P.fN, tid, nt);
+    for (int iy = tid; iy < P.n; iy += NT) stage[iy * S + (c - c0)] = slot[spad(iy)];
+    __syncthreads();
+  }
+  float2* Xb = X + (size_t)b * xs;
+  const int w = c1 - c0;
+  for (int e = tid; e < P.n * w; e += NT) {
+    const int iy = e / w, cc = e % w;
+    Xb[(size_t)iy * P.ncol + c0 + cc] = stage[iy * S + cc];
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(1024) k_rows_adj(DevPlan P, const float2* __restrict__ X, long long xs, float* __restrict__ f,
+                           long long fs, int RP, int nt) {
+  extern __shared__ float2 sm[];
+  const int b = blockIdx.y;
+  const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
+  const int N = P.N;
+  const int SL = spad_len(N);
+  float2* buf = sm + g * SL;
+  const int pair = blockIdx.x * RP + g;
+  const int iy1 = 2 * pair, iy2 = 2 * pair + 1;
+  const bool v1 = iy1 < P.n, v2 = iy2 < P.n;
+  const float2* Xb = X + (size_t)b * xs;
+  for (int q = gt; q < N; q += nt) {
+    float2 z = make_float2(0.f, 0.f);
+    if (q != N / 2) {
+      const int qq = q < N / 2 ? q : N - q;
+      float2 h1 = v1 ? cmulc(Xb[(size_t)iy1 * P.ncol + qq], P.phase[qq]) : make_float2(0.f, 0.f);
+      float2 h2 = v2 ? cmulc(Xb[(size_t)iy2 * P.ncol + qq], P.phase[qq]) : make_float2(0.f, 0.f);
+      if (qq == 0) { h1.y = 0.f; h2.y = 0.f; }
+      if (q > N / 2) { h1 = cconj(h1); h2 = cconj(h2); }
+      z = make_float2(h1.x - h2.y, h1.y + h2.x);
+    }
+    buf[spad(q)] = z;
+  }
+  __syncthreads();
+  fft<L, true>(buf, P.fN, gt, nt);
+  float* fb = f + (size_t)b * fs;
+  const int2 r1 = v1 ? P.rowrange[iy1] : make_int2(0, 0);
+  const int2 r2 = v2 ? P.rowrange[iy2] : make_int2(0, 0);
+  for (int ix = gt; ix < P.n; ix += nt) {
+    const float2 z = buf[spad(ix)];
+    if (v1) fb[(size_t)iy1 * P.n + ix] = (ix >= r1.x && ix < r1.y) ? P.adj_scale * z.x : 0.f;
+    if (v2) fb[(size_t)iy2 * P.n + ix] = (ix >= r2.x && ix < r2.y) ? P.adj_scale * z.y : 0.f;
+  }
+}
+
+}  // namespace
+}  // namespace tat

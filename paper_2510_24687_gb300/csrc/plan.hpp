@@ -1,0 +1,110 @@
+// Internal plan layout shared by the host plan builder (plan.cpp), the CUDA
+// kernels (kernels.cu) and the C ABI (capi.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "tat.h"
+
+namespace tat {
+
+// Number of trapezoid nodes j = 0..kLowA-1 replaced by the clustered
+// low-mode quadrature, and its number of Gauss-Legendre nodes (Section 3.1:
+// "discretization points clustering toward lambda = 0" for k = -1, 0, 1).
+constexpr int kLowA = 8;
+constexpr int kLowM = 20;
+
+constexpr int kMaxPass = 16;
+
+// One FFT length: radix schedule and its twiddle table e^{-2 pi i k/L}, k < L.
+struct FftDev {
+  int L;
+  int npass;
+  int radix[kMaxPass];
+  const float2* tw;
+};
+
+// One half-plane polar sample: polar slot p (ring*nh + l'), stencil row k0
+// (signed frequency index) and bilinear weights a, b.  Points are sorted by
+// stencil column i0 (implicit in the column offsets), then by k0.
+struct PolarEntry {
+  int p;
+  int k0;
+  float a;
+  float b;
+};
+
+// Everything a kernel needs, passed by value.
+struct DevPlan {
+  int n, n_det, n_t;
+  int N, M, J, n_phi, K, nh;       // K = n_phi/2, nh = n_phi/2 (half circle)
+  int n_low, n_rings;              // n_rings = J + 1 + n_low
+  int ncol;                        // N/2 half-plane columns
+  int low_on;
+  float h2_2pi;                    // h^2 / (2 pi)
+  float adj_scale;                 // (h^2/2pi) * W_Y / W_X
+  FftDev fN, fphi, f2M, fdet;
+  const float2* phase;             // [N] e^{i q dxi}, q the signed frequency of FFT bin
+  const int2* rowrange;            // [n] support columns [lo, hi) of each image row
+  const float* gamma;              // [n_det] 1 on the arc Gamma, else 0
+  const PolarEntry* pts;           // [n_points]
+  const int* coloff;               // [ncol+1] points with i0 = c: [coloff[c], coloff[c+1])
+  const float* Bt;                 // [(K+1) x (J+1)] dlam*lam_j*J_k(lam_j)/n_phi
+  const float* Bh;                 // [2 x n_low]     w_q*dlam*lam_q*J_k(lam_q)/n_phi
+  const float* Lcos;               // [n_low x n_t]   cos(lam_q t_m)
+  const float2* cs_half;           // [nh] (cos phi, sin phi) of the half-circle angles
+};
+
+// Launch shapes (host-side knobs; chosen per plan).
+struct LaunchCfg {
+  int rows_pairs;     // row pairs per CTA in the row pass
+  int strip;          // owned columns per CTA in the column pass
+  int rings_per_cta;  // rings per CTA in the angular pass
+  int t_tile;         // time samples per CTA in the theta pass (even)
+  int nt_N, nt_phi, nt_2M, nt_det;  // threads per FFT of each length
+};
+
+}  // namespace tat
+
+struct tat_plan_s {
+  tat_plan_desc desc;
+  int device;
+  tat::DevPlan d;
+  tat::LaunchCfg cfg;
+  tat_plan_info info;
+  // sizes of the per-image workspace regions, in float2 elements
+  size_t ws_x;  // row spectra / per-mode coefficients
+  size_t ws_y;  // polar samples / time modes
+  std::vector<void*> allocations;  // device memory owned by the plan
+};
+
+namespace tat {
+// Grid integers and spacings derived from a plan descriptor (host only).
+struct Grids {
+  double Tn, h, dt, T_ext, dlam, dxi, lam_c;
+  long long M, N, J;
+  int n_phi;
+  bool low_on;
+};
+// plan.cpp
+tat_status derive_grids(const tat_plan_desc& desc, Grids* g);
+void fill_info(const Grids& g, tat_plan_info* info);
+tat_status build_plan(const tat_plan_desc& desc, tat_plan_s* plan);
+void free_plan(tat_plan_s* plan);
+// host-side FP64 helpers (exported for the C ABI self-tests)
+void cos_sin_2pi(long long num, long long den, double* c, double* s);
+long long smooth_ceil(double x, bool even);
+void bessel_orders(double x, int kmax, double* out);
+void low_mode_rule(double* nodes, double* weights);
+// kernels.cu
+tat_status configure_kernels();
+tat_status validate_shapes(const tat_plan_s* P);
+tat_status launch_forward(const tat_plan_s* P, int batch, const float* f, long long fs,
+                          float* g, long long gs, void* ws, cudaStream_t st);
+tat_status launch_adjoint(const tat_plan_s* P, int batch, const float* g, long long gs,
+                          float* f, long long fs, void* ws, cudaStream_t st);
+}  // namespace tat

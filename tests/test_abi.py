@@ -1,0 +1,79 @@
+"""The C ABI library builds, loads and exports every function include/*.h declares.
+
+Host-only calls are exercised here; nothing launches GPU work.
+"""
+import math
+
+import pytest
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_24687_gb300 as p
+    return p
+
+
+def test_exports_every_declared_symbol(pkg):
+    lib = pkg.load()
+    names = pkg.header_symbols()
+    assert "tat_plan_create" in names and "tat_forward_batched" in names
+    missing = [s for s in names if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_status_strings(pkg):
+    assert pkg.tat_status_string(0) == "ok"
+    assert pkg.tat_status_string(1) == "invalid argument"
+    assert pkg.tat_status_string(4) == "CUDA error"
+    assert pkg.tat_status_string(99) == "unknown status"
+
+
+@pytest.mark.parametrize("bad", [
+    dict(n=4), dict(n_det=7), dict(n_det=130, n_phi=130), dict(n_t=3), dict(c=0.0), dict(R=-1.0),
+    dict(T=0.0), dict(n_phi=64), dict(support_radius=0.0), dict(pad_L=-1.0),
+])
+def test_query_rejects_invalid_descriptors(pkg, bad):
+    d = pkg.tat_plan_desc_default(64, 128, 128)
+    for k, v in bad.items():
+        setattr(d, k, v)
+    with pytest.raises(pkg.TatError) as e:
+        pkg.tat_plan_query(d)
+    assert e.value.status == 1
+
+
+def test_unsupported_sizes(pkg):
+    d = pkg.tat_plan_desc_default(4000, 8000, 8000)     # padded grid beyond 16384
+    with pytest.raises(pkg.TatError) as e:
+        pkg.tat_plan_query(d)
+    assert e.value.status == 2
+
+
+def test_null_handles_are_rejected(pkg):
+    lib = pkg.load()
+    assert lib.tat_forward(None, None, None, None, None) == 1
+    assert lib.tat_adjoint_batched(None, 1, None, 0, None, 0, None, None) == 1
+    assert lib.tat_plan_destroy(None) == 1
+    assert lib.tat_workspace_size(None, 1) == 0
+
+
+def test_plan_create_without_device_fails_cleanly(pkg):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(pkg.TatError) as e:
+        pkg.tat_plan_create(64, 128, 128)
+    assert e.value.status == 4
+    # argument errors are reported before any CUDA call
+    with pytest.raises(pkg.TatError) as e:
+        pkg.tat_plan_create(64, 127, 128)
+    assert e.value.status == 1
+
+
+def test_default_descriptor_is_the_papers(pkg):
+    d = pkg.tat_plan_desc_default(257, 360, 513, 1.0, 1.0, 4.0)
+    assert d.support_radius == 0.98 and d.low_mode_quadrature == 1
+    assert d.arc_begin == 0.0 and abs(d.arc_len - 2 * math.pi) < 1e-15
+    info = pkg.tat_plan_query(d)
+    assert info["n_phi"] == 360 and info["K"] == 180

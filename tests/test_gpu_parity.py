@@ -1,0 +1,187 @@
+"""GPU parity: libtat's CUDA path against the FP64 oracle, through the C ABI.
+
+Bar: relative L2 error <= 1e-5 per image / per sinogram for FP32 device
+arithmetic against the FP64 oracle on identical (FP32-representable) inputs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import tat_oracle as O
+from tat_inputs import ellipse_phantom, random_sinogram
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_24687_gb300 as p
+    return p
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return t
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
+CASES = {
+    "n64": dict(n=64, n_det=128, n_t=128, support_radius=0.9),
+    "n64_nolow": dict(n=64, n_det=128, n_t=128, support_radius=0.9, low_mode_quadrature=0),
+    "n64_halfcircle": dict(n=64, n_det=128, n_t=128, support_radius=0.9, arc_begin=0.0, arc_len=math.pi),
+    "n64_arc120": dict(n=64, n_det=128, n_t=128, support_radius=0.9, arc_begin=math.pi / 6, arc_len=2 * math.pi / 3),
+    "n48_runtime_lengths": dict(n=48, n_det=96, n_t=100, support_radius=0.9),
+    "n33_odd": dict(n=33, n_det=64, n_t=70, support_radius=0.98),
+    "n64_fold": dict(n=64, n_det=64, n_t=128, support_radius=0.9, n_phi=256),
+    "n64_physical": dict(n=64, n_det=128, n_t=128, support_radius=0.9, c=1.5, R=0.8, T=1.6),
+    "n64_pad16": dict(n=64, n_det=128, n_t=128, support_radius=0.9, pad_L=16.0),
+}
+
+_ORACLE_KEYS = {"low_mode_quadrature": "low_mode"}
+
+
+def make(pkg, torch, kw):
+    desc = dict(kw)
+    n, nd, nt = desc.pop("n"), desc.pop("n_det"), desc.pop("n_t")
+    c, R, T = desc.pop("c", 1.0), desc.pop("R", 1.0), desc.pop("T", 2.0)
+    op = pkg.TatOperator(n, nd, nt, c=c, R=R, T=T, device="cuda:0", **desc)
+    okw = {_ORACLE_KEYS.get(k, k): (bool(v) if k == "low_mode_quadrature" else v) for k, v in desc.items()}
+    P = O.OraclePlan(n, nd, nt, c=c, R=R, T=T, **okw)
+    return op, P
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_forward_parity(pkg, torch, name):
+    op, P = make(pkg, torch, CASES[name])
+    f = f32(ellipse_phantom(P.n, 0))
+    g = op.forward(torch.tensor(f, dtype=torch.float32, device="cuda:0")).cpu().numpy()
+    ref = O.forward(P, f)
+    assert g.shape == (P.n_det, P.n_t)
+    assert rel(g, ref) <= TOL
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_adjoint_parity(pkg, torch, name):
+    op, P = make(pkg, torch, CASES[name])
+    gin = f32(random_sinogram(P.n_det, P.n_t, 1))
+    f = op.adjoint(torch.tensor(gin, dtype=torch.float32, device="cuda:0")).cpu().numpy()
+    ref = O.adjoint(P, gin)
+    assert f.shape == (P.n, P.n)
+    assert rel(f, ref) <= TOL
+
+
+def test_plan_matches_oracle_grid(pkg, torch):
+    op, P = make(pkg, torch, CASES["n64"])
+    info = op.info
+    assert (info["N"], info["M"], info["J"], info["n_phi"]) == (P.N, P.M, P.J, P.n_phi)
+
+
+def test_dot_product_fp32(pkg, torch):
+    """<A f, g>_Y = <f, A* g>_X with both sides computed by the CUDA path."""
+    op, P = make(pkg, torch, CASES["n64"])
+    f = f32(ellipse_phantom(64, 3))
+    g = f32(random_sinogram(128, 128, 4))
+    Af = op.forward(torch.tensor(f, dtype=torch.float32, device="cuda:0")).cpu().numpy().astype(np.float64)
+    Asg = op.adjoint(torch.tensor(g, dtype=torch.float32, device="cuda:0")).cpu().numpy().astype(np.float64)
+    lhs = P.W_Y * np.sum(Af * g)
+    rhs = P.W_X * np.sum(f * Asg)
+    # normalised by the Cauchy-Schwarz bound of both sides
+    scale = max(P.W_Y * np.linalg.norm(Af) * np.linalg.norm(g), P.W_X * np.linalg.norm(f) * np.linalg.norm(Asg))
+    assert abs(lhs - rhs) <= 1e-5 * scale
+
+
+def test_batched_equals_single_and_strides(pkg, torch):
+    op, P = make(pkg, torch, CASES["n64"])
+    B = 5
+    fs = np.stack([f32(ellipse_phantom(64, s)) for s in range(B)])
+    # padded stride between images
+    pad = np.zeros((B, 64 * 64 + 37), np.float32)
+    pad[:, : 64 * 64] = fs.reshape(B, -1)
+    fpad = torch.tensor(pad, device="cuda:0")
+    g = torch.empty((B, 128 * 128 + 5), dtype=torch.float32, device="cuda:0")
+    ws = op.workspace(B)
+    pkg.tat_forward_batched(op.plan, B, fpad.data_ptr(), pad.shape[1], g.data_ptr(), g.shape[1], ws.data_ptr(),
+                            torch.cuda.current_stream().cuda_stream)
+    gb = g[:, : 128 * 128].reshape(B, 128, 128).cpu().numpy()
+    for s in range(B):
+        single = op.forward(torch.tensor(fs[s], dtype=torch.float32, device="cuda:0")).cpu().numpy()
+        assert np.array_equal(gb[s], single)
+        assert rel(gb[s], O.forward(P, fs[s])) <= TOL
+    gs = np.stack([f32(random_sinogram(128, 128, 10 + s)) for s in range(B)])
+    fa = op.adjoint(torch.tensor(gs, dtype=torch.float32, device="cuda:0")).cpu().numpy()
+    for s in (0, B - 1):
+        assert rel(fa[s], O.adjoint(P, gs[s])) <= TOL
+
+
+def test_zero_input_and_determinism(pkg, torch):
+    op, P = make(pkg, torch, CASES["n64"])
+    z = torch.zeros((2, 64, 64), dtype=torch.float32, device="cuda:0")
+    assert float(op.forward(z).abs().max()) == 0.0
+    zg = torch.zeros((2, 128, 128), dtype=torch.float32, device="cuda:0")
+    assert float(op.adjoint(zg).abs().max()) == 0.0
+    f = torch.tensor(f32(ellipse_phantom(64, 9)), dtype=torch.float32, device="cuda:0")
+    a, b = op.forward(f), op.forward(f)
+    assert torch.equal(a, b)
+
+
+def test_invalid_arguments(pkg, torch):
+    op, P = make(pkg, torch, CASES["n64"])
+    f = torch.zeros((64, 64), dtype=torch.float32, device="cuda:0")
+    g = torch.zeros((128, 128), dtype=torch.float32, device="cuda:0")
+    ws = op.workspace(1)
+    st = torch.cuda.current_stream().cuda_stream
+    with pytest.raises(pkg.TatError) as e:
+        pkg.tat_forward(op.plan, f.data_ptr(), g.data_ptr(), 0, st)
+    assert e.value.status == 1
+    with pytest.raises(pkg.TatError):
+        pkg.tat_forward(op.plan, f.data_ptr(), g.data_ptr(), ws.data_ptr() + 4, st)   # misaligned workspace
+    with pytest.raises(pkg.TatError):
+        pkg.tat_forward_batched(op.plan, 1, f.data_ptr(), 100, g.data_ptr(), 128 * 128, ws.data_ptr(), st)
+    with pytest.raises(pkg.TatError):
+        pkg.tat_forward_batched(op.plan, 0, f.data_ptr(), 64 * 64, g.data_ptr(), 128 * 128, ws.data_ptr(), st)
+
+
+def test_n256_batch32_sampled(pkg, torch):
+    """Batched workload n=256, 512 detectors x 512 samples, B=32: images 0 and 31 against the oracle."""
+    op, P = make(pkg, torch, dict(n=256, n_det=512, n_t=512, support_radius=0.9))
+    B = 32
+    fs = np.stack([f32(ellipse_phantom(256, s)) for s in range(B)])
+    g = op.forward(torch.tensor(fs, dtype=torch.float32, device="cuda:0")).cpu().numpy()
+    for s in (0, B - 1):
+        assert rel(g[s], O.forward(P, fs[s])) <= TOL
+    gs = np.stack([f32(random_sinogram(512, 512, 100 + s)) for s in (0, 1)])
+    gi = torch.zeros((B, 512, 512), dtype=torch.float32, device="cuda:0")
+    gi[0] = torch.tensor(gs[0], device="cuda:0")
+    gi[B - 1] = torch.tensor(gs[1], device="cuda:0")
+    fa = op.adjoint(gi).cpu().numpy()
+    assert rel(fa[0], O.adjoint(P, gs[0])) <= TOL
+    assert rel(fa[B - 1], O.adjoint(P, gs[1])) <= TOL
+    assert float(np.abs(fa[1:B - 1]).max()) == 0.0
+
+
+def test_headline_n512_full(pkg, torch):
+    """n=512, 1024 detectors x 1024 samples, in the batched launch the benchmark times (B=4 here)."""
+    op, P = make(pkg, torch, dict(n=512, n_det=1024, n_t=1024, support_radius=0.9))
+    B = 4
+    fs = np.stack([f32(ellipse_phantom(512, s)) for s in range(B)])
+    g = op.forward(torch.tensor(fs, dtype=torch.float32, device="cuda:0")).cpu().numpy()
+    assert rel(g[2], O.forward(P, fs[2])) <= TOL
+    gin = f32(random_sinogram(1024, 1024, 5))
+    gi = torch.tensor(np.stack([gin] * B), dtype=torch.float32, device="cuda:0")
+    fa = op.adjoint(gi).cpu().numpy()
+    assert rel(fa[1], O.adjoint(P, gin)) <= TOL
