@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""Throughput of the fast A / A* pair at n = 512 on GB300.
+
+One step = A then A* (Algorithms 1 and 2) over one batch of B = 32 seeded
+random-ellipse phantoms: n = 512, 1024 detectors x 1024 time samples on [0, 2],
+R = c = 1, support radius 0.9.  The batch's inputs and working set exceed the
+129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  `value` is A+A* pairs per second over all
+ranks (replicas: every rank runs its own batch, no collective on the data
+path).  `--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "A+A* pairs/s at n=512 FP32 (≤1e-5 rel L2 vs FP64 oracle), % of HBM roofline"
+N_IMG, N_DET, N_T, T_WIN, RSUP = 512, 1024, 1024, 2.0, 0.9
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0   # GB300: 152 SMs x 128 FP32 lanes, 2070 MHz max
+FWD_STAGES = ["rows_fwd", "cols_fwd", "rings_fwd", "modes_fwd", "theta_fwd"]
+ADJ_STAGES = ["theta_adj", "modes_adj", "rings_adj", "cols_adj", "rows_adj"]
+KERNEL_NAMES = {"rows_fwd": "k_rows_fwd", "cols_fwd": "k_cols_fwd", "rings_fwd": "k_rings_fwd",
+                "modes_fwd": "k_modes_fwd", "theta_fwd": "k_theta_fwd", "theta_adj": "k_theta_adj",
+                "modes_adj": "k_modes_adj", "rings_adj": "k_rings_adj", "cols_adj": "k_cols_adj",
+                "rows_adj": "k_rows_adj"}
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--batch", type=int, default=32)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2510_24687_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".cpp", ".hpp")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        reasons = set()
+        for r in rows:
+            for name, val in zip(["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"], r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
+
+
+def stage_flops(info, B):
+    """Algorithmic flops per launch of each stage (5 L log2 L per complex FFT of length L)."""
+    n, N, M, J, K, nphi, nlow = N_IMG, info["N"], info["M"], info["J"], info["K"], info["n_phi"], info["n_low"]
+    fft = lambda L: 5.0 * L * math.log2(L)
+    npts = info["n_points"]
+    rows = B * ((n + 1) // 2) * fft(N)
+    cols = B * ((N // 2) * fft(N) + 30.0 * npts)
+    rings = B * ((J + nlow) * fft(nphi) + 8.0 * (K + 1) * J)
+    modes = B * ((K + 1) * fft(2 * M) + 2.0 * 4 * nlow * N_T)
+    theta = B * ((N_T + 1) // 2) * fft(N_DET)
+    return {"rows_fwd": rows, "cols_fwd": cols, "rings_fwd": rings, "modes_fwd": modes, "theta_fwd": theta,
+            "rows_adj": rows, "cols_adj": cols, "rings_adj": rings, "modes_adj": modes, "theta_adj": theta}
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernels."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if t.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    v = t.get("dram_bytes_per_launch", {}).get(kernel)
+    return float(v) if v is not None else None
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+
+def time_oracle(sample_ops=2, seed=0):
+    """Times `sample_ops` oracle applications (A, A*, A, ...) at n = 512 on the host cores."""
+    import numpy as np
+    from oracle import tat_oracle as O
+    from tat_inputs import ellipse_phantom, random_sinogram
+    P = O.OraclePlan(N_IMG, N_DET, N_T, T=T_WIN, support_radius=RSUP)
+    f = ellipse_phantom(N_IMG, seed).astype(np.float32).astype(np.float64)
+    g = random_sinogram(N_DET, N_T, seed + 1)
+    t0 = time.perf_counter()
+    for i in range(sample_ops):
+        if i % 2 == 0:
+            g = O.forward(P, f)
+        else:
+            f = O.adjoint(P, g)
+    return time.perf_counter() - t0
+
+
+def cpu_threads():
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count() or 1
+
+
+def run_reference(args, rank, world):
+    unit = "pairs/s"
+    if rank != 0:
+        return
+    warm = min(args.warmup, 1)
+    for _ in range(warm):
+        time_oracle(1)
+    t = 0.0
+    for s in range(args.steps):
+        t += time_oracle(1, seed=s)     # one step = one operator application = half a pair
+    pairs = 0.5 * args.steps
+    value = pairs / t
+    sample = "one oracle application per step (A on even steps, A* on odd ones), n=512, n_det=n_t=1024"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": unit, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args.batch),
+            "cpu_baseline": {"value": value, "unit": unit, "cores": cpu_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(batch):
+    return {"workload": f"A+A* pair, n={N_IMG}, n_det={N_DET}, n_t={N_T}, T={T_WIN}, B={batch} per GPU",
+            "n": N_IMG, "n_det": N_DET, "n_t": N_T, "T": T_WIN, "support_radius": RSUP, "batch_per_gpu": batch,
+            "phantoms": "random ellipses, seeds rank*B..rank*B+B-1",
+            "l2": "inputs exceed L2 (batch inputs 160 MB + 0.5 GB working set per step), no flush"}
+
+
+# ------------------------------------------------------------------ GPU benchmark
+
+def main():
+    args = parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_24687_gb300 as pkg
+    from tat_inputs import phantom_batch
+
+    B = args.batch
+    op = pkg.TatOperator(N_IMG, N_DET, N_T, T=T_WIN, support_radius=RSUP, device=dev)
+    info = op.info
+    fh = phantom_batch(N_IMG, B, seed0=rank * B).astype(np.float32)
+    f = torch.tensor(fh, device=dev)
+    g = torch.empty((B, N_DET, N_T), dtype=torch.float32, device=dev)
+    f2 = torch.empty_like(f)
+    ws = op.workspace(B)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    fs, gs = N_IMG * N_IMG, N_DET * N_T
+
+    def step():
+        pkg.tat_forward_batched(op.plan, B, f.data_ptr(), fs, g.data_ptr(), gs, ws.data_ptr(), sptr)
+        pkg.tat_adjoint_batched(op.plan, B, g.data_ptr(), gs, f2.data_ptr(), fs, ws.data_ptr(), sptr)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+
+    # ---- main timed region: public batched API, device-resident inputs
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = B * args.steps * world / (ms / 1e3)
+
+    # ---- per-stage timing (same work, events between the five stages of each direction)
+    ksteps = max(3, min(args.steps, 10))
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(12)] for _ in range(ksteps)]
+    for row in evs:
+        for e in row:
+            e.record(stream)
+    torch.cuda.synchronize()
+    for row in evs:
+        pkg.tat_debug_forward_batched_timed(op.plan, B, f.data_ptr(), fs, g.data_ptr(), gs, ws.data_ptr(), sptr,
+                                            [e.cuda_event for e in row[:6]])
+        pkg.tat_debug_adjoint_batched_timed(op.plan, B, g.data_ptr(), gs, f2.data_ptr(), fs, ws.data_ptr(), sptr,
+                                            [e.cuda_event for e in row[6:]])
+    torch.cuda.synchronize()
+    stage_ms = {}
+    for i, name in enumerate(FWD_STAGES):
+        stage_ms[name] = statistics.mean(r[i].elapsed_time(r[i + 1]) for r in evs)
+    for i, name in enumerate(ADJ_STAGES):
+        stage_ms[name] = statistics.mean(r[6 + i].elapsed_time(r[7 + i]) for r in evs)
+    flops = stage_flops(info, B)
+    dom = max(stage_ms, key=stage_ms.get)
+    peak_alu = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops[dom] / (stage_ms[dom] / 1e3) / 1e12
+    roofline = {"bound": "alu", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": peak_alu,
+                "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": traffic_for(KERNEL_NAMES[dom]),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FP32 FMA, non-tensor)",
+                "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+                "stage_tflops": {k: round(flops[k] / (stage_ms[k] / 1e3) / 1e12, 3) for k in stage_ms}}
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    pair_bytes = 2 * (4 * N_IMG * N_IMG + 4 * N_DET * N_T)
+    hbm = {"compulsory_bytes_per_pair": pair_bytes, "achieved_gbs": value / world * pair_bytes / 1e9,
+           "peak_gbs": hbm_peak, "peak_source": "measured" if peaks else "fallback"}
+    hbm["frac"] = hbm["achieved_gbs"] / hbm_peak
+
+    # ---- end to end: pinned host buffers, copies inside the timed region
+    fh_pin = torch.from_numpy(fh).pin_memory()
+    out_pin = torch.empty_like(fh_pin).pin_memory()
+    fd = torch.empty_like(f)
+
+    def step_e2e():
+        fd.copy_(fh_pin, non_blocking=True)
+        pkg.tat_forward_batched(op.plan, B, fd.data_ptr(), fs, g.data_ptr(), gs, ws.data_ptr(), sptr)
+        pkg.tat_adjoint_batched(op.plan, B, g.data_ptr(), gs, f2.data_ptr(), fs, ws.data_ptr(), sptr)
+        out_pin.copy_(f2, non_blocking=True)
+
+    step_e2e()
+    torch.cuda.synchronize()
+    esteps = max(3, min(args.steps, 10))
+    barrier()
+    e0.record(stream)
+    for _ in range(esteps):
+        step_e2e()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ems = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ems], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ems = float(t.item())
+    e2e = {"value": B * esteps * world / (ems / 1e3), "unit": "pairs/s", "h2d_bytes_per_step": fh.nbytes,
+           "d2h_bytes_per_step": fh.nbytes, "steps": esteps}
+
+    # ---- CPU oracle on a bounded sample (rank 0, single GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ops = 2
+        t = time_oracle(ops)
+        cpu = {"value": 0.5 * ops / t, "unit": "pairs/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": "one A+A* pair of the n=512 workload (image seed 0) through the FP64 numpy/scipy oracle"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded random-ellipse phantoms; the paper's phantoms are not published)",
+                "config": workload_config(B), "roofline": roofline, "hbm_roofline_pair": hbm,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 10 * args.steps,
+                "clocks": clk, "plan": {k: info[k] for k in ("N", "M", "J", "n_phi", "n_low", "n_points")},
+                "kernel_source_hash": kernel_source_hash()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

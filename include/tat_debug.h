@@ -34,6 +34,18 @@ tat_status tat_debug_low_mode_rule(double* nodes, double* weights, int* count);
 tat_status tat_debug_stencils(const tat_plan_desc* desc, int* ring, int* lp, int* i0, int* k0, double* a,
                               double* b, int count);
 
+/* Same work as tat_forward_batched / tat_adjoint_batched, and additionally
+ * records events[0] on `stream` before the first stage and events[s] after
+ * stage s, s = 1..5 (forward: rows, columns, rings, modes, detectors; adjoint:
+ * detectors, modes, rings, columns, rows).  `events` holds 6 caller-created
+ * cudaEvent_t handles; the calls are for per-stage timing only. */
+tat_status tat_debug_forward_batched_timed(tat_plan_t plan, int batch, const float* f, long long f_stride,
+                                           float* g, long long g_stride, void* workspace, tat_stream_t stream,
+                                           void* const* events);
+tat_status tat_debug_adjoint_batched_timed(tat_plan_t plan, int batch, const float* g, long long g_stride,
+                                           float* f, long long f_stride, void* workspace, tat_stream_t stream,
+                                           void* const* events);
+
 #ifdef __cplusplus
 }
 #endif

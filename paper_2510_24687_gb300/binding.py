@@ -77,6 +77,8 @@ def load() -> ctypes.CDLL:
         "tat_debug_stencils": (_I, [ctypes.POINTER(tat_plan_desc), ctypes.POINTER(_I), ctypes.POINTER(_I),
                                     ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D),
                                     ctypes.POINTER(_D), _I]),
+        "tat_debug_forward_batched_timed": (_I, [_P, _I, _P, _LL, _P, _LL, _P, _P, ctypes.POINTER(_P)]),
+        "tat_debug_adjoint_batched_timed": (_I, [_P, _I, _P, _LL, _P, _LL, _P, _P, ctypes.POINTER(_P)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -159,6 +161,22 @@ def tat_forward_batched(plan, batch, f_ptr, f_stride, g_ptr, g_stride, ws_ptr, s
 def tat_adjoint_batched(plan, batch, g_ptr, g_stride, f_ptr, f_stride, ws_ptr, stream=0):
     _check(load().tat_adjoint_batched(plan, batch, g_ptr, g_stride, f_ptr, f_stride, ws_ptr, stream or None),
            "tat_adjoint_batched")
+
+
+def _events(evs):
+    arr = (_P * len(evs))(*evs)
+    return arr
+
+
+def tat_debug_forward_batched_timed(plan, batch, f_ptr, f_stride, g_ptr, g_stride, ws_ptr, stream, events):
+    """events: 6 raw cudaEvent_t handles (e.g. torch.cuda.Event(...).cuda_event after one record())."""
+    _check(load().tat_debug_forward_batched_timed(plan, batch, f_ptr, f_stride, g_ptr, g_stride, ws_ptr,
+                                                  stream or None, _events(events)), "tat_debug_forward_batched_timed")
+
+
+def tat_debug_adjoint_batched_timed(plan, batch, g_ptr, g_stride, f_ptr, f_stride, ws_ptr, stream, events):
+    _check(load().tat_debug_adjoint_batched_timed(plan, batch, g_ptr, g_stride, f_ptr, f_stride, ws_ptr,
+                                                  stream or None, _events(events)), "tat_debug_adjoint_batched_timed")
 
 
 def tat_status_string(status: int) -> str:

@@ -5,7 +5,7 @@
 namespace tat {
 
 tat_status launch_adjoint(const tat_plan_s* Pl, int batch, const float* g, long long gs, float* f, long long fs,
-                          void* ws, cudaStream_t st) {
+                          void* ws, cudaStream_t st, cudaEvent_t const* ev) {
   const DevPlan& P = Pl->d;
   const LaunchCfg& c = Pl->cfg;
   const Shapes s = shapes(Pl, batch);
@@ -14,27 +14,37 @@ tat_status launch_adjoint(const tat_plan_s* Pl, int batch, const float* g, long 
   const long long xs = (long long)Pl->ws_x, ys = (long long)Pl->ws_y;
   const int dev = Pl->device;
   bool ok = true;
+  int mark = 0;
+  auto stage_done = [&]() {
+    if (ev) cudaEventRecord(ev[mark++], st);
+  };
+  stage_done();
   dispatch_ang(P.n_det, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_theta_adj<L>>(dev);
     k_theta_adj<L><<<s.theta_grid, s.theta_block, s.theta_smem, st>>>(P, g, gs, Y, ys, c.t_tile, c.nt_det);
+    stage_done();
   });
   dispatch_2M(2 * P.M, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_modes_adj<L>>(dev);
     k_modes_adj<L><<<s.modes_grid, s.modes_block, s.modes_smem, st>>>(P, Y, ys, X, xs, c.nt_2M);
+    stage_done();
   });
   dispatch_ang(P.n_phi, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_rings_adj<L>>(dev);
     k_rings_adj<L><<<s.rings_grid, s.rings_block, s.rings_smem, st>>>(P, X, xs, Y, ys, c.rings_per_cta, c.nt_phi,
                                                                       s.ntiles);
+    stage_done();
   });
   dispatch_N(P.N, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_cols_adj<L>>(dev) && ensure_smem<k_rows_adj<L>>(dev);
     k_cols_adj<L><<<s.cols_grid_a, s.cols_block, s.cols_smem_a, st>>>(P, Y, ys, X, xs, c.strip, c.nt_N);
+    stage_done();
     k_rows_adj<L><<<s.rows_grid, s.rows_block, s.rows_smem, st>>>(P, X, xs, f, fs, c.rows_pairs, c.nt_N);
+    stage_done();
   });
   return check_launch(ok);
 }

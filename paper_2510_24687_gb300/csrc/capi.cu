@@ -178,6 +178,32 @@ tat_status tat_debug_stencils(const tat_plan_desc* desc, int* ring, int* lp, int
   return TAT_OK;
 }
 
+tat_status tat_debug_forward_batched_timed(tat_plan_t plan, int batch, const float* f, long long f_stride,
+                                           float* g, long long g_stride, void* workspace, tat_stream_t stream,
+                                           void* const* events) {
+  if (!plan || batch < 1 || !events) return TAT_ERR_INVALID_ARG;
+  const tat::DevPlan& d = plan->d;
+  if (f_stride < (long long)d.n * d.n || g_stride < (long long)d.n_det * d.n_t) return TAT_ERR_INVALID_ARG;
+  tat_status s = check_pointers(f, g, workspace);
+  if (s == TAT_OK) s = check_device(plan);
+  if (s != TAT_OK) return s;
+  return tat::launch_forward(plan, batch, f, f_stride, g, g_stride, workspace, static_cast<cudaStream_t>(stream),
+                             reinterpret_cast<cudaEvent_t const*>(events));
+}
+
+tat_status tat_debug_adjoint_batched_timed(tat_plan_t plan, int batch, const float* g, long long g_stride,
+                                           float* f, long long f_stride, void* workspace, tat_stream_t stream,
+                                           void* const* events) {
+  if (!plan || batch < 1 || !events) return TAT_ERR_INVALID_ARG;
+  const tat::DevPlan& d = plan->d;
+  if (f_stride < (long long)d.n * d.n || g_stride < (long long)d.n_det * d.n_t) return TAT_ERR_INVALID_ARG;
+  tat_status s = check_pointers(g, f, workspace);
+  if (s == TAT_OK) s = check_device(plan);
+  if (s != TAT_OK) return s;
+  return tat::launch_adjoint(plan, batch, g, g_stride, f, f_stride, workspace, static_cast<cudaStream_t>(stream),
+                             reinterpret_cast<cudaEvent_t const*>(events));
+}
+
 const char* tat_status_string(tat_status s) {
   switch (s) {
     case TAT_OK: return "ok";

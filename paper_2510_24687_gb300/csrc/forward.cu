@@ -23,7 +23,7 @@ tat_status validate_shapes(const tat_plan_s* Pl) {
 }
 
 tat_status launch_forward(const tat_plan_s* Pl, int batch, const float* f, long long fs, float* g, long long gs,
-                          void* ws, cudaStream_t st) {
+                          void* ws, cudaStream_t st, cudaEvent_t const* ev) {
   const DevPlan& P = Pl->d;
   const LaunchCfg& c = Pl->cfg;
   const Shapes s = shapes(Pl, batch);
@@ -32,27 +32,37 @@ tat_status launch_forward(const tat_plan_s* Pl, int batch, const float* f, long 
   const long long xs = (long long)Pl->ws_x, ys = (long long)Pl->ws_y;
   const int dev = Pl->device;
   bool ok = true;
+  int mark = 0;
+  auto stage_done = [&]() {
+    if (ev) cudaEventRecord(ev[mark++], st);
+  };
+  stage_done();
   dispatch_N(P.N, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_rows_fwd<L>>(dev) && ensure_smem<k_cols_fwd<L>>(dev);
     k_rows_fwd<L><<<s.rows_grid, s.rows_block, s.rows_smem, st>>>(P, f, fs, X, xs, c.rows_pairs, c.nt_N);
+    stage_done();
     k_cols_fwd<L><<<s.cols_grid_f, s.cols_block, s.cols_smem_f, st>>>(P, X, xs, Y, ys, c.strip, c.nt_N);
+    stage_done();
   });
   dispatch_ang(P.n_phi, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_rings_fwd<L>>(dev);
     k_rings_fwd<L><<<s.rings_grid, s.rings_block, s.rings_smem, st>>>(P, Y, ys, X, xs, c.rings_per_cta, c.nt_phi,
                                                                       s.ntiles);
+    stage_done();
   });
   dispatch_2M(2 * P.M, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_modes_fwd<L>>(dev);
     k_modes_fwd<L><<<s.modes_grid, s.modes_block, s.modes_smem, st>>>(P, X, xs, Y, ys, c.nt_2M);
+    stage_done();
   });
   dispatch_ang(P.n_det, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_theta_fwd<L>>(dev);
     k_theta_fwd<L><<<s.theta_grid, s.theta_block, s.theta_smem, st>>>(P, Y, ys, g, gs, c.t_tile, c.nt_det);
+    stage_done();
   });
   return check_launch(ok);
 }

@@ -103,8 +103,9 @@ void low_mode_rule(double* nodes, double* weights);
 // kernels.cu
 tat_status configure_kernels();
 tat_status validate_shapes(const tat_plan_s* P);
+// `ev` (optional): 6 events recorded before the first and after every stage.
 tat_status launch_forward(const tat_plan_s* P, int batch, const float* f, long long fs,
-                          float* g, long long gs, void* ws, cudaStream_t st);
+                          float* g, long long gs, void* ws, cudaStream_t st, cudaEvent_t const* ev = nullptr);
 tat_status launch_adjoint(const tat_plan_s* P, int batch, const float* g, long long gs,
-                          float* f, long long fs, void* ws, cudaStream_t st);
+                          float* f, long long fs, void* ws, cudaStream_t st, cudaEvent_t const* ev = nullptr);
 }  // namespace tat
