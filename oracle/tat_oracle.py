@@ -11,7 +11,7 @@ detection geometry", arXiv 2510.24687):
 * ``forward`` -- Algorithm 1, in the paper's order and notation:
   1. extend f by zero to the square [-L, L]^2 (Section 3.1, L ~ T_new + 2);
   2. 2D FFT -> fhat(xi) on a Cartesian grid, with the unitary convention
-     fhat(xi) = (1/2pi) int f(x) exp(-i xi.x) dx (Section 2.1);
+     fhat(xi) = (1/2pi) int f(x) exp(-i xi.x) dx (Section 2.1.1);
   3. bilinear interpolation to the polar grid (lambda_j, phi_l);
   4. per ring, Fourier coefficients fhat_k(lambda) in phi (Eq. eq3);
   5. g_k(t) = i^|k| int lambda fhat_k(lambda) J_|k|(lambda) cos(lambda t) dlambda
