@@ -129,6 +129,21 @@ tat_status tat_adjoint_batched(tat_plan_t plan, int batch, const float* g, long 
                                float* f, long long f_stride, void* workspace,
                                tat_stream_t stream);
 
+/* g = A f for one image, like tat_forward, but with no workspace argument: the
+ * scratch lives in a static 16 MiB device buffer inside the library.  The
+ * paper has no counterpart; this exists for callers that cannot allocate
+ * device memory when they need A (a process whose GPU memory is all handed to
+ * its own pool, or a loop that cannot afford cudaMalloc's implicit device
+ * synchronisation).  The call itself allocates nothing.  Every GPU that loads
+ * the library holds the 16 MiB until the process exits.  The first call on
+ * each device looks up the buffer's device address (cudaGetSymbolAddress), so
+ * make that first call before any stream capture.  All calls on a device
+ * share the one buffer: calls that overlap on the GPU (different streams or
+ * host threads) race and must be serialised by the caller.  Plans whose
+ * scratch exceeds 16 MiB (tat_workspace_size(plan, 1)) are rejected with
+ * TAT_ERR_UNSUPPORTED; n = 512 with 1024 detectors x 1024 samples fits. */
+tat_status tat_forward_noalloc(tat_plan_t plan, const float* f, float* g, tat_stream_t stream);
+
 /* Static string for a status code. */
 const char* tat_status_string(tat_status status);
 

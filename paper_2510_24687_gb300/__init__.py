@@ -8,13 +8,13 @@ whose C ABI is declared in include/tat.h; this package is its thin binding.
 from .binding import (TatError, TatOperator, header_symbols, load, tat_adjoint, tat_adjoint_batched,
                       tat_debug_adjoint_batched_timed, tat_debug_bessel, tat_debug_forward_batched_timed,
                       tat_debug_low_mode_rule, tat_debug_stencils, tat_forward,
-                      tat_forward_batched, tat_plan_create, tat_plan_create_ex, tat_plan_desc,
+                      tat_forward_batched, tat_forward_noalloc, tat_plan_create, tat_plan_create_ex, tat_plan_desc,
                       tat_plan_desc_default, tat_plan_destroy, tat_plan_get_info, tat_plan_info,
                       tat_plan_query, tat_status_string, tat_workspace_size)
 
 __all__ = ["TatError", "TatOperator", "header_symbols", "load", "tat_adjoint", "tat_adjoint_batched",
            "tat_debug_adjoint_batched_timed", "tat_debug_bessel", "tat_debug_forward_batched_timed",
            "tat_debug_low_mode_rule", "tat_debug_stencils", "tat_forward",
-           "tat_forward_batched", "tat_plan_create", "tat_plan_create_ex", "tat_plan_desc",
+           "tat_forward_batched", "tat_forward_noalloc", "tat_plan_create", "tat_plan_create_ex", "tat_plan_desc",
            "tat_plan_desc_default", "tat_plan_destroy", "tat_plan_get_info", "tat_plan_info", "tat_plan_query",
            "tat_status_string", "tat_workspace_size"]

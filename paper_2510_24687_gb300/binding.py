@@ -77,6 +77,7 @@ def load() -> ctypes.CDLL:
         "tat_debug_stencils": (_I, [ctypes.POINTER(tat_plan_desc), ctypes.POINTER(_I), ctypes.POINTER(_I),
                                     ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D),
                                     ctypes.POINTER(_D), _I]),
+        "tat_forward_noalloc": (_I, [_P, _P, _P, _P]),
         "tat_debug_forward_batched_timed": (_I, [_P, _I, _P, _LL, _P, _LL, _P, _P, ctypes.POINTER(_P)]),
         "tat_debug_adjoint_batched_timed": (_I, [_P, _I, _P, _LL, _P, _LL, _P, _P, ctypes.POINTER(_P)]),
     }
@@ -151,6 +152,11 @@ def tat_forward(plan, f_ptr, g_ptr, ws_ptr, stream=0):
 
 def tat_adjoint(plan, g_ptr, f_ptr, ws_ptr, stream=0):
     _check(load().tat_adjoint(plan, g_ptr, f_ptr, ws_ptr, stream or None), "tat_adjoint")
+
+
+def tat_forward_noalloc(plan, f_ptr, g_ptr, stream=0):
+    """A f for one image using the library's static scratch buffer (no workspace, no allocation)."""
+    _check(load().tat_forward_noalloc(plan, f_ptr, g_ptr, stream or None), "tat_forward_noalloc")
 
 
 def tat_forward_batched(plan, batch, f_ptr, f_stride, g_ptr, g_stride, ws_ptr, stream=0):
