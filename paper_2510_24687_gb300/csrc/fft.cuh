@@ -1,13 +1,21 @@
 // Shared-memory FFT core for the stages of Algorithms 1 and 2.
 //
-// Stockham autosort, decimation in time, mixed radix 8/4/3/2, natural order in
-// and out, unnormalised.  Each pass reads R elements with stride L/R, applies
-// the twiddles e^{-+2 pi i r (j mod Ns)/(Ns R)} from an FP64-derived table,
-// does a radix-R DFT in registers, synchronises, and writes the results back
-// in place at (j - j mod Ns) R + j mod Ns + r Ns.  A group of `nthr` threads
-// works on one transform; every thread holds at most 16 values per pass.
-// The buffer index is padded by one element per 32 to spread the strided
-// accesses over the shared-memory banks.
+// Stockham autosort, decimation in time, mixed radix 16/8/4/3/2, natural order
+// in and out, unnormalised.  Each pass reads R elements with stride L/R,
+// applies the twiddles e^{-+2 pi i r (j mod Ns)/(Ns R)}, does a radix-R DFT in
+// registers, synchronises, and writes the results back in place at
+// (j - j mod Ns) R + j mod Ns + r Ns.  A group of `nthr` threads works on one
+// transform; every thread holds at most 16 values per pass.
+//
+// * Twiddles: one to four exact values per butterfly come from an FP64-derived
+//   table (w^1, w^2, w^4, w^8); the other powers are products of at most three
+//   of them.
+// * The buffer index is padded by one element per 16, which makes the strided
+//   stores of radix-16 passes free of shared-memory bank conflicts.
+// * Pruning: the first pass reads only indices < n_in (the rest is taken as
+//   zero and never touched), the last pass writes only indices < n_out.
+// * `pre` multiplies the input by conj(pre[i]) in the first pass and `post`
+//   multiplies the output by post[o] in the last pass (either may be null).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -16,8 +24,8 @@
 
 namespace tat {
 
-__device__ __forceinline__ int spad(int i) { return i + (i >> 5); }
-__host__ __device__ __forceinline__ int spad_len(int L) { return L + (L >> 5) + 1; }
+__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+__host__ __device__ __forceinline__ int spad_len(int L) { return L + (L >> 4) + 1; }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -35,18 +43,11 @@ __device__ __forceinline__ float2 mul_mi(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
-template <int R, bool INV>
-__device__ __forceinline__ void bfly(float2* v);
-
-template <>
-__device__ __forceinline__ void bfly<2, false>(float2* v) {
-  float2 a = v[0], b = v[1];
-  v[0] = cadd(a, b);
-  v[1] = csub(a, b);
-}
-template <>
-__device__ __forceinline__ void bfly<2, true>(float2* v) {
-  bfly<2, false>(v);
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  const float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
 }
 
 template <bool INV>
@@ -57,10 +58,6 @@ __device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2&
   x1 = cadd(b, d);
   x3 = csub(b, d);
 }
-template <>
-__device__ __forceinline__ void bfly<4, false>(float2* v) { dft4<false>(v[0], v[1], v[2], v[3]); }
-template <>
-__device__ __forceinline__ void bfly<4, true>(float2* v) { dft4<true>(v[0], v[1], v[2], v[3]); }
 
 template <bool INV>
 __device__ __forceinline__ void dft8(float2* v) {
@@ -82,32 +79,109 @@ __device__ __forceinline__ void dft8(float2* v) {
   v[3] = cadd(e3, o3);
   v[7] = csub(e3, o3);
 }
-template <>
-__device__ __forceinline__ void bfly<8, false>(float2* v) { dft8<false>(v); }
-template <>
-__device__ __forceinline__ void bfly<8, true>(float2* v) { dft8<true>(v); }
+
+// a * e^{-+ 2 pi i E/16} for the exponents a 16-point DFT needs.
+template <int E, bool INV>
+__device__ __forceinline__ float2 w16(float2 a) {
+  constexpr float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f, s2 = 0.70710678118654752440f;
+  constexpr float cr = E == 1 ? c1 : E == 2 ? s2 : E == 3 ? s1 : E == 6 ? -s2 : E == 9 ? -c1 : 1.f;
+  constexpr float si = E == 1 ? -s1 : E == 2 ? -s2 : E == 3 ? -c1 : E == 6 ? -s2 : E == 9 ? s1 : 0.f;
+  const float wi = INV ? -si : si;
+  return make_float2(a.x * cr - a.y * wi, a.x * wi + a.y * cr);
+}
 
 template <bool INV>
-__device__ __forceinline__ void dft3(float2* v) {
-  const float s3 = 0.86602540378443864676f;
-  float2 a = v[0], b = v[1], c = v[2];
-  float2 s = cadd(b, c);
-  float2 t = make_float2(a.x - 0.5f * s.x, a.y - 0.5f * s.y);
-  float2 d = csub(b, c);
-  // -i*s3*d (forward) or +i*s3*d (inverse)
-  float2 u = INV ? make_float2(-s3 * d.y, s3 * d.x) : make_float2(s3 * d.y, -s3 * d.x);
-  v[0] = cadd(a, s);
-  v[1] = cadd(t, u);
-  v[2] = csub(t, u);
+__device__ __forceinline__ void dft16(float2* v) {
+  // x[n1 + 4 n2]: DFT4 over n2 for each n1, twiddle w16^(n1 k2), DFT4 over n1.
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) dft4<INV>(v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]);
+  // v[n1 + 4 k2] now holds y[n1][k2]
+  v[5] = w16<1, INV>(v[5]);
+  v[6] = w16<2, INV>(v[6]);
+  v[7] = w16<3, INV>(v[7]);
+  v[9] = w16<2, INV>(v[9]);
+  v[10] = mul_mi<INV>(v[10]);
+  v[11] = w16<6, INV>(v[11]);
+  v[13] = w16<3, INV>(v[13]);
+  v[14] = w16<6, INV>(v[14]);
+  v[15] = w16<9, INV>(v[15]);
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2) dft4<INV>(v[4 * k2], v[4 * k2 + 1], v[4 * k2 + 2], v[4 * k2 + 3]);
+  // v[4 k2 + k1] holds X[4 k1 + k2]; transpose the 4 x 4 block in registers
+  float2 t;
+  t = v[1]; v[1] = v[4]; v[4] = t;
+  t = v[2]; v[2] = v[8]; v[8] = t;
+  t = v[3]; v[3] = v[12]; v[12] = t;
+  t = v[6]; v[6] = v[9]; v[9] = t;
+  t = v[7]; v[7] = v[13]; v[13] = t;
+  t = v[11]; v[11] = v[14]; v[14] = t;
 }
-template <>
-__device__ __forceinline__ void bfly<3, false>(float2* v) { dft3<false>(v); }
-template <>
-__device__ __forceinline__ void bfly<3, true>(float2* v) { dft3<true>(v); }
+
+template <int R, bool INV>
+__device__ __forceinline__ void bfly(float2* v) {
+  if constexpr (R == 16) {
+    dft16<INV>(v);
+  } else if constexpr (R == 8) {
+    dft8<INV>(v);
+  } else if constexpr (R == 4) {
+    dft4<INV>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 3) {
+    const float s3 = 0.86602540378443864676f;
+    float2 a = v[0], b = v[1], c = v[2];
+    float2 s = cadd(b, c);
+    float2 t = make_float2(a.x - 0.5f * s.x, a.y - 0.5f * s.y);
+    float2 d = csub(b, c);
+    float2 u = INV ? make_float2(-s3 * d.y, s3 * d.x) : make_float2(s3 * d.y, -s3 * d.x);
+    v[0] = cadd(a, s);
+    v[1] = cadd(t, u);
+    v[2] = csub(t, u);
+  } else {
+    dft2<INV>(v[0], v[1]);
+  }
+}
+
+// Multiplies v[r] by w^r (INV: conj(w)^r), r = 1..R-1, for the butterfly
+// twiddle w = tw[base].  w^1, w^2, w^4, w^8 are read from the table; every other
+// power is a product of at most three of them, formed just before it is used
+// so that few twiddles are live at once.
+template <int R, bool INV>
+__device__ __forceinline__ void apply_twiddles(float2* v, const float2* __restrict__ tw, int base) {
+  auto mul = [](float2 a, float2 w) { return INV ? cmulc(a, w) : cmul(a, w); };
+  const float2 w1 = __ldg(&tw[base]);
+  v[1] = mul(v[1], w1);
+  if constexpr (R >= 3) {
+    const float2 w2 = __ldg(&tw[2 * base]);
+    v[2] = mul(v[2], w2);
+    if constexpr (R >= 4) {
+      const float2 w3 = cmul(w1, w2);
+      v[3] = mul(v[3], w3);
+      if constexpr (R >= 8) {
+        const float2 w4 = __ldg(&tw[4 * base]);
+        v[4] = mul(v[4], w4);
+        v[5] = mul(v[5], cmul(w4, w1));
+        v[6] = mul(v[6], cmul(w4, w2));
+        v[7] = mul(v[7], cmul(w4, w3));
+        if constexpr (R >= 16) {
+          const float2 w8 = __ldg(&tw[8 * base]);
+          v[8] = mul(v[8], w8);
+          v[9] = mul(v[9], cmul(w8, w1));
+          v[10] = mul(v[10], cmul(w8, w2));
+          v[11] = mul(v[11], cmul(w8, w3));
+          const float2 w12 = cmul(w8, w4);
+          v[12] = mul(v[12], w12);
+          v[13] = mul(v[13], cmul(w12, w1));
+          v[14] = mul(v[14], cmul(w12, w2));
+          v[15] = mul(v[15], cmul(w12, w3));
+        }
+      }
+    }
+  }
+}
 
 template <int R, bool INV>
 __device__ __forceinline__ void fft_pass(float2* buf, int L, int Ns, const float2* __restrict__ tw, int tid,
-                                         int nthr) {
+                                         int nthr, bool first, bool last, int n_in, int n_out,
+                                         const float2* __restrict__ pre, const float2* __restrict__ post) {
   constexpr int NB = 16 / R;
   const int nb = L / R;
   const int tws = L / (Ns * R);
@@ -118,15 +192,17 @@ __device__ __forceinline__ void fft_pass(float2* buf, int L, int Ns, const float
     const int j = tid + b * nthr;
     if (act && j < nb) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b][r] = buf[spad(j + r * nb)];
-      if (Ns > 1) {
-        const int k = j % Ns;
-#pragma unroll
-        for (int r = 1; r < R; ++r) {
-          float2 w = __ldg(&tw[k * r * tws]);
-          v[b][r] = INV ? cmulc(v[b][r], w) : cmul(v[b][r], w);
+      for (int r = 0; r < R; ++r) {
+        const int idx = j + r * nb;
+        if (first) {
+          float2 x = idx < n_in ? buf[spad(idx)] : make_float2(0.f, 0.f);
+          if (pre != nullptr && idx < n_in) x = cmulc(x, __ldg(&pre[idx]));
+          v[b][r] = x;
+        } else {
+          v[b][r] = buf[spad(idx)];
         }
       }
+      if (Ns > 1) apply_twiddles<R, INV>(v[b], tw, (j % Ns) * tws);
       bfly<R, INV>(v[b]);
     }
   }
@@ -138,60 +214,80 @@ __device__ __forceinline__ void fft_pass(float2* buf, int L, int Ns, const float
       const int k = j % Ns;
       const int base = (j - k) * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[spad(base + r * Ns)] = v[b][r];
+      for (int r = 0; r < R; ++r) {
+        const int o = base + r * Ns;
+        if (last) {
+          if (o < n_out) buf[spad(o)] = post != nullptr ? cmul(v[b][r], __ldg(&post[o])) : v[b][r];
+        } else {
+          buf[spad(o)] = v[b][r];
+        }
+      }
     }
   }
   __syncthreads();
 }
 
-// Radix schedule of a length L = 2^k 3^m: all radix-3 passes, then radix-8
-// passes, then radix-4 passes (a trailing 8*2 is done as 4*4), then at most
-// one radix-2 pass.  The plan builder uses the same rule.
+// Radix schedule of a length L = 2^k 3^m: all radix-3 passes, then radix-16
+// passes, then the remainder of k mod 4 as 8*4 (one 16 fewer), 4 or 8, or a
+// single 2 for k = 1.  The plan builder uses the same rule.
 template <int L>
 struct Sched {
-  static constexpr int pow3(int x) { return x % 3 == 0 ? 1 + pow3(x / 3) : 0; }
-  static constexpr int strip3(int x) { return x % 3 == 0 ? strip3(x / 3) : x; }
-  static constexpr int log2i(int x) { return x <= 1 ? 0 : 1 + log2i(x / 2); }
+  __host__ __device__ static constexpr int pow3(int x) { return x % 3 == 0 ? 1 + pow3(x / 3) : 0; }
+  __host__ __device__ static constexpr int strip3(int x) { return x % 3 == 0 ? strip3(x / 3) : x; }
+  __host__ __device__ static constexpr int log2i(int x) { return x <= 1 ? 0 : 1 + log2i(x / 2); }
   static constexpr int n3 = pow3(L);
   static constexpr int k = log2i(strip3(L));
-  static constexpr int n8 = (k % 3 == 1 && k >= 4) ? k / 3 - 1 : k / 3;
-  static constexpr int n4 = (k % 3 == 1) ? (k >= 4 ? 2 : 0) : (k % 3 == 2 ? 1 : 0);
-  static constexpr int n2 = (k % 3 == 1 && k < 4) ? 1 : 0;
+  static constexpr int n16full = k / 4, rem = k % 4;
+  static constexpr int n16 = (rem == 1 && n16full >= 1) ? n16full - 1 : n16full;
+  static constexpr int ntail = rem == 0 ? 0 : (rem == 1 && n16full >= 1) ? 2 : 1;
+  static constexpr int npass = n3 + n16 + ntail;
+  __host__ __device__ static constexpr int radix(int s) {
+    return s < n3 ? 3
+         : s < n3 + n16 ? 16
+         : rem == 1 ? (n16full >= 1 ? (s == n3 + n16 ? 8 : 4) : 2)
+         : rem == 2 ? 4
+         : 8;
+  }
 };
 
-// Compile-time length: every pass is unrolled with constant strides.
-template <int L, bool INV>
-__device__ __forceinline__ void fft_ct(float2* buf, const float2* __restrict__ tw, int tid, int nthr) {
-  using S = Sched<L>;
-  int Ns = 1;
-#pragma unroll
-  for (int s = 0; s < S::n3; ++s) { fft_pass<3, INV>(buf, L, Ns, tw, tid, nthr); Ns *= 3; }
-#pragma unroll
-  for (int s = 0; s < S::n8; ++s) { fft_pass<8, INV>(buf, L, Ns, tw, tid, nthr); Ns *= 8; }
-#pragma unroll
-  for (int s = 0; s < S::n4; ++s) { fft_pass<4, INV>(buf, L, Ns, tw, tid, nthr); Ns *= 4; }
-  if (S::n2) fft_pass<2, INV>(buf, L, Ns, tw, tid, nthr);
+template <int L, bool INV, int S, int NS>
+__device__ __forceinline__ void fft_ct_from(float2* buf, const float2* __restrict__ tw, int tid, int nthr, int n_in,
+                                            int n_out, const float2* pre, const float2* post) {
+  if constexpr (S < Sched<L>::npass) {
+    constexpr int R = Sched<L>::radix(S);
+    fft_pass<R, INV>(buf, L, NS, tw, tid, nthr, S == 0, S == Sched<L>::npass - 1, n_in, n_out, pre, post);
+    fft_ct_from<L, INV, S + 1, NS * R>(buf, tw, tid, nthr, n_in, n_out, pre, post);
+  }
 }
 
 // Runtime length (any 2^k 3^m): the same schedule read from the plan.
 template <bool INV>
-__device__ __forceinline__ void fft_run(float2* buf, const FftDev& f, int tid, int nthr) {
+__device__ __forceinline__ void fft_run(float2* buf, const FftDev& f, int tid, int nthr, int n_in, int n_out,
+                                        const float2* pre, const float2* post) {
   const int L = f.L;
-  int Ns = 1, s = 0;
+  int Ns = 1;
 #pragma unroll 1
-  for (; s < f.npass && f.radix[s] == 3; ++s, Ns *= 3) fft_pass<3, INV>(buf, L, Ns, f.tw, tid, nthr);
-#pragma unroll 1
-  for (; s < f.npass && f.radix[s] == 8; ++s, Ns *= 8) fft_pass<8, INV>(buf, L, Ns, f.tw, tid, nthr);
-#pragma unroll 1
-  for (; s < f.npass && f.radix[s] == 4; ++s, Ns *= 4) fft_pass<4, INV>(buf, L, Ns, f.tw, tid, nthr);
-  if (s < f.npass && f.radix[s] == 2) fft_pass<2, INV>(buf, L, Ns, f.tw, tid, nthr);
+  for (int s = 0; s < f.npass; ++s) {
+    const int R = f.radix[s];
+    const bool first = s == 0, last = s == f.npass - 1;
+    switch (R) {
+      case 16: fft_pass<16, INV>(buf, L, Ns, f.tw, tid, nthr, first, last, n_in, n_out, pre, post); break;
+      case 8: fft_pass<8, INV>(buf, L, Ns, f.tw, tid, nthr, first, last, n_in, n_out, pre, post); break;
+      case 4: fft_pass<4, INV>(buf, L, Ns, f.tw, tid, nthr, first, last, n_in, n_out, pre, post); break;
+      case 3: fft_pass<3, INV>(buf, L, Ns, f.tw, tid, nthr, first, last, n_in, n_out, pre, post); break;
+      default: fft_pass<2, INV>(buf, L, Ns, f.tw, tid, nthr, first, last, n_in, n_out, pre, post); break;
+    }
+    Ns *= R;
+  }
 }
 
 // L > 0: compile-time schedule (must equal f.L); L == 0: runtime schedule.
+// Reads buf[0, n_in), writes buf[0, n_out); every thread of the CTA must call it.
 template <int L, bool INV>
-__device__ __forceinline__ void fft(float2* buf, const FftDev& f, int tid, int nthr) {
-  if constexpr (L == 0) fft_run<INV>(buf, f, tid, nthr);
-  else fft_ct<L, INV>(buf, f.tw, tid, nthr);
+__device__ __forceinline__ void fft(float2* buf, const FftDev& f, int tid, int nthr, int n_in, int n_out,
+                                    const float2* pre = nullptr, const float2* post = nullptr) {
+  if constexpr (L == 0) fft_run<INV>(buf, f, tid, nthr, n_in, n_out, pre, post);
+  else fft_ct_from<L, INV, 0, 1>(buf, f.tw, tid, nthr, n_in, n_out, pre, post);
 }
 
 }  // namespace tat

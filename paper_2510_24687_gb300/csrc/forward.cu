@@ -16,6 +16,9 @@ tat_status validate_shapes(const tat_plan_s* Pl) {
     if (b < 32 || b > 1024 || b % 32) return TAT_ERR_UNSUPPORTED;
   if (s.rings_block < 96) return TAT_ERR_UNSUPPORTED;  // reduction scratch of the low-mode rings
   if (s.cols_block > 512) return TAT_ERR_UNSUPPORTED;  // launch bound of the column kernels
+  const int N = Pl->d.N;
+  const bool ct = N == 256 || N == 512 || N == 1024 || N == 2048 || N == 4096 || N == 8192;
+  if (ct && N <= 4096 && s.cols_block > 256) return TAT_ERR_UNSUPPORTED;
   for (size_t m : smem)
     if (m > mx) return TAT_ERR_UNSUPPORTED;
   if (Pl->cfg.t_tile % 2 || Pl->cfg.strip < 1 || Pl->cfg.rings_per_cta < 1) return TAT_ERR_INVALID_ARG;

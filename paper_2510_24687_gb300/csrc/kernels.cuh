@@ -50,8 +50,8 @@ __device__ __forceinline__ int wrapN(int q, int N) { return q < 0 ? q + N : q; }
 // ------------------------------------------------------------------ forward
 
 template <int L>
-__global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __restrict__ f, long long fs, float2* __restrict__ X,
-                           long long xs, int RP, int nt) {
+__global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __restrict__ f, long long fs,
+                                                   float2* __restrict__ X, long long xs, int RP, int nt) {
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
   const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
@@ -63,14 +63,15 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __res
   const float* fb = f + (size_t)b * fs;
   const int2 r1 = v1 ? P.rowrange[iy1] : make_int2(0, 0);
   const int2 r2 = v2 ? P.rowrange[iy2] : make_int2(0, 0);
-  for (int ix = gt; ix < P.N; ix += nt) {
+  // only the n leading entries are written: the FFT's first pass reads [0, n)
+  for (int ix = gt; ix < P.n; ix += nt) {
     float a = 0.f, c = 0.f;
     if (ix >= r1.x && ix < r1.y) a = fb[(size_t)iy1 * P.n + ix];
     if (ix >= r2.x && ix < r2.y) c = fb[(size_t)iy2 * P.n + ix];
     buf[spad(ix)] = make_float2(a, c);
   }
   __syncthreads();
-  fft<L, false>(buf, P.fN, gt, nt);
+  fft<L, false>(buf, P.fN, gt, nt, P.n, P.N);
   float2* Xb = X + (size_t)b * xs;
   for (int q = gt; q < P.ncol; q += nt) {
     const float2 Z = buf[spad(q)];
@@ -84,45 +85,45 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __res
   }
 }
 
+// Column kernels: 256 threads and 2 CTAs per SM (<= 128 registers, no spills)
+// for the compile-time lengths up to 4096, 512 threads otherwise.  Measured on
+// GB300 at n = 512: 2 CTAs without spills beat 3 CTAs with 200 B of spills by 7%.
+#define TAT_COLS_BOUNDS __launch_bounds__((L > 0 && L <= 4096) ? 256 : 512, (L > 0 && L <= 4096) ? 2 : 1)
+
 template <int L>
-__global__ void __launch_bounds__(512) k_cols_fwd(DevPlan P, const float2* __restrict__ X, long long xs, float2* __restrict__ Y,
-                           long long ys, int S, int nt) {
+__global__ void TAT_COLS_BOUNDS k_cols_fwd(DevPlan P, const float2* __restrict__ X, long long xs,
+                                           float2* __restrict__ Y, long long ys, int S, int nt) {
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
   const int SL = spad_len(P.N);
   float2* slot0 = sm;
   float2* slot1 = sm + SL;
-  float2* stage = sm + 2 * SL;  // [n][S+1]
   const int tid = threadIdx.x, NT = blockDim.x;
   const int c0 = blockIdx.x * S;
   const int c1 = min(c0 + S, P.ncol - 1);  // owned stencil columns i0 in [c0, c1)
   const int ncols = c1 - c0 + 1;           // spectrum columns c0..c1
   const float2* Xb = X + (size_t)b * xs;
-  for (int e = tid; e < P.n * ncols; e += NT) {
-    const int iy = e / ncols, cc = e % ncols;
-    stage[iy * (S + 1) + cc] = Xb[(size_t)iy * P.ncol + c0 + cc];
-  }
-  __syncthreads();
   float2* Yb = Y + (size_t)b * ys;
   const int N = P.N;
 #pragma unroll 1
   for (int cc = 0; cc < ncols; ++cc) {
     float2* buf = (cc & 1) ? slot1 : slot0;
-    for (int q = tid; q < N; q += NT) buf[spad(q)] = q < P.n ? stage[q * (S + 1) + cc] : make_float2(0.f, 0.f);
+    const int c = c0 + cc;
+    for (int iy = tid; iy < P.n; iy += NT) buf[spad(iy)] = Xb[(size_t)iy * P.ncol + c];
     __syncthreads();
-    fft<L, false>(buf, P.fN, tid, nt);
+    // column DFT over the n nonzero rows, times the phase e^{i q dxi} of each output row
+    fft<L, false>(buf, P.fN, tid, nt, P.n, N, nullptr, P.phase);
     if (cc > 0) {
-      const float2* A = (cc & 1) ? slot0 : slot1;  // column c0+cc-1
-      const float2* B = buf;                       // column c0+cc
-      const int ci = c0 + cc - 1;
-      const int e1 = P.coloff[ci + 1];
-      for (int e = P.coloff[ci] + tid; e < e1; e += NT) {
+      const float2* A = (cc & 1) ? slot0 : slot1;  // column c-1
+      const float2* B = buf;                       // column c
+      const int e1 = P.coloff[c];
+      for (int e = P.coloff[c - 1] + tid; e < e1; e += NT) {
         const PolarEntry pe = P.pts[e];
         const int qa = wrapN(pe.k0, N), qb = wrapN(pe.k0 + 1, N);
         const float a = pe.a, bb = pe.b;
         const float2 va = cadd(cscale(A[spad(qa)], 1.f - a), cscale(B[spad(qa)], a));
         const float2 vb = cadd(cscale(A[spad(qb)], 1.f - a), cscale(B[spad(qb)], a));
-        Yb[pe.p] = cadd(cscale(cmul(P.phase[qa], va), 1.f - bb), cscale(cmul(P.phase[qb], vb), bb));
+        Yb[pe.p] = cadd(cscale(va, 1.f - bb), cscale(vb, bb));
       }
     }
     __syncthreads();
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(1024) k_rings_fwd(DevPlan P, const float2* __r
     buf[spad(l)] = v;
   }
   __syncthreads();
-  fft<L, false>(buf, P.fphi, gt, nt);
+  fft<L, false>(buf, P.fphi, gt, nt, P.n_phi, P.K + 1);
   for (int e = threadIdx.x; e < (P.K + 1) * RPC; e += blockDim.x) {
     const int k = e / RPC, gg = e % RPC;
     const int rr = rbase + gg;
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(1024) k_modes_fwd(DevPlan P, const float2* __r
     sm[spad(j)] = v;
   }
   __syncthreads();
-  fft<L, false>(sm, P.f2M, threadIdx.x, nt);
+  fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, P.n_t);
   float2* G = Y + (size_t)b * ys + (size_t)k * P.n_t;
   const bool low = P.low_on && k <= 1;
   const float2* Ch = X + (size_t)b * xs + (size_t)(P.K + 1) * J1 + (size_t)k * P.n_low;
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(1024) k_theta_fwd(DevPlan P, const float2* __r
   __syncthreads();
   {
     const int gi = threadIdx.x / nt, gt = threadIdx.x % nt;
-    fft<L, true>(sm + gi * SL, P.fdet, gt, nt);
+    fft<L, true>(sm + gi * SL, P.fdet, gt, nt, P.n_det, P.n_det);
   }
   float* gb = g + (size_t)b * gs;
   for (int e = threadIdx.x; e < nd * TT; e += blockDim.x) {
@@ -309,7 +310,7 @@ __global__ void __launch_bounds__(1024) k_theta_adj(DevPlan P, const float* __re
   __syncthreads();
   {
     const int gi = threadIdx.x / nt, gt = threadIdx.x % nt;
-    fft<L, false>(sm + gi * SL, P.fdet, gt, nt);
+    fft<L, false>(sm + gi * SL, P.fdet, gt, nt, P.n_det, P.n_det);
   }
   float2* Gp = Y + (size_t)b * ys;
   for (int e = threadIdx.x; e < (P.K + 1) * TT; e += blockDim.x) {
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(1024) k_modes_adj(DevPlan P, const float2* __r
   }
   __syncthreads();
   const float2 g0 = Gp[0];
-  fft<L, false>(sm, P.f2M, threadIdx.x, nt);
+  fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, P.J + 1);
   float2* Dm = X + (size_t)b * xs + (size_t)k * J1;
   const bool low = P.low_on && k <= 1;
   for (int j = threadIdx.x; j < J1; j += blockDim.x) {
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
   __syncthreads();
   const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
   float2* buf = sm + g * SL;
-  fft<L, true>(buf, P.fphi, gt, nt);
+  fft<L, true>(buf, P.fphi, gt, nt, P.n_phi, P.n_phi);
   const int r = rbase + g;
   if (r <= P.J) {
     const int q4 = P.n_phi / 4;
@@ -428,67 +429,80 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
   }
 }
 
+// Transposed bilinear weights of the points with stencil column i0 = c into
+// the column buffers of c (weight 1-a) and c+1 (weight a); either may be null.
+__device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* __restrict__ Yb, int c, float2* left,
+                                               float2* right, int tid, int NT) {
+  const int e1 = P.coloff[c + 1];
+  for (int e = P.coloff[c] + tid; e < e1; e += NT) {
+    const PolarEntry pe = P.pts[e];
+    const float2 val = Yb[pe.p];
+    const int qa = wrapN(pe.k0, P.N), qb = wrapN(pe.k0 + 1, P.N);
+    const float wa0 = 1.f - pe.b, wa1 = pe.b;
+    if (left != nullptr) {
+      const float w = 1.f - pe.a;
+      atomicAdd(&left[spad(qa)].x, w * wa0 * val.x);
+      atomicAdd(&left[spad(qa)].y, w * wa0 * val.y);
+      atomicAdd(&left[spad(qb)].x, w * wa1 * val.x);
+      atomicAdd(&left[spad(qb)].y, w * wa1 * val.y);
+    }
+    if (right != nullptr) {
+      const float w = pe.a;
+      atomicAdd(&right[spad(qa)].x, w * wa0 * val.x);
+      atomicAdd(&right[spad(qa)].y, w * wa0 * val.y);
+      atomicAdd(&right[spad(qb)].x, w * wa1 * val.x);
+      atomicAdd(&right[spad(qb)].y, w * wa1 * val.y);
+    }
+  }
+}
+
 template <int L>
-__global__ void __launch_bounds__(512) k_cols_adj(DevPlan P, const float2* __restrict__ Y, long long ys, float2* __restrict__ X,
-                           long long xs, int S, int nt) {
+__global__ void TAT_COLS_BOUNDS k_cols_adj(DevPlan P, const float2* __restrict__ Y, long long ys,
+                                           float2* __restrict__ X, long long xs, int S, int nt) {
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
   const int N = P.N;
   const int SL = spad_len(N);
-  float2* slot = sm;
-  float2* stage = sm + SL;  // [n][S]
   const int tid = threadIdx.x, NT = blockDim.x;
   const int c0 = blockIdx.x * S;
-  const int c1 = min(c0 + S, P.ncol);
+  const int c1 = min(c0 + S, P.ncol);  // owned columns [c0, c1)
   const float2* Yb = Y + (size_t)b * ys;
+  float2* Xb = X + (size_t)b * xs;
+  auto slot = [&](int c) { return sm + ((c - c0) & 1) * SL; };
+  {
+    float2* first = slot(c0);
+    for (int q = tid; q < SL; q += NT) first[q] = make_float2(0.f, 0.f);
+    __syncthreads();
+    if (c0 >= 1) scatter_column(P, Yb, c0 - 1, nullptr, first, tid, NT);  // right side of the previous column
+  }
 #pragma unroll 1
   for (int c = c0; c < c1; ++c) {
-    for (int q = tid; q < SL; q += NT) slot[q] = make_float2(0.f, 0.f);
+    float2* cur = slot(c);
+    float2* nxt = c + 1 < c1 ? slot(c + 1) : nullptr;
+    if (nxt != nullptr)
+      for (int q = tid; q < SL; q += NT) nxt[q] = make_float2(0.f, 0.f);
     __syncthreads();
-    // Transposed bilinear weights: points whose stencil has column c on the
-    // left (i0 = c, weight 1-a) or on the right (i0 = c-1, weight a).
-    for (int side = 0; side < 2; ++side) {
-      const int ci = side == 0 ? c : c - 1;
-      if (ci < 0 || ci > P.ncol - 2) continue;
-      const int e1 = P.coloff[ci + 1];
-      for (int e = P.coloff[ci] + tid; e < e1; e += NT) {
-        const PolarEntry pe = P.pts[e];
-        const float wa = side == 0 ? 1.f - pe.a : pe.a;
-        const float2 val = Yb[pe.p];
-        const int qa = wrapN(pe.k0, N), qb = wrapN(pe.k0 + 1, N);
-        const float2 va = cscale(cmulc(val, P.phase[qa]), wa * (1.f - pe.b));
-        const float2 vb = cscale(cmulc(val, P.phase[qb]), wa * pe.b);
-        atomicAdd(&slot[spad(qa)].x, va.x);
-        atomicAdd(&slot[spad(qa)].y, va.y);
-        atomicAdd(&slot[spad(qb)].x, vb.x);
-        atomicAdd(&slot[spad(qb)].y, vb.y);
-      }
-    }
+    if (c <= P.ncol - 2) scatter_column(P, Yb, c, cur, nxt, tid, NT);
     __syncthreads();
     if (c == 0) {
       // Column 0 also receives the mirrored samples of the other half circle:
       // F'(0, q) += conj(F'(0, -q)).
-      for (int q = tid; q <= N / 2 - 1; q += NT) {
+      for (int q = tid; q < N / 2; q += NT) {
         if (q == 0) {
-          const float2 s = slot[0];
-          slot[0] = make_float2(2.f * s.x, 0.f);
+          const float2 s = cur[0];
+          cur[0] = make_float2(2.f * s.x, 0.f);
         } else {
-          const float2 A = slot[spad(q)], B = slot[spad(N - q)];
-          slot[spad(q)] = cadd(A, cconj(B));
-          slot[spad(N - q)] = cadd(B, cconj(A));
+          const float2 A = cur[spad(q)], B = cur[spad(N - q)];
+          cur[spad(q)] = cadd(A, cconj(B));
+          cur[spad(N - q)] = cadd(B, cconj(A));
         }
       }
       __syncthreads();
     }
-    fft<L, true>(slot, P.fN, tid, nt);
-    for (int iy = tid; iy < P.n; iy += NT) stage[iy * S + (c - c0)] = slot[spad(iy)];
+    // inverse column DFT of conj(phase) * F', first n rows only
+    fft<L, true>(cur, P.fN, tid, nt, N, P.n, P.phase, nullptr);
+    for (int iy = tid; iy < P.n; iy += NT) Xb[(size_t)iy * P.ncol + c] = cur[spad(iy)];
     __syncthreads();
-  }
-  float2* Xb = X + (size_t)b * xs;
-  const int w = c1 - c0;
-  for (int e = tid; e < P.n * w; e += NT) {
-    const int iy = e / w, cc = e % w;
-    Xb[(size_t)iy * P.ncol + c0 + cc] = stage[iy * S + cc];
   }
 }
 
@@ -518,7 +532,7 @@ __global__ void __launch_bounds__(1024) k_rows_adj(DevPlan P, const float2* __re
     buf[spad(q)] = z;
   }
   __syncthreads();
-  fft<L, true>(buf, P.fN, gt, nt);
+  fft<L, true>(buf, P.fN, gt, nt, N, P.n);
   float* fb = f + (size_t)b * fs;
   const int2 r1 = v1 ? P.rowrange[iy1] : make_int2(0, 0);
   const int2 r2 = v2 ? P.rowrange[iy2] : make_int2(0, 0);

@@ -70,20 +70,26 @@ void parallel_for(int count, F&& fn) {
   for (auto& x : th) x.join();
 }
 
-// Radix schedule: radix-3 passes, radix-8 passes, radix-4 passes (a trailing
-// 8*2 becomes 4*4), at most one radix-2 pass; the device code uses the same rule.
+// Radix schedule: radix-3 passes, radix-16 passes, then the remainder of
+// log2 mod 4 as 8*4 (one 16 fewer), 4 or 8 (or one 2 for a length-2 factor);
+// the device code uses the same rule.
 int fft_schedule(int L, int* radix) {
   int r = L, np = 0;
   while (r % 3 == 0) { radix[np++] = 3; r /= 3; }
   int k = 0;
   while ((1 << k) < r) ++k;
   if ((1 << k) != r) return -1;
-  int n8 = (k % 3 == 1 && k >= 4) ? k / 3 - 1 : k / 3;
-  int n4 = (k % 3 == 1) ? (k >= 4 ? 2 : 0) : (k % 3 == 2 ? 1 : 0);
-  int n2 = (k % 3 == 1 && k < 4) ? 1 : 0;
-  for (int i = 0; i < n8; ++i) radix[np++] = 8;
-  for (int i = 0; i < n4; ++i) radix[np++] = 4;
-  for (int i = 0; i < n2; ++i) radix[np++] = 2;
+  const int n16full = k / 4, rem = k % 4;
+  const int n16 = (rem == 1 && n16full >= 1) ? n16full - 1 : n16full;
+  for (int i = 0; i < n16; ++i) radix[np++] = 16;
+  if (rem == 1) {
+    if (n16full >= 1) { radix[np++] = 8; radix[np++] = 4; }
+    else radix[np++] = 2;
+  } else if (rem == 2) {
+    radix[np++] = 4;
+  } else if (rem == 3) {
+    radix[np++] = 8;
+  }
   return np;
 }
 
