@@ -90,26 +90,41 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __res
 // GB300 at n = 512: 2 CTAs without spills beat 3 CTAs with 200 B of spills by 7%.
 #define TAT_COLS_BOUNDS __launch_bounds__((L > 0 && L <= 4096) ? 256 : 512, (L > 0 && L <= 4096) ? 2 : 1)
 
+// Column strips are launched strip-major (all images' strip 0 first): the
+// strips near q_x = 0 hold up to 7x the average number of polar samples, so
+// starting them first keeps them off the kernel's tail.
+__device__ __forceinline__ void strip_and_image(int batch, int* strip, int* b) {
+  *strip = blockIdx.x / batch;
+  *b = blockIdx.x % batch;
+}
+
 template <int L>
 __global__ void TAT_COLS_BOUNDS k_cols_fwd(DevPlan P, const float2* __restrict__ X, long long xs,
-                                           float2* __restrict__ Y, long long ys, int S, int nt) {
+                                           float2* __restrict__ Y, long long ys, int S, int nt, int batch) {
   extern __shared__ float2 sm[];
-  const int b = blockIdx.y;
+  int strip, b;
+  strip_and_image(batch, &strip, &b);
   const int SL = spad_len(P.N);
   float2* slot0 = sm;
   float2* slot1 = sm + SL;
+  float2* stage = sm + 2 * SL;  // [n][S+1]: the strip's input, loaded row by row
   const int tid = threadIdx.x, NT = blockDim.x;
-  const int c0 = blockIdx.x * S;
+  const int c0 = strip * S;
   const int c1 = min(c0 + S, P.ncol - 1);  // owned stencil columns i0 in [c0, c1)
   const int ncols = c1 - c0 + 1;           // spectrum columns c0..c1
   const float2* Xb = X + (size_t)b * xs;
   float2* Yb = Y + (size_t)b * ys;
   const int N = P.N;
+  for (int e = tid; e < P.n * ncols; e += NT) {
+    const int iy = e / ncols, cc = e - iy * ncols;
+    stage[iy * (S + 1) + cc] = Xb[(size_t)iy * P.ncol + c0 + cc];
+  }
+  __syncthreads();
 #pragma unroll 1
   for (int cc = 0; cc < ncols; ++cc) {
     float2* buf = (cc & 1) ? slot1 : slot0;
     const int c = c0 + cc;
-    for (int iy = tid; iy < P.n; iy += NT) buf[spad(iy)] = Xb[(size_t)iy * P.ncol + c];
+    for (int iy = tid; iy < P.n; iy += NT) buf[spad(iy)] = stage[iy * (S + 1) + cc];
     __syncthreads();
     // column DFT over the n nonzero rows, times the phase e^{i q dxi} of each output row
     fft<L, false>(buf, P.fN, tid, nt, P.n, N, nullptr, P.phase);
@@ -431,40 +446,76 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
 
 // Transposed bilinear weights of the points with stencil column i0 = c into
 // the column buffers of c (weight 1-a) and c+1 (weight a); either may be null.
+// Each warp takes 32 consecutive points.  Points are sorted by stencil row k0,
+// so equal rows form runs of lanes; when a warp holds runs, they are summed
+// with a segmented shuffle scan and only the last lane of each run issues the
+// shared-memory atomics (near the origin up to 64 samples share a cell).
 __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* __restrict__ Yb, int c, float2* left,
                                                float2* right, int tid, int NT) {
-  const int e1 = P.coloff[c + 1];
-  for (int e = P.coloff[c] + tid; e < e1; e += NT) {
-    const PolarEntry pe = P.pts[e];
-    const float2 val = Yb[pe.p];
-    const int qa = wrapN(pe.k0, P.N), qb = wrapN(pe.k0 + 1, P.N);
-    const float wa0 = 1.f - pe.b, wa1 = pe.b;
-    if (left != nullptr) {
-      const float w = 1.f - pe.a;
-      atomicAdd(&left[spad(qa)].x, w * wa0 * val.x);
-      atomicAdd(&left[spad(qa)].y, w * wa0 * val.y);
-      atomicAdd(&left[spad(qb)].x, w * wa1 * val.x);
-      atomicAdd(&left[spad(qb)].y, w * wa1 * val.y);
+  const unsigned full = 0xffffffffu;
+  const int lane = tid & 31, warp = tid >> 5, nwarp = NT >> 5;
+  const int e0 = P.coloff[c], e1 = P.coloff[c + 1];
+  for (int base = e0 + warp * 32; base < e1; base += nwarp * 32) {
+    const int e = base + lane;
+    int key = 0x7fffffff;
+    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // left qa, left qb, right qa, right qb (re, im)
+    if (e < e1) {
+      const PolarEntry pe = P.pts[e];
+      const float2 val = Yb[pe.p];
+      key = pe.k0;
+      const float wl = 1.f - pe.a, wr = pe.a, w0 = 1.f - pe.b, w1 = pe.b;
+      v[0] = wl * w0 * val.x; v[1] = wl * w0 * val.y;
+      v[2] = wl * w1 * val.x; v[3] = wl * w1 * val.y;
+      v[4] = wr * w0 * val.x; v[5] = wr * w0 * val.y;
+      v[6] = wr * w1 * val.x; v[7] = wr * w1 * val.y;
     }
-    if (right != nullptr) {
-      const float w = pe.a;
-      atomicAdd(&right[spad(qa)].x, w * wa0 * val.x);
-      atomicAdd(&right[spad(qa)].y, w * wa0 * val.y);
-      atomicAdd(&right[spad(qb)].x, w * wa1 * val.x);
-      atomicAdd(&right[spad(qb)].y, w * wa1 * val.y);
+    const int prev = __shfl_up_sync(full, key, 1);
+    const bool head = lane == 0 || prev != key;
+    const unsigned heads = __ballot_sync(full, head);
+    bool emit = key != 0x7fffffff;
+    if (__popc(heads) <= 24) {
+      // segmented inclusive scan; the run's last lane ends up with the run's sum
+      const int seg = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const float t = __shfl_up_sync(full, v[q], o);
+          if (lane - o >= seg) v[q] += t;
+        }
+      }
+      const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+      emit = emit && tail;
+    }
+    if (emit) {
+      const int qa = wrapN(key, P.N), qb = wrapN(key + 1, P.N);
+      if (left != nullptr) {
+        atomicAdd(&left[spad(qa)].x, v[0]);
+        atomicAdd(&left[spad(qa)].y, v[1]);
+        atomicAdd(&left[spad(qb)].x, v[2]);
+        atomicAdd(&left[spad(qb)].y, v[3]);
+      }
+      if (right != nullptr) {
+        atomicAdd(&right[spad(qa)].x, v[4]);
+        atomicAdd(&right[spad(qa)].y, v[5]);
+        atomicAdd(&right[spad(qb)].x, v[6]);
+        atomicAdd(&right[spad(qb)].y, v[7]);
+      }
     }
   }
 }
 
 template <int L>
 __global__ void TAT_COLS_BOUNDS k_cols_adj(DevPlan P, const float2* __restrict__ Y, long long ys,
-                                           float2* __restrict__ X, long long xs, int S, int nt) {
+                                           float2* __restrict__ X, long long xs, int S, int nt, int batch) {
   extern __shared__ float2 sm[];
-  const int b = blockIdx.y;
+  int strip, b;
+  strip_and_image(batch, &strip, &b);
   const int N = P.N;
   const int SL = spad_len(N);
+  float2* stage = sm + 2 * SL;  // [n][S]: the strip's output rows, written out at the end
   const int tid = threadIdx.x, NT = blockDim.x;
-  const int c0 = blockIdx.x * S;
+  const int c0 = strip * S;
   const int c1 = min(c0 + S, P.ncol);  // owned columns [c0, c1)
   const float2* Yb = Y + (size_t)b * ys;
   float2* Xb = X + (size_t)b * xs;
@@ -501,8 +552,13 @@ __global__ void TAT_COLS_BOUNDS k_cols_adj(DevPlan P, const float2* __restrict__
     }
     // inverse column DFT of conj(phase) * F', first n rows only
     fft<L, true>(cur, P.fN, tid, nt, N, P.n, P.phase, nullptr);
-    for (int iy = tid; iy < P.n; iy += NT) Xb[(size_t)iy * P.ncol + c] = cur[spad(iy)];
+    for (int iy = tid; iy < P.n; iy += NT) stage[iy * S + (c - c0)] = cur[spad(iy)];
     __syncthreads();
+  }
+  const int w = c1 - c0;
+  for (int e = tid; e < P.n * w; e += NT) {
+    const int iy = e / w, cc = e - iy * w;
+    Xb[(size_t)iy * P.ncol + c0 + cc] = stage[iy * S + cc];
   }
 }
 
