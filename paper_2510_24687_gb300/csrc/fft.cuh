@@ -291,3 +291,131 @@ __device__ __forceinline__ void fft(float2* buf, const FftDev& f, int tid, int n
 }
 
 }  // namespace tat
+
+namespace tat {
+
+// ------------------------------------------------------------------------
+// In-place four-step DFT of length N = RA * 256 (RA in {2, 4, 8, 16}) for the
+// column transforms, where a column's spectrum stays in shared memory.
+//   n = 256 n1 + n2, k = k1 + RA k2, k2 = k21 + 16 k22:
+//   step A : per n2, DFT_RA over n1, twiddle w_N^(n2 k1)          (256 threads)
+//   step B1: per (k1, m2), DFT16 over m1 of y[k1][16 m1 + m2],
+//            twiddle w_256^(m2 k21)                                (16 threads/block)
+//   step B2: per (k1, k21), DFT16 over m2                          (same warp)
+// Every thread reads and writes back the same set of positions in each step,
+// so only two CTA barriers are needed.  The output stays in the permuted
+// layout colpos(q) = 256 k1 + 16 k21 + k22, which the resampling reads and
+// writes directly.  The inverse runs the conjugate transposes in reverse.
+template <int L>
+struct FourStep {
+  static constexpr bool on = L == 512 || L == 1024 || L == 2048 || L == 4096;
+  static constexpr int RA = on ? L / 256 : 1;
+};
+
+// Position of FFT bin q of a column buffer (identity for other lengths).
+template <int L>
+__device__ __forceinline__ int colpos(int q) {
+  if constexpr (FourStep<L>::on) {
+    constexpr int RA = FourStep<L>::RA;
+    const int k1 = q & (RA - 1), r = q / RA;
+    return 256 * k1 + 16 * (r & 15) + (r >> 4);
+  } else {
+    return q;
+  }
+}
+
+// Forward: x[0, n_in) in natural order -> X[q] * post[q] at colpos(q).
+template <int L>
+__device__ __forceinline__ void col_fft_fwd(float2* buf, const FftDev& f, int tid, int nthr, int n_in,
+                                            const float2* __restrict__ post) {
+  if constexpr (!FourStep<L>::on) {
+    fft<L, false>(buf, f, tid, nthr, n_in, f.L, nullptr, post);
+  } else {
+    constexpr int RA = FourStep<L>::RA;
+    const float2* __restrict__ tw = f.tw;
+    if (tid < 256) {
+      const int n2 = tid;
+      float2 v[RA];
+#pragma unroll
+      for (int n1 = 0; n1 < RA; ++n1) {
+        const int idx = 256 * n1 + n2;
+        v[n1] = idx < n_in ? buf[spad(idx)] : make_float2(0.f, 0.f);
+      }
+      bfly<RA, false>(v);
+      apply_twiddles<RA, false>(v, tw, n2);
+#pragma unroll
+      for (int k1 = 0; k1 < RA; ++k1) buf[spad(256 * k1 + n2)] = v[k1];
+    }
+    __syncthreads();
+    if (tid < RA * 16) {
+      const int blk = tid >> 4, m = tid & 15;
+      const int base = 256 * blk;
+      float2 v[16];
+#pragma unroll
+      for (int m1 = 0; m1 < 16; ++m1) v[m1] = buf[spad(base + 16 * m1 + m)];
+      bfly<16, false>(v);
+      apply_twiddles<16, false>(v, tw, RA * m);
+#pragma unroll
+      for (int k21 = 0; k21 < 16; ++k21) buf[spad(base + 16 * k21 + m)] = v[k21];
+      __syncwarp();
+#pragma unroll
+      for (int m2 = 0; m2 < 16; ++m2) v[m2] = buf[spad(base + 16 * m + m2)];
+      bfly<16, false>(v);
+#pragma unroll
+      for (int k22 = 0; k22 < 16; ++k22) {
+        float2 x = v[k22];
+        if (post != nullptr) x = cmul(x, __ldg(&post[blk + RA * (m + 16 * k22)]));
+        buf[spad(base + 16 * m + k22)] = x;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Inverse (unnormalised): Z[q] at colpos(q), times conj(pre[q]) -> z[0, n_out) in natural order.
+template <int L>
+__device__ __forceinline__ void col_fft_inv(float2* buf, const FftDev& f, int tid, int nthr, int n_out,
+                                            const float2* __restrict__ pre) {
+  if constexpr (!FourStep<L>::on) {
+    fft<L, true>(buf, f, tid, nthr, f.L, n_out, pre, nullptr);
+  } else {
+    constexpr int RA = FourStep<L>::RA;
+    const float2* __restrict__ tw = f.tw;
+    if (tid < RA * 16) {
+      const int blk = tid >> 4, m = tid & 15;
+      const int base = 256 * blk;
+      float2 v[16];
+#pragma unroll
+      for (int k22 = 0; k22 < 16; ++k22) {
+        float2 x = buf[spad(base + 16 * m + k22)];
+        if (pre != nullptr) x = cmulc(x, __ldg(&pre[blk + RA * (m + 16 * k22)]));
+        v[k22] = x;
+      }
+      bfly<16, true>(v);
+#pragma unroll
+      for (int m2 = 0; m2 < 16; ++m2) buf[spad(base + 16 * m + m2)] = v[m2];
+      __syncwarp();
+#pragma unroll
+      for (int k21 = 0; k21 < 16; ++k21) v[k21] = buf[spad(base + 16 * k21 + m)];
+      apply_twiddles<16, true>(v, tw, RA * m);
+      bfly<16, true>(v);
+#pragma unroll
+      for (int m1 = 0; m1 < 16; ++m1) buf[spad(base + 16 * m1 + m)] = v[m1];
+    }
+    __syncthreads();
+    if (tid < 256) {
+      const int n2 = tid;
+      float2 v[RA];
+#pragma unroll
+      for (int k1 = 0; k1 < RA; ++k1) v[k1] = buf[spad(256 * k1 + n2)];
+      apply_twiddles<RA, true>(v, tw, n2);
+      bfly<RA, true>(v);
+#pragma unroll
+      for (int n1 = 0; n1 < RA; ++n1)
+        if (256 * n1 + n2 < n_out) buf[spad(256 * n1 + n2)] = v[n1];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace tat

@@ -72,23 +72,32 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __res
   }
   __syncthreads();
   fft<L, false>(buf, P.fN, gt, nt, P.n, P.N);
+  // Split the two real rows and store R[q][iy] (column-major); the RP pairs of
+  // this CTA are adjacent rows, so consecutive threads write consecutive rows.
   float2* Xb = X + (size_t)b * xs;
-  for (int q = gt; q < P.ncol; q += nt) {
-    const float2 Z = buf[spad(q)];
-    const float2 Zc = cconj(buf[spad(q == 0 ? 0 : P.N - q)]);
+  const int pair0 = blockIdx.x * RP;
+  for (int e = threadIdx.x; e < P.ncol * RP; e += blockDim.x) {
+    const int q = e / RP, gg = e - q * RP;
+    const int py1 = 2 * (pair0 + gg);
+    if (py1 >= P.n) continue;
+    const float2* bg = sm + gg * SL;
+    const float2 Z = bg[spad(q)];
+    const float2 Zc = cconj(bg[spad(q == 0 ? 0 : P.N - q)]);
     const float2 x1 = cscale(cadd(Z, Zc), 0.5f);
     const float2 dd = csub(Z, Zc);
     const float2 x2 = make_float2(0.5f * dd.y, -0.5f * dd.x);
     const float2 ph = cscale(P.phase[q], P.h2_2pi);
-    if (v1) Xb[(size_t)iy1 * P.ncol + q] = cmul(ph, x1);
-    if (v2) Xb[(size_t)iy2 * P.ncol + q] = cmul(ph, x2);
+    float2* col = Xb + (size_t)q * P.n;
+    col[py1] = cmul(ph, x1);
+    if (py1 + 1 < P.n) col[py1 + 1] = cmul(ph, x2);
   }
 }
 
-// Column kernels: 256 threads and 2 CTAs per SM (<= 128 registers, no spills)
-// for the compile-time lengths up to 4096, 512 threads otherwise.  Measured on
-// GB300 at n = 512: 2 CTAs without spills beat 3 CTAs with 200 B of spills by 7%.
-#define TAT_COLS_BOUNDS __launch_bounds__((L > 0 && L <= 4096) ? 256 : 512, (L > 0 && L <= 4096) ? 2 : 1)
+// Column kernels: 256 threads for the compile-time lengths up to 4096 (512
+// otherwise), with 3 CTAs per SM for the forward and 2 for the adjoint, whose
+// scatter needs more registers (best of both settings measured on GB300, n = 512).
+#define TAT_COLS_BOUNDS_F __launch_bounds__((L > 0 && L <= 4096) ? 256 : 512, (L > 0 && L <= 4096) ? 3 : 1)
+#define TAT_COLS_BOUNDS_A __launch_bounds__((L > 0 && L <= 4096) ? 256 : 512, (L > 0 && L <= 4096) ? 2 : 1)
 
 // Column strips are launched strip-major (all images' strip 0 first): the
 // strips near q_x = 0 hold up to 7x the average number of polar samples, so
@@ -99,7 +108,7 @@ __device__ __forceinline__ void strip_and_image(int batch, int* strip, int* b) {
 }
 
 template <int L>
-__global__ void TAT_COLS_BOUNDS k_cols_fwd(DevPlan P, const float2* __restrict__ X, long long xs,
+__global__ void TAT_COLS_BOUNDS_F k_cols_fwd(DevPlan P, const float2* __restrict__ X, long long xs,
                                            float2* __restrict__ Y, long long ys, int S, int nt, int batch) {
   extern __shared__ float2 sm[];
   int strip, b;
@@ -107,7 +116,6 @@ __global__ void TAT_COLS_BOUNDS k_cols_fwd(DevPlan P, const float2* __restrict__
   const int SL = spad_len(P.N);
   float2* slot0 = sm;
   float2* slot1 = sm + SL;
-  float2* stage = sm + 2 * SL;  // [n][S+1]: the strip's input, loaded row by row
   const int tid = threadIdx.x, NT = blockDim.x;
   const int c0 = strip * S;
   const int c1 = min(c0 + S, P.ncol - 1);  // owned stencil columns i0 in [c0, c1)
@@ -115,30 +123,28 @@ __global__ void TAT_COLS_BOUNDS k_cols_fwd(DevPlan P, const float2* __restrict__
   const float2* Xb = X + (size_t)b * xs;
   float2* Yb = Y + (size_t)b * ys;
   const int N = P.N;
-  for (int e = tid; e < P.n * ncols; e += NT) {
-    const int iy = e / ncols, cc = e - iy * ncols;
-    stage[iy * (S + 1) + cc] = Xb[(size_t)iy * P.ncol + c0 + cc];
-  }
-  __syncthreads();
 #pragma unroll 1
   for (int cc = 0; cc < ncols; ++cc) {
     float2* buf = (cc & 1) ? slot1 : slot0;
     const int c = c0 + cc;
-    for (int iy = tid; iy < P.n; iy += NT) buf[spad(iy)] = stage[iy * (S + 1) + cc];
+    const float2* col = Xb + (size_t)c * P.n;  // R[c][0..n): contiguous
+    for (int iy = tid; iy < P.n; iy += NT) buf[spad(iy)] = col[iy];
     __syncthreads();
-    // column DFT over the n nonzero rows, times the phase e^{i q dxi} of each output row
-    fft<L, false>(buf, P.fN, tid, nt, P.n, N, nullptr, P.phase);
+    // column DFT over the n nonzero rows (the phase e^{i q dxi} of each output
+    // row is applied by the gather below)
+    col_fft_fwd<L>(buf, P.fN, tid, nt, P.n, nullptr);
     if (cc > 0) {
       const float2* A = (cc & 1) ? slot0 : slot1;  // column c-1
       const float2* B = buf;                       // column c
       const int e1 = P.coloff[c];
       for (int e = P.coloff[c - 1] + tid; e < e1; e += NT) {
         const PolarEntry pe = P.pts[e];
-        const int qa = wrapN(pe.k0, N), qb = wrapN(pe.k0 + 1, N);
+        const int ra = wrapN(pe.k0, N), rb = wrapN(pe.k0 + 1, N);
+        const int qa = spad(colpos<L>(ra)), qb = spad(colpos<L>(rb));
         const float a = pe.a, bb = pe.b;
-        const float2 va = cadd(cscale(A[spad(qa)], 1.f - a), cscale(B[spad(qa)], a));
-        const float2 vb = cadd(cscale(A[spad(qb)], 1.f - a), cscale(B[spad(qb)], a));
-        Yb[pe.p] = cadd(cscale(va, 1.f - bb), cscale(vb, bb));
+        const float2 va = cadd(cscale(A[qa], 1.f - a), cscale(B[qa], a));
+        const float2 vb = cadd(cscale(A[qb], 1.f - a), cscale(B[qb], a));
+        Yb[pe.p] = cadd(cscale(cmul(va, __ldg(&P.phase[ra])), 1.f - bb), cscale(cmul(vb, __ldg(&P.phase[rb])), bb));
       }
     }
     __syncthreads();
@@ -450,6 +456,7 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
 // so equal rows form runs of lanes; when a warp holds runs, they are summed
 // with a segmented shuffle scan and only the last lane of each run issues the
 // shared-memory atomics (near the origin up to 64 samples share a cell).
+template <int L>
 __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* __restrict__ Yb, int c, float2* left,
                                                float2* right, int tid, int NT) {
   const unsigned full = 0xffffffffu;
@@ -463,11 +470,14 @@ __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* _
       const PolarEntry pe = P.pts[e];
       const float2 val = Yb[pe.p];
       key = pe.k0;
+      // conj(phase) of the two stencil rows (transpose of the column phase)
+      const float2 va = cmulc(val, __ldg(&P.phase[wrapN(key, P.N)]));
+      const float2 vb = cmulc(val, __ldg(&P.phase[wrapN(key + 1, P.N)]));
       const float wl = 1.f - pe.a, wr = pe.a, w0 = 1.f - pe.b, w1 = pe.b;
-      v[0] = wl * w0 * val.x; v[1] = wl * w0 * val.y;
-      v[2] = wl * w1 * val.x; v[3] = wl * w1 * val.y;
-      v[4] = wr * w0 * val.x; v[5] = wr * w0 * val.y;
-      v[6] = wr * w1 * val.x; v[7] = wr * w1 * val.y;
+      v[0] = wl * w0 * va.x; v[1] = wl * w0 * va.y;
+      v[2] = wl * w1 * vb.x; v[3] = wl * w1 * vb.y;
+      v[4] = wr * w0 * va.x; v[5] = wr * w0 * va.y;
+      v[6] = wr * w1 * vb.x; v[7] = wr * w1 * vb.y;
     }
     const int prev = __shfl_up_sync(full, key, 1);
     const bool head = lane == 0 || prev != key;
@@ -488,32 +498,31 @@ __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* _
       emit = emit && tail;
     }
     if (emit) {
-      const int qa = wrapN(key, P.N), qb = wrapN(key + 1, P.N);
+      const int qa = spad(colpos<L>(wrapN(key, P.N))), qb = spad(colpos<L>(wrapN(key + 1, P.N)));
       if (left != nullptr) {
-        atomicAdd(&left[spad(qa)].x, v[0]);
-        atomicAdd(&left[spad(qa)].y, v[1]);
-        atomicAdd(&left[spad(qb)].x, v[2]);
-        atomicAdd(&left[spad(qb)].y, v[3]);
+        atomicAdd(&left[qa].x, v[0]);
+        atomicAdd(&left[qa].y, v[1]);
+        atomicAdd(&left[qb].x, v[2]);
+        atomicAdd(&left[qb].y, v[3]);
       }
       if (right != nullptr) {
-        atomicAdd(&right[spad(qa)].x, v[4]);
-        atomicAdd(&right[spad(qa)].y, v[5]);
-        atomicAdd(&right[spad(qb)].x, v[6]);
-        atomicAdd(&right[spad(qb)].y, v[7]);
+        atomicAdd(&right[qa].x, v[4]);
+        atomicAdd(&right[qa].y, v[5]);
+        atomicAdd(&right[qb].x, v[6]);
+        atomicAdd(&right[qb].y, v[7]);
       }
     }
   }
 }
 
 template <int L>
-__global__ void TAT_COLS_BOUNDS k_cols_adj(DevPlan P, const float2* __restrict__ Y, long long ys,
+__global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict__ Y, long long ys,
                                            float2* __restrict__ X, long long xs, int S, int nt, int batch) {
   extern __shared__ float2 sm[];
   int strip, b;
   strip_and_image(batch, &strip, &b);
   const int N = P.N;
   const int SL = spad_len(N);
-  float2* stage = sm + 2 * SL;  // [n][S]: the strip's output rows, written out at the end
   const int tid = threadIdx.x, NT = blockDim.x;
   const int c0 = strip * S;
   const int c1 = min(c0 + S, P.ncol);  // owned columns [c0, c1)
@@ -524,7 +533,7 @@ __global__ void TAT_COLS_BOUNDS k_cols_adj(DevPlan P, const float2* __restrict__
     float2* first = slot(c0);
     for (int q = tid; q < SL; q += NT) first[q] = make_float2(0.f, 0.f);
     __syncthreads();
-    if (c0 >= 1) scatter_column(P, Yb, c0 - 1, nullptr, first, tid, NT);  // right side of the previous column
+    if (c0 >= 1) scatter_column<L>(P, Yb, c0 - 1, nullptr, first, tid, NT);  // right side of the previous column
   }
 #pragma unroll 1
   for (int c = c0; c < c1; ++c) {
@@ -533,32 +542,30 @@ __global__ void TAT_COLS_BOUNDS k_cols_adj(DevPlan P, const float2* __restrict__
     if (nxt != nullptr)
       for (int q = tid; q < SL; q += NT) nxt[q] = make_float2(0.f, 0.f);
     __syncthreads();
-    if (c <= P.ncol - 2) scatter_column(P, Yb, c, cur, nxt, tid, NT);
+    if (c <= P.ncol - 2) scatter_column<L>(P, Yb, c, cur, nxt, tid, NT);
     __syncthreads();
     if (c == 0) {
       // Column 0 also receives the mirrored samples of the other half circle:
       // F'(0, q) += conj(F'(0, -q)).
       for (int q = tid; q < N / 2; q += NT) {
         if (q == 0) {
-          const float2 s = cur[0];
-          cur[0] = make_float2(2.f * s.x, 0.f);
+          const int p0 = spad(colpos<L>(0));
+          const float2 s = cur[p0];
+          cur[p0] = make_float2(2.f * s.x, 0.f);
         } else {
-          const float2 A = cur[spad(q)], B = cur[spad(N - q)];
-          cur[spad(q)] = cadd(A, cconj(B));
-          cur[spad(N - q)] = cadd(B, cconj(A));
+          const int pa = spad(colpos<L>(q)), pb = spad(colpos<L>(N - q));
+          const float2 A = cur[pa], B = cur[pb];
+          cur[pa] = cadd(A, cconj(B));
+          cur[pb] = cadd(B, cconj(A));
         }
       }
       __syncthreads();
     }
-    // inverse column DFT of conj(phase) * F', first n rows only
-    fft<L, true>(cur, P.fN, tid, nt, N, P.n, P.phase, nullptr);
-    for (int iy = tid; iy < P.n; iy += NT) stage[iy * S + (c - c0)] = cur[spad(iy)];
+    // inverse column DFT (conj(phase) already applied by the scatter), first n rows only
+    col_fft_inv<L>(cur, P.fN, tid, nt, P.n, nullptr);
+    float2* col = Xb + (size_t)c * P.n;  // R'[c][0..n): contiguous
+    for (int iy = tid; iy < P.n; iy += NT) col[iy] = cur[spad(iy)];
     __syncthreads();
-  }
-  const int w = c1 - c0;
-  for (int e = tid; e < P.n * w; e += NT) {
-    const int iy = e / w, cc = e - iy * w;
-    Xb[(size_t)iy * P.ncol + c0 + cc] = stage[iy * S + cc];
   }
 }
 
@@ -575,17 +582,21 @@ __global__ void __launch_bounds__(1024) k_rows_adj(DevPlan P, const float2* __re
   const int iy1 = 2 * pair, iy2 = 2 * pair + 1;
   const bool v1 = iy1 < P.n, v2 = iy2 < P.n;
   const float2* Xb = X + (size_t)b * xs;
-  for (int q = gt; q < N; q += nt) {
-    float2 z = make_float2(0.f, 0.f);
-    if (q != N / 2) {
-      const int qq = q < N / 2 ? q : N - q;
-      float2 h1 = v1 ? cmulc(Xb[(size_t)iy1 * P.ncol + qq], P.phase[qq]) : make_float2(0.f, 0.f);
-      float2 h2 = v2 ? cmulc(Xb[(size_t)iy2 * P.ncol + qq], P.phase[qq]) : make_float2(0.f, 0.f);
-      if (qq == 0) { h1.y = 0.f; h2.y = 0.f; }
-      if (q > N / 2) { h1 = cconj(h1); h2 = cconj(h2); }
-      z = make_float2(h1.x - h2.y, h1.y + h2.x);
-    }
-    buf[spad(q)] = z;
+  // Rebuild each row's Hermitian spectrum from R'[q][iy] (column-major):
+  // H[q] = conj(phase[q]) R'[q] for q < N/2, H[N-q] = conj(H[q]), H[N/2] = 0;
+  // consecutive threads read consecutive rows of one column.
+  const int pair0 = blockIdx.x * RP;
+  for (int e = threadIdx.x; e < P.ncol * RP; e += blockDim.x) {
+    const int q = e / RP, gg = e - q * RP;
+    const int py1 = 2 * (pair0 + gg);
+    float2* bg = sm + gg * SL;
+    const float2* col = Xb + (size_t)q * P.n;
+    float2 h1 = py1 < P.n ? cmulc(col[py1], P.phase[q]) : make_float2(0.f, 0.f);
+    float2 h2 = py1 + 1 < P.n ? cmulc(col[py1 + 1], P.phase[q]) : make_float2(0.f, 0.f);
+    if (q == 0) { h1.y = 0.f; h2.y = 0.f; }
+    bg[spad(q)] = make_float2(h1.x - h2.y, h1.y + h2.x);
+    if (q > 0) bg[spad(N - q)] = make_float2(h1.x + h2.y, h2.x - h1.y);  // conj(h1) + i conj(h2)
+    else bg[spad(N / 2)] = make_float2(0.f, 0.f);
   }
   __syncthreads();
   fft<L, true>(buf, P.fN, gt, nt, N, P.n);

@@ -457,7 +457,7 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
   }
   // Launch shapes.
   LaunchCfg& c = P->cfg;
-  c.rows_pairs = 2;
+  c.rows_pairs = std::max(1, std::min(4, 1024 / c.nt_N));  // up to 4 row pairs (1024 threads) per CTA
   c.strip = 8;
   c.rings_per_cta = 4;
   c.t_tile = 16;
