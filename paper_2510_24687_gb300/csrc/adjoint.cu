@@ -43,7 +43,7 @@ tat_status launch_adjoint(const tat_plan_s* Pl, int batch, const float* g, long 
     ok &= ensure_smem<k_cols_adj<L>>(dev) && ensure_smem<k_rows_adj<L>>(dev);
     k_cols_adj<L><<<s.cols_grid_a, s.cols_block, s.cols_smem_a, st>>>(P, Y, ys, X, xs, c.strip, c.nt_N, batch);
     stage_done();
-    k_rows_adj<L><<<s.rows_grid, s.rows_block, s.rows_smem, st>>>(P, X, xs, f, fs, c.rows_pairs, c.nt_N);
+    k_rows_adj<L><<<s.rows_grid, s.rows_block, s.rows_smem, st>>>(P, X, xs, f, fs, c.rows_pairs, c.nt_rows);
     stage_done();
   });
   return check_launch(ok);

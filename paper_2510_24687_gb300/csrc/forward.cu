@@ -43,7 +43,7 @@ tat_status launch_forward(const tat_plan_s* Pl, int batch, const float* f, long 
   dispatch_N(P.N, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_rows_fwd<L>>(dev) && ensure_smem<k_cols_fwd<L>>(dev);
-    k_rows_fwd<L><<<s.rows_grid, s.rows_block, s.rows_smem, st>>>(P, f, fs, X, xs, c.rows_pairs, c.nt_N);
+    k_rows_fwd<L><<<s.rows_grid, s.rows_block, s.rows_smem, st>>>(P, f, fs, X, xs, c.rows_pairs, c.nt_rows);
     stage_done();
     k_cols_fwd<L><<<s.cols_grid_f, s.cols_block, s.cols_smem_f, st>>>(P, X, xs, Y, ys, c.strip, c.nt_N, batch);
     stage_done();

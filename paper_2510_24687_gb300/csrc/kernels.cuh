@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __res
     buf[spad(ix)] = make_float2(a, c);
   }
   __syncthreads();
-  fft<L, false>(buf, P.fN, gt, nt, P.n, P.N);
+  col_fft_fwd<L>(buf, P.fN, gt, nt, P.n, nullptr);
   // Split the two real rows and store R[q][iy] (column-major); the RP pairs of
   // this CTA are adjacent rows, so consecutive threads write consecutive rows.
   float2* Xb = X + (size_t)b * xs;
@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __res
     const int py1 = 2 * (pair0 + gg);
     if (py1 >= P.n) continue;
     const float2* bg = sm + gg * SL;
-    const float2 Z = bg[spad(q)];
-    const float2 Zc = cconj(bg[spad(q == 0 ? 0 : P.N - q)]);
+    const float2 Z = bg[spad(colpos<L>(q))];
+    const float2 Zc = cconj(bg[spad(colpos<L>(q == 0 ? 0 : P.N - q))]);
     const float2 x1 = cscale(cadd(Z, Zc), 0.5f);
     const float2 dd = csub(Z, Zc);
     const float2 x2 = make_float2(0.5f * dd.y, -0.5f * dd.x);
@@ -594,12 +594,12 @@ __global__ void __launch_bounds__(1024) k_rows_adj(DevPlan P, const float2* __re
     float2 h1 = py1 < P.n ? cmulc(col[py1], P.phase[q]) : make_float2(0.f, 0.f);
     float2 h2 = py1 + 1 < P.n ? cmulc(col[py1 + 1], P.phase[q]) : make_float2(0.f, 0.f);
     if (q == 0) { h1.y = 0.f; h2.y = 0.f; }
-    bg[spad(q)] = make_float2(h1.x - h2.y, h1.y + h2.x);
-    if (q > 0) bg[spad(N - q)] = make_float2(h1.x + h2.y, h2.x - h1.y);  // conj(h1) + i conj(h2)
-    else bg[spad(N / 2)] = make_float2(0.f, 0.f);
+    bg[spad(colpos<L>(q))] = make_float2(h1.x - h2.y, h1.y + h2.x);
+    if (q > 0) bg[spad(colpos<L>(N - q))] = make_float2(h1.x + h2.y, h2.x - h1.y);  // conj(h1) + i conj(h2)
+    else bg[spad(colpos<L>(N / 2))] = make_float2(0.f, 0.f);
   }
   __syncthreads();
-  fft<L, true>(buf, P.fN, gt, nt, N, P.n);
+  col_fft_inv<L>(buf, P.fN, gt, nt, P.n, nullptr);
   float* fb = f + (size_t)b * fs;
   const int2 r1 = v1 ? P.rowrange[iy1] : make_int2(0, 0);
   const int2 r2 = v2 ? P.rowrange[iy2] : make_int2(0, 0);

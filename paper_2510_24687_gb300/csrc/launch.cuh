@@ -24,7 +24,7 @@ inline Shapes shapes(const tat_plan_s* Pl, int batch) {
   Shapes s;
   const int npairs = (P.n + 1) / 2;
   s.rows_grid = dim3((npairs + c.rows_pairs - 1) / c.rows_pairs, batch);
-  s.rows_block = c.rows_pairs * c.nt_N;
+  s.rows_block = c.rows_pairs * c.nt_rows;
   s.rows_smem = (size_t)c.rows_pairs * spad_len(P.N) * sizeof(float2);
   // 1-D, strip-major: blockIdx.x = strip * batch + image
   s.cols_grid_f = dim3(((P.ncol - 1 + c.strip - 1) / c.strip) * batch);

@@ -457,7 +457,11 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
   }
   // Launch shapes.
   LaunchCfg& c = P->cfg;
-  c.rows_pairs = std::max(1, std::min(4, 1024 / c.nt_N));  // up to 4 row pairs (1024 threads) per CTA
+  // Lengths RA*256 (RA = 2..16) use the in-place four-step transform, which
+  // needs 256 threads; up to 4 row pairs (1024 threads) per CTA.
+  const bool four_step = d.N == 512 || d.N == 1024 || d.N == 2048 || d.N == 4096;
+  c.nt_rows = four_step ? std::max(c.nt_N, 256) : c.nt_N;
+  c.rows_pairs = std::max(1, std::min(4, 1024 / c.nt_rows));
   c.strip = 8;
   c.rings_per_cta = 4;
   c.t_tile = 16;

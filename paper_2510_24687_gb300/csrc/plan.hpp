@@ -66,6 +66,7 @@ struct LaunchCfg {
   int rings_per_cta;  // rings per CTA in the angular pass
   int t_tile;         // time samples per CTA in the theta pass (even)
   int nt_N, nt_phi, nt_2M, nt_det;  // threads per FFT of each length
+  int nt_rows;        // threads per row transform (the four-step lengths need 256)
 };
 
 }  // namespace tat
