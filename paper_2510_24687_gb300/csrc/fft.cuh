@@ -178,6 +178,35 @@ __device__ __forceinline__ void apply_twiddles(float2* v, const float2* __restri
   }
 }
 
+// Same as apply_twiddles, with w^1, w^2, w^4, w^8 supplied by the caller.
+template <int R, bool INV>
+__device__ __forceinline__ void apply_twiddles_given(float2* v, float2 w1, float2 w2, float2 w4, float2 w8) {
+  auto mul = [](float2 a, float2 w) { return INV ? cmulc(a, w) : cmul(a, w); };
+  v[1] = mul(v[1], w1);
+  if constexpr (R >= 3) v[2] = mul(v[2], w2);
+  if constexpr (R >= 4) {
+    const float2 w3 = cmul(w1, w2);
+    v[3] = mul(v[3], w3);
+    if constexpr (R >= 8) {
+      v[4] = mul(v[4], w4);
+      v[5] = mul(v[5], cmul(w4, w1));
+      v[6] = mul(v[6], cmul(w4, w2));
+      v[7] = mul(v[7], cmul(w4, w3));
+      if constexpr (R >= 16) {
+        v[8] = mul(v[8], w8);
+        v[9] = mul(v[9], cmul(w8, w1));
+        v[10] = mul(v[10], cmul(w8, w2));
+        v[11] = mul(v[11], cmul(w8, w3));
+        const float2 w12 = cmul(w8, w4);
+        v[12] = mul(v[12], w12);
+        v[13] = mul(v[13], cmul(w12, w1));
+        v[14] = mul(v[14], cmul(w12, w2));
+        v[15] = mul(v[15], cmul(w12, w3));
+      }
+    }
+  }
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void fft_pass(float2* buf, int L, int Ns, const float2* __restrict__ tw, int tid,
                                          int nthr, bool first, bool last, int n_in, int n_out,
@@ -324,15 +353,35 @@ __device__ __forceinline__ int colpos(int q) {
   }
 }
 
+// Twiddle tables of the four-step transform, 192 float2 per transform length
+// (FP64-computed in the plan; copied to shared memory once per CTA):
+//   [  0, 64): w_N^(16 a p), a < 16, p in {1,2,4,8}   (step A, high digit of n2)
+//   [ 64,128): w_N^(b p),    b < 16                   (step A, low digit of n2)
+//   [128,192): w_256^(m p),  m < 16                   (step B1)
+// stored as [p][a], [p][b], [p][m] with p index 0..3 for powers 1, 2, 4, 8.
+constexpr int kFourStepTw = 192;
+
+__device__ __forceinline__ void load_fourstep_tw(float2* smtw, const float2* __restrict__ g, int tid, int nthr) {
+  for (int i = tid; i < kFourStepTw; i += nthr) smtw[i] = g[i];
+}
+
+__device__ __forceinline__ void stepA_tw(const float2* smtw, int n2, float2& w1, float2& w2, float2& w4, float2& w8) {
+  const int a = n2 >> 4, b = n2 & 15;
+  w1 = cmul(smtw[a], smtw[64 + b]);
+  w2 = cmul(smtw[16 + a], smtw[80 + b]);
+  w4 = cmul(smtw[32 + a], smtw[96 + b]);
+  w8 = cmul(smtw[48 + a], smtw[112 + b]);
+}
+
 // Forward: x[0, n_in) in natural order -> X[q] * post[q] at colpos(q).
+// `smtw`: the shared-memory copy of the four-step twiddle table.
 template <int L>
-__device__ __forceinline__ void col_fft_fwd(float2* buf, const FftDev& f, int tid, int nthr, int n_in,
-                                            const float2* __restrict__ post) {
+__device__ __forceinline__ void col_fft_fwd(float2* buf, const FftDev& f, const float2* smtw, int tid, int nthr,
+                                            int n_in, const float2* __restrict__ post) {
   if constexpr (!FourStep<L>::on) {
     fft<L, false>(buf, f, tid, nthr, n_in, f.L, nullptr, post);
   } else {
     constexpr int RA = FourStep<L>::RA;
-    const float2* __restrict__ tw = f.tw;
     if (tid < 256) {
       const int n2 = tid;
       float2 v[RA];
@@ -342,7 +391,9 @@ __device__ __forceinline__ void col_fft_fwd(float2* buf, const FftDev& f, int ti
         v[n1] = idx < n_in ? buf[spad(idx)] : make_float2(0.f, 0.f);
       }
       bfly<RA, false>(v);
-      apply_twiddles<RA, false>(v, tw, n2);
+      float2 w1, w2, w4, w8;
+      stepA_tw(smtw, n2, w1, w2, w4, w8);
+      apply_twiddles_given<RA, false>(v, w1, w2, w4, w8);
 #pragma unroll
       for (int k1 = 0; k1 < RA; ++k1) buf[spad(256 * k1 + n2)] = v[k1];
     }
@@ -354,7 +405,7 @@ __device__ __forceinline__ void col_fft_fwd(float2* buf, const FftDev& f, int ti
 #pragma unroll
       for (int m1 = 0; m1 < 16; ++m1) v[m1] = buf[spad(base + 16 * m1 + m)];
       bfly<16, false>(v);
-      apply_twiddles<16, false>(v, tw, RA * m);
+      apply_twiddles_given<16, false>(v, smtw[128 + m], smtw[144 + m], smtw[160 + m], smtw[176 + m]);
 #pragma unroll
       for (int k21 = 0; k21 < 16; ++k21) buf[spad(base + 16 * k21 + m)] = v[k21];
       __syncwarp();
@@ -374,13 +425,12 @@ __device__ __forceinline__ void col_fft_fwd(float2* buf, const FftDev& f, int ti
 
 // Inverse (unnormalised): Z[q] at colpos(q), times conj(pre[q]) -> z[0, n_out) in natural order.
 template <int L>
-__device__ __forceinline__ void col_fft_inv(float2* buf, const FftDev& f, int tid, int nthr, int n_out,
-                                            const float2* __restrict__ pre) {
+__device__ __forceinline__ void col_fft_inv(float2* buf, const FftDev& f, const float2* smtw, int tid, int nthr,
+                                            int n_out, const float2* __restrict__ pre) {
   if constexpr (!FourStep<L>::on) {
     fft<L, true>(buf, f, tid, nthr, f.L, n_out, pre, nullptr);
   } else {
     constexpr int RA = FourStep<L>::RA;
-    const float2* __restrict__ tw = f.tw;
     if (tid < RA * 16) {
       const int blk = tid >> 4, m = tid & 15;
       const int base = 256 * blk;
@@ -397,7 +447,7 @@ __device__ __forceinline__ void col_fft_inv(float2* buf, const FftDev& f, int ti
       __syncwarp();
 #pragma unroll
       for (int k21 = 0; k21 < 16; ++k21) v[k21] = buf[spad(base + 16 * k21 + m)];
-      apply_twiddles<16, true>(v, tw, RA * m);
+      apply_twiddles_given<16, true>(v, smtw[128 + m], smtw[144 + m], smtw[160 + m], smtw[176 + m]);
       bfly<16, true>(v);
 #pragma unroll
       for (int m1 = 0; m1 < 16; ++m1) buf[spad(base + 16 * m1 + m)] = v[m1];
@@ -408,7 +458,9 @@ __device__ __forceinline__ void col_fft_inv(float2* buf, const FftDev& f, int ti
       float2 v[RA];
 #pragma unroll
       for (int k1 = 0; k1 < RA; ++k1) v[k1] = buf[spad(256 * k1 + n2)];
-      apply_twiddles<RA, true>(v, tw, n2);
+      float2 w1, w2, w4, w8;
+      stepA_tw(smtw, n2, w1, w2, w4, w8);
+      apply_twiddles_given<RA, true>(v, w1, w2, w4, w8);
       bfly<RA, true>(v);
 #pragma unroll
       for (int n1 = 0; n1 < RA; ++n1)

@@ -57,6 +57,8 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __res
   const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
   const int SL = spad_len(P.N);
   float2* buf = sm + g * SL;
+  float2* smtw = sm + RP * SL;  // four-step twiddles
+  load_fourstep_tw(smtw, P.fstw, threadIdx.x, blockDim.x);
   const int pair = blockIdx.x * RP + g;
   const int iy1 = 2 * pair, iy2 = 2 * pair + 1;
   const bool v1 = iy1 < P.n, v2 = iy2 < P.n;
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __res
     buf[spad(ix)] = make_float2(a, c);
   }
   __syncthreads();
-  col_fft_fwd<L>(buf, P.fN, gt, nt, P.n, nullptr);
+  col_fft_fwd<L>(buf, P.fN, smtw, gt, nt, P.n, nullptr);
   // Split the two real rows and store R[q][iy] (column-major); the RP pairs of
   // this CTA are adjacent rows, so consecutive threads write consecutive rows.
   float2* Xb = X + (size_t)b * xs;
@@ -116,7 +118,9 @@ __global__ void TAT_COLS_BOUNDS_F k_cols_fwd(DevPlan P, const float2* __restrict
   const int SL = spad_len(P.N);
   float2* slot0 = sm;
   float2* slot1 = sm + SL;
+  float2* smtw = sm + 2 * SL;  // four-step twiddles
   const int tid = threadIdx.x, NT = blockDim.x;
+  load_fourstep_tw(smtw, P.fstw, tid, NT);
   const int c0 = strip * S;
   const int c1 = min(c0 + S, P.ncol - 1);  // owned stencil columns i0 in [c0, c1)
   const int ncols = c1 - c0 + 1;           // spectrum columns c0..c1
@@ -132,7 +136,7 @@ __global__ void TAT_COLS_BOUNDS_F k_cols_fwd(DevPlan P, const float2* __restrict
     __syncthreads();
     // column DFT over the n nonzero rows (the phase e^{i q dxi} of each output
     // row is applied by the gather below)
-    col_fft_fwd<L>(buf, P.fN, tid, nt, P.n, nullptr);
+    col_fft_fwd<L>(buf, P.fN, smtw, tid, nt, P.n, nullptr);
     if (cc > 0) {
       const float2* A = (cc & 1) ? slot0 : slot1;  // column c-1
       const float2* B = buf;                       // column c
@@ -524,6 +528,8 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
   const int N = P.N;
   const int SL = spad_len(N);
   const int tid = threadIdx.x, NT = blockDim.x;
+  float2* smtw = sm + 2 * SL;  // four-step twiddles
+  load_fourstep_tw(smtw, P.fstw, tid, NT);
   const int c0 = strip * S;
   const int c1 = min(c0 + S, P.ncol);  // owned columns [c0, c1)
   const float2* Yb = Y + (size_t)b * ys;
@@ -562,7 +568,7 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
       __syncthreads();
     }
     // inverse column DFT (conj(phase) already applied by the scatter), first n rows only
-    col_fft_inv<L>(cur, P.fN, tid, nt, P.n, nullptr);
+    col_fft_inv<L>(cur, P.fN, smtw, tid, nt, P.n, nullptr);
     float2* col = Xb + (size_t)c * P.n;  // R'[c][0..n): contiguous
     for (int iy = tid; iy < P.n; iy += NT) col[iy] = cur[spad(iy)];
     __syncthreads();
@@ -578,6 +584,8 @@ __global__ void __launch_bounds__(1024) k_rows_adj(DevPlan P, const float2* __re
   const int N = P.N;
   const int SL = spad_len(N);
   float2* buf = sm + g * SL;
+  float2* smtw = sm + RP * SL;  // four-step twiddles
+  load_fourstep_tw(smtw, P.fstw, threadIdx.x, blockDim.x);
   const int pair = blockIdx.x * RP + g;
   const int iy1 = 2 * pair, iy2 = 2 * pair + 1;
   const bool v1 = iy1 < P.n, v2 = iy2 < P.n;
@@ -599,7 +607,7 @@ __global__ void __launch_bounds__(1024) k_rows_adj(DevPlan P, const float2* __re
     else bg[spad(colpos<L>(N / 2))] = make_float2(0.f, 0.f);
   }
   __syncthreads();
-  col_fft_inv<L>(buf, P.fN, gt, nt, P.n, nullptr);
+  col_fft_inv<L>(buf, P.fN, smtw, gt, nt, P.n, nullptr);
   float* fb = f + (size_t)b * fs;
   const int2 r1 = v1 ? P.rowrange[iy1] : make_int2(0, 0);
   const int2 r2 = v2 ? P.rowrange[iy2] : make_int2(0, 0);

@@ -25,13 +25,13 @@ inline Shapes shapes(const tat_plan_s* Pl, int batch) {
   const int npairs = (P.n + 1) / 2;
   s.rows_grid = dim3((npairs + c.rows_pairs - 1) / c.rows_pairs, batch);
   s.rows_block = c.rows_pairs * c.nt_rows;
-  s.rows_smem = (size_t)c.rows_pairs * spad_len(P.N) * sizeof(float2);
+  s.rows_smem = ((size_t)c.rows_pairs * spad_len(P.N) + kFourStepTw) * sizeof(float2);
   // 1-D, strip-major: blockIdx.x = strip * batch + image
   s.cols_grid_f = dim3(((P.ncol - 1 + c.strip - 1) / c.strip) * batch);
   s.cols_grid_a = dim3(((P.ncol + c.strip - 1) / c.strip) * batch);
   s.cols_block = c.nt_N < 256 ? 256 : c.nt_N;
-  s.cols_smem_f = 2 * (size_t)spad_len(P.N) * sizeof(float2);
-  s.cols_smem_a = 2 * (size_t)spad_len(P.N) * sizeof(float2);
+  s.cols_smem_f = (2 * (size_t)spad_len(P.N) + kFourStepTw) * sizeof(float2);
+  s.cols_smem_a = (2 * (size_t)spad_len(P.N) + kFourStepTw) * sizeof(float2);
   s.ntiles = (P.J + c.rings_per_cta - 1) / c.rings_per_cta;
   s.rings_grid = dim3(s.ntiles + P.n_low, batch);
   s.rings_block = c.rings_per_cta * c.nt_phi;  // >= 128: room for the 96-float reduction scratch

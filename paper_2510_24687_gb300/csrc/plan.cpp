@@ -357,6 +357,25 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
     }
     TAT_TRY(upload(P, ph, &d.phase));
   }
+  // Four-step twiddles of the length-N row/column transforms (N = RA*256):
+  // w_N^(16 a p), w_N^(b p), w_256^(m p) for a, b, m < 16 and p = 1, 2, 4, 8.
+  {
+    std::vector<float2> ft(192, make_float2(1.f, 0.f));
+    if (d.N % 256 == 0) {
+      const int pw[4] = {1, 2, 4, 8};
+      for (int pi = 0; pi < 4; ++pi)
+        for (int i = 0; i < 16; ++i) {
+          double c, s;
+          cos_sin_2pi(-(long long)16 * i * pw[pi], d.N, &c, &s);
+          ft[pi * 16 + i] = make_float2((float)c, (float)s);
+          cos_sin_2pi(-(long long)i * pw[pi], d.N, &c, &s);
+          ft[64 + pi * 16 + i] = make_float2((float)c, (float)s);
+          cos_sin_2pi(-(long long)i * pw[pi], 256, &c, &s);
+          ft[128 + pi * 16 + i] = make_float2((float)c, (float)s);
+        }
+    }
+    TAT_TRY(upload(P, ft, &d.fstw));
+  }
   // Support disk Pi_Omega0: node kept iff (2ix-(n-1))^2 + (2iy-(n-1))^2 <= (r (n-1))^2.
   {
     const double rr = (D.support_radius * (n - 1)) * (D.support_radius * (n - 1));

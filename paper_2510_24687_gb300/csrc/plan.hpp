@@ -57,6 +57,7 @@ struct DevPlan {
   const float* Bh;                 // [2 x n_low]     w_q*dlam*lam_q*J_k(lam_q)/n_phi
   const float* Lcos;               // [n_low x n_t]   cos(lam_q t_m)
   const float2* cs_half;           // [nh] (cos phi, sin phi) of the half-circle angles
+  const float2* fstw;              // [192] four-step twiddles of the length-N transforms
 };
 
 // Launch shapes (host-side knobs; chosen per plan).
