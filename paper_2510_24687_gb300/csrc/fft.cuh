@@ -207,10 +207,31 @@ __device__ __forceinline__ void apply_twiddles_given(float2* v, float2 w1, float
   }
 }
 
+// Base powers w^1, w^2, w^4, w^8 of twiddle index k < Ns from a per-pass
+// shared-memory table (layout in FftDev); only the powers radix R needs.
+template <int R>
+__device__ __forceinline__ void pass_tw(const float2* t, int Ns, int k, float2& w1, float2& w2, float2& w4,
+                                        float2& w8) {
+  if (Ns <= 16 || (Ns & 15)) {
+    w1 = t[k];
+    if constexpr (R >= 3) w2 = t[Ns + k];
+    if constexpr (R >= 8) w4 = t[2 * Ns + k];
+    if constexpr (R >= 16) w8 = t[3 * Ns + k];
+  } else {
+    const int na = Ns >> 4, a = k >> 4, b = k & 15;
+    const float2* lo = t + 4 * na;
+    w1 = cmul(t[a], lo[b]);
+    if constexpr (R >= 3) w2 = cmul(t[na + a], lo[16 + b]);
+    if constexpr (R >= 8) w4 = cmul(t[2 * na + a], lo[32 + b]);
+    if constexpr (R >= 16) w8 = cmul(t[3 * na + a], lo[48 + b]);
+  }
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void fft_pass(float2* buf, int L, int Ns, const float2* __restrict__ tw, int tid,
                                          int nthr, bool first, bool last, int n_in, int n_out,
-                                         const float2* __restrict__ pre, const float2* __restrict__ post) {
+                                         const float2* __restrict__ pre, const float2* __restrict__ post,
+                                         const float2* ptws = nullptr) {
   constexpr int NB = 16 / R;
   const int nb = L / R;
   const int tws = L / (Ns * R);
@@ -231,7 +252,15 @@ __device__ __forceinline__ void fft_pass(float2* buf, int L, int Ns, const float
           v[b][r] = buf[spad(idx)];
         }
       }
-      if (Ns > 1) apply_twiddles<R, INV>(v[b], tw, (j % Ns) * tws);
+      if (Ns > 1) {
+        if (ptws != nullptr) {
+          float2 w1 = make_float2(1.f, 0.f), w2 = w1, w4 = w1, w8 = w1;
+          pass_tw<R>(ptws, Ns, j % Ns, w1, w2, w4, w8);
+          apply_twiddles_given<R, INV>(v[b], w1, w2, w4, w8);
+        } else {
+          apply_twiddles<R, INV>(v[b], tw, (j % Ns) * tws);
+        }
+      }
       bfly<R, INV>(v[b]);
     }
   }
@@ -280,31 +309,33 @@ struct Sched {
 };
 
 template <int L, bool INV, int S, int NS>
-__device__ __forceinline__ void fft_ct_from(float2* buf, const float2* __restrict__ tw, int tid, int nthr, int n_in,
-                                            int n_out, const float2* pre, const float2* post) {
+__device__ __forceinline__ void fft_ct_from(float2* buf, const FftDev& f, int tid, int nthr, int n_in, int n_out,
+                                            const float2* pre, const float2* post, const float2* smptw) {
   if constexpr (S < Sched<L>::npass) {
     constexpr int R = Sched<L>::radix(S);
-    fft_pass<R, INV>(buf, L, NS, tw, tid, nthr, S == 0, S == Sched<L>::npass - 1, n_in, n_out, pre, post);
-    fft_ct_from<L, INV, S + 1, NS * R>(buf, tw, tid, nthr, n_in, n_out, pre, post);
+    fft_pass<R, INV>(buf, L, NS, f.tw, tid, nthr, S == 0, S == Sched<L>::npass - 1, n_in, n_out, pre, post,
+                     smptw != nullptr && S > 0 ? smptw + f.ptw_off[S] : nullptr);
+    fft_ct_from<L, INV, S + 1, NS * R>(buf, f, tid, nthr, n_in, n_out, pre, post, smptw);
   }
 }
 
 // Runtime length (any 2^k 3^m): the same schedule read from the plan.
 template <bool INV>
 __device__ __forceinline__ void fft_run(float2* buf, const FftDev& f, int tid, int nthr, int n_in, int n_out,
-                                        const float2* pre, const float2* post) {
+                                        const float2* pre, const float2* post, const float2* smptw) {
   const int L = f.L;
   int Ns = 1;
 #pragma unroll 1
   for (int s = 0; s < f.npass; ++s) {
     const int R = f.radix[s];
     const bool first = s == 0, last = s == f.npass - 1;
+    const float2* pt = smptw != nullptr && s > 0 ? smptw + f.ptw_off[s] : nullptr;
     switch (R) {
-      case 16: fft_pass<16, INV>(buf, L, Ns, f.tw, tid, nthr, first, last, n_in, n_out, pre, post); break;
-      case 8: fft_pass<8, INV>(buf, L, Ns, f.tw, tid, nthr, first, last, n_in, n_out, pre, post); break;
-      case 4: fft_pass<4, INV>(buf, L, Ns, f.tw, tid, nthr, first, last, n_in, n_out, pre, post); break;
-      case 3: fft_pass<3, INV>(buf, L, Ns, f.tw, tid, nthr, first, last, n_in, n_out, pre, post); break;
-      default: fft_pass<2, INV>(buf, L, Ns, f.tw, tid, nthr, first, last, n_in, n_out, pre, post); break;
+      case 16: fft_pass<16, INV>(buf, L, Ns, f.tw, tid, nthr, first, last, n_in, n_out, pre, post, pt); break;
+      case 8: fft_pass<8, INV>(buf, L, Ns, f.tw, tid, nthr, first, last, n_in, n_out, pre, post, pt); break;
+      case 4: fft_pass<4, INV>(buf, L, Ns, f.tw, tid, nthr, first, last, n_in, n_out, pre, post, pt); break;
+      case 3: fft_pass<3, INV>(buf, L, Ns, f.tw, tid, nthr, first, last, n_in, n_out, pre, post, pt); break;
+      default: fft_pass<2, INV>(buf, L, Ns, f.tw, tid, nthr, first, last, n_in, n_out, pre, post, pt); break;
     }
     Ns *= R;
   }
@@ -312,11 +343,18 @@ __device__ __forceinline__ void fft_run(float2* buf, const FftDev& f, int tid, i
 
 // L > 0: compile-time schedule (must equal f.L); L == 0: runtime schedule.
 // Reads buf[0, n_in), writes buf[0, n_out); every thread of the CTA must call it.
+// `smptw`: shared-memory copy of f.ptw (null: twiddles from the global table).
 template <int L, bool INV>
 __device__ __forceinline__ void fft(float2* buf, const FftDev& f, int tid, int nthr, int n_in, int n_out,
-                                    const float2* pre = nullptr, const float2* post = nullptr) {
-  if constexpr (L == 0) fft_run<INV>(buf, f, tid, nthr, n_in, n_out, pre, post);
-  else fft_ct_from<L, INV, 0, 1>(buf, f.tw, tid, nthr, n_in, n_out, pre, post);
+                                    const float2* pre = nullptr, const float2* post = nullptr,
+                                    const float2* smptw = nullptr) {
+  if constexpr (L == 0) fft_run<INV>(buf, f, tid, nthr, n_in, n_out, pre, post, smptw);
+  else fft_ct_from<L, INV, 0, 1>(buf, f, tid, nthr, n_in, n_out, pre, post, smptw);
+}
+
+// Copies an FFT's per-pass twiddle tables to shared memory (caller syncs).
+__device__ __forceinline__ void load_pass_tw(float2* dst, const FftDev& f, int tid, int nthr) {
+  for (int i = tid; i < f.ptw_len; i += nthr) dst[i] = f.ptw[i];
 }
 
 }  // namespace tat

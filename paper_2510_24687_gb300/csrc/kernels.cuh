@@ -205,6 +205,8 @@ __global__ void __launch_bounds__(1024) k_rings_fwd(DevPlan P, const float2* __r
   const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
   const int SL = spad_len(P.n_phi);
   float2* buf = sm + g * SL;
+  float2* smptw = sm + RPC * SL;
+  load_pass_tw(smptw, P.fphi, threadIdx.x, blockDim.x);
   const int rbase = 1 + blockIdx.x * RPC;
   const int r = rbase + g;
   const bool valid = r <= P.J;
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(1024) k_rings_fwd(DevPlan P, const float2* __r
     buf[spad(l)] = v;
   }
   __syncthreads();
-  fft<L, false>(buf, P.fphi, gt, nt, P.n_phi, P.K + 1);
+  fft<L, false>(buf, P.fphi, gt, nt, P.n_phi, P.K + 1, nullptr, nullptr, smptw);
   for (int e = threadIdx.x; e < (P.K + 1) * RPC; e += blockDim.x) {
     const int k = e / RPC, gg = e % RPC;
     const int rr = rbase + gg;
@@ -237,6 +239,8 @@ __global__ void __launch_bounds__(1024) k_modes_fwd(DevPlan P, const float2* __r
   const int b = blockIdx.y, k = blockIdx.x;
   const int J1 = P.J + 1, L2 = 2 * P.M;
   const float2* Cm = X + (size_t)b * xs + (size_t)k * J1;
+  float2* smptw = sm + spad_len(L2);
+  load_pass_tw(smptw, P.f2M, threadIdx.x, blockDim.x);
   for (int j = threadIdx.x; j < L2; j += blockDim.x) {
     float2 v = make_float2(0.f, 0.f);
     if (j >= 1 && j <= P.J) v = Cm[j];
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(1024) k_modes_fwd(DevPlan P, const float2* __r
     sm[spad(j)] = v;
   }
   __syncthreads();
-  fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, P.n_t);
+  fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, P.n_t, nullptr, nullptr, smptw);
   float2* G = Y + (size_t)b * ys + (size_t)k * P.n_t;
   const bool low = P.low_on && k <= 1;
   const float2* Ch = X + (size_t)b * xs + (size_t)(P.K + 1) * J1 + (size_t)k * P.n_low;
@@ -289,6 +293,8 @@ __global__ void __launch_bounds__(1024) k_theta_fwd(DevPlan P, const float2* __r
   const int SL = spad_len(P.n_det);
   const int nd = P.n_det;
   const float2* G = Y + (size_t)b * ys;
+  float2* smptw = sm + npair * SL;
+  load_pass_tw(smptw, P.fdet, threadIdx.x, blockDim.x);
   for (int e = threadIdx.x; e < (nd / 2 + 1) * npair; e += blockDim.x) {
     const int bin = e / npair, p = e % npair;
     const int m1 = m0 + 2 * p, m2 = m1 + 1;
@@ -302,7 +308,7 @@ __global__ void __launch_bounds__(1024) k_theta_fwd(DevPlan P, const float2* __r
   __syncthreads();
   {
     const int gi = threadIdx.x / nt, gt = threadIdx.x % nt;
-    fft<L, true>(sm + gi * SL, P.fdet, gt, nt, P.n_det, P.n_det);
+    fft<L, true>(sm + gi * SL, P.fdet, gt, nt, P.n_det, P.n_det, nullptr, nullptr, smptw);
   }
   float* gb = g + (size_t)b * gs;
   for (int e = threadIdx.x; e < nd * TT; e += blockDim.x) {
@@ -325,6 +331,8 @@ __global__ void __launch_bounds__(1024) k_theta_adj(DevPlan P, const float* __re
   const int SL = spad_len(P.n_det);
   const int nd = P.n_det;
   const float* gb = g + (size_t)b * gs;
+  float2* smptw = sm + (TT / 2) * SL;
+  load_pass_tw(smptw, P.fdet, threadIdx.x, blockDim.x);
   for (int e = threadIdx.x; e < nd * TT; e += blockDim.x) {
     const int d = e / TT, tt = e % TT;
     const int m = m0 + tt;
@@ -335,7 +343,7 @@ __global__ void __launch_bounds__(1024) k_theta_adj(DevPlan P, const float* __re
   __syncthreads();
   {
     const int gi = threadIdx.x / nt, gt = threadIdx.x % nt;
-    fft<L, false>(sm + gi * SL, P.fdet, gt, nt, P.n_det, P.n_det);
+    fft<L, false>(sm + gi * SL, P.fdet, gt, nt, P.n_det, P.n_det, nullptr, nullptr, smptw);
   }
   float2* Gp = Y + (size_t)b * ys;
   for (int e = threadIdx.x; e < (P.K + 1) * TT; e += blockDim.x) {
@@ -364,6 +372,8 @@ __global__ void __launch_bounds__(1024) k_modes_adj(DevPlan P, const float2* __r
   const int b = blockIdx.y, k = blockIdx.x;
   const int J1 = P.J + 1, L2 = 2 * P.M;
   const float2* Gp = Y + (size_t)b * ys + (size_t)k * P.n_t;
+  float2* smptw = sm + spad_len(L2);
+  load_pass_tw(smptw, P.f2M, threadIdx.x, blockDim.x);
   for (int j = threadIdx.x; j < L2; j += blockDim.x) {
     float2 v = make_float2(0.f, 0.f);
     if (j < P.n_t) v = Gp[j];
@@ -372,7 +382,7 @@ __global__ void __launch_bounds__(1024) k_modes_adj(DevPlan P, const float2* __r
   }
   __syncthreads();
   const float2 g0 = Gp[0];
-  fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, P.J + 1);
+  fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, P.J + 1, nullptr, nullptr, smptw);
   float2* Dm = X + (size_t)b * xs + (size_t)k * J1;
   const bool low = P.low_on && k <= 1;
   for (int j = threadIdx.x; j < J1; j += blockDim.x) {
@@ -425,6 +435,8 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
     return;
   }
   const int SL = spad_len(P.n_phi);
+  float2* smptw = sm + RPC * SL;
+  load_pass_tw(smptw, P.fphi, threadIdx.x, blockDim.x);
   const int rbase = 1 + blockIdx.x * RPC;
   for (int e = threadIdx.x; e < (P.K + 1) * RPC; e += blockDim.x) {
     const int k = e / RPC, gg = e % RPC;
@@ -442,7 +454,7 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
   __syncthreads();
   const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
   float2* buf = sm + g * SL;
-  fft<L, true>(buf, P.fphi, gt, nt, P.n_phi, P.n_phi);
+  fft<L, true>(buf, P.fphi, gt, nt, P.n_phi, P.n_phi, nullptr, nullptr, smptw);
   const int r = rbase + g;
   if (r <= P.J) {
     const int q4 = P.n_phi / 4;

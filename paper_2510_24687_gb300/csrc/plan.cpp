@@ -278,7 +278,35 @@ tat_status make_fft(tat_plan_s* P, int L, FftDev* f, int* nthreads) {
   }
   *nthreads = fft_threads(*f);
   if (*nthreads < 0) return TAT_ERR_UNSUPPORTED;
-  return upload(P, tw, &f->tw);
+  TAT_TRY(upload(P, tw, &f->tw));
+  // per-pass base-power tables (see FftDev)
+  std::vector<float2> pt;
+  long long Ns = 1;
+  for (int s = 0; s < f->npass; ++s) {
+    const int R = f->radix[s];
+    f->ptw_off[s] = (int)pt.size();
+    if (s > 0) {
+      const long long den = Ns * R;
+      auto push = [&](long long k, int p) {
+        double c, sn;
+        cos_sin_2pi(-k * p, den, &c, &sn);
+        pt.push_back(make_float2((float)c, (float)sn));
+      };
+      const int pw[4] = {1, 2, 4, 8};
+      if (Ns <= 16 || Ns % 16) {
+        for (int pi = 0; pi < 4; ++pi)
+          for (long long k = 0; k < Ns; ++k) push(k, pw[pi]);
+      } else {
+        for (int pi = 0; pi < 4; ++pi)
+          for (long long a = 0; a < Ns / 16; ++a) push(16 * a, pw[pi]);
+        for (int pi = 0; pi < 4; ++pi)
+          for (long long b = 0; b < 16; ++b) push(b, pw[pi]);
+      }
+    }
+    Ns *= R;
+  }
+  f->ptw_len = (int)pt.size();
+  return upload(P, pt, &f->ptw);
 }
 
 }  // namespace

@@ -20,12 +20,20 @@ constexpr int kLowM = 20;
 
 constexpr int kMaxPass = 16;
 
-// One FFT length: radix schedule and its twiddle table e^{-2 pi i k/L}, k < L.
+// One FFT length: radix schedule, its twiddle table e^{-2 pi i k/L}, k < L,
+// and the per-pass tables of the base powers w^p, p = 1, 2, 4, 8, that the
+// kernels stage in shared memory: for a pass with Ns > 1 and twiddle index
+// k < Ns, w = e^{-2 pi i k/(Ns R)}; if Ns <= 16 (or not a multiple of 16) the
+// table is direct, [p][k]; otherwise k = 16a + b and w^p = hi[p][a] * lo[p][b]
+// with hi of Ns/16 and lo of 16 entries per power.
 struct FftDev {
   int L;
   int npass;
   int radix[kMaxPass];
   const float2* tw;
+  const float2* ptw;        // concatenated per-pass tables
+  int ptw_off[kMaxPass];    // offset of pass s (s >= 1)
+  int ptw_len;              // total entries
 };
 
 // One half-plane polar sample: polar slot p (ring*nh + l'), stencil row k0
