@@ -378,6 +378,9 @@ struct FourStep {
   static constexpr bool on = L == 512 || L == 1024 || L == 2048 || L == 4096;
   static constexpr int RA = on ? L / 256 : 1;
 };
+// Steps A and B are looped when a group has fewer threads than 256 (step A)
+// or RA*16 (step B); group sizes are multiples of 32, so every lane of a warp
+// runs the same iterations of step B and __syncwarp stays warp-uniform.
 
 // Position of FFT bin q of a column buffer (identity for other lengths).
 template <int L>
@@ -412,16 +415,17 @@ __device__ __forceinline__ void stepA_tw(const float2* smtw, int n2, float2& w1,
 }
 
 // Forward: x[0, n_in) in natural order -> X[q] * post[q] at colpos(q).
-// `smtw`: the shared-memory copy of the four-step twiddle table.
+// `smtw`: the shared-memory copy of the four-step twiddle table; `nthr`: the
+// threads of the calling group (tid < nthr, all take part in the four-step
+// loops); `sthr` (<= nthr): the thread count of the Stockham fallback.
 template <int L>
 __device__ __forceinline__ void col_fft_fwd(float2* buf, const FftDev& f, const float2* smtw, int tid, int nthr,
-                                            int n_in, const float2* __restrict__ post) {
+                                            int sthr, int n_in, const float2* __restrict__ post) {
   if constexpr (!FourStep<L>::on) {
-    fft<L, false>(buf, f, tid, nthr, n_in, f.L, nullptr, post);
+    fft<L, false>(buf, f, tid, sthr, n_in, f.L, nullptr, post);
   } else {
     constexpr int RA = FourStep<L>::RA;
-    if (tid < 256) {
-      const int n2 = tid;
+    for (int n2 = tid; n2 < 256; n2 += nthr) {
       float2 v[RA];
 #pragma unroll
       for (int n1 = 0; n1 < RA; ++n1) {
@@ -436,8 +440,8 @@ __device__ __forceinline__ void col_fft_fwd(float2* buf, const FftDev& f, const 
       for (int k1 = 0; k1 < RA; ++k1) buf[spad(256 * k1 + n2)] = v[k1];
     }
     __syncthreads();
-    if (tid < RA * 16) {
-      const int blk = tid >> 4, m = tid & 15;
+    for (int t = tid; t < RA * 16; t += nthr) {
+      const int blk = t >> 4, m = t & 15;
       const int base = 256 * blk;
       float2 v[16];
 #pragma unroll
@@ -464,13 +468,13 @@ __device__ __forceinline__ void col_fft_fwd(float2* buf, const FftDev& f, const 
 // Inverse (unnormalised): Z[q] at colpos(q), times conj(pre[q]) -> z[0, n_out) in natural order.
 template <int L>
 __device__ __forceinline__ void col_fft_inv(float2* buf, const FftDev& f, const float2* smtw, int tid, int nthr,
-                                            int n_out, const float2* __restrict__ pre) {
+                                            int sthr, int n_out, const float2* __restrict__ pre) {
   if constexpr (!FourStep<L>::on) {
-    fft<L, true>(buf, f, tid, nthr, f.L, n_out, pre, nullptr);
+    fft<L, true>(buf, f, tid, sthr, f.L, n_out, pre, nullptr);
   } else {
     constexpr int RA = FourStep<L>::RA;
-    if (tid < RA * 16) {
-      const int blk = tid >> 4, m = tid & 15;
+    for (int t = tid; t < RA * 16; t += nthr) {
+      const int blk = t >> 4, m = t & 15;
       const int base = 256 * blk;
       float2 v[16];
 #pragma unroll
@@ -491,8 +495,7 @@ __device__ __forceinline__ void col_fft_inv(float2* buf, const FftDev& f, const 
       for (int m1 = 0; m1 < 16; ++m1) buf[spad(base + 16 * m1 + m)] = v[m1];
     }
     __syncthreads();
-    if (tid < 256) {
-      const int n2 = tid;
+    for (int n2 = tid; n2 < 256; n2 += nthr) {
       float2 v[RA];
 #pragma unroll
       for (int k1 = 0; k1 < RA; ++k1) v[k1] = buf[spad(256 * k1 + n2)];

@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __res
   const int SL = spad_len(P.N);
   float2* buf = sm + g * SL;
   float2* smtw = sm + RP * SL;  // four-step twiddles
-  load_fourstep_tw(smtw, P.fstw, threadIdx.x, blockDim.x);
+  load_fourstep_tw(smtw, P.fN.fstw, threadIdx.x, blockDim.x);
   const int pair = blockIdx.x * RP + g;
   const int iy1 = 2 * pair, iy2 = 2 * pair + 1;
   const bool v1 = iy1 < P.n, v2 = iy2 < P.n;
@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __res
     buf[spad(ix)] = make_float2(a, c);
   }
   __syncthreads();
-  col_fft_fwd<L>(buf, P.fN, smtw, gt, nt, P.n, nullptr);
+  col_fft_fwd<L>(buf, P.fN, smtw, gt, nt, nt, P.n, nullptr);
   // Split the two real rows and store R[q][iy] (column-major); the RP pairs of
   // this CTA are adjacent rows, so consecutive threads write consecutive rows.
   float2* Xb = X + (size_t)b * xs;
@@ -120,7 +120,7 @@ __global__ void TAT_COLS_BOUNDS_F k_cols_fwd(DevPlan P, const float2* __restrict
   float2* slot1 = sm + SL;
   float2* smtw = sm + 2 * SL;  // four-step twiddles
   const int tid = threadIdx.x, NT = blockDim.x;
-  load_fourstep_tw(smtw, P.fstw, tid, NT);
+  load_fourstep_tw(smtw, P.fN.fstw, tid, NT);
   const int c0 = strip * S;
   const int c1 = min(c0 + S, P.ncol - 1);  // owned stencil columns i0 in [c0, c1)
   const int ncols = c1 - c0 + 1;           // spectrum columns c0..c1
@@ -136,7 +136,7 @@ __global__ void TAT_COLS_BOUNDS_F k_cols_fwd(DevPlan P, const float2* __restrict
     __syncthreads();
     // column DFT over the n nonzero rows (the phase e^{i q dxi} of each output
     // row is applied by the gather below)
-    col_fft_fwd<L>(buf, P.fN, smtw, tid, nt, P.n, nullptr);
+    col_fft_fwd<L>(buf, P.fN, smtw, tid, NT, nt, P.n, nullptr);
     if (cc > 0) {
       const float2* A = (cc & 1) ? slot0 : slot1;  // column c-1
       const float2* B = buf;                       // column c
@@ -206,7 +206,9 @@ __global__ void __launch_bounds__(1024) k_rings_fwd(DevPlan P, const float2* __r
   const int SL = spad_len(P.n_phi);
   float2* buf = sm + g * SL;
   float2* smptw = sm + RPC * SL;
+  float2* smtw = smptw + P.fphi.ptw_len;
   load_pass_tw(smptw, P.fphi, threadIdx.x, blockDim.x);
+  load_fourstep_tw(smtw, P.fphi.fstw, threadIdx.x, blockDim.x);
   const int rbase = 1 + blockIdx.x * RPC;
   const int r = rbase + g;
   const bool valid = r <= P.J;
@@ -222,13 +224,14 @@ __global__ void __launch_bounds__(1024) k_rings_fwd(DevPlan P, const float2* __r
     buf[spad(l)] = v;
   }
   __syncthreads();
-  fft<L, false>(buf, P.fphi, gt, nt, P.n_phi, P.K + 1, nullptr, nullptr, smptw);
+  if constexpr (FourStep<L>::on) col_fft_fwd<L>(buf, P.fphi, smtw, gt, nt, nt, P.n_phi, nullptr);
+  else fft<L, false>(buf, P.fphi, gt, nt, P.n_phi, P.K + 1, nullptr, nullptr, smptw);
   for (int e = threadIdx.x; e < (P.K + 1) * RPC; e += blockDim.x) {
     const int k = e / RPC, gg = e % RPC;
     const int rr = rbase + gg;
     if (rr > P.J) continue;
     const float bt = (P.low_on && k <= 1 && rr < kLowA) ? 0.f : P.Bt[(size_t)k * J1 + rr];
-    Xb[(size_t)k * J1 + rr] = mul_ipow(cscale(sm[gg * SL + spad(k)], bt), k);
+    Xb[(size_t)k * J1 + rr] = mul_ipow(cscale(sm[gg * SL + spad(colpos<L>(k))], bt), k);
   }
 }
 
@@ -294,7 +297,9 @@ __global__ void __launch_bounds__(1024) k_theta_fwd(DevPlan P, const float2* __r
   const int nd = P.n_det;
   const float2* G = Y + (size_t)b * ys;
   float2* smptw = sm + npair * SL;
+  float2* smtw = smptw + P.fdet.ptw_len;
   load_pass_tw(smptw, P.fdet, threadIdx.x, blockDim.x);
+  load_fourstep_tw(smtw, P.fdet.fstw, threadIdx.x, blockDim.x);
   for (int e = threadIdx.x; e < (nd / 2 + 1) * npair; e += blockDim.x) {
     const int bin = e / npair, p = e % npair;
     const int m1 = m0 + 2 * p, m2 = m1 + 1;
@@ -302,13 +307,14 @@ __global__ void __launch_bounds__(1024) k_theta_fwd(DevPlan P, const float2* __r
     float2 x2 = m2 < P.n_t ? folded_mode(P, G, bin, m2) : make_float2(0.f, 0.f);
     if (bin == 0 || bin == nd / 2) { x1.y = 0.f; x2.y = 0.f; }
     float2* z = sm + p * SL;
-    z[spad(bin)] = make_float2(x1.x - x2.y, x1.y + x2.x);
-    if (bin > 0 && bin < nd / 2) z[spad(nd - bin)] = make_float2(x1.x + x2.y, x2.x - x1.y);
+    z[spad(colpos<L>(bin))] = make_float2(x1.x - x2.y, x1.y + x2.x);
+    if (bin > 0 && bin < nd / 2) z[spad(colpos<L>(nd - bin))] = make_float2(x1.x + x2.y, x2.x - x1.y);
   }
   __syncthreads();
   {
     const int gi = threadIdx.x / nt, gt = threadIdx.x % nt;
-    fft<L, true>(sm + gi * SL, P.fdet, gt, nt, P.n_det, P.n_det, nullptr, nullptr, smptw);
+    if constexpr (FourStep<L>::on) col_fft_inv<L>(sm + gi * SL, P.fdet, smtw, gt, nt, nt, P.n_det, nullptr);
+    else fft<L, true>(sm + gi * SL, P.fdet, gt, nt, P.n_det, P.n_det, nullptr, nullptr, smptw);
   }
   float* gb = g + (size_t)b * gs;
   for (int e = threadIdx.x; e < nd * TT; e += blockDim.x) {
@@ -332,7 +338,9 @@ __global__ void __launch_bounds__(1024) k_theta_adj(DevPlan P, const float* __re
   const int nd = P.n_det;
   const float* gb = g + (size_t)b * gs;
   float2* smptw = sm + (TT / 2) * SL;
+  float2* smtw = smptw + P.fdet.ptw_len;
   load_pass_tw(smptw, P.fdet, threadIdx.x, blockDim.x);
+  load_fourstep_tw(smtw, P.fdet.fstw, threadIdx.x, blockDim.x);
   for (int e = threadIdx.x; e < nd * TT; e += blockDim.x) {
     const int d = e / TT, tt = e % TT;
     const int m = m0 + tt;
@@ -343,7 +351,8 @@ __global__ void __launch_bounds__(1024) k_theta_adj(DevPlan P, const float* __re
   __syncthreads();
   {
     const int gi = threadIdx.x / nt, gt = threadIdx.x % nt;
-    fft<L, false>(sm + gi * SL, P.fdet, gt, nt, P.n_det, P.n_det, nullptr, nullptr, smptw);
+    if constexpr (FourStep<L>::on) col_fft_fwd<L>(sm + gi * SL, P.fdet, smtw, gt, nt, nt, P.n_det, nullptr);
+    else fft<L, false>(sm + gi * SL, P.fdet, gt, nt, P.n_det, P.n_det, nullptr, nullptr, smptw);
   }
   float2* Gp = Y + (size_t)b * ys;
   for (int e = threadIdx.x; e < (P.K + 1) * TT; e += blockDim.x) {
@@ -352,8 +361,8 @@ __global__ void __launch_bounds__(1024) k_theta_adj(DevPlan P, const float* __re
     if (m >= P.n_t) continue;
     const int bin = k % nd;
     const float2* z = sm + (tt >> 1) * SL;
-    const float2 Z = z[spad(bin)];
-    const float2 Zc = cconj(z[spad(bin == 0 ? 0 : nd - bin)]);
+    const float2 Z = z[spad(colpos<L>(bin))];
+    const float2 Zc = cconj(z[spad(colpos<L>(bin == 0 ? 0 : nd - bin))]);
     float2 x;
     if (tt & 1) {
       const float2 dd = csub(Z, Zc);
@@ -436,7 +445,9 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
   }
   const int SL = spad_len(P.n_phi);
   float2* smptw = sm + RPC * SL;
+  float2* smtw = smptw + P.fphi.ptw_len;
   load_pass_tw(smptw, P.fphi, threadIdx.x, blockDim.x);
+  load_fourstep_tw(smtw, P.fphi.fstw, threadIdx.x, blockDim.x);
   const int rbase = 1 + blockIdx.x * RPC;
   for (int e = threadIdx.x; e < (P.K + 1) * RPC; e += blockDim.x) {
     const int k = e / RPC, gg = e % RPC;
@@ -445,16 +456,17 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
     if (rr <= P.J && !(P.low_on && k <= 1 && rr < kLowA))
       w = mul_mipow(cscale(Xb[(size_t)k * J1 + rr], P.Bt[(size_t)k * J1 + rr]), k);
     float2* bg = sm + gg * SL;
-    bg[spad(k)] = w;
+    bg[spad(colpos<L>(k))] = w;
     if (k >= 1 && k < P.K) {
       const float2 wc = cconj(w);
-      bg[spad(P.n_phi - k)] = (k & 1) ? make_float2(-wc.x, -wc.y) : wc;
+      bg[spad(colpos<L>(P.n_phi - k))] = (k & 1) ? make_float2(-wc.x, -wc.y) : wc;
     }
   }
   __syncthreads();
   const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
   float2* buf = sm + g * SL;
-  fft<L, true>(buf, P.fphi, gt, nt, P.n_phi, P.n_phi, nullptr, nullptr, smptw);
+  if constexpr (FourStep<L>::on) col_fft_inv<L>(buf, P.fphi, smtw, gt, nt, nt, P.n_phi, nullptr);
+  else fft<L, true>(buf, P.fphi, gt, nt, P.n_phi, P.n_phi, nullptr, nullptr, smptw);
   const int r = rbase + g;
   if (r <= P.J) {
     const int q4 = P.n_phi / 4;
@@ -541,7 +553,7 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
   const int SL = spad_len(N);
   const int tid = threadIdx.x, NT = blockDim.x;
   float2* smtw = sm + 2 * SL;  // four-step twiddles
-  load_fourstep_tw(smtw, P.fstw, tid, NT);
+  load_fourstep_tw(smtw, P.fN.fstw, tid, NT);
   const int c0 = strip * S;
   const int c1 = min(c0 + S, P.ncol);  // owned columns [c0, c1)
   const float2* Yb = Y + (size_t)b * ys;
@@ -580,7 +592,7 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
       __syncthreads();
     }
     // inverse column DFT (conj(phase) already applied by the scatter), first n rows only
-    col_fft_inv<L>(cur, P.fN, smtw, tid, nt, P.n, nullptr);
+    col_fft_inv<L>(cur, P.fN, smtw, tid, NT, nt, P.n, nullptr);
     float2* col = Xb + (size_t)c * P.n;  // R'[c][0..n): contiguous
     for (int iy = tid; iy < P.n; iy += NT) col[iy] = cur[spad(iy)];
     __syncthreads();
@@ -597,7 +609,7 @@ __global__ void __launch_bounds__(1024) k_rows_adj(DevPlan P, const float2* __re
   const int SL = spad_len(N);
   float2* buf = sm + g * SL;
   float2* smtw = sm + RP * SL;  // four-step twiddles
-  load_fourstep_tw(smtw, P.fstw, threadIdx.x, blockDim.x);
+  load_fourstep_tw(smtw, P.fN.fstw, threadIdx.x, blockDim.x);
   const int pair = blockIdx.x * RP + g;
   const int iy1 = 2 * pair, iy2 = 2 * pair + 1;
   const bool v1 = iy1 < P.n, v2 = iy2 < P.n;
@@ -619,7 +631,7 @@ __global__ void __launch_bounds__(1024) k_rows_adj(DevPlan P, const float2* __re
     else bg[spad(colpos<L>(N / 2))] = make_float2(0.f, 0.f);
   }
   __syncthreads();
-  col_fft_inv<L>(buf, P.fN, smtw, gt, nt, P.n, nullptr);
+  col_fft_inv<L>(buf, P.fN, smtw, gt, nt, nt, P.n, nullptr);
   float* fb = f + (size_t)b * fs;
   const int2 r1 = v1 ? P.rowrange[iy1] : make_int2(0, 0);
   const int2 r2 = v2 ? P.rowrange[iy2] : make_int2(0, 0);

@@ -35,14 +35,14 @@ inline Shapes shapes(const tat_plan_s* Pl, int batch) {
   s.ntiles = (P.J + c.rings_per_cta - 1) / c.rings_per_cta;
   s.rings_grid = dim3(s.ntiles + P.n_low, batch);
   s.rings_block = c.rings_per_cta * c.nt_phi;  // >= 128: room for the 96-float reduction scratch
-  s.rings_smem = ((size_t)c.rings_per_cta * spad_len(P.n_phi) + P.fphi.ptw_len) * sizeof(float2);
+  s.rings_smem = ((size_t)c.rings_per_cta * spad_len(P.n_phi) + P.fphi.ptw_len + kFourStepTw) * sizeof(float2);
   if (s.rings_smem < 96 * sizeof(float)) s.rings_smem = 96 * sizeof(float);
   s.modes_grid = dim3(P.K + 1, batch);
   s.modes_block = c.nt_2M;
   s.modes_smem = ((size_t)spad_len(2 * P.M) + P.f2M.ptw_len) * sizeof(float2);
   s.theta_grid = dim3((P.n_t + c.t_tile - 1) / c.t_tile, batch);
   s.theta_block = (c.t_tile / 2) * c.nt_det;
-  s.theta_smem = ((size_t)(c.t_tile / 2) * spad_len(P.n_det) + P.fdet.ptw_len) * sizeof(float2);
+  s.theta_smem = ((size_t)(c.t_tile / 2) * spad_len(P.n_det) + P.fdet.ptw_len + kFourStepTw) * sizeof(float2);
   return s;
 }
 

@@ -306,7 +306,24 @@ tat_status make_fft(tat_plan_s* P, int L, FftDev* f, int* nthreads) {
     Ns *= R;
   }
   f->ptw_len = (int)pt.size();
-  return upload(P, pt, &f->ptw);
+  TAT_TRY(upload(P, pt, &f->ptw));
+  // Four-step twiddles for L = RA*256 (RA = 2, 4, 8, 16):
+  // w_L^(16 a p), w_L^(b p), w_256^(m p) for a, b, m < 16 and p = 1, 2, 4, 8.
+  std::vector<float2> ft(192, make_float2(1.f, 0.f));
+  if (L % 256 == 0 && (L / 256 == 2 || L / 256 == 4 || L / 256 == 8 || L / 256 == 16)) {
+    const int pw[4] = {1, 2, 4, 8};
+    for (int pi = 0; pi < 4; ++pi)
+      for (int i = 0; i < 16; ++i) {
+        double c, sn;
+        cos_sin_2pi(-(long long)16 * i * pw[pi], L, &c, &sn);
+        ft[pi * 16 + i] = make_float2((float)c, (float)sn);
+        cos_sin_2pi(-(long long)i * pw[pi], L, &c, &sn);
+        ft[64 + pi * 16 + i] = make_float2((float)c, (float)sn);
+        cos_sin_2pi(-(long long)i * pw[pi], 256, &c, &sn);
+        ft[128 + pi * 16 + i] = make_float2((float)c, (float)sn);
+      }
+  }
+  return upload(P, ft, &f->fstw);
 }
 
 }  // namespace
@@ -384,25 +401,6 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
       ph[q] = make_float2((float)c, (float)s);
     }
     TAT_TRY(upload(P, ph, &d.phase));
-  }
-  // Four-step twiddles of the length-N row/column transforms (N = RA*256):
-  // w_N^(16 a p), w_N^(b p), w_256^(m p) for a, b, m < 16 and p = 1, 2, 4, 8.
-  {
-    std::vector<float2> ft(192, make_float2(1.f, 0.f));
-    if (d.N % 256 == 0) {
-      const int pw[4] = {1, 2, 4, 8};
-      for (int pi = 0; pi < 4; ++pi)
-        for (int i = 0; i < 16; ++i) {
-          double c, s;
-          cos_sin_2pi(-(long long)16 * i * pw[pi], d.N, &c, &s);
-          ft[pi * 16 + i] = make_float2((float)c, (float)s);
-          cos_sin_2pi(-(long long)i * pw[pi], d.N, &c, &s);
-          ft[64 + pi * 16 + i] = make_float2((float)c, (float)s);
-          cos_sin_2pi(-(long long)i * pw[pi], 256, &c, &s);
-          ft[128 + pi * 16 + i] = make_float2((float)c, (float)s);
-        }
-    }
-    TAT_TRY(upload(P, ft, &d.fstw));
   }
   // Support disk Pi_Omega0: node kept iff (2ix-(n-1))^2 + (2iy-(n-1))^2 <= (r (n-1))^2.
   {
@@ -508,6 +506,9 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
   // needs 256 threads; up to 4 row pairs (1024 threads) per CTA.
   const bool four_step = d.N == 512 || d.N == 1024 || d.N == 2048 || d.N == 4096;
   c.nt_rows = four_step ? std::max(c.nt_N, 256) : c.nt_N;
+  // the four-step transform needs groups of at least 64 threads (step B of RA = 4)
+  if (d.n_phi == 1024) c.nt_phi = std::max(c.nt_phi, 64);
+  if (n_det == 1024) c.nt_det = std::max(c.nt_det, 64);
   c.rows_pairs = std::max(1, std::min(4, 1024 / c.nt_rows));
   c.strip = 8;
   c.rings_per_cta = 4;

@@ -34,6 +34,7 @@ struct FftDev {
   const float2* ptw;        // concatenated per-pass tables
   int ptw_off[kMaxPass];    // offset of pass s (s >= 1)
   int ptw_len;              // total entries
+  const float2* fstw;       // four-step twiddles (192 entries) when L = RA*256, RA in {2,4,8,16}
 };
 
 // One half-plane polar sample: polar slot p (ring*nh + l'), stencil row k0
@@ -65,7 +66,6 @@ struct DevPlan {
   const float* Bh;                 // [2 x n_low]     w_q*dlam*lam_q*J_k(lam_q)/n_phi
   const float* Lcos;               // [n_low x n_t]   cos(lam_q t_m)
   const float2* cs_half;           // [nh] (cos phi, sin phi) of the half-circle angles
-  const float2* fstw;              // [192] four-step twiddles of the length-N transforms
 };
 
 // Launch shapes (host-side knobs; chosen per plan).
