@@ -14,7 +14,6 @@ tat_status validate_shapes(const tat_plan_s* Pl) {
   const size_t smem[] = {s.rows_smem, s.cols_smem_f, s.cols_smem_a, s.rings_smem, s.modes_smem, s.theta_smem};
   for (int b : blocks)
     if (b < 32 || b > 1024 || b % 32) return TAT_ERR_UNSUPPORTED;
-  if (s.rings_block < 96) return TAT_ERR_UNSUPPORTED;  // reduction scratch of the low-mode rings
   if (s.cols_block > 512) return TAT_ERR_UNSUPPORTED;  // launch bound of the column kernels
   const int N = Pl->d.N;
   const bool ct = N == 256 || N == 512 || N == 1024 || N == 2048 || N == 4096 || N == 8192;

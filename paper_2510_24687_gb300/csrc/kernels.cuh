@@ -29,21 +29,16 @@
 namespace tat {
 namespace {
 
-__device__ __forceinline__ float2 mul_ipow(float2 v, int k) {  // v * i^k
-  switch (k & 3) {
-    case 1: return make_float2(-v.y, v.x);
-    case 2: return make_float2(-v.x, -v.y);
-    case 3: return make_float2(v.y, -v.x);
-    default: return v;
-  }
+// v * i^k and v * (-i)^k without branches (lanes of a warp hold different k).
+__device__ __forceinline__ float2 mul_ipow(float2 v, int k) {
+  float2 w = (k & 1) ? make_float2(-v.y, v.x) : v;
+  const float s = (k & 2) ? -1.f : 1.f;
+  return make_float2(s * w.x, s * w.y);
 }
-__device__ __forceinline__ float2 mul_mipow(float2 v, int k) {  // v * (-i)^k
-  switch (k & 3) {
-    case 1: return make_float2(v.y, -v.x);
-    case 2: return make_float2(-v.x, -v.y);
-    case 3: return make_float2(-v.y, v.x);
-    default: return v;
-  }
+__device__ __forceinline__ float2 mul_mipow(float2 v, int k) {
+  float2 w = (k & 1) ? make_float2(v.y, -v.x) : v;
+  const float s = (k & 2) ? -1.f : 1.f;
+  return make_float2(s * w.x, s * w.y);
 }
 __device__ __forceinline__ int wrapN(int q, int N) { return q < 0 ? q + N : q; }
 
@@ -169,7 +164,8 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
 
 template <int L>
 __global__ void __launch_bounds__(1024) k_rings_fwd(DevPlan P, const float2* __restrict__ Y, long long ys, float2* __restrict__ X,
-                            long long xs, int RPC, int nt, int ntiles) {
+                            long long xs, int /*rings per CTA*/, int nt, int ntiles) {
+  constexpr int RPC = rings_per_cta_for(L);
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
   const float2* Yb = Y + (size_t)b * ys;
@@ -288,7 +284,8 @@ __device__ __forceinline__ float2 folded_mode(const DevPlan& P, const float2* G,
 
 template <int L>
 __global__ void __launch_bounds__(1024) k_theta_fwd(DevPlan P, const float2* __restrict__ Y, long long ys, float* __restrict__ g,
-                            long long gs, int TT, int nt) {
+                            long long gs, int /*time tile*/, int nt) {
+  constexpr int TT = time_tile_for(L);
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
   const int m0 = blockIdx.x * TT;
@@ -330,7 +327,8 @@ __global__ void __launch_bounds__(1024) k_theta_fwd(DevPlan P, const float2* __r
 
 template <int L>
 __global__ void __launch_bounds__(1024) k_theta_adj(DevPlan P, const float* __restrict__ g, long long gs, float2* __restrict__ Y,
-                            long long ys, int TT, int nt) {
+                            long long ys, int /*time tile*/, int nt) {
+  constexpr int TT = time_tile_for(L);
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
   const int m0 = blockIdx.x * TT;
@@ -422,7 +420,8 @@ __global__ void __launch_bounds__(1024) k_modes_adj(DevPlan P, const float2* __r
 
 template <int L>
 __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __restrict__ X, long long xs, float2* __restrict__ Y,
-                            long long ys, int RPC, int nt, int ntiles) {
+                            long long ys, int /*rings per CTA*/, int nt, int ntiles) {
+  constexpr int RPC = rings_per_cta_for(L);
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
   const float2* Xb = X + (size_t)b * xs;

@@ -34,7 +34,7 @@ inline Shapes shapes(const tat_plan_s* Pl, int batch) {
   s.cols_smem_a = (2 * (size_t)spad_len(P.N) + kFourStepTw) * sizeof(float2);
   s.ntiles = (P.J + c.rings_per_cta - 1) / c.rings_per_cta;
   s.rings_grid = dim3(s.ntiles + P.n_low, batch);
-  s.rings_block = c.rings_per_cta * c.nt_phi;  // >= 128: room for the 96-float reduction scratch
+  s.rings_block = c.rings_per_cta * c.nt_phi;
   s.rings_smem = ((size_t)c.rings_per_cta * spad_len(P.n_phi) + P.fphi.ptw_len + kFourStepTw) * sizeof(float2);
   if (s.rings_smem < 96 * sizeof(float)) s.rings_smem = 96 * sizeof(float);
   s.modes_grid = dim3(P.K + 1, batch);

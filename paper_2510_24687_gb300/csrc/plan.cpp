@@ -511,8 +511,8 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
   if (n_det == 1024) c.nt_det = std::max(c.nt_det, 64);
   c.rows_pairs = std::max(1, std::min(4, 1024 / c.nt_rows));
   c.strip = 8;
-  c.rings_per_cta = 4;
-  c.t_tile = 16;
+  c.rings_per_cta = rings_per_cta_for(n_phi);
+  c.t_tile = time_tile_for(n_det);
   // Workspace per image (float2): X holds row spectra (n x N/2) or per-mode
   // coefficients ((K+1) x (J+1) + 2 low-mode rows); Y holds polar samples
   // (n_rings x nh) or time modes ((K+1) x n_t).

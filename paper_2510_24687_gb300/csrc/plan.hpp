@@ -68,6 +68,17 @@ struct DevPlan {
   const float2* cs_half;           // [nh] (cos phi, sin phi) of the half-circle angles
 };
 
+// Tile shapes fixed at compile time per FFT length (index arithmetic by
+// shifts); the host uses the same functions for the launch shapes.  Lengths
+// with a compile-time schedule below 4096 take 8 rings / 16 time samples per
+// CTA; 4096 takes 2 / 4 and runtime lengths (L = 0) 1 / 2, so that a CTA never
+// exceeds 1024 threads.
+__host__ __device__ constexpr bool ct_angular_length(int L) {
+  return L == 64 || L == 128 || L == 256 || L == 512 || L == 1024 || L == 2048;
+}
+__host__ __device__ constexpr int rings_per_cta_for(int L) { return ct_angular_length(L) ? 8 : L == 4096 ? 2 : 1; }
+__host__ __device__ constexpr int time_tile_for(int L) { return ct_angular_length(L) ? 16 : L == 4096 ? 4 : 2; }
+
 // Launch shapes (host-side knobs; chosen per plan).
 struct LaunchCfg {
   int rows_pairs;     // row pairs per CTA in the row pass
