@@ -45,6 +45,8 @@ def parse_args():
     p.add_argument("--batch", type=int, default=32)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", choices=["pair", "solves"], default="pair",
+                   help="pair: the A+A* throughput line (default); solves: batched NNLS + TV-PDHG reconstructions")
     return p.parse_args()
 
 
@@ -213,6 +215,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "solves":
+        return run_solves(args, rank, world, local)
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -354,6 +358,190 @@ def main():
                 "config": workload_config(B), "roofline": roofline, "hbm_roofline_pair": hbm,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 10 * args.steps,
                 "clocks": clk, "plan": {k: info[k] for k in ("N", "M", "J", "n_phi", "n_low", "n_points")},
+                "kernel_source_hash": kernel_source_hash()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ solves workload
+
+SOLVE_N, SOLVE_DET, SOLVE_T, SOLVE_B, SOLVE_IT, SOLVE_ALPHA = 256, 512, 512, 16, 100, 1e-3
+SOLVE_METRIC = "reconstructions/s (100 NNLS + 100 TV-PDHG iterations per image, n=256, 256 of 512 detectors)"
+
+
+def solves_config(batch):
+    return {"workload": f"NNLS + TV-PDHG solves, n={SOLVE_N}, n_det={SOLVE_DET} (half circle active), "
+                        f"n_t={SOLVE_T}, B={batch} per GPU, {SOLVE_IT}+{SOLVE_IT} iterations, alpha={SOLVE_ALPHA}",
+            "n": SOLVE_N, "n_det": SOLVE_DET, "n_t": SOLVE_T, "arc": "theta in [0, pi)", "batch_per_gpu": batch,
+            "iterations": {"nnls": SOLVE_IT, "tv_pdhg": SOLVE_IT}, "alpha": SOLVE_ALPHA, "noise": "1 %",
+            "roi": "upper half disk, radius 0.9",
+            "l2": "state per iteration (f, q, p, g, workspace) exceeds L2 at B=16, no flush"}
+
+
+def time_oracle_solve_iteration(seed=0):
+    """One NNLS iteration (A then A*) of the solves workload on one image through the FP64 oracle."""
+    import numpy as np
+    import torch
+    from oracle import solvers as S
+    from oracle import tat_oracle as O
+    from tat_inputs import add_noise, ellipse_phantom, roi_mask
+    P = O.OraclePlan(SOLVE_N, SOLVE_DET, SOLVE_T, T=T_WIN, support_radius=RSUP, arc_begin=0.0, arc_len=math.pi)
+    g = torch.tensor(add_noise(O.forward(P, ellipse_phantom(SOLVE_N, seed)), 0.01, seed))
+    mask = torch.tensor(roi_mask(SOLVE_N, radius=RSUP, upper_half=True))
+    t0 = time.perf_counter()
+    S.nnls(S.plan_op(P), g, 1.0, 1, mask=mask)
+    return time.perf_counter() - t0
+
+
+def run_solves(args, rank, world, local):
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t = statistics.median(time_oracle_solve_iteration(s) for s in range(max(1, min(args.steps, 3))))
+        value = 1.0 / (2 * SOLVE_IT * t)
+        line = {"impl": "reference", "metric": SOLVE_METRIC, "value": value, "unit": "reconstructions/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": 0, "ms_per_step": 1e3 * t,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": solves_config(SOLVE_B),
+                "cpu_baseline": {"value": value, "unit": "reconstructions/s", "cores": cpu_threads(), "kind": "oracle",
+                                 "sample": "one oracle NNLS iteration (A + A*) on one n=256 image, scaled to "
+                                           f"{2 * SOLVE_IT} iterations per reconstruction"},
+                "e2e": {"value": value, "unit": "reconstructions/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_24687_gb300 as pkg
+    from tat_inputs import add_noise, phantom_batch, roi_mask
+
+    B = SOLVE_B if args.batch == 32 else args.batch
+    op = pkg.TatOperator(SOLVE_N, SOLVE_DET, SOLVE_T, T=T_WIN, support_radius=RSUP, arc_begin=0.0,
+                         arc_len=math.pi, device=dev)
+    fh = phantom_batch(SOLVE_N, B, seed0=rank * B).astype(np.float32)
+    g_clean = op.forward(torch.tensor(fh, device=dev)).cpu().numpy()
+    gh = np.stack([add_noise(g_clean[b], 0.01, 7000 + rank * B + b) for b in range(B)]).astype(np.float32)
+    mask = torch.tensor(roi_mask(SOLVE_N, radius=RSUP, upper_half=True), dtype=torch.float32, device=dev)
+    g = torch.tensor(gh, device=dev)
+    L = pkg.power_norm_sq(op, iters=40)
+    lam = 1.0 / L
+    sigma, tau, s = pkg.pdhg_steps(1.05 * L, op.info["h"])
+    solver = pkg.TatSolver(op, B, mask=mask)
+    nnls_out = torch.empty((B, SOLVE_N, SOLVE_N), device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(graph=True, slv=solver, gg=g, out=nnls_out):
+        out.copy_(slv.nnls(gg, SOLVE_IT, lam, graph=graph))
+        return slv.tv(gg, SOLVE_ALPHA, SOLVE_IT, sigma, tau, s, graph=graph)
+
+    def timed(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms = timed(step, args.steps)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = B * world / (ms / 1e3)
+
+    # comparisons: eager launches, one image at a time, and the bare A+A* pairs of the same iterations
+    ms_eager = timed(lambda: step(graph=False), 2)
+    single = pkg.TatSolver(op, 1, mask=mask)
+    out1 = torch.empty((1, SOLVE_N, SOLVE_N), device=dev)
+    gsingle = [g[b:b + 1].clone() for b in range(B)]
+    for gb in gsingle[:1]:
+        step(True, single, gb, out1)
+    ms_single = timed(lambda: [step(True, single, gb, out1) for gb in gsingle], 1)
+    ws = op.workspace(B)
+    fs, gs = SOLVE_N * SOLVE_N, SOLVE_DET * SOLVE_T
+    ybuf = torch.empty((B, SOLVE_DET, SOLVE_T), device=dev)
+    xbuf = torch.empty((B, SOLVE_N, SOLVE_N), device=dev)
+    sptr = stream.cuda_stream
+
+    def pairs_only():
+        for _ in range(2 * SOLVE_IT):
+            pkg.tat_forward_batched(op.plan, B, xbuf.data_ptr(), fs, ybuf.data_ptr(), gs, ws.data_ptr(), sptr)
+            pkg.tat_adjoint_batched(op.plan, B, ybuf.data_ptr(), gs, xbuf.data_ptr(), fs, ws.data_ptr(), sptr)
+    xbuf.copy_(torch.tensor(fh, device=dev))
+    ms_pairs = timed(pairs_only, 1)
+
+    # element-wise fused steps: HBM roofline of one TV primal launch (reads f, Asq, p(2), mask; writes f, fbar)
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    xb = torch.zeros((B, SOLVE_N, SOLVE_N), device=dev)
+    pb = torch.zeros((B, 2, SOLVE_N, SOLVE_N), device=dev)
+    fbb = torch.zeros_like(xb)
+    f0 = torch.zeros_like(xb)
+
+    def primal():
+        pkg.tat_tv_primal(B, SOLVE_N, op.info["h"] / s, tau, xb.data_ptr(), pb.data_ptr(), mask.data_ptr(),
+                          f0.data_ptr(), f0.data_ptr(), fbb.data_ptr(), sptr)
+    primal()
+    ms_primal = timed(primal, 50)
+    primal_bytes = 4 * B * SOLVE_N * SOLVE_N * (1 + 1 + 2 + 1 + 1)
+    achieved = primal_bytes / (ms_primal / 1e3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_tv_primal", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": "measured" if peaks else "fallback",
+                "note": "fused element-wise step; algorithmic bytes = f, A*q, p (2 planes), fbar, f_out per pixel"}
+
+    # end to end: sinograms from pinned host memory, reconstructions back to pinned memory
+    g_pin = torch.from_numpy(gh).pin_memory()
+    out_pin = torch.empty((2, B, SOLVE_N, SOLVE_N), dtype=torch.float32).pin_memory()
+    gdev = torch.empty_like(g)
+
+    def step_e2e():
+        gdev.copy_(g_pin, non_blocking=True)
+        f_tv = step(True, solver, gdev, nnls_out)
+        out_pin[0].copy_(nnls_out, non_blocking=True)
+        out_pin[1].copy_(f_tv, non_blocking=True)
+    step_e2e()
+    ms_e2e = timed(step_e2e, max(1, min(args.steps, 3)))
+    e2e = {"value": B * world / (ms_e2e / 1e3), "unit": "reconstructions/s", "h2d_bytes_per_step": gh.nbytes,
+           "d2h_bytes_per_step": out_pin.numel() * 4}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t = time_oracle_solve_iteration(0)
+        cpu = {"value": 1.0 / (2 * SOLVE_IT * t), "unit": "reconstructions/s", "cores": cpu_threads(),
+               "kind": "oracle", "sample": "one FP64 oracle NNLS iteration (A + A*) on one n=256 image, scaled to "
+                                           f"{2 * SOLVE_IT} iterations per reconstruction"}
+    # launches per step: per iteration one A (5) + one A* (5) + 2 fused element-wise kernels (NNLS) or 3 (TV)
+    launches = SOLVE_IT * (10 + 2) + SOLVE_IT * (10 + 3)
+    if rank == 0:
+        line = {"metric": SOLVE_METRIC, "value": value, "unit": "reconstructions/s", "n_gpus": world,
+                "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded random-ellipse phantoms, g = A f + 1 % Gaussian noise)",
+                "config": solves_config(B), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches * args.steps, "clocks": clk,
+                "comparison_ms_per_step": {"graphs": ms, "eager_launches": ms_eager,
+                                           "one_image_at_a_time": ms_single,
+                                           "bare_A_Astar_pairs_same_count": ms_pairs},
+                "steps_params": {"norm_sq": L, "lambda": lam, "sigma": sigma, "tau": tau, "s": s},
                 "kernel_source_hash": kernel_source_hash()}
         print(json.dumps(line), flush=True)
     if world > 1:

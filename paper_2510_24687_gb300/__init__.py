@@ -18,3 +18,13 @@ __all__ = ["TatError", "TatOperator", "header_symbols", "load", "tat_adjoint", "
            "tat_forward_batched", "tat_forward_noalloc", "tat_plan_create", "tat_plan_create_ex", "tat_plan_desc",
            "tat_plan_desc_default", "tat_plan_destroy", "tat_plan_get_info", "tat_plan_info", "tat_plan_query",
            "tat_status_string", "tat_workspace_size"]
+
+from . import autograd, solvers  # noqa: E402
+from .autograd import A, Astar  # noqa: E402
+from .solvers import TatSolver, nnls_unrolled, pdhg_steps, power_norm_sq, tv_unrolled  # noqa: E402
+from .binding import (tat_axpby_clamp, tat_axpby_clamp_backward, tat_pd_dual_data, tat_tv_dual,  # noqa: E402
+                      tat_tv_dual_backward, tat_tv_primal, tat_tv_primal_backward)
+
+__all__ += ["autograd", "solvers", "A", "Astar", "TatSolver", "nnls_unrolled", "pdhg_steps", "power_norm_sq",
+            "tv_unrolled", "tat_axpby_clamp", "tat_axpby_clamp_backward", "tat_pd_dual_data", "tat_tv_dual",
+            "tat_tv_dual_backward", "tat_tv_primal", "tat_tv_primal_backward"]

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libtat.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["plan.cpp", "forward.cu", "adjoint.cu", "capi.cu", "noalloc.cu"]
+SOURCES = ["plan.cpp", "forward.cu", "adjoint.cu", "capi.cu", "noalloc.cu", "solvers.cu"]
 
 
 def _nvcc() -> str:
@@ -36,7 +36,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Builds libtat.so if any source is newer than it; returns its path."""
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     deps = srcs + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".hpp", ".cuh"))]
-    deps.append(os.path.join(ROOT, "include", "tat.h"))
+    inc = os.path.join(ROOT, "include")
+    deps += [os.path.join(inc, h) for h in os.listdir(inc) if h.endswith(".h")]
     if not force and os.path.exists(LIB):
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= t for d in deps):

@@ -49,6 +49,7 @@ _P = ctypes.c_void_p
 _I = ctypes.c_int
 _LL = ctypes.c_longlong
 _D = ctypes.c_double
+_F = ctypes.c_float
 
 
 def load() -> ctypes.CDLL:
@@ -80,6 +81,13 @@ def load() -> ctypes.CDLL:
         "tat_forward_noalloc": (_I, [_P, _P, _P, _P]),
         "tat_debug_forward_batched_timed": (_I, [_P, _I, _P, _LL, _P, _LL, _P, _P, ctypes.POINTER(_P)]),
         "tat_debug_adjoint_batched_timed": (_I, [_P, _I, _P, _LL, _P, _LL, _P, _P, ctypes.POINTER(_P)]),
+        "tat_axpby_clamp": (_I, [_LL, _F, _P, _F, _P, _F, _P, _LL, _P, _P]),
+        "tat_axpby_clamp_backward": (_I, [_LL, _P, _F, _P, _LL, _P, _F, _P, _F, _P, _P]),
+        "tat_pd_dual_data": (_I, [_LL, _F, _P, _P, _P, _P, _P]),
+        "tat_tv_dual": (_I, [_I, _I, _F, _F, _F, _P, _P, _P, _P]),
+        "tat_tv_dual_backward": (_I, [_I, _I, _F, _F, _F, _P, _P, _P, _P, _P, _P]),
+        "tat_tv_primal": (_I, [_I, _I, _F, _F, _P, _P, _P, _P, _P, _P, _P]),
+        "tat_tv_primal_backward": (_I, [_I, _I, _F, _F, _P, _P, _P, _P, _P, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -185,6 +193,51 @@ def tat_debug_adjoint_batched_timed(plan, batch, g_ptr, g_stride, f_ptr, f_strid
                                                   stream or None, _events(events)), "tat_debug_adjoint_batched_timed")
 
 
+def tat_axpby_clamp(count, a, x_ptr, b, y_ptr, lo, mask_ptr, mask_period, out_ptr, stream=0):
+    """out = mask * max(lo, a*x + b*y); y_ptr / mask_ptr may be 0."""
+    _check(load().tat_axpby_clamp(count, a, x_ptr, b, y_ptr or None, lo, mask_ptr or None, mask_period, out_ptr,
+                                  stream or None), "tat_axpby_clamp")
+
+
+def tat_axpby_clamp_backward(count, out_ptr, lo, mask_ptr, mask_period, grad_out_ptr, a, grad_x_ptr, b, grad_y_ptr,
+                             stream=0):
+    """G = mask [out > lo] grad_out; grad_x = a G, grad_y = b G (either pointer may be 0)."""
+    _check(load().tat_axpby_clamp_backward(count, out_ptr, lo, mask_ptr or None, mask_period, grad_out_ptr, a,
+                                           grad_x_ptr or None, b, grad_y_ptr or None, stream or None),
+           "tat_axpby_clamp_backward")
+
+
+def tat_pd_dual_data(count, sigma, Af_ptr, g_ptr, q_in_ptr, q_out_ptr, stream=0):
+    """q_out = (q_in + sigma (Af - g)) / (1 + sigma)."""
+    _check(load().tat_pd_dual_data(count, sigma, Af_ptr, g_ptr, q_in_ptr, q_out_ptr, stream or None),
+           "tat_pd_dual_data")
+
+
+def tat_tv_dual(batch, n, h_eff, sigma, bound, fbar_ptr, p_in_ptr, p_out_ptr, stream=0):
+    """p_out = proj_{|p|<=bound}(p_in + sigma grad_h fbar)."""
+    _check(load().tat_tv_dual(batch, n, h_eff, sigma, bound, fbar_ptr, p_in_ptr, p_out_ptr, stream or None),
+           "tat_tv_dual")
+
+
+def tat_tv_dual_backward(batch, n, h_eff, sigma, bound, fbar_ptr, p_in_ptr, grad_p_out_ptr, grad_p_in_ptr,
+                         grad_fbar_ptr, stream=0):
+    _check(load().tat_tv_dual_backward(batch, n, h_eff, sigma, bound, fbar_ptr, p_in_ptr, grad_p_out_ptr,
+                                       grad_p_in_ptr, grad_fbar_ptr or None, stream or None), "tat_tv_dual_backward")
+
+
+def tat_tv_primal(batch, n, h_eff, tau, Asq_ptr, p_ptr, mask_ptr, f_in_ptr, f_out_ptr, fbar_ptr, stream=0):
+    """f_out = mask max(0, f_in - tau (Asq - div_h p)); fbar = 2 f_out - f_in."""
+    _check(load().tat_tv_primal(batch, n, h_eff, tau, Asq_ptr, p_ptr, mask_ptr or None, f_in_ptr, f_out_ptr,
+                                fbar_ptr, stream or None), "tat_tv_primal")
+
+
+def tat_tv_primal_backward(batch, n, h_eff, tau, f_out_ptr, mask_ptr, grad_f_out_ptr, grad_fbar_ptr, grad_f_in_ptr,
+                           grad_Asq_ptr, grad_p_ptr, stream=0):
+    _check(load().tat_tv_primal_backward(batch, n, h_eff, tau, f_out_ptr, mask_ptr or None, grad_f_out_ptr or None,
+                                         grad_fbar_ptr or None, grad_f_in_ptr or None, grad_Asq_ptr or None,
+                                         grad_p_ptr or None, stream or None), "tat_tv_primal_backward")
+
+
 def tat_status_string(status: int) -> str:
     return load().tat_status_string(status).decode()
 
@@ -235,6 +288,9 @@ class TatOperator:
             self.plan = tat_plan_create_ex(desc)
         self.info = tat_plan_get_info(self.plan)
         self.n, self.n_det, self.n_t = n, n_det, n_t
+        # inner-product weights of X and Y (Eq. innerProducts): A* = W_X^{-1} A^T W_Y
+        self.W_X = (self.info["h"] * R) ** 2
+        self.W_Y = (self.info["dt"] * R / c) * (2 * math.pi * R / n_det)
         self._ws = {}
 
     def workspace(self, batch):

@@ -2,7 +2,8 @@
 
 This module is shared by the FP64 oracle, the tests and the benchmark.  It
 holds no arithmetic of the operators themselves: only a counter-based random
-stream, the random-ellipse phantoms and white Gaussian noise.
+stream, the random-ellipse phantoms, white Gaussian noise and region-of-
+interest masks.
 
 Workloads follow the paper's description of its test objects: "smoothed
 characteristic functions" (Section 4.1) and training sets of randomly
@@ -105,3 +106,18 @@ def add_noise(g: np.ndarray, eps: float, seed: int) -> np.ndarray:
     """g + eps*||g||*xi/||xi|| (relative white Gaussian noise)."""
     xi = gaussian(seed, g.size).reshape(g.shape)
     return g + eps * np.linalg.norm(g) * xi / np.linalg.norm(xi)
+
+
+def roi_mask(n: int, radius: float = 0.98, upper_half: bool = False) -> np.ndarray:
+    """Region of interest Omega_0 as an n x n 0/1 array (f[iy, ix]).
+
+    The disk |x| <= radius of the node-centred grid, optionally cut to its
+    upper half y >= 0 (the visible half for detectors on theta in [0, pi),
+    Section 4.3).  An input choice of the caller, not part of A.
+    """
+    s = (2 * np.arange(n) - (n - 1)).astype(np.float64)   # (n-1) * x_i
+    rr = (radius * (n - 1)) ** 2
+    m = (s[None, :] ** 2 + s[:, None] ** 2) <= rr
+    if upper_half:
+        m &= (s[:, None] >= 0)
+    return m.astype(np.float64)
