@@ -125,31 +125,67 @@ class ClockSampler:
                 "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
 
 
-def stage_flops(info, B):
+def stage_flops(info, B, n=N_IMG, n_det=N_DET, n_t=N_T):
     """Algorithmic flops per launch of each stage (5 L log2 L per complex FFT of length L)."""
-    n, N, M, J, K, nphi, nlow = N_IMG, info["N"], info["M"], info["J"], info["K"], info["n_phi"], info["n_low"]
+    N, M, J, K, nphi, nlow = info["N"], info["M"], info["J"], info["K"], info["n_phi"], info["n_low"]
     fft = lambda L: 5.0 * L * math.log2(L)
     npts = info["n_points"]
     rows = B * ((n + 1) // 2) * fft(N)
     cols = B * ((N // 2) * fft(N) + 30.0 * npts)
     rings = B * ((J + nlow) * fft(nphi) + 8.0 * (K + 1) * J)
-    modes = B * ((K + 1) * fft(2 * M) + 2.0 * 4 * nlow * N_T)
-    theta = B * ((N_T + 1) // 2) * fft(N_DET)
+    modes = B * ((K + 1) * fft(2 * M) + 2.0 * 4 * nlow * n_t)
+    theta = B * ((n_t + 1) // 2) * fft(n_det)
     return {"rows_fwd": rows, "cols_fwd": cols, "rings_fwd": rings, "modes_fwd": modes, "theta_fwd": theta,
             "rows_adj": rows, "cols_adj": cols, "rings_adj": rings, "modes_adj": modes, "theta_adj": theta}
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current kernels."""
+def traffic_for(kernel, workload="pair_n512_b32"):
+    """DRAM bytes per launch from the committed ncu summaries, if taken on the current kernels."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
-            t = json.load(fh)
+            t = json.load(fh).get(workload, {})
     except (OSError, ValueError):
         return None
     if t.get("kernel_source_hash") != kernel_source_hash():
         return None
     v = t.get("dram_bytes_per_launch", {}).get(kernel)
     return float(v) if v is not None else None
+
+
+def stage_times(pkg, op, B, x, y, x2, ws, stream, ksteps):
+    """Mean ms of each of the ten stages, from events recorded between the stages."""
+    import torch
+    n, nd, nt = op.n, op.n_det, op.n_t
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(12)] for _ in range(ksteps)]
+    for row in evs:
+        for e in row:
+            e.record(stream)
+    torch.cuda.synchronize()
+    sptr = stream.cuda_stream
+    for row in evs:
+        pkg.tat_debug_forward_batched_timed(op.plan, B, x.data_ptr(), n * n, y.data_ptr(), nd * nt, ws.data_ptr(),
+                                            sptr, [e.cuda_event for e in row[:6]])
+        pkg.tat_debug_adjoint_batched_timed(op.plan, B, y.data_ptr(), nd * nt, x2.data_ptr(), n * n, ws.data_ptr(),
+                                            sptr, [e.cuda_event for e in row[6:]])
+    torch.cuda.synchronize()
+    stage_ms = {}
+    for i, name in enumerate(FWD_STAGES):
+        stage_ms[name] = statistics.mean(r[i].elapsed_time(r[i + 1]) for r in evs)
+    for i, name in enumerate(ADJ_STAGES):
+        stage_ms[name] = statistics.mean(r[6 + i].elapsed_time(r[7 + i]) for r in evs)
+    return stage_ms
+
+
+def alu_roofline(stage_ms, flops, workload):
+    """FP32-ALU roofline of the dominant stage (the stages are FFT/shared-memory kernels, not HBM-bound)."""
+    dom = max(stage_ms, key=stage_ms.get)
+    peak_alu = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops[dom] / (stage_ms[dom] / 1e3) / 1e12
+    return {"bound": "alu", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": peak_alu,
+            "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": traffic_for(KERNEL_NAMES[dom], workload),
+            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FP32 FMA, non-tensor)",
+            "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+            "stage_tflops": {k: round(flops[k] / (stage_ms[k] / 1e3) / 1e12, 3) for k in stage_ms}}
 
 
 # ------------------------------------------------------------------ CPU oracle timing
@@ -281,32 +317,8 @@ def main():
     value = B * args.steps * world / (ms / 1e3)
 
     # ---- per-stage timing (same work, events between the five stages of each direction)
-    ksteps = max(3, min(args.steps, 10))
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(12)] for _ in range(ksteps)]
-    for row in evs:
-        for e in row:
-            e.record(stream)
-    torch.cuda.synchronize()
-    for row in evs:
-        pkg.tat_debug_forward_batched_timed(op.plan, B, f.data_ptr(), fs, g.data_ptr(), gs, ws.data_ptr(), sptr,
-                                            [e.cuda_event for e in row[:6]])
-        pkg.tat_debug_adjoint_batched_timed(op.plan, B, g.data_ptr(), gs, f2.data_ptr(), fs, ws.data_ptr(), sptr,
-                                            [e.cuda_event for e in row[6:]])
-    torch.cuda.synchronize()
-    stage_ms = {}
-    for i, name in enumerate(FWD_STAGES):
-        stage_ms[name] = statistics.mean(r[i].elapsed_time(r[i + 1]) for r in evs)
-    for i, name in enumerate(ADJ_STAGES):
-        stage_ms[name] = statistics.mean(r[6 + i].elapsed_time(r[7 + i]) for r in evs)
-    flops = stage_flops(info, B)
-    dom = max(stage_ms, key=stage_ms.get)
-    peak_alu = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = flops[dom] / (stage_ms[dom] / 1e3) / 1e12
-    roofline = {"bound": "alu", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": peak_alu,
-                "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": traffic_for(KERNEL_NAMES[dom]),
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FP32 FMA, non-tensor)",
-                "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-                "stage_tflops": {k: round(flops[k] / (stage_ms[k] / 1e3) / 1e12, 3) for k in stage_ms}}
+    stage_ms = stage_times(pkg, op, B, f, g, f2, ws, stream, max(3, min(args.steps, 10)))
+    roofline = alu_roofline(stage_ms, stage_flops(info, B), "pair_n512_b32")
     peaks = measured_peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     pair_bytes = 2 * (4 * N_IMG * N_IMG + 4 * N_DET * N_T)
@@ -487,6 +499,7 @@ def run_solves(args, rank, world, local):
             pkg.tat_adjoint_batched(op.plan, B, ybuf.data_ptr(), gs, xbuf.data_ptr(), fs, ws.data_ptr(), sptr)
     xbuf.copy_(torch.tensor(fh, device=dev))
     ms_pairs = timed(pairs_only, 1)
+    x_tmp2 = torch.empty_like(xbuf)
 
     # element-wise fused steps: HBM roofline of one TV primal launch (reads f, Asq, p(2), mask; writes f, fbar)
     peaks = measured_peaks()
@@ -503,10 +516,12 @@ def run_solves(args, rank, world, local):
     ms_primal = timed(primal, 50)
     primal_bytes = 4 * B * SOLVE_N * SOLVE_N * (1 + 1 + 2 + 1 + 1)
     achieved = primal_bytes / (ms_primal / 1e3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_tv_primal", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
-                "peak_source": "measured" if peaks else "fallback",
-                "note": "fused element-wise step; algorithmic bytes = f, A*q, p (2 planes), fbar, f_out per pixel"}
+    fused = {"bound": "hbm", "kernel": "k_tv_primal", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+             "frac": achieved / hbm_peak, "traffic": traffic_for("k_tv_primal", "solves_n256_b16"),
+             "peak_source": "measured" if peaks else "fallback", "ms": ms_primal,
+             "note": "fused element-wise step; algorithmic bytes = f, A*q, p (2 planes), mask, f_out, fbar per pixel"}
+    stage_ms = stage_times(pkg, op, B, xbuf, ybuf, x_tmp2, ws, stream, 5)
+    roofline = alu_roofline(stage_ms, stage_flops(op.info, B, SOLVE_N, SOLVE_DET, SOLVE_T), "solves_n256_b16")
 
     # end to end: sinograms from pinned host memory, reconstructions back to pinned memory
     g_pin = torch.from_numpy(gh).pin_memory()
@@ -536,7 +551,8 @@ def run_solves(args, rank, world, local):
                 "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded random-ellipse phantoms, g = A f + 1 % Gaussian noise)",
-                "config": solves_config(B), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "config": solves_config(B), "roofline": roofline, "fused_steps_roofline": fused,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches * args.steps, "clocks": clk,
                 "comparison_ms_per_step": {"graphs": ms, "eager_launches": ms_eager,
                                            "one_image_at_a_time": ms_single,
