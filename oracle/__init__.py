@@ -3,8 +3,8 @@
 TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
 and the CPU-baseline leg of ``bench.py``, never by the product package.
 """
-from .tat_oracle import (OraclePlan, adjoint, forward, hybrid_rule, kwave_truth,
+from .tat_oracle import (OraclePlan, adjoint, forward, hybrid_rule, inverse, inverse_direct, kwave_truth,
                          poisson_truth, smooth_ceil)
 
-__all__ = ["OraclePlan", "forward", "adjoint", "hybrid_rule", "kwave_truth",
+__all__ = ["OraclePlan", "forward", "adjoint", "inverse", "inverse_direct", "hybrid_rule", "kwave_truth",
            "poisson_truth", "smooth_ceil"]

@@ -27,6 +27,10 @@ detection geometry", arXiv 2510.24687):
   (-i)^|k| J_|k| multiplier of Eq. Four_coef_u, phi-series, resampling, 2D
   inverse FFT, restriction to Omega_0), each as the transpose of its forward
   counterpart.
+* ``inverse`` -- Algorithm 3, the approximate inverse by the universal
+  backprojection formula (Eq. approx_UBP) with the constant C of Eq.
+  silly_integral; ``inverse_direct`` evaluates the same formula at the
+  Cartesian nodes without the polar grid.
 * ``kwave_truth`` -- the unaccelerated Fourier method of Eq. kwave on the same
   Cartesian frequency grid (the paper's own accuracy check, Section 2.1.1).
 * ``poisson_truth`` -- the Green's-function form of A, Eq. green_conv.
@@ -314,6 +318,108 @@ def adjoint(P: OraclePlan, g: np.ndarray) -> np.ndarray:
     f = (P.h * P.h / TWO_PI) * Z[: P.n, : P.n].real
     # step 1^T and the inner-product weight of X
     return f * P.mask / P.W_X
+
+
+# ----------------------------------------------------------------- inverse
+
+def inverse_modes(P: OraclePlan, g: np.ndarray) -> np.ndarray:
+    """Steps 1-3 of Algorithm 3: vhat_k(lambda_j) on the radial grid, all n_phi mode bins.
+
+    g_k(t_m) = (1/n_det) sum_d g(t_m, theta_d) e^{-ik theta_d} (Eq. FourSerForg, data
+    zero off Gamma); the t-integral of Eq. Four_coef_v by the trapezoid rule on
+    t_m = m dt (the t = 0 term vanishes), and
+        vhat_k(lambda) = -2 (-i)^|k| J'_|k|(lambda) int_0^T g_k(t) sin(lambda t) dt.
+    The constant -2 replaces the printed -4 pi: the appendix writes the Fourier
+    transform of G without the 1/(2 pi) of the convention that Eq. green_conv
+    and Eq. gseries use (with -4 pi, A^{-1} A f would be 2 pi f).
+    """
+    if P.n_phi != P.n_det:
+        raise ValueError("the inverse keeps the data's own modes: n_phi must equal n_det")
+    gg = np.asarray(g, dtype=np.float64) * P.gamma[:, None]
+    Gk = np.fft.fft(gg, axis=0) / P.n_det                    # (n_phi, n_t), bin order
+    w = np.full(P.n_t, P.dt)
+    w[-1] *= 0.5
+    S = np.sin(np.outer(P.lam, P.t)) @ (w[:, None] * Gk.T)    # (J+1, n_phi)
+    ak = P.absk
+    dJ = 0.5 * (jv(ak - 1, P.lam[:, None]) - jv(ak + 1, P.lam[:, None]))   # J'_|k|, J_{-1} = -J_1
+    return -2.0 * ((-1j) ** ak)[None, :] * dJ * S
+
+
+def inverse_resample(P: OraclePlan, V: np.ndarray) -> np.ndarray:
+    """Step 5: bilinear interpolation in (lambda, phi) of V[j, l] = vhat(lambda_j, phi_l)
+    at every Cartesian node xi_q of the N x N grid (FFT order); zero beyond ring J."""
+    q = np.fft.fftfreq(P.N, 1.0 / P.N)
+    QX, QY = np.meshgrid(q, q, indexing="xy")
+    u = np.hypot(QX, QY) * P.dxi / P.dlam
+    j0 = np.floor(u).astype(np.int64)
+    a = u - j0
+    inside = j0 + 1 <= P.J
+    j0 = np.where(inside, j0, 0)
+    s = (np.arctan2(QY, QX) / TWO_PI * P.n_phi) % P.n_phi
+    l0 = np.floor(s).astype(np.int64)
+    b = s - l0
+    l0 %= P.n_phi
+    l1 = (l0 + 1) % P.n_phi
+    out = ((1 - a) * ((1 - b) * V[j0, l0] + b * V[j0, l1]) + a * ((1 - b) * V[j0 + 1, l0] + b * V[j0 + 1, l1]))
+    return np.where(inside, out, 0.0)
+
+
+def _annulus(P: OraclePlan) -> np.ndarray:
+    """Nodes of Omega \\ Omega_0: inside the disk |x| <= R, outside the support mask."""
+    i = np.arange(P.n)
+    s = (2 * i - (P.n - 1)).astype(np.float64)
+    inside = (s[:, None] ** 2 + s[None, :] ** 2) <= float(P.n - 1) ** 2
+    return inside & (P.mask == 0)
+
+
+def inverse(P: OraclePlan, g: np.ndarray, with_constant: bool = True) -> np.ndarray:
+    """f ~ A^{-1} g (Algorithm 3): universal backprojection (Eq. approx_UBP) on the grids of A*.
+
+    Steps: detector DFT and sine transform (inverse_modes), angular series
+    vhat(lambda_j, phi_l) = sum_k e^{ik phi_l} vhat_k (step 4), bilinear resampling to
+    the Cartesian grid (step 5), the 2D inverse transform
+    v(x) = (dxi^2 / 2 pi) sum_q vhat(xi_q) e^{i xi_q . x} on the image nodes (step 6),
+    C = -mean of v over Omega \\ Omega_0 (Eq. silly_integral, step 7) and
+    Pi_Omega0 (v + C) (step 8).
+    """
+    V = np.fft.ifft(inverse_modes(P, g), axis=1) * P.n_phi
+    Vc = inverse_resample(P, V)
+    q = np.fft.fftfreq(P.N, 1.0 / P.N)
+    ph = np.exp(-1j * q * P.dxi)                      # e^{i xi_q x_0}, x_0 = -1
+    Z = np.fft.ifft2(Vc * ph[:, None] * ph[None, :]) * (P.N * P.N)
+    v = (P.dxi * P.dxi / TWO_PI) * Z[: P.n, : P.n].real
+    ann = _annulus(P)
+    C = -v[ann].mean() if (with_constant and ann.any()) else 0.0
+    return (v + C) * P.mask
+
+
+def inverse_direct(P: OraclePlan, g: np.ndarray) -> np.ndarray:
+    """Algorithm 3 without the polar grid: vhat evaluated at every Cartesian node by the
+    mode sum of Eq. Four_ser_v with the exact J'_|k|(|xi|) and sin(|xi| t) (no
+    interpolation), then steps 6-8.  O(N^2 n_phi n_t): tiny grids only."""
+    gg = np.asarray(g, dtype=np.float64) * P.gamma[:, None]
+    Gk = np.fft.fft(gg, axis=0) / P.n_det
+    w = np.full(P.n_t, P.dt)
+    w[-1] *= 0.5
+    q = np.fft.fftfreq(P.N, 1.0 / P.N)
+    QX, QY = np.meshgrid(q, q, indexing="xy")
+    lam = (np.hypot(QX, QY) * P.dxi).ravel()
+    phi = np.arctan2(QY, QX).ravel()
+    keep = lam < P.J * P.dlam
+    Vc = np.zeros(lam.size, dtype=np.complex128)
+    L, F = lam[keep], phi[keep]
+    S = np.sin(np.outer(L, P.t)) @ (w[:, None] * Gk.T)         # (nodes, n_phi)
+    ak = P.absk
+    dJ = 0.5 * (jv(ak[None, :] - 1, L[:, None]) - jv(ak[None, :] + 1, L[:, None]))
+    E = np.exp(1j * F[:, None] * P.k[None, :])
+    Vc[keep] = (-2.0 * ((-1j) ** ak)[None, :] * dJ * S * E).sum(axis=1)
+    Vc = Vc.reshape(P.N, P.N)
+    ph = np.exp(-1j * q * P.dxi)
+    Z = np.fft.ifft2(Vc * ph[:, None] * ph[None, :]) * (P.N * P.N)
+    v = (P.dxi * P.dxi / TWO_PI) * Z[: P.n, : P.n].real
+    ann = _annulus(P)
+    C = -v[ann].mean() if ann.any() else 0.0
+    return (v + C) * P.mask
 
 
 # ----------------------------------------------------------------- slow truths
