@@ -347,13 +347,19 @@ def inverse_modes(P: OraclePlan, g: np.ndarray) -> np.ndarray:
 
 def inverse_resample(P: OraclePlan, V: np.ndarray) -> np.ndarray:
     """Step 5: bilinear interpolation in (lambda, phi) of V[j, l] = vhat(lambda_j, phi_l)
-    at every Cartesian node xi_q of the N x N grid (FFT order); zero beyond ring J."""
+    at every Cartesian node xi_q of the N x N grid (FFT order); zero beyond ring J.
+
+    The cut-off is the resampling's only discontinuity; ties u = |xi_q|/dlam = J occur
+    exactly on some grids (dxi/dlam rational), so the rule is stated with a margin."""
     q = np.fft.fftfreq(P.N, 1.0 / P.N)
     QX, QY = np.meshgrid(q, q, indexing="xy")
     u = np.hypot(QX, QY) * P.dxi / P.dlam
-    j0 = np.floor(u).astype(np.int64)
-    a = u - j0
-    inside = j0 + 1 <= P.J
+    # Closed cut-off: nodes up to ring J (within 1e-6 of a cell, so that exact
+    # rational ties such as u = J are inside whatever the rounding) take the
+    # interpolated value; beyond it vhat = 0.
+    inside = u <= P.J + 1e-6
+    j0 = np.minimum(np.floor(u).astype(np.int64), P.J - 1)
+    a = np.minimum(u - j0, 1.0)
     j0 = np.where(inside, j0, 0)
     s = (np.arctan2(QY, QX) / TWO_PI * P.n_phi) % P.n_phi
     l0 = np.floor(s).astype(np.int64)
@@ -405,7 +411,7 @@ def inverse_direct(P: OraclePlan, g: np.ndarray) -> np.ndarray:
     QX, QY = np.meshgrid(q, q, indexing="xy")
     lam = (np.hypot(QX, QY) * P.dxi).ravel()
     phi = np.arctan2(QY, QX).ravel()
-    keep = lam < P.J * P.dlam
+    keep = lam / P.dlam <= P.J + 1e-6
     Vc = np.zeros(lam.size, dtype=np.complex128)
     L, F = lam[keep], phi[keep]
     S = np.sin(np.outer(L, P.t)) @ (w[:, None] * Gk.T)         # (nodes, n_phi)
