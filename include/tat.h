@@ -129,6 +129,24 @@ tat_status tat_adjoint_batched(tat_plan_t plan, int batch, const float* g, long 
                                float* f, long long f_stride, void* workspace,
                                tat_stream_t stream);
 
+/* f ~ A^{-1} g  (Algorithm 3): the universal backprojection formula for data
+ * on (0, T) x Gamma extended by zero (Eq. approx_UBP), computed on the grids of
+ * A*: detector DFT (Eq. FourSerForg), sine transform in t, the per-mode factor
+ * -2 (-i)^|k| J'_|k|(lambda) of Eq. Four_coef_v (the paper prints -4 pi; the
+ * 2 pi belongs to the transform of G used in its appendix, and -2 is the value
+ * consistent with Eq. green_conv: A^{-1} A f = f for full data as T grows),
+ * the angular series, bilinear polar -> Cartesian interpolation in
+ * (lambda, phi), the 2D inverse DFT, then Pi_Omega0 (v + C) with C the
+ * negative mean of v over the disk |x| <= R outside Omega_0 (Eq.
+ * silly_integral; C = 0 when that set has no grid node).  The result does not
+ * depend on c and R beyond T' = cT/R.  Requires n_phi == n_det (the default),
+ * else TAT_ERR_UNSUPPORTED.  g: n_det*n_t floats, f: n*n floats; workspace as
+ * for A*.  A left inverse on complete data (Gamma the full circle, T large);
+ * on partial data it is the paper's approximate reconstruction. */
+tat_status tat_inverse(tat_plan_t plan, const float* g, float* f, void* workspace, tat_stream_t stream);
+tat_status tat_inverse_batched(tat_plan_t plan, int batch, const float* g, long long g_stride,
+                               float* f, long long f_stride, void* workspace, tat_stream_t stream);
+
 /* g = A f for one image, like tat_forward, but with no workspace argument: the
  * scratch lives in a static 16 MiB device buffer inside the library.  The
  * paper has no counterpart; this exists for callers that cannot allocate

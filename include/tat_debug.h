@@ -45,6 +45,11 @@ tat_status tat_debug_forward_batched_timed(tat_plan_t plan, int batch, const flo
 tat_status tat_debug_adjoint_batched_timed(tat_plan_t plan, int batch, const float* g, long long g_stride,
                                            float* f, long long f_stride, void* workspace, tat_stream_t stream,
                                            void* const* events);
+/* tat_inverse_batched with 7 events: before the first stage and after each of
+ * detectors, modes (sine transform), rings, columns, rows, and the constant C. */
+tat_status tat_debug_inverse_batched_timed(tat_plan_t plan, int batch, const float* g, long long g_stride,
+                                           float* f, long long f_stride, void* workspace, tat_stream_t stream,
+                                           void* const* events);
 
 #ifdef __cplusplus
 }

@@ -22,9 +22,10 @@ __all__ = ["TatError", "TatOperator", "header_symbols", "load", "tat_adjoint", "
 from . import autograd, solvers  # noqa: E402
 from .autograd import A, Astar  # noqa: E402
 from .solvers import TatSolver, nnls_unrolled, pdhg_steps, power_norm_sq, tv_unrolled  # noqa: E402
+from .binding import tat_debug_inverse_batched_timed, tat_inverse, tat_inverse_batched  # noqa: E402
 from .binding import (tat_axpby_clamp, tat_axpby_clamp_backward, tat_pd_dual_data, tat_tv_dual,  # noqa: E402
                       tat_tv_dual_backward, tat_tv_primal, tat_tv_primal_backward)
 
-__all__ += ["autograd", "solvers", "A", "Astar", "TatSolver", "nnls_unrolled", "pdhg_steps", "power_norm_sq",
+__all__ += ["tat_inverse", "tat_inverse_batched", "tat_debug_inverse_batched_timed", "autograd", "solvers", "A", "Astar", "TatSolver", "nnls_unrolled", "pdhg_steps", "power_norm_sq",
             "tv_unrolled", "tat_axpby_clamp", "tat_axpby_clamp_backward", "tat_pd_dual_data", "tat_tv_dual",
             "tat_tv_dual_backward", "tat_tv_primal", "tat_tv_primal_backward"]

@@ -1,4 +1,4 @@
-"""ctypes binding of libtat (include/tat.h, include/tat_debug.h).
+"""ctypes binding of libtat (include/tat.h, include/tat_debug.h, include/tat_solvers.h).
 
 Argument marshalling only: every step of A and A* runs in the CUDA kernels of
 libtat.  Functions keep the C names.  Device buffers are passed as integer
@@ -79,6 +79,9 @@ def load() -> ctypes.CDLL:
                                     ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_D),
                                     ctypes.POINTER(_D), _I]),
         "tat_forward_noalloc": (_I, [_P, _P, _P, _P]),
+        "tat_inverse": (_I, [_P, _P, _P, _P, _P]),
+        "tat_inverse_batched": (_I, [_P, _I, _P, _LL, _P, _LL, _P, _P]),
+        "tat_debug_inverse_batched_timed": (_I, [_P, _I, _P, _LL, _P, _LL, _P, _P, ctypes.POINTER(_P)]),
         "tat_debug_forward_batched_timed": (_I, [_P, _I, _P, _LL, _P, _LL, _P, _P, ctypes.POINTER(_P)]),
         "tat_debug_adjoint_batched_timed": (_I, [_P, _I, _P, _LL, _P, _LL, _P, _P, ctypes.POINTER(_P)]),
         "tat_axpby_clamp": (_I, [_LL, _F, _P, _F, _P, _F, _P, _LL, _P, _P]),
@@ -160,6 +163,21 @@ def tat_forward(plan, f_ptr, g_ptr, ws_ptr, stream=0):
 
 def tat_adjoint(plan, g_ptr, f_ptr, ws_ptr, stream=0):
     _check(load().tat_adjoint(plan, g_ptr, f_ptr, ws_ptr, stream or None), "tat_adjoint")
+
+
+def tat_inverse(plan, g_ptr, f_ptr, ws_ptr, stream=0):
+    _check(load().tat_inverse(plan, g_ptr, f_ptr, ws_ptr, stream or None), "tat_inverse")
+
+
+def tat_inverse_batched(plan, batch, g_ptr, g_stride, f_ptr, f_stride, ws_ptr, stream=0):
+    _check(load().tat_inverse_batched(plan, batch, g_ptr, g_stride, f_ptr, f_stride, ws_ptr, stream or None),
+           "tat_inverse_batched")
+
+
+def tat_debug_inverse_batched_timed(plan, batch, g_ptr, g_stride, f_ptr, f_stride, ws_ptr, stream, events):
+    """events: 7 raw cudaEvent_t handles."""
+    _check(load().tat_debug_inverse_batched_timed(plan, batch, g_ptr, g_stride, f_ptr, f_stride, ws_ptr,
+                                                  stream or None, _events(events)), "tat_debug_inverse_batched_timed")
 
 
 def tat_forward_noalloc(plan, f_ptr, g_ptr, stream=0):
@@ -329,6 +347,21 @@ class TatOperator:
         ws = self.workspace(B)
         with torch.cuda.device(self.device):
             tat_adjoint_batched(self.plan, B, gb.data_ptr(), self.n_det * self.n_t, f.data_ptr(), self.n * self.n,
+                                ws.data_ptr(), self._stream())
+        return f[0] if single and out is None else f
+
+    def inverse(self, g, out=None):
+        """f ~ A^{-1} g (Algorithm 3) for (n_det, n_t) or (B, n_det, n_t) data."""
+        torch = self.torch
+        single = g.dim() == 2
+        gb = g.reshape(-1, self.n_det, self.n_t)
+        if gb.dtype != torch.float32 or not gb.is_cuda or not gb.is_contiguous():
+            raise ValueError("g must be a contiguous float32 CUDA tensor")
+        B = gb.shape[0]
+        f = out if out is not None else torch.empty((B, self.n, self.n), dtype=torch.float32, device=gb.device)
+        ws = self.workspace(B)
+        with torch.cuda.device(self.device):
+            tat_inverse_batched(self.plan, B, gb.data_ptr(), self.n_det * self.n_t, f.data_ptr(), self.n * self.n,
                                 ws.data_ptr(), self._stream())
         return f[0] if single and out is None else f
 

@@ -142,6 +142,24 @@ tat_status tat_adjoint(tat_plan_t plan, const float* g, float* f, void* workspac
                              (long long)plan->d.n * plan->d.n, workspace, stream);
 }
 
+tat_status tat_inverse_batched(tat_plan_t plan, int batch, const float* g, long long g_stride, float* f,
+                               long long f_stride, void* workspace, tat_stream_t stream) {
+  if (!plan || batch < 1) return TAT_ERR_INVALID_ARG;
+  const tat::DevPlan& d = plan->d;
+  if (f_stride < (long long)d.n * d.n || g_stride < (long long)d.n_det * d.n_t) return TAT_ERR_INVALID_ARG;
+  if (!d.inv_ok) return TAT_ERR_UNSUPPORTED;
+  tat_status s = check_pointers(g, f, workspace);
+  if (s == TAT_OK) s = check_device(plan);
+  if (s != TAT_OK) return s;
+  return tat::launch_inverse(plan, batch, g, g_stride, f, f_stride, workspace, static_cast<cudaStream_t>(stream));
+}
+
+tat_status tat_inverse(tat_plan_t plan, const float* g, float* f, void* workspace, tat_stream_t stream) {
+  if (!plan) return TAT_ERR_INVALID_ARG;
+  return tat_inverse_batched(plan, 1, g, (long long)plan->d.n_det * plan->d.n_t, f,
+                             (long long)plan->d.n * plan->d.n, workspace, stream);
+}
+
 tat_status tat_debug_bessel(double x, int kmax, double* out) {
   if (!out || kmax < 0 || !(x >= 0)) return TAT_ERR_INVALID_ARG;
   tat::bessel_orders(x, kmax, out);
@@ -201,6 +219,20 @@ tat_status tat_debug_adjoint_batched_timed(tat_plan_t plan, int batch, const flo
   if (s == TAT_OK) s = check_device(plan);
   if (s != TAT_OK) return s;
   return tat::launch_adjoint(plan, batch, g, g_stride, f, f_stride, workspace, static_cast<cudaStream_t>(stream),
+                             reinterpret_cast<cudaEvent_t const*>(events));
+}
+
+tat_status tat_debug_inverse_batched_timed(tat_plan_t plan, int batch, const float* g, long long g_stride,
+                                           float* f, long long f_stride, void* workspace, tat_stream_t stream,
+                                           void* const* events) {
+  if (!plan || batch < 1 || !events) return TAT_ERR_INVALID_ARG;
+  const tat::DevPlan& d = plan->d;
+  if (f_stride < (long long)d.n * d.n || g_stride < (long long)d.n_det * d.n_t) return TAT_ERR_INVALID_ARG;
+  if (!d.inv_ok) return TAT_ERR_UNSUPPORTED;
+  tat_status s = check_pointers(g, f, workspace);
+  if (s == TAT_OK) s = check_device(plan);
+  if (s != TAT_OK) return s;
+  return tat::launch_inverse(plan, batch, g, g_stride, f, f_stride, workspace, static_cast<cudaStream_t>(stream),
                              reinterpret_cast<cudaEvent_t const*>(events));
 }
 

@@ -1,0 +1,67 @@
+// Launcher of the approximate inverse A^{-1} (Algorithm 3, universal
+// backprojection with the constant C of Eq. silly_integral): six
+// stream-ordered kernels per batch on the grids of the adjoint; see
+// kernels.cuh for what each stage computes.
+#include "launch.cuh"
+
+namespace tat {
+
+tat_status launch_inverse(const tat_plan_s* Pl, int batch, const float* g, long long gs, float* f, long long fs,
+                          void* ws, cudaStream_t st, cudaEvent_t const* ev) {
+  const DevPlan& P = Pl->d;
+  if (!P.inv_ok) return TAT_ERR_UNSUPPORTED;
+  const LaunchCfg& c = Pl->cfg;
+  const Shapes s = shapes(Pl, batch);
+  float2* X = static_cast<float2*>(ws);
+  float2* Y = X + (size_t)batch * Pl->ws_x;
+  const long long xs = (long long)Pl->ws_x, ys = (long long)Pl->ws_y;
+  // the per-image accumulator of C: element 0 of the image's Y region, as a float
+  float* acc = reinterpret_cast<float*>(Y);
+  const long long accs = 2 * ys;
+  const int dev = Pl->device;
+  bool ok = true;
+  int mark = 0;
+  auto stage_done = [&]() {
+    if (ev) cudaEventRecord(ev[mark++], st);
+  };
+  stage_done();
+  dispatch_ang(P.n_det, [&](auto Lc) {
+    constexpr int L = decltype(Lc)::value;
+    ok &= ensure_smem<k_theta_adj<L>>(dev);
+    k_theta_adj<L><<<s.theta_grid, s.theta_block, s.theta_smem, st>>>(P, g, gs, Y, ys, c.t_tile, c.nt_det);
+    stage_done();
+  });
+  dispatch_2M(2 * P.M, [&](auto Lc) {
+    constexpr int L = decltype(Lc)::value;
+    ok &= ensure_smem<k_modes_inv<L>>(dev);
+    k_modes_inv<L><<<s.modes_grid, s.modes_block, s.modes_smem, st>>>(P, Y, ys, X, xs, c.nt_2M);
+    stage_done();
+  });
+  dispatch_ang(P.n_phi, [&](auto Lc) {
+    constexpr int L = decltype(Lc)::value;
+    ok &= ensure_smem<k_rings_adj<L, true>>(dev);
+    const dim3 grid(s.ntiles, batch);
+    k_rings_adj<L, true><<<grid, s.rings_block, s.rings_smem, st>>>(P, X, xs, Y, ys, c.rings_per_cta, c.nt_phi,
+                                                                     s.ntiles);
+    stage_done();
+  });
+  dispatch_N(P.N, [&](auto Lc) {
+    constexpr int L = decltype(Lc)::value;
+    ok &= ensure_smem<k_cols_inv<L>>(dev) && ensure_smem<k_rows_inv<L>>(dev);
+    k_cols_inv<L><<<s.cols_grid_a, s.cols_block, s.cols_smem_i, st>>>(P, Y, ys, X, xs, c.strip, c.nt_N, batch, acc,
+                                                                      accs);
+    stage_done();
+    k_rows_inv<L><<<s.rows_grid, s.rows_block, s.rows_smem, st>>>(P, X, xs, f, fs, acc, accs, c.rows_pairs,
+                                                                  c.nt_rows);
+    stage_done();
+  });
+  {
+    const long long count = (long long)batch * P.n * P.n;
+    const int blocks = (int)std::min<long long>((count + 255) / 256, 152LL * 8);
+    k_inv_finish<<<blocks, 256, 0, st>>>(P, batch, acc, accs, f, fs);
+    stage_done();
+  }
+  return check_launch(ok);
+}
+
+}  // namespace tat

@@ -418,7 +418,10 @@ __global__ void __launch_bounds__(1024) k_modes_adj(DevPlan P, const float2* __r
   }
 }
 
-template <int L>
+// INV = false: the adjoint's per-mode multiplier (-i)^k dlam lam_j J_k(lam_j)/n_phi and
+// the low-mode rings.  INV = true: the inverse's (Eq. Four_coef_v, see k_modes_inv)
+// (-i)^(k+1) J'_k(lam_j) dt/n_det and no low-mode rings.  Rings 1..J are written.
+template <int L, bool INV = false>
 __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __restrict__ X, long long xs, float2* __restrict__ Y,
                             long long ys, int /*rings per CTA*/, int nt, int ntiles) {
   constexpr int RPC = rings_per_cta_for(L);
@@ -427,7 +430,7 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
   const float2* Xb = X + (size_t)b * xs;
   float2* Yb = Y + (size_t)b * ys;
   const int J1 = P.J + 1;
-  if ((int)blockIdx.x >= ntiles) {
+  if (!INV && (int)blockIdx.x >= ntiles) {
     // Low-mode ring: F'(phi) = c0 + c1 e^{i phi} + c_{-1} e^{-i phi}, c_{-1} = -conj(c1).
     const int q = blockIdx.x - ntiles;
     const int r = P.J + 1 + q;
@@ -452,8 +455,11 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
     const int k = e / RPC, gg = e % RPC;
     const int rr = rbase + gg;
     float2 w = make_float2(0.f, 0.f);
-    if (rr <= P.J && !(P.low_on && k <= 1 && rr < kLowA))
+    if constexpr (INV) {
+      if (rr <= P.J) w = mul_mipow(cscale(Xb[(size_t)k * J1 + rr], P.Binv[(size_t)k * J1 + rr]), k + 1);
+    } else if (rr <= P.J && !(P.low_on && k <= 1 && rr < kLowA)) {
       w = mul_mipow(cscale(Xb[(size_t)k * J1 + rr], P.Bt[(size_t)k * J1 + rr]), k);
+    }
     float2* bg = sm + gg * SL;
     bg[spad(colpos<L>(k))] = w;
     if (k >= 1 && k < P.K) {
@@ -598,21 +604,19 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
   }
 }
 
+// Row stage of A* and A^{-1}: rebuilds the Hermitian row spectra of this CTA's
+// RP row pairs from the column-major R'[q][iy] and runs the inverse row DFTs;
+// row pair g of the CTA ends in sm + g * spad_len(N), rows 2*pair and 2*pair+1
+// in the real and imaginary parts.
 template <int L>
-__global__ void __launch_bounds__(1024) k_rows_adj(DevPlan P, const float2* __restrict__ X, long long xs, float* __restrict__ f,
-                           long long fs, int RP, int nt) {
-  extern __shared__ float2 sm[];
-  const int b = blockIdx.y;
+__device__ __forceinline__ void rows_inverse_dft(const DevPlan& P, const float2* __restrict__ Xb, float2* sm, int RP,
+                                                 int nt) {
   const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
   const int N = P.N;
   const int SL = spad_len(N);
   float2* buf = sm + g * SL;
   float2* smtw = sm + RP * SL;  // four-step twiddles
   load_fourstep_tw(smtw, P.fN.fstw, threadIdx.x, blockDim.x);
-  const int pair = blockIdx.x * RP + g;
-  const int iy1 = 2 * pair, iy2 = 2 * pair + 1;
-  const bool v1 = iy1 < P.n, v2 = iy2 < P.n;
-  const float2* Xb = X + (size_t)b * xs;
   // Rebuild each row's Hermitian spectrum from R'[q][iy] (column-major):
   // H[q] = conj(phase[q]) R'[q] for q < N/2, H[N-q] = conj(H[q]), H[N/2] = 0;
   // consecutive threads read consecutive rows of one column.
@@ -631,6 +635,19 @@ __global__ void __launch_bounds__(1024) k_rows_adj(DevPlan P, const float2* __re
   }
   __syncthreads();
   col_fft_inv<L>(buf, P.fN, smtw, gt, nt, nt, P.n, nullptr);
+}
+
+template <int L>
+__global__ void __launch_bounds__(1024) k_rows_adj(DevPlan P, const float2* __restrict__ X, long long xs, float* __restrict__ f,
+                           long long fs, int RP, int nt) {
+  extern __shared__ float2 sm[];
+  const int b = blockIdx.y;
+  const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
+  rows_inverse_dft<L>(P, X + (size_t)b * xs, sm, RP, nt);
+  const float2* buf = sm + g * spad_len(P.N);
+  const int pair = blockIdx.x * RP + g;
+  const int iy1 = 2 * pair, iy2 = 2 * pair + 1;
+  const bool v1 = iy1 < P.n, v2 = iy2 < P.n;
   float* fb = f + (size_t)b * fs;
   const int2 r1 = v1 ? P.rowrange[iy1] : make_int2(0, 0);
   const int2 r2 = v2 ? P.rowrange[iy2] : make_int2(0, 0);
@@ -638,6 +655,198 @@ __global__ void __launch_bounds__(1024) k_rows_adj(DevPlan P, const float2* __re
     const float2 z = buf[spad(ix)];
     if (v1) fb[(size_t)iy1 * P.n + ix] = (ix >= r1.x && ix < r1.y) ? P.adj_scale * z.x : 0.f;
     if (v2) fb[(size_t)iy2 * P.n + ix] = (ix >= r2.x && ix < r2.y) ? P.adj_scale * z.y : 0.f;
+  }
+}
+
+// ------------------------------------------------------------------ inverse (Algorithm 3)
+//
+// v(x) = F^{-1}[ sum_k e^{ik phi} vhat_k(lambda) ](x), with
+//   vhat_k(lambda) = -2 (-i)^|k| J'_|k|(lambda) int_0^T g_k(t) sin(lambda t) dt
+// (Eq. Four_coef_v; the constant is fixed by the Fourier transform of G that
+// Eq. green_conv and Eq. gseries use), then f = Pi_Omega0 (v + C) with C such
+// that v + C has zero mean over Omega \ Omega0 (Eq. silly_integral).  Stages:
+// k_theta_adj (g'_k(t_m) = sum_d g e^{-ik theta_d} = n_det g_k), k_modes_inv,
+// k_rings_adj<L, true>, k_cols_inv, k_rows_inv, k_inv_finish.
+
+// Sine transform per mode (Algorithm 3, step 3): the length-2M FFT of the odd
+// extension of the trapezoid-weighted samples (weight 1/2 at t = T; t = 0 drops
+// out) gives FFT_j = -2i sum_m w_m sin(lam_j t_m) g'_k(t_m).  The factor i/2 and
+// the -2 of Eq. Four_coef_v make the ring multiplier (-i)^(k+1) J'_k dt/n_det.
+template <int L>
+__global__ void __launch_bounds__(1024) k_modes_inv(DevPlan P, const float2* __restrict__ Y, long long ys,
+                                                    float2* __restrict__ X, long long xs, int nt) {
+  extern __shared__ float2 sm[];
+  const int b = blockIdx.y, k = blockIdx.x;
+  const int J1 = P.J + 1, L2 = 2 * P.M;
+  const float2* Gp = Y + (size_t)b * ys + (size_t)k * P.n_t;
+  float2* smptw = sm + spad_len(L2);
+  load_pass_tw(smptw, P.f2M, threadIdx.x, blockDim.x);
+  for (int j = threadIdx.x; j < L2; j += blockDim.x) {
+    float2 v = make_float2(0.f, 0.f);
+    const int m = j <= P.M ? j : L2 - j;
+    if (m > 0 && m < P.n_t) {
+      v = Gp[m];
+      if (m == P.n_t - 1) v = cscale(v, 0.5f);
+      if (j > P.M) v = make_float2(-v.x, -v.y);
+    }
+    sm[spad(j)] = v;
+  }
+  __syncthreads();
+  fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, J1, nullptr, nullptr, smptw);
+  float2* Dm = X + (size_t)b * xs + (size_t)k * J1;
+  for (int j = threadIdx.x; j < J1; j += blockDim.x) Dm[j] = sm[spad(j)];
+}
+
+// Polar sample Y[ring j][l'] of the half circle; ring 0 (lambda = 0) is zero for
+// the inverse, and l' = nh (phi = pi/2) is the conjugate of l' = 0 (phi = -pi/2).
+__device__ __forceinline__ float2 inv_polar(const DevPlan& P, const float2* __restrict__ Yb, int j, int l) {
+  if (j == 0) return make_float2(0.f, 0.f);
+  if (l >= P.nh) return cconj(Yb[(size_t)j * P.nh + (l - P.nh)]);
+  return Yb[(size_t)j * P.nh + l];
+}
+
+// vhat at the Cartesian node (c, qs) of the half plane (Algorithm 3, step 5):
+// bilinear interpolation in (lambda, phi) of the polar samples, zero beyond
+// ring J + 1e-6.  lambda/dlam and the offset of phi from the grid angle phi_l0 are
+// formed in two-float arithmetic (an FP32 position is off by ~1e-4 of a cell
+// at the outer rings, which the interpolation weights would carry).
+__device__ __forceinline__ float2 inv_node(const DevPlan& P, const float2* __restrict__ Yb, int c, int qs) {
+  const int n2 = c * c + qs * qs;
+  if (n2 == 0) return make_float2(0.f, 0.f);
+  // r = |(c, qs)| = s + ds exactly to ~1e-14 relative
+  const float n2h = (float)n2;
+  const float n2l = (float)(n2 - (int)n2h);
+  const float s = sqrtf(n2h);
+  const float ds = (fmaf(-s, s, n2h) + n2l) / (2.f * s);
+  // u = r * dxi / dlam = uh + ul
+  const float uh = s * P.inv_rho_hi;
+  const float ul = fmaf(s, P.inv_rho_hi, -uh) + fmaf(s, P.inv_rho_lo, ds * P.inv_rho_hi);
+  float jf = floorf(uh);
+  float a = (uh - jf) + ul;
+  if (a < 0.f) {
+    a += 1.f;
+    jf -= 1.f;
+  } else if (a >= 1.f) {
+    a -= 1.f;
+    jf += 1.f;
+  }
+  int j = (int)jf;
+  if (j >= P.J) {
+    // closed cut-off at ring J, with ties (u = J exactly on grids where dxi/dlam
+    // is rational) inside: u in [J, J + 1e-6] takes the ring-J value
+    if (j > P.J || a > 1e-6f) return make_float2(0.f, 0.f);
+    j = P.J - 1;
+    a = 1.f;
+  }
+  // angle: approximate cell from atan2f, exact offset from phi_l0 by
+  // sin(phi - phi_l0) = (qs cos phi_l0 - c sin phi_l0) / r with a two-float cos/sin table
+  const float qf = (float)qs, cf = (float)c;
+  const float pos = fmaf(atan2f(qf, cf), P.inv_nphi_2pi, (float)(P.nh / 2));
+  const int l0 = min(max((int)floorf(pos), 0), P.nh - 1);
+  const float2 ch = P.cs_half[l0], cl = P.cs_half_lo[l0];
+  const float t1 = qf * ch.x, t2 = cf * ch.y;
+  const float e1 = fmaf(qf, ch.x, -t1), e2 = fmaf(cf, ch.y, -t2);
+  const float num = (t1 - t2) + ((e1 - e2) + (qf * cl.x - cf * cl.y));
+  const float bb = asinf(num / (s + ds)) * P.inv_nphi_2pi;
+  const float2 v00 = inv_polar(P, Yb, j, l0), v01 = inv_polar(P, Yb, j, l0 + 1);
+  const float2 v10 = inv_polar(P, Yb, j + 1, l0), v11 = inv_polar(P, Yb, j + 1, l0 + 1);
+  const float2 va = cadd(cscale(v00, 1.f - bb), cscale(v01, bb));
+  const float2 vb = cadd(cscale(v10, 1.f - bb), cscale(v11, bb));
+  return cadd(cscale(va, 1.f - a), cscale(vb, a));
+}
+
+// Steps 5-6 (columns): per strip of half-plane columns, vhat on the whole
+// column (times conj(e^{i q dxi}), the x_0 = -1 phase of the inverse DFT), the
+// inverse column DFT, first n rows kept -> X = V'[c][iy].  The strip-0 CTA of
+// each image also clears the image's accumulator of the constant C (`acc`, in
+// element 0 of the image's Y region: ring 0, which this kernel never reads).
+template <int L>
+__global__ void TAT_COLS_BOUNDS_F k_cols_inv(DevPlan P, const float2* __restrict__ Y, long long ys,
+                                           float2* __restrict__ X, long long xs, int S, int nt, int batch,
+                                           float* acc, long long accs) {
+  extern __shared__ float2 sm[];
+  int strip, b;
+  strip_and_image(batch, &strip, &b);
+  const int N = P.N;
+  const int SL = spad_len(N);
+  const int tid = threadIdx.x, NT = blockDim.x;
+  float2* buf = sm;
+  float2* smtw = sm + SL;  // four-step twiddles
+  load_fourstep_tw(smtw, P.fN.fstw, tid, NT);
+  const int c0 = strip * S;
+  const int c1 = min(c0 + S, P.ncol);
+  const float2* Yb = Y + (size_t)b * ys;
+  float2* Xb = X + (size_t)b * xs;
+  if (strip == 0 && tid == 0) acc[(size_t)b * accs] = 0.f;
+#pragma unroll 1
+  for (int c = c0; c < c1; ++c) {
+    for (int q = tid; q < N; q += NT) {
+      const int qs = q < N / 2 ? q : q - N;
+      buf[spad(colpos<L>(q))] = cmulc(inv_node(P, Yb, c, qs), __ldg(&P.phase[q]));
+    }
+    __syncthreads();
+    col_fft_inv<L>(buf, P.fN, smtw, tid, NT, nt, P.n, nullptr);
+    float2* col = Xb + (size_t)c * P.n;
+    for (int iy = tid; iy < P.n; iy += NT) col[iy] = buf[spad(iy)];
+    __syncthreads();
+  }
+}
+
+// Steps 6 (rows) and 7: the inverse row DFTs give v on the whole n x n grid
+// (times dxi^2/2pi); each CTA adds its sum of v over Omega \ Omega0 into the
+// image's accumulator.
+template <int L>
+__global__ void __launch_bounds__(1024) k_rows_inv(DevPlan P, const float2* __restrict__ X, long long xs,
+                                                   float* __restrict__ f, long long fs, float* acc, long long accs,
+                                                   int RP, int nt) {
+  extern __shared__ float2 sm[];
+  const int b = blockIdx.y;
+  const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
+  rows_inverse_dft<L>(P, X + (size_t)b * xs, sm, RP, nt);
+  const float2* buf = sm + g * spad_len(P.N);
+  const int pair = blockIdx.x * RP + g;
+  const int iy1 = 2 * pair, iy2 = 2 * pair + 1;
+  const bool v1 = iy1 < P.n, v2 = iy2 < P.n;
+  float* fb = f + (size_t)b * fs;
+  const int2 s1 = v1 ? P.rowrange[iy1] : make_int2(0, 0), o1 = v1 ? P.outrange[iy1] : make_int2(0, 0);
+  const int2 s2 = v2 ? P.rowrange[iy2] : make_int2(0, 0), o2 = v2 ? P.outrange[iy2] : make_int2(0, 0);
+  float ring = 0.f;
+  for (int ix = gt; ix < P.n; ix += nt) {
+    const float2 z = buf[spad(ix)];
+    const float a = P.inv_scale * z.x, c = P.inv_scale * z.y;
+    if (v1) {
+      fb[(size_t)iy1 * P.n + ix] = a;
+      if (ix >= o1.x && ix < o1.y && !(ix >= s1.x && ix < s1.y)) ring += a;
+    }
+    if (v2) {
+      fb[(size_t)iy2 * P.n + ix] = c;
+      if (ix >= o2.x && ix < o2.y && !(ix >= s2.x && ix < s2.y)) ring += c;
+    }
+  }
+  // block sum in shared memory (the block need not be a multiple of 32 threads)
+  __syncthreads();
+  float* red = reinterpret_cast<float*>(sm);
+  red[threadIdx.x] = ring;
+  __syncthreads();
+  for (int st = 1; st < (int)blockDim.x; st <<= 1) {
+    if ((threadIdx.x & (2 * st - 1)) == 0 && threadIdx.x + st < blockDim.x) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && red[0] != 0.f) atomicAdd(acc + (size_t)b * accs, red[0]);
+}
+
+// Step 8: f = Pi_Omega0 (v + C), C = -(sum of v over Omega \ Omega0) / (its node count).
+__global__ void k_inv_finish(DevPlan P, int batch, const float* __restrict__ acc, long long accs, float* f,
+                             long long fs) {
+  const long long nn = (long long)P.n * P.n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn * batch;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / nn, r = i - b * nn;
+    const int iy = (int)(r / P.n), ix = (int)(r - (long long)iy * P.n);
+    const float C = P.inv_count > 0.f ? -acc[(size_t)b * accs] / P.inv_count : 0.f;
+    const int2 s = P.rowrange[iy];
+    float* p = f + (size_t)b * fs + r;
+    *p = (ix >= s.x && ix < s.y) ? *p + C : 0.f;
   }
 }
 

@@ -417,6 +417,27 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
       rr_rows[iy] = make_int2(lo, hi);
     }
     TAT_TRY(upload(P, rr_rows, &d.rowrange));
+    // The disk Omega inside the detector circle (|x| <= R: (2ix-(n-1))^2 + (2iy-(n-1))^2 <= (n-1)^2)
+    // and the node count of Omega \ Omega0, over which the inverse's constant C is fixed.
+    const double ro = (double)(n - 1) * (double)(n - 1);
+    std::vector<int2> out_rows(n);
+    long long ring_nodes = 0;
+    for (int iy = 0; iy < n; ++iy) {
+      int lo = n, hi = 0;
+      const double sy = 2.0 * iy - (n - 1);
+      for (int ix = 0; ix < n; ++ix) {
+        const double sx = 2.0 * ix - (n - 1);
+        if (sx * sx + sy * sy <= ro) {
+          lo = std::min(lo, ix);
+          hi = ix + 1;
+          if (!(ix >= rr_rows[iy].x && ix < rr_rows[iy].y)) ++ring_nodes;
+        }
+      }
+      if (hi == 0) lo = 0;
+      out_rows[iy] = make_int2(lo, hi);
+    }
+    TAT_TRY(upload(P, out_rows, &d.outrange));
+    d.inv_count = (float)ring_nodes;
   }
   // Detector arc Gamma.
   {
@@ -438,20 +459,32 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
     low_mode_rule(lx.data(), lw.data());
     for (int q = 0; q < kLowM; ++q) lam[d.J + 1 + q] = lx[q] * dlam;
   }
-  // Bessel table J_k(lambda_r) for k = 0..K (Section 3.1: precomputed once per plan).
-  std::vector<double> Jt((size_t)d.n_rings * (d.K + 1));
-  parallel_for(d.n_rings, [&](int r) { bessel_orders(lam[r], d.K, &Jt[(size_t)r * (d.K + 1)]); });
+  // Bessel table J_k(lambda_r) for k = 0..K+1 (Section 3.1: precomputed once per plan;
+  // order K+1 enters J'_K of the inverse).
+  const int KS = d.K + 2;
+  std::vector<double> Jt((size_t)d.n_rings * KS);
+  parallel_for(d.n_rings, [&](int r) { bessel_orders(lam[r], d.K + 1, &Jt[(size_t)r * KS]); });
   {
     std::vector<float> Bt((size_t)(d.K + 1) * (d.J + 1));
     for (int k = 0; k <= d.K; ++k)
       for (int j = 0; j <= d.J; ++j)
-        Bt[(size_t)k * (d.J + 1) + j] = (float)(dlam * lam[j] * Jt[(size_t)j * (d.K + 1) + k] / n_phi);
+        Bt[(size_t)k * (d.J + 1) + j] = (float)(dlam * lam[j] * Jt[(size_t)j * KS + k] / n_phi);
     TAT_TRY(upload(P, Bt, &d.Bt));
+    // Inverse (Eq. Four_coef_v): J'_0 = -J_1, J'_k = (J_{k-1} - J_{k+1}) / 2, times the
+    // time step and the 1/n_det of the detector DFT (Eq. FourSerForg).
+    std::vector<float> Bi((size_t)(d.K + 1) * (d.J + 1));
+    for (int k = 0; k <= d.K; ++k)
+      for (int j = 0; j <= d.J; ++j) {
+        const double* Jr = &Jt[(size_t)j * KS];
+        const double dJ = k == 0 ? -Jr[1] : 0.5 * (Jr[k - 1] - Jr[k + 1]);
+        Bi[(size_t)k * (d.J + 1) + j] = (float)(dJ * dt / n_det);
+      }
+    TAT_TRY(upload(P, Bi, &d.Binv));
     std::vector<float> Bh(2 * std::max(d.n_low, 1), 0.0f), Lc((size_t)std::max(d.n_low, 1) * n_t, 0.0f);
     for (int q = 0; q < d.n_low; ++q) {
       const int r = d.J + 1 + q;
       for (int k = 0; k < 2; ++k)
-        Bh[k * d.n_low + q] = (float)(lw[q] * dlam * lam[r] * Jt[(size_t)r * (d.K + 1) + k] / n_phi);
+        Bh[k * d.n_low + q] = (float)(lw[q] * dlam * lam[r] * Jt[(size_t)r * KS + k] / n_phi);
       for (int m = 0; m < n_t; ++m) Lc[(size_t)q * n_t + m] = (float)std::cos(lam[r] * ((double)m * dt));
     }
     TAT_TRY(upload(P, Bh, &d.Bh));
@@ -461,11 +494,21 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
   std::vector<double> hc(d.nh), hs(d.nh);
   {
     std::vector<float2> cs(d.nh);
+    std::vector<float2> cs_lo(d.nh);
     for (int lp = 0; lp < d.nh; ++lp) {
       cos_sin_2pi(lp - n_phi / 4, n_phi, &hc[lp], &hs[lp]);
       cs[lp] = make_float2((float)hc[lp], (float)hs[lp]);
+      cs_lo[lp] = make_float2((float)(hc[lp] - (double)cs[lp].x), (float)(hs[lp] - (double)cs[lp].y));
     }
     TAT_TRY(upload(P, cs, &d.cs_half));
+    TAT_TRY(upload(P, cs_lo, &d.cs_half_lo));
+    // Scalars of the inverse's polar -> Cartesian resampling and 2D inverse DFT.
+    const double rho = dxi / dlam;
+    d.inv_rho_hi = (float)rho;
+    d.inv_rho_lo = (float)(rho - (double)d.inv_rho_hi);
+    d.inv_nphi_2pi = (float)(n_phi / (2.0 * kPi));
+    d.inv_scale = (float)(dxi * dxi / (2.0 * kPi));
+    d.inv_ok = n_phi == n_det ? 1 : 0;
   }
   // Bilinear stencils of every half-plane polar sample (rings 1..J and the
   // low-mode rings), bucketed by stencil column i0 and sorted by row k0.

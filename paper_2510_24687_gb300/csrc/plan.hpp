@@ -66,6 +66,15 @@ struct DevPlan {
   const float* Bh;                 // [2 x n_low]     w_q*dlam*lam_q*J_k(lam_q)/n_phi
   const float* Lcos;               // [n_low x n_t]   cos(lam_q t_m)
   const float2* cs_half;           // [nh] (cos phi, sin phi) of the half-circle angles
+  // inverse A^{-1} (Algorithm 3)
+  const float* Binv;               // [(K+1) x (J+1)] J'_k(lam_j) dt / n_det
+  const float2* cs_half_lo;        // [nh] cos, sin of the half-circle angles minus their FP32 values
+  const int2* outrange;            // [n] columns [lo, hi) of each row inside |x| <= R (the disk Omega)
+  float inv_scale;                 // dxi^2 / (2 pi)
+  float inv_rho_hi, inv_rho_lo;    // dxi / dlam as a two-float sum
+  float inv_nphi_2pi;              // n_phi / (2 pi)
+  float inv_count;                 // nodes of Omega \ Omega0 (0: no constant C)
+  int inv_ok;                      // n_phi == n_det (the inverse keeps the data's own modes)
 };
 
 // Tile shapes fixed at compile time per FFT length (index arithmetic by
@@ -128,5 +137,8 @@ tat_status validate_shapes(const tat_plan_s* P);
 tat_status launch_forward(const tat_plan_s* P, int batch, const float* f, long long fs,
                           float* g, long long gs, void* ws, cudaStream_t st, cudaEvent_t const* ev = nullptr);
 tat_status launch_adjoint(const tat_plan_s* P, int batch, const float* g, long long gs,
+                          float* f, long long fs, void* ws, cudaStream_t st, cudaEvent_t const* ev = nullptr);
+// `ev` (optional): 7 events recorded before the first and after every stage.
+tat_status launch_inverse(const tat_plan_s* P, int batch, const float* g, long long gs,
                           float* f, long long fs, void* ws, cudaStream_t st, cudaEvent_t const* ev = nullptr);
 }  // namespace tat
