@@ -45,8 +45,10 @@ def parse_args():
     p.add_argument("--batch", type=int, default=32)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", choices=["pair", "solves"], default="pair",
-                   help="pair: the A+A* throughput line (default); solves: batched NNLS + TV-PDHG reconstructions")
+    p.add_argument("--workload", choices=["pair", "solves", "inverse", "service"], default="pair",
+                   help="pair: the A+A* throughput line (default); solves: batched NNLS + TV-PDHG "
+                        "reconstructions; inverse: the approximate inverse (Algorithm 3); service: 64 mixed-size "
+                        "requests through the batching runtime")
     return p.parse_args()
 
 
@@ -253,6 +255,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.workload == "solves":
         return run_solves(args, rank, world, local)
+    if args.workload == "inverse":
+        return run_inverse(args, rank, world, local)
+    if args.workload == "service":
+        return run_service(args, rank, world, local)
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -371,6 +377,313 @@ def main():
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 10 * args.steps,
                 "clocks": clk, "plan": {k: info[k] for k in ("N", "M", "J", "n_phi", "n_low", "n_points")},
                 "kernel_source_hash": kernel_source_hash()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ inverse workload
+
+INV_STAGES = ["theta_inv", "modes_inv", "rings_inv", "cols_inv", "rows_inv", "finish_inv"]
+INV_METRIC = "A^-1 applications/s at n=512 FP32 (Algorithm 3, <=1e-5 rel L2 vs FP64 oracle)"
+
+
+def inverse_stage_flops(info, B, n=N_IMG, n_det=N_DET, n_t=N_T):
+    """Algorithmic flops per launch of each inverse stage (5 L log2 L per complex FFT; the
+    Cartesian gather counts 40 flops per node inside the cut-off disk)."""
+    N, M, J, K, nphi = info["N"], info["M"], info["J"], info["K"], info["n_phi"]
+    fft = lambda L: 5.0 * L * math.log2(L)
+    nodes = math.pi * (J * info["dlam"] / info["dxi"]) ** 2 / 2
+    return {"theta_inv": B * ((n_t + 1) // 2) * fft(n_det), "modes_inv": B * (K + 1) * fft(2 * M),
+            "rings_inv": B * (J * fft(nphi) + 8.0 * (K + 1) * J),
+            "cols_inv": B * ((N // 2) * fft(N) + 40.0 * nodes), "rows_inv": B * ((n + 1) // 2) * fft(N),
+            "finish_inv": B * 2.0 * n * n}
+
+
+def time_oracle_inverse(seed=0):
+    import numpy as np
+    from oracle import tat_oracle as O
+    from tat_inputs import random_sinogram
+    P = O.OraclePlan(N_IMG, N_DET, N_T, T=T_WIN, support_radius=RSUP)
+    g = random_sinogram(N_DET, N_T, seed).astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    O.inverse(P, g)
+    return time.perf_counter() - t0
+
+
+def run_inverse(args, rank, world, local):
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t = statistics.median(time_oracle_inverse(s) for s in range(max(1, min(args.steps, 3))))
+        line = {"impl": "reference", "metric": INV_METRIC, "value": 1.0 / t, "unit": "inverses/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": 0, "ms_per_step": 1e3 * t,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": inverse_config(args.batch),
+                "cpu_baseline": {"value": 1.0 / t, "unit": "inverses/s", "cores": cpu_threads(), "kind": "oracle",
+                                 "sample": "one FP64 oracle A^-1 of one n=512 sinogram per step"},
+                "e2e": {"value": 1.0 / t, "unit": "inverses/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_24687_gb300 as pkg
+    from tat_inputs import add_noise, phantom_batch
+
+    B = args.batch
+    op = pkg.TatOperator(N_IMG, N_DET, N_T, T=T_WIN, support_radius=RSUP, device=dev)
+    info = op.info
+    fh = phantom_batch(N_IMG, B, seed0=rank * B).astype(np.float32)
+    gclean = op.forward(torch.tensor(fh, device=dev)).cpu().numpy()
+    gh = np.stack([add_noise(gclean[b], 0.01, 9000 + rank * B + b) for b in range(B)]).astype(np.float32)
+    g = torch.tensor(gh, device=dev)
+    f = torch.empty((B, N_IMG, N_IMG), device=dev)
+    ws = op.workspace(B)
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    fs, gs = N_IMG * N_IMG, N_DET * N_T
+
+    def step():
+        pkg.tat_inverse_batched(op.plan, B, g.data_ptr(), gs, f.data_ptr(), fs, ws.data_ptr(), sptr)
+
+    def timed(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / reps
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms = timed(step, args.steps)
+    clk = clocks.stop()
+    value = B * world / (ms / 1e3)
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(5)]
+    for row in evs:
+        for e in row:
+            e.record(stream)
+    torch.cuda.synchronize()
+    for row in evs:
+        pkg.tat_debug_inverse_batched_timed(op.plan, B, g.data_ptr(), gs, f.data_ptr(), fs, ws.data_ptr(), sptr,
+                                            [e.cuda_event for e in row])
+    torch.cuda.synchronize()
+    stage_ms = {name: statistics.mean(r[i].elapsed_time(r[i + 1]) for r in evs) for i, name in enumerate(INV_STAGES)}
+    flops = inverse_stage_flops(info, B)
+    dom = max(stage_ms, key=stage_ms.get)
+    peak_alu = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops[dom] / (stage_ms[dom] / 1e3) / 1e12
+    kname = {"theta_inv": "k_theta_adj", "modes_inv": "k_modes_inv", "rings_inv": "k_rings_adj<INV>",
+             "cols_inv": "k_cols_inv", "rows_inv": "k_rows_inv", "finish_inv": "k_inv_finish"}
+    roofline = {"bound": "alu", "kernel": kname[dom], "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
+                "frac": achieved / peak_alu, "traffic": traffic_for(kname[dom], "inverse_n512_b32"),
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (FP32 FMA, non-tensor)",
+                "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+                "stage_tflops": {k: round(flops[k] / (stage_ms[k] / 1e3) / 1e12, 3) for k in stage_ms}}
+    peaks = measured_peaks()
+    hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
+    io = 4 * N_IMG * N_IMG + 4 * N_DET * N_T
+    hbm = {"compulsory_bytes_per_inverse": io, "achieved_gbs": value / world * io / 1e9, "peak_gbs": hbm_peak,
+           "peak_source": "measured" if peaks else "fallback"}
+    hbm["frac"] = hbm["achieved_gbs"] / hbm_peak
+
+    g_pin = torch.from_numpy(gh).pin_memory()
+    out_pin = torch.empty((B, N_IMG, N_IMG), dtype=torch.float32).pin_memory()
+    gdev = torch.empty_like(g)
+
+    def step_e2e():
+        gdev.copy_(g_pin, non_blocking=True)
+        pkg.tat_inverse_batched(op.plan, B, gdev.data_ptr(), gs, f.data_ptr(), fs, ws.data_ptr(), sptr)
+        out_pin.copy_(f, non_blocking=True)
+    step_e2e()
+    ems = timed(step_e2e, max(3, min(args.steps, 10)))
+    e2e = {"value": B * world / (ems / 1e3), "unit": "inverses/s", "h2d_bytes_per_step": gh.nbytes,
+           "d2h_bytes_per_step": out_pin.numel() * 4}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t = time_oracle_inverse(0)
+        cpu = {"value": 1.0 / t, "unit": "inverses/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": "one n=512 sinogram through the FP64 numpy oracle of Algorithm 3"}
+    if rank == 0:
+        line = {"metric": INV_METRIC, "value": value, "unit": "inverses/s", "n_gpus": world, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic (seeded random-ellipse phantoms, g = A f + 1 % noise)",
+                "config": inverse_config(B), "roofline": roofline, "hbm_roofline": hbm, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": 6 * args.steps, "clocks": clk,
+                "kernel_source_hash": kernel_source_hash()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def inverse_config(batch):
+    return {"workload": f"A^-1 (Algorithm 3), n={N_IMG}, n_det={N_DET}, n_t={N_T}, T={T_WIN}, B={batch} per GPU",
+            "n": N_IMG, "n_det": N_DET, "n_t": N_T, "T": T_WIN, "support_radius": RSUP, "batch_per_gpu": batch,
+            "l2": "inputs exceed L2 (batch data 134 MB), no flush"}
+
+
+# ------------------------------------------------------------------ service workload
+
+SVC_REQ, SVC_SIZES = 64, (128, 256, 512, 1024)
+SVC_METRIC = "requests/s, 64 mixed-size A requests (n in {128,256,512,1024}, n_det=n_t=2n), with p50/p99 latency"
+
+
+def service_requests(seed=0):
+    """Seeded request mix: n ~ U{128, 256, 512, 1024}, n_det = n_t = 2n, one A per request."""
+    from tat_inputs import uniform
+    u = uniform(seed + 4242, SVC_REQ)
+    return [SVC_SIZES[min(int(x * len(SVC_SIZES)), len(SVC_SIZES) - 1)] for x in u]
+
+
+def service_config(sizes):
+    counts = {n: sizes.count(n) for n in SVC_SIZES}
+    return {"workload": f"{SVC_REQ} requests of A, n ~ U{{128,256,512,1024}} (seeded), n_det=n_t=2n, T=2",
+            "requests_per_size": counts, "arrival": "all requests queued at t=0, one flush",
+            "max_batch": 32, "graphs": True, "l2": "inputs and working set exceed L2, no flush"}
+
+
+def run_service(args, rank, world, local):
+    sizes = service_requests(rank)
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import numpy as np
+        from oracle import tat_oracle as O
+        from tat_inputs import ellipse_phantom
+        n = 128
+        P = O.OraclePlan(n, 2 * n, 2 * n, T=T_WIN, support_radius=RSUP)
+        f = ellipse_phantom(n, 0)
+        t0 = time.perf_counter()
+        O.forward(P, f)
+        t128 = time.perf_counter() - t0
+        # scale by the O(n^2 log n) cost of each request's size
+        cost = sum((m / 128.0) ** 2 * math.log2(m) / math.log2(128) for m in sizes)
+        t = t128 * cost
+        value = SVC_REQ / t
+        line = {"impl": "reference", "metric": SVC_METRIC, "value": value, "unit": "requests/s",
+                "n_gpus": args.gpus, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * t, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": service_config(sizes),
+                "cpu_baseline": {"value": value, "unit": "requests/s", "cores": cpu_threads(), "kind": "oracle",
+                                 "sample": "one n=128 oracle A, scaled by n^2 log n to the request mix"},
+                "e2e": {"value": value, "unit": "requests/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_24687_gb300 as pkg
+    from tat_inputs import ellipse_phantom
+
+    xs = [torch.tensor(ellipse_phantom(n, 100 * rank + i).astype(np.float32), device=dev) for i, n in enumerate(sizes)]
+    outs = [torch.empty((2 * n, 2 * n), device=dev) for n in sizes]
+    descs = {n: pkg.TatService.desc(n, 2 * n, 2 * n, T=T_WIN, support_radius=RSUP) for n in SVC_SIZES}
+    svc = pkg.TatService(memory_budget=8 << 30, max_batch=32, use_graphs=True)
+
+    def round_():
+        ids = [svc.submit(descs[n], "forward", x, o) for n, x, o in zip(sizes, xs, outs)]
+        svc.flush()
+        svc.synchronize()
+        return ids
+
+    for _ in range(max(args.warmup, 3)):
+        round_()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    lat = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ids = round_()
+        lat += [svc.latency(i)[0] for i in ids]
+    wall = (time.perf_counter() - t0) / args.steps
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([wall], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        wall = float(t.item())
+    value = SVC_REQ * world / wall
+    st = svc.stats()
+
+    # one request at a time through the same runtime (no batching across requests)
+    solo = pkg.TatService(memory_budget=2 << 30, max_batch=1, use_graphs=True)
+    for n, x, o in zip(sizes, xs, outs):
+        solo.submit(descs[n], "forward", x, o)
+    solo.flush()
+    solo.synchronize()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    solo_lat = []
+    for n, x, o in zip(sizes, xs, outs):
+        rid = solo.submit(descs[n], "forward", x, o)
+        solo.flush()
+        solo.synchronize()
+        solo_lat.append(solo.latency(rid)[0])
+    solo_wall = time.perf_counter() - t1
+    solo.close()
+
+    # end to end: host (pinned) inputs copied in and results copied out inside the timed region
+    pins = [x.cpu().pin_memory() for x in xs]
+    opins = [torch.empty(o.shape, dtype=torch.float32).pin_memory() for o in outs]
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    for _ in range(max(1, min(args.steps, 3))):
+        for p, x in zip(pins, xs):
+            x.copy_(p, non_blocking=True)
+        torch.cuda.synchronize()
+        round_()
+        for o, op_ in zip(outs, opins):
+            op_.copy_(o, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_wall = (time.perf_counter() - t2) / max(1, min(args.steps, 3))
+    svc.close()
+    lat_np = np.array(lat)
+    if rank == 0:
+        line = {"metric": SVC_METRIC, "value": value, "unit": "requests/s", "n_gpus": world, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * wall, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (random-ellipse phantoms)",
+                "config": service_config(sizes),
+                "latency_ms": {"p50": float(np.percentile(lat_np, 50)), "p99": float(np.percentile(lat_np, 99)),
+                               "max": float(lat_np.max()), "samples": int(lat_np.size),
+                               "timing": "host clock, submission to completion callback"},
+                "one_at_a_time": {"requests_per_s": SVC_REQ / solo_wall,
+                                  "p50_ms": float(np.percentile(solo_lat, 50)),
+                                  "p99_ms": float(np.percentile(solo_lat, 99))},
+                "service_stats": st,
+                "e2e": {"value": SVC_REQ * world / e2e_wall, "unit": "requests/s",
+                        "h2d_bytes_per_step": int(sum(4 * n * n for n in sizes)),
+                        "d2h_bytes_per_step": int(sum(4 * 4 * n * n for n in sizes))},
+                "roofline": None, "cpu_baseline": None,
+                "gpu_launches": 5 * st["launches"] // max(1, args.steps + max(args.warmup, 3)) * args.steps,
+                "clocks": clk, "kernel_source_hash": kernel_source_hash()}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -1,0 +1,108 @@
+/*
+ * tat_service.h -- runtime around the operators of tat.h for many problems of
+ * mixed sizes (serving, and solvers that call A / A* / A^{-1} on a stream of
+ * requests).  The paper gives the cost structure that makes batching pay
+ * (Section 3.3: every stage is a set of independent 1-D transforms per image,
+ * O(n^2 log n) per image, plans precomputed once per geometry); the service
+ * adds:
+ *
+ *  - a plan cache per problem descriptor (the Bessel table and stencils are
+ *    built once per geometry, as Section 3.1 recommends);
+ *  - batching: pending requests with the same descriptor and operation are
+ *    launched together, up to max_batch images per launch;
+ *  - admission by device memory: every (problem, operation) pair owns a
+ *    staging slot (inputs, outputs, workspace) carved from one device arena
+ *    of memory_budget bytes; when a slot does not fit, idle slots are evicted
+ *    (least recently used first) and then the batch cap of the new slot is
+ *    halved until it fits; a request that fits at no batch size completes
+ *    with TAT_ERR_OOM;
+ *  - one CUDA stream per (problem, operation) pair, so different sizes run
+ *    concurrently, and one CUDA graph per (problem, operation, batch) replayed
+ *    for every later launch of that shape;
+ *  - an autotuner for the launch shapes that the kernels take at run time.
+ *
+ * Pointers passed to tat_service_submit are DEVICE pointers owned by the
+ * caller; they must stay valid, and the output must not be read, until the
+ * request has completed (tat_service_synchronize).  Inputs are copied into the
+ * slot on the slot's stream after tat_service_flush, so the caller must not
+ * modify them before then either.  A service is used from one host thread;
+ * completion times are recorded from CUDA host callbacks.
+ */
+#ifndef TAT_SERVICE_H_
+#define TAT_SERVICE_H_
+
+#include <stddef.h>
+
+#include "tat.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tat_service_s* tat_service_t;
+
+typedef enum { TAT_OP_FORWARD = 0, TAT_OP_ADJOINT = 1, TAT_OP_INVERSE = 2 } tat_op;
+
+typedef struct {
+  size_t memory_budget; /* bytes of device memory for all staging slots (one arena) */
+  int max_batch;        /* images per launch and per (problem, operation) pair, >= 1 */
+  int use_graphs;       /* 1: capture and replay one CUDA graph per (problem, operation, batch) */
+  int autotune;         /* 1: run tat_plan_autotune on each new plan at its slot's batch size */
+} tat_service_config;
+
+typedef struct {
+  long long requests;   /* submitted */
+  long long completed;  /* completed (including failed) */
+  long long launches;   /* batched operator launches */
+  long long graph_launches;
+  long long evictions;  /* slots evicted to admit others */
+  int plans;            /* plans in the cache */
+  int slots;            /* slots resident now */
+  size_t arena_bytes;   /* size of the arena */
+  size_t peak_bytes;    /* most arena bytes held by slots at once */
+} tat_service_stats;
+
+/* Defaults: 8 GiB budget, max_batch 32, graphs on, autotune off. */
+tat_status tat_service_config_default(tat_service_config* cfg);
+
+/* Creates a service on the current device and allocates its arena.
+ * TAT_ERR_OOM if the arena cannot be allocated. */
+tat_status tat_service_create(tat_service_t* svc, const tat_service_config* cfg);
+tat_status tat_service_destroy(tat_service_t svc);
+
+/* Queues op(in) -> out for the problem `desc` (validated on the host; the
+ * plan is built at the first flush that needs it).  in/out sizes: n*n floats
+ * for images, n_det*n_t floats for data.  *id receives the request's index
+ * (0, 1, 2, ... in submission order). */
+tat_status tat_service_submit(tat_service_t svc, const tat_plan_desc* desc, tat_op op, const float* in,
+                              float* out, long long* id);
+
+/* Launches every queued request (asynchronously) and returns. */
+tat_status tat_service_flush(tat_service_t svc);
+
+/* Waits for all launched work. */
+tat_status tat_service_synchronize(tat_service_t svc);
+
+/* Host time in ms from a request's submission to its completion, and its
+ * status (TAT_ERR_INVALID_ARG if the id is unknown or it has not completed). */
+tat_status tat_service_latency(tat_service_t svc, long long id, double* ms, tat_status* status);
+
+tat_status tat_service_get_stats(tat_service_t svc, tat_service_stats* stats);
+
+/* Times the launch shapes the kernels take at run time -- column strips of
+ * 2, 4, 8, 16, 32 half-plane columns per CTA in the column stages and 1, 2, 4
+ * row pairs per CTA in the row stages (those within the device limits) -- on
+ * one A then one A* of `batch` images at f (device, batch*n*n floats, output
+ * of A* written to f_out) with g (batch*n_det*n_t floats) and the workspace
+ * for `batch`, and keeps the fastest for every later call on this plan.  The
+ * shapes only regroup work: results are unchanged (up to the rounding order
+ * of the adjoint's shared-memory atomics).  Synchronises `stream`.  *ms_best
+ * (optional) receives the chosen shape's time for the pair, *strip and
+ * *row_pairs (optional) the chosen knobs. */
+tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, float* f_out, void* workspace,
+                             tat_stream_t stream, double* ms_best, int* strip, int* row_pairs);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TAT_SERVICE_H_ */

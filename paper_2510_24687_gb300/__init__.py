@@ -23,9 +23,14 @@ from . import autograd, solvers  # noqa: E402
 from .autograd import A, Astar  # noqa: E402
 from .solvers import TatSolver, nnls_unrolled, pdhg_steps, power_norm_sq, tv_unrolled  # noqa: E402
 from .binding import tat_debug_inverse_batched_timed, tat_inverse, tat_inverse_batched  # noqa: E402
+from .binding import (TatService, tat_plan_autotune, tat_service_config_default, tat_service_create,  # noqa: E402
+                      tat_service_destroy, tat_service_flush, tat_service_get_stats, tat_service_latency,
+                      tat_service_submit, tat_service_synchronize)
 from .binding import (tat_axpby_clamp, tat_axpby_clamp_backward, tat_pd_dual_data, tat_tv_dual,  # noqa: E402
                       tat_tv_dual_backward, tat_tv_primal, tat_tv_primal_backward)
 
-__all__ += ["tat_inverse", "tat_inverse_batched", "tat_debug_inverse_batched_timed", "autograd", "solvers", "A", "Astar", "TatSolver", "nnls_unrolled", "pdhg_steps", "power_norm_sq",
+__all__ += ["TatService", "tat_plan_autotune", "tat_service_config_default", "tat_service_create",
+            "tat_service_destroy", "tat_service_flush", "tat_service_get_stats", "tat_service_latency",
+            "tat_service_submit", "tat_service_synchronize", "tat_inverse", "tat_inverse_batched", "tat_debug_inverse_batched_timed", "autograd", "solvers", "A", "Astar", "TatSolver", "nnls_unrolled", "pdhg_steps", "power_norm_sq",
             "tv_unrolled", "tat_axpby_clamp", "tat_axpby_clamp_backward", "tat_pd_dual_data", "tat_tv_dual",
             "tat_tv_dual_backward", "tat_tv_primal", "tat_tv_primal_backward"]

@@ -1,4 +1,5 @@
-"""ctypes binding of libtat (include/tat.h, include/tat_debug.h, include/tat_solvers.h).
+"""ctypes binding of libtat (include/tat.h, include/tat_debug.h, include/tat_solvers.h,
+include/tat_service.h).
 
 Argument marshalling only: every step of A and A* runs in the CUDA kernels of
 libtat.  Functions keep the C names.  Device buffers are passed as integer
@@ -44,6 +45,22 @@ class tat_plan_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class tat_service_config(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_size_t), ("max_batch", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
+
+
+class tat_service_stats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("launches", ctypes.c_longlong),
+                ("graph_launches", ctypes.c_longlong), ("evictions", ctypes.c_longlong), ("plans", ctypes.c_int),
+                ("slots", ctypes.c_int), ("arena_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+TAT_OP_FORWARD, TAT_OP_ADJOINT, TAT_OP_INVERSE = 0, 1, 2
+
 _lib = None
 _P = ctypes.c_void_p
 _I = ctypes.c_int
@@ -84,6 +101,16 @@ def load() -> ctypes.CDLL:
         "tat_debug_inverse_batched_timed": (_I, [_P, _I, _P, _LL, _P, _LL, _P, _P, ctypes.POINTER(_P)]),
         "tat_debug_forward_batched_timed": (_I, [_P, _I, _P, _LL, _P, _LL, _P, _P, ctypes.POINTER(_P)]),
         "tat_debug_adjoint_batched_timed": (_I, [_P, _I, _P, _LL, _P, _LL, _P, _P, ctypes.POINTER(_P)]),
+        "tat_service_config_default": (_I, [ctypes.POINTER(tat_service_config)]),
+        "tat_service_create": (_I, [ctypes.POINTER(_P), ctypes.POINTER(tat_service_config)]),
+        "tat_service_destroy": (_I, [_P]),
+        "tat_service_submit": (_I, [_P, ctypes.POINTER(tat_plan_desc), _I, _P, _P, ctypes.POINTER(_LL)]),
+        "tat_service_flush": (_I, [_P]),
+        "tat_service_synchronize": (_I, [_P]),
+        "tat_service_latency": (_I, [_P, _LL, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
+        "tat_service_get_stats": (_I, [_P, ctypes.POINTER(tat_service_stats)]),
+        "tat_plan_autotune": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_I),
+                                   ctypes.POINTER(_I)]),
         "tat_axpby_clamp": (_I, [_LL, _F, _P, _F, _P, _F, _P, _LL, _P, _P]),
         "tat_axpby_clamp_backward": (_I, [_LL, _P, _F, _P, _LL, _P, _F, _P, _F, _P, _P]),
         "tat_pd_dual_data": (_I, [_LL, _F, _P, _P, _P, _P, _P]),
@@ -256,6 +283,57 @@ def tat_tv_primal_backward(batch, n, h_eff, tau, f_out_ptr, mask_ptr, grad_f_out
                                          grad_p_ptr or None, stream or None), "tat_tv_primal_backward")
 
 
+def tat_plan_autotune(plan, batch, f_ptr, g_ptr, f_out_ptr, ws_ptr, stream=0):
+    """Times the runtime launch shapes on one A + A* of `batch` images; returns (ms, strip, row_pairs)."""
+    ms, strip, rp = _D(0), _I(0), _I(0)
+    _check(load().tat_plan_autotune(plan, batch, f_ptr, g_ptr, f_out_ptr, ws_ptr, stream or None, ctypes.byref(ms),
+                                    ctypes.byref(strip), ctypes.byref(rp)), "tat_plan_autotune")
+    return ms.value, strip.value, rp.value
+
+
+def tat_service_config_default() -> tat_service_config:
+    c = tat_service_config()
+    _check(load().tat_service_config_default(ctypes.byref(c)), "tat_service_config_default")
+    return c
+
+
+def tat_service_create(cfg: tat_service_config) -> int:
+    h = _P()
+    _check(load().tat_service_create(ctypes.byref(h), ctypes.byref(cfg)), "tat_service_create")
+    return h.value
+
+
+def tat_service_destroy(svc):
+    _check(load().tat_service_destroy(svc), "tat_service_destroy")
+
+
+def tat_service_submit(svc, desc: tat_plan_desc, op: int, in_ptr, out_ptr) -> int:
+    rid = _LL(0)
+    _check(load().tat_service_submit(svc, ctypes.byref(desc), op, in_ptr, out_ptr, ctypes.byref(rid)),
+           "tat_service_submit")
+    return rid.value
+
+
+def tat_service_flush(svc):
+    _check(load().tat_service_flush(svc), "tat_service_flush")
+
+
+def tat_service_synchronize(svc):
+    _check(load().tat_service_synchronize(svc), "tat_service_synchronize")
+
+
+def tat_service_latency(svc, rid):
+    ms, st = _D(0), _I(0)
+    _check(load().tat_service_latency(svc, rid, ctypes.byref(ms), ctypes.byref(st)), "tat_service_latency")
+    return ms.value, st.value
+
+
+def tat_service_get_stats(svc) -> dict:
+    st = tat_service_stats()
+    _check(load().tat_service_get_stats(svc, ctypes.byref(st)), "tat_service_get_stats")
+    return st.as_dict()
+
+
 def tat_status_string(status: int) -> str:
     return load().tat_status_string(status).decode()
 
@@ -369,6 +447,66 @@ class TatOperator:
         if getattr(self, "plan", None):
             tat_plan_destroy(self.plan)
             self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class TatService:
+    """Mixed-size request runtime (include/tat_service.h) on the current CUDA device.
+
+    ``submit(desc_kw, op, x, out)`` queues op(x) -> out for the problem described by
+    ``desc_kw`` (n, n_det, n_t and optional tat_plan_desc fields); x and out are
+    contiguous float32 CUDA tensors that must stay alive until ``synchronize``.
+    """
+
+    OPS = {"forward": TAT_OP_FORWARD, "adjoint": TAT_OP_ADJOINT, "inverse": TAT_OP_INVERSE}
+
+    def __init__(self, memory_budget=None, max_batch=None, use_graphs=True, autotune=False):
+        cfg = tat_service_config_default()
+        if memory_budget is not None:
+            cfg.memory_budget = int(memory_budget)
+        if max_batch is not None:
+            cfg.max_batch = int(max_batch)
+        cfg.use_graphs = 1 if use_graphs else 0
+        cfg.autotune = 1 if autotune else 0
+        self.handle = tat_service_create(cfg)
+        self._keep = []
+
+    @staticmethod
+    def desc(n, n_det, n_t, c=1.0, R=1.0, T=2.0, **kw):
+        d = tat_plan_desc_default(n, n_det, n_t, c, R, T)
+        for k, v in kw.items():
+            setattr(d, k, v)
+        return d
+
+    def submit(self, desc, op, x, out):
+        for t in (x, out):
+            if not (t.is_cuda and t.is_contiguous() and t.dtype.itemsize == 4):
+                raise ValueError("x and out must be contiguous float32 CUDA tensors")
+        self._keep.append((x, out))
+        return tat_service_submit(self.handle, desc, self.OPS[op], x.data_ptr(), out.data_ptr())
+
+    def flush(self):
+        tat_service_flush(self.handle)
+
+    def synchronize(self):
+        tat_service_synchronize(self.handle)
+        self._keep = []
+
+    def latency(self, rid):
+        return tat_service_latency(self.handle, rid)
+
+    def stats(self):
+        return tat_service_get_stats(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            tat_service_destroy(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:

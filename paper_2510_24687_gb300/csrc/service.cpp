@@ -1,0 +1,481 @@
+// Runtime for streams of mixed-size requests (include/tat_service.h): plan
+// cache, batching per (problem, operation), one device arena with admission
+// and LRU eviction of staging slots, a stream per slot, CUDA graphs per
+// (slot, batch), and the launch-shape autotuner.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "plan.hpp"
+#include "tat_service.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+tat_status cuda_ok(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return TAT_OK;
+  fprintf(stderr, "tat service: %s: %s\n", what, cudaGetErrorString(e));
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? TAT_ERR_OOM : TAT_ERR_CUDA;
+}
+
+struct Request {
+  long long id;
+  const float* in;
+  float* out;
+  Clock::time_point submitted, done;
+  tat_status status = TAT_OK;
+  bool completed = false;
+};
+
+struct Slot;
+
+// First-fit allocator over the arena (offsets only; the arena is one cudaMalloc).
+class Arena {
+ public:
+  size_t size = 0;
+  char* base = nullptr;
+  std::map<size_t, size_t> used;  // offset -> bytes
+  size_t held = 0, peak = 0;
+
+  bool alloc(size_t bytes, size_t* off) {
+    size_t cur = 0;
+    for (const auto& u : used) {
+      if (u.first - cur >= bytes) break;
+      cur = align_up(u.first + u.second);
+    }
+    if (cur + bytes > size) return false;
+    used[cur] = bytes;
+    held += bytes;
+    peak = std::max(peak, held);
+    *off = cur;
+    return true;
+  }
+  void release(size_t off) {
+    auto it = used.find(off);
+    if (it == used.end()) return;
+    held -= it->second;
+    used.erase(it);
+  }
+};
+
+struct Slot {
+  std::string key;
+  tat_plan_t plan = nullptr;
+  tat_op op = TAT_OP_FORWARD;
+  cudaStream_t stream = nullptr;
+  int cap = 0;                        // images per launch (0: not resident)
+  size_t off = 0, bytes = 0;          // arena region
+  float* in = nullptr;
+  float* out = nullptr;
+  void* ws = nullptr;
+  size_t in_elems = 0, out_elems = 0;
+  std::map<int, cudaGraphExec_t> graphs;  // batch -> executable graph
+  std::vector<long long> pending;
+  unsigned long long last_use = 0;
+  bool tuned = false;
+};
+
+struct Completion {
+  tat_service_s* svc;
+  std::vector<long long> ids;
+};
+
+}  // namespace
+
+struct tat_service_s {
+  tat_service_config cfg;
+  int device = 0;
+  Arena arena;
+  std::map<std::string, tat_plan_t> plans;  // descriptor bytes -> plan
+  std::map<std::string, std::unique_ptr<Slot>> slots;
+  std::deque<Request> requests;
+  std::mutex mu;                            // guards request completion fields
+  unsigned long long tick = 0;
+  tat_service_stats st{};
+};
+
+namespace {
+
+std::string desc_key(const tat_plan_desc& d) { return std::string(reinterpret_cast<const char*>(&d), sizeof d); }
+
+void CUDART_CB on_complete(void* p) {
+  std::unique_ptr<Completion> c(static_cast<Completion*>(p));
+  const Clock::time_point now = Clock::now();
+  std::lock_guard<std::mutex> lock(c->svc->mu);
+  for (long long id : c->ids) {
+    Request& r = c->svc->requests[(size_t)id];
+    r.done = now;
+    r.completed = true;
+  }
+  c->svc->st.completed += (long long)c->ids.size();
+}
+
+void fail_now(tat_service_s* S, const std::vector<long long>& ids, tat_status why) {
+  const Clock::time_point now = Clock::now();
+  std::lock_guard<std::mutex> lock(S->mu);
+  for (long long id : ids) {
+    Request& r = S->requests[(size_t)id];
+    r.status = why;
+    r.done = now;
+    r.completed = true;
+  }
+  S->st.completed += (long long)ids.size();
+}
+
+tat_status launch_op(tat_plan_t plan, tat_op op, int b, const float* in, long long in_s, float* out, long long out_s,
+                     void* ws, cudaStream_t st) {
+  switch (op) {
+    case TAT_OP_FORWARD: return tat_forward_batched(plan, b, in, in_s, out, out_s, ws, st);
+    case TAT_OP_ADJOINT: return tat_adjoint_batched(plan, b, in, in_s, out, out_s, ws, st);
+    case TAT_OP_INVERSE: return tat_inverse_batched(plan, b, in, in_s, out, out_s, ws, st);
+  }
+  return TAT_ERR_INVALID_ARG;
+}
+
+size_t slot_bytes(const Slot& s, int cap) {
+  return align_up(s.in_elems * sizeof(float) * cap) + align_up(s.out_elems * sizeof(float) * cap) +
+         align_up(tat_workspace_size(s.plan, cap));
+}
+
+void drop_graphs(Slot& s) {
+  for (auto& g : s.graphs) cudaGraphExecDestroy(g.second);
+  s.graphs.clear();
+}
+
+void evict(tat_service_s* S, Slot& s) {
+  cudaStreamSynchronize(s.stream);
+  drop_graphs(s);
+  S->arena.release(s.off);
+  s.cap = 0;
+  s.in = s.out = nullptr;
+  s.ws = nullptr;
+  ++S->st.evictions;
+}
+
+// Makes `s` resident with the largest batch cap <= max_batch that fits,
+// evicting idle slots (least recently used first) when needed.
+tat_status admit(tat_service_s* S, Slot& s) {
+  if (s.cap > 0) return TAT_OK;
+  for (int cap = S->cfg.max_batch; cap >= 1; cap /= 2) {
+    const size_t need = slot_bytes(s, cap);
+    size_t off = 0;
+    bool ok = S->arena.alloc(need, &off);
+    while (!ok) {
+      Slot* victim = nullptr;
+      for (auto& kv : S->slots) {
+        Slot& o = *kv.second;
+        if (&o == &s || o.cap == 0 || !o.pending.empty()) continue;
+        if (!victim || o.last_use < victim->last_use) victim = &o;
+      }
+      if (!victim) break;
+      evict(S, *victim);
+      ok = S->arena.alloc(need, &off);
+    }
+    if (!ok) continue;
+    s.off = off;
+    s.bytes = need;
+    s.cap = cap;
+    char* p = S->arena.base + off;
+    s.in = reinterpret_cast<float*>(p);
+    p += align_up(s.in_elems * sizeof(float) * cap);
+    s.out = reinterpret_cast<float*>(p);
+    p += align_up(s.out_elems * sizeof(float) * cap);
+    s.ws = p;
+    return TAT_OK;
+  }
+  return TAT_ERR_OOM;
+}
+
+tat_status ensure_plan(tat_service_s* S, const tat_plan_desc& d, tat_plan_t* out) {
+  const std::string k = desc_key(d);
+  auto it = S->plans.find(k);
+  if (it != S->plans.end()) {
+    *out = it->second;
+    return TAT_OK;
+  }
+  tat_plan_t p = nullptr;
+  const tat_status s = tat_plan_create_ex(&p, &d);
+  if (s != TAT_OK) return s;
+  S->plans[k] = p;
+  S->st.plans = (int)S->plans.size();
+  *out = p;
+  return TAT_OK;
+}
+
+tat_status run_chunk(tat_service_s* S, Slot& s, const std::vector<long long>& ids) {
+  const int b = (int)ids.size();
+  for (int i = 0; i < b; ++i) {
+    const Request& r = S->requests[(size_t)ids[i]];
+    tat_status e = cuda_ok(cudaMemcpyAsync(s.in + (size_t)i * s.in_elems, r.in, s.in_elems * sizeof(float),
+                                           cudaMemcpyDeviceToDevice, s.stream),
+                           "staging copy");
+    if (e != TAT_OK) return e;
+  }
+  auto g = s.graphs.find(b);
+  if (g != s.graphs.end()) {
+    tat_status e = cuda_ok(cudaGraphLaunch(g->second, s.stream), "graph launch");
+    if (e != TAT_OK) return e;
+    ++S->st.graph_launches;
+  } else {
+    tat_status e = launch_op(s.plan, s.op, b, s.in, (long long)s.in_elems, s.out, (long long)s.out_elems, s.ws,
+                             s.stream);
+    if (e != TAT_OK) return e;
+    if (S->cfg.use_graphs) {
+      // capture the same launch for the next chunk of this size (capture runs nothing)
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      if (cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const tat_status le = launch_op(s.plan, s.op, b, s.in, (long long)s.in_elems, s.out,
+                                        (long long)s.out_elems, s.ws, s.stream);
+        const cudaError_t ce = cudaStreamEndCapture(s.stream, &graph);
+        if (le == TAT_OK && ce == cudaSuccess && graph &&
+            cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+          s.graphs[b] = exec;
+        }
+        if (graph) cudaGraphDestroy(graph);
+      }
+      cudaGetLastError();
+    }
+  }
+  ++S->st.launches;
+  for (int i = 0; i < b; ++i) {
+    const Request& r = S->requests[(size_t)ids[i]];
+    tat_status e = cuda_ok(cudaMemcpyAsync(r.out, s.out + (size_t)i * s.out_elems, s.out_elems * sizeof(float),
+                                           cudaMemcpyDeviceToDevice, s.stream),
+                           "result copy");
+    if (e != TAT_OK) return e;
+  }
+  Completion* c = new Completion{S, ids};
+  const cudaError_t e = cudaLaunchHostFunc(s.stream, on_complete, c);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_ok(e, "host callback");
+  }
+  return TAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tat_status tat_service_config_default(tat_service_config* cfg) {
+  if (!cfg) return TAT_ERR_INVALID_ARG;
+  cfg->memory_budget = (size_t)8 << 30;
+  cfg->max_batch = 32;
+  cfg->use_graphs = 1;
+  cfg->autotune = 0;
+  return TAT_OK;
+}
+
+tat_status tat_service_create(tat_service_t* svc, const tat_service_config* cfg) {
+  if (!svc) return TAT_ERR_INVALID_ARG;
+  *svc = nullptr;
+  if (!cfg || cfg->max_batch < 1 || cfg->memory_budget < kAlign) return TAT_ERR_INVALID_ARG;
+  auto* S = new (std::nothrow) tat_service_s();
+  if (!S) return TAT_ERR_OOM;
+  S->cfg = *cfg;
+  if (cudaGetDevice(&S->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete S;
+    return TAT_ERR_CUDA;
+  }
+  S->arena.size = cfg->memory_budget / kAlign * kAlign;
+  void* p = nullptr;
+  const tat_status e = cuda_ok(cudaMalloc(&p, S->arena.size), "arena allocation");
+  if (e != TAT_OK) {
+    delete S;
+    return e;
+  }
+  S->arena.base = static_cast<char*>(p);
+  S->st.arena_bytes = S->arena.size;
+  *svc = S;
+  return TAT_OK;
+}
+
+tat_status tat_service_destroy(tat_service_t S) {
+  if (!S) return TAT_ERR_INVALID_ARG;
+  for (auto& kv : S->slots) {
+    Slot& s = *kv.second;
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    drop_graphs(s);
+    if (s.stream) cudaStreamDestroy(s.stream);
+  }
+  for (auto& kv : S->plans) tat_plan_destroy(kv.second);
+  cudaFree(S->arena.base);
+  delete S;
+  return TAT_OK;
+}
+
+tat_status tat_service_submit(tat_service_t S, const tat_plan_desc* desc, tat_op op, const float* in, float* out,
+                              long long* id) {
+  if (!S || !desc || !in || !out || !id) return TAT_ERR_INVALID_ARG;
+  if (op != TAT_OP_FORWARD && op != TAT_OP_ADJOINT && op != TAT_OP_INVERSE) return TAT_ERR_INVALID_ARG;
+  tat_plan_info info;
+  const tat_status q = tat_plan_query(desc, &info);
+  if (q != TAT_OK) return q;
+  std::string key = desc_key(*desc);
+  key.push_back((char)op);
+  auto& slot = S->slots[key];
+  if (!slot) {
+    slot.reset(new Slot());
+    slot->key = key;
+    slot->op = op;
+    const size_t img = (size_t)desc->n * desc->n, dat = (size_t)desc->n_det * desc->n_t;
+    slot->in_elems = op == TAT_OP_FORWARD ? img : dat;
+    slot->out_elems = op == TAT_OP_FORWARD ? dat : img;
+  }
+  Request r;
+  r.id = (long long)S->requests.size();
+  r.in = in;
+  r.out = out;
+  r.submitted = Clock::now();
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->requests.push_back(r);
+  }
+  slot->pending.push_back(r.id);
+  ++S->st.requests;
+  *id = r.id;
+  return TAT_OK;
+}
+
+tat_status tat_service_flush(tat_service_t S) {
+  if (!S) return TAT_ERR_INVALID_ARG;
+  tat_status first_error = TAT_OK;
+  for (auto& kv : S->slots) {
+    Slot& s = *kv.second;
+    if (s.pending.empty()) continue;
+    s.last_use = ++S->tick;
+    tat_plan_desc d;
+    std::memcpy(&d, s.key.data(), sizeof d);
+    tat_status e = s.plan ? TAT_OK : ensure_plan(S, d, &s.plan);
+    if (e == TAT_OK && !s.stream) e = cuda_ok(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking), "stream");
+    if (e == TAT_OK) e = admit(S, s);
+    if (e == TAT_OK && S->cfg.autotune && !s.tuned && s.op != TAT_OP_INVERSE) {
+      // tune on zeroed slot buffers at the slot's batch size (the knobs belong to the plan)
+      const tat_plan_desc& pd = d;
+      const size_t img = (size_t)pd.n * pd.n, dat = (size_t)pd.n_det * pd.n_t;
+      float* fbuf = s.op == TAT_OP_FORWARD ? s.in : s.out;
+      float* gbuf = s.op == TAT_OP_FORWARD ? s.out : s.in;
+      cudaMemsetAsync(fbuf, 0, img * sizeof(float) * s.cap, s.stream);
+      cudaMemsetAsync(gbuf, 0, dat * sizeof(float) * s.cap, s.stream);
+      e = tat_plan_autotune(s.plan, s.cap, fbuf, gbuf, fbuf, s.ws, s.stream, nullptr, nullptr, nullptr);
+      drop_graphs(s);
+      s.tuned = true;
+    }
+    if (e != TAT_OK) {
+      fail_now(S, s.pending, e);
+      s.pending.clear();
+      if (first_error == TAT_OK) first_error = e;
+      continue;
+    }
+    for (size_t i = 0; i < s.pending.size(); i += (size_t)s.cap) {
+      const size_t j = std::min(s.pending.size(), i + (size_t)s.cap);
+      std::vector<long long> ids(s.pending.begin() + (long)i, s.pending.begin() + (long)j);
+      e = run_chunk(S, s, ids);
+      if (e != TAT_OK) {
+        fail_now(S, ids, e);
+        if (first_error == TAT_OK) first_error = e;
+      }
+    }
+    s.pending.clear();
+  }
+  S->st.slots = 0;
+  for (auto& kv : S->slots) S->st.slots += kv.second->cap > 0 ? 1 : 0;
+  S->st.peak_bytes = S->arena.peak;
+  return first_error;
+}
+
+tat_status tat_service_synchronize(tat_service_t S) {
+  if (!S) return TAT_ERR_INVALID_ARG;
+  tat_status r = TAT_OK;
+  for (auto& kv : S->slots)
+    if (kv.second->stream) {
+      const tat_status e = cuda_ok(cudaStreamSynchronize(kv.second->stream), "synchronize");
+      if (r == TAT_OK) r = e;
+    }
+  return r;
+}
+
+tat_status tat_service_latency(tat_service_t S, long long id, double* ms, tat_status* status) {
+  if (!S || !ms || id < 0) return TAT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(S->mu);
+  if ((size_t)id >= S->requests.size()) return TAT_ERR_INVALID_ARG;
+  const Request& r = S->requests[(size_t)id];
+  if (!r.completed) return TAT_ERR_INVALID_ARG;
+  *ms = std::chrono::duration<double, std::milli>(r.done - r.submitted).count();
+  if (status) *status = r.status;
+  return TAT_OK;
+}
+
+tat_status tat_service_get_stats(tat_service_t S, tat_service_stats* out) {
+  if (!S || !out) return TAT_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(S->mu);
+  *out = S->st;
+  out->peak_bytes = S->arena.peak;
+  return TAT_OK;
+}
+
+tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, float* f_out, void* workspace,
+                             tat_stream_t stream, double* ms_best, int* strip_out, int* rp_out) {
+  if (!plan || batch < 1 || !f || !g || !f_out || !workspace) return TAT_ERR_INVALID_ARG;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const tat::LaunchCfg base = plan->cfg;
+  const long long fs = (long long)plan->d.n * plan->d.n, gs = (long long)plan->d.n_det * plan->d.n_t;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    return TAT_ERR_CUDA;
+  }
+  tat::LaunchCfg best = base;
+  float best_ms = 1e30f;
+  tat_status err = TAT_OK;
+  for (int strip : {2, 4, 8, 16, 32}) {
+    for (int rp : {1, 2, 4}) {
+      plan->cfg = base;
+      plan->cfg.strip = strip;
+      plan->cfg.rows_pairs = rp;
+      if (rp * plan->cfg.nt_rows > 1024 || tat::validate_shapes(plan) != TAT_OK) continue;
+      float ms = 0.f;
+      for (int rep = 0; rep < 3 && err == TAT_OK; ++rep) {
+        cudaEventRecord(e0, st);
+        err = tat::launch_forward(plan, batch, f, fs, g, gs, workspace, st);
+        if (err == TAT_OK) err = tat::launch_adjoint(plan, batch, g, gs, f_out, fs, workspace, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) err = TAT_ERR_CUDA;
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        if (rep > 0) ms += t;  // first repetition is the warm-up
+      }
+      if (err != TAT_OK) break;
+      ms /= 2.f;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = plan->cfg;
+      }
+    }
+    if (err != TAT_OK) break;
+  }
+  plan->cfg = err == TAT_OK ? best : base;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != TAT_OK) return err;
+  if (ms_best) *ms_best = best_ms;
+  if (strip_out) *strip_out = best.strip;
+  if (rp_out) *rp_out = best.rows_pairs;
+  return TAT_OK;
+}
+
+}  // extern "C"

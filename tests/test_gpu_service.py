@@ -1,0 +1,128 @@
+"""GPU tests of the mixed-size request runtime (include/tat_service.h) and the
+launch-shape autotuner: results equal the direct batched calls, graphs are
+reused, admission under a tight memory budget evicts and shrinks batches and
+reports out-of-memory for a request that fits at no batch size.
+"""
+import numpy as np
+import pytest
+
+from tat_inputs import ellipse_phantom, random_sinogram
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_24687_gb300 as p
+    return p
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return t
+
+
+SIZES = [(64, 128, 128), (96, 192, 160), (128, 256, 256)]
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _requests(torch, count=12):
+    reqs = []
+    for i in range(count):
+        n, nd, nt = SIZES[i % len(SIZES)]
+        op = ("forward", "adjoint", "inverse")[(i // len(SIZES)) % 3]
+        if op == "forward":
+            x = torch.tensor(ellipse_phantom(n, i).astype(np.float32), device="cuda:0")
+            out = torch.empty((nd, nt), device="cuda:0")
+        else:
+            x = torch.tensor(random_sinogram(nd, nt, i).astype(np.float32), device="cuda:0")
+            out = torch.empty((n, n), device="cuda:0")
+        reqs.append((n, nd, nt, op, x, out))
+    return reqs
+
+
+def _direct(pkg, torch, n, nd, nt, op, x):
+    o = pkg.TatOperator(n, nd, nt, device="cuda:0", support_radius=0.9)
+    return getattr(o, op)(x).cpu().numpy()
+
+
+def test_service_matches_direct_calls_and_reuses_graphs(pkg, torch):
+    svc = pkg.TatService(memory_budget=2 << 30, max_batch=4)
+    reqs = _requests(torch)
+    for rnd in range(2):
+        ids = [svc.submit(svc.desc(n, nd, nt, support_radius=0.9), op, x, out) for n, nd, nt, op, x, out in reqs]
+        svc.flush()
+        svc.synchronize()
+        for rid, (n, nd, nt, op, x, out) in zip(ids, reqs):
+            ms, status = svc.latency(rid)
+            assert status == 0 and ms > 0
+            ref = _direct(pkg, torch, n, nd, nt, op, x)
+            if op == "forward":
+                assert np.array_equal(out.cpu().numpy(), ref)
+            else:
+                assert rel(out.cpu().numpy(), ref) <= 1e-6
+    st = svc.stats()
+    assert st["requests"] == st["completed"] == 2 * len(reqs)
+    assert st["plans"] == len(SIZES) and st["graph_launches"] > 0 and st["evictions"] == 0
+    svc.close()
+
+
+def test_admission_evicts_and_shrinks_batches(pkg, torch):
+    """A budget that holds one (n = 128, batch 2) slot at a time: slots are evicted between sizes and
+    the batch cap is halved; results stay exact."""
+    info = pkg.tat_plan_query(pkg.tat_plan_desc_default(128, 256, 256))
+    plan = pkg.tat_plan_create(128, 256, 256)
+    ws1 = pkg.tat_workspace_size(plan, 1)
+    pkg.tat_plan_destroy(plan)
+    per_image = ws1 + 4 * (128 * 128 + 256 * 256) + 1024
+    svc = pkg.TatService(memory_budget=int(2.5 * per_image), max_batch=8)
+    reqs = [r for r in _requests(torch, 9) if r[3] == "forward"] + \
+           [r for r in _requests(torch, 9) if r[3] == "adjoint"]
+    ids = [svc.submit(svc.desc(n, nd, nt, support_radius=0.9), op, x, out) for n, nd, nt, op, x, out in reqs]
+    svc.flush()
+    svc.synchronize()
+    for rid, (n, nd, nt, op, x, out) in zip(ids, reqs):
+        assert svc.latency(rid)[1] == 0
+        ref = _direct(pkg, torch, n, nd, nt, op, x)
+        assert rel(out.cpu().numpy(), ref) <= 1e-6
+    st = svc.stats()
+    assert st["evictions"] > 0 and st["peak_bytes"] <= st["arena_bytes"]
+    assert info["N"] == 1024
+    svc.close()
+
+
+def test_request_too_large_reports_oom(pkg, torch):
+    svc = pkg.TatService(memory_budget=1 << 20, max_batch=2)
+    x = torch.zeros((128, 128), device="cuda:0")
+    out = torch.empty((256, 256), device="cuda:0")
+    rid = svc.submit(svc.desc(128, 256, 256), "forward", x, out)
+    with pytest.raises(pkg.TatError):
+        svc.flush()
+    svc.synchronize()
+    assert svc.latency(rid)[1] == 3      # TAT_ERR_OOM
+    svc.close()
+
+
+def test_autotune_keeps_results(pkg, torch):
+    n, nd, nt, B = 128, 256, 256, 4
+    op = pkg.TatOperator(n, nd, nt, device="cuda:0", support_radius=0.9)
+    f = torch.tensor(np.stack([ellipse_phantom(n, 30 + b) for b in range(B)]).astype(np.float32), device="cuda:0")
+    g0 = op.forward(f).cpu().numpy()
+    a0 = op.adjoint(op.forward(f)).cpu().numpy()
+    g = torch.empty((B, nd, nt), device="cuda:0")
+    f2 = torch.empty_like(f)
+    ws = op.workspace(B)
+    s = torch.cuda.current_stream().cuda_stream
+    ms, strip, rp = pkg.tat_plan_autotune(op.plan, B, f.data_ptr(), g.data_ptr(), f2.data_ptr(), ws.data_ptr(), s)
+    assert ms > 0 and strip in (2, 4, 8, 16, 32) and rp in (1, 2, 4)
+    assert np.array_equal(op.forward(f).cpu().numpy(), g0)
+    assert rel(op.adjoint(op.forward(f)).cpu().numpy(), a0) <= 1e-6
