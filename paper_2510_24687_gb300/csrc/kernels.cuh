@@ -707,47 +707,37 @@ __device__ __forceinline__ float2 inv_polar(const DevPlan& P, const float2* __re
 
 // vhat at the Cartesian node (c, qs) of the half plane (Algorithm 3, step 5):
 // bilinear interpolation in (lambda, phi) of the polar samples, zero beyond
-// ring J + 1e-6.  lambda/dlam and the offset of phi from the grid angle phi_l0 are
-// formed in two-float arithmetic (an FP32 position is off by ~1e-4 of a cell
-// at the outer rings, which the interpolation weights would carry).
+// the cut-off.  The node's ring and angle positions come from the plan's FP64
+// quadrant table (an FP32 position would be off by ~1e-4 of a cell at the
+// outer rings, which the interpolation weights would carry); qs < 0 is the
+// mirror phi -> -phi of |qs|.  Half-circle angle cell: l' = nh/2 + phi cells.
 __device__ __forceinline__ float2 inv_node(const DevPlan& P, const float2* __restrict__ Yb, int c, int qs) {
-  const int n2 = c * c + qs * qs;
-  if (n2 == 0) return make_float2(0.f, 0.f);
-  // r = |(c, qs)| = s + ds exactly to ~1e-14 relative
-  const float n2h = (float)n2;
-  const float n2l = (float)(n2 - (int)n2h);
-  const float s = sqrtf(n2h);
-  const float ds = (fmaf(-s, s, n2h) + n2l) / (2.f * s);
-  // u = r * dxi / dlam = uh + ul
-  const float uh = s * P.inv_rho_hi;
-  const float ul = fmaf(s, P.inv_rho_hi, -uh) + fmaf(s, P.inv_rho_lo, ds * P.inv_rho_hi);
-  float jf = floorf(uh);
-  float a = (uh - jf) + ul;
-  if (a < 0.f) {
-    a += 1.f;
-    jf -= 1.f;
-  } else if (a >= 1.f) {
-    a -= 1.f;
-    jf += 1.f;
+  const int h2 = P.N >> 1;
+  const int aq = qs < 0 ? -qs : qs;
+  if (aq >= h2) return make_float2(0.f, 0.f);  // the Nyquist row lies beyond the cut-off
+  const size_t e = (size_t)c * h2 + aq;
+  const unsigned jl = __ldg(&P.inv_jl[e]);
+  const int j = (int)(jl & 0xffffu);
+  if (j == 0xffff) return make_float2(0.f, 0.f);
+  const float2 ab = __ldg(&P.inv_ab[e]);
+  const int L = (int)(jl >> 16);
+  int l0;
+  float bb;
+  if (qs >= 0) {
+    l0 = (P.nh >> 1) + L;
+    bb = ab.y;
+  } else if (ab.y > 0.f) {
+    l0 = (P.nh >> 1) - L - 1;
+    bb = 1.f - ab.y;
+  } else {
+    l0 = (P.nh >> 1) - L;
+    bb = 0.f;
   }
-  int j = (int)jf;
-  if (j >= P.J) {
-    // closed cut-off at ring J, with ties (u = J exactly on grids where dxi/dlam
-    // is rational) inside: u in [J, J + 1e-6] takes the ring-J value
-    if (j > P.J || a > 1e-6f) return make_float2(0.f, 0.f);
-    j = P.J - 1;
-    a = 1.f;
+  if (l0 >= P.nh) {  // phi = pi/2 exactly
+    l0 = P.nh - 1;
+    bb = 1.f;
   }
-  // angle: approximate cell from atan2f, exact offset from phi_l0 by
-  // sin(phi - phi_l0) = (qs cos phi_l0 - c sin phi_l0) / r with a two-float cos/sin table
-  const float qf = (float)qs, cf = (float)c;
-  const float pos = fmaf(atan2f(qf, cf), P.inv_nphi_2pi, (float)(P.nh / 2));
-  const int l0 = min(max((int)floorf(pos), 0), P.nh - 1);
-  const float2 ch = P.cs_half[l0], cl = P.cs_half_lo[l0];
-  const float t1 = qf * ch.x, t2 = cf * ch.y;
-  const float e1 = fmaf(qf, ch.x, -t1), e2 = fmaf(cf, ch.y, -t2);
-  const float num = (t1 - t2) + ((e1 - e2) + (qf * cl.x - cf * cl.y));
-  const float bb = asinf(num / (s + ds)) * P.inv_nphi_2pi;
+  const float a = ab.x;
   const float2 v00 = inv_polar(P, Yb, j, l0), v01 = inv_polar(P, Yb, j, l0 + 1);
   const float2 v10 = inv_polar(P, Yb, j + 1, l0), v11 = inv_polar(P, Yb, j + 1, l0 + 1);
   const float2 va = cadd(cscale(v00, 1.f - bb), cscale(v01, bb));
@@ -760,8 +750,10 @@ __device__ __forceinline__ float2 inv_node(const DevPlan& P, const float2* __res
 // inverse column DFT, first n rows kept -> X = V'[c][iy].  The strip-0 CTA of
 // each image also clears the image's accumulator of the constant C (`acc`, in
 // element 0 of the image's Y region: ring 0, which this kernel never reads).
+#define TAT_COLS_BOUNDS_I __launch_bounds__((L > 0 && L <= 4096) ? 256 : 512, (L > 0 && L <= 4096) ? 4 : 1)
+
 template <int L>
-__global__ void TAT_COLS_BOUNDS_F k_cols_inv(DevPlan P, const float2* __restrict__ Y, long long ys,
+__global__ void TAT_COLS_BOUNDS_I k_cols_inv(DevPlan P, const float2* __restrict__ Y, long long ys,
                                            float2* __restrict__ X, long long xs, int S, int nt, int batch,
                                            float* acc, long long accs) {
   extern __shared__ float2 sm[];

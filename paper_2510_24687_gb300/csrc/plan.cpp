@@ -494,19 +494,42 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
   std::vector<double> hc(d.nh), hs(d.nh);
   {
     std::vector<float2> cs(d.nh);
-    std::vector<float2> cs_lo(d.nh);
     for (int lp = 0; lp < d.nh; ++lp) {
       cos_sin_2pi(lp - n_phi / 4, n_phi, &hc[lp], &hs[lp]);
       cs[lp] = make_float2((float)hc[lp], (float)hs[lp]);
-      cs_lo[lp] = make_float2((float)(hc[lp] - (double)cs[lp].x), (float)(hs[lp] - (double)cs[lp].y));
     }
     TAT_TRY(upload(P, cs, &d.cs_half));
-    TAT_TRY(upload(P, cs_lo, &d.cs_half_lo));
-    // Scalars of the inverse's polar -> Cartesian resampling and 2D inverse DFT.
-    const double rho = dxi / dlam;
-    d.inv_rho_hi = (float)rho;
-    d.inv_rho_lo = (float)(rho - (double)d.inv_rho_hi);
-    d.inv_nphi_2pi = (float)(n_phi / (2.0 * kPi));
+  }
+  // Inverse (Algorithm 3, step 5): polar position of every node (c, q) of one
+  // quadrant of the Cartesian spectrum grid, in FP64 (the other quadrants of
+  // the half plane are its mirror q -> -q).  Ring: u = |(c, q)| dxi / dlam,
+  // kept up to J + 1e-6 (ties u = J occur exactly when dxi/dlam is rational),
+  // j = min(floor(u), J-1), a = u - j; angle: phi = atan2(q, c) in cells of
+  // 2pi/n_phi, L = floor, b = the fraction.
+  {
+    const int h2 = d.N / 2;
+    std::vector<unsigned> jl((size_t)h2 * h2);
+    std::vector<float2> ab((size_t)h2 * h2);
+    const double rho = dxi / dlam, acell = n_phi / (2.0 * kPi);
+    parallel_for(h2, [&](int c) {
+      for (int q = 0; q < h2; ++q) {
+        const size_t e = (size_t)c * h2 + q;
+        const double u = std::sqrt((double)c * c + (double)q * q) * rho;
+        const double ph = std::atan2((double)q, (double)c) * acell;
+        const double Lf = std::floor(ph);
+        unsigned j = 0xffffu;
+        double a = 0.0;
+        if (u <= d.J + 1e-6) {
+          const double jf = std::min(std::floor(u), (double)(d.J - 1));
+          j = (unsigned)jf;
+          a = std::min(u - jf, 1.0);
+        }
+        jl[e] = j | ((unsigned)Lf << 16);
+        ab[e] = make_float2((float)a, (float)(ph - Lf));
+      }
+    });
+    TAT_TRY(upload(P, jl, &d.inv_jl));
+    TAT_TRY(upload(P, ab, &d.inv_ab));
     d.inv_scale = (float)(dxi * dxi / (2.0 * kPi));
     d.inv_ok = n_phi == n_det ? 1 : 0;
   }

@@ -68,11 +68,11 @@ struct DevPlan {
   const float2* cs_half;           // [nh] (cos phi, sin phi) of the half-circle angles
   // inverse A^{-1} (Algorithm 3)
   const float* Binv;               // [(K+1) x (J+1)] J'_k(lam_j) dt / n_det
-  const float2* cs_half_lo;        // [nh] cos, sin of the half-circle angles minus their FP32 values
+  const unsigned* inv_jl;          // [N/2][N/2] quadrant node (c, q): ring j (low 16 bits, 0xffff: beyond
+                                   // the cut-off) and angle cell L = floor(atan2(q, c) n_phi / 2pi) (high)
+  const float2* inv_ab;            // [N/2][N/2] (a, b): fractional ring and angle positions
   const int2* outrange;            // [n] columns [lo, hi) of each row inside |x| <= R (the disk Omega)
   float inv_scale;                 // dxi^2 / (2 pi)
-  float inv_rho_hi, inv_rho_lo;    // dxi / dlam as a two-float sum
-  float inv_nphi_2pi;              // n_phi / (2 pi)
   float inv_count;                 // nodes of Omega \ Omega0 (0: no constant C)
   int inv_ok;                      // n_phi == n_det (the inverse keeps the data's own modes)
 };
