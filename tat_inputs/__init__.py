@@ -113,7 +113,7 @@ def roi_mask(n: int, radius: float = 0.98, upper_half: bool = False) -> np.ndarr
 
     The disk |x| <= radius of the node-centred grid, optionally cut to its
     upper half y >= 0 (the visible half for detectors on theta in [0, pi),
-    Section 4.3).  An input choice of the caller, not part of A.
+    Section 4.4).  An input choice of the caller, not part of A.
     """
     s = (2 * np.arange(n) - (n - 1)).astype(np.float64)   # (n-1) * x_i
     rr = (radius * (n - 1)) ** 2

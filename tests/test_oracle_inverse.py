@@ -4,7 +4,7 @@ The inverse is pinned against what the mathematics fixes, not against itself:
 the universal backprojection formula is a left inverse of A for complete data
 and T -> infinity (Eq. inverse), so A^{-1} A f must return a smooth f up to a
 small error that falls as T grows (the paper reports 0.22 % relative L2 for its
-phantom with T = 4, Section 4.4); the same formula evaluated at the Cartesian
+phantom with T = 4, Section 4.3); the same formula evaluated at the Cartesian
 nodes without the polar grid must agree with the fast path up to the bilinear
 interpolation error; and exact symmetries of the grids (quarter turn, mirror)
 must hold to rounding.
