@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libtat.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["plan.cpp", "forward.cu", "adjoint.cu", "capi.cu", "noalloc.cu", "solvers.cu", "inverse.cu", "service.cpp"]
+SOURCES = ["plan.cpp", "forward.cu", "adjoint.cu", "capi.cu", "noalloc.cu", "solvers.cu", "inverse.cu", "service.cpp", "lpd.cu"]
 
 
 def _nvcc() -> str:

@@ -111,6 +111,19 @@ def load() -> ctypes.CDLL:
         "tat_service_get_stats": (_I, [_P, ctypes.POINTER(tat_service_stats)]),
         "tat_plan_autotune": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_I),
                                    ctypes.POINTER(_I)]),
+        "tat_lpd_scratch_floats": (ctypes.c_size_t, [_I, _I, _I]),
+        "tat_conv_in_fwd": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P]),
+        "tat_conv_in_bwd_data": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _I, _P]),
+        "tat_conv_in_bwd_weights": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
+        "tat_conv_mid_fwd": (_I, [_I, _I, _I, _P, _P, _P, _P, _P]),
+        "tat_conv_mid_bwd_data": (_I, [_I, _I, _I, _P, _P, _P, _P, _P]),
+        "tat_conv_mid_bwd_weights": (_I, [_I, _I, _I, _P, _P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
+        "tat_conv_out_fwd": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P]),
+        "tat_conv_out_bwd": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
+        "tat_adam": (_I, [_LL, _F, _F, _F, _F, _I, _P, _P, _P, _P, _P, _P]),
+        "tat_to_bf16": (_I, [_LL, _P, _P, _P]),
+        "tat_fill": (_I, [_LL, _F, _P, _P]),
+        "tat_mse": (_I, [_LL, _P, _P, _F, _P, _P, _P]),
         "tat_axpby_clamp": (_I, [_LL, _F, _P, _F, _P, _F, _P, _LL, _P, _P]),
         "tat_axpby_clamp_backward": (_I, [_LL, _P, _F, _P, _LL, _P, _F, _P, _F, _P, _P]),
         "tat_pd_dual_data": (_I, [_LL, _F, _P, _P, _P, _P, _P]),
@@ -332,6 +345,65 @@ def tat_service_get_stats(svc) -> dict:
     st = tat_service_stats()
     _check(load().tat_service_get_stats(svc, ctypes.byref(st)), "tat_service_get_stats")
     return st.as_dict()
+
+
+# learned primal-dual kernels (include/tat_lpd.h); pointers are ints, 0 for NULL
+
+def tat_lpd_scratch_floats(batch, H, W) -> int:
+    return int(load().tat_lpd_scratch_floats(batch, H, W))
+
+
+def tat_conv_in_fwd(batch, H, W, cin, x0, x1, x2, w, b, h, stream=0):
+    _check(load().tat_conv_in_fwd(batch, H, W, cin, x0, x1, x2 or None, w, b, h, stream or None), "tat_conv_in_fwd")
+
+
+def tat_conv_in_bwd_data(batch, H, W, cin, g_h, h, w, gx0, gx1, gx2, accumulate, stream=0):
+    _check(load().tat_conv_in_bwd_data(batch, H, W, cin, g_h, h, w, gx0 or None, gx1 or None, gx2 or None,
+                                       accumulate, stream or None), "tat_conv_in_bwd_data")
+
+
+def tat_conv_in_bwd_weights(batch, H, W, cin, x0, x1, x2, g_h, h, scratch, scratch_floats, gw, gb, stream=0):
+    _check(load().tat_conv_in_bwd_weights(batch, H, W, cin, x0, x1, x2 or None, g_h, h, scratch, scratch_floats, gw,
+                                          gb, stream or None), "tat_conv_in_bwd_weights")
+
+
+def tat_conv_mid_fwd(batch, H, W, h_in, w, b, h_out, stream=0):
+    _check(load().tat_conv_mid_fwd(batch, H, W, h_in, w, b, h_out, stream or None), "tat_conv_mid_fwd")
+
+
+def tat_conv_mid_bwd_data(batch, H, W, g_out, h_out, w, g_in, stream=0):
+    _check(load().tat_conv_mid_bwd_data(batch, H, W, g_out, h_out, w, g_in, stream or None), "tat_conv_mid_bwd_data")
+
+
+def tat_conv_mid_bwd_weights(batch, H, W, h_in, g_out, h_out, scratch, scratch_floats, gw, gb, stream=0):
+    _check(load().tat_conv_mid_bwd_weights(batch, H, W, h_in, g_out, h_out, scratch, scratch_floats, gw, gb,
+                                           stream or None), "tat_conv_mid_bwd_weights")
+
+
+def tat_conv_out_fwd(batch, H, W, h, w, b, residual, out, stream=0):
+    _check(load().tat_conv_out_fwd(batch, H, W, h, w, b, residual, out, stream or None), "tat_conv_out_fwd")
+
+
+def tat_conv_out_bwd(batch, H, W, g_out, h, w, g_h, scratch, scratch_floats, gw, gb, stream=0):
+    _check(load().tat_conv_out_bwd(batch, H, W, g_out, h, w, g_h, scratch, scratch_floats, gw, gb, stream or None),
+           "tat_conv_out_bwd")
+
+
+def tat_adam(count, lr, beta1, beta2, eps, step, param, grad, m, v, w_bf16, stream=0):
+    _check(load().tat_adam(count, lr, beta1, beta2, eps, step, param, grad, m, v, w_bf16 or None, stream or None),
+           "tat_adam")
+
+
+def tat_fill(count, value, out, stream=0):
+    _check(load().tat_fill(count, value, out, stream or None), "tat_fill")
+
+
+def tat_to_bf16(count, x, out, stream=0):
+    _check(load().tat_to_bf16(count, x, out, stream or None), "tat_to_bf16")
+
+
+def tat_mse(count, a, b, scale, grad, loss, stream=0):
+    _check(load().tat_mse(count, a, b, scale, grad or None, loss, stream or None), "tat_mse")
 
 
 def tat_status_string(status: int) -> str:

@@ -23,6 +23,12 @@ def test_exports_every_declared_symbol(pkg):
     assert not missing, missing
 
 
+def test_package_binds_every_declared_function(pkg):
+    """The Python binding offers each C entry point under its own name (argument marshalling only)."""
+    missing = [s for s in pkg.header_symbols() if not callable(getattr(pkg, s, None))]
+    assert not missing, missing
+
+
 def test_status_strings(pkg):
     assert pkg.tat_status_string(0) == "ok"
     assert pkg.tat_status_string(1) == "invalid argument"

@@ -1,0 +1,201 @@
+"""GPU parity of the learned primal-dual kernels (include/tat_lpd.h) and of the
+whole unrolled network, forward and backward, against the FP64 oracle with
+BF16 rounding at the same storage points (oracle/lpd.py).
+
+Bars (derived from the arithmetic): values stored in BF16 may differ from the
+oracle by one BF16 rounding where the FP32 and FP64 accumulations fall on
+opposite sides of a rounding boundary (rare: the accumulations agree to
+~1e-6 while a BF16 step is 2^-8 relative), so BF16 outputs are held to 1e-3
+relative L2; FP32 outputs computed from identical BF16 operands to 1e-5;
+weight gradients (FP32 sums over up to 10^5 products) to 1e-4.  The whole
+network, where flips propagate through 3 unrolled iterations, to 2e-3 on the
+loss and 2e-2 on the parameter gradient.
+"""
+import numpy as np
+import pytest
+
+from tat_inputs import ellipse_phantom, gaussian, uniform
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_24687_gb300 as p
+    return p
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    if not t.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return t
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def r16(torch, x):
+    return torch.as_tensor(x, dtype=torch.float64).to(torch.bfloat16).to(torch.float64)
+
+
+def dev_bf16(torch, x):
+    return torch.as_tensor(np.asarray(x, np.float32)).to(torch.bfloat16).view(torch.int16).cuda().contiguous()
+
+
+def host_bf16(torch, t):
+    return t.view(torch.bfloat16).to(torch.float64).cpu()
+
+
+def dev32(torch, x):
+    return torch.as_tensor(np.asarray(x, np.float32)).cuda().contiguous()
+
+
+B_, H_, W_ = 2, 20, 36     # not multiples of the 8 x 16 tiles
+
+
+def _stream(torch):
+    return torch.cuda.current_stream().cuda_stream
+
+
+@pytest.mark.parametrize("cin", [2, 3])
+def test_conv_in_forward_backward(pkg, torch, cin):
+    import torch.nn.functional as F
+    xs = [uniform(10 + c, B_ * H_ * W_).reshape(B_, H_, W_) - 0.3 for c in range(cin)]
+    w = 0.3 * gaussian(20, 9 * cin * 32)
+    b = 0.1 * gaussian(21, 32)
+    s = _stream(torch)
+    xd = [dev32(torch, x) for x in xs]
+    wd, bd = dev_bf16(torch, w), dev32(torch, b)
+    h = torch.empty((B_, H_, W_, 32), dtype=torch.int16, device="cuda")
+    pkg.tat_conv_in_fwd(B_, H_, W_, cin, xd[0].data_ptr(), xd[1].data_ptr(), xd[2].data_ptr() if cin == 3 else 0,
+                        wd.data_ptr(), bd.data_ptr(), h.data_ptr(), s)
+    X = r16(torch, np.stack(xs, 1)).requires_grad_(True)
+    Wt = r16(torch, w).reshape(3, 3, cin, 32).permute(3, 2, 0, 1).contiguous().requires_grad_(True)
+    Bt = torch.tensor(np.asarray(b, np.float32), dtype=torch.float64).requires_grad_(True)
+    pre = F.conv2d(X, Wt, Bt, padding=1)
+    ref = r16(torch, torch.relu(pre).detach())                                   # (B, 32, H, W)
+    assert rel(host_bf16(torch, h).permute(0, 3, 1, 2), ref) <= 1e-3
+    # backward: G (BF16) at the output; mask from the device forward
+    G = 0.5 * gaussian(30, B_ * H_ * W_ * 32).reshape(B_, H_, W_, 32)
+    Gd = dev_bf16(torch, G)
+    gx = [torch.full((B_, H_, W_), 7.0, device="cuda") for _ in range(cin)]
+    pkg.tat_conv_in_bwd_data(B_, H_, W_, cin, Gd.data_ptr(), h.data_ptr(), wd.data_ptr(), gx[0].data_ptr(),
+                             gx[1].data_ptr(), gx[2].data_ptr() if cin == 3 else 0, 0b01, s)
+    scratch = torch.empty(pkg.tat_lpd_scratch_floats(B_, H_, W_), device="cuda")
+    gw = torch.zeros(9 * cin * 32, device="cuda")
+    gb = torch.zeros(32, device="cuda")
+    pkg.tat_conv_in_bwd_weights(B_, H_, W_, cin, xd[0].data_ptr(), xd[1].data_ptr(),
+                                xd[2].data_ptr() if cin == 3 else 0, Gd.data_ptr(), h.data_ptr(), scratch.data_ptr(),
+                                scratch.numel(), gw.data_ptr(), gb.data_ptr(), s)
+    Gt = r16(torch, G).permute(0, 3, 1, 2)
+    (torch.relu(pre) * Gt).sum().backward()
+    gxr = X.grad.numpy()
+    gxr[:, 0] += 7.0                                                              # channel 0 accumulated
+    assert rel(np.stack([t.cpu().numpy() for t in gx], 1), gxr) <= 1e-5
+    gwr = Wt.grad.permute(2, 3, 1, 0).reshape(-1).numpy()                        # back to [tap][ci][co]
+    assert rel(gw.cpu().numpy(), gwr) <= 1e-4
+    assert rel(gb.cpu().numpy(), Bt.grad.numpy()) <= 1e-4
+
+
+def test_conv_mid_forward_backward(pkg, torch):
+    import torch.nn.functional as F
+    hin = np.maximum(gaussian(40, B_ * H_ * W_ * 32), 0).reshape(B_, H_, W_, 32)
+    w = 0.08 * gaussian(41, 9 * 32 * 32)
+    b = 0.05 * gaussian(42, 32)
+    s = _stream(torch)
+    hd, wd, bd = dev_bf16(torch, hin), dev_bf16(torch, w), dev32(torch, b)
+    out = torch.empty_like(hd)
+    pkg.tat_conv_mid_fwd(B_, H_, W_, hd.data_ptr(), wd.data_ptr(), bd.data_ptr(), out.data_ptr(), s)
+    X = r16(torch, hin).permute(0, 3, 1, 2).contiguous().requires_grad_(True)
+    Wt = r16(torch, w).reshape(3, 3, 32, 32).permute(2, 3, 0, 1).contiguous().requires_grad_(True)
+    Bt = torch.tensor(np.asarray(b, np.float32), dtype=torch.float64).requires_grad_(True)
+    pre = F.conv2d(X, Wt, Bt, padding=1)
+    assert rel(host_bf16(torch, out).permute(0, 3, 1, 2), r16(torch, torch.relu(pre).detach())) <= 1e-3
+    G = 0.5 * gaussian(43, B_ * H_ * W_ * 32).reshape(B_, H_, W_, 32)
+    Gd = dev_bf16(torch, G)
+    gin = torch.empty_like(hd)
+    pkg.tat_conv_mid_bwd_data(B_, H_, W_, Gd.data_ptr(), out.data_ptr(), wd.data_ptr(), gin.data_ptr(), s)
+    scratch = torch.empty(pkg.tat_lpd_scratch_floats(B_, H_, W_), device="cuda")
+    gw = torch.zeros(9 * 32 * 32, device="cuda")
+    gb = torch.zeros(32, device="cuda")
+    pkg.tat_conv_mid_bwd_weights(B_, H_, W_, hd.data_ptr(), Gd.data_ptr(), out.data_ptr(), scratch.data_ptr(),
+                                 scratch.numel(), gw.data_ptr(), gb.data_ptr(), s)
+    (torch.relu(pre) * r16(torch, G).permute(0, 3, 1, 2)).sum().backward()
+    assert rel(host_bf16(torch, gin).permute(0, 3, 1, 2), r16(torch, X.grad)) <= 1e-3
+    assert rel(gw.cpu().numpy(), Wt.grad.permute(2, 3, 0, 1).reshape(-1).numpy()) <= 1e-4   # [tap][co][ci]
+    assert rel(gb.cpu().numpy(), Bt.grad.numpy()) <= 1e-4
+
+
+def test_conv_out_forward_backward(pkg, torch):
+    import torch.nn.functional as F
+    hin = np.maximum(gaussian(50, B_ * H_ * W_ * 32), 0).reshape(B_, H_, W_, 32)
+    w = 0.1 * gaussian(51, 9 * 32)
+    b = np.array([0.3])
+    res = gaussian(52, B_ * H_ * W_).reshape(B_, H_, W_)
+    s = _stream(torch)
+    hd, wd, bd, rd = dev_bf16(torch, hin), dev_bf16(torch, w), dev32(torch, b), dev32(torch, res)
+    out = torch.empty((B_, H_, W_), device="cuda")
+    pkg.tat_conv_out_fwd(B_, H_, W_, hd.data_ptr(), wd.data_ptr(), bd.data_ptr(), rd.data_ptr(), out.data_ptr(), s)
+    X = r16(torch, hin).permute(0, 3, 1, 2).contiguous().requires_grad_(True)
+    Wt = r16(torch, w).reshape(3, 3, 32).permute(2, 0, 1).unsqueeze(0).contiguous().requires_grad_(True)
+    Bt = torch.tensor(np.asarray(b, np.float32), dtype=torch.float64).requires_grad_(True)
+    ref = torch.tensor(np.asarray(res, np.float32), dtype=torch.float64) + F.conv2d(X, Wt, Bt, padding=1)[:, 0]
+    assert rel(out.cpu().numpy(), ref.detach().numpy()) <= 1e-5
+    G = gaussian(53, B_ * H_ * W_).reshape(B_, H_, W_)
+    Gd = dev32(torch, G)
+    gh = torch.empty_like(hd)
+    scratch = torch.empty(pkg.tat_lpd_scratch_floats(B_, H_, W_), device="cuda")
+    gw = torch.zeros(9 * 32, device="cuda")
+    gb = torch.zeros(1, device="cuda")
+    pkg.tat_conv_out_bwd(B_, H_, W_, Gd.data_ptr(), hd.data_ptr(), wd.data_ptr(), gh.data_ptr(), scratch.data_ptr(),
+                         scratch.numel(), gw.data_ptr(), gb.data_ptr(), s)
+    (ref * torch.tensor(np.asarray(G, np.float32), dtype=torch.float64)).sum().backward()
+    assert rel(host_bf16(torch, gh).permute(0, 3, 1, 2), r16(torch, X.grad)) <= 1e-3
+    assert rel(gw.cpu().numpy(), Wt.grad[0].permute(1, 2, 0).reshape(-1).numpy()) <= 1e-4
+    assert rel(gb.cpu().numpy(), Bt.grad.numpy()) <= 1e-4
+
+
+def _problem(pkg, torch, n=32, B=2, seed=0):
+    from oracle import solvers as S
+    from oracle import tat_oracle as O
+    op = pkg.TatOperator(n, 2 * n, 2 * n, device="cuda:0", support_radius=0.9)
+    P = O.OraclePlan(n, 2 * n, 2 * n, support_radius=0.9)
+    f = np.stack([ellipse_phantom(n, seed + b) for b in range(B)]).astype(np.float32)
+    y = np.stack([O.forward(P, f[b].astype(np.float64)) for b in range(B)]).astype(np.float32)
+    return op, S.plan_op(P), f, y
+
+
+def test_lpd_loss_and_gradient_vs_oracle(pkg, torch):
+    from oracle import lpd as OL
+    op, oop, f, y = _problem(pkg, torch)
+    _, npar = OL.layout()
+    assert npar == pkg.lpd.NPARAM
+    p = (0.1 * gaussian(60, npar)).astype(np.float32)
+    net = pkg.lpd.LPD(op, 2, K=3, params=torch.tensor(p))
+    loss, grad = net.loss_and_grad(dev32(torch, y), dev32(torch, f))
+    lref, gref = OL.loss_and_grad(torch.tensor(p, dtype=torch.float64), oop, torch.tensor(y, dtype=torch.float64),
+                                  torch.tensor(f, dtype=torch.float64), K=3, bf16=True)
+    assert abs(float(loss.item()) - lref) <= 2e-3 * lref
+    assert rel(grad.cpu().numpy(), gref.numpy()) <= 2e-2
+    fk = net.f[3].cpu().numpy()
+    fref = OL.reconstruct(torch.tensor(p, dtype=torch.float64), oop, torch.tensor(y, dtype=torch.float64), 3, True)
+    assert rel(fk, fref.detach().numpy()) <= 2e-3
+
+
+def test_lpd_training_reduces_loss_and_graph_matches(pkg, torch):
+    op, _, f, y = _problem(pkg, torch, n=32, B=4, seed=10)
+    yd, fd = dev32(torch, y), dev32(torch, f)
+    eager = pkg.lpd.LPD(op, 4, K=3, seed=1, lr=2e-3)
+    graph = pkg.lpd.LPD(op, 4, K=3, seed=1, lr=2e-3)
+    le, lg = [], []
+    for _ in range(40):
+        le.append(float(eager.train_step(yd, fd).item()))
+        lg.append(float(graph.train_step(yd, fd, graph=True).item()))
+    assert le[-1] < 0.5 * le[0]
+    assert np.allclose(le, lg, rtol=1e-3, atol=0)
