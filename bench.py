@@ -45,10 +45,11 @@ def parse_args():
     p.add_argument("--batch", type=int, default=32)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", choices=["pair", "solves", "inverse", "service"], default="pair",
+    p.add_argument("--train-steps", type=int, default=1500, help="lpd workload: training steps before evaluation")
+    p.add_argument("--workload", choices=["pair", "solves", "inverse", "service", "lpd"], default="pair",
                    help="pair: the A+A* throughput line (default); solves: batched NNLS + TV-PDHG "
                         "reconstructions; inverse: the approximate inverse (Algorithm 3); service: 64 mixed-size "
-                        "requests through the batching runtime")
+                        "requests through the batching runtime; lpd: learned primal-dual training")
     return p.parse_args()
 
 
@@ -259,6 +260,8 @@ def main():
         return run_inverse(args, rank, world, local)
     if args.workload == "service":
         return run_service(args, rank, world, local)
+    if args.workload == "lpd":
+        return run_lpd(args, rank, world, local)
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -683,6 +686,200 @@ def run_service(args, rank, world, local):
                         "d2h_bytes_per_step": int(sum(4 * 4 * n * n for n in sizes))},
                 "roofline": None, "cpu_baseline": None,
                 "gpu_launches": 5 * st["launches"] // max(1, args.steps + max(args.warmup, 3)) * args.steps,
+                "clocks": clk, "kernel_source_hash": kernel_source_hash()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ learned primal-dual workload
+
+LPD_N, LPD_DET, LPD_T, LPD_B, LPD_K, LPD_TRAIN, LPD_NOISE = 128, 256, 256, 8, 10, 2000, 0.02
+LPD_METRIC = "LPD train steps/s (n=128, 256x256 data, K=10, batch 8, BF16 convs, FP32 operators)"
+
+
+def lpd_config(train_steps):
+    return {"workload": f"learned primal-dual training, n={LPD_N}, n_det=n_t={LPD_DET}, K={LPD_K}, batch {LPD_B}",
+            "nets": "3-layer 3x3 convs, 32 channels, BF16 operands, FP32 accumulation; 20 584 parameters",
+            "training_set": f"{LPD_TRAIN} seeded ellipse phantoms, g = A f + 2 % noise (A = this library's)",
+            "optimizer": "Adam lr 1e-3", "train_steps_before_eval": train_steps,
+            "test_set": "16 held-out phantoms (seeds 100000..100015), same noise",
+            "l2": "activations of 10 unrolled iterations (~850 MB) exceed L2, no flush"}
+
+
+def run_lpd(args, rank, world, local):
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import numpy as np
+        import torch
+        from oracle import lpd as OL
+        from oracle import solvers as S
+        from oracle import tat_oracle as O
+        from tat_inputs import ellipse_phantom
+        P = O.OraclePlan(LPD_N, LPD_DET, LPD_T, T=T_WIN, support_radius=RSUP)
+        op = S.plan_op(P)
+        _, npar = OL.layout()
+        p = torch.zeros(npar, dtype=torch.float64)
+        f = torch.tensor(ellipse_phantom(LPD_N, 0))[None]
+        y = op.A(f)
+        t0 = time.perf_counter()
+        OL.loss_and_grad(p, op, y, f, K=1, bf16=False)
+        t1 = time.perf_counter() - t0
+        t = t1 * LPD_K * LPD_B     # one image, one unrolled iteration -> a batch of 8 with K = 10
+        line = {"impl": "reference", "metric": LPD_METRIC, "value": 1.0 / t, "unit": "train steps/s",
+                "n_gpus": args.gpus, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * t, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": lpd_config(args.train_steps),
+                "cpu_baseline": {"value": 1.0 / t, "unit": "train steps/s", "cores": cpu_threads(), "kind": "oracle",
+                                 "sample": "one FP64 oracle loss+gradient of one image with K = 1, scaled x K x batch"},
+                "e2e": {"value": 1.0 / t, "unit": "train steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_24687_gb300 as pkg
+    from tat_inputs import gaussian, phantom_batch, roi_mask
+
+    op = pkg.TatOperator(LPD_N, LPD_DET, LPD_T, T=T_WIN, support_radius=RSUP, device=dev)
+
+    def make_data(seed0, count):
+        f = torch.tensor(phantom_batch(LPD_N, count, seed0=seed0).astype(np.float32), device=dev)
+        g = torch.empty((count, LPD_DET, LPD_T), device=dev)
+        for i in range(0, count, 64):
+            op.forward(f[i:i + 64], out=g[i:i + 64])
+        # 2 % noise relative to each sinogram's norm (tat_inputs.add_noise, with the noise drawn on the host)
+        xi = torch.tensor(gaussian(seed0 + 777, count * LPD_DET * LPD_T).astype(np.float32).reshape(count, -1),
+                          device=dev)
+        gn = torch.linalg.vector_norm(g.reshape(count, -1), dim=1, keepdim=True)
+        xn = torch.linalg.vector_norm(xi, dim=1, keepdim=True)
+        return f, (g.reshape(count, -1) + LPD_NOISE * gn * xi / xn).reshape(count, LPD_DET, LPD_T)
+
+    t_data = time.perf_counter()
+    f_train, y_train = make_data(rank * LPD_TRAIN, LPD_TRAIN)
+    f_test, y_test = make_data(100000, 16)
+    t_data = time.perf_counter() - t_data
+    net = pkg.lpd.LPD(op, LPD_B, K=LPD_K, seed=rank, lr=1e-3)
+    gen = torch.Generator().manual_seed(1234 + rank)
+
+    def batch():
+        idx = torch.randint(0, LPD_TRAIN, (LPD_B,), generator=gen).to(dev)
+        return y_train[idx].contiguous(), f_train[idx].contiguous()
+
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    yb, fb = batch()
+    for _ in range(max(args.warmup, 3)):
+        net.train_step(yb, fb, graph=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ms = timed(lambda: net.train_step(yb, fb, graph=True), args.steps)
+    clk = clocks.stop()
+    ms_eager = timed(lambda: net.train_step(yb, fb, graph=False), max(3, min(args.steps, 10)))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1e3 / ms
+
+    # time of the operator calls inside one step: 4K applications of A or A* on the batch
+    ws = op.workspace(LPD_B)
+    xb = torch.zeros((LPD_B, LPD_N, LPD_N), device=dev)
+    gbuf = torch.zeros((LPD_B, LPD_DET, LPD_T), device=dev)
+    sptr = stream.cuda_stream
+
+    def ops_only():
+        for _ in range(2 * LPD_K):
+            pkg.tat_forward_batched(op.plan, LPD_B, xb.data_ptr(), LPD_N ** 2, gbuf.data_ptr(), LPD_DET * LPD_T,
+                                    ws.data_ptr(), sptr)
+            pkg.tat_adjoint_batched(op.plan, LPD_B, gbuf.data_ptr(), LPD_DET * LPD_T, xb.data_ptr(), LPD_N ** 2,
+                                    ws.data_ptr(), sptr)
+    ms_ops = timed(ops_only, 3)
+
+    # train for a while on the training set, then compare on the held-out phantoms
+    t_train = time.perf_counter()
+    losses = []
+    for it in range(args.train_steps):
+        yb, fb = batch()
+        loss = net.train_step(yb, fb, graph=True)
+        if it % 100 == 0 or it == args.train_steps - 1:
+            losses.append((it, float(loss.item())))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t_train
+
+    def rel_err(rec, ref):
+        return float((torch.linalg.vector_norm((rec - ref).reshape(16, -1), dim=1) /
+                      torch.linalg.vector_norm(ref.reshape(16, -1), dim=1)).mean())
+
+    rec = torch.empty_like(f_test)
+    for i in range(0, 16, LPD_B):
+        rec[i:i + LPD_B] = net.reconstruct(y_test[i:i + LPD_B])
+    err_lpd = rel_err(rec, f_test)
+    torch.cuda.synchronize()
+    t_inf0 = time.perf_counter()
+    for _ in range(5):
+        net.reconstruct(y_test[:LPD_B])
+    torch.cuda.synchronize()
+    inf_per_s = 5 * LPD_B / (time.perf_counter() - t_inf0)
+    # TV-LS on the same operators: 100 PDHG iterations, alpha picked on 8 training images
+    L2 = pkg.power_norm_sq(op, iters=40)
+    sigma, tau, s_ = pkg.pdhg_steps(1.05 * L2, op.info["h"])
+    solver = pkg.TatSolver(op, LPD_B, mask=torch.tensor(roi_mask(LPD_N, radius=RSUP), dtype=torch.float32, device=dev))
+    yv, fv = y_train[:LPD_B].contiguous(), f_train[:LPD_B]
+    best_alpha, best = None, 1e30
+    for alpha in (1e-5, 3e-5, 1e-4, 3e-4, 1e-3, 3e-3):
+        r = solver.tv(yv, alpha, 100, sigma, tau, s_, graph=True).clone()
+        e = float((torch.linalg.vector_norm((r - fv).reshape(LPD_B, -1), dim=1) /
+                   torch.linalg.vector_norm(fv.reshape(LPD_B, -1), dim=1)).mean())
+        if e < best:
+            best_alpha, best = alpha, e
+    rec_tv = torch.empty_like(f_test)
+    rec_nnls = torch.empty_like(f_test)
+    for i in range(0, 16, LPD_B):
+        rec_tv[i:i + LPD_B] = solver.tv(y_test[i:i + LPD_B].contiguous(), best_alpha, 100, sigma, tau, s_, graph=True)
+        rec_nnls[i:i + LPD_B] = solver.nnls(y_test[i:i + LPD_B].contiguous(), 100, 1.0 / L2, graph=True)
+    err_tv, err_nnls = rel_err(rec_tv, f_test), rel_err(rec_nnls, f_test)
+
+    # e2e: one training step with the batch copied in from pinned host memory and the loss read back
+    yb_h, fb_h = yb.cpu().pin_memory(), fb.cpu().pin_memory()
+    t_e2e = time.perf_counter()
+    for _ in range(5):
+        net.train_step(yb_h.to(dev, non_blocking=True), fb_h.to(dev, non_blocking=True), graph=True).item()
+    e2e_v = 5 / (time.perf_counter() - t_e2e)
+    if rank == 0:
+        line = {"metric": LPD_METRIC, "value": value, "unit": "train steps/s", "n_gpus": world, "steps": args.steps,
+                "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16 convs / f32 operators",
+                "data": "synthetic (seeded ellipse phantoms, data from this library's A + 2 % noise)",
+                "config": lpd_config(args.train_steps),
+                "comparison_ms_per_step": {"graph": ms, "eager": ms_eager, "operators_only_4K_calls": ms_ops},
+                "reconstruction_rel_l2_test": {"lpd": err_lpd, "tv_ls": err_tv, "tv_alpha": best_alpha,
+                                               "nnls": err_nnls},
+                "training": {"steps": args.train_steps, "seconds": t_train, "loss_curve": losses,
+                             "data_generation_s": t_data},
+                "inference_reconstructions_per_s": inf_per_s,
+                "e2e": {"value": e2e_v, "unit": "train steps/s",
+                        "h2d_bytes_per_step": int(yb_h.numel() * 4 + fb_h.numel() * 4), "d2h_bytes_per_step": 4},
+                "roofline": None, "cpu_baseline": None,
+                "gpu_launches": args.steps * (LPD_K * 2 * 5 + LPD_K * 6 + LPD_K * 2 * (5 + 10)),
                 "clocks": clk, "kernel_source_hash": kernel_source_hash()}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -176,8 +176,16 @@ __global__ void k_conv_in_bwd_data(int B, int H, int W, const tat_bf16* __restri
   }
 }
 
-// Per-CTA partial sums of dW[tap][c][co] (9*CIN*C values) and db[co] (C values)
-// over chunks of 128 pixels staged in shared memory.
+// Contiguous pixel range [i0, i1) of CTA `blockIdx.x` out of gridDim.x.
+__device__ __forceinline__ void cta_range(long long total, long long* i0, long long* i1) {
+  const long long per = (total + gridDim.x - 1) / gridDim.x;
+  *i0 = (long long)blockIdx.x * per;
+  *i1 = *i0 + per < total ? *i0 + per : total;
+}
+
+// Per-CTA partial sums of dW[tap][c][co] (9*CIN*C values) and db[co] (C values):
+// lane = co, the 8 warps take every 8th pixel of the CTA's range, then the
+// warps' sums are added in shared memory.
 template <int CIN>
 __global__ void __launch_bounds__(256) k_conv_in_bwd_weights(int B, int H, int W, const float* __restrict__ x0,
                                                              const float* __restrict__ x1,
@@ -185,67 +193,60 @@ __global__ void __launch_bounds__(256) k_conv_in_bwd_weights(int B, int H, int W
                                                              const tat_bf16* __restrict__ g_h,
                                                              const tat_bf16* __restrict__ h, float* partial) {
   constexpr int NW = 9 * CIN * C + C;
-  constexpr int PER = (NW + 255) / 256;
-  constexpr int CH = 128;
-  __shared__ float Gs[CH][C];
-  __shared__ float Xs[CH][9 * CIN + 1];
-  const float* xs[3] = {x0, x1, x2};
-  const long long hw = (long long)H * W, total = (long long)B * hw;
-  float acc[PER];
+  __shared__ float red[8][NW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long hw = (long long)H * W;
+  long long i0, i1;
+  cta_range((long long)B * hw, &i0, &i1);
+  float acc[9 * CIN], bacc = 0.f;
 #pragma unroll
-  for (int k = 0; k < PER; ++k) acc[k] = 0.f;
-  for (long long base = (long long)blockIdx.x * CH; base < total; base += (long long)gridDim.x * CH) {
-    __syncthreads();
-    for (int e = threadIdx.x; e < CH * C; e += blockDim.x) {
-      const int pi = e / C, co = e % C;
-      const long long i = base + pi;
-      float v = 0.f;
-      if (i < total) {
-        const float g = bf(g_h[i * C + co]), hv = bf(h[i * C + co]);
-        v = hv > 0.f ? g : 0.f;
-      }
-      Gs[pi][co] = v;
-    }
-    for (int e = threadIdx.x; e < CH * 9 * CIN; e += blockDim.x) {
-      const int pi = e / (9 * CIN), r = e % (9 * CIN);
-      const int tap = r / CIN, c = r % CIN;
-      const long long i = base + pi;
-      float v = 0.f;
-      if (i < total) {
-        const Px p = px_of(i, H, W);
-        const int yy = p.y + tap / 3 - 1, xx = p.x + tap % 3 - 1;
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W) v = rbf(xs[c][(long long)p.b * hw + (long long)yy * W + xx]);
-      }
-      Xs[pi][r] = v;
-    }
-    if (threadIdx.x < CH) Xs[threadIdx.x][9 * CIN] = 1.f;  // bias column
-    __syncthreads();
+  for (int k = 0; k < 9 * CIN; ++k) acc[k] = 0.f;
+  for (long long i = i0 + warp; i < i1; i += 8) {
+    const float gv = bf(g_h[i * C + lane]), hv = bf(h[i * C + lane]);
+    const float G = hv > 0.f ? gv : 0.f;
+    bacc += G;
+    const Px p = px_of(i, H, W);
 #pragma unroll
-    for (int k = 0; k < PER; ++k) {
-      const int o = threadIdx.x + 256 * k;
-      if (o >= NW) break;
-      const int co = o % C, r = o / C;  // r = tap*CIN + c, or 9*CIN for the bias
-      float s = 0.f;
-      for (int pi = 0; pi < CH; ++pi) s = fmaf(Gs[pi][co], Xs[pi][r], s);
-      acc[k] += s;
+    for (int tap = 0; tap < 9; ++tap) {
+      const int yy = p.y + tap / 3 - 1, xx = p.x + tap % 3 - 1;
+      if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+      const long long o = (long long)p.b * hw + (long long)yy * W + xx;
+      acc[tap * CIN + 0] = fmaf(G, rbf(x0[o]), acc[tap * CIN + 0]);
+      acc[tap * CIN + 1] = fmaf(G, rbf(x1[o]), acc[tap * CIN + 1]);
+      if (CIN == 3) acc[tap * CIN + CIN - 1] = fmaf(G, rbf(x2[o]), acc[tap * CIN + CIN - 1]);
     }
   }
 #pragma unroll
-  for (int k = 0; k < PER; ++k) {
-    const int o = threadIdx.x + 256 * k;
-    if (o < NW) partial[(size_t)blockIdx.x * NW + o] = acc[k];
+  for (int k = 0; k < 9 * CIN; ++k) red[warp][k * C + lane] = acc[k];
+  red[warp][9 * CIN * C + lane] = bacc;
+  __syncthreads();
+  for (int o = threadIdx.x; o < NW; o += blockDim.x) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w][o];
+    partial[(size_t)blockIdx.x * NW + o] = t;
   }
 }
 
-// out[e] += sum over CTAs of partial[cta][e]; e < nw maps to gw[e] (e < nw_w) or gb[e - nw_w].
-__global__ void k_reduce_partials(int nctas, int nw_w, int nb, const float* __restrict__ partial, float* gw,
-                                  float* gb) {
+// out[e] += sum over CTAs of partial[cta][e] (fixed order); e < nw_w goes to gw[e], the rest to
+// gb[e - nw_w].  A block covers 32 outputs (lanes); its 8 warps split the CTAs.
+__global__ void __launch_bounds__(256) k_reduce_partials(int nctas, int nw_w, int nb, const float* __restrict__ partial,
+                                                         float* gw, float* gb) {
+  __shared__ float red[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = nw_w + nb;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nw; e += gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int c = 0; c < nctas; ++c) s += partial[(size_t)c * nw + e];
-    if (e < nw_w) gw[e] += s;
-    else gb[e - nw_w] += s;
+  const int e = blockIdx.x * 32 + lane;
+  float s = 0.f;
+  if (e < nw)
+    for (int c = warp; c < nctas; c += 8) s += partial[(size_t)c * nw + e];
+  red[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && e < nw) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w][lane];
+    if (e < nw_w) gw[e] += t;
+    else gb[e - nw_w] += t;
   }
 }
 
@@ -291,20 +292,10 @@ __device__ __forceinline__ void load_halo(tat_bf16* hs, const tat_bf16* __restri
 
 // FWD: out = relu(conv(in) + b).  BWD (data gradient): out = conv^T(g * [h > 0]),
 // i.e. the same implicit GEMM with the taps flipped and in/out channels swapped.
+// One 8 x 16 output tile of the mid layer from the staged halo and weights.
 template <bool BWD>
-__global__ void __launch_bounds__(256) k_conv_mid(int H, int W, const tat_bf16* __restrict__ in,
-                                                  const tat_bf16* __restrict__ mask, const tat_bf16* __restrict__ w,
-                                                  const float* __restrict__ bias, tat_bf16* __restrict__ out) {
-  __shared__ __align__(16) tat_bf16 hs[(TY + 2) * (TX + 2) * CP];
-  __shared__ __align__(16) tat_bf16 wsm[9 * C * CP];
-  const int b = blockIdx.z, y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
-  // weights: wsm[tap][n][k] with n the output channel of this GEMM, k its input channel
-  for (int e = threadIdx.x; e < 9 * C * C; e += blockDim.x) {
-    const int tap = e / (C * C), r = e % (C * C), n = r / C, k = r % C;
-    wsm[(tap * C + n) * CP + k] = BWD ? w[((8 - tap) * C + k) * C + n] : w[(tap * C + n) * C + k];
-  }
-  load_halo<BWD>(hs, in, mask, b, y0, x0, H, W);
-  __syncthreads();
+__device__ __forceinline__ void mid_tile(const tat_bf16* hs, const tat_bf16* wsm, const float* __restrict__ bias,
+                                         tat_bf16* __restrict__ out, int b, int y0, int x0, int H, int W) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   float acc[4][4];
 #pragma unroll
@@ -332,7 +323,7 @@ __global__ void __launch_bounds__(256) k_conv_mid(int H, int W, const tat_bf16* 
     }
   }
   const int y = y0 + warp;
-  if (y >= H) return;
+  if (y >= H) return;  // (no barrier follows inside the tile)
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
     const int x = x0 + g + 8 * half;
@@ -348,6 +339,32 @@ __global__ void __launch_bounds__(256) k_conv_mid(int H, int W, const tat_bf16* 
       }
       *reinterpret_cast<unsigned*>(dst + co) = (unsigned)tobf(v0) | ((unsigned)tobf(v1) << 16);
     }
+  }
+}
+
+template <bool BWD>
+__global__ void __launch_bounds__(256) k_conv_mid(int B, int H, int W, const tat_bf16* __restrict__ in,
+                                                  const tat_bf16* __restrict__ mask, const tat_bf16* __restrict__ w,
+                                                  const float* __restrict__ bias, tat_bf16* __restrict__ out) {
+  __shared__ __align__(16) tat_bf16 hs[(TY + 2) * (TX + 2) * CP];
+  __shared__ __align__(16) tat_bf16 wsm[9 * C * CP];
+  // weights, read in global order (coalesced): wsm[tap][n][k] with n the output
+  // channel of this GEMM and k its input channel
+  for (int e = threadIdx.x; e < 9 * C * C; e += blockDim.x) {
+    const int tap = e / (C * C), r = e % (C * C), co = r / C, ci = r % C;
+    if (BWD) wsm[((8 - tap) * C + ci) * CP + co] = w[e];
+    else wsm[(tap * C + co) * CP + ci] = w[e];
+  }
+  const int tilesx = (W + TX - 1) / TX, tilesy = (H + TY - 1) / TY;
+  const long long ntiles = (long long)B * tilesx * tilesy;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int b = (int)(tile / (tilesx * tilesy));
+    const int rr = (int)(tile % (tilesx * tilesy));
+    const int y0 = (rr / tilesx) * TY, x0 = (rr % tilesx) * TX;
+    __syncthreads();
+    load_halo<BWD>(hs, in, mask, b, y0, x0, H, W);
+    __syncthreads();
+    mid_tile<BWD>(hs, wsm, bias, out, b, y0, x0, H, W);
   }
 }
 
@@ -507,28 +524,40 @@ __global__ void k_conv_out_bwd_data(int B, int H, int W, const float* __restrict
   }
 }
 
-// Per-CTA partials of dW[tap][ci] (288) and db (1): thread o < 288 owns (tap, ci), thread 288 the bias.
-__global__ void __launch_bounds__(320) k_conv_out_wgrad(int B, int H, int W, const float* __restrict__ gout,
+// Per-CTA partials of dW[tap][ci] (288) and db (1): lane = ci, the 8 warps take
+// every 8th pixel of the CTA's range, then the warps' sums are added in shared memory.
+__global__ void __launch_bounds__(256) k_conv_out_wgrad(int B, int H, int W, const float* __restrict__ gout,
                                                         const tat_bf16* __restrict__ h, float* partial) {
-  const int o = threadIdx.x;
-  const int tap = o / C, ci = o % C;
-  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-  const long long hw = (long long)H * W, total = (long long)B * hw;
-  const long long per = (total + gridDim.x - 1) / gridDim.x;
-  const long long i0 = (long long)blockIdx.x * per, i1 = i0 + per < total ? i0 + per : total;
-  float s = 0.f;
-  for (long long i = i0; i < i1; ++i) {
+  constexpr int NW = 9 * C + 1;
+  __shared__ float red[8][NW];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long hw = (long long)H * W;
+  long long i0, i1;
+  cta_range((long long)B * hw, &i0, &i1);
+  float acc[9], bacc = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k] = 0.f;
+  for (long long i = i0 + warp; i < i1; i += 8) {
     const float gv = gout[i];
-    if (o < 9 * C) {
-      const Px p = px_of(i, H, W);
-      const int yy = p.y + dy, xx = p.x + dx;
-      if (yy >= 0 && yy < H && xx >= 0 && xx < W)
-        s = fmaf(gv, bf(h[((long long)p.b * hw + (long long)yy * W + xx) * C + ci]), s);
-    } else if (o == 9 * C) {
-      s += gv;
+    bacc += gv;
+    const Px p = px_of(i, H, W);
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int yy = p.y + tap / 3 - 1, xx = p.x + tap % 3 - 1;
+      if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+      acc[tap] = fmaf(gv, bf(h[((long long)p.b * hw + (long long)yy * W + xx) * C + lane]), acc[tap]);
     }
   }
-  if (o <= 9 * C) partial[(size_t)blockIdx.x * (9 * C + 1) + o] = s;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) red[warp][k * C + lane] = acc[k];
+  if (lane == 0) red[warp][9 * C] = bacc;
+  __syncthreads();
+  for (int o = threadIdx.x; o < NW; o += blockDim.x) {
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += red[w][o];
+    partial[(size_t)blockIdx.x * NW + o] = t;
+  }
 }
 
 // ------------------------------------------------------------------ optimizer and loss
@@ -576,6 +605,13 @@ __global__ void k_mse(long long n, const float* __restrict__ a, const float* __r
 
 bool bad_sizes(int batch, int H, int W) { return batch < 1 || H < 1 || W < 1; }
 
+// Persistent tensor-core conv: up to 4 CTAs per SM (37 KB of shared memory and
+// ~40 registers each), every CTA loads the weights once and loops over tiles.
+int mid_ctas(int batch, int H, int W) {
+  const long long tiles = (long long)batch * ((H + TY - 1) / TY) * ((W + TX - 1) / TX);
+  return (int)(tiles < 4 * 152 ? tiles : 4 * 152);
+}
+
 int wgrad_ctas(int batch, int H, int W) {
   const long long tiles = (long long)batch * ((H + TY - 1) / TY) * ((W + TX - 1) / TX);
   return (int)(tiles < kMaxCtas ? tiles : kMaxCtas);
@@ -620,30 +656,30 @@ tat_status tat_conv_in_bwd_weights(int batch, int H, int W, int cin, const float
     return TAT_ERR_INVALID_ARG;
   const int nw = 9 * cin * C + C;
   const long long total = (long long)batch * H * W;
-  const int ctas = (int)((total + 127) / 128 < kMaxCtas ? (total + 127) / 128 : kMaxCtas);
+  const int ctas = (int)((total + 255) / 256 < kMaxCtas ? (total + 255) / 256 : kMaxCtas);
   if (scratch_floats < (size_t)ctas * nw) return TAT_ERR_INVALID_ARG;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cin == 2) k_conv_in_bwd_weights<2><<<ctas, 256, 0, s>>>(batch, H, W, x0, x1, nullptr, g_h, h, scratch);
   else k_conv_in_bwd_weights<3><<<ctas, 256, 0, s>>>(batch, H, W, x0, x1, x2, g_h, h, scratch);
   tat_status st = launched("tat_conv_in_bwd_weights");
   if (st != TAT_OK) return st;
-  k_reduce_partials<<<(nw + 255) / 256, 256, 0, s>>>(ctas, 9 * cin * C, C, scratch, gw, gb);
+  k_reduce_partials<<<(nw + 31) / 32, 256, 0, s>>>(ctas, 9 * cin * C, C, scratch, gw, gb);
   return launched("tat_conv_in_bwd_weights");
 }
 
 tat_status tat_conv_mid_fwd(int batch, int H, int W, const tat_bf16* h_in, const tat_bf16* w, const float* b,
                             tat_bf16* h_out, tat_stream_t stream) {
   if (bad_sizes(batch, H, W) || !h_in || !w || !b || !h_out) return TAT_ERR_INVALID_ARG;
-  const dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY, batch);
-  k_conv_mid<false><<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(H, W, h_in, nullptr, w, b, h_out);
+  k_conv_mid<false><<<mid_ctas(batch, H, W), 256, 0, static_cast<cudaStream_t>(stream)>>>(batch, H, W, h_in, nullptr,
+                                                                                           w, b, h_out);
   return launched("tat_conv_mid_fwd");
 }
 
 tat_status tat_conv_mid_bwd_data(int batch, int H, int W, const tat_bf16* g_out, const tat_bf16* h_out,
                                  const tat_bf16* w, tat_bf16* g_in, tat_stream_t stream) {
   if (bad_sizes(batch, H, W) || !g_out || !h_out || !w || !g_in) return TAT_ERR_INVALID_ARG;
-  const dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY, batch);
-  k_conv_mid<true><<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(H, W, g_out, h_out, w, nullptr, g_in);
+  k_conv_mid<true><<<mid_ctas(batch, H, W), 256, 0, static_cast<cudaStream_t>(stream)>>>(batch, H, W, g_out, h_out,
+                                                                                          w, nullptr, g_in);
   return launched("tat_conv_mid_bwd_data");
 }
 
@@ -658,7 +694,7 @@ tat_status tat_conv_mid_bwd_weights(int batch, int H, int W, const tat_bf16* h_i
   k_conv_mid_wgrad<<<ctas, 288, 0, s>>>(batch, H, W, h_in, g_out, h_out, scratch);
   tat_status st = launched("tat_conv_mid_bwd_weights");
   if (st != TAT_OK) return st;
-  k_reduce_partials<<<(nw + 255) / 256, 256, 0, s>>>(ctas, 9 * C * C, C, scratch, gw, gb);
+  k_reduce_partials<<<(nw + 31) / 32, 256, 0, s>>>(ctas, 9 * C * C, C, scratch, gw, gb);
   return launched("tat_conv_mid_bwd_weights");
 }
 
@@ -682,10 +718,10 @@ tat_status tat_conv_out_bwd(int batch, int H, int W, const float* g_out, const t
   k_conv_out_bwd_data<<<blocks_for(n, 256), 256, 0, s>>>(batch, H, W, g_out, w, g_h);
   tat_status st = launched("tat_conv_out_bwd");
   if (st != TAT_OK) return st;
-  k_conv_out_wgrad<<<ctas, 320, 0, s>>>(batch, H, W, g_out, h, scratch);
+  k_conv_out_wgrad<<<ctas, 256, 0, s>>>(batch, H, W, g_out, h, scratch);
   st = launched("tat_conv_out_bwd");
   if (st != TAT_OK) return st;
-  k_reduce_partials<<<2, 256, 0, s>>>(ctas, 9 * C, 1, scratch, gw, gb);
+  k_reduce_partials<<<(9 * C + 1 + 31) / 32, 256, 0, s>>>(ctas, 9 * C, 1, scratch, gw, gb);
   return launched("tat_conv_out_bwd");
 }
 
