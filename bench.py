@@ -46,6 +46,8 @@ def parse_args():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--train-steps", type=int, default=1500, help="lpd workload: training steps before evaluation")
+    p.add_argument("--arc", choices=["full", "half"], default="full",
+                   help="lpd workload: detectors on the full circle, or on theta in [0, pi) (limited view)")
     p.add_argument("--workload", choices=["pair", "solves", "inverse", "service", "lpd"], default="pair",
                    help="pair: the A+A* throughput line (default); solves: batched NNLS + TV-PDHG "
                         "reconstructions; inverse: the approximate inverse (Algorithm 3); service: 64 mixed-size "
@@ -698,8 +700,9 @@ LPD_N, LPD_DET, LPD_T, LPD_B, LPD_K, LPD_TRAIN, LPD_NOISE = 128, 256, 256, 8, 10
 LPD_METRIC = "LPD train steps/s (n=128, 256x256 data, K=10, batch 8, BF16 convs, FP32 operators)"
 
 
-def lpd_config(train_steps):
+def lpd_config(train_steps, arc="full"):
     return {"workload": f"learned primal-dual training, n={LPD_N}, n_det=n_t={LPD_DET}, K={LPD_K}, batch {LPD_B}",
+            "detectors": "full circle" if arc == "full" else "half circle theta in [0, pi) (limited view)",
             "nets": "3-layer 3x3 convs, 32 channels, BF16 operands, FP32 accumulation; 20 584 parameters",
             "training_set": f"{LPD_TRAIN} seeded ellipse phantoms, g = A f + 2 % noise (A = this library's)",
             "optimizer": "Adam lr 1e-3", "train_steps_before_eval": train_steps,
@@ -748,7 +751,8 @@ def run_lpd(args, rank, world, local):
     import paper_2510_24687_gb300 as pkg
     from tat_inputs import gaussian, phantom_batch, roi_mask
 
-    op = pkg.TatOperator(LPD_N, LPD_DET, LPD_T, T=T_WIN, support_radius=RSUP, device=dev)
+    arc_kw = {} if args.arc == "full" else dict(arc_begin=0.0, arc_len=math.pi)
+    op = pkg.TatOperator(LPD_N, LPD_DET, LPD_T, T=T_WIN, support_radius=RSUP, device=dev, **arc_kw)
 
     def make_data(seed0, count):
         f = torch.tensor(phantom_batch(LPD_N, count, seed0=seed0).astype(np.float32), device=dev)
@@ -869,7 +873,7 @@ def run_lpd(args, rank, world, local):
                 "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16 convs / f32 operators",
                 "data": "synthetic (seeded ellipse phantoms, data from this library's A + 2 % noise)",
-                "config": lpd_config(args.train_steps),
+                "config": lpd_config(args.train_steps, args.arc),
                 "comparison_ms_per_step": {"graph": ms, "eager": ms_eager, "operators_only_4K_calls": ms_ops},
                 "reconstruction_rel_l2_test": {"lpd": err_lpd, "tv_ls": err_tv, "tv_alpha": best_alpha,
                                                "nnls": err_nnls},

@@ -242,3 +242,16 @@ class LPD:
             self._backward()
         self._adam()
         return self.loss
+
+    def fit(self, f_train, y_train, steps, seed=0, graph=True, log_every=100):
+        """Adam on random batches (with replacement, seeded) of the training pairs
+        (f_train (N, n, n), y_train (N, n_det, n_t), device tensors); returns
+        [(step, loss)] every `log_every` steps and at the last one."""
+        gen = torch.Generator().manual_seed(seed)
+        curve = []
+        for it in range(steps):
+            idx = torch.randint(0, f_train.shape[0], (self.B,), generator=gen).to(self.dev)
+            loss = self.train_step(y_train[idx].contiguous(), f_train[idx].contiguous(), graph=graph)
+            if it % log_every == 0 or it == steps - 1:
+                curve.append((it, float(loss.item())))
+        return curve
