@@ -57,12 +57,17 @@ def parse_args():
 
 # ------------------------------------------------------------------ helpers
 
-def kernel_source_hash():
+OPERATOR_SOURCES = ("fft.cuh", "kernels.cuh", "launch.cuh", "plan.cpp", "plan.hpp", "forward.cu", "adjoint.cu",
+                    "inverse.cu")
+
+
+def kernel_source_hash(names=None):
+    """Hash of the CUDA sources that define the operator kernels (or of `names`): a committed
+    ncu traffic figure is used only while its kernels are unchanged."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2510_24687_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".cpp", ".hpp")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    for name in sorted(names or OPERATOR_SOURCES):
+        h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -144,14 +149,15 @@ def stage_flops(info, B, n=N_IMG, n_det=N_DET, n_t=N_T):
             "rows_adj": rows, "cols_adj": cols, "rings_adj": rings, "modes_adj": modes, "theta_adj": theta}
 
 
-def traffic_for(kernel, workload="pair_n512_b32"):
-    """DRAM bytes per launch from the committed ncu summaries, if taken on the current kernels."""
+def traffic_for(kernel, workload="pair_n512_b32", sources=None):
+    """DRAM bytes per launch from the committed ncu summaries, if taken on the current kernels
+    (`sources`: the files that define them; default the operator kernels)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             t = json.load(fh).get(workload, {})
     except (OSError, ValueError):
         return None
-    if t.get("kernel_source_hash") != kernel_source_hash():
+    if t.get("kernel_source_hash") != kernel_source_hash(sources):
         return None
     v = t.get("dram_bytes_per_launch", {}).get(kernel)
     return float(v) if v is not None else None
@@ -1031,7 +1037,7 @@ def run_solves(args, rank, world, local):
     primal_bytes = 4 * B * SOLVE_N * SOLVE_N * (1 + 1 + 2 + 1 + 1)
     achieved = primal_bytes / (ms_primal / 1e3) / 1e9
     fused = {"bound": "hbm", "kernel": "k_tv_primal", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-             "frac": achieved / hbm_peak, "traffic": traffic_for("k_tv_primal", "solves_n256_b16"),
+             "frac": achieved / hbm_peak, "traffic": traffic_for("k_tv_primal", "solves_n256_b16", ("solvers.cu",)),
              "peak_source": "measured" if peaks else "fallback", "ms": ms_primal,
              "note": "fused element-wise step; algorithmic bytes = f, A*q, p (2 planes), mask, f_out, fbar per pixel"}
     stage_ms = stage_times(pkg, op, B, xbuf, ybuf, x_tmp2, ws, stream, 5)
