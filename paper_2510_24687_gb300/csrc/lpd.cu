@@ -24,7 +24,8 @@ namespace {
 constexpr int C = 32;       // hidden channels
 constexpr int CP = 40;      // padded channel stride in shared memory (BF16 elements)
 constexpr int TY = 8, TX = 16;  // output tile of the tensor-core kernels
-constexpr int kMaxCtas = 2 * 152;
+constexpr int kMaxCtas = 2 * 152;   // CTAs of the tensor-core weight gradient
+constexpr int kRedCtas = 8 * 152;   // CTAs of the CUDA-core weight gradients (latency-bound loops)
 
 tat_status launched(const char* what) {
   const cudaError_t e = cudaGetLastError();
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(256) k_conv_in_bwd_weights(int B, int H, int W
   float acc[9 * CIN], bacc = 0.f;
 #pragma unroll
   for (int k = 0; k < 9 * CIN; ++k) acc[k] = 0.f;
+#pragma unroll 4
   for (long long i = i0 + warp; i < i1; i += 8) {
     const float gv = bf(g_h[i * C + lane]), hv = bf(h[i * C + lane]);
     const float G = hv > 0.f ? gv : 0.f;
@@ -537,6 +539,7 @@ __global__ void __launch_bounds__(256) k_conv_out_wgrad(int B, int H, int W, con
   float acc[9], bacc = 0.f;
 #pragma unroll
   for (int k = 0; k < 9; ++k) acc[k] = 0.f;
+#pragma unroll 4
   for (long long i = i0 + warp; i < i1; i += 8) {
     const float gv = gout[i];
     bacc += gv;
@@ -623,7 +626,8 @@ extern "C" {
 
 size_t tat_lpd_scratch_floats(int batch, int H, int W) {
   if (bad_sizes(batch, H, W)) return 0;
-  return (size_t)kMaxCtas * (9 * C * C + C);
+  const size_t a = (size_t)kMaxCtas * (9 * C * C + C), b = (size_t)kRedCtas * (9 * 3 * C + C);
+  return a > b ? a : b;
 }
 
 tat_status tat_conv_in_fwd(int batch, int H, int W, int cin, const float* x0, const float* x1, const float* x2,
@@ -656,7 +660,7 @@ tat_status tat_conv_in_bwd_weights(int batch, int H, int W, int cin, const float
     return TAT_ERR_INVALID_ARG;
   const int nw = 9 * cin * C + C;
   const long long total = (long long)batch * H * W;
-  const int ctas = (int)((total + 255) / 256 < kMaxCtas ? (total + 255) / 256 : kMaxCtas);
+  const int ctas = (int)((total + 63) / 64 < kRedCtas ? (total + 63) / 64 : kRedCtas);
   if (scratch_floats < (size_t)ctas * nw) return TAT_ERR_INVALID_ARG;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (cin == 2) k_conv_in_bwd_weights<2><<<ctas, 256, 0, s>>>(batch, H, W, x0, x1, nullptr, g_h, h, scratch);
@@ -712,7 +716,7 @@ tat_status tat_conv_out_bwd(int batch, int H, int W, const float* g_out, const t
                             tat_stream_t stream) {
   if (bad_sizes(batch, H, W) || !g_out || !h || !w || !g_h || !scratch || !gw || !gb) return TAT_ERR_INVALID_ARG;
   const long long n = (long long)batch * H * W;
-  const int ctas = (int)(n < kMaxCtas ? n : kMaxCtas);
+  const int ctas = (int)((n + 63) / 64 < kRedCtas ? (n + 63) / 64 : kRedCtas);
   if (scratch_floats < (size_t)ctas * (9 * C + 1)) return TAT_ERR_INVALID_ARG;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   k_conv_out_bwd_data<<<blocks_for(n, 256), 256, 0, s>>>(batch, H, W, g_out, w, g_h);
