@@ -45,6 +45,9 @@ def parse_args():
     p.add_argument("--batch", type=int, default=32)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-compare", action="store_true", help="pair workload: skip the per-image and cuFFT comparisons")
+    p.add_argument("--size", type=int, default=512,
+                   help="pair workload: image size n (n_det = n_t = 2n); 512 is the headline, 256 the batched config")
     p.add_argument("--train-steps", type=int, default=1500, help="lpd workload: training steps before evaluation")
     p.add_argument("--arc", choices=["full", "half"], default="full",
                    help="lpd workload: detectors on the full circle, or on theta in [0, pi) (limited view)")
@@ -255,10 +258,139 @@ def workload_config(batch):
             "l2": "inputs exceed L2 (batch inputs 160 MB + 0.5 GB working set per step), no flush"}
 
 
+
+# ------------------------------------------------------------------ cuFFT-composed comparison
+
+class CufftComposed:
+    """A and A* composed from cuFFT transforms (torch.fft) and PyTorch gathers/scatters in FP32,
+    materialising the full N x N spectrum and the polar grid on the full circle -- the timed
+    comparison for the fused kernels (same discretisation and tables, computed here in FP64 from
+    the plan's grid integers; the low-mode rule comes from the library's debug call)."""
+
+    def __init__(self, pkg, op, dev):
+        import numpy as np
+        import torch
+        from scipy.special import jv
+        t = torch
+        self.t, self.dev = t, dev
+        info = op.info
+        n, nd, nt = op.n, op.n_det, op.n_t
+        N, M, J, nphi = info["N"], info["M"], info["J"], info["n_phi"]
+        h, dt, dlam, dxi = info["h"], info["dt"], info["dlam"], info["dxi"]
+        if nphi != nd:
+            raise ValueError("the comparison covers n_phi = n_det")
+        self.n, self.nd, self.nt, self.N, self.M, self.J, self.nphi = n, nd, nt, N, M, J, nphi
+        s = 2.0 * np.arange(n) - (n - 1)
+        rs = op.desc.support_radius * (n - 1)
+        self.mask = t.tensor(((s[:, None] ** 2 + s[None, :] ** 2) <= rs * rs).astype(np.float32), device=dev)
+        q = np.fft.fftfreq(N, 1.0 / N)
+        ph = np.exp(1j * q * dxi)
+        self.ph = t.tensor(ph.astype(np.complex64), device=dev)
+        self.scale = h * h / (2 * np.pi)
+        xl, wl = pkg.tat_debug_low_mode_rule()
+        self.low = np.asarray(xl) * dlam
+        self.low_w = np.asarray(wl)
+        lam = np.arange(J + 1) * dlam
+        radii = np.concatenate([lam, self.low])
+        phi = 2 * np.pi * np.arange(nphi) / nphi
+        u = radii[:, None] * np.cos(phi)[None, :] / dxi
+        v = radii[:, None] * np.sin(phi)[None, :] / dxi
+        i0, k0 = np.floor(u), np.floor(v)
+        a, b = u - i0, v - k0
+        i0 = i0.astype(np.int64) % N
+        k0 = k0.astype(np.int64) % N
+        i1, k1 = (i0 + 1) % N, (k0 + 1) % N
+        self.idx = [t.tensor((kk * N + ii).ravel(), device=dev) for kk, ii in ((k0, i0), (k0, i1), (k1, i0), (k1, i1))]
+        self.wts = [t.tensor(w.ravel().astype(np.float32), device=dev)
+                    for w in ((1 - a) * (1 - b), a * (1 - b), (1 - a) * b, a * b)]
+        self.R = radii.size
+        k = np.where(np.arange(nphi) < nphi // 2, np.arange(nphi), np.arange(nphi) - nphi)
+        ak = np.abs(k)
+        ik = (1j) ** ak
+        Jt = jv(ak[None, :].astype(np.float64), lam[:, None])
+        self.Bt = t.tensor((ik[None, :] * (dlam * lam)[:, None] * Jt).astype(np.complex64), device=dev)
+        self.Bt_adj = t.tensor((np.conj(ik)[None, :] * (dlam * lam)[:, None] * Jt).astype(np.complex64), device=dev)
+        tm = np.arange(nt) * dt
+        self.low_bins = [int(np.nonzero(k == kk)[0][0]) for kk in (-1, 0, 1)]
+        Jl = jv(ak[None, :].astype(np.float64), self.low[:, None])
+        self.cl = t.tensor(np.stack([ik[bb] * self.low_w * dlam * self.low * Jl[:, bb] for bb in self.low_bins])
+                           .astype(np.complex64), device=dev)                       # (3, 20)
+        self.cl_adj = t.tensor(np.stack([np.conj(ik[bb]) * self.low_w * dlam * self.low * Jl[:, bb]
+                                         for bb in self.low_bins]).astype(np.complex64), device=dev)
+        self.Cl = t.tensor(np.cos(self.low[:, None] * tm[None, :]).astype(np.complex64), device=dev)   # (20, nt)
+        self.C8 = t.tensor(np.cos(lam[:8, None] * tm[None, :]).astype(np.complex64), device=dev)        # (8, nt)
+        self.W_X, self.W_Y = op.W_X, op.W_Y
+
+    def forward(self, f):
+        t = self.t
+        B, n, N, M, J, nphi, nt = f.shape[0], self.n, self.N, self.M, self.J, self.nphi, self.nt
+        pad = t.zeros((B, N, N), dtype=t.complex64, device=self.dev)
+        pad[:, :n, :n] = f * self.mask
+        F = t.fft.fft2(pad) * (self.scale * self.ph[None, :, None] * self.ph[None, None, :])
+        Ff = F.reshape(B, -1)
+        Fp = sum(Ff[:, ix] * w for ix, w in zip(self.idx, self.wts)).reshape(B, self.R, nphi)
+        fh = t.fft.fft(Fp, dim=2) / nphi
+        H = self.Bt[None] * fh[:, :J + 1]                                                 # (B, J+1, nphi)
+        y = t.zeros((B, 2 * M, nphi), dtype=t.complex64, device=self.dev)
+        y[:, :J + 1] = H
+        y[:, 2 * M - J:] = t.flip(H[:, 1:], dims=[1])
+        G = 0.5 * (t.fft.fft(y, dim=1)[:, :nt] + H[:, :1])                               # (B, nt, nphi)
+        for r, bb in enumerate(self.low_bins):
+            corr = -(H[:, :8, bb] @ self.C8) + (self.cl[r][None] * fh[:, J + 1:, bb]) @ self.Cl
+            G[:, :, bb] = G[:, :, bb] + corr
+        g = (t.fft.ifft(G, dim=2) * nphi).real                                           # (B, nt, n_det)
+        return g.transpose(1, 2).contiguous()
+
+    def adjoint(self, g):
+        t = self.t
+        B, n, N, M, J, nphi, nt = g.shape[0], self.n, self.N, self.M, self.J, self.nphi, self.nt
+        gp = t.fft.fft(g.to(t.complex64) * self.W_Y, dim=1)                             # (B, nphi, nt)
+        y = t.zeros((B, nphi, 2 * M), dtype=t.complex64, device=self.dev)
+        y[:, :, :nt] = gp
+        y[:, :, 2 * M - nt + 1:] = t.flip(gp[:, :, 1:], dims=[2])
+        S = 0.5 * (t.fft.fft(y, dim=2)[:, :, :J + 1] + gp[:, :, :1])                   # (B, nphi, J+1)
+        fh = self.Bt_adj[None] * S.transpose(1, 2)                                        # (B, J+1, nphi)
+        low = t.zeros((B, self.R - J - 1, nphi), dtype=t.complex64, device=self.dev)
+        for r, bb in enumerate(self.low_bins):
+            fh[:, :8, bb] = 0
+            low[:, :, bb] = self.cl_adj[r][None] * (gp[:, bb, :] @ self.Cl.T)
+        Fp = t.fft.ifft(t.cat([fh, low], dim=1), dim=2).reshape(B, -1)                  # (B, R*nphi)
+        Fc = t.zeros((B, N * N), dtype=t.complex64, device=self.dev)
+        for ix, w in zip(self.idx, self.wts):
+            Fc.index_add_(1, ix, Fp * w)
+        Z = t.fft.ifft2(Fc.reshape(B, N, N) * t.conj(self.ph)[None, :, None] * t.conj(self.ph)[None, None, :]) * (N * N)
+        return (self.scale * Z[:, :n, :n].real) * self.mask / self.W_X
+
+
+def cufft_comparison(pkg, op, f, g_fast, f2_fast, steps=3):
+    """Pairs/s of the cuFFT-composed A+A* on the same batch, and its relative L2 distance to the fused path."""
+    import torch
+    base = CufftComposed(pkg, op, f.device)
+    g = base.forward(f)
+    fa = base.adjoint(g_fast)
+    acc = {"A_rel_l2_vs_fused": float(torch.linalg.vector_norm(g - g_fast) / torch.linalg.vector_norm(g_fast)),
+           "Astar_rel_l2_vs_fused": float(torch.linalg.vector_norm(fa - f2_fast) / torch.linalg.vector_norm(f2_fast))}
+    del g, fa
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        base.adjoint(base.forward(f))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"pairs_per_s": f.shape[0] / (ms / 1e3), "ms_per_step": ms, **acc,
+            "what": "torch.fft (cuFFT) fft2/ifft2 of the N x N spectrum, full-circle polar gather / index_add scatter, "
+                    "FFT-based cosine transforms, FP32"}
+
+
 # ------------------------------------------------------------------ GPU benchmark
 
 def main():
+    global N_IMG, N_DET, N_T
     args = parse_args()
+    if args.size != 512:
+        N_IMG, N_DET, N_T = args.size, 2 * args.size, 2 * args.size
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -335,7 +467,7 @@ def main():
 
     # ---- per-stage timing (same work, events between the five stages of each direction)
     stage_ms = stage_times(pkg, op, B, f, g, f2, ws, stream, max(3, min(args.steps, 10)))
-    roofline = alu_roofline(stage_ms, stage_flops(info, B), "pair_n512_b32")
+    roofline = alu_roofline(stage_ms, stage_flops(info, B), f"pair_n{N_IMG}_b{B}")
     peaks = measured_peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     pair_bytes = 2 * (4 * N_IMG * N_IMG + 4 * N_DET * N_T)
@@ -371,21 +503,56 @@ def main():
     e2e = {"value": B * esteps * world / (ems / 1e3), "unit": "pairs/s", "h2d_bytes_per_step": fh.nbytes,
            "d2h_bytes_per_step": fh.nbytes, "steps": esteps}
 
+    # ---- comparisons on the same batch: the plain per-image path (one A and one A* call per
+    # image) and the cuFFT-composed pipeline (materialised spectrum)
+    comparisons = {}
+    if not args.no_compare:
+        f1 = [f[b:b + 1].clone() for b in range(B)]
+        g1 = torch.empty((1, N_DET, N_T), device=dev)
+        o1 = torch.empty((1, N_IMG, N_IMG), device=dev)
+        ws1 = op.workspace(B)
+
+        def per_image():
+            for fb in f1:
+                pkg.tat_forward(op.plan, fb.data_ptr(), g1.data_ptr(), ws1.data_ptr(), sptr)
+                pkg.tat_adjoint(op.plan, g1.data_ptr(), o1.data_ptr(), ws1.data_ptr(), sptr)
+        per_image()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(3):
+            per_image()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / 3
+        comparisons["per_image_plain_path"] = {"pairs_per_s": B / (pms / 1e3), "ms_per_step": pms,
+                                               "what": "tat_forward + tat_adjoint once per image, same kernels"}
+        step()
+        torch.cuda.synchronize()
+        try:
+            comparisons["cufft_composed"] = cufft_comparison(pkg, op, f, g, f2)
+        except RuntimeError as exc:     # e.g. out of memory on a smaller device
+            comparisons["cufft_composed"] = {"unavailable": str(exc).splitlines()[0]}
+        for k in ("per_image_plain_path", "cufft_composed"):
+            v = comparisons[k].get("pairs_per_s")
+            if v:
+                comparisons[k]["fused_speedup"] = value / world / v
+
     # ---- CPU oracle on a bounded sample (rank 0, single GPU only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ops = 2
         t = time_oracle(ops)
         cpu = {"value": 0.5 * ops / t, "unit": "pairs/s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": "one A+A* pair of the n=512 workload (image seed 0) through the FP64 numpy/scipy oracle"}
+               "sample": f"one A+A* pair of the n={N_IMG} workload (image seed 0) through the FP64 numpy/scipy oracle"}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        line = {"metric": METRIC.replace("n=512", f"n={N_IMG}"), "value": value, "unit": "pairs/s", "n_gpus": world,
+                "steps": args.steps,
                 "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded random-ellipse phantoms; the paper's phantoms are not published)",
                 "config": workload_config(B), "roofline": roofline, "hbm_roofline_pair": hbm,
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 10 * args.steps,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 10 * args.steps, "comparisons": comparisons,
                 "clocks": clk, "plan": {k: info[k] for k in ("N", "M", "J", "n_phi", "n_low", "n_points")},
                 "kernel_source_hash": kernel_source_hash()}
         print(json.dumps(line), flush=True)
