@@ -382,6 +382,20 @@ struct FourStep {
 // or RA*16 (step B); group sizes are multiples of 32, so every lane of a warp
 // runs the same iterations of step B and __syncwarp stays warp-uniform.
 
+// Shared-memory slot of element i of a transform buffer of length L: one pad
+// slot per 16 elements (the Stockham passes), and for the four-step lengths one
+// more per 256, so that the permuted layout's neighbouring bins q, q+1 (256
+// slots apart) fall into different banks when a warp walks q.
+template <int L>
+__device__ __forceinline__ int xpad(int i) {
+  if constexpr (FourStep<L>::on) return i + (i >> 4) + (i >> 8);
+  else return i + (i >> 4);
+}
+__host__ __device__ __forceinline__ int xpad_len(int L) {
+  const bool four = L == 512 || L == 1024 || L == 2048 || L == 4096;
+  return L + (L >> 4) + (four ? (L >> 8) : 0) + 1;
+}
+
 // Position of FFT bin q of a column buffer (identity for other lengths).
 template <int L>
 __device__ __forceinline__ int colpos(int q) {
@@ -430,14 +444,14 @@ __device__ __forceinline__ void col_fft_fwd(float2* buf, const FftDev& f, const 
 #pragma unroll
       for (int n1 = 0; n1 < RA; ++n1) {
         const int idx = 256 * n1 + n2;
-        v[n1] = idx < n_in ? buf[spad(idx)] : make_float2(0.f, 0.f);
+        v[n1] = idx < n_in ? buf[xpad<L>(idx)] : make_float2(0.f, 0.f);
       }
       bfly<RA, false>(v);
       float2 w1, w2, w4, w8;
       stepA_tw(smtw, n2, w1, w2, w4, w8);
       apply_twiddles_given<RA, false>(v, w1, w2, w4, w8);
 #pragma unroll
-      for (int k1 = 0; k1 < RA; ++k1) buf[spad(256 * k1 + n2)] = v[k1];
+      for (int k1 = 0; k1 < RA; ++k1) buf[xpad<L>(256 * k1 + n2)] = v[k1];
     }
     __syncthreads();
     for (int t = tid; t < RA * 16; t += nthr) {
@@ -445,20 +459,20 @@ __device__ __forceinline__ void col_fft_fwd(float2* buf, const FftDev& f, const 
       const int base = 256 * blk;
       float2 v[16];
 #pragma unroll
-      for (int m1 = 0; m1 < 16; ++m1) v[m1] = buf[spad(base + 16 * m1 + m)];
+      for (int m1 = 0; m1 < 16; ++m1) v[m1] = buf[xpad<L>(base + 16 * m1 + m)];
       bfly<16, false>(v);
       apply_twiddles_given<16, false>(v, smtw[128 + m], smtw[144 + m], smtw[160 + m], smtw[176 + m]);
 #pragma unroll
-      for (int k21 = 0; k21 < 16; ++k21) buf[spad(base + 16 * k21 + m)] = v[k21];
+      for (int k21 = 0; k21 < 16; ++k21) buf[xpad<L>(base + 16 * k21 + m)] = v[k21];
       __syncwarp();
 #pragma unroll
-      for (int m2 = 0; m2 < 16; ++m2) v[m2] = buf[spad(base + 16 * m + m2)];
+      for (int m2 = 0; m2 < 16; ++m2) v[m2] = buf[xpad<L>(base + 16 * m + m2)];
       bfly<16, false>(v);
 #pragma unroll
       for (int k22 = 0; k22 < 16; ++k22) {
         float2 x = v[k22];
         if (post != nullptr) x = cmul(x, __ldg(&post[blk + RA * (m + 16 * k22)]));
-        buf[spad(base + 16 * m + k22)] = x;
+        buf[xpad<L>(base + 16 * m + k22)] = x;
       }
     }
     __syncthreads();
@@ -479,33 +493,33 @@ __device__ __forceinline__ void col_fft_inv(float2* buf, const FftDev& f, const 
       float2 v[16];
 #pragma unroll
       for (int k22 = 0; k22 < 16; ++k22) {
-        float2 x = buf[spad(base + 16 * m + k22)];
+        float2 x = buf[xpad<L>(base + 16 * m + k22)];
         if (pre != nullptr) x = cmulc(x, __ldg(&pre[blk + RA * (m + 16 * k22)]));
         v[k22] = x;
       }
       bfly<16, true>(v);
 #pragma unroll
-      for (int m2 = 0; m2 < 16; ++m2) buf[spad(base + 16 * m + m2)] = v[m2];
+      for (int m2 = 0; m2 < 16; ++m2) buf[xpad<L>(base + 16 * m + m2)] = v[m2];
       __syncwarp();
 #pragma unroll
-      for (int k21 = 0; k21 < 16; ++k21) v[k21] = buf[spad(base + 16 * k21 + m)];
+      for (int k21 = 0; k21 < 16; ++k21) v[k21] = buf[xpad<L>(base + 16 * k21 + m)];
       apply_twiddles_given<16, true>(v, smtw[128 + m], smtw[144 + m], smtw[160 + m], smtw[176 + m]);
       bfly<16, true>(v);
 #pragma unroll
-      for (int m1 = 0; m1 < 16; ++m1) buf[spad(base + 16 * m1 + m)] = v[m1];
+      for (int m1 = 0; m1 < 16; ++m1) buf[xpad<L>(base + 16 * m1 + m)] = v[m1];
     }
     __syncthreads();
     for (int n2 = tid; n2 < 256; n2 += nthr) {
       float2 v[RA];
 #pragma unroll
-      for (int k1 = 0; k1 < RA; ++k1) v[k1] = buf[spad(256 * k1 + n2)];
+      for (int k1 = 0; k1 < RA; ++k1) v[k1] = buf[xpad<L>(256 * k1 + n2)];
       float2 w1, w2, w4, w8;
       stepA_tw(smtw, n2, w1, w2, w4, w8);
       apply_twiddles_given<RA, true>(v, w1, w2, w4, w8);
       bfly<RA, true>(v);
 #pragma unroll
       for (int n1 = 0; n1 < RA; ++n1)
-        if (256 * n1 + n2 < n_out) buf[spad(256 * n1 + n2)] = v[n1];
+        if (256 * n1 + n2 < n_out) buf[xpad<L>(256 * n1 + n2)] = v[n1];
     }
     __syncthreads();
   }

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __res
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
   const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
-  const int SL = spad_len(P.N);
+  const int SL = xpad_len(P.N);
   float2* buf = sm + g * SL;
   float2* smtw = sm + RP * SL;  // four-step twiddles
   load_fourstep_tw(smtw, P.fN.fstw, threadIdx.x, blockDim.x);
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __res
     float a = 0.f, c = 0.f;
     if (ix >= r1.x && ix < r1.y) a = fb[(size_t)iy1 * P.n + ix];
     if (ix >= r2.x && ix < r2.y) c = fb[(size_t)iy2 * P.n + ix];
-    buf[spad(ix)] = make_float2(a, c);
+    buf[xpad<L>(ix)] = make_float2(a, c);
   }
   __syncthreads();
   col_fft_fwd<L>(buf, P.fN, smtw, gt, nt, nt, P.n, nullptr);
@@ -78,8 +78,8 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __res
     const int py1 = 2 * (pair0 + gg);
     if (py1 >= P.n) continue;
     const float2* bg = sm + gg * SL;
-    const float2 Z = bg[spad(colpos<L>(q))];
-    const float2 Zc = cconj(bg[spad(colpos<L>(q == 0 ? 0 : P.N - q))]);
+    const float2 Z = bg[xpad<L>(colpos<L>(q))];
+    const float2 Zc = cconj(bg[xpad<L>(colpos<L>(q == 0 ? 0 : P.N - q))]);
     const float2 x1 = cscale(cadd(Z, Zc), 0.5f);
     const float2 dd = csub(Z, Zc);
     const float2 x2 = make_float2(0.5f * dd.y, -0.5f * dd.x);
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __res
 // otherwise), with 3 CTAs per SM for the forward and 2 for the adjoint, whose
 // scatter needs more registers (best of both settings measured on GB300, n = 512).
 #define TAT_COLS_BOUNDS_F __launch_bounds__((L > 0 && L <= 4096) ? 256 : 512, (L > 0 && L <= 4096) ? 3 : 1)
-#define TAT_COLS_BOUNDS_A __launch_bounds__((L > 0 && L <= 4096) ? 256 : 512, (L > 0 && L <= 4096) ? 2 : 1)
+#define TAT_COLS_BOUNDS_A __launch_bounds__((L > 0 && L <= 4096) ? 256 : 512, (L > 0 && L <= 4096) ? 3 : 1)
 
 // Column strips are launched strip-major (all images' strip 0 first): the
 // strips near q_x = 0 hold up to 7x the average number of polar samples, so
@@ -110,7 +110,7 @@ __global__ void TAT_COLS_BOUNDS_F k_cols_fwd(DevPlan P, const float2* __restrict
   extern __shared__ float2 sm[];
   int strip, b;
   strip_and_image(batch, &strip, &b);
-  const int SL = spad_len(P.N);
+  const int SL = xpad_len(P.N);
   float2* slot0 = sm;
   float2* slot1 = sm + SL;
   float2* smtw = sm + 2 * SL;  // four-step twiddles
@@ -127,7 +127,7 @@ __global__ void TAT_COLS_BOUNDS_F k_cols_fwd(DevPlan P, const float2* __restrict
     float2* buf = (cc & 1) ? slot1 : slot0;
     const int c = c0 + cc;
     const float2* col = Xb + (size_t)c * P.n;  // R[c][0..n): contiguous
-    for (int iy = tid; iy < P.n; iy += NT) buf[spad(iy)] = col[iy];
+    for (int iy = tid; iy < P.n; iy += NT) buf[xpad<L>(iy)] = col[iy];
     __syncthreads();
     // column DFT over the n nonzero rows (the phase e^{i q dxi} of each output
     // row is applied by the gather below)
@@ -139,7 +139,7 @@ __global__ void TAT_COLS_BOUNDS_F k_cols_fwd(DevPlan P, const float2* __restrict
       for (int e = P.coloff[c - 1] + tid; e < e1; e += NT) {
         const PolarEntry pe = P.pts[e];
         const int ra = wrapN(pe.k0, N), rb = wrapN(pe.k0 + 1, N);
-        const int qa = spad(colpos<L>(ra)), qb = spad(colpos<L>(rb));
+        const int qa = xpad<L>(colpos<L>(ra)), qb = xpad<L>(colpos<L>(rb));
         const float a = pe.a, bb = pe.b;
         const float2 va = cadd(cscale(A[qa], 1.f - a), cscale(B[qa], a));
         const float2 vb = cadd(cscale(A[qb], 1.f - a), cscale(B[qb], a));
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(1024) k_rings_fwd(DevPlan P, const float2* __r
     return;
   }
   const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
-  const int SL = spad_len(P.n_phi);
+  const int SL = xpad_len(P.n_phi);
   float2* buf = sm + g * SL;
   float2* smptw = sm + RPC * SL;
   float2* smtw = smptw + P.fphi.ptw_len;
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(1024) k_rings_fwd(DevPlan P, const float2* __r
       else if (l < 3 * q4) v = cconj(Fr[l - q4]);
       else v = Fr[l - 3 * q4];
     }
-    buf[spad(l)] = v;
+    buf[xpad<L>(l)] = v;
   }
   __syncthreads();
   if constexpr (FourStep<L>::on) col_fft_fwd<L>(buf, P.fphi, smtw, gt, nt, nt, P.n_phi, nullptr);
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(1024) k_rings_fwd(DevPlan P, const float2* __r
     const int rr = rbase + gg;
     if (rr > P.J) continue;
     const float bt = (P.low_on && k <= 1 && rr < kLowA) ? 0.f : P.Bt[(size_t)k * J1 + rr];
-    Xb[(size_t)k * J1 + rr] = mul_ipow(cscale(sm[gg * SL + spad(colpos<L>(k))], bt), k);
+    Xb[(size_t)k * J1 + rr] = mul_ipow(cscale(sm[gg * SL + xpad<L>(colpos<L>(k))], bt), k);
   }
 }
 
@@ -238,13 +238,13 @@ __global__ void __launch_bounds__(1024) k_modes_fwd(DevPlan P, const float2* __r
   const int b = blockIdx.y, k = blockIdx.x;
   const int J1 = P.J + 1, L2 = 2 * P.M;
   const float2* Cm = X + (size_t)b * xs + (size_t)k * J1;
-  float2* smptw = sm + spad_len(L2);
+  float2* smptw = sm + xpad_len(L2);
   load_pass_tw(smptw, P.f2M, threadIdx.x, blockDim.x);
   for (int j = threadIdx.x; j < L2; j += blockDim.x) {
     float2 v = make_float2(0.f, 0.f);
     if (j >= 1 && j <= P.J) v = Cm[j];
     else if (j >= L2 - P.J) v = Cm[L2 - j];
-    sm[spad(j)] = v;
+    sm[xpad<L>(j)] = v;
   }
   __syncthreads();
   fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, P.n_t, nullptr, nullptr, smptw);
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(1024) k_modes_fwd(DevPlan P, const float2* __r
   const bool low = P.low_on && k <= 1;
   const float2* Ch = X + (size_t)b * xs + (size_t)(P.K + 1) * J1 + (size_t)k * P.n_low;
   for (int m = threadIdx.x; m < P.n_t; m += blockDim.x) {
-    float2 v = cscale(sm[spad(m)], 0.5f);
+    float2 v = cscale(sm[xpad<L>(m)], 0.5f);
     if (low) {
       for (int q = 0; q < P.n_low; ++q) {
         const float c = P.Lcos[(size_t)q * P.n_t + m];
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(1024) k_theta_fwd(DevPlan P, const float2* __r
   const int b = blockIdx.y;
   const int m0 = blockIdx.x * TT;
   const int npair = TT / 2;
-  const int SL = spad_len(P.n_det);
+  const int SL = xpad_len(P.n_det);
   const int nd = P.n_det;
   const float2* G = Y + (size_t)b * ys;
   float2* smptw = sm + npair * SL;
@@ -304,8 +304,8 @@ __global__ void __launch_bounds__(1024) k_theta_fwd(DevPlan P, const float2* __r
     float2 x2 = m2 < P.n_t ? folded_mode(P, G, bin, m2) : make_float2(0.f, 0.f);
     if (bin == 0 || bin == nd / 2) { x1.y = 0.f; x2.y = 0.f; }
     float2* z = sm + p * SL;
-    z[spad(colpos<L>(bin))] = make_float2(x1.x - x2.y, x1.y + x2.x);
-    if (bin > 0 && bin < nd / 2) z[spad(colpos<L>(nd - bin))] = make_float2(x1.x + x2.y, x2.x - x1.y);
+    z[xpad<L>(colpos<L>(bin))] = make_float2(x1.x - x2.y, x1.y + x2.x);
+    if (bin > 0 && bin < nd / 2) z[xpad<L>(colpos<L>(nd - bin))] = make_float2(x1.x + x2.y, x2.x - x1.y);
   }
   __syncthreads();
   {
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(1024) k_theta_fwd(DevPlan P, const float2* __r
     const int d = e / TT, tt = e % TT;
     const int m = m0 + tt;
     if (m >= P.n_t) continue;
-    const float2 z = sm[(tt >> 1) * SL + spad(d)];
+    const float2 z = sm[(tt >> 1) * SL + xpad<L>(d)];
     gb[(size_t)d * P.n_t + m] = P.gamma[d] * ((tt & 1) ? z.y : z.x);
   }
 }
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(1024) k_theta_adj(DevPlan P, const float* __re
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
   const int m0 = blockIdx.x * TT;
-  const int SL = spad_len(P.n_det);
+  const int SL = xpad_len(P.n_det);
   const int nd = P.n_det;
   const float* gb = g + (size_t)b * gs;
   float2* smptw = sm + (TT / 2) * SL;
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(1024) k_theta_adj(DevPlan P, const float* __re
     const int d = e / TT, tt = e % TT;
     const int m = m0 + tt;
     const float v = m < P.n_t ? P.gamma[d] * gb[(size_t)d * P.n_t + m] : 0.f;
-    float* z = reinterpret_cast<float*>(sm + (tt >> 1) * SL + spad(d));
+    float* z = reinterpret_cast<float*>(sm + (tt >> 1) * SL + xpad<L>(d));
     z[tt & 1] = v;
   }
   __syncthreads();
@@ -359,8 +359,8 @@ __global__ void __launch_bounds__(1024) k_theta_adj(DevPlan P, const float* __re
     if (m >= P.n_t) continue;
     const int bin = k % nd;
     const float2* z = sm + (tt >> 1) * SL;
-    const float2 Z = z[spad(colpos<L>(bin))];
-    const float2 Zc = cconj(z[spad(colpos<L>(bin == 0 ? 0 : nd - bin))]);
+    const float2 Z = z[xpad<L>(colpos<L>(bin))];
+    const float2 Zc = cconj(z[xpad<L>(colpos<L>(bin == 0 ? 0 : nd - bin))]);
     float2 x;
     if (tt & 1) {
       const float2 dd = csub(Z, Zc);
@@ -379,13 +379,13 @@ __global__ void __launch_bounds__(1024) k_modes_adj(DevPlan P, const float2* __r
   const int b = blockIdx.y, k = blockIdx.x;
   const int J1 = P.J + 1, L2 = 2 * P.M;
   const float2* Gp = Y + (size_t)b * ys + (size_t)k * P.n_t;
-  float2* smptw = sm + spad_len(L2);
+  float2* smptw = sm + xpad_len(L2);
   load_pass_tw(smptw, P.f2M, threadIdx.x, blockDim.x);
   for (int j = threadIdx.x; j < L2; j += blockDim.x) {
     float2 v = make_float2(0.f, 0.f);
     if (j < P.n_t) v = Gp[j];
     else if (j > L2 - P.n_t) v = Gp[L2 - j];
-    sm[spad(j)] = v;
+    sm[xpad<L>(j)] = v;
   }
   __syncthreads();
   const float2 g0 = Gp[0];
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(1024) k_modes_adj(DevPlan P, const float2* __r
   float2* Dm = X + (size_t)b * xs + (size_t)k * J1;
   const bool low = P.low_on && k <= 1;
   for (int j = threadIdx.x; j < J1; j += blockDim.x) {
-    float2 v = cscale(cadd(sm[spad(j)], g0), 0.5f);
+    float2 v = cscale(cadd(sm[xpad<L>(j)], g0), 0.5f);
     if (low && j < kLowA) v = make_float2(0.f, 0.f);
     Dm[j] = v;
   }
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
     }
     return;
   }
-  const int SL = spad_len(P.n_phi);
+  const int SL = xpad_len(P.n_phi);
   float2* smptw = sm + RPC * SL;
   float2* smtw = smptw + P.fphi.ptw_len;
   load_pass_tw(smptw, P.fphi, threadIdx.x, blockDim.x);
@@ -461,10 +461,10 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
       w = mul_mipow(cscale(Xb[(size_t)k * J1 + rr], P.Bt[(size_t)k * J1 + rr]), k);
     }
     float2* bg = sm + gg * SL;
-    bg[spad(colpos<L>(k))] = w;
+    bg[xpad<L>(colpos<L>(k))] = w;
     if (k >= 1 && k < P.K) {
       const float2 wc = cconj(w);
-      bg[spad(colpos<L>(P.n_phi - k))] = (k & 1) ? make_float2(-wc.x, -wc.y) : wc;
+      bg[xpad<L>(colpos<L>(P.n_phi - k))] = (k & 1) ? make_float2(-wc.x, -wc.y) : wc;
     }
   }
   __syncthreads();
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
     for (int l = gt; l < P.nh; l += nt) {
       int s = l - q4;
       if (s < 0) s += P.n_phi;
-      Yb[(size_t)r * P.nh + l] = buf[spad(s)];
+      Yb[(size_t)r * P.nh + l] = buf[xpad<L>(s)];
     }
   }
 }
@@ -531,7 +531,7 @@ __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* _
       emit = emit && tail;
     }
     if (emit) {
-      const int qa = spad(colpos<L>(wrapN(key, P.N))), qb = spad(colpos<L>(wrapN(key + 1, P.N)));
+      const int qa = xpad<L>(colpos<L>(wrapN(key, P.N))), qb = xpad<L>(colpos<L>(wrapN(key + 1, P.N)));
       if (left != nullptr) {
         atomicAdd(&left[qa].x, v[0]);
         atomicAdd(&left[qa].y, v[1]);
@@ -555,7 +555,7 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
   int strip, b;
   strip_and_image(batch, &strip, &b);
   const int N = P.N;
-  const int SL = spad_len(N);
+  const int SL = xpad_len(N);
   const int tid = threadIdx.x, NT = blockDim.x;
   float2* smtw = sm + 2 * SL;  // four-step twiddles
   load_fourstep_tw(smtw, P.fN.fstw, tid, NT);
@@ -584,11 +584,11 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
       // F'(0, q) += conj(F'(0, -q)).
       for (int q = tid; q < N / 2; q += NT) {
         if (q == 0) {
-          const int p0 = spad(colpos<L>(0));
+          const int p0 = xpad<L>(colpos<L>(0));
           const float2 s = cur[p0];
           cur[p0] = make_float2(2.f * s.x, 0.f);
         } else {
-          const int pa = spad(colpos<L>(q)), pb = spad(colpos<L>(N - q));
+          const int pa = xpad<L>(colpos<L>(q)), pb = xpad<L>(colpos<L>(N - q));
           const float2 A = cur[pa], B = cur[pb];
           cur[pa] = cadd(A, cconj(B));
           cur[pb] = cadd(B, cconj(A));
@@ -599,21 +599,21 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
     // inverse column DFT (conj(phase) already applied by the scatter), first n rows only
     col_fft_inv<L>(cur, P.fN, smtw, tid, NT, nt, P.n, nullptr);
     float2* col = Xb + (size_t)c * P.n;  // R'[c][0..n): contiguous
-    for (int iy = tid; iy < P.n; iy += NT) col[iy] = cur[spad(iy)];
+    for (int iy = tid; iy < P.n; iy += NT) col[iy] = cur[xpad<L>(iy)];
     __syncthreads();
   }
 }
 
 // Row stage of A* and A^{-1}: rebuilds the Hermitian row spectra of this CTA's
 // RP row pairs from the column-major R'[q][iy] and runs the inverse row DFTs;
-// row pair g of the CTA ends in sm + g * spad_len(N), rows 2*pair and 2*pair+1
+// row pair g of the CTA ends in sm + g * xpad_len(N), rows 2*pair and 2*pair+1
 // in the real and imaginary parts.
 template <int L>
 __device__ __forceinline__ void rows_inverse_dft(const DevPlan& P, const float2* __restrict__ Xb, float2* sm, int RP,
                                                  int nt) {
   const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
   const int N = P.N;
-  const int SL = spad_len(N);
+  const int SL = xpad_len(N);
   float2* buf = sm + g * SL;
   float2* smtw = sm + RP * SL;  // four-step twiddles
   load_fourstep_tw(smtw, P.fN.fstw, threadIdx.x, blockDim.x);
@@ -629,9 +629,9 @@ __device__ __forceinline__ void rows_inverse_dft(const DevPlan& P, const float2*
     float2 h1 = py1 < P.n ? cmulc(col[py1], P.phase[q]) : make_float2(0.f, 0.f);
     float2 h2 = py1 + 1 < P.n ? cmulc(col[py1 + 1], P.phase[q]) : make_float2(0.f, 0.f);
     if (q == 0) { h1.y = 0.f; h2.y = 0.f; }
-    bg[spad(colpos<L>(q))] = make_float2(h1.x - h2.y, h1.y + h2.x);
-    if (q > 0) bg[spad(colpos<L>(N - q))] = make_float2(h1.x + h2.y, h2.x - h1.y);  // conj(h1) + i conj(h2)
-    else bg[spad(colpos<L>(N / 2))] = make_float2(0.f, 0.f);
+    bg[xpad<L>(colpos<L>(q))] = make_float2(h1.x - h2.y, h1.y + h2.x);
+    if (q > 0) bg[xpad<L>(colpos<L>(N - q))] = make_float2(h1.x + h2.y, h2.x - h1.y);  // conj(h1) + i conj(h2)
+    else bg[xpad<L>(colpos<L>(N / 2))] = make_float2(0.f, 0.f);
   }
   __syncthreads();
   col_fft_inv<L>(buf, P.fN, smtw, gt, nt, nt, P.n, nullptr);
@@ -644,7 +644,7 @@ __global__ void __launch_bounds__(1024) k_rows_adj(DevPlan P, const float2* __re
   const int b = blockIdx.y;
   const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
   rows_inverse_dft<L>(P, X + (size_t)b * xs, sm, RP, nt);
-  const float2* buf = sm + g * spad_len(P.N);
+  const float2* buf = sm + g * xpad_len(P.N);
   const int pair = blockIdx.x * RP + g;
   const int iy1 = 2 * pair, iy2 = 2 * pair + 1;
   const bool v1 = iy1 < P.n, v2 = iy2 < P.n;
@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(1024) k_rows_adj(DevPlan P, const float2* __re
   const int2 r1 = v1 ? P.rowrange[iy1] : make_int2(0, 0);
   const int2 r2 = v2 ? P.rowrange[iy2] : make_int2(0, 0);
   for (int ix = gt; ix < P.n; ix += nt) {
-    const float2 z = buf[spad(ix)];
+    const float2 z = buf[xpad<L>(ix)];
     if (v1) fb[(size_t)iy1 * P.n + ix] = (ix >= r1.x && ix < r1.y) ? P.adj_scale * z.x : 0.f;
     if (v2) fb[(size_t)iy2 * P.n + ix] = (ix >= r2.x && ix < r2.y) ? P.adj_scale * z.y : 0.f;
   }
@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(1024) k_modes_inv(DevPlan P, const float2* __r
   const int b = blockIdx.y, k = blockIdx.x;
   const int J1 = P.J + 1, L2 = 2 * P.M;
   const float2* Gp = Y + (size_t)b * ys + (size_t)k * P.n_t;
-  float2* smptw = sm + spad_len(L2);
+  float2* smptw = sm + xpad_len(L2);
   load_pass_tw(smptw, P.f2M, threadIdx.x, blockDim.x);
   for (int j = threadIdx.x; j < L2; j += blockDim.x) {
     float2 v = make_float2(0.f, 0.f);
@@ -689,12 +689,12 @@ __global__ void __launch_bounds__(1024) k_modes_inv(DevPlan P, const float2* __r
       if (m == P.n_t - 1) v = cscale(v, 0.5f);
       if (j > P.M) v = make_float2(-v.x, -v.y);
     }
-    sm[spad(j)] = v;
+    sm[xpad<L>(j)] = v;
   }
   __syncthreads();
   fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, J1, nullptr, nullptr, smptw);
   float2* Dm = X + (size_t)b * xs + (size_t)k * J1;
-  for (int j = threadIdx.x; j < J1; j += blockDim.x) Dm[j] = sm[spad(j)];
+  for (int j = threadIdx.x; j < J1; j += blockDim.x) Dm[j] = sm[xpad<L>(j)];
 }
 
 // Polar sample Y[ring j][l'] of the half circle; ring 0 (lambda = 0) is zero for
@@ -760,7 +760,7 @@ __global__ void TAT_COLS_BOUNDS_I k_cols_inv(DevPlan P, const float2* __restrict
   int strip, b;
   strip_and_image(batch, &strip, &b);
   const int N = P.N;
-  const int SL = spad_len(N);
+  const int SL = xpad_len(N);
   const int tid = threadIdx.x, NT = blockDim.x;
   float2* buf = sm;
   float2* smtw = sm + SL;  // four-step twiddles
@@ -774,12 +774,12 @@ __global__ void TAT_COLS_BOUNDS_I k_cols_inv(DevPlan P, const float2* __restrict
   for (int c = c0; c < c1; ++c) {
     for (int q = tid; q < N; q += NT) {
       const int qs = q < N / 2 ? q : q - N;
-      buf[spad(colpos<L>(q))] = cmulc(inv_node(P, Yb, c, qs), __ldg(&P.phase[q]));
+      buf[xpad<L>(colpos<L>(q))] = cmulc(inv_node(P, Yb, c, qs), __ldg(&P.phase[q]));
     }
     __syncthreads();
     col_fft_inv<L>(buf, P.fN, smtw, tid, NT, nt, P.n, nullptr);
     float2* col = Xb + (size_t)c * P.n;
-    for (int iy = tid; iy < P.n; iy += NT) col[iy] = buf[spad(iy)];
+    for (int iy = tid; iy < P.n; iy += NT) col[iy] = buf[xpad<L>(iy)];
     __syncthreads();
   }
 }
@@ -795,7 +795,7 @@ __global__ void __launch_bounds__(1024) k_rows_inv(DevPlan P, const float2* __re
   const int b = blockIdx.y;
   const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
   rows_inverse_dft<L>(P, X + (size_t)b * xs, sm, RP, nt);
-  const float2* buf = sm + g * spad_len(P.N);
+  const float2* buf = sm + g * xpad_len(P.N);
   const int pair = blockIdx.x * RP + g;
   const int iy1 = 2 * pair, iy2 = 2 * pair + 1;
   const bool v1 = iy1 < P.n, v2 = iy2 < P.n;
@@ -804,7 +804,7 @@ __global__ void __launch_bounds__(1024) k_rows_inv(DevPlan P, const float2* __re
   const int2 s2 = v2 ? P.rowrange[iy2] : make_int2(0, 0), o2 = v2 ? P.outrange[iy2] : make_int2(0, 0);
   float ring = 0.f;
   for (int ix = gt; ix < P.n; ix += nt) {
-    const float2 z = buf[spad(ix)];
+    const float2 z = buf[xpad<L>(ix)];
     const float a = P.inv_scale * z.x, c = P.inv_scale * z.y;
     if (v1) {
       fb[(size_t)iy1 * P.n + ix] = a;

@@ -26,25 +26,25 @@ inline Shapes shapes(const tat_plan_s* Pl, int batch) {
   const int npairs = (P.n + 1) / 2;
   s.rows_grid = dim3((npairs + c.rows_pairs - 1) / c.rows_pairs, batch);
   s.rows_block = c.rows_pairs * c.nt_rows;
-  s.rows_smem = ((size_t)c.rows_pairs * spad_len(P.N) + kFourStepTw) * sizeof(float2);
+  s.rows_smem = ((size_t)c.rows_pairs * xpad_len(P.N) + kFourStepTw) * sizeof(float2);
   // 1-D, strip-major: blockIdx.x = strip * batch + image
   s.cols_grid_f = dim3(((P.ncol - 1 + c.strip - 1) / c.strip) * batch);
   s.cols_grid_a = dim3(((P.ncol + c.strip - 1) / c.strip) * batch);
   s.cols_block = c.nt_N < 256 ? 256 : c.nt_N;
-  s.cols_smem_f = (2 * (size_t)spad_len(P.N) + kFourStepTw) * sizeof(float2);
-  s.cols_smem_a = (2 * (size_t)spad_len(P.N) + kFourStepTw) * sizeof(float2);
-  s.cols_smem_i = ((size_t)spad_len(P.N) + kFourStepTw) * sizeof(float2);
+  s.cols_smem_f = (2 * (size_t)xpad_len(P.N) + kFourStepTw) * sizeof(float2);
+  s.cols_smem_a = (2 * (size_t)xpad_len(P.N) + kFourStepTw) * sizeof(float2);
+  s.cols_smem_i = ((size_t)xpad_len(P.N) + kFourStepTw) * sizeof(float2);
   s.ntiles = (P.J + c.rings_per_cta - 1) / c.rings_per_cta;
   s.rings_grid = dim3(s.ntiles + P.n_low, batch);
   s.rings_block = c.rings_per_cta * c.nt_phi;
-  s.rings_smem = ((size_t)c.rings_per_cta * spad_len(P.n_phi) + P.fphi.ptw_len + kFourStepTw) * sizeof(float2);
+  s.rings_smem = ((size_t)c.rings_per_cta * xpad_len(P.n_phi) + P.fphi.ptw_len + kFourStepTw) * sizeof(float2);
   if (s.rings_smem < 96 * sizeof(float)) s.rings_smem = 96 * sizeof(float);
   s.modes_grid = dim3(P.K + 1, batch);
   s.modes_block = c.nt_2M;
-  s.modes_smem = ((size_t)spad_len(2 * P.M) + P.f2M.ptw_len) * sizeof(float2);
+  s.modes_smem = ((size_t)xpad_len(2 * P.M) + P.f2M.ptw_len) * sizeof(float2);
   s.theta_grid = dim3((P.n_t + c.t_tile - 1) / c.t_tile, batch);
   s.theta_block = (c.t_tile / 2) * c.nt_det;
-  s.theta_smem = ((size_t)(c.t_tile / 2) * spad_len(P.n_det) + P.fdet.ptw_len + kFourStepTw) * sizeof(float2);
+  s.theta_smem = ((size_t)(c.t_tile / 2) * xpad_len(P.n_det) + P.fdet.ptw_len + kFourStepTw) * sizeof(float2);
   return s;
 }
 
