@@ -428,7 +428,23 @@ __device__ __forceinline__ void stepA_tw(const float2* smtw, int n2, float2& w1,
   w8 = cmul(smtw[48 + a], smtw[112 + b]);
 }
 
+// e^{-+2 pi i k / R} (R in {2, 4, 8, 16}; INV takes the + sign) from the 16th roots of unity.
+template <int R, bool INV>
+__device__ __forceinline__ float2 unit_root(int k) {
+  constexpr float c16[16] = {1.f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508978f,
+                             0.f, -0.38268343236508978f, -0.70710678118654752f, -0.92387953251128674f,
+                             -1.f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508978f,
+                             0.f, 0.38268343236508978f, 0.70710678118654752f, 0.92387953251128674f};
+  const int j = (k * (16 / R)) & 15;
+  const float s = c16[(j + 12) & 15];  // sin(2 pi j / 16) = cos(2 pi (j - 4) / 16)
+  return make_float2(c16[j], INV ? s : -s);
+}
+
 // Forward: x[0, n_in) in natural order -> X[q] * post[q] at colpos(q).
+// When n_in <= 512 only the inputs n1 = 0, 1 of the DFT_RA of step A are
+// non-zero (the zero padding of the rows and columns), and step A reduces to
+// X[k1] = x0 + x1 e^{-2 pi i k1 / RA}; the inverse likewise keeps only the
+// outputs n1 = 0, 1 when n_out <= 512.
 // `smtw`: the shared-memory copy of the four-step twiddle table; `nthr`: the
 // threads of the calling group (tid < nthr, all take part in the four-step
 // loops); `sthr` (<= nthr): the thread count of the Stockham fallback.
@@ -441,12 +457,19 @@ __device__ __forceinline__ void col_fft_fwd(float2* buf, const FftDev& f, const 
     constexpr int RA = FourStep<L>::RA;
     for (int n2 = tid; n2 < 256; n2 += nthr) {
       float2 v[RA];
+      if (n_in <= 512) {
+        const float2 x0 = n2 < n_in ? buf[xpad<L>(n2)] : make_float2(0.f, 0.f);
+        const float2 x1 = 256 + n2 < n_in ? buf[xpad<L>(256 + n2)] : make_float2(0.f, 0.f);
 #pragma unroll
-      for (int n1 = 0; n1 < RA; ++n1) {
-        const int idx = 256 * n1 + n2;
-        v[n1] = idx < n_in ? buf[xpad<L>(idx)] : make_float2(0.f, 0.f);
+        for (int k1 = 0; k1 < RA; ++k1) v[k1] = cadd(x0, cmul(x1, unit_root<RA, false>(k1)));
+      } else {
+#pragma unroll
+        for (int n1 = 0; n1 < RA; ++n1) {
+          const int idx = 256 * n1 + n2;
+          v[n1] = idx < n_in ? buf[xpad<L>(idx)] : make_float2(0.f, 0.f);
+        }
+        bfly<RA, false>(v);
       }
-      bfly<RA, false>(v);
       float2 w1, w2, w4, w8;
       stepA_tw(smtw, n2, w1, w2, w4, w8);
       apply_twiddles_given<RA, false>(v, w1, w2, w4, w8);
@@ -516,10 +539,21 @@ __device__ __forceinline__ void col_fft_inv(float2* buf, const FftDev& f, const 
       float2 w1, w2, w4, w8;
       stepA_tw(smtw, n2, w1, w2, w4, w8);
       apply_twiddles_given<RA, true>(v, w1, w2, w4, w8);
-      bfly<RA, true>(v);
+      if (n_out <= 512) {
+        float2 o0 = v[0], o1 = v[0];
 #pragma unroll
-      for (int n1 = 0; n1 < RA; ++n1)
-        if (256 * n1 + n2 < n_out) buf[xpad<L>(256 * n1 + n2)] = v[n1];
+        for (int k1 = 1; k1 < RA; ++k1) {
+          o0 = cadd(o0, v[k1]);
+          o1 = cadd(o1, cmul(v[k1], unit_root<RA, true>(k1)));
+        }
+        if (n2 < n_out) buf[xpad<L>(n2)] = o0;
+        if (256 + n2 < n_out) buf[xpad<L>(256 + n2)] = o1;
+      } else {
+        bfly<RA, true>(v);
+#pragma unroll
+        for (int n1 = 0; n1 < RA; ++n1)
+          if (256 * n1 + n2 < n_out) buf[xpad<L>(256 * n1 + n2)] = v[n1];
+      }
     }
     __syncthreads();
   }
