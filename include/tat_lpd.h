@@ -19,7 +19,8 @@
  * stored in BF16, hidden activations and their gradients stored in BF16),
  * FP32 accumulation, FP32 biases, residual planes, outputs of the out layer,
  * gradients of the FP32 planes and of all weights.  The 32 -> 32 layer runs on
- * the tensor cores (mma.sync m16n8k16, BF16 x BF16 -> FP32).
+ * the tensor cores (mma.sync m16n8k16, BF16 x BF16 -> FP32) with its input
+ * tiles staged by TMA; its activation pointers must be 16-byte aligned.
  *
  * Layouts (all DEVICE pointers owned by the caller): planes FP32 [batch][H][W];
  * hidden activations BF16 NHWC [batch][H][W][32] (BF16 as its 16-bit pattern,
@@ -79,6 +80,11 @@ tat_status tat_conv_out_fwd(int batch, int H, int W, const tat_bf16* h, const ta
 tat_status tat_conv_out_bwd(int batch, int H, int W, const float* g_out, const tat_bf16* h, const tat_bf16* w,
                             tat_bf16* g_h, float* scratch, size_t scratch_floats, float* gw, float* gb,
                             tat_stream_t stream);
+
+/* TAT_ERR_TIMEOUT (and the flag cleared) if a tensor-core convolution gave up
+ * waiting for one of its TMA tile copies since the last call, else TAT_OK.
+ * Synchronises with the device. */
+tat_status tat_lpd_check(void);
 
 /* Adam step (bias-corrected, step >= 1) on FP32 parameters; w_bf16 (optional)
  * receives the updated parameters rounded to BF16. */

@@ -123,6 +123,7 @@ def load() -> ctypes.CDLL:
         "tat_adam": (_I, [_LL, _F, _F, _F, _F, _I, _P, _P, _P, _P, _P, _P]),
         "tat_to_bf16": (_I, [_LL, _P, _P, _P]),
         "tat_fill": (_I, [_LL, _F, _P, _P]),
+        "tat_lpd_check": (_I, []),
         "tat_mse": (_I, [_LL, _P, _P, _F, _P, _P, _P]),
         "tat_axpby_clamp": (_I, [_LL, _F, _P, _F, _P, _F, _P, _LL, _P, _P]),
         "tat_axpby_clamp_backward": (_I, [_LL, _P, _F, _P, _LL, _P, _F, _P, _F, _P, _P]),
@@ -392,6 +393,11 @@ def tat_conv_out_bwd(batch, H, W, g_out, h, w, g_h, scratch, scratch_floats, gw,
 def tat_adam(count, lr, beta1, beta2, eps, step, param, grad, m, v, w_bf16, stream=0):
     _check(load().tat_adam(count, lr, beta1, beta2, eps, step, param, grad, m, v, w_bf16 or None, stream or None),
            "tat_adam")
+
+
+def tat_lpd_check():
+    """Raises TatError (timeout) if a tensor-core convolution gave up waiting for a TMA tile copy."""
+    _check(load().tat_lpd_check(), "tat_lpd_check")
 
 
 def tat_fill(count, value, out, stream=0):

@@ -4,18 +4,23 @@
 // precision.
 //
 // The 32 -> 32 layer is an implicit GEMM on the tensor cores: per CTA an
-// 8 x 16 pixel tile (one warp per image row of 16 pixels = one m16 tile), the
-// 10 x 18 x 32 input halo and the 9 x 32 x 32 weights staged in shared memory
-// with rows padded to 40 BF16 (80 bytes, conflict-free for the fragment loads
-// and for ldmatrix), K = 9 taps x 32 channels in 18 mma.sync.m16n8k16 steps.
+// 8 x 16 pixel tile (one warp per image row of 16 pixels = one m16 tile) and
+// K = 9 taps x 32 channels in 18 mma.sync.m16n8k16 steps.  The 10 x 18 x 32
+// input halo of each tile arrives by TMA (a 4-D tensor map over the NHWC
+// activations, zero fill outside the image, 64-byte swizzle, which keeps the
+// fragment loads conflict-free), double-buffered on two mbarriers so that the
+// next tile's halo is in flight while the current one's MMAs run; the CTAs are
+// persistent and stage the 9 x 32 x 32 weights once, rows padded to 40 BF16.
 // Its weight gradient is the GEMM dW[tap] = G'^T In_tap over the pixels, one
 // warp per tap, operands fetched with ldmatrix.trans.  The thin layers (2 or 3
 // planes -> 32, and 32 -> 1) run on the CUDA cores.
+#include <cuda.h>  // CUtensorMap and its enums (types only; the encoder is looked up at run time)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
-#include <cstdio>
 #include <cstdint>
+#include <cstdio>
+#include <mutex>
 
 #include "tat_lpd.h"
 
@@ -292,12 +297,72 @@ __device__ __forceinline__ void load_halo(tat_bf16* hs, const tat_bf16* __restri
   }
 }
 
+// ---- TMA staging of the halo
+
+constexpr int HALO_PIX = (TY + 2) * (TX + 2);  // 180 pixels of 64 bytes
+constexpr int HALO_BYTES = HALO_PIX * C * 2;   // 11 520 bytes per tile
+constexpr int HALO_SLOT = 12288;               // tile slot, a multiple of the 512-byte swizzle period
+constexpr int kSpinLimit = 1 << 22;            // tries of a bounded mbarrier wait before giving up
+
+__device__ int g_lpd_timeout = 0;  // set when a CTA gave up waiting for a tile
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase `parity` of `bar` to complete; false if it did not.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (int i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// One 4-D tile (channels, x, y, image) of `map` into shared memory at `dst`,
+// completing `bytes` on `bar`.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 32-bit word (channels c, c+1) of halo pixel p in a tile written by TMA with
+// the 64-byte swizzle: 16-byte chunk j of the 64-byte row p sits at j ^ ((p >> 1) & 3).
+__device__ __forceinline__ unsigned ldsw(const unsigned char* tile, int p, int c) {
+  const int byte = 2 * c;
+  const int chunk = (byte >> 4) ^ ((p >> 1) & 3);
+  return *reinterpret_cast<const unsigned*>(tile + p * 64 + (chunk << 4) + (byte & 15));
+}
+
+// g * [h > 0] for the two BF16 values of a word (h > 0: sign clear and not zero).
+__device__ __forceinline__ unsigned relu_masked(unsigned g, unsigned h) {
+  const unsigned lo = h & 0xffffu, hi = h >> 16;
+  const unsigned m = ((lo - 1u) < 0x7fffu ? 0x0000ffffu : 0u) | ((hi - 1u) < 0x7fffu ? 0xffff0000u : 0u);
+  return g & m;
+}
+
+// One 8 x 16 output tile of the mid layer from a staged halo (and, for BWD, the
+// staged ReLU mask) and the staged weights.
 // FWD: out = relu(conv(in) + b).  BWD (data gradient): out = conv^T(g * [h > 0]),
 // i.e. the same implicit GEMM with the taps flipped and in/out channels swapped.
-// One 8 x 16 output tile of the mid layer from the staged halo and weights.
 template <bool BWD>
-__device__ __forceinline__ void mid_tile(const tat_bf16* hs, const tat_bf16* wsm, const float* __restrict__ bias,
-                                         tat_bf16* __restrict__ out, int b, int y0, int x0, int H, int W) {
+__device__ __forceinline__ void mid_tile(const unsigned char* tile, const unsigned char* mtile, const tat_bf16* wsm,
+                                         const float* __restrict__ bias, tat_bf16* __restrict__ out, int b, int y0,
+                                         int x0, int H, int W) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   float acc[4][4];
 #pragma unroll
@@ -307,15 +372,17 @@ __device__ __forceinline__ void mid_tile(const tat_bf16* hs, const tat_bf16* wsm
 #pragma unroll
   for (int tap = 0; tap < 9; ++tap) {
     const int dy = tap / 3, dx = tap % 3;  // halo offsets (tap - 1 in each direction, plus the halo's +1)
-    const tat_bf16* r0 = hs + ((warp + dy) * (TX + 2) + g + dx) * CP;
-    const tat_bf16* r1 = r0 + 8 * CP;  // pixel g + 8
+    const int p0 = (warp + dy) * (TX + 2) + g + dx, p1 = p0 + 8;  // pixels g and g + 8 of the warp's row
 #pragma unroll
     for (int kc = 0; kc < 2; ++kc) {
-      unsigned a[4];
-      a[0] = ld32(r0 + kc * 16 + 2 * t);
-      a[1] = ld32(r1 + kc * 16 + 2 * t);
-      a[2] = ld32(r0 + kc * 16 + 8 + 2 * t);
-      a[3] = ld32(r1 + kc * 16 + 8 + 2 * t);
+      const int c0 = kc * 16 + 2 * t, c1 = c0 + 8;
+      unsigned a[4] = {ldsw(tile, p0, c0), ldsw(tile, p1, c0), ldsw(tile, p0, c1), ldsw(tile, p1, c1)};
+      if (BWD) {
+        a[0] = relu_masked(a[0], ldsw(mtile, p0, c0));
+        a[1] = relu_masked(a[1], ldsw(mtile, p1, c0));
+        a[2] = relu_masked(a[2], ldsw(mtile, p0, c1));
+        a[3] = relu_masked(a[3], ldsw(mtile, p1, c1));
+      }
 #pragma unroll
       for (int nt = 0; nt < 4; ++nt) {
         const tat_bf16* wr = wsm + (tap * C + nt * 8 + g) * CP + kc * 16 + 2 * t;
@@ -344,12 +411,24 @@ __device__ __forceinline__ void mid_tile(const tat_bf16* hs, const tat_bf16* wsm
   }
 }
 
+// Dynamic shared memory of the mid-layer kernel: alignment slack, two stages
+// (value tile, and for BWD the mask tile), the padded weights, two mbarriers.
 template <bool BWD>
-__global__ void __launch_bounds__(256) k_conv_mid(int B, int H, int W, const tat_bf16* __restrict__ in,
-                                                  const tat_bf16* __restrict__ mask, const tat_bf16* __restrict__ w,
-                                                  const float* __restrict__ bias, tat_bf16* __restrict__ out) {
-  __shared__ __align__(16) tat_bf16 hs[(TY + 2) * (TX + 2) * CP];
-  __shared__ __align__(16) tat_bf16 wsm[9 * C * CP];
+constexpr size_t mid_smem_bytes() {
+  return 1024 + 2 * (BWD ? 2 : 1) * HALO_SLOT + 9 * C * CP * 2 + 2 * sizeof(uint64_t);
+}
+
+template <bool BWD>
+__global__ void __launch_bounds__(256) k_conv_mid(int B, int H, int W, const __grid_constant__ CUtensorMap map_in,
+                                                  const __grid_constant__ CUtensorMap map_mask,
+                                                  const tat_bf16* __restrict__ w, const float* __restrict__ bias,
+                                                  tat_bf16* __restrict__ out) {
+  extern __shared__ unsigned char dsm[];
+  unsigned char* sm = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);  // 1024-aligned (swizzle period)
+  constexpr int NT = BWD ? 2 : 1;
+  constexpr int STAGE = NT * HALO_SLOT;
+  tat_bf16* wsm = reinterpret_cast<tat_bf16*>(sm + 2 * STAGE);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * STAGE + 9 * C * CP * 2);
   // weights, read in global order (coalesced): wsm[tap][n][k] with n the output
   // channel of this GEMM and k its input channel
   for (int e = threadIdx.x; e < 9 * C * C; e += blockDim.x) {
@@ -357,16 +436,46 @@ __global__ void __launch_bounds__(256) k_conv_mid(int B, int H, int W, const tat
     if (BWD) wsm[((8 - tap) * C + ci) * CP + co] = w[e];
     else wsm[(tap * C + co) * CP + ci] = w[e];
   }
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
   const int tilesx = (W + TX - 1) / TX, tilesy = (H + TY - 1) / TY;
   const long long ntiles = (long long)B * tilesx * tilesy;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int b = (int)(tile / (tilesx * tilesy));
+  auto coords = [&](long long tile, int* b, int* y0, int* x0) {
+    *b = (int)(tile / (tilesx * tilesy));
     const int rr = (int)(tile % (tilesx * tilesy));
-    const int y0 = (rr / tilesx) * TY, x0 = (rr % tilesx) * TX;
+    *y0 = (rr / tilesx) * TY;
+    *x0 = (rr % tilesx) * TX;
+  };
+  auto issue = [&](long long tile, int s) {
+    if (threadIdx.x != 0) return;
+    int b, y0, x0;
+    coords(tile, &b, &y0, &x0);
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic reads of the slot come first
+    mbar_expect_tx(&bar[s], NT * HALO_BYTES);
+    tma_load_4d(sm + s * STAGE, &map_in, 0, x0 - 1, y0 - 1, b, &bar[s]);
+    if (BWD) tma_load_4d(sm + s * STAGE + HALO_SLOT, &map_mask, 0, x0 - 1, y0 - 1, b, &bar[s]);
+  };
+  if ((long long)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+  int i = 0;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+    const int s = i & 1;
+    const long long next = tile + gridDim.x;
+    if (next < ntiles) issue(next, s ^ 1);  // that slot was released by the barrier ending the previous tile
+    const bool ok = mbar_wait(&bar[s], (unsigned)((i >> 1) & 1));
+    if (__syncthreads_or(!ok)) {
+      // give up: record it, let the copy still in flight land (bounded), and leave
+      if (threadIdx.x == 0) atomicExch(&g_lpd_timeout, 1);
+      if (next < ntiles) mbar_wait(&bar[s ^ 1], (unsigned)(((i + 1) >> 1) & 1));
+      return;
+    }
+    int b, y0, x0;
+    coords(tile, &b, &y0, &x0);
+    mid_tile<BWD>(sm + s * STAGE, sm + s * STAGE + HALO_SLOT, wsm, bias, out, b, y0, x0, H, W);
     __syncthreads();
-    load_halo<BWD>(hs, in, mask, b, y0, x0, H, W);
-    __syncthreads();
-    mid_tile<BWD>(hs, wsm, bias, out, b, y0, x0, H, W);
   }
 }
 
@@ -608,11 +717,69 @@ __global__ void k_mse(long long n, const float* __restrict__ a, const float* __r
 
 bool bad_sizes(int batch, int H, int W) { return batch < 1 || H < 1 || W < 1; }
 
-// Persistent tensor-core conv: up to 4 CTAs per SM (37 KB of shared memory and
-// ~40 registers each), every CTA loads the weights once and loops over tiles.
+// Persistent tensor-core conv: up to 3 CTAs per SM, every CTA stages the
+// weights once and loops over tiles.
 int mid_ctas(int batch, int H, int W) {
   const long long tiles = (long long)batch * ((H + TY - 1) / TY) * ((W + TX - 1) / TX);
-  return (int)(tiles < 4 * 152 ? tiles : 4 * 152);
+  return (int)(tiles < 3 * 152 ? tiles : 3 * 152);
+}
+
+// cuTensorMapEncodeTiled, looked up through the runtime (no link-time driver dependency).
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder() {
+  static EncodeTiled fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// Tensor map of a [batch][H][W][32] BF16 activation for (TY+2) x (TX+2) x 32 halo boxes.
+bool halo_map(CUtensorMap* m, const tat_bf16* base, int batch, int H, int W) {
+  const EncodeTiled fn = encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)batch};
+  const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+  const cuuint32_t box[4] = {(cuuint32_t)C, TX + 2, TY + 2, 1};
+  const cuuint32_t estride[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<tat_bf16*>(base), dims, strides, box, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <bool BWD>
+tat_status launch_mid(int batch, int H, int W, const tat_bf16* in, const tat_bf16* mask, const tat_bf16* w,
+                      const float* b, tat_bf16* out, cudaStream_t s, const char* what) {
+  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(mask)) & 15) return TAT_ERR_INVALID_ARG;
+  CUtensorMap mi, mm;
+  if (!halo_map(&mi, in, batch, H, W) || !halo_map(&mm, BWD ? mask : in, batch, H, W)) {
+    fprintf(stderr, "%s: tensor map encoding failed\n", what);
+    return TAT_ERR_CUDA;
+  }
+  static int attr_done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+    if (cudaFuncSetAttribute(k_conv_mid<BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)mid_smem_bytes<BWD>()) != cudaSuccess) {
+      cudaGetLastError();
+      return TAT_ERR_CUDA;
+    }
+    attr_done[dev] = 1;
+  }
+  k_conv_mid<BWD><<<mid_ctas(batch, H, W), 256, mid_smem_bytes<BWD>(), s>>>(batch, H, W, mi, mm, w, b, out);
+  return launched(what);
 }
 
 int wgrad_ctas(int batch, int H, int W) {
@@ -674,17 +841,27 @@ tat_status tat_conv_in_bwd_weights(int batch, int H, int W, int cin, const float
 tat_status tat_conv_mid_fwd(int batch, int H, int W, const tat_bf16* h_in, const tat_bf16* w, const float* b,
                             tat_bf16* h_out, tat_stream_t stream) {
   if (bad_sizes(batch, H, W) || !h_in || !w || !b || !h_out) return TAT_ERR_INVALID_ARG;
-  k_conv_mid<false><<<mid_ctas(batch, H, W), 256, 0, static_cast<cudaStream_t>(stream)>>>(batch, H, W, h_in, nullptr,
-                                                                                           w, b, h_out);
-  return launched("tat_conv_mid_fwd");
+  return launch_mid<false>(batch, H, W, h_in, nullptr, w, b, h_out, static_cast<cudaStream_t>(stream),
+                           "tat_conv_mid_fwd");
 }
 
 tat_status tat_conv_mid_bwd_data(int batch, int H, int W, const tat_bf16* g_out, const tat_bf16* h_out,
                                  const tat_bf16* w, tat_bf16* g_in, tat_stream_t stream) {
   if (bad_sizes(batch, H, W) || !g_out || !h_out || !w || !g_in) return TAT_ERR_INVALID_ARG;
-  k_conv_mid<true><<<mid_ctas(batch, H, W), 256, 0, static_cast<cudaStream_t>(stream)>>>(batch, H, W, g_out, h_out,
-                                                                                          w, nullptr, g_in);
-  return launched("tat_conv_mid_bwd_data");
+  return launch_mid<true>(batch, H, W, g_out, h_out, w, nullptr, g_in, static_cast<cudaStream_t>(stream),
+                          "tat_conv_mid_bwd_data");
+}
+
+tat_status tat_lpd_check(void) {
+  int flag = 0;
+  if (cudaMemcpyFromSymbol(&flag, g_lpd_timeout, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return TAT_ERR_CUDA;
+  }
+  if (!flag) return TAT_OK;
+  const int zero = 0;
+  cudaMemcpyToSymbol(g_lpd_timeout, &zero, sizeof(int));
+  return TAT_ERR_TIMEOUT;
 }
 
 tat_status tat_conv_mid_bwd_weights(int batch, int H, int W, const tat_bf16* h_in, const tat_bf16* g_out,
