@@ -355,6 +355,12 @@ __device__ __forceinline__ unsigned relu_masked(unsigned g, unsigned h) {
   return g & m;
 }
 
+__device__ __forceinline__ void ldsm_x4(unsigned* r, const unsigned char* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+
 // One 8 x 16 output tile of the mid layer from a staged halo (and, for BWD, the
 // staged ReLU mask) and the staged weights.
 // FWD: out = relu(conv(in) + b).  BWD (data gradient): out = conv^T(g * [h > 0]),
@@ -375,19 +381,27 @@ __device__ __forceinline__ void mid_tile(const unsigned char* tile, const unsign
     const int p0 = (warp + dy) * (TX + 2) + g + dx, p1 = p0 + 8;  // pixels g and g + 8 of the warp's row
 #pragma unroll
     for (int kc = 0; kc < 2; ++kc) {
-      const int c0 = kc * 16 + 2 * t, c1 = c0 + 8;
-      unsigned a[4] = {ldsw(tile, p0, c0), ldsw(tile, p1, c0), ldsw(tile, p0, c1), ldsw(tile, p1, c1)};
+      // A (16 pixels x 16 channels) by one ldmatrix.x4: lane l addresses row l & 7 of
+      // matrix l >> 3 = (pixels +8 if odd, channels +8 if >= 2), swizzled 16-byte chunk
+      const int m = lane >> 3;
+      const int pa = (m & 1 ? p1 : p0) + (lane & 7) - g;
+      const int chunk = (2 * kc + (m >> 1)) ^ ((pa >> 1) & 3);
+      unsigned a[4];
+      ldsm_x4(a, tile + pa * 64 + (chunk << 4));
       if (BWD) {
-        a[0] = relu_masked(a[0], ldsw(mtile, p0, c0));
-        a[1] = relu_masked(a[1], ldsw(mtile, p1, c0));
-        a[2] = relu_masked(a[2], ldsw(mtile, p0, c1));
-        a[3] = relu_masked(a[3], ldsw(mtile, p1, c1));
-      }
+        unsigned mk[4];
+        ldsm_x4(mk, mtile + pa * 64 + (chunk << 4));
 #pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const tat_bf16* wr = wsm + (tap * C + nt * 8 + g) * CP + kc * 16 + 2 * t;
-        unsigned bb[2] = {ld32(wr), ld32(wr + 8)};
-        mma_bf16(acc[nt], a, bb);
+        for (int j = 0; j < 4; ++j) a[j] = relu_masked(a[j], mk[j]);
+      }
+      // B for n-tiles (2np, 2np+1): matrices (nt 2np, k 0-7), (2np, k 8-15), (2np+1, k 0-7), (2np+1, k 8-15)
+#pragma unroll
+      for (int np = 0; np < 2; ++np) {
+        unsigned bq[4];
+        ldsm_x4(bq, reinterpret_cast<const unsigned char*>(
+                        wsm + (tap * C + (2 * np + (m >> 1)) * 8 + (lane & 7)) * CP + kc * 16 + (m & 1) * 8));
+        mma_bf16(acc[2 * np], a, bq);
+        mma_bf16(acc[2 * np + 1], a, bq + 2);
       }
     }
   }
