@@ -166,8 +166,9 @@ def traffic_for(kernel, workload="pair_n512_b32", sources=None):
     return float(v) if v is not None else None
 
 
-def stage_times(pkg, op, B, x, y, x2, ws, stream, ksteps):
-    """Mean ms of each of the ten stages, from events recorded between the stages."""
+def stage_times(pkg, op, B, x, y, x2, ws, stream, ksteps, adjoint=True):
+    """Mean ms of each of the ten stages (the five of A alone with adjoint=False), from events
+    recorded between the stages."""
     import torch
     n, nd, nt = op.n, op.n_det, op.n_t
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(12)] for _ in range(ksteps)]
@@ -179,14 +180,16 @@ def stage_times(pkg, op, B, x, y, x2, ws, stream, ksteps):
     for row in evs:
         pkg.tat_debug_forward_batched_timed(op.plan, B, x.data_ptr(), n * n, y.data_ptr(), nd * nt, ws.data_ptr(),
                                             sptr, [e.cuda_event for e in row[:6]])
-        pkg.tat_debug_adjoint_batched_timed(op.plan, B, y.data_ptr(), nd * nt, x2.data_ptr(), n * n, ws.data_ptr(),
-                                            sptr, [e.cuda_event for e in row[6:]])
+        if adjoint:
+            pkg.tat_debug_adjoint_batched_timed(op.plan, B, y.data_ptr(), nd * nt, x2.data_ptr(), n * n,
+                                                ws.data_ptr(), sptr, [e.cuda_event for e in row[6:]])
     torch.cuda.synchronize()
     stage_ms = {}
     for i, name in enumerate(FWD_STAGES):
         stage_ms[name] = statistics.mean(r[i].elapsed_time(r[i + 1]) for r in evs)
-    for i, name in enumerate(ADJ_STAGES):
-        stage_ms[name] = statistics.mean(r[6 + i].elapsed_time(r[7 + i]) for r in evs)
+    if adjoint:
+        for i, name in enumerate(ADJ_STAGES):
+            stage_ms[name] = statistics.mean(r[6 + i].elapsed_time(r[7 + i]) for r in evs)
     return stage_ms
 
 
@@ -741,30 +744,53 @@ def service_config(sizes):
             "max_batch": 32, "graphs": True, "l2": "inputs and working set exceed L2, no flush"}
 
 
+SVC_ORACLE_SAMPLE = "one n=256 oracle A (n_det=n_t=512), scaled by n^2 log n to the 64-request mix"
+
+
+def service_oracle_seconds(sizes):
+    """Oracle seconds for the whole request mix, from one timed n=256 request."""
+    from oracle import tat_oracle as O
+    from tat_inputs import ellipse_phantom
+    n = 256
+    P = O.OraclePlan(n, 2 * n, 2 * n, T=T_WIN, support_radius=RSUP)
+    f = ellipse_phantom(n, 0)
+    t0 = time.perf_counter()
+    O.forward(P, f)
+    t1 = time.perf_counter() - t0
+    # scale by the O(n^2 log n) cost of each request's size
+    return t1 * sum((m / n) ** 2 * math.log2(m) / math.log2(n) for m in sizes)
+
+
+def service_roofline(pkg, sizes, stream, dev):
+    """FP32-ALU roofline of the dominant stage of the service's largest group (n = 1024 requests,
+    batched up to the service's max batch), timed with events between the stages of A."""
+    import torch
+    n = max(sizes)
+    B = min(sizes.count(n), 32)
+    op = pkg.TatOperator(n, 2 * n, 2 * n, T=T_WIN, support_radius=RSUP, device=dev)
+    x = torch.zeros((B, n, n), device=dev)
+    y = torch.empty((B, 2 * n, 2 * n), device=dev)
+    ws = op.workspace(B)
+    stage_times(pkg, op, B, x, y, x, ws, stream, 2, adjoint=False)
+    ms = stage_times(pkg, op, B, x, y, x, ws, stream, 5, adjoint=False)
+    r = alu_roofline(ms, stage_flops(op.info, B, n, 2 * n, 2 * n), f"service_n{n}_b{B}")
+    r["group"] = f"{B} requests of n={n} (n_det=n_t={2 * n}) in one batched A"
+    return r
+
+
 def run_service(args, rank, world, local):
     sizes = service_requests(rank)
     if args.impl == "reference":
         if rank != 0:
             return
-        import numpy as np
-        from oracle import tat_oracle as O
-        from tat_inputs import ellipse_phantom
-        n = 128
-        P = O.OraclePlan(n, 2 * n, 2 * n, T=T_WIN, support_radius=RSUP)
-        f = ellipse_phantom(n, 0)
-        t0 = time.perf_counter()
-        O.forward(P, f)
-        t128 = time.perf_counter() - t0
-        # scale by the O(n^2 log n) cost of each request's size
-        cost = sum((m / 128.0) ** 2 * math.log2(m) / math.log2(128) for m in sizes)
-        t = t128 * cost
+        t = service_oracle_seconds(sizes)
         value = SVC_REQ / t
         line = {"impl": "reference", "metric": SVC_METRIC, "value": value, "unit": "requests/s",
                 "n_gpus": args.gpus, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * t, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": service_config(sizes),
                 "cpu_baseline": {"value": value, "unit": "requests/s", "cores": cpu_threads(), "kind": "oracle",
-                                 "sample": "one n=128 oracle A, scaled by n^2 log n to the request mix"},
+                                 "sample": SVC_ORACLE_SAMPLE},
                 "e2e": {"value": value, "unit": "requests/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
@@ -843,6 +869,12 @@ def run_service(args, rank, world, local):
         torch.cuda.synchronize()
     e2e_wall = (time.perf_counter() - t2) / max(1, min(args.steps, 3))
     svc.close()
+    roofline = service_roofline(pkg, sizes, torch.cuda.current_stream(dev), dev)
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        t_cpu = service_oracle_seconds(sizes)
+        cpu = {"value": SVC_REQ / t_cpu, "unit": "requests/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": SVC_ORACLE_SAMPLE}
     lat_np = np.array(lat)
     if rank == 0:
         line = {"metric": SVC_METRIC, "value": value, "unit": "requests/s", "n_gpus": world, "steps": args.steps,
@@ -859,7 +891,7 @@ def run_service(args, rank, world, local):
                 "e2e": {"value": SVC_REQ * world / e2e_wall, "unit": "requests/s",
                         "h2d_bytes_per_step": int(sum(4 * n * n for n in sizes)),
                         "d2h_bytes_per_step": int(sum(4 * 4 * n * n for n in sizes))},
-                "roofline": None, "cpu_baseline": None,
+                "roofline": roofline, "cpu_baseline": cpu,
                 "gpu_launches": 5 * st["launches"] // max(1, args.steps + max(args.warmup, 3)) * args.steps,
                 "clocks": clk, "kernel_source_hash": kernel_source_hash()}
         print(json.dumps(line), flush=True)
@@ -883,32 +915,132 @@ def lpd_config(train_steps, arc="full"):
             "l2": "activations of 10 unrolled iterations (~850 MB) exceed L2, no flush"}
 
 
+LPD_ORACLE_SAMPLE = ("FP64 oracle loss + gradient (BF16 emulation on) of one image with K = 2 unrolled "
+                     "iterations, scaled x K/2 x batch")
+
+
+def lpd_oracle_seconds():
+    """Oracle seconds of one training step's loss and gradient (batch 8, K = 10), from one image
+    with K = 2 (the cost is linear in both)."""
+    import torch
+    from oracle import lpd as OL
+    from oracle import solvers as S
+    from oracle import tat_oracle as O
+    from tat_inputs import ellipse_phantom, gaussian
+    P = O.OraclePlan(LPD_N, LPD_DET, LPD_T, T=T_WIN, support_radius=RSUP)
+    op = S.plan_op(P)
+    _, npar = OL.layout()
+    p = torch.tensor(0.05 * gaussian(1, npar))
+    f = torch.tensor(ellipse_phantom(LPD_N, 0))[None]
+    y = op.A(f)
+    t0 = time.perf_counter()
+    OL.loss_and_grad(p, op, y, f, K=2, bf16=True)
+    return (time.perf_counter() - t0) * (LPD_K / 2) * LPD_B
+
+
+def lpd_kernel_roofline(pkg, stream, dev, peaks):
+    """Per-call time of each convolution call of the dual net (B = 8 planes of 256 x 256, the larger
+    of the two nets; each call runs K times per training step), measured live with events on
+    `stream`, and the roofline of the slowest one against the tighter of its ALU (or tensor) and
+    HBM bounds."""
+    import torch
+    B, H, W, C = LPD_B, LPD_DET, LPD_T, 32
+    P = B * H * W
+    gen = torch.Generator().manual_seed(7)
+
+    def bf16(shape, scale=1.0):
+        return (scale * torch.randn(shape, generator=gen)).to(torch.bfloat16).to(dev)
+
+    x = [torch.randn((B, H, W), generator=gen).to(dev) for _ in range(3)]
+    h_in, h_out, g_h, g_in = (bf16((B, H, W, C)) for _ in range(4))
+    w_in, w_mid, w_out = bf16((9 * 3 * C,), 0.1), bf16((9 * C * C,), 0.05), bf16((9 * C,), 0.1)
+    bias = torch.zeros(C, device=dev)
+    gout = torch.randn((B, H, W), generator=gen).to(dev)
+    out = torch.empty((B, H, W), device=dev)
+    gx = [torch.empty((B, H, W), device=dev) for _ in range(3)]
+    nscr = pkg.tat_lpd_scratch_floats(B, H, W)
+    scr = torch.empty(nscr, device=dev)
+    gw, gb = torch.zeros(9 * C * C, device=dev), torch.zeros(C, device=dev)
+    s = stream.cuda_stream
+    a = lambda t: t.data_ptr()
+    # name: (call, algorithmic flops, algorithmic HBM bytes, compute bound, kernels launched)
+    calls = {
+        "tat_conv_in_fwd (cin=3)": (
+            lambda: pkg.tat_conv_in_fwd(B, H, W, 3, a(x[0]), a(x[1]), a(x[2]), a(w_in), a(bias), a(h_in), s),
+            2 * P * 27 * C, P * (12 + 2 * C), "alu", "k_conv_in_fwd<3>"),
+        "tat_conv_in_bwd_data (cin=3)": (
+            lambda: pkg.tat_conv_in_bwd_data(B, H, W, 3, a(g_h), a(h_in), a(w_in), a(gx[0]), a(gx[1]), a(gx[2]), 0, s),
+            2 * P * 27 * C, P * (4 * C + 12), "alu", "k_conv_in_bwd_data<3>"),
+        "tat_conv_in_bwd_weights (cin=3)": (
+            lambda: pkg.tat_conv_in_bwd_weights(B, H, W, 3, a(x[0]), a(x[1]), a(x[2]), a(g_h), a(h_in), a(scr), nscr,
+                                                a(gw), a(gb), s),
+            2 * P * 27 * C, P * (12 + 4 * C), "alu", "k_conv_in_bwd_weights<3> + k_reduce_partials"),
+        "tat_conv_mid_fwd": (
+            lambda: pkg.tat_conv_mid_fwd(B, H, W, a(h_in), a(w_mid), a(bias), a(h_out), s),
+            2 * P * 9 * C * C, P * 4 * C, "tensor", "k_conv_mid<0>"),
+        "tat_conv_mid_bwd_data": (
+            lambda: pkg.tat_conv_mid_bwd_data(B, H, W, a(g_h), a(h_out), a(w_mid), a(g_in), s),
+            2 * P * 9 * C * C, P * 6 * C, "tensor", "k_conv_mid<1>"),
+        "tat_conv_mid_bwd_weights": (
+            lambda: pkg.tat_conv_mid_bwd_weights(B, H, W, a(h_in), a(g_h), a(h_out), a(scr), nscr, a(gw), a(gb), s),
+            2 * P * 9 * C * C, P * 6 * C, "tensor", "k_conv_mid_wgrad + k_reduce_partials"),
+        "tat_conv_out_fwd": (
+            lambda: pkg.tat_conv_out_fwd(B, H, W, a(h_out), a(w_out), a(bias), a(x[0]), a(out), s),
+            2 * P * 9 * C, P * (2 * C + 8), "alu", "k_conv_out_fwd"),
+        "tat_conv_out_bwd": (
+            lambda: pkg.tat_conv_out_bwd(B, H, W, a(gout), a(h_out), a(w_out), a(g_in), a(scr), nscr, a(gw), a(gb), s),
+            4 * P * 9 * C, P * (4 + 4 * C), "alu", "k_conv_out_bwd_data + k_conv_out_wgrad + k_reduce_partials"),
+    }
+    reps = 20
+    times = {}
+    for name, (fn, *_rest) in calls.items():
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1) / reps
+    pkg.tat_lpd_check()
+    dom = max(times, key=times.get)
+    _, flops, nbytes, kind, kernels = calls[dom]
+    t = times[dom] / 1e3
+    peak_alu = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    peak_tc = peaks["bf16_tflops"] if peaks else 1900.0
+    peak_hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    t_compute = flops / ((peak_tc if kind == "tensor" else peak_alu) * 1e12)
+    t_hbm = nbytes / (peak_hbm * 1e9)
+    if t_hbm > t_compute:
+        r = {"bound": "hbm", "achieved": nbytes / t / 1e9, "peak": peak_hbm, "unit": "GB/s"}
+    else:
+        r = {"bound": kind, "achieved": flops / t / 1e12, "peak": peak_tc if kind == "tensor" else peak_alu,
+             "unit": "TFLOP/s"}
+    r["frac"] = r["achieved"] / r["peak"]
+    r.update({"traffic": None, "kernel": dom, "kernels": kernels, "call_us": 1e3 * times[dom],
+              "algorithmic": {"flops": flops, "hbm_bytes": nbytes},
+              "peak_source": "measured" if peaks else "fallback",
+              "call_us_all": {k: round(1e3 * v, 2) for k, v in times.items()},
+              "workload": f"dual net, {B} x {H} x {W} pixels, 32 channels"})
+    return r
+
+
 def run_lpd(args, rank, world, local):
     if args.impl == "reference":
         if rank != 0:
             return
-        import numpy as np
-        import torch
-        from oracle import lpd as OL
-        from oracle import solvers as S
-        from oracle import tat_oracle as O
-        from tat_inputs import ellipse_phantom
-        P = O.OraclePlan(LPD_N, LPD_DET, LPD_T, T=T_WIN, support_radius=RSUP)
-        op = S.plan_op(P)
-        _, npar = OL.layout()
-        p = torch.zeros(npar, dtype=torch.float64)
-        f = torch.tensor(ellipse_phantom(LPD_N, 0))[None]
-        y = op.A(f)
-        t0 = time.perf_counter()
-        OL.loss_and_grad(p, op, y, f, K=1, bf16=False)
-        t1 = time.perf_counter() - t0
-        t = t1 * LPD_K * LPD_B     # one image, one unrolled iteration -> a batch of 8 with K = 10
+        t = 0.0
+        for _ in range(max(1, args.steps)):
+            t += lpd_oracle_seconds()
+        t /= max(1, args.steps)
         line = {"impl": "reference", "metric": LPD_METRIC, "value": 1.0 / t, "unit": "train steps/s",
-                "n_gpus": args.gpus, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * t, "higher_is_better": True,
+                "n_gpus": args.gpus, "steps": max(1, args.steps), "warmup": 0, "ms_per_step": 1e3 * t, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": lpd_config(args.train_steps),
                 "cpu_baseline": {"value": 1.0 / t, "unit": "train steps/s", "cores": cpu_threads(), "kind": "oracle",
-                                 "sample": "one FP64 oracle loss+gradient of one image with K = 1, scaled x K x batch"},
+                                 "sample": LPD_ORACLE_SAMPLE},
                 "e2e": {"value": 1.0 / t, "unit": "train steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
@@ -1035,6 +1167,13 @@ def run_lpd(args, rank, world, local):
         rec_nnls[i:i + LPD_B] = solver.nnls(y_test[i:i + LPD_B].contiguous(), 100, 1.0 / L2, graph=True)
     err_tv, err_nnls = rel_err(rec_tv, f_test), rel_err(rec_nnls, f_test)
 
+    roofline = lpd_kernel_roofline(pkg, stream, dev, measured_peaks())
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        t_cpu = lpd_oracle_seconds()
+        cpu = {"value": 1.0 / t_cpu, "unit": "train steps/s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": LPD_ORACLE_SAMPLE}
+
     # e2e: one training step with the batch copied in from pinned host memory and the loss read back
     yb_h, fb_h = yb.cpu().pin_memory(), fb.cpu().pin_memory()
     t_e2e = time.perf_counter()
@@ -1055,7 +1194,7 @@ def run_lpd(args, rank, world, local):
                 "inference_reconstructions_per_s": inf_per_s,
                 "e2e": {"value": e2e_v, "unit": "train steps/s",
                         "h2d_bytes_per_step": int(yb_h.numel() * 4 + fb_h.numel() * 4), "d2h_bytes_per_step": 4},
-                "roofline": None, "cpu_baseline": None,
+                "roofline": roofline, "cpu_baseline": cpu,
                 "gpu_launches": args.steps * (LPD_K * 2 * 5 + LPD_K * 6 + LPD_K * 2 * (5 + 10)),
                 "clocks": clk, "kernel_source_hash": kernel_source_hash()}
         print(json.dumps(line), flush=True)
