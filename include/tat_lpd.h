@@ -18,9 +18,12 @@
  * Precision: BF16 operands (inputs rounded to BF16 as they are read, weights
  * stored in BF16, hidden activations and their gradients stored in BF16),
  * FP32 accumulation, FP32 biases, residual planes, outputs of the out layer,
- * gradients of the FP32 planes and of all weights.  The 32 -> 32 layer runs on
- * the tensor cores (mma.sync m16n8k16, BF16 x BF16 -> FP32) with its input
- * tiles staged by TMA; its activation pointers must be 16-byte aligned.
+ * gradients of the FP32 planes and of all weights.  All layers run on the
+ * tensor cores (mma.sync m16n8k16, BF16 x BF16 -> FP32, exact products); the
+ * FP32 gradient entering the out layer's backward is split into two BF16 terms
+ * (hi + lo, 16 significand bits).  Tiles of the hidden activations are staged
+ * by TMA, so those pointers (h, h_in, h_out, g_h, g_out of the BF16 layers)
+ * must be 16-byte aligned (TAT_ERR_INVALID_ARG otherwise).
  *
  * Layouts (all DEVICE pointers owned by the caller): planes FP32 [batch][H][W];
  * hidden activations BF16 NHWC [batch][H][W][32] (BF16 as its 16-bit pattern,
@@ -61,6 +64,13 @@ tat_status tat_conv_in_bwd_data(int batch, int H, int W, int cin, const tat_bf16
 tat_status tat_conv_in_bwd_weights(int batch, int H, int W, int cin, const float* x0, const float* x1,
                                    const float* x2, const tat_bf16* g_h, const tat_bf16* h, float* scratch,
                                    size_t scratch_floats, float* gw, float* gb, tat_stream_t stream);
+/* Both of the above in one pass over g_h and h: the data-plane gradients (skipped when
+ * gx0, gx1 and gx2 are all NULL; w may then be NULL) and the weight gradients (skipped when
+ * gw is NULL; x0, x1, x2 (cin == 3), scratch and gb are then required). */
+tat_status tat_conv_in_bwd(int batch, int H, int W, int cin, const float* x0, const float* x1, const float* x2,
+                           const tat_bf16* g_h, const tat_bf16* h, const tat_bf16* w, float* gx0, float* gx1,
+                           float* gx2, int accumulate, float* scratch, size_t scratch_floats, float* gw, float* gb,
+                           tat_stream_t stream);
 
 /* h_out = relu(conv_mid(h_in) + b)  (tensor cores). */
 tat_status tat_conv_mid_fwd(int batch, int H, int W, const tat_bf16* h_in, const tat_bf16* w, const float* b,

@@ -20,7 +20,7 @@ __all__ = ["TatError", "TatOperator", "header_symbols", "load", "tat_adjoint", "
            "tat_status_string", "tat_workspace_size"]
 
 from . import autograd, lpd, solvers  # noqa: E402
-from .binding import (tat_adam, tat_conv_in_bwd_data, tat_conv_in_bwd_weights, tat_conv_in_fwd,  # noqa: E402
+from .binding import (tat_adam, tat_conv_in_bwd, tat_conv_in_bwd_data, tat_conv_in_bwd_weights, tat_conv_in_fwd,  # noqa: E402
                       tat_conv_mid_bwd_data, tat_conv_mid_bwd_weights, tat_conv_mid_fwd, tat_conv_out_bwd,
                       tat_conv_out_fwd, tat_fill, tat_lpd_check, tat_lpd_scratch_floats, tat_mse, tat_to_bf16)
 from .autograd import A, Astar  # noqa: E402
@@ -32,7 +32,7 @@ from .binding import (TatService, tat_plan_autotune, tat_service_config_default,
 from .binding import (tat_axpby_clamp, tat_axpby_clamp_backward, tat_pd_dual_data, tat_tv_dual,  # noqa: E402
                       tat_tv_dual_backward, tat_tv_primal, tat_tv_primal_backward)
 
-__all__ += ["lpd", "tat_adam", "tat_conv_in_bwd_data", "tat_conv_in_bwd_weights", "tat_conv_in_fwd",
+__all__ += ["lpd", "tat_adam", "tat_conv_in_bwd", "tat_conv_in_bwd_data", "tat_conv_in_bwd_weights", "tat_conv_in_fwd",
             "tat_conv_mid_bwd_data", "tat_conv_mid_bwd_weights", "tat_conv_mid_fwd", "tat_conv_out_bwd",
             "tat_conv_out_fwd", "tat_fill", "tat_lpd_check", "tat_lpd_scratch_floats", "tat_mse", "tat_to_bf16", "TatService", "tat_plan_autotune", "tat_service_config_default", "tat_service_create",
             "tat_service_destroy", "tat_service_flush", "tat_service_get_stats", "tat_service_latency",

@@ -115,6 +115,8 @@ def load() -> ctypes.CDLL:
         "tat_conv_in_fwd": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P]),
         "tat_conv_in_bwd_data": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _I, _P]),
         "tat_conv_in_bwd_weights": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
+        "tat_conv_in_bwd": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P, ctypes.c_size_t, _P, _P,
+                                 _P]),
         "tat_conv_mid_fwd": (_I, [_I, _I, _I, _P, _P, _P, _P, _P]),
         "tat_conv_mid_bwd_data": (_I, [_I, _I, _I, _P, _P, _P, _P, _P]),
         "tat_conv_mid_bwd_weights": (_I, [_I, _I, _I, _P, _P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
@@ -366,6 +368,13 @@ def tat_conv_in_bwd_data(batch, H, W, cin, g_h, h, w, gx0, gx1, gx2, accumulate,
 def tat_conv_in_bwd_weights(batch, H, W, cin, x0, x1, x2, g_h, h, scratch, scratch_floats, gw, gb, stream=0):
     _check(load().tat_conv_in_bwd_weights(batch, H, W, cin, x0, x1, x2 or None, g_h, h, scratch, scratch_floats, gw,
                                           gb, stream or None), "tat_conv_in_bwd_weights")
+
+
+def tat_conv_in_bwd(batch, H, W, cin, x0, x1, x2, g_h, h, w, gx0, gx1, gx2, accumulate, scratch, scratch_floats, gw,
+                    gb, stream=0):
+    _check(load().tat_conv_in_bwd(batch, H, W, cin, x0 or None, x1 or None, x2 or None, g_h, h, w or None, gx0 or None,
+                                  gx1 or None, gx2 or None, accumulate, scratch or None, scratch_floats, gw or None,
+                                  gb or None, stream or None), "tat_conv_in_bwd")
 
 
 def tat_conv_mid_fwd(batch, H, W, h_in, w, b, h_out, stream=0):

@@ -13,7 +13,9 @@
 // persistent and stage the 9 x 32 x 32 weights once, rows padded to 40 BF16.
 // Its weight gradient is the GEMM dW[tap] = G'^T In_tap over the pixels, one
 // warp per tap, operands fetched with ldmatrix.trans.  The thin layers (2 or 3
-// planes -> 32, and 32 -> 1) run on the CUDA cores.
+// planes -> 32, and 32 -> 1) are implicit GEMMs on the same tiles with one
+// dimension of 8 to 27; their backward passes compute the data and the weight
+// gradients in one pass over the tiles.
 #include <cuda.h>  // CUtensorMap and its enums (types only; the encoder is looked up at run time)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -29,8 +31,9 @@ namespace {
 constexpr int C = 32;       // hidden channels
 constexpr int CP = 40;      // padded channel stride in shared memory (BF16 elements)
 constexpr int TY = 8, TX = 16;  // output tile of the tensor-core kernels
-constexpr int kMaxCtas = 2 * 152;   // CTAs of the tensor-core weight gradient
-constexpr int kRedCtas = 8 * 152;   // CTAs of the CUDA-core weight gradients (latency-bound loops)
+constexpr int kMaxCtas = 2 * 152;   // CTAs of the 32 -> 32 weight gradient
+constexpr int XH = TY + 2, XW = TX + 2;  // 10 x 18 halo of a tile
+constexpr int XP = 20;              // row pitch (BF16 elements) of the halo copies of FP32 planes
 
 tat_status launched(const char* what) {
   const cudaError_t e = cudaGetLastError();
@@ -43,7 +46,6 @@ tat_status launched(const char* what) {
 
 __device__ __forceinline__ float bf(const tat_bf16 v) { return __bfloat162float(__ushort_as_bfloat16(v)); }
 __device__ __forceinline__ tat_bf16 tobf(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
-__device__ __forceinline__ float rbf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 
 // 8 BF16 values (16 bytes) <-> floats
 __device__ __forceinline__ void unpack8(const uint4& u, float* f) {
@@ -61,19 +63,6 @@ __device__ __forceinline__ uint4 pack8(const float* f) {
   return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-struct Px {
-  int b, y, x;
-};
-__device__ __forceinline__ Px px_of(long long i, int H, int W) {
-  Px p;
-  const long long hw = (long long)H * W;
-  p.b = (int)(i / hw);
-  const long long r = i - (long long)p.b * hw;
-  p.y = (int)(r / W);
-  p.x = (int)(r - (long long)p.y * W);
-  return p;
-}
-
 #define GRID_STRIDE(i, n) \
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
@@ -82,158 +71,7 @@ int blocks_for(long long n, int threads) {
   return (int)(b < 1 ? 1 : (b > 152LL * 16 ? 152LL * 16 : b));
 }
 
-// ------------------------------------------------------------------ in layer (CUDA cores)
-
-template <int CIN>
-__global__ void k_conv_in_fwd(int B, int H, int W, const float* __restrict__ x0, const float* __restrict__ x1,
-                              const float* __restrict__ x2, const tat_bf16* __restrict__ w,
-                              const float* __restrict__ bias, tat_bf16* __restrict__ h) {
-  __shared__ float ws[9 * CIN * C];
-  __shared__ float bs[C];
-  for (int i = threadIdx.x; i < 9 * CIN * C; i += blockDim.x) ws[i] = bf(w[i]);
-  for (int i = threadIdx.x; i < C; i += blockDim.x) bs[i] = bias[i];
-  __syncthreads();
-  const float* xs[3] = {x0, x1, x2};
-  const long long hw = (long long)H * W;
-  GRID_STRIDE(i, (long long)B * hw) {
-    const Px p = px_of(i, H, W);
-    float acc[C];
-#pragma unroll
-    for (int co = 0; co < C; ++co) acc[co] = bs[co];
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int yy = p.y + dy;
-      if (yy < 0 || yy >= H) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int xx = p.x + dx;
-        if (xx < 0 || xx >= W) continue;
-        const int tap = 3 * (dy + 1) + (dx + 1);
-        const long long o = (long long)p.b * hw + (long long)yy * W + xx;
-#pragma unroll
-        for (int c = 0; c < CIN; ++c) {
-          const float v = rbf(xs[c][o]);
-          const float* wr = ws + (tap * CIN + c) * C;
-#pragma unroll
-          for (int co = 0; co < C; ++co) acc[co] = fmaf(v, wr[co], acc[co]);
-        }
-      }
-    }
-    uint4* dst = reinterpret_cast<uint4*>(h + i * C);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float f[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) f[k] = fmaxf(acc[8 * q + k], 0.f);
-      dst[q] = pack8(f);
-    }
-  }
-}
-
-// G'(pixel) = g_h * [h > 0] as 32 floats
-__device__ __forceinline__ void masked_grad(const tat_bf16* g, const tat_bf16* h, long long pix, float* out) {
-  const uint4* gp = reinterpret_cast<const uint4*>(g + pix * C);
-  const uint4* hp = reinterpret_cast<const uint4*>(h + pix * C);
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    float gv[8], hv[8];
-    unpack8(gp[q], gv);
-    unpack8(hp[q], hv);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) out[8 * q + k] = hv[k] > 0.f ? gv[k] : 0.f;
-  }
-}
-
-template <int CIN>
-__global__ void k_conv_in_bwd_data(int B, int H, int W, const tat_bf16* __restrict__ g_h,
-                                   const tat_bf16* __restrict__ h, const tat_bf16* __restrict__ w, float* gx0,
-                                   float* gx1, float* gx2, int accumulate) {
-  __shared__ float ws[9 * CIN * C];
-  for (int i = threadIdx.x; i < 9 * CIN * C; i += blockDim.x) ws[i] = bf(w[i]);
-  __syncthreads();
-  float* gxs[3] = {gx0, gx1, gx2};
-  const long long hw = (long long)H * W;
-  GRID_STRIDE(i, (long long)B * hw) {
-    const Px p = px_of(i, H, W);
-    float acc[CIN];
-#pragma unroll
-    for (int c = 0; c < CIN; ++c) acc[c] = 0.f;
-    // the output pixel (y - dy, x - dx) saw this input through tap (dy, dx)
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int yy = p.y - dy;
-      if (yy < 0 || yy >= H) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int xx = p.x - dx;
-        if (xx < 0 || xx >= W) continue;
-        const int tap = 3 * (dy + 1) + (dx + 1);
-        float G[C];
-        masked_grad(g_h, h, (long long)p.b * hw + (long long)yy * W + xx, G);
-#pragma unroll
-        for (int c = 0; c < CIN; ++c) {
-          const float* wr = ws + (tap * CIN + c) * C;
-          float s = 0.f;
-#pragma unroll
-          for (int co = 0; co < C; ++co) s = fmaf(G[co], wr[co], s);
-          acc[c] += s;
-        }
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < CIN; ++c)
-      if (gxs[c] != nullptr) gxs[c][i] = (((accumulate >> c) & 1) ? gxs[c][i] : 0.f) + acc[c];
-  }
-}
-
-// Contiguous pixel range [i0, i1) of CTA `blockIdx.x` out of gridDim.x.
-__device__ __forceinline__ void cta_range(long long total, long long* i0, long long* i1) {
-  const long long per = (total + gridDim.x - 1) / gridDim.x;
-  *i0 = (long long)blockIdx.x * per;
-  *i1 = *i0 + per < total ? *i0 + per : total;
-}
-
-// Per-CTA partial sums of dW[tap][c][co] (9*CIN*C values) and db[co] (C values):
-// lane = co, the 8 warps take every 8th pixel of the CTA's range, then the
-// warps' sums are added in shared memory.
-template <int CIN>
-__global__ void __launch_bounds__(256) k_conv_in_bwd_weights(int B, int H, int W, const float* __restrict__ x0,
-                                                             const float* __restrict__ x1,
-                                                             const float* __restrict__ x2,
-                                                             const tat_bf16* __restrict__ g_h,
-                                                             const tat_bf16* __restrict__ h, float* partial) {
-  constexpr int NW = 9 * CIN * C + C;
-  __shared__ float red[8][NW];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long hw = (long long)H * W;
-  long long i0, i1;
-  cta_range((long long)B * hw, &i0, &i1);
-  float acc[9 * CIN], bacc = 0.f;
-#pragma unroll
-  for (int k = 0; k < 9 * CIN; ++k) acc[k] = 0.f;
-#pragma unroll 4
-  for (long long i = i0 + warp; i < i1; i += 8) {
-    const float gv = bf(g_h[i * C + lane]), hv = bf(h[i * C + lane]);
-    const float G = hv > 0.f ? gv : 0.f;
-    bacc += G;
-    const Px p = px_of(i, H, W);
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int yy = p.y + tap / 3 - 1, xx = p.x + tap % 3 - 1;
-      if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
-      const long long o = (long long)p.b * hw + (long long)yy * W + xx;
-      acc[tap * CIN + 0] = fmaf(G, rbf(x0[o]), acc[tap * CIN + 0]);
-      acc[tap * CIN + 1] = fmaf(G, rbf(x1[o]), acc[tap * CIN + 1]);
-      if (CIN == 3) acc[tap * CIN + CIN - 1] = fmaf(G, rbf(x2[o]), acc[tap * CIN + CIN - 1]);
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < 9 * CIN; ++k) red[warp][k * C + lane] = acc[k];
-  red[warp][9 * CIN * C + lane] = bacc;
-  __syncthreads();
-  for (int o = threadIdx.x; o < NW; o += blockDim.x) {
-    float t = 0.f;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) t += red[w][o];
-    partial[(size_t)blockIdx.x * NW + o] = t;
-  }
-}
+// ------------------------------------------------------------------ weight-gradient partial sums
 
 // out[e] += sum over CTAs of partial[cta][e] (fixed order); e < nw_w goes to gw[e], the rest to
 // gb[e - nw_w].  A block covers 32 outputs (lanes); its 8 warps split the CTAs.
@@ -267,7 +105,6 @@ __device__ __forceinline__ void mma_bf16(float* d, const unsigned* a, const unsi
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-__device__ __forceinline__ unsigned ld32(const tat_bf16* p) { return *reinterpret_cast<const unsigned*>(p); }
 
 // Loads the (TY+2) x (TX+2) x 32 halo of image b around the tile (y0, x0) into
 // hs[(TY+2)*(TX+2)][CP]; out-of-image pixels are zero.  With MASK the value is
@@ -340,14 +177,6 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// 32-bit word (channels c, c+1) of halo pixel p in a tile written by TMA with
-// the 64-byte swizzle: 16-byte chunk j of the 64-byte row p sits at j ^ ((p >> 1) & 3).
-__device__ __forceinline__ unsigned ldsw(const unsigned char* tile, int p, int c) {
-  const int byte = 2 * c;
-  const int chunk = (byte >> 4) ^ ((p >> 1) & 3);
-  return *reinterpret_cast<const unsigned*>(tile + p * 64 + (chunk << 4) + (byte & 15));
-}
-
 // g * [h > 0] for the two BF16 values of a word (h > 0: sign clear and not zero).
 __device__ __forceinline__ unsigned relu_masked(unsigned g, unsigned h) {
   const unsigned lo = h & 0xffffu, hi = h >> 16;
@@ -359,6 +188,79 @@ __device__ __forceinline__ void ldsm_x4(unsigned* r, const unsigned char* p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(smem_u32(p)));
+}
+
+__device__ __forceinline__ void ldsm_x4_trans(unsigned* r, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_u32(p)));
+}
+
+// Address of the 16-byte chunk `chunk` of halo pixel p in a tile written by TMA with the
+// 64-byte swizzle.
+__device__ __forceinline__ const unsigned char* swz(const unsigned char* tile, int p, int chunk) {
+  return tile + p * 64 + ((chunk ^ ((p >> 1) & 3)) << 4);
+}
+
+// Persistent loop over the 8 x 16 tiles of a [B][H][W] grid; tile i of this CTA uses slot
+// i & 1.  One tile ahead of its use, thread 0 arms bar[slot] with `bytes` and issue(b, y0,
+// x0, slot) starts the tile's TMA copies (none when bytes == 0), and every thread runs
+// prefetch(b, y0, x0), plain loads into registers.  commit() moves those registers into
+// shared memory once the previous tile is done with it, and body(b, y0, x0, slot) runs when
+// the copies have landed.  Returns false, with the timeout flag set, if a wait gave up (after
+// a bounded wait for the copy still in flight).  bar[] must be initialised, and the
+// initialisation made visible by a barrier, before the call.
+template <class Issue, class Prefetch, class Commit, class Body>
+__device__ __forceinline__ bool tile_loop(int B, int H, int W, uint64_t* bar, unsigned bytes, Issue issue,
+                                          Prefetch prefetch, Commit commit, Body body) {
+  const int tilesx = (W + TX - 1) / TX, tilesy = (H + TY - 1) / TY;
+  const long long ntiles = (long long)B * tilesx * tilesy;
+  auto coords = [&](long long tile, int& b, int& y0, int& x0) {
+    b = (int)(tile / (tilesx * tilesy));
+    const int rr = (int)(tile % (tilesx * tilesy));
+    y0 = (rr / tilesx) * TY;
+    x0 = (rr % tilesx) * TX;
+  };
+  auto start = [&](long long tile, int s) {
+    int b, y0, x0;
+    coords(tile, b, y0, x0);
+    if (bytes != 0 && threadIdx.x == 0) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic reads of the slot come first
+      mbar_expect_tx(&bar[s], bytes);
+      issue(b, y0, x0, s);
+    }
+    prefetch(b, y0, x0);
+  };
+  if ((long long)blockIdx.x < ntiles) {
+    start(blockIdx.x, 0);
+    commit();
+  }
+  int i = 0;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+    const int s = i & 1;
+    const long long next = tile + gridDim.x;
+    if (next < ntiles) start(next, s ^ 1);  // slot s^1 was released by the barrier ending the previous tile
+    const bool ok = bytes == 0 || mbar_wait(&bar[s], (unsigned)((i >> 1) & 1));
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicExch(&g_lpd_timeout, 1);
+      if (bytes != 0 && next < ntiles) mbar_wait(&bar[s ^ 1], (unsigned)(((i + 1) >> 1) & 1));
+      return false;
+    }
+    int b, y0, x0;
+    coords(tile, b, y0, x0);
+    body(b, y0, x0, s);
+    __syncthreads();
+    if (next < ntiles) commit();
+  }
+  return true;
+}
+
+__device__ __forceinline__ void init_bars(uint64_t* bar) {
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
 }
 
 // One 8 x 16 output tile of the mid layer from a staged halo (and, for BWD, the
@@ -450,54 +352,18 @@ __global__ void __launch_bounds__(256) k_conv_mid(int B, int H, int W, const __g
     if (BWD) wsm[((8 - tap) * C + ci) * CP + co] = w[e];
     else wsm[(tap * C + co) * CP + ci] = w[e];
   }
-  if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-  }
+  init_bars(bar);
   __syncthreads();
-  const int tilesx = (W + TX - 1) / TX, tilesy = (H + TY - 1) / TY;
-  const long long ntiles = (long long)B * tilesx * tilesy;
-  auto coords = [&](long long tile, int* b, int* y0, int* x0) {
-    *b = (int)(tile / (tilesx * tilesy));
-    const int rr = (int)(tile % (tilesx * tilesy));
-    *y0 = (rr / tilesx) * TY;
-    *x0 = (rr % tilesx) * TX;
-  };
-  auto issue = [&](long long tile, int s) {
-    if (threadIdx.x != 0) return;
-    int b, y0, x0;
-    coords(tile, &b, &y0, &x0);
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic reads of the slot come first
-    mbar_expect_tx(&bar[s], NT * HALO_BYTES);
-    tma_load_4d(sm + s * STAGE, &map_in, 0, x0 - 1, y0 - 1, b, &bar[s]);
-    if (BWD) tma_load_4d(sm + s * STAGE + HALO_SLOT, &map_mask, 0, x0 - 1, y0 - 1, b, &bar[s]);
-  };
-  if ((long long)blockIdx.x < ntiles) issue(blockIdx.x, 0);
-  int i = 0;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
-    const int s = i & 1;
-    const long long next = tile + gridDim.x;
-    if (next < ntiles) issue(next, s ^ 1);  // that slot was released by the barrier ending the previous tile
-    const bool ok = mbar_wait(&bar[s], (unsigned)((i >> 1) & 1));
-    if (__syncthreads_or(!ok)) {
-      // give up: record it, let the copy still in flight land (bounded), and leave
-      if (threadIdx.x == 0) atomicExch(&g_lpd_timeout, 1);
-      if (next < ntiles) mbar_wait(&bar[s ^ 1], (unsigned)(((i + 1) >> 1) & 1));
-      return;
-    }
-    int b, y0, x0;
-    coords(tile, &b, &y0, &x0);
-    mid_tile<BWD>(sm + s * STAGE, sm + s * STAGE + HALO_SLOT, wsm, bias, out, b, y0, x0, H, W);
-    __syncthreads();
-  }
-}
-
-__device__ __forceinline__ void ldsm_x4_trans(unsigned* r, const tat_bf16* p) {
-  const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(addr));
+  tile_loop(
+      B, H, W, bar, NT * HALO_BYTES,
+      [&](int b, int y0, int x0, int s) {
+        tma_load_4d(sm + s * STAGE, &map_in, 0, x0 - 1, y0 - 1, b, &bar[s]);
+        if (BWD) tma_load_4d(sm + s * STAGE + HALO_SLOT, &map_mask, 0, x0 - 1, y0 - 1, b, &bar[s]);
+      },
+      [](int, int, int) {}, [] {},
+      [&](int b, int y0, int x0, int s) {
+        mid_tile<BWD>(sm + s * STAGE, sm + s * STAGE + HALO_SLOT, wsm, bias, out, b, y0, x0, H, W);
+      });
 }
 
 // dW[tap][co][ci] = sum_p G'(p)[co] in(p + tap)[ci], db[co] = sum_p G'(p)[co],
@@ -587,102 +453,487 @@ __global__ void __launch_bounds__(288) k_conv_mid_wgrad(int B, int H, int W, con
   if (threadIdx.x < C) pp[9 * C * C + threadIdx.x] = bsum;
 }
 
-// ------------------------------------------------------------------ out layer (CUDA cores)
+// ------------------------------------------------------------------ thin layers (tensor cores)
+//
+// The in layer (cin = 2 or 3 planes -> 32) and the out layer (32 -> 1) are implicit GEMMs too,
+// with one dimension of 8 to 27: mma.sync m16n8k16 on 8 x 16 pixel tiles, one warp per tile
+// row, persistent CTAs.  BF16 x BF16 products are exact in FP32, so the tensor cores give the
+// sums the CUDA cores would, in another order.  An FP32 operand (the gradient of the out
+// layer's output) enters as two BF16 terms hi + lo, hi = bf16(v), lo = bf16(v - hi), which
+// carry 16 of its 24 significand bits (relative error below 2^-16 per product).
 
-__global__ void k_conv_out_fwd(int B, int H, int W, const tat_bf16* __restrict__ h, const tat_bf16* __restrict__ w,
-                               const float* __restrict__ bias, const float* residual, float* out) {
-  __shared__ float ws[9 * C];
-  for (int i = threadIdx.x; i < 9 * C; i += blockDim.x) ws[i] = bf(w[i]);
-  __syncthreads();
-  const long long hw = (long long)H * W;
-  const float b0 = bias[0];
-  GRID_STRIDE(i, (long long)B * hw) {
-    const Px p = px_of(i, H, W);
-    float acc = b0;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int yy = p.y + dy;
-      if (yy < 0 || yy >= H) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int xx = p.x + dx;
-        if (xx < 0 || xx >= W) continue;
-        const float* wr = ws + (3 * (dy + 1) + (dx + 1)) * C;
-        const uint4* src = reinterpret_cast<const uint4*>(h + ((long long)p.b * hw + (long long)yy * W + xx) * C);
+// Halo of CIN FP32 planes around a tile, prefetched into registers (kXPer values per thread)
+// and committed to shared memory as BF16.
+constexpr int kXPer = (3 * XH * XW + 255) / 256;
+
+__device__ __forceinline__ const float* pick(int c, const float* p0, const float* p1, const float* p2) {
+  return c == 0 ? p0 : (c == 1 ? p1 : p2);
+}
+
+template <int CIN>
+__device__ __forceinline__ void x_prefetch(float* v, const float* x0, const float* x1, const float* x2, int b,
+                                           int y0, int x0c, int H, int W) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float f[8];
-          unpack8(src[q], f);
+  for (int k = 0; k < kXPer; ++k) {
+    const int e = threadIdx.x + 256 * k;
+    v[k] = 0.f;
+    if (e < CIN * XH * XW) {
+      const int c = e / (XH * XW), r = (e / XW) % XH, j = e % XW;
+      const int yy = y0 - 1 + r, xx = x0c - 1 + j;
+      if (yy >= 0 && yy < H && xx >= 0 && xx < W) v[k] = pick(c, x0, x1, x2)[((long long)b * H + yy) * W + xx];
+    }
+  }
+}
+
+// h = relu(conv_in(x) + b): A[pixel][k = tap * CIN + c] gathered from the BF16 halo (K padded
+// to 32), B = w[k][co] held in registers, N = 32.
+template <int CIN>
+__global__ void __launch_bounds__(256) k_conv_in_fwd(int B, int H, int W, const float* __restrict__ x0,
+                                                     const float* __restrict__ x1, const float* __restrict__ x2,
+                                                     const tat_bf16* __restrict__ w, const float* __restrict__ bias,
+                                                     tat_bf16* __restrict__ h) {
+  constexpr int KV = 9 * CIN;
+  __shared__ __align__(16) unsigned short xs[CIN * XH * XW];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  unsigned bw[2][4][2];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) acc = fmaf(f[k], wr[8 * q + k], acc);
+  for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        const int k = ks * 16 + hf * 8 + 2 * t, n = nt * 8 + g;
+        const unsigned lo = k < KV ? w[k * C + n] : 0u, hi = k + 1 < KV ? w[(k + 1) * C + n] : 0u;
+        bw[ks][nt][hf] = lo | (hi << 16);
+      }
+  // halo offsets of the thread's A columns k = 16 ks + {2t, 2t+1, 2t+8, 2t+9}; -1 past K
+  int aoff[2][4];
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = ks * 16 + 2 * t + (j & 1) + (j >> 1) * 8, tap = k / CIN;
+      aoff[ks][j] = k < KV ? (k % CIN) * XH * XW + (tap / 3) * XW + tap % 3 + warp * XW : -1;
+    }
+  float xv[kXPer];
+  tile_loop(
+      B, H, W, nullptr, 0, [](int, int, int, int) {},
+      [&](int b, int y0, int x0c) { x_prefetch<CIN>(xv, x0, x1, x2, b, y0, x0c, H, W); },
+      [&] {
+#pragma unroll
+        for (int k = 0; k < kXPer; ++k) {
+          const int e = threadIdx.x + 256 * k;
+          if (e < CIN * XH * XW) xs[e] = tobf(xv[k]);
         }
-      }
-    }
-    out[i] = residual[i] + acc;
-  }
+      },
+      [&](int b, int y0, int x0c, int) {
+        float acc[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) acc[nt][k] = 0.f;
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+          auto ld = [&](int j, int px) -> unsigned { return aoff[ks][j] < 0 ? 0u : (unsigned)xs[aoff[ks][j] + px]; };
+          const unsigned a[4] = {ld(0, g) | (ld(1, g) << 16), ld(0, g + 8) | (ld(1, g + 8) << 16),
+                                 ld(2, g) | (ld(3, g) << 16), ld(2, g + 8) | (ld(3, g + 8) << 16)};
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[nt], a, bw[ks][nt]);
+        }
+        const int y = y0 + warp;
+        if (y >= H) return;
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          const int x = x0c + g + 8 * hf;
+          if (x >= W) continue;
+          tat_bf16* dst = h + (((long long)b * H + y) * W + x) * C;
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt) {
+            const int co = nt * 8 + 2 * t;
+            const float v0 = fmaxf(acc[nt][2 * hf] + bias[co], 0.f), v1 = fmaxf(acc[nt][2 * hf + 1] + bias[co + 1], 0.f);
+            *reinterpret_cast<unsigned*>(dst + co) = (unsigned)tobf(v0) | ((unsigned)tobf(v1) << 16);
+          }
+        }
+      });
 }
 
-__global__ void k_conv_out_bwd_data(int B, int H, int W, const float* __restrict__ gout,
-                                    const tat_bf16* __restrict__ w, tat_bf16* __restrict__ gh) {
-  __shared__ float ws[9 * C];
-  for (int i = threadIdx.x; i < 9 * C; i += blockDim.x) ws[i] = bf(w[i]);
+// Dynamic shared memory of k_conv_in_bwd: alignment slack, two slots of (g, h) halos, the
+// flipped weights [9][8][CP], two BF16 copies of the x halo (second one shifted by one
+// column, so that every pixel pair is a 4-byte word in one of them), two mbarriers.
+template <int CIN>
+constexpr size_t in_bwd_smem_bytes() {
+  return 1024 + 2 * 2 * HALO_SLOT + 9 * 8 * CP * 2 + 2 * CIN * XH * XP * 2 + 2 * sizeof(uint64_t);
+}
+
+// Backward of the in layer in one pass over the tiles of g_h and h (G' = g_h * [h > 0]):
+//   DATA : gx_c(p) = sum_{tap, co} G'(p - tap)[co] w[tap][c][co]   (A = shifted G', N = 8 >= CIN)
+//   WGRAD: dW[tap * CIN + c][co] = sum_p G'(p)[co] x_c(p + tap), db[co] = sum_p G'(p)[co]
+//          (A = G'^T by ldmatrix.trans, B = x pairs, plus a column of ones for db), per-CTA
+//          partials [9 CIN + 1][32].
+template <int CIN, bool DATA, bool WGRAD>
+__global__ void __launch_bounds__(256, 2) k_conv_in_bwd(int B, int H, int W, const __grid_constant__ CUtensorMap map_g,
+                                                        const __grid_constant__ CUtensorMap map_h,
+                                                        const float* __restrict__ x0, const float* __restrict__ x1,
+                                                        const float* __restrict__ x2, const tat_bf16* __restrict__ w,
+                                                        float* gx0, float* gx1, float* gx2, int accumulate,
+                                                        float* __restrict__ partial) {
+  constexpr int KV = 9 * CIN;
+  constexpr int NTW = (KV + 1 + 7) / 8;  // n-tiles of the weight-gradient GEMM (with the ones column)
+  constexpr int STAGE = 2 * HALO_SLOT;
+  constexpr int XCOPY = CIN * XH * XP;
+  extern __shared__ unsigned char dsm[];
+  unsigned char* sm = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
+  tat_bf16* wsb = reinterpret_cast<tat_bf16*>(sm + 2 * STAGE);
+  unsigned short* xs = reinterpret_cast<unsigned short*>(sm + 2 * STAGE + 9 * 8 * CP * 2);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * STAGE + 9 * 8 * CP * 2 + 2 * XCOPY * 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  if (DATA)
+    for (int e = threadIdx.x; e < 9 * 8 * C; e += blockDim.x) {
+      const int tap = e / (8 * C), n = (e / C) % 8, co = e % C;
+      wsb[(tap * 8 + n) * CP + co] = n < CIN ? w[((8 - tap) * CIN + n) * C + co] : (tat_bf16)0;
+    }
+  // B of the weight gradient: per n-tile the word offset of the thread's x pair (column n = 8 nt + g)
+  int boff[NTW];
+  unsigned bconst[NTW];
+#pragma unroll
+  for (int nt = 0; nt < NTW; ++nt) {
+    const int n = nt * 8 + g;
+    boff[nt] = -1;
+    bconst[nt] = n == KV ? 0x3f803f80u : 0u;  // (1, 1) in BF16 for the bias column
+    if (n < KV) {
+      const int tap = n / CIN, c = n % CIN, dy = tap / 3, dx = tap % 3;
+      boff[nt] = dx == 1 ? XCOPY + c * XH * XP + (warp + dy) * XP + 2 * t : c * XH * XP + (warp + dy) * XP + 2 * t + dx;
+    }
+  }
+  init_bars(bar);
   __syncthreads();
-  const long long hw = (long long)H * W;
-  GRID_STRIDE(i, (long long)B * hw) {
-    const Px p = px_of(i, H, W);
-    float acc[C];
+  float accw[2][NTW][4];
 #pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = 0.f;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int yy = p.y - dy;
-      if (yy < 0 || yy >= H) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int xx = p.x - dx;
-        if (xx < 0 || xx >= W) continue;
-        const float gv = gout[(long long)p.b * hw + (long long)yy * W + xx];
-        const float* wr = ws + (3 * (dy + 1) + (dx + 1)) * C;
+  for (int mh = 0; mh < 2; ++mh)
 #pragma unroll
-        for (int c = 0; c < C; ++c) acc[c] = fmaf(gv, wr[c], acc[c]);
-      }
+    for (int nt = 0; nt < NTW; ++nt)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) accw[mh][nt][k] = 0.f;
+  float xv[kXPer];
+  const bool ok = tile_loop(
+      B, H, W, bar, 2 * HALO_BYTES,
+      [&](int b, int y0, int x0c, int s) {
+        tma_load_4d(sm + s * STAGE, &map_g, 0, x0c - 1, y0 - 1, b, &bar[s]);
+        tma_load_4d(sm + s * STAGE + HALO_SLOT, &map_h, 0, x0c - 1, y0 - 1, b, &bar[s]);
+      },
+      [&](int b, int y0, int x0c) {
+        if (WGRAD) x_prefetch<CIN>(xv, x0, x1, x2, b, y0, x0c, H, W);
+      },
+      [&] {
+        if (WGRAD)
+#pragma unroll
+          for (int k = 0; k < kXPer; ++k) {
+            const int e = threadIdx.x + 256 * k;
+            if (e < CIN * XH * XW) {
+              const int c = e / (XH * XW), r = (e / XW) % XH, j = e % XW;
+              const unsigned short v = tobf(xv[k]);
+              xs[c * XH * XP + r * XP + j] = v;
+              if (j > 0) xs[XCOPY + c * XH * XP + r * XP + j - 1] = v;
+            }
+          }
+      },
+      [&](int b, int y0, int x0c, int s) {
+        const unsigned char* gt = sm + s * STAGE;
+        const unsigned char* ht = gt + HALO_SLOT;
+        const int m = lane >> 3;
+        if (DATA) {
+          float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+          for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap % 3;
+            unsigned bq[4];
+            ldsm_x4(bq, reinterpret_cast<const unsigned char*>(wsb + (tap * 8 + (lane & 7)) * CP + m * 8));
+            const int pa = (warp + dy) * XW + dx + (m & 1) * 8 + (lane & 7);
+#pragma unroll
+            for (int kc = 0; kc < 2; ++kc) {
+              unsigned a[4], mk[4];
+              ldsm_x4(a, swz(gt, pa, 2 * kc + (m >> 1)));
+              ldsm_x4(mk, swz(ht, pa, 2 * kc + (m >> 1)));
+#pragma unroll
+              for (int j = 0; j < 4; ++j) a[j] = relu_masked(a[j], mk[j]);
+              mma_bf16(acc, a, bq + 2 * kc);
+            }
+          }
+          const int y = y0 + warp;
+          if (t < 2 && y < H) {
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+              const int x = x0c + g + 8 * hf;
+              if (x >= W) continue;
+              const long long pix = ((long long)b * H + y) * W + x;
+#pragma unroll
+              for (int j = 0; j < 2; ++j) {
+                const int c = 2 * t + j;
+                if (c >= CIN) continue;
+                float* gx = c == 0 ? gx0 : (c == 1 ? gx1 : gx2);
+                if (gx != nullptr) gx[pix] = (((accumulate >> c) & 1) ? gx[pix] : 0.f) + acc[2 * hf + j];
+              }
+            }
+          }
+        }
+        if (WGRAD) {
+          unsigned a[2][4];
+#pragma unroll
+          for (int mh = 0; mh < 2; ++mh) {
+            // A = G'^T (co x pixel): matrices (co 0-7, px 0-7), (co 8-15, px 0-7), (co 0-7, px 8-15), (co 8-15, px 8-15)
+            const int p = (warp + 1) * XW + 1 + (m >> 1) * 8 + (lane & 7);
+            unsigned mk[4];
+            ldsm_x4_trans(a[mh], swz(gt, p, 2 * mh + (m & 1)));
+            ldsm_x4_trans(mk, swz(ht, p, 2 * mh + (m & 1)));
+#pragma unroll
+            for (int j = 0; j < 4; ++j) a[mh][j] = relu_masked(a[mh][j], mk[j]);
+          }
+#pragma unroll
+          for (int nt = 0; nt < NTW; ++nt) {
+            unsigned bb[2] = {bconst[nt], bconst[nt]};
+            if (boff[nt] >= 0) {
+              bb[0] = *reinterpret_cast<const unsigned*>(xs + boff[nt]);
+              bb[1] = *reinterpret_cast<const unsigned*>(xs + boff[nt] + 8);
+            }
+            mma_bf16(accw[0][nt], a[0], bb);
+            mma_bf16(accw[1][nt], a[1], bb);
+          }
+        }
+      });
+  if (!WGRAD || !ok) return;
+  // per-warp sums [warp][n][co] in the (now idle) tile slots, then a fixed-order sum over the warps
+  constexpr int NW = (KV + 1) * C;
+  float* red = reinterpret_cast<float*>(sm);
+#pragma unroll
+  for (int mh = 0; mh < 2; ++mh)
+#pragma unroll
+    for (int nt = 0; nt < NTW; ++nt) {
+      const int co = mh * 16 + g, n = nt * 8 + 2 * t;
+      float* r = red + warp * NTW * 8 * C;
+      r[n * C + co] = accw[mh][nt][0];
+      r[(n + 1) * C + co] = accw[mh][nt][1];
+      r[n * C + co + 8] = accw[mh][nt][2];
+      r[(n + 1) * C + co + 8] = accw[mh][nt][3];
     }
-    uint4* dst = reinterpret_cast<uint4*>(gh + i * C);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dst[q] = pack8(acc + 8 * q);
-  }
-}
-
-// Per-CTA partials of dW[tap][ci] (288) and db (1): lane = ci, the 8 warps take
-// every 8th pixel of the CTA's range, then the warps' sums are added in shared memory.
-__global__ void __launch_bounds__(256) k_conv_out_wgrad(int B, int H, int W, const float* __restrict__ gout,
-                                                        const tat_bf16* __restrict__ h, float* partial) {
-  constexpr int NW = 9 * C + 1;
-  __shared__ float red[8][NW];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long hw = (long long)H * W;
-  long long i0, i1;
-  cta_range((long long)B * hw, &i0, &i1);
-  float acc[9], bacc = 0.f;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) acc[k] = 0.f;
-#pragma unroll 4
-  for (long long i = i0 + warp; i < i1; i += 8) {
-    const float gv = gout[i];
-    bacc += gv;
-    const Px p = px_of(i, H, W);
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int yy = p.y + tap / 3 - 1, xx = p.x + tap % 3 - 1;
-      if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
-      acc[tap] = fmaf(gv, bf(h[((long long)p.b * hw + (long long)yy * W + xx) * C + lane]), acc[tap]);
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < 9; ++k) red[warp][k * C + lane] = acc[k];
-  if (lane == 0) red[warp][9 * C] = bacc;
   __syncthreads();
   for (int o = threadIdx.x; o < NW; o += blockDim.x) {
-    float t = 0.f;
+    float sum = 0.f;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) t += red[w][o];
-    partial[(size_t)blockIdx.x * NW + o] = t;
+    for (int wp = 0; wp < 8; ++wp) sum += red[wp * NTW * 8 * C + o];
+    partial[(size_t)blockIdx.x * NW + o] = sum;
+  }
+}
+
+// Dynamic shared memory of the out-layer kernels: alignment slack, two slots of h halos,
+// [9][8][CP] weights (forward) or the hi / lo x 2-copy halo of g_out (backward), two mbarriers.
+constexpr size_t out_fwd_smem_bytes() { return 1024 + 2 * HALO_SLOT + 9 * 8 * CP * 2 + 2 * sizeof(uint64_t); }
+constexpr size_t out_bwd_smem_bytes() { return 1024 + 2 * HALO_SLOT + 4 * XH * XP * 2 + 2 * sizeof(uint64_t); }
+
+// out = residual + b + conv_out(h): the 32 -> 32 forward with N = 8 (weights in column 0).
+__global__ void __launch_bounds__(256) k_conv_out_fwd(int B, int H, int W, const __grid_constant__ CUtensorMap map_h,
+                                                      const tat_bf16* __restrict__ w, const float* __restrict__ bias,
+                                                      const float* residual, float* out) {
+  extern __shared__ unsigned char dsm[];
+  unsigned char* sm = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
+  tat_bf16* wso = reinterpret_cast<tat_bf16*>(sm + 2 * HALO_SLOT);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * HALO_SLOT + 9 * 8 * CP * 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  for (int e = threadIdx.x; e < 9 * 8 * C; e += blockDim.x) {
+    const int tap = e / (8 * C), n = (e / C) % 8, k = e % C;
+    wso[(tap * 8 + n) * CP + k] = n == 0 ? w[tap * C + k] : (tat_bf16)0;
+  }
+  init_bars(bar);
+  __syncthreads();
+  const float b0 = bias[0];
+  tile_loop(
+      B, H, W, bar, HALO_BYTES,
+      [&](int b, int y0, int x0c, int s) { tma_load_4d(sm + s * HALO_SLOT, &map_h, 0, x0c - 1, y0 - 1, b, &bar[s]); },
+      [](int, int, int) {}, [] {},
+      [&](int b, int y0, int x0c, int s) {
+        const unsigned char* ht = sm + s * HALO_SLOT;
+        const int m = lane >> 3;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          const int dy = tap / 3, dx = tap % 3;
+          unsigned bq[4];
+          ldsm_x4(bq, reinterpret_cast<const unsigned char*>(wso + (tap * 8 + (lane & 7)) * CP + m * 8));
+          const int pa = (warp + dy) * XW + dx + (m & 1) * 8 + (lane & 7);
+#pragma unroll
+          for (int kc = 0; kc < 2; ++kc) {
+            unsigned a[4];
+            ldsm_x4(a, swz(ht, pa, 2 * kc + (m >> 1)));
+            mma_bf16(acc, a, bq + 2 * kc);
+          }
+        }
+        const int y = y0 + warp;
+        if (t != 0 || y >= H) return;
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          const int x = x0c + g + 8 * hf;
+          if (x >= W) continue;
+          const long long pix = ((long long)b * H + y) * W + x;
+          out[pix] = residual[pix] + b0 + acc[2 * hf];
+        }
+      });
+}
+
+// Backward of the out layer in one pass (g = g_out split as hi + lo):
+//   g_h(p)[ci] = sum_tap g(p - tap) w[tap][ci]           (A[pixel][tap] gathered, B = w, N = 32)
+//   dW[tap][ci] = sum_q h(q)[ci] g(q - tap), db = sum g   (A = h^T by ldmatrix.trans, B = g pairs,
+//                                                          n = part * 9 + tap), per-CTA partials [289].
+__global__ void __launch_bounds__(256, 2) k_conv_out_bwd(int B, int H, int W, const __grid_constant__ CUtensorMap map_h,
+                                                         const float* __restrict__ gout, const tat_bf16* __restrict__ w,
+                                                         tat_bf16* __restrict__ gh, float* __restrict__ partial) {
+  constexpr int PART = 2 * XH * XP, CPY = XH * XP;  // gs[part][copy][XH][XP]
+  extern __shared__ unsigned char dsm[];
+  unsigned char* sm = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
+  unsigned short* gs = reinterpret_cast<unsigned short*>(sm + 2 * HALO_SLOT);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * HALO_SLOT + 4 * XH * XP * 2);
+  __shared__ float dbred[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  // B of g_h: w[k = tap][n = ci], K = 16 (taps 9..15 zero)
+  unsigned bo[4][2];
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    const int n = nt * 8 + g, k = 2 * t;
+    bo[nt][0] = (unsigned)w[k * C + n] | ((unsigned)w[(k + 1) * C + n] << 16);
+    bo[nt][1] = k + 8 < 9 ? (unsigned)w[(k + 8) * C + n] : 0u;
+  }
+  // A of g_h: halo offsets of the taps k = 2t, 2t+1, 2t+8, 2t+9 (g(p - tap) sits at halo row
+  // r + 2 - tap / 3, column j + 2 - tap % 3); -1 for k >= 9
+  int goff[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int k = 2 * t + (j & 1) + (j >> 1) * 8;
+    goff[j] = k < 9 ? (warp + 2 - k / 3) * XP + 2 - k % 3 : -1;
+  }
+  // B of dW: word offset of the thread's g pair for column n = 8 nt + g (part n / 9, tap n % 9)
+  int boff[3];
+#pragma unroll
+  for (int nt = 0; nt < 3; ++nt) {
+    const int n = nt * 8 + g;
+    boff[nt] = -1;
+    if (n < 18) {
+      const int part = n / 9, tap = n % 9, dxo = 2 - tap % 3;
+      boff[nt] = part * PART + (warp + 2 - tap / 3) * XP + (dxo == 1 ? CPY + 2 * t : 2 * t + dxo);
+    }
+  }
+  init_bars(bar);
+  __syncthreads();
+  float accw[2][3][4];
+#pragma unroll
+  for (int mh = 0; mh < 2; ++mh)
+#pragma unroll
+    for (int nt = 0; nt < 3; ++nt)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) accw[mh][nt][k] = 0.f;
+  float gv = 0.f, dbacc = 0.f;
+  int gr = 0, gj = 0;
+  const bool ok = tile_loop(
+      B, H, W, bar, HALO_BYTES,
+      [&](int b, int y0, int x0c, int s) { tma_load_4d(sm + s * HALO_SLOT, &map_h, 0, x0c - 1, y0 - 1, b, &bar[s]); },
+      [&](int b, int y0, int x0c) {
+        gv = 0.f;
+        gr = threadIdx.x / XW;
+        gj = threadIdx.x % XW;
+        if (threadIdx.x < XH * XW) {
+          const int yy = y0 - 1 + gr, xx = x0c - 1 + gj;
+          if (yy >= 0 && yy < H && xx >= 0 && xx < W) gv = gout[((long long)b * H + yy) * W + xx];
+        }
+      },
+      [&] {
+        if (threadIdx.x < XH * XW) {
+          const unsigned short hi = tobf(gv), lo = tobf(gv - bf(hi));
+          gs[gr * XP + gj] = hi;
+          gs[PART + gr * XP + gj] = lo;
+          if (gj > 0) {
+            gs[CPY + gr * XP + gj - 1] = hi;
+            gs[PART + CPY + gr * XP + gj - 1] = lo;
+          }
+          if (gr >= 1 && gr <= TY && gj >= 1 && gj <= TX) dbacc += gv;
+        }
+      },
+      [&](int b, int y0, int x0c, int s) {
+        const unsigned char* ht = sm + s * HALO_SLOT;
+        const int m = lane >> 3;
+        // g_h
+        {
+          float acc[4][4];
+#pragma unroll
+          for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[nt][k] = 0.f;
+#pragma unroll
+          for (int part = 0; part < 2; ++part) {
+            auto ld = [&](int j, int px) -> unsigned {
+              return goff[j] < 0 ? 0u : (unsigned)gs[part * PART + goff[j] + px];
+            };
+            const unsigned a[4] = {ld(0, g) | (ld(1, g) << 16), ld(0, g + 8) | (ld(1, g + 8) << 16),
+                                   ld(2, g) | (ld(3, g) << 16), ld(2, g + 8) | (ld(3, g + 8) << 16)};
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[nt], a, bo[nt]);
+          }
+          const int y = y0 + warp;
+          if (y < H) {
+#pragma unroll
+            for (int hf = 0; hf < 2; ++hf) {
+              const int x = x0c + g + 8 * hf;
+              if (x >= W) continue;
+              tat_bf16* dst = gh + (((long long)b * H + y) * W + x) * C;
+#pragma unroll
+              for (int nt = 0; nt < 4; ++nt)
+                *reinterpret_cast<unsigned*>(dst + nt * 8 + 2 * t) =
+                    (unsigned)tobf(acc[nt][2 * hf]) | ((unsigned)tobf(acc[nt][2 * hf + 1]) << 16);
+            }
+          }
+        }
+        // dW
+        unsigned a[2][4];
+#pragma unroll
+        for (int mh = 0; mh < 2; ++mh) {
+          const int p = (warp + 1) * XW + 1 + (m >> 1) * 8 + (lane & 7);
+          ldsm_x4_trans(a[mh], swz(ht, p, 2 * mh + (m & 1)));
+        }
+#pragma unroll
+        for (int nt = 0; nt < 3; ++nt) {
+          unsigned bb[2] = {0u, 0u};
+          if (boff[nt] >= 0) {
+            bb[0] = *reinterpret_cast<const unsigned*>(gs + boff[nt]);
+            bb[1] = *reinterpret_cast<const unsigned*>(gs + boff[nt] + 8);
+          }
+          mma_bf16(accw[0][nt], a[0], bb);
+          mma_bf16(accw[1][nt], a[1], bb);
+        }
+      });
+  if (!ok) return;
+  float* red = reinterpret_cast<float*>(sm);  // [warp][24][32] in the idle tile slots
+#pragma unroll
+  for (int mh = 0; mh < 2; ++mh)
+#pragma unroll
+    for (int nt = 0; nt < 3; ++nt) {
+      const int ci = mh * 16 + g, n = nt * 8 + 2 * t;
+      float* r = red + warp * 24 * C;
+      r[n * C + ci] = accw[mh][nt][0];
+      r[(n + 1) * C + ci] = accw[mh][nt][1];
+      r[n * C + ci + 8] = accw[mh][nt][2];
+      r[(n + 1) * C + ci + 8] = accw[mh][nt][3];
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dbacc += __shfl_xor_sync(0xffffffffu, dbacc, o);
+  if (lane == 0) dbred[warp] = dbacc;
+  __syncthreads();
+  constexpr int NW = 9 * C + 1;
+  for (int o = threadIdx.x; o < NW; o += blockDim.x) {
+    float sum = 0.f;
+    if (o < 9 * C) {
+#pragma unroll
+      for (int wp = 0; wp < 8; ++wp) sum += red[wp * 24 * C + o] + red[wp * 24 * C + 9 * C + o];
+    } else {
+#pragma unroll
+      for (int wp = 0; wp < 8; ++wp) sum += dbred[wp];
+    }
+    partial[(size_t)blockIdx.x * NW + o] = sum;
   }
 }
 
@@ -772,28 +1023,84 @@ bool halo_map(CUtensorMap* m, const tat_bf16* base, int batch, int H, int W) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Raises the dynamic shared-memory limit of `Kern` to `bytes` once per device.
+template <auto Kern>
+bool smem_attr(size_t bytes) {
+  static int done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return false;
+  }
+  if (!done[dev]) {
+    if (cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    done[dev] = 1;
+  }
+  return true;
+}
+
+bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) != 0; }
+
 template <bool BWD>
 tat_status launch_mid(int batch, int H, int W, const tat_bf16* in, const tat_bf16* mask, const tat_bf16* w,
                       const float* b, tat_bf16* out, cudaStream_t s, const char* what) {
-  if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(mask)) & 15) return TAT_ERR_INVALID_ARG;
+  if (misaligned(in) || misaligned(mask)) return TAT_ERR_INVALID_ARG;
   CUtensorMap mi, mm;
   if (!halo_map(&mi, in, batch, H, W) || !halo_map(&mm, BWD ? mask : in, batch, H, W)) {
     fprintf(stderr, "%s: tensor map encoding failed\n", what);
     return TAT_ERR_CUDA;
   }
-  static int attr_done[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-    if (cudaFuncSetAttribute(k_conv_mid<BWD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)mid_smem_bytes<BWD>()) != cudaSuccess) {
-      cudaGetLastError();
-      return TAT_ERR_CUDA;
-    }
-    attr_done[dev] = 1;
-  }
+  if (!smem_attr<k_conv_mid<BWD>>(mid_smem_bytes<BWD>())) return TAT_ERR_CUDA;
   k_conv_mid<BWD><<<mid_ctas(batch, H, W), 256, mid_smem_bytes<BWD>(), s>>>(batch, H, W, mi, mm, w, b, out);
   return launched(what);
+}
+
+// CTAs of the persistent thin-layer kernels: up to `per_sm` per SM, never more than the tiles.
+int thin_ctas(int batch, int H, int W, int per_sm) {
+  const long long tiles = (long long)batch * ((H + TY - 1) / TY) * ((W + TX - 1) / TX);
+  return (int)(tiles < per_sm * 152LL ? tiles : per_sm * 152LL);
+}
+
+template <int CIN, bool DATA, bool WGRAD>
+tat_status launch_in_bwd(int batch, int H, int W, const CUtensorMap& mg, const CUtensorMap& mh, const float* x0,
+                         const float* x1, const float* x2, const tat_bf16* w, float* gx0, float* gx1, float* gx2,
+                         int accumulate, float* scratch, int ctas, cudaStream_t s) {
+  constexpr size_t smem = in_bwd_smem_bytes<CIN>();
+  if (!smem_attr<k_conv_in_bwd<CIN, DATA, WGRAD>>(smem)) return TAT_ERR_CUDA;
+  k_conv_in_bwd<CIN, DATA, WGRAD><<<ctas, 256, smem, s>>>(batch, H, W, mg, mh, x0, x1, x2, w, gx0, gx1, gx2,
+                                                           accumulate, scratch);
+  return launched("tat_conv_in_bwd");
+}
+
+template <int CIN>
+tat_status in_bwd(int batch, int H, int W, const float* x0, const float* x1, const float* x2, const tat_bf16* g_h,
+                  const tat_bf16* h, const tat_bf16* w, float* gx0, float* gx1, float* gx2, int accumulate,
+                  float* scratch, size_t scratch_floats, float* gw, float* gb, cudaStream_t s) {
+  const bool data = gx0 || gx1 || gx2, wgrad = gw != nullptr;
+  if (!data && !wgrad) return TAT_OK;
+  const int ctas = thin_ctas(batch, H, W, 2);
+  const int nw = (9 * CIN + 1) * C;
+  if (wgrad && scratch_floats < (size_t)ctas * nw) return TAT_ERR_INVALID_ARG;
+  CUtensorMap mg, mh;
+  if (!halo_map(&mg, g_h, batch, H, W) || !halo_map(&mh, h, batch, H, W)) {
+    fprintf(stderr, "tat_conv_in_bwd: tensor map encoding failed\n");
+    return TAT_ERR_CUDA;
+  }
+  tat_status st;
+  if (data && wgrad)
+    st = launch_in_bwd<CIN, true, true>(batch, H, W, mg, mh, x0, x1, x2, w, gx0, gx1, gx2, accumulate, scratch, ctas, s);
+  else if (data)
+    st = launch_in_bwd<CIN, true, false>(batch, H, W, mg, mh, x0, x1, x2, w, gx0, gx1, gx2, accumulate, scratch, ctas,
+                                         s);
+  else
+    st = launch_in_bwd<CIN, false, true>(batch, H, W, mg, mh, x0, x1, x2, w, gx0, gx1, gx2, accumulate, scratch, ctas,
+                                         s);
+  if (st != TAT_OK || !wgrad) return st;
+  k_reduce_partials<<<(nw + 31) / 32, 256, 0, s>>>(ctas, 9 * CIN * C, C, scratch, gw, gb);
+  return launched("tat_conv_in_bwd");
 }
 
 int wgrad_ctas(int batch, int H, int W) {
@@ -807,8 +1114,7 @@ extern "C" {
 
 size_t tat_lpd_scratch_floats(int batch, int H, int W) {
   if (bad_sizes(batch, H, W)) return 0;
-  const size_t a = (size_t)kMaxCtas * (9 * C * C + C), b = (size_t)kRedCtas * (9 * 3 * C + C);
-  return a > b ? a : b;
+  return (size_t)kMaxCtas * (9 * C * C + C);  // the largest of the per-CTA partial sets
 }
 
 tat_status tat_conv_in_fwd(int batch, int H, int W, int cin, const float* x0, const float* x1, const float* x2,
@@ -816,40 +1122,40 @@ tat_status tat_conv_in_fwd(int batch, int H, int W, int cin, const float* x0, co
   if (bad_sizes(batch, H, W) || (cin != 2 && cin != 3) || !x0 || !x1 || (cin == 3 && !x2) || !w || !b || !h)
     return TAT_ERR_INVALID_ARG;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const long long n = (long long)batch * H * W;
-  if (cin == 2) k_conv_in_fwd<2><<<blocks_for(n, 256), 256, 0, s>>>(batch, H, W, x0, x1, nullptr, w, b, h);
-  else k_conv_in_fwd<3><<<blocks_for(n, 256), 256, 0, s>>>(batch, H, W, x0, x1, x2, w, b, h);
+  const int ctas = thin_ctas(batch, H, W, 3);
+  if (cin == 2) k_conv_in_fwd<2><<<ctas, 256, 0, s>>>(batch, H, W, x0, x1, nullptr, w, b, h);
+  else k_conv_in_fwd<3><<<ctas, 256, 0, s>>>(batch, H, W, x0, x1, x2, w, b, h);
   return launched("tat_conv_in_fwd");
+}
+
+tat_status tat_conv_in_bwd(int batch, int H, int W, int cin, const float* x0, const float* x1, const float* x2,
+                           const tat_bf16* g_h, const tat_bf16* h, const tat_bf16* w, float* gx0, float* gx1,
+                           float* gx2, int accumulate, float* scratch, size_t scratch_floats, float* gw, float* gb,
+                           tat_stream_t stream) {
+  if (bad_sizes(batch, H, W) || (cin != 2 && cin != 3) || !g_h || !h || misaligned(g_h) || misaligned(h))
+    return TAT_ERR_INVALID_ARG;
+  if ((gx0 || gx1 || gx2) && !w) return TAT_ERR_INVALID_ARG;
+  if (gw && (!x0 || !x1 || (cin == 3 && !x2) || !scratch || !gb)) return TAT_ERR_INVALID_ARG;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cin == 2)
+    return in_bwd<2>(batch, H, W, x0, x1, nullptr, g_h, h, w, gx0, gx1, nullptr, accumulate, scratch, scratch_floats,
+                     gw, gb, s);
+  return in_bwd<3>(batch, H, W, x0, x1, x2, g_h, h, w, gx0, gx1, gx2, accumulate, scratch, scratch_floats, gw, gb, s);
 }
 
 tat_status tat_conv_in_bwd_data(int batch, int H, int W, int cin, const tat_bf16* g_h, const tat_bf16* h,
                                 const tat_bf16* w, float* gx0, float* gx1, float* gx2, int accumulate,
                                 tat_stream_t stream) {
-  if (bad_sizes(batch, H, W) || (cin != 2 && cin != 3) || !g_h || !h || !w) return TAT_ERR_INVALID_ARG;
-  const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const long long n = (long long)batch * H * W;
-  if (cin == 2) k_conv_in_bwd_data<2><<<blocks_for(n, 256), 256, 0, s>>>(batch, H, W, g_h, h, w, gx0, gx1, nullptr, accumulate);
-  else k_conv_in_bwd_data<3><<<blocks_for(n, 256), 256, 0, s>>>(batch, H, W, g_h, h, w, gx0, gx1, gx2, accumulate);
-  return launched("tat_conv_in_bwd_data");
+  return tat_conv_in_bwd(batch, H, W, cin, nullptr, nullptr, nullptr, g_h, h, w, gx0, gx1, cin == 3 ? gx2 : nullptr,
+                         accumulate, nullptr, 0, nullptr, nullptr, stream);
 }
 
 tat_status tat_conv_in_bwd_weights(int batch, int H, int W, int cin, const float* x0, const float* x1,
                                    const float* x2, const tat_bf16* g_h, const tat_bf16* h, float* scratch,
                                    size_t scratch_floats, float* gw, float* gb, tat_stream_t stream) {
-  if (bad_sizes(batch, H, W) || (cin != 2 && cin != 3) || !x0 || !x1 || (cin == 3 && !x2) || !g_h || !h ||
-      !scratch || !gw || !gb)
-    return TAT_ERR_INVALID_ARG;
-  const int nw = 9 * cin * C + C;
-  const long long total = (long long)batch * H * W;
-  const int ctas = (int)((total + 63) / 64 < kRedCtas ? (total + 63) / 64 : kRedCtas);
-  if (scratch_floats < (size_t)ctas * nw) return TAT_ERR_INVALID_ARG;
-  const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cin == 2) k_conv_in_bwd_weights<2><<<ctas, 256, 0, s>>>(batch, H, W, x0, x1, nullptr, g_h, h, scratch);
-  else k_conv_in_bwd_weights<3><<<ctas, 256, 0, s>>>(batch, H, W, x0, x1, x2, g_h, h, scratch);
-  tat_status st = launched("tat_conv_in_bwd_weights");
-  if (st != TAT_OK) return st;
-  k_reduce_partials<<<(nw + 31) / 32, 256, 0, s>>>(ctas, 9 * cin * C, C, scratch, gw, gb);
-  return launched("tat_conv_in_bwd_weights");
+  if (!gw) return TAT_ERR_INVALID_ARG;
+  return tat_conv_in_bwd(batch, H, W, cin, x0, x1, x2, g_h, h, nullptr, nullptr, nullptr, nullptr, 0, scratch,
+                         scratch_floats, gw, gb, stream);
 }
 
 tat_status tat_conv_mid_fwd(int batch, int H, int W, const tat_bf16* h_in, const tat_bf16* w, const float* b,
@@ -895,26 +1201,34 @@ tat_status tat_conv_mid_bwd_weights(int batch, int H, int W, const tat_bf16* h_i
 
 tat_status tat_conv_out_fwd(int batch, int H, int W, const tat_bf16* h, const tat_bf16* w, const float* b,
                             const float* residual, float* out, tat_stream_t stream) {
-  if (bad_sizes(batch, H, W) || !h || !w || !b || !residual || !out) return TAT_ERR_INVALID_ARG;
-  const long long n = (long long)batch * H * W;
-  k_conv_out_fwd<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(batch, H, W, h, w, b, residual,
-                                                                                      out);
+  if (bad_sizes(batch, H, W) || !h || !w || !b || !residual || !out || misaligned(h)) return TAT_ERR_INVALID_ARG;
+  CUtensorMap mh;
+  if (!halo_map(&mh, h, batch, H, W)) {
+    fprintf(stderr, "tat_conv_out_fwd: tensor map encoding failed\n");
+    return TAT_ERR_CUDA;
+  }
+  if (!smem_attr<k_conv_out_fwd>(out_fwd_smem_bytes())) return TAT_ERR_CUDA;
+  k_conv_out_fwd<<<thin_ctas(batch, H, W, 3), 256, out_fwd_smem_bytes(), static_cast<cudaStream_t>(stream)>>>(
+      batch, H, W, mh, w, b, residual, out);
   return launched("tat_conv_out_fwd");
 }
 
 tat_status tat_conv_out_bwd(int batch, int H, int W, const float* g_out, const tat_bf16* h, const tat_bf16* w,
                             tat_bf16* g_h, float* scratch, size_t scratch_floats, float* gw, float* gb,
                             tat_stream_t stream) {
-  if (bad_sizes(batch, H, W) || !g_out || !h || !w || !g_h || !scratch || !gw || !gb) return TAT_ERR_INVALID_ARG;
-  const long long n = (long long)batch * H * W;
-  const int ctas = (int)((n + 63) / 64 < kRedCtas ? (n + 63) / 64 : kRedCtas);
+  if (bad_sizes(batch, H, W) || !g_out || !h || !w || !g_h || !scratch || !gw || !gb || misaligned(h))
+    return TAT_ERR_INVALID_ARG;
+  const int ctas = thin_ctas(batch, H, W, 2);
   if (scratch_floats < (size_t)ctas * (9 * C + 1)) return TAT_ERR_INVALID_ARG;
+  CUtensorMap mh;
+  if (!halo_map(&mh, h, batch, H, W)) {
+    fprintf(stderr, "tat_conv_out_bwd: tensor map encoding failed\n");
+    return TAT_ERR_CUDA;
+  }
+  if (!smem_attr<k_conv_out_bwd>(out_bwd_smem_bytes())) return TAT_ERR_CUDA;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  k_conv_out_bwd_data<<<blocks_for(n, 256), 256, 0, s>>>(batch, H, W, g_out, w, g_h);
+  k_conv_out_bwd<<<ctas, 256, out_bwd_smem_bytes(), s>>>(batch, H, W, mh, g_out, w, g_h, scratch);
   tat_status st = launched("tat_conv_out_bwd");
-  if (st != TAT_OK) return st;
-  k_conv_out_wgrad<<<ctas, 256, 0, s>>>(batch, H, W, g_out, h, scratch);
-  st = launched("tat_conv_out_bwd");
   if (st != TAT_OK) return st;
   k_reduce_partials<<<(9 * C + 1 + 31) / 32, 256, 0, s>>>(ctas, 9 * C, 1, scratch, gw, gb);
   return launched("tat_conv_out_bwd");

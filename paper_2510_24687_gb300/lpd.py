@@ -171,11 +171,9 @@ class LPD:
         B.tat_conv_mid_bwd_data(Bn, H, W, g_h2.data_ptr(), h2.data_ptr(), self._w(net, "w_mid"), g_h1.data_ptr(), s)
         B.tat_conv_mid_bwd_weights(Bn, H, W, h1.data_ptr(), g_h2.data_ptr(), h2.data_ptr(), sc, nsc,
                                    self._g(net, "w_mid"), self._g(net, "b_mid"), s)
-        B.tat_conv_in_bwd_data(Bn, H, W, cin, g_h1.data_ptr(), h1.data_ptr(), self._w(net, "w_in"), gx0.data_ptr(),
-                               gx1.data_ptr(), 0, acc_mask, s)
-        B.tat_conv_in_bwd_weights(Bn, H, W, cin, x0.data_ptr(), x1.data_ptr(), x2.data_ptr() if x2 is not None else 0,
-                                  g_h1.data_ptr(), h1.data_ptr(), sc, nsc, self._g(net, "w_in"), self._g(net, "b_in"),
-                                  s)
+        B.tat_conv_in_bwd(Bn, H, W, cin, x0.data_ptr(), x1.data_ptr(), x2.data_ptr() if x2 is not None else 0,
+                          g_h1.data_ptr(), h1.data_ptr(), self._w(net, "w_in"), gx0.data_ptr(), gx1.data_ptr(), 0,
+                          acc_mask, sc, nsc, self._g(net, "w_in"), self._g(net, "b_in"), s)
 
     def _backward(self):
         """Gradient of the loss w.r.t. all parameters into self.grad (zeroed first)."""

@@ -83,3 +83,23 @@ def test_default_descriptor_is_the_papers(pkg):
     assert d.arc_begin == 0.0 and abs(d.arc_len - 2 * math.pi) < 1e-15
     info = pkg.tat_plan_query(d)
     assert info["n_phi"] == 360 and info["K"] == 180
+
+
+def test_lpd_layers_reject_bad_arguments_before_any_device_work(pkg):
+    """Argument checks of the convolution layers return before touching memory: misaligned
+    activation pointers (the TMA-staged layers need 16 bytes), a missing weight pointer for
+    data gradients, a scratch buffer that is too small."""
+    bad = pkg.TatError
+    fake, odd = 1 << 20, (1 << 20) + 2           # never dereferenced
+    with pytest.raises(bad):
+        pkg.tat_conv_out_fwd(1, 8, 16, odd, fake, fake, fake, fake)
+    with pytest.raises(bad):
+        pkg.tat_conv_mid_fwd(1, 8, 16, odd, fake, fake, fake)
+    with pytest.raises(bad):
+        pkg.tat_conv_in_bwd(1, 8, 16, 3, fake, fake, fake, odd, fake, fake, fake, 0, 0, 0, 0, 0, 0, 0)
+    with pytest.raises(bad):
+        pkg.tat_conv_in_bwd(1, 8, 16, 3, fake, fake, fake, fake, fake, 0, fake, 0, 0, 0, 0, 0, 0, 0)
+    with pytest.raises(bad):
+        pkg.tat_conv_out_bwd(1, 8, 16, fake, fake, fake, fake, fake, 1, fake, fake)
+    with pytest.raises(bad):
+        pkg.tat_conv_in_fwd(1, 8, 16, 4, fake, fake, fake, fake, fake, fake)

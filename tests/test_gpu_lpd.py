@@ -101,6 +101,16 @@ def test_conv_in_forward_backward(pkg, torch, cin):
     gwr = Wt.grad.permute(2, 3, 1, 0).reshape(-1).numpy()                        # back to [tap][ci][co]
     assert rel(gw.cpu().numpy(), gwr) <= 1e-4
     assert rel(gb.cpu().numpy(), Bt.grad.numpy()) <= 1e-4
+    # the fused call: both gradients in one pass, weight gradients accumulated onto the first ones
+    gx2_ = [torch.full((B_, H_, W_), 7.0, device="cuda") for _ in range(cin)]
+    pkg.tat_conv_in_bwd(B_, H_, W_, cin, xd[0].data_ptr(), xd[1].data_ptr(), xd[2].data_ptr() if cin == 3 else 0,
+                        Gd.data_ptr(), h.data_ptr(), wd.data_ptr(), gx2_[0].data_ptr(), gx2_[1].data_ptr(),
+                        gx2_[2].data_ptr() if cin == 3 else 0, 0b01, scratch.data_ptr(), scratch.numel(),
+                        gw.data_ptr(), gb.data_ptr(), s)
+    assert rel(np.stack([t.cpu().numpy() for t in gx2_], 1), gxr) <= 1e-5
+    assert rel(gw.cpu().numpy(), 2 * gwr) <= 1e-4
+    assert rel(gb.cpu().numpy(), 2 * Bt.grad.numpy()) <= 1e-4
+    pkg.tat_lpd_check()
 
 
 def test_conv_mid_forward_backward(pkg, torch):
@@ -160,6 +170,7 @@ def test_conv_out_forward_backward(pkg, torch):
     assert rel(host_bf16(torch, gh).permute(0, 3, 1, 2), r16(torch, X.grad)) <= 1e-3
     assert rel(gw.cpu().numpy(), Wt.grad[0].permute(1, 2, 0).reshape(-1).numpy()) <= 1e-4
     assert rel(gb.cpu().numpy(), Bt.grad.numpy()) <= 1e-4
+    pkg.tat_lpd_check()
 
 
 def _problem(pkg, torch, n=32, B=2, seed=0):
