@@ -967,29 +967,27 @@ def lpd_kernel_roofline(pkg, stream, dev, peaks):
     calls = {
         "tat_conv_in_fwd (cin=3)": (
             lambda: pkg.tat_conv_in_fwd(B, H, W, 3, a(x[0]), a(x[1]), a(x[2]), a(w_in), a(bias), a(h_in), s),
-            2 * P * 27 * C, P * (12 + 2 * C), "alu", "k_conv_in_fwd<3>"),
-        "tat_conv_in_bwd_data (cin=3)": (
-            lambda: pkg.tat_conv_in_bwd_data(B, H, W, 3, a(g_h), a(h_in), a(w_in), a(gx[0]), a(gx[1]), a(gx[2]), 0, s),
-            2 * P * 27 * C, P * (4 * C + 12), "alu", "k_conv_in_bwd_data<3>"),
-        "tat_conv_in_bwd_weights (cin=3)": (
-            lambda: pkg.tat_conv_in_bwd_weights(B, H, W, 3, a(x[0]), a(x[1]), a(x[2]), a(g_h), a(h_in), a(scr), nscr,
-                                                a(gw), a(gb), s),
-            2 * P * 27 * C, P * (12 + 4 * C), "alu", "k_conv_in_bwd_weights<3> + k_reduce_partials"),
+            2 * P * 27 * C, P * (12 + 2 * C), "tensor", "k_conv_in_fwd<3>"),
+        "tat_conv_in_bwd (cin=3, data + weights, pre-masked)": (
+            lambda: pkg.tat_conv_in_bwd(B, H, W, 3, a(x[0]), a(x[1]), a(x[2]), a(g_h), 0, a(w_in), a(gx[0]),
+                                        a(gx[1]), a(gx[2]), 0, a(scr), nscr, a(gw), a(gb), s),
+            4 * P * 27 * C, P * (2 * C + 24), "tensor", "k_conv_in_bwd<3, 0> + k_reduce_partials"),
         "tat_conv_mid_fwd": (
             lambda: pkg.tat_conv_mid_fwd(B, H, W, a(h_in), a(w_mid), a(bias), a(h_out), s),
-            2 * P * 9 * C * C, P * 4 * C, "tensor", "k_conv_mid<0>"),
-        "tat_conv_mid_bwd_data": (
-            lambda: pkg.tat_conv_mid_bwd_data(B, H, W, a(g_h), a(h_out), a(w_mid), a(g_in), s),
-            2 * P * 9 * C * C, P * 6 * C, "tensor", "k_conv_mid<1>"),
-        "tat_conv_mid_bwd_weights": (
-            lambda: pkg.tat_conv_mid_bwd_weights(B, H, W, a(h_in), a(g_h), a(h_out), a(scr), nscr, a(gw), a(gb), s),
-            2 * P * 9 * C * C, P * 6 * C, "tensor", "k_conv_mid_wgrad + k_reduce_partials"),
+            2 * P * 9 * C * C, P * 4 * C, "tensor", "k_conv_mid<0, 0, 0>"),
+        "tat_conv_mid_bwd_data (pre-masked, masks its output)": (
+            lambda: pkg.tat_conv_mid_bwd_data(B, H, W, a(g_h), 0, a(w_mid), a(h_in), a(g_in), s),
+            2 * P * 9 * C * C, P * 6 * C, "tensor", "k_conv_mid<1, 0, 1>"),
+        "tat_conv_mid_bwd_weights (pre-masked)": (
+            lambda: pkg.tat_conv_mid_bwd_weights(B, H, W, a(h_in), a(g_h), 0, a(scr), nscr, a(gw), a(gb), s),
+            2 * P * 9 * C * C, P * 4 * C, "tensor", "k_conv_mid_wgrad<0> + k_reduce_partials"),
         "tat_conv_out_fwd": (
             lambda: pkg.tat_conv_out_fwd(B, H, W, a(h_out), a(w_out), a(bias), a(x[0]), a(out), s),
-            2 * P * 9 * C, P * (2 * C + 8), "alu", "k_conv_out_fwd"),
+            2 * P * 9 * C, P * (2 * C + 8), "tensor", "k_conv_out_fwd"),
         "tat_conv_out_bwd": (
-            lambda: pkg.tat_conv_out_bwd(B, H, W, a(gout), a(h_out), a(w_out), a(g_in), a(scr), nscr, a(gw), a(gb), s),
-            4 * P * 9 * C, P * (4 + 4 * C), "alu", "k_conv_out_bwd_data + k_conv_out_wgrad + k_reduce_partials"),
+            lambda: pkg.tat_conv_out_bwd(B, H, W, a(gout), a(h_out), a(w_out), 1, a(g_in), a(scr), nscr, a(gw), a(gb),
+                                         s),
+            4 * P * 9 * C, P * (4 + 4 * C), "tensor", "k_conv_out_bwd<1> + k_reduce_partials"),
     }
     reps = 20
     times = {}

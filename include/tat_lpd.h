@@ -57,7 +57,8 @@ size_t tat_lpd_scratch_floats(int batch, int H, int W);
 tat_status tat_conv_in_fwd(int batch, int H, int W, int cin, const float* x0, const float* x1, const float* x2,
                            const tat_bf16* w, const float* b, tat_bf16* h, tat_stream_t stream);
 /* gx_c (+)= d/dx_c of <g_h, h> through the ReLU (mask h > 0); gx_c may be NULL;
- * bit c of `accumulate` set adds into gx_c, clear overwrites it. */
+ * bit c of `accumulate` set adds into gx_c, clear overwrites it.  h == NULL here
+ * and below: g_h is already masked (tat_conv_mid_bwd_data with h_in writes it so). */
 tat_status tat_conv_in_bwd_data(int batch, int H, int W, int cin, const tat_bf16* g_h, const tat_bf16* h,
                                 const tat_bf16* w, float* gx0, float* gx1, float* gx2, int accumulate,
                                 tat_stream_t stream);
@@ -75,10 +76,14 @@ tat_status tat_conv_in_bwd(int batch, int H, int W, int cin, const float* x0, co
 /* h_out = relu(conv_mid(h_in) + b)  (tensor cores). */
 tat_status tat_conv_mid_fwd(int batch, int H, int W, const tat_bf16* h_in, const tat_bf16* w, const float* b,
                             tat_bf16* h_out, tat_stream_t stream);
-/* g_in = d/dh_in of <g_out, h_out> through the ReLU (tensor cores; BF16 output). */
+/* g_in = d/dh_in of <g_out, h_out> through the ReLU (tensor cores; BF16 output).
+ * h_out == NULL: g_out is already the gradient of the pre-activation (masked by
+ * the ReLU, as tat_conv_out_bwd with mask_relu writes it).  h_in != NULL: g_in
+ * is multiplied by [h_in > 0], i.e. it is the gradient of the in layer's
+ * pre-activation (h_in being that layer's ReLU output). */
 tat_status tat_conv_mid_bwd_data(int batch, int H, int W, const tat_bf16* g_out, const tat_bf16* h_out,
-                                 const tat_bf16* w, tat_bf16* g_in, tat_stream_t stream);
-/* gw += d/dw, gb += d/db of <g_out, h_out> (tensor cores). */
+                                 const tat_bf16* w, const tat_bf16* h_in, tat_bf16* g_in, tat_stream_t stream);
+/* gw += d/dw, gb += d/db of <g_out, h_out> (tensor cores; h_out == NULL as above). */
 tat_status tat_conv_mid_bwd_weights(int batch, int H, int W, const tat_bf16* h_in, const tat_bf16* g_out,
                                     const tat_bf16* h_out, float* scratch, size_t scratch_floats, float* gw,
                                     float* gb, tat_stream_t stream);
@@ -86,9 +91,11 @@ tat_status tat_conv_mid_bwd_weights(int batch, int H, int W, const tat_bf16* h_i
 /* out = residual + conv_out(h) + b; out may alias residual. */
 tat_status tat_conv_out_fwd(int batch, int H, int W, const tat_bf16* h, const tat_bf16* w, const float* b,
                             const float* residual, float* out, tat_stream_t stream);
-/* g_h = d/dh <g_out, out> (BF16), gw += d/dw, gb += d/db.  (d/d residual = g_out.) */
+/* g_h = d/dh <g_out, out> (BF16), times [h > 0] when mask_relu != 0 (then g_h is
+ * the gradient of the mid layer's pre-activation, h being that layer's ReLU
+ * output); gw += d/dw, gb += d/db.  (d/d residual = g_out.) */
 tat_status tat_conv_out_bwd(int batch, int H, int W, const float* g_out, const tat_bf16* h, const tat_bf16* w,
-                            tat_bf16* g_h, float* scratch, size_t scratch_floats, float* gw, float* gb,
+                            int mask_relu, tat_bf16* g_h, float* scratch, size_t scratch_floats, float* gw, float* gb,
                             tat_stream_t stream);
 
 /* TAT_ERR_TIMEOUT (and the flag cleared) if a tensor-core convolution gave up

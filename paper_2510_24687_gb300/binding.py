@@ -118,10 +118,10 @@ def load() -> ctypes.CDLL:
         "tat_conv_in_bwd": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I, _P, ctypes.c_size_t, _P, _P,
                                  _P]),
         "tat_conv_mid_fwd": (_I, [_I, _I, _I, _P, _P, _P, _P, _P]),
-        "tat_conv_mid_bwd_data": (_I, [_I, _I, _I, _P, _P, _P, _P, _P]),
+        "tat_conv_mid_bwd_data": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P]),
         "tat_conv_mid_bwd_weights": (_I, [_I, _I, _I, _P, _P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
         "tat_conv_out_fwd": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P]),
-        "tat_conv_out_bwd": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P, _P]),
+        "tat_conv_out_bwd": (_I, [_I, _I, _I, _P, _P, _P, _I, _P, _P, ctypes.c_size_t, _P, _P, _P]),
         "tat_adam": (_I, [_LL, _F, _F, _F, _F, _I, _P, _P, _P, _P, _P, _P]),
         "tat_to_bf16": (_I, [_LL, _P, _P, _P]),
         "tat_fill": (_I, [_LL, _F, _P, _P]),
@@ -361,18 +361,19 @@ def tat_conv_in_fwd(batch, H, W, cin, x0, x1, x2, w, b, h, stream=0):
 
 
 def tat_conv_in_bwd_data(batch, H, W, cin, g_h, h, w, gx0, gx1, gx2, accumulate, stream=0):
-    _check(load().tat_conv_in_bwd_data(batch, H, W, cin, g_h, h, w, gx0 or None, gx1 or None, gx2 or None,
+    _check(load().tat_conv_in_bwd_data(batch, H, W, cin, g_h, h or None, w, gx0 or None, gx1 or None, gx2 or None,
                                        accumulate, stream or None), "tat_conv_in_bwd_data")
 
 
 def tat_conv_in_bwd_weights(batch, H, W, cin, x0, x1, x2, g_h, h, scratch, scratch_floats, gw, gb, stream=0):
-    _check(load().tat_conv_in_bwd_weights(batch, H, W, cin, x0, x1, x2 or None, g_h, h, scratch, scratch_floats, gw,
+    _check(load().tat_conv_in_bwd_weights(batch, H, W, cin, x0, x1, x2 or None, g_h, h or None, scratch, scratch_floats, gw,
                                           gb, stream or None), "tat_conv_in_bwd_weights")
 
 
 def tat_conv_in_bwd(batch, H, W, cin, x0, x1, x2, g_h, h, w, gx0, gx1, gx2, accumulate, scratch, scratch_floats, gw,
                     gb, stream=0):
-    _check(load().tat_conv_in_bwd(batch, H, W, cin, x0 or None, x1 or None, x2 or None, g_h, h, w or None, gx0 or None,
+    _check(load().tat_conv_in_bwd(batch, H, W, cin, x0 or None, x1 or None, x2 or None, g_h, h or None, w or None,
+                                  gx0 or None,
                                   gx1 or None, gx2 or None, accumulate, scratch or None, scratch_floats, gw or None,
                                   gb or None, stream or None), "tat_conv_in_bwd")
 
@@ -381,12 +382,13 @@ def tat_conv_mid_fwd(batch, H, W, h_in, w, b, h_out, stream=0):
     _check(load().tat_conv_mid_fwd(batch, H, W, h_in, w, b, h_out, stream or None), "tat_conv_mid_fwd")
 
 
-def tat_conv_mid_bwd_data(batch, H, W, g_out, h_out, w, g_in, stream=0):
-    _check(load().tat_conv_mid_bwd_data(batch, H, W, g_out, h_out, w, g_in, stream or None), "tat_conv_mid_bwd_data")
+def tat_conv_mid_bwd_data(batch, H, W, g_out, h_out, w, h_in, g_in, stream=0):
+    _check(load().tat_conv_mid_bwd_data(batch, H, W, g_out, h_out or None, w, h_in or None, g_in, stream or None),
+           "tat_conv_mid_bwd_data")
 
 
 def tat_conv_mid_bwd_weights(batch, H, W, h_in, g_out, h_out, scratch, scratch_floats, gw, gb, stream=0):
-    _check(load().tat_conv_mid_bwd_weights(batch, H, W, h_in, g_out, h_out, scratch, scratch_floats, gw, gb,
+    _check(load().tat_conv_mid_bwd_weights(batch, H, W, h_in, g_out, h_out or None, scratch, scratch_floats, gw, gb,
                                            stream or None), "tat_conv_mid_bwd_weights")
 
 
@@ -394,9 +396,9 @@ def tat_conv_out_fwd(batch, H, W, h, w, b, residual, out, stream=0):
     _check(load().tat_conv_out_fwd(batch, H, W, h, w, b, residual, out, stream or None), "tat_conv_out_fwd")
 
 
-def tat_conv_out_bwd(batch, H, W, g_out, h, w, g_h, scratch, scratch_floats, gw, gb, stream=0):
-    _check(load().tat_conv_out_bwd(batch, H, W, g_out, h, w, g_h, scratch, scratch_floats, gw, gb, stream or None),
-           "tat_conv_out_bwd")
+def tat_conv_out_bwd(batch, H, W, g_out, h, w, mask_relu, g_h, scratch, scratch_floats, gw, gb, stream=0):
+    _check(load().tat_conv_out_bwd(batch, H, W, g_out, h, w, int(mask_relu), g_h, scratch, scratch_floats, gw, gb,
+                                   stream or None), "tat_conv_out_bwd")
 
 
 def tat_adam(count, lr, beta1, beta2, eps, step, param, grad, m, v, w_bf16, stream=0):

@@ -47,22 +47,6 @@ tat_status launched(const char* what) {
 __device__ __forceinline__ float bf(const tat_bf16 v) { return __bfloat162float(__ushort_as_bfloat16(v)); }
 __device__ __forceinline__ tat_bf16 tobf(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
 
-// 8 BF16 values (16 bytes) <-> floats
-__device__ __forceinline__ void unpack8(const uint4& u, float* f) {
-  const unsigned w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    f[2 * i] = bf((tat_bf16)(w[i] & 0xffffu));
-    f[2 * i + 1] = bf((tat_bf16)(w[i] >> 16));
-  }
-}
-__device__ __forceinline__ uint4 pack8(const float* f) {
-  unsigned w[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) w[i] = (unsigned)tobf(f[2 * i]) | ((unsigned)tobf(f[2 * i + 1]) << 16);
-  return make_uint4(w[0], w[1], w[2], w[3]);
-}
-
 #define GRID_STRIDE(i, n) \
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
@@ -105,34 +89,6 @@ __device__ __forceinline__ void mma_bf16(float* d, const unsigned* a, const unsi
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-
-// Loads the (TY+2) x (TX+2) x 32 halo of image b around the tile (y0, x0) into
-// hs[(TY+2)*(TX+2)][CP]; out-of-image pixels are zero.  With MASK the value is
-// v * [m > 0] (the ReLU mask of the layer's forward output).
-template <bool MASK>
-__device__ __forceinline__ void load_halo(tat_bf16* hs, const tat_bf16* __restrict__ v, const tat_bf16* __restrict__ m,
-                                          int b, int y0, int x0, int H, int W) {
-  constexpr int NP = (TY + 2) * (TX + 2);
-  for (int e = threadIdx.x; e < NP * 4; e += blockDim.x) {
-    const int pix = e >> 2, q = e & 3;
-    const int yy = y0 - 1 + pix / (TX + 2), xx = x0 - 1 + pix % (TX + 2);
-    uint4 u = make_uint4(0u, 0u, 0u, 0u);
-    if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-      const long long o = (((long long)b * H + yy) * W + xx) * C + 8 * q;
-      u = *reinterpret_cast<const uint4*>(v + o);
-      if (MASK) {
-        const uint4 mu = *reinterpret_cast<const uint4*>(m + o);
-        float fv[8], fm[8];
-        unpack8(u, fv);
-        unpack8(mu, fm);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) fv[k] = fm[k] > 0.f ? fv[k] : 0.f;
-        u = pack8(fv);
-      }
-    }
-    *reinterpret_cast<uint4*>(hs + pix * CP + 8 * q) = u;
-  }
-}
 
 // ---- TMA staging of the halo
 
@@ -263,12 +219,16 @@ __device__ __forceinline__ void init_bars(uint64_t* bar) {
   }
 }
 
-// One 8 x 16 output tile of the mid layer from a staged halo (and, for BWD, the
+// One 8 x 16 output tile of the mid layer from a staged halo (and, with MASK, the
 // staged ReLU mask) and the staged weights.
 // FWD: out = relu(conv(in) + b).  BWD (data gradient): out = conv^T(g * [h > 0]),
-// i.e. the same implicit GEMM with the taps flipped and in/out channels swapped.
-template <bool BWD>
-__device__ __forceinline__ void mid_tile(const unsigned char* tile, const unsigned char* mtile, const tat_bf16* wsm,
+// i.e. the same implicit GEMM with the taps flipped and in/out channels swapped;
+// without MASK the gradient arrives already masked.  With OMASK the output is
+// multiplied by [h_in > 0] from the staged halo `otile` (the gradient of the
+// previous layer's pre-activation).
+template <bool BWD, bool MASK, bool OMASK>
+__device__ __forceinline__ void mid_tile(const unsigned char* tile, const unsigned char* mtile,
+                                         const unsigned char* otile, const tat_bf16* wsm,
                                          const float* __restrict__ bias, tat_bf16* __restrict__ out, int b, int y0,
                                          int x0, int H, int W) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -290,7 +250,7 @@ __device__ __forceinline__ void mid_tile(const unsigned char* tile, const unsign
       const int chunk = (2 * kc + (m >> 1)) ^ ((pa >> 1) & 3);
       unsigned a[4];
       ldsm_x4(a, tile + pa * 64 + (chunk << 4));
-      if (BWD) {
+      if (MASK) {
         unsigned mk[4];
         ldsm_x4(mk, mtile + pa * 64 + (chunk << 4));
 #pragma unroll
@@ -314,6 +274,7 @@ __device__ __forceinline__ void mid_tile(const unsigned char* tile, const unsign
     const int x = x0 + g + 8 * half;
     if (x >= W) continue;
     tat_bf16* dst = out + (((long long)b * H + y) * W + x) * C;
+    const int p = (warp + 1) * XW + g + 8 * half + 1;  // this pixel in a staged halo
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
       const int co = nt * 8 + 2 * t;
@@ -322,26 +283,31 @@ __device__ __forceinline__ void mid_tile(const unsigned char* tile, const unsign
         v0 = fmaxf(v0 + bias[co], 0.f);
         v1 = fmaxf(v1 + bias[co + 1], 0.f);
       }
-      *reinterpret_cast<unsigned*>(dst + co) = (unsigned)tobf(v0) | ((unsigned)tobf(v1) << 16);
+      unsigned v = (unsigned)tobf(v0) | ((unsigned)tobf(v1) << 16);
+      if (OMASK) v = relu_masked(v, *reinterpret_cast<const unsigned*>(swz(otile, p, nt) + 4 * t));
+      *reinterpret_cast<unsigned*>(dst + co) = v;
     }
   }
 }
 
-// Dynamic shared memory of the mid-layer kernel: alignment slack, two stages
-// (value tile, and for BWD the mask tile), the padded weights, two mbarriers.
-template <bool BWD>
+// Dynamic shared memory of the mid-layer kernel: alignment slack, two stages of NT
+// tiles (value tile, the mask tile with MASK, the output-mask tile with OMASK), the
+// padded weights, two mbarriers.
+template <int NT>
 constexpr size_t mid_smem_bytes() {
-  return 1024 + 2 * (BWD ? 2 : 1) * HALO_SLOT + 9 * C * CP * 2 + 2 * sizeof(uint64_t);
+  return 1024 + 2 * NT * HALO_SLOT + 9 * C * CP * 2 + 2 * sizeof(uint64_t);
 }
 
-template <bool BWD>
+template <bool BWD, bool MASK, bool OMASK>
 __global__ void __launch_bounds__(256) k_conv_mid(int B, int H, int W, const __grid_constant__ CUtensorMap map_in,
                                                   const __grid_constant__ CUtensorMap map_mask,
+                                                  const __grid_constant__ CUtensorMap map_omask,
                                                   const tat_bf16* __restrict__ w, const float* __restrict__ bias,
                                                   tat_bf16* __restrict__ out) {
   extern __shared__ unsigned char dsm[];
   unsigned char* sm = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);  // 1024-aligned (swizzle period)
-  constexpr int NT = BWD ? 2 : 1;
+  constexpr int NT = 1 + MASK + OMASK;
+  constexpr int OT = (1 + MASK) * HALO_SLOT;  // offset of the output-mask tile in a stage
   constexpr int STAGE = NT * HALO_SLOT;
   tat_bf16* wsm = reinterpret_cast<tat_bf16*>(sm + 2 * STAGE);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * STAGE + 9 * C * CP * 2);
@@ -358,91 +324,106 @@ __global__ void __launch_bounds__(256) k_conv_mid(int B, int H, int W, const __g
       B, H, W, bar, NT * HALO_BYTES,
       [&](int b, int y0, int x0, int s) {
         tma_load_4d(sm + s * STAGE, &map_in, 0, x0 - 1, y0 - 1, b, &bar[s]);
-        if (BWD) tma_load_4d(sm + s * STAGE + HALO_SLOT, &map_mask, 0, x0 - 1, y0 - 1, b, &bar[s]);
+        if (MASK) tma_load_4d(sm + s * STAGE + HALO_SLOT, &map_mask, 0, x0 - 1, y0 - 1, b, &bar[s]);
+        if (OMASK) tma_load_4d(sm + s * STAGE + OT, &map_omask, 0, x0 - 1, y0 - 1, b, &bar[s]);
       },
       [](int, int, int) {}, [] {},
       [&](int b, int y0, int x0, int s) {
-        mid_tile<BWD>(sm + s * STAGE, sm + s * STAGE + HALO_SLOT, wsm, bias, out, b, y0, x0, H, W);
+        mid_tile<BWD, MASK, OMASK>(sm + s * STAGE, sm + s * STAGE + HALO_SLOT, sm + s * STAGE + OT, wsm, bias, out, b,
+                                   y0, x0, H, W);
       });
 }
 
+// Dynamic shared memory of k_conv_mid_wgrad: alignment slack, two slots of three halos
+// (input, gradient, forward output -- the last unused when the gradient arrives masked),
+// two mbarriers.
+constexpr size_t wgrad_smem_bytes() { return 1024 + 2 * 3 * HALO_SLOT + 2 * sizeof(uint64_t); }
+
 // dW[tap][co][ci] = sum_p G'(p)[co] in(p + tap)[ci], db[co] = sum_p G'(p)[co],
-// G' = g * [h_out > 0].  9 warps, warp w = tap w; per-CTA partials.
-__global__ void __launch_bounds__(288) k_conv_mid_wgrad(int B, int H, int W, const tat_bf16* __restrict__ in,
-                                                        const tat_bf16* __restrict__ g,
-                                                        const tat_bf16* __restrict__ hout, float* partial) {
-  __shared__ __align__(16) tat_bf16 hs[(TY + 2) * (TX + 2) * CP];
-  __shared__ __align__(16) tat_bf16 gs[TY * TX * CP];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, t = lane & 3;
-  const int tilesx = (W + TX - 1) / TX, tilesy = (H + TY - 1) / TY;
-  const long long ntiles = (long long)B * tilesx * tilesy;
-  float acc[2][4][4];
+// G' = g * [h_out > 0] (or g itself, already masked, without MASK).  9 warps, warp w =
+// tap w: per tile row a K = 16 step with A = G'^T (ldmatrix.trans of the g and h_out
+// halos, masked in registers) and
+// B = the input row shifted by the tap; warp 0 also multiplies A by a column of
+// ones for db.  The three halos of the next tile arrive by TMA meanwhile.
+// Per-CTA partials [tap][co][ci] then [co].
+template <bool MASK>
+__global__ void __launch_bounds__(288, 2) k_conv_mid_wgrad(int B, int H, int W, const __grid_constant__ CUtensorMap map_in,
+                                                           const __grid_constant__ CUtensorMap map_g,
+                                                           const __grid_constant__ CUtensorMap map_h,
+                                                           float* __restrict__ partial) {
+  constexpr int STAGE = 3 * HALO_SLOT;
+  extern __shared__ unsigned char dsm[];
+  unsigned char* sm = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * STAGE);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int dy = warp / 3, dx = warp % 3, m = lane >> 3;
+  init_bars(bar);
+  __syncthreads();
+  float acc[2][4][4], accb[2][4];
 #pragma unroll
-  for (int mh = 0; mh < 2; ++mh)
+  for (int mh = 0; mh < 2; ++mh) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) accb[mh][k] = 0.f;
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt)
 #pragma unroll
       for (int k = 0; k < 4; ++k) acc[mh][nt][k] = 0.f;
-  float bsum = 0.f;  // thread co < 32 of warp 0
-  const int dy = warp / 3, dx = warp % 3;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int b = (int)(tile / (tilesx * tilesy));
-    const int r = (int)(tile % (tilesx * tilesy));
-    const int y0 = (r / tilesx) * TY, x0 = (r % tilesx) * TX;
-    __syncthreads();
-    load_halo<false>(hs, in, nullptr, b, y0, x0, H, W);
-    // masked gradient tile gs[pixel][co], pixel = row * TX + col; zero outside the image
-    for (int e = threadIdx.x; e < TY * TX * 4; e += blockDim.x) {
-      const int pix = e >> 2, q = e & 3;
-      const int yy = y0 + pix / TX, xx = x0 + pix % TX;
-      uint4 u = make_uint4(0u, 0u, 0u, 0u);
-      if (yy < H && xx < W) {
-        const long long o = (((long long)b * H + yy) * W + xx) * C + 8 * q;
-        float fv[8], fm[8];
-        unpack8(*reinterpret_cast<const uint4*>(g + o), fv);
-        unpack8(*reinterpret_cast<const uint4*>(hout + o), fm);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) fv[k] = fm[k] > 0.f ? fv[k] : 0.f;
-        u = pack8(fv);
-      }
-      *reinterpret_cast<uint4*>(gs + pix * CP + 8 * q) = u;
-    }
-    __syncthreads();
-    if (threadIdx.x < C)
-      for (int pix = 0; pix < TY * TX; ++pix) bsum += bf(gs[pix * CP + threadIdx.x]);
-    // K loop: one tile row (16 pixels) per step
-    const int m = lane >> 3, i = lane & 7;
-#pragma unroll 1
-    for (int row = 0; row < TY; ++row) {
-      unsigned a[2][4];
-#pragma unroll
-      for (int mh = 0; mh < 2; ++mh) {
-        // matrices: (co 0-7, px 0-7), (co 8-15, px 0-7), (co 0-7, px 8-15), (co 8-15, px 8-15) of A = G'^T
-        const int px = (m >= 2 ? 8 : 0) + i, co = mh * 16 + ((m & 1) ? 8 : 0);
-        ldsm_x4_trans(a[mh], gs + (row * TX + px) * CP + co);
-      }
-#pragma unroll
-      for (int np = 0; np < 2; ++np) {
-        // matrices: (ci of n-tile 2np, px 0-7), (2np, px 8-15), (2np+1, px 0-7), (2np+1, px 8-15)
-        const int px = ((m & 1) ? 8 : 0) + i, ci = (2 * np + (m >> 1)) * 8;
-        unsigned bq[4];
-        ldsm_x4_trans(bq, hs + ((row + dy) * (TX + 2) + px + dx) * CP + ci);
-#pragma unroll
-        for (int mh = 0; mh < 2; ++mh) {
-          mma_bf16(acc[mh][2 * np], a[mh], bq);
-          mma_bf16(acc[mh][2 * np + 1], a[mh], bq + 2);
-        }
-      }
-    }
   }
-  // partial layout: [tap][co][ci] then [co] for the bias
+  const unsigned ones[2] = {0x3f803f80u, 0x3f803f80u};
+  const bool ok = tile_loop(
+      B, H, W, bar, (MASK ? 3 : 2) * HALO_BYTES,
+      [&](int b, int y0, int x0, int s) {
+        unsigned char* slot = sm + s * STAGE;
+        tma_load_4d(slot, &map_in, 0, x0 - 1, y0 - 1, b, &bar[s]);
+        tma_load_4d(slot + HALO_SLOT, &map_g, 0, x0 - 1, y0 - 1, b, &bar[s]);
+        if (MASK) tma_load_4d(slot + 2 * HALO_SLOT, &map_h, 0, x0 - 1, y0 - 1, b, &bar[s]);
+      },
+      [](int, int, int) {}, [] {},
+      [&](int, int, int, int s) {
+        const unsigned char* it = sm + s * STAGE;
+        const unsigned char* gt = it + HALO_SLOT;
+        const unsigned char* ht = it + 2 * HALO_SLOT;
+#pragma unroll 2
+        for (int row = 0; row < TY; ++row) {
+          unsigned a[2][4];
+#pragma unroll
+          for (int mh = 0; mh < 2; ++mh) {
+            // matrices (co 0-7, px 0-7), (co 8-15, px 0-7), (co 0-7, px 8-15), (co 8-15, px 8-15) of G'^T
+            const int p = (row + 1) * XW + 1 + (m >> 1) * 8 + (lane & 7);
+            ldsm_x4_trans(a[mh], swz(gt, p, 2 * mh + (m & 1)));
+            if (MASK) {
+              unsigned mk[4];
+              ldsm_x4_trans(mk, swz(ht, p, 2 * mh + (m & 1)));
+#pragma unroll
+              for (int j = 0; j < 4; ++j) a[mh][j] = relu_masked(a[mh][j], mk[j]);
+            }
+          }
+#pragma unroll
+          for (int np = 0; np < 2; ++np) {
+            // matrices (ci of n-tile 2np, px 0-7), (2np, px 8-15), (2np+1, px 0-7), (2np+1, px 8-15)
+            const int p = (row + dy) * XW + dx + (m & 1) * 8 + (lane & 7);
+            unsigned bq[4];
+            ldsm_x4_trans(bq, swz(it, p, 2 * np + (m >> 1)));
+#pragma unroll
+            for (int mh = 0; mh < 2; ++mh) {
+              mma_bf16(acc[mh][2 * np], a[mh], bq);
+              mma_bf16(acc[mh][2 * np + 1], a[mh], bq + 2);
+            }
+          }
+          if (warp == 0) {
+            mma_bf16(accb[0], a[0], ones);
+            mma_bf16(accb[1], a[1], ones);
+          }
+        }
+      });
+  if (!ok) return;
   constexpr int NW = 9 * C * C + C;
   float* pp = partial + (size_t)blockIdx.x * NW;
 #pragma unroll
   for (int mh = 0; mh < 2; ++mh)
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
-      const int co = mh * 16 + gq, ci = nt * 8 + 2 * t;
+      const int co = mh * 16 + g, ci = nt * 8 + 2 * t;
       float* d0 = pp + (warp * C + co) * C + ci;
       float* d1 = pp + (warp * C + co + 8) * C + ci;
       d0[0] = acc[mh][nt][0];
@@ -450,7 +431,13 @@ __global__ void __launch_bounds__(288) k_conv_mid_wgrad(int B, int H, int W, con
       d1[0] = acc[mh][nt][2];
       d1[1] = acc[mh][nt][3];
     }
-  if (threadIdx.x < C) pp[9 * C * C + threadIdx.x] = bsum;
+  if (warp == 0 && t == 0) {
+#pragma unroll
+    for (int mh = 0; mh < 2; ++mh) {
+      pp[9 * C * C + mh * 16 + g] = accb[mh][0];
+      pp[9 * C * C + mh * 16 + g + 8] = accb[mh][2];
+    }
+  }
 }
 
 // ------------------------------------------------------------------ thin layers (tensor cores)
@@ -557,35 +544,44 @@ __global__ void __launch_bounds__(256) k_conv_in_fwd(int B, int H, int W, const 
       });
 }
 
-// Dynamic shared memory of k_conv_in_bwd: alignment slack, two slots of (g, h) halos, the
-// flipped weights [9][8][CP], two BF16 copies of the x halo (second one shifted by one
-// column, so that every pixel pair is a 4-byte word in one of them), two mbarriers.
-template <int CIN>
-constexpr size_t in_bwd_smem_bytes() {
-  return 1024 + 2 * 2 * HALO_SLOT + 9 * 8 * CP * 2 + 2 * CIN * XH * XP * 2 + 2 * sizeof(uint64_t);
-}
+// Layout of k_conv_in_bwd's dynamic shared memory: alignment slack; two slots of the g
+// halo (and, with MASK, the h halo), a region that afterwards holds the per-warp weight-
+// gradient sums; the flipped weights [9][8][CP]; two BF16 copies of the x halo (the second
+// shifted by one column, so that every pixel pair is a 4-byte word in one of them); two
+// mbarriers.
+template <int CIN, bool MASK>
+struct InBwdSmem {
+  static constexpr int STAGE = (MASK ? 2 : 1) * HALO_SLOT;
+  static constexpr int NTW = (9 * CIN + 1 + 7) / 8;  // n-tiles of the weight-gradient GEMM (with the ones column)
+  static constexpr int RED = 8 * NTW * 8 * C * 4;
+  static constexpr int REGION = 2 * STAGE > RED ? 2 * STAGE : RED;
+  static constexpr int XCOPY = CIN * XH * XP;
+  static constexpr int WSB = REGION, XS = WSB + 9 * 8 * CP * 2, BAR = XS + 2 * XCOPY * 2;
+  static constexpr size_t BYTES = 1024 + BAR + 2 * sizeof(uint64_t);
+};
 
-// Backward of the in layer in one pass over the tiles of g_h and h (G' = g_h * [h > 0]):
+// Backward of the in layer in one pass over the tiles of G' = g_h * [h > 0] (with MASK;
+// without it g_h arrives masked, as tat_conv_mid_bwd_data with h_in writes it):
 //   DATA : gx_c(p) = sum_{tap, co} G'(p - tap)[co] w[tap][c][co]   (A = shifted G', N = 8 >= CIN)
 //   WGRAD: dW[tap * CIN + c][co] = sum_p G'(p)[co] x_c(p + tap), db[co] = sum_p G'(p)[co]
 //          (A = G'^T by ldmatrix.trans, B = x pairs, plus a column of ones for db), per-CTA
 //          partials [9 CIN + 1][32].
-template <int CIN, bool DATA, bool WGRAD>
+// DATA and WGRAD are the bits 1 and 2 of `parts` (uniform branches).
+template <int CIN, bool MASK>
 __global__ void __launch_bounds__(256, 2) k_conv_in_bwd(int B, int H, int W, const __grid_constant__ CUtensorMap map_g,
                                                         const __grid_constant__ CUtensorMap map_h,
                                                         const float* __restrict__ x0, const float* __restrict__ x1,
                                                         const float* __restrict__ x2, const tat_bf16* __restrict__ w,
-                                                        float* gx0, float* gx1, float* gx2, int accumulate,
+                                                        float* gx0, float* gx1, float* gx2, int accumulate, int parts,
                                                         float* __restrict__ partial) {
-  constexpr int KV = 9 * CIN;
-  constexpr int NTW = (KV + 1 + 7) / 8;  // n-tiles of the weight-gradient GEMM (with the ones column)
-  constexpr int STAGE = 2 * HALO_SLOT;
-  constexpr int XCOPY = CIN * XH * XP;
+  using L = InBwdSmem<CIN, MASK>;
+  constexpr int KV = 9 * CIN, NTW = L::NTW, STAGE = L::STAGE, XCOPY = L::XCOPY;
+  const bool DATA = parts & 1, WGRAD = parts & 2;
   extern __shared__ unsigned char dsm[];
   unsigned char* sm = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
-  tat_bf16* wsb = reinterpret_cast<tat_bf16*>(sm + 2 * STAGE);
-  unsigned short* xs = reinterpret_cast<unsigned short*>(sm + 2 * STAGE + 9 * 8 * CP * 2);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * STAGE + 9 * 8 * CP * 2 + 2 * XCOPY * 2);
+  tat_bf16* wsb = reinterpret_cast<tat_bf16*>(sm + L::WSB);
+  unsigned short* xs = reinterpret_cast<unsigned short*>(sm + L::XS);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::BAR);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   if (DATA)
     for (int e = threadIdx.x; e < 9 * 8 * C; e += blockDim.x) {
@@ -616,10 +612,10 @@ __global__ void __launch_bounds__(256, 2) k_conv_in_bwd(int B, int H, int W, con
       for (int k = 0; k < 4; ++k) accw[mh][nt][k] = 0.f;
   float xv[kXPer];
   const bool ok = tile_loop(
-      B, H, W, bar, 2 * HALO_BYTES,
+      B, H, W, bar, (MASK ? 2 : 1) * HALO_BYTES,
       [&](int b, int y0, int x0c, int s) {
         tma_load_4d(sm + s * STAGE, &map_g, 0, x0c - 1, y0 - 1, b, &bar[s]);
-        tma_load_4d(sm + s * STAGE + HALO_SLOT, &map_h, 0, x0c - 1, y0 - 1, b, &bar[s]);
+        if (MASK) tma_load_4d(sm + s * STAGE + HALO_SLOT, &map_h, 0, x0c - 1, y0 - 1, b, &bar[s]);
       },
       [&](int b, int y0, int x0c) {
         if (WGRAD) x_prefetch<CIN>(xv, x0, x1, x2, b, y0, x0c, H, W);
@@ -651,11 +647,14 @@ __global__ void __launch_bounds__(256, 2) k_conv_in_bwd(int B, int H, int W, con
             const int pa = (warp + dy) * XW + dx + (m & 1) * 8 + (lane & 7);
 #pragma unroll
             for (int kc = 0; kc < 2; ++kc) {
-              unsigned a[4], mk[4];
+              unsigned a[4];
               ldsm_x4(a, swz(gt, pa, 2 * kc + (m >> 1)));
-              ldsm_x4(mk, swz(ht, pa, 2 * kc + (m >> 1)));
+              if (MASK) {
+                unsigned mk[4];
+                ldsm_x4(mk, swz(ht, pa, 2 * kc + (m >> 1)));
 #pragma unroll
-              for (int j = 0; j < 4; ++j) a[j] = relu_masked(a[j], mk[j]);
+                for (int j = 0; j < 4; ++j) a[j] = relu_masked(a[j], mk[j]);
+              }
               mma_bf16(acc, a, bq + 2 * kc);
             }
           }
@@ -682,11 +681,13 @@ __global__ void __launch_bounds__(256, 2) k_conv_in_bwd(int B, int H, int W, con
           for (int mh = 0; mh < 2; ++mh) {
             // A = G'^T (co x pixel): matrices (co 0-7, px 0-7), (co 8-15, px 0-7), (co 0-7, px 8-15), (co 8-15, px 8-15)
             const int p = (warp + 1) * XW + 1 + (m >> 1) * 8 + (lane & 7);
-            unsigned mk[4];
             ldsm_x4_trans(a[mh], swz(gt, p, 2 * mh + (m & 1)));
-            ldsm_x4_trans(mk, swz(ht, p, 2 * mh + (m & 1)));
+            if (MASK) {
+              unsigned mk[4];
+              ldsm_x4_trans(mk, swz(ht, p, 2 * mh + (m & 1)));
 #pragma unroll
-            for (int j = 0; j < 4; ++j) a[mh][j] = relu_masked(a[mh][j], mk[j]);
+              for (int j = 0; j < 4; ++j) a[mh][j] = relu_masked(a[mh][j], mk[j]);
+            }
           }
 #pragma unroll
           for (int nt = 0; nt < NTW; ++nt) {
@@ -779,9 +780,11 @@ __global__ void __launch_bounds__(256) k_conv_out_fwd(int B, int H, int W, const
 }
 
 // Backward of the out layer in one pass (g = g_out split as hi + lo):
-//   g_h(p)[ci] = sum_tap g(p - tap) w[tap][ci]           (A[pixel][tap] gathered, B = w, N = 32)
+//   g_h(p)[ci] = sum_tap g(p - tap) w[tap][ci]           (A[pixel][tap] gathered, B = w, N = 32),
+//                times [h(p)[ci] > 0] with MASK (the gradient of the mid layer's pre-activation)
 //   dW[tap][ci] = sum_q h(q)[ci] g(q - tap), db = sum g   (A = h^T by ldmatrix.trans, B = g pairs,
 //                                                          n = part * 9 + tap), per-CTA partials [289].
+template <bool MASK>
 __global__ void __launch_bounds__(256, 2) k_conv_out_bwd(int B, int H, int W, const __grid_constant__ CUtensorMap map_h,
                                                          const float* __restrict__ gout, const tat_bf16* __restrict__ w,
                                                          tat_bf16* __restrict__ gh, float* __restrict__ partial) {
@@ -881,10 +884,14 @@ __global__ void __launch_bounds__(256, 2) k_conv_out_bwd(int B, int H, int W, co
               const int x = x0c + g + 8 * hf;
               if (x >= W) continue;
               tat_bf16* dst = gh + (((long long)b * H + y) * W + x) * C;
+              const int p = (warp + 1) * XW + g + 8 * hf + 1;  // this pixel in the staged h halo
 #pragma unroll
-              for (int nt = 0; nt < 4; ++nt)
-                *reinterpret_cast<unsigned*>(dst + nt * 8 + 2 * t) =
-                    (unsigned)tobf(acc[nt][2 * hf]) | ((unsigned)tobf(acc[nt][2 * hf + 1]) << 16);
+              for (int nt = 0; nt < 4; ++nt) {
+                unsigned v = (unsigned)tobf(acc[nt][2 * hf]) | ((unsigned)tobf(acc[nt][2 * hf + 1]) << 16);
+                if (MASK)
+                  v = relu_masked(v, *reinterpret_cast<const unsigned*>(swz(ht, p, nt) + 4 * t));
+                *reinterpret_cast<unsigned*>(dst + nt * 8 + 2 * t) = v;
+              }
             }
           }
         }
@@ -1044,17 +1051,19 @@ bool smem_attr(size_t bytes) {
 
 bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) != 0; }
 
-template <bool BWD>
-tat_status launch_mid(int batch, int H, int W, const tat_bf16* in, const tat_bf16* mask, const tat_bf16* w,
-                      const float* b, tat_bf16* out, cudaStream_t s, const char* what) {
-  if (misaligned(in) || misaligned(mask)) return TAT_ERR_INVALID_ARG;
-  CUtensorMap mi, mm;
-  if (!halo_map(&mi, in, batch, H, W) || !halo_map(&mm, BWD ? mask : in, batch, H, W)) {
+template <bool BWD, bool MASK, bool OMASK>
+tat_status launch_mid(int batch, int H, int W, const tat_bf16* in, const tat_bf16* mask, const tat_bf16* omask,
+                      const tat_bf16* w, const float* b, tat_bf16* out, cudaStream_t s, const char* what) {
+  if (misaligned(in) || misaligned(mask) || misaligned(omask)) return TAT_ERR_INVALID_ARG;
+  CUtensorMap mi, mm, mo;
+  if (!halo_map(&mi, in, batch, H, W) || !halo_map(&mm, MASK ? mask : in, batch, H, W) ||
+      !halo_map(&mo, OMASK ? omask : in, batch, H, W)) {
     fprintf(stderr, "%s: tensor map encoding failed\n", what);
     return TAT_ERR_CUDA;
   }
-  if (!smem_attr<k_conv_mid<BWD>>(mid_smem_bytes<BWD>())) return TAT_ERR_CUDA;
-  k_conv_mid<BWD><<<mid_ctas(batch, H, W), 256, mid_smem_bytes<BWD>(), s>>>(batch, H, W, mi, mm, w, b, out);
+  constexpr size_t smem = mid_smem_bytes<1 + MASK + OMASK>();
+  if (!smem_attr<k_conv_mid<BWD, MASK, OMASK>>(smem)) return TAT_ERR_CUDA;
+  k_conv_mid<BWD, MASK, OMASK><<<mid_ctas(batch, H, W), 256, smem, s>>>(batch, H, W, mi, mm, mo, w, b, out);
   return launched(what);
 }
 
@@ -1064,14 +1073,14 @@ int thin_ctas(int batch, int H, int W, int per_sm) {
   return (int)(tiles < per_sm * 152LL ? tiles : per_sm * 152LL);
 }
 
-template <int CIN, bool DATA, bool WGRAD>
+template <int CIN, bool MASK>
 tat_status launch_in_bwd(int batch, int H, int W, const CUtensorMap& mg, const CUtensorMap& mh, const float* x0,
                          const float* x1, const float* x2, const tat_bf16* w, float* gx0, float* gx1, float* gx2,
-                         int accumulate, float* scratch, int ctas, cudaStream_t s) {
-  constexpr size_t smem = in_bwd_smem_bytes<CIN>();
-  if (!smem_attr<k_conv_in_bwd<CIN, DATA, WGRAD>>(smem)) return TAT_ERR_CUDA;
-  k_conv_in_bwd<CIN, DATA, WGRAD><<<ctas, 256, smem, s>>>(batch, H, W, mg, mh, x0, x1, x2, w, gx0, gx1, gx2,
-                                                           accumulate, scratch);
+                         int accumulate, int parts, float* scratch, int ctas, cudaStream_t s) {
+  constexpr size_t smem = InBwdSmem<CIN, MASK>::BYTES;
+  if (!smem_attr<k_conv_in_bwd<CIN, MASK>>(smem)) return TAT_ERR_CUDA;
+  k_conv_in_bwd<CIN, MASK><<<ctas, 256, smem, s>>>(batch, H, W, mg, mh, x0, x1, x2, w, gx0, gx1, gx2, accumulate,
+                                                    parts, scratch);
   return launched("tat_conv_in_bwd");
 }
 
@@ -1085,19 +1094,15 @@ tat_status in_bwd(int batch, int H, int W, const float* x0, const float* x1, con
   const int nw = (9 * CIN + 1) * C;
   if (wgrad && scratch_floats < (size_t)ctas * nw) return TAT_ERR_INVALID_ARG;
   CUtensorMap mg, mh;
-  if (!halo_map(&mg, g_h, batch, H, W) || !halo_map(&mh, h, batch, H, W)) {
+  if (!halo_map(&mg, g_h, batch, H, W) || !halo_map(&mh, h ? h : g_h, batch, H, W)) {
     fprintf(stderr, "tat_conv_in_bwd: tensor map encoding failed\n");
     return TAT_ERR_CUDA;
   }
-  tat_status st;
-  if (data && wgrad)
-    st = launch_in_bwd<CIN, true, true>(batch, H, W, mg, mh, x0, x1, x2, w, gx0, gx1, gx2, accumulate, scratch, ctas, s);
-  else if (data)
-    st = launch_in_bwd<CIN, true, false>(batch, H, W, mg, mh, x0, x1, x2, w, gx0, gx1, gx2, accumulate, scratch, ctas,
-                                         s);
-  else
-    st = launch_in_bwd<CIN, false, true>(batch, H, W, mg, mh, x0, x1, x2, w, gx0, gx1, gx2, accumulate, scratch, ctas,
-                                         s);
+  const int parts = (data ? 1 : 0) | (wgrad ? 2 : 0);
+  const tat_status st =
+      h ? launch_in_bwd<CIN, true>(batch, H, W, mg, mh, x0, x1, x2, w, gx0, gx1, gx2, accumulate, parts, scratch, ctas, s)
+        : launch_in_bwd<CIN, false>(batch, H, W, mg, mh, x0, x1, x2, w, gx0, gx1, gx2, accumulate, parts, scratch, ctas,
+                                    s);
   if (st != TAT_OK || !wgrad) return st;
   k_reduce_partials<<<(nw + 31) / 32, 256, 0, s>>>(ctas, 9 * CIN * C, C, scratch, gw, gb);
   return launched("tat_conv_in_bwd");
@@ -1132,7 +1137,7 @@ tat_status tat_conv_in_bwd(int batch, int H, int W, int cin, const float* x0, co
                            const tat_bf16* g_h, const tat_bf16* h, const tat_bf16* w, float* gx0, float* gx1,
                            float* gx2, int accumulate, float* scratch, size_t scratch_floats, float* gw, float* gb,
                            tat_stream_t stream) {
-  if (bad_sizes(batch, H, W) || (cin != 2 && cin != 3) || !g_h || !h || misaligned(g_h) || misaligned(h))
+  if (bad_sizes(batch, H, W) || (cin != 2 && cin != 3) || !g_h || misaligned(g_h) || misaligned(h))
     return TAT_ERR_INVALID_ARG;
   if ((gx0 || gx1 || gx2) && !w) return TAT_ERR_INVALID_ARG;
   if (gw && (!x0 || !x1 || (cin == 3 && !x2) || !scratch || !gb)) return TAT_ERR_INVALID_ARG;
@@ -1161,15 +1166,19 @@ tat_status tat_conv_in_bwd_weights(int batch, int H, int W, int cin, const float
 tat_status tat_conv_mid_fwd(int batch, int H, int W, const tat_bf16* h_in, const tat_bf16* w, const float* b,
                             tat_bf16* h_out, tat_stream_t stream) {
   if (bad_sizes(batch, H, W) || !h_in || !w || !b || !h_out) return TAT_ERR_INVALID_ARG;
-  return launch_mid<false>(batch, H, W, h_in, nullptr, w, b, h_out, static_cast<cudaStream_t>(stream),
-                           "tat_conv_mid_fwd");
+  return launch_mid<false, false, false>(batch, H, W, h_in, nullptr, nullptr, w, b, h_out,
+                                         static_cast<cudaStream_t>(stream), "tat_conv_mid_fwd");
 }
 
 tat_status tat_conv_mid_bwd_data(int batch, int H, int W, const tat_bf16* g_out, const tat_bf16* h_out,
-                                 const tat_bf16* w, tat_bf16* g_in, tat_stream_t stream) {
-  if (bad_sizes(batch, H, W) || !g_out || !h_out || !w || !g_in) return TAT_ERR_INVALID_ARG;
-  return launch_mid<true>(batch, H, W, g_out, h_out, w, nullptr, g_in, static_cast<cudaStream_t>(stream),
-                          "tat_conv_mid_bwd_data");
+                                 const tat_bf16* w, const tat_bf16* h_in, tat_bf16* g_in, tat_stream_t stream) {
+  if (bad_sizes(batch, H, W) || !g_out || !w || !g_in) return TAT_ERR_INVALID_ARG;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const char* what = "tat_conv_mid_bwd_data";
+  if (h_out && h_in) return launch_mid<true, true, true>(batch, H, W, g_out, h_out, h_in, w, nullptr, g_in, s, what);
+  if (h_out) return launch_mid<true, true, false>(batch, H, W, g_out, h_out, nullptr, w, nullptr, g_in, s, what);
+  if (h_in) return launch_mid<true, false, true>(batch, H, W, g_out, nullptr, h_in, w, nullptr, g_in, s, what);
+  return launch_mid<true, false, false>(batch, H, W, g_out, nullptr, nullptr, w, nullptr, g_in, s, what);
 }
 
 tat_status tat_lpd_check(void) {
@@ -1187,12 +1196,26 @@ tat_status tat_lpd_check(void) {
 tat_status tat_conv_mid_bwd_weights(int batch, int H, int W, const tat_bf16* h_in, const tat_bf16* g_out,
                                     const tat_bf16* h_out, float* scratch, size_t scratch_floats, float* gw,
                                     float* gb, tat_stream_t stream) {
-  if (bad_sizes(batch, H, W) || !h_in || !g_out || !h_out || !scratch || !gw || !gb) return TAT_ERR_INVALID_ARG;
+  if (bad_sizes(batch, H, W) || !h_in || !g_out || !scratch || !gw || !gb || misaligned(h_in) ||
+      misaligned(g_out) || misaligned(h_out))
+    return TAT_ERR_INVALID_ARG;
   const int ctas = wgrad_ctas(batch, H, W);
   const int nw = 9 * C * C + C;
   if (scratch_floats < (size_t)ctas * nw) return TAT_ERR_INVALID_ARG;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  k_conv_mid_wgrad<<<ctas, 288, 0, s>>>(batch, H, W, h_in, g_out, h_out, scratch);
+  CUtensorMap mi, mg, mh;
+  if (!halo_map(&mi, h_in, batch, H, W) || !halo_map(&mg, g_out, batch, H, W) ||
+      !halo_map(&mh, h_out ? h_out : g_out, batch, H, W)) {
+    fprintf(stderr, "tat_conv_mid_bwd_weights: tensor map encoding failed\n");
+    return TAT_ERR_CUDA;
+  }
+  if (h_out) {
+    if (!smem_attr<k_conv_mid_wgrad<true>>(wgrad_smem_bytes())) return TAT_ERR_CUDA;
+    k_conv_mid_wgrad<true><<<ctas, 288, wgrad_smem_bytes(), s>>>(batch, H, W, mi, mg, mh, scratch);
+  } else {
+    if (!smem_attr<k_conv_mid_wgrad<false>>(wgrad_smem_bytes())) return TAT_ERR_CUDA;
+    k_conv_mid_wgrad<false><<<ctas, 288, wgrad_smem_bytes(), s>>>(batch, H, W, mi, mg, mh, scratch);
+  }
   tat_status st = launched("tat_conv_mid_bwd_weights");
   if (st != TAT_OK) return st;
   k_reduce_partials<<<(nw + 31) / 32, 256, 0, s>>>(ctas, 9 * C * C, C, scratch, gw, gb);
@@ -1214,7 +1237,7 @@ tat_status tat_conv_out_fwd(int batch, int H, int W, const tat_bf16* h, const ta
 }
 
 tat_status tat_conv_out_bwd(int batch, int H, int W, const float* g_out, const tat_bf16* h, const tat_bf16* w,
-                            tat_bf16* g_h, float* scratch, size_t scratch_floats, float* gw, float* gb,
+                            int mask_relu, tat_bf16* g_h, float* scratch, size_t scratch_floats, float* gw, float* gb,
                             tat_stream_t stream) {
   if (bad_sizes(batch, H, W) || !g_out || !h || !w || !g_h || !scratch || !gw || !gb || misaligned(h))
     return TAT_ERR_INVALID_ARG;
@@ -1225,9 +1248,14 @@ tat_status tat_conv_out_bwd(int batch, int H, int W, const float* g_out, const t
     fprintf(stderr, "tat_conv_out_bwd: tensor map encoding failed\n");
     return TAT_ERR_CUDA;
   }
-  if (!smem_attr<k_conv_out_bwd>(out_bwd_smem_bytes())) return TAT_ERR_CUDA;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  k_conv_out_bwd<<<ctas, 256, out_bwd_smem_bytes(), s>>>(batch, H, W, mh, g_out, w, g_h, scratch);
+  if (mask_relu) {
+    if (!smem_attr<k_conv_out_bwd<true>>(out_bwd_smem_bytes())) return TAT_ERR_CUDA;
+    k_conv_out_bwd<true><<<ctas, 256, out_bwd_smem_bytes(), s>>>(batch, H, W, mh, g_out, w, g_h, scratch);
+  } else {
+    if (!smem_attr<k_conv_out_bwd<false>>(out_bwd_smem_bytes())) return TAT_ERR_CUDA;
+    k_conv_out_bwd<false><<<ctas, 256, out_bwd_smem_bytes(), s>>>(batch, H, W, mh, g_out, w, g_h, scratch);
+  }
   tat_status st = launched("tat_conv_out_bwd");
   if (st != TAT_OK) return st;
   k_reduce_partials<<<(9 * C + 1 + 31) / 32, 256, 0, s>>>(ctas, 9 * C, 1, scratch, gw, gb);

@@ -166,13 +166,15 @@ class LPD:
     def _net_backward(self, net, H, W, cin, g_out, h1, h2, g_h2, g_h1, x0, x1, x2, gx0, gx1, acc_mask):
         s = self._s()
         Bn, sc, nsc = self.B, self.scratch.data_ptr(), self.scratch_floats
-        B.tat_conv_out_bwd(Bn, H, W, g_out.data_ptr(), h2.data_ptr(), self._w(net, "w_out"), g_h2.data_ptr(), sc, nsc,
-                           self._g(net, "w_out"), self._g(net, "b_out"), s)
-        B.tat_conv_mid_bwd_data(Bn, H, W, g_h2.data_ptr(), h2.data_ptr(), self._w(net, "w_mid"), g_h1.data_ptr(), s)
-        B.tat_conv_mid_bwd_weights(Bn, H, W, h1.data_ptr(), g_h2.data_ptr(), h2.data_ptr(), sc, nsc,
-                                   self._g(net, "w_mid"), self._g(net, "b_mid"), s)
+        # each gradient leaves its kernel already masked by the ReLU of the layer below it
+        # (g_h2 by h2 > 0, g_h1 by h1 > 0), so the next kernel reads no mask
+        B.tat_conv_out_bwd(Bn, H, W, g_out.data_ptr(), h2.data_ptr(), self._w(net, "w_out"), 1, g_h2.data_ptr(), sc,
+                           nsc, self._g(net, "w_out"), self._g(net, "b_out"), s)
+        B.tat_conv_mid_bwd_weights(Bn, H, W, h1.data_ptr(), g_h2.data_ptr(), 0, sc, nsc, self._g(net, "w_mid"),
+                                   self._g(net, "b_mid"), s)
+        B.tat_conv_mid_bwd_data(Bn, H, W, g_h2.data_ptr(), 0, self._w(net, "w_mid"), h1.data_ptr(), g_h1.data_ptr(), s)
         B.tat_conv_in_bwd(Bn, H, W, cin, x0.data_ptr(), x1.data_ptr(), x2.data_ptr() if x2 is not None else 0,
-                          g_h1.data_ptr(), h1.data_ptr(), self._w(net, "w_in"), gx0.data_ptr(), gx1.data_ptr(), 0,
+                          g_h1.data_ptr(), 0, self._w(net, "w_in"), gx0.data_ptr(), gx1.data_ptr(), 0,
                           acc_mask, sc, nsc, self._g(net, "w_in"), self._g(net, "b_in"), s)
 
     def _backward(self):

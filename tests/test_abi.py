@@ -100,6 +100,6 @@ def test_lpd_layers_reject_bad_arguments_before_any_device_work(pkg):
     with pytest.raises(bad):
         pkg.tat_conv_in_bwd(1, 8, 16, 3, fake, fake, fake, fake, fake, 0, fake, 0, 0, 0, 0, 0, 0, 0)
     with pytest.raises(bad):
-        pkg.tat_conv_out_bwd(1, 8, 16, fake, fake, fake, fake, fake, 1, fake, fake)
+        pkg.tat_conv_out_bwd(1, 8, 16, fake, fake, fake, 0, fake, fake, 1, fake, fake)
     with pytest.raises(bad):
         pkg.tat_conv_in_fwd(1, 8, 16, 4, fake, fake, fake, fake, fake, fake)

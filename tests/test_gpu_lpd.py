@@ -110,6 +110,16 @@ def test_conv_in_forward_backward(pkg, torch, cin):
     assert rel(np.stack([t.cpu().numpy() for t in gx2_], 1), gxr) <= 1e-5
     assert rel(gw.cpu().numpy(), 2 * gwr) <= 1e-4
     assert rel(gb.cpu().numpy(), 2 * Bt.grad.numpy()) <= 1e-4
+    # pre-masked gradient (h = NULL): G * [h > 0] formed on the host
+    Gm = dev_bf16(torch, (r16(torch, G) * (host_bf16(torch, h) > 0).to(torch.float64)).numpy())
+    gx3 = [torch.full((B_, H_, W_), 7.0, device="cuda") for _ in range(cin)]
+    pkg.tat_conv_in_bwd(B_, H_, W_, cin, xd[0].data_ptr(), xd[1].data_ptr(), xd[2].data_ptr() if cin == 3 else 0,
+                        Gm.data_ptr(), 0, wd.data_ptr(), gx3[0].data_ptr(), gx3[1].data_ptr(),
+                        gx3[2].data_ptr() if cin == 3 else 0, 0b01, scratch.data_ptr(), scratch.numel(),
+                        gw.data_ptr(), gb.data_ptr(), s)
+    assert rel(np.stack([t.cpu().numpy() for t in gx3], 1), gxr) <= 1e-5
+    assert rel(gw.cpu().numpy(), 3 * gwr) <= 1e-4
+    assert rel(gb.cpu().numpy(), 3 * Bt.grad.numpy()) <= 1e-4
     pkg.tat_lpd_check()
 
 
@@ -130,7 +140,7 @@ def test_conv_mid_forward_backward(pkg, torch):
     G = 0.5 * gaussian(43, B_ * H_ * W_ * 32).reshape(B_, H_, W_, 32)
     Gd = dev_bf16(torch, G)
     gin = torch.empty_like(hd)
-    pkg.tat_conv_mid_bwd_data(B_, H_, W_, Gd.data_ptr(), out.data_ptr(), wd.data_ptr(), gin.data_ptr(), s)
+    pkg.tat_conv_mid_bwd_data(B_, H_, W_, Gd.data_ptr(), out.data_ptr(), wd.data_ptr(), 0, gin.data_ptr(), s)
     scratch = torch.empty(pkg.tat_lpd_scratch_floats(B_, H_, W_), device="cuda")
     gw = torch.zeros(9 * 32 * 32, device="cuda")
     gb = torch.zeros(32, device="cuda")
@@ -138,8 +148,26 @@ def test_conv_mid_forward_backward(pkg, torch):
                                  scratch.numel(), gw.data_ptr(), gb.data_ptr(), s)
     (torch.relu(pre) * r16(torch, G).permute(0, 3, 1, 2)).sum().backward()
     assert rel(host_bf16(torch, gin).permute(0, 3, 1, 2), r16(torch, X.grad)) <= 1e-3
-    assert rel(gw.cpu().numpy(), Wt.grad.permute(2, 3, 0, 1).reshape(-1).numpy()) <= 1e-4   # [tap][co][ci]
+    gwr = Wt.grad.permute(2, 3, 0, 1).reshape(-1).numpy()                                   # [tap][co][ci]
+    assert rel(gw.cpu().numpy(), gwr) <= 1e-4
     assert rel(gb.cpu().numpy(), Bt.grad.numpy()) <= 1e-4
+    # pre-masked gradient (h_out = NULL): G * [out > 0] formed on the host gives the same results
+    outm = (host_bf16(torch, out) > 0).to(torch.float64)
+    Gm = dev_bf16(torch, (r16(torch, G) * outm).numpy())
+    gin2 = torch.empty_like(hd)
+    pkg.tat_conv_mid_bwd_data(B_, H_, W_, Gm.data_ptr(), 0, wd.data_ptr(), 0, gin2.data_ptr(), s)
+    assert torch.equal(host_bf16(torch, gin2), host_bf16(torch, gin))        # same operands up to the sign of 0
+    # h_in: the result masked by [h_in > 0] (both with the mask read in-kernel and pre-masked)
+    inm = (host_bf16(torch, hd) > 0).to(torch.float64)
+    for gsrc, hsrc in ((Gd, out), (Gm, None)):
+        gin3 = torch.empty_like(hd)
+        pkg.tat_conv_mid_bwd_data(B_, H_, W_, gsrc.data_ptr(), hsrc.data_ptr() if hsrc is not None else 0,
+                                  wd.data_ptr(), hd.data_ptr(), gin3.data_ptr(), s)
+        assert torch.equal(host_bf16(torch, gin3), host_bf16(torch, gin) * inm)
+    pkg.tat_conv_mid_bwd_weights(B_, H_, W_, hd.data_ptr(), Gm.data_ptr(), 0, scratch.data_ptr(), scratch.numel(),
+                                 gw.data_ptr(), gb.data_ptr(), s)
+    assert rel(gw.cpu().numpy(), 2 * gwr) <= 1e-4
+    assert rel(gb.cpu().numpy(), 2 * Bt.grad.numpy()) <= 1e-4
     pkg.tat_lpd_check()     # no TMA tile wait gave up
 
 
@@ -164,12 +192,19 @@ def test_conv_out_forward_backward(pkg, torch):
     scratch = torch.empty(pkg.tat_lpd_scratch_floats(B_, H_, W_), device="cuda")
     gw = torch.zeros(9 * 32, device="cuda")
     gb = torch.zeros(1, device="cuda")
-    pkg.tat_conv_out_bwd(B_, H_, W_, Gd.data_ptr(), hd.data_ptr(), wd.data_ptr(), gh.data_ptr(), scratch.data_ptr(),
-                         scratch.numel(), gw.data_ptr(), gb.data_ptr(), s)
+    pkg.tat_conv_out_bwd(B_, H_, W_, Gd.data_ptr(), hd.data_ptr(), wd.data_ptr(), 0, gh.data_ptr(),
+                         scratch.data_ptr(), scratch.numel(), gw.data_ptr(), gb.data_ptr(), s)
     (ref * torch.tensor(np.asarray(G, np.float32), dtype=torch.float64)).sum().backward()
     assert rel(host_bf16(torch, gh).permute(0, 3, 1, 2), r16(torch, X.grad)) <= 1e-3
     assert rel(gw.cpu().numpy(), Wt.grad[0].permute(1, 2, 0).reshape(-1).numpy()) <= 1e-4
     assert rel(gb.cpu().numpy(), Bt.grad.numpy()) <= 1e-4
+    # mask_relu: the same gradient times [h > 0] (h holds exact zeros where its ReLU clipped)
+    ghm = torch.empty_like(hd)
+    pkg.tat_conv_out_bwd(B_, H_, W_, Gd.data_ptr(), hd.data_ptr(), wd.data_ptr(), 1, ghm.data_ptr(),
+                         scratch.data_ptr(), scratch.numel(), gw.data_ptr(), gb.data_ptr(), s)
+    mask = (X > 0).to(torch.float64)
+    assert rel(host_bf16(torch, ghm).permute(0, 3, 1, 2), r16(torch, X.grad) * mask) <= 1e-3
+    assert rel(gw.cpu().numpy(), 2 * Wt.grad[0].permute(1, 2, 0).reshape(-1).numpy()) <= 1e-4
     pkg.tat_lpd_check()
 
 
