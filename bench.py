@@ -727,11 +727,11 @@ def inverse_config(batch):
 # ------------------------------------------------------------------ service workload
 
 SVC_REQ, SVC_SIZES = 64, (128, 256, 512, 1024)
-SVC_METRIC = "requests/s, 64 mixed-size A requests (n in {128,256,512,1024}, n_det=n_t=2n), with p50/p99 latency"
+SVC_METRIC = "requests/s, 64 mixed-size A+A* requests (n in {128,256,512,1024}, n_det=n_t=2n), with p50/p99 latency"
 
 
 def service_requests(seed=0):
-    """Seeded request mix: n ~ U{128, 256, 512, 1024}, n_det = n_t = 2n, one A per request."""
+    """Seeded request mix: n ~ U{128, 256, 512, 1024}, n_det = n_t = 2n, one A+A* pair per request."""
     from tat_inputs import uniform
     u = uniform(seed + 4242, SVC_REQ)
     return [SVC_SIZES[min(int(x * len(SVC_SIZES)), len(SVC_SIZES) - 1)] for x in u]
@@ -739,12 +739,13 @@ def service_requests(seed=0):
 
 def service_config(sizes):
     counts = {n: sizes.count(n) for n in SVC_SIZES}
-    return {"workload": f"{SVC_REQ} requests of A, n ~ U{{128,256,512,1024}} (seeded), n_det=n_t=2n, T=2",
+    return {"workload": f"{SVC_REQ} requests of A*A (one A+A* pair each), n ~ U{{128,256,512,1024}} (seeded), "
+                        "n_det=n_t=2n, T=2",
             "requests_per_size": counts, "arrival": "all requests queued at t=0, one flush",
             "max_batch": 32, "graphs": True, "l2": "inputs and working set exceed L2, no flush"}
 
 
-SVC_ORACLE_SAMPLE = "one n=256 oracle A (n_det=n_t=512), scaled by n^2 log n to the 64-request mix"
+SVC_ORACLE_SAMPLE = "one n=256 oracle A+A* pair (n_det=n_t=512), scaled by n^2 log n to the 64-request mix"
 
 
 def service_oracle_seconds(sizes):
@@ -755,7 +756,7 @@ def service_oracle_seconds(sizes):
     P = O.OraclePlan(n, 2 * n, 2 * n, T=T_WIN, support_radius=RSUP)
     f = ellipse_phantom(n, 0)
     t0 = time.perf_counter()
-    O.forward(P, f)
+    O.adjoint(P, O.forward(P, f))
     t1 = time.perf_counter() - t0
     # scale by the O(n^2 log n) cost of each request's size
     return t1 * sum((m / n) ** 2 * math.log2(m) / math.log2(n) for m in sizes)
@@ -763,7 +764,7 @@ def service_oracle_seconds(sizes):
 
 def service_roofline(pkg, sizes, stream, dev):
     """FP32-ALU roofline of the dominant stage of the service's largest group (n = 1024 requests,
-    batched up to the service's max batch), timed with events between the stages of A."""
+    batched up to the service's max batch), timed with events between the stages of A and A*."""
     import torch
     n = max(sizes)
     B = min(sizes.count(n), 32)
@@ -771,10 +772,11 @@ def service_roofline(pkg, sizes, stream, dev):
     x = torch.zeros((B, n, n), device=dev)
     y = torch.empty((B, 2 * n, 2 * n), device=dev)
     ws = op.workspace(B)
-    stage_times(pkg, op, B, x, y, x, ws, stream, 2, adjoint=False)
-    ms = stage_times(pkg, op, B, x, y, x, ws, stream, 5, adjoint=False)
+    x2 = torch.empty_like(x)
+    stage_times(pkg, op, B, x, y, x2, ws, stream, 2)
+    ms = stage_times(pkg, op, B, x, y, x2, ws, stream, 5)
     r = alu_roofline(ms, stage_flops(op.info, B, n, 2 * n, 2 * n), f"service_n{n}_b{B}")
-    r["group"] = f"{B} requests of n={n} (n_det=n_t={2 * n}) in one batched A"
+    r["group"] = f"{B} requests of n={n} (n_det=n_t={2 * n}) in one batched A and A*"
     return r
 
 
@@ -807,12 +809,12 @@ def run_service(args, rank, world, local):
     from tat_inputs import ellipse_phantom
 
     xs = [torch.tensor(ellipse_phantom(n, 100 * rank + i).astype(np.float32), device=dev) for i, n in enumerate(sizes)]
-    outs = [torch.empty((2 * n, 2 * n), device=dev) for n in sizes]
+    outs = [torch.empty((n, n), device=dev) for n in sizes]
     descs = {n: pkg.TatService.desc(n, 2 * n, 2 * n, T=T_WIN, support_radius=RSUP) for n in SVC_SIZES}
     svc = pkg.TatService(memory_budget=8 << 30, max_batch=32, use_graphs=True)
 
     def round_():
-        ids = [svc.submit(descs[n], "forward", x, o) for n, x, o in zip(sizes, xs, outs)]
+        ids = [svc.submit(descs[n], "pair", x, o) for n, x, o in zip(sizes, xs, outs)]
         svc.flush()
         svc.synchronize()
         return ids
@@ -840,19 +842,41 @@ def run_service(args, rank, world, local):
     # one request at a time through the same runtime (no batching across requests)
     solo = pkg.TatService(memory_budget=2 << 30, max_batch=1, use_graphs=True)
     for n, x, o in zip(sizes, xs, outs):
-        solo.submit(descs[n], "forward", x, o)
+        solo.submit(descs[n], "pair", x, o)
     solo.flush()
     solo.synchronize()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     solo_lat = []
     for n, x, o in zip(sizes, xs, outs):
-        rid = solo.submit(descs[n], "forward", x, o)
+        rid = solo.submit(descs[n], "pair", x, o)
         solo.flush()
         solo.synchronize()
         solo_lat.append(solo.latency(rid)[0])
     solo_wall = time.perf_counter() - t1
     solo.close()
+
+    # the plain per-request path: direct tat_forward + tat_adjoint on each image (plans and
+    # buffers made beforehand), synchronised per request; no runtime, no batching, no graphs
+    ops = {n: pkg.TatOperator(n, 2 * n, 2 * n, T=T_WIN, support_radius=RSUP, device=dev) for n in SVC_SIZES}
+    gbufs = {n: torch.empty((2 * n, 2 * n), device=dev) for n in SVC_SIZES}
+    wss = {n: ops[n].workspace(1) for n in SVC_SIZES}
+    sptr = torch.cuda.current_stream(dev).cuda_stream
+
+    def plain(n, x, o):
+        pkg.tat_forward(ops[n].plan, x.data_ptr(), gbufs[n].data_ptr(), wss[n].data_ptr(), sptr)
+        pkg.tat_adjoint(ops[n].plan, gbufs[n].data_ptr(), o.data_ptr(), wss[n].data_ptr(), sptr)
+        torch.cuda.synchronize()
+
+    for n, x, o in zip(sizes, xs, outs):
+        plain(n, x, o)
+    plain_lat = []
+    t3 = time.perf_counter()
+    for n, x, o in zip(sizes, xs, outs):
+        t4 = time.perf_counter()
+        plain(n, x, o)
+        plain_lat.append(1e3 * (time.perf_counter() - t4))
+    plain_wall = time.perf_counter() - t3
 
     # end to end: host (pinned) inputs copied in and results copied out inside the timed region
     pins = [x.cpu().pin_memory() for x in xs]
@@ -886,13 +910,19 @@ def run_service(args, rank, world, local):
                                "timing": "host clock, submission to completion callback"},
                 "one_at_a_time": {"requests_per_s": SVC_REQ / solo_wall,
                                   "p50_ms": float(np.percentile(solo_lat, 50)),
-                                  "p99_ms": float(np.percentile(solo_lat, 99))},
+                                  "p99_ms": float(np.percentile(solo_lat, 99)),
+                                  "what": "the same runtime with max_batch 1 (graphs on), one flush per request"},
+                "per_request_plain_path": {"requests_per_s": SVC_REQ / plain_wall,
+                                           "p50_ms": float(np.percentile(plain_lat, 50)),
+                                           "p99_ms": float(np.percentile(plain_lat, 99)),
+                                           "what": "tat_forward + tat_adjoint per request, synchronised",
+                                           "service_speedup": plain_wall / wall},
                 "service_stats": st,
                 "e2e": {"value": SVC_REQ * world / e2e_wall, "unit": "requests/s",
                         "h2d_bytes_per_step": int(sum(4 * n * n for n in sizes)),
-                        "d2h_bytes_per_step": int(sum(4 * 4 * n * n for n in sizes))},
+                        "d2h_bytes_per_step": int(sum(4 * n * n for n in sizes))},
                 "roofline": roofline, "cpu_baseline": cpu,
-                "gpu_launches": 5 * st["launches"] // max(1, args.steps + max(args.warmup, 3)) * args.steps,
+                "gpu_launches": 10 * st["launches"] // max(1, args.steps + max(args.warmup, 3)) * args.steps,
                 "clocks": clk, "kernel_source_hash": kernel_source_hash()}
         print(json.dumps(line), flush=True)
     if world > 1:

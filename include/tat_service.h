@@ -41,7 +41,9 @@ extern "C" {
 
 typedef struct tat_service_s* tat_service_t;
 
-typedef enum { TAT_OP_FORWARD = 0, TAT_OP_ADJOINT = 1, TAT_OP_INVERSE = 2 } tat_op;
+/* TAT_OP_PAIR: out = A*(A in), image to image (the gradient of 1/2 |A f - g|^2 at g = 0,
+ * the unit of work of the iterative solvers); A in stays in the slot. */
+typedef enum { TAT_OP_FORWARD = 0, TAT_OP_ADJOINT = 1, TAT_OP_INVERSE = 2, TAT_OP_PAIR = 3 } tat_op;
 
 typedef struct {
   size_t memory_budget; /* bytes of device memory for all staging slots (one arena) */
@@ -72,7 +74,7 @@ tat_status tat_service_destroy(tat_service_t svc);
 
 /* Queues op(in) -> out for the problem `desc` (validated on the host; the
  * plan is built at the first flush that needs it).  in/out sizes: n*n floats
- * for images, n_det*n_t floats for data.  *id receives the request's index
+ * for images, n_det*n_t floats for data (TAT_OP_PAIR: both images).  *id receives the request's index
  * (0, 1, 2, ... in submission order). */
 tat_status tat_service_submit(tat_service_t svc, const tat_plan_desc* desc, tat_op op, const float* in,
                               float* out, long long* id);

@@ -59,7 +59,7 @@ class tat_service_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-TAT_OP_FORWARD, TAT_OP_ADJOINT, TAT_OP_INVERSE = 0, 1, 2
+TAT_OP_FORWARD, TAT_OP_ADJOINT, TAT_OP_INVERSE, TAT_OP_PAIR = 0, 1, 2, 3
 
 _lib = None
 _P = ctypes.c_void_p
@@ -552,7 +552,7 @@ class TatService:
     contiguous float32 CUDA tensors that must stay alive until ``synchronize``.
     """
 
-    OPS = {"forward": TAT_OP_FORWARD, "adjoint": TAT_OP_ADJOINT, "inverse": TAT_OP_INVERSE}
+    OPS = {"forward": TAT_OP_FORWARD, "adjoint": TAT_OP_ADJOINT, "inverse": TAT_OP_INVERSE, "pair": TAT_OP_PAIR}
 
     def __init__(self, memory_budget=None, max_batch=None, use_graphs=True, autotune=False):
         cfg = tat_service_config_default()

@@ -117,9 +117,44 @@ __device__ __forceinline__ void dft16(float2* v) {
   t = v[11]; v[11] = v[14]; v[14] = t;
 }
 
+// cos(2 pi j / 32), j = 0..31 (sin(2 pi j / 32) = entry (j + 24) mod 32).
+__device__ constexpr float kCos32[32] = {
+    1.f, 0.98078528040323044913f, 0.92387953251128675613f, 0.83146961230254523708f,
+    0.70710678118654752440f, 0.55557023301960222474f, 0.38268343236508977173f, 0.19509032201612826785f,
+    0.f, -0.19509032201612826785f, -0.38268343236508977173f, -0.55557023301960222474f,
+    -0.70710678118654752440f, -0.83146961230254523708f, -0.92387953251128675613f, -0.98078528040323044913f,
+    -1.f, -0.98078528040323044913f, -0.92387953251128675613f, -0.83146961230254523708f,
+    -0.70710678118654752440f, -0.55557023301960222474f, -0.38268343236508977173f, -0.19509032201612826785f,
+    0.f, 0.19509032201612826785f, 0.38268343236508977173f, 0.55557023301960222474f,
+    0.70710678118654752440f, 0.83146961230254523708f, 0.92387953251128675613f, 0.98078528040323044913f};
+
+// 32-point DFT: two 16-point DFTs of the even and odd samples and one radix-2 step
+// X[k] = E[k] + w^k O[k], X[k + 16] = E[k] - w^k O[k], w = e^{-+2 pi i / 32}.
+template <bool INV>
+__device__ __forceinline__ void dft32(float2* v) {
+  float2 e[16], o[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    e[i] = v[2 * i];
+    o[i] = v[2 * i + 1];
+  }
+  dft16<INV>(e);
+  dft16<INV>(o);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float c = kCos32[k], sn = kCos32[(k + 24) & 31];
+    const float2 w = make_float2(c, INV ? sn : -sn);
+    const float2 t = cmul(o[k], w);
+    v[k] = cadd(e[k], t);
+    v[k + 16] = csub(e[k], t);
+  }
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void bfly(float2* v) {
-  if constexpr (R == 16) {
+  if constexpr (R == 32) {
+    dft32<INV>(v);
+  } else if constexpr (R == 16) {
     dft16<INV>(v);
   } else if constexpr (R == 8) {
     dft8<INV>(v);
@@ -375,7 +410,7 @@ namespace tat {
 // writes directly.  The inverse runs the conjugate transposes in reverse.
 template <int L>
 struct FourStep {
-  static constexpr bool on = L == 512 || L == 1024 || L == 2048 || L == 4096;
+  static constexpr bool on = L == 512 || L == 1024 || L == 2048 || L == 4096 || L == 8192;
   static constexpr int RA = on ? L / 256 : 1;
 };
 // Steps A and B are looped when a group has fewer threads than 256 (step A)
@@ -392,7 +427,7 @@ __device__ __forceinline__ int xpad(int i) {
   else return i + (i >> 4);
 }
 __host__ __device__ __forceinline__ int xpad_len(int L) {
-  const bool four = L == 512 || L == 1024 || L == 2048 || L == 4096;
+  const bool four = L == 512 || L == 1024 || L == 2048 || L == 4096 || L == 8192;
   return L + (L >> 4) + (four ? (L >> 8) : 0) + 1;
 }
 
@@ -428,16 +463,28 @@ __device__ __forceinline__ void stepA_tw(const float2* smtw, int n2, float2& w1,
   w8 = cmul(smtw[48 + a], smtw[112 + b]);
 }
 
-// e^{-+2 pi i k / R} (R in {2, 4, 8, 16}; INV takes the + sign) from the 16th roots of unity.
+// e^{-+2 pi i k / R} (R in {2, 4, 8, 16, 32}; INV takes the + sign) from the 32nd roots of unity.
 template <int R, bool INV>
 __device__ __forceinline__ float2 unit_root(int k) {
-  constexpr float c16[16] = {1.f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508978f,
-                             0.f, -0.38268343236508978f, -0.70710678118654752f, -0.92387953251128674f,
-                             -1.f, -0.92387953251128674f, -0.70710678118654752f, -0.38268343236508978f,
-                             0.f, 0.38268343236508978f, 0.70710678118654752f, 0.92387953251128674f};
-  const int j = (k * (16 / R)) & 15;
-  const float s = c16[(j + 12) & 15];  // sin(2 pi j / 16) = cos(2 pi (j - 4) / 16)
-  return make_float2(c16[j], INV ? s : -s);
+  const int j = (k * (32 / R)) & 31;
+  const float s = kCos32[(j + 24) & 31];  // sin(2 pi j / 32) = cos(2 pi (j - 8) / 32)
+  return make_float2(kCos32[j], INV ? s : -s);
+}
+
+// Step A twiddles v[k1] *= w^(k1 n2) (INV: conjugate) from w^(n2 p), p = 1, 2, 4, 8; for
+// RA = 32 the power 16 is the square of the power 8.
+template <int RA, bool INV>
+__device__ __forceinline__ void stepA_apply(float2* v, float2 w1, float2 w2, float2 w4, float2 w8) {
+  if constexpr (RA <= 16) {
+    apply_twiddles_given<RA, INV>(v, w1, w2, w4, w8);
+  } else {
+    static_assert(RA == 32, "four-step lengths are RA * 256 with RA <= 32");
+    apply_twiddles_given<16, INV>(v, w1, w2, w4, w8);
+    const float2 w16 = cmul(w8, w8);
+#pragma unroll
+    for (int r = 16; r < 32; ++r) v[r] = INV ? cmulc(v[r], w16) : cmul(v[r], w16);
+    apply_twiddles_given<16, INV>(v + 16, w1, w2, w4, w8);
+  }
 }
 
 // Forward: x[0, n_in) in natural order -> X[q] * post[q] at colpos(q).
@@ -472,7 +519,7 @@ __device__ __forceinline__ void col_fft_fwd(float2* buf, const FftDev& f, const 
       }
       float2 w1, w2, w4, w8;
       stepA_tw(smtw, n2, w1, w2, w4, w8);
-      apply_twiddles_given<RA, false>(v, w1, w2, w4, w8);
+      stepA_apply<RA, false>(v, w1, w2, w4, w8);
 #pragma unroll
       for (int k1 = 0; k1 < RA; ++k1) buf[xpad<L>(256 * k1 + n2)] = v[k1];
     }
@@ -538,7 +585,7 @@ __device__ __forceinline__ void col_fft_inv(float2* buf, const FftDev& f, const 
       for (int k1 = 0; k1 < RA; ++k1) v[k1] = buf[xpad<L>(256 * k1 + n2)];
       float2 w1, w2, w4, w8;
       stepA_tw(smtw, n2, w1, w2, w4, w8);
-      apply_twiddles_given<RA, true>(v, w1, w2, w4, w8);
+      stepA_apply<RA, true>(v, w1, w2, w4, w8);
       if (n_out <= 512) {
         float2 o0 = v[0], o1 = v[0];
 #pragma unroll

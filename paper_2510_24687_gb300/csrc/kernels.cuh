@@ -44,8 +44,12 @@ __device__ __forceinline__ int wrapN(int q, int N) { return q < 0 ? q + N : q; }
 
 // ------------------------------------------------------------------ forward
 
+// Row kernels: up to 1024 threads (4 row pairs); at L = 8192 one row pair of 512
+// threads, whose 32-point step A needs the registers of a 512-thread bound.
+#define TAT_ROWS_BOUNDS __launch_bounds__(L == 8192 ? 512 : 1024)
+
 template <int L>
-__global__ void __launch_bounds__(1024) k_rows_fwd(DevPlan P, const float* __restrict__ f, long long fs,
+__global__ void TAT_ROWS_BOUNDS k_rows_fwd(DevPlan P, const float* __restrict__ f, long long fs,
                                                    float2* __restrict__ X, long long xs, int RP, int nt) {
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
@@ -638,7 +642,7 @@ __device__ __forceinline__ void rows_inverse_dft(const DevPlan& P, const float2*
 }
 
 template <int L>
-__global__ void __launch_bounds__(1024) k_rows_adj(DevPlan P, const float2* __restrict__ X, long long xs, float* __restrict__ f,
+__global__ void TAT_ROWS_BOUNDS k_rows_adj(DevPlan P, const float2* __restrict__ X, long long xs, float* __restrict__ f,
                            long long fs, int RP, int nt) {
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
@@ -788,7 +792,7 @@ __global__ void TAT_COLS_BOUNDS_I k_cols_inv(DevPlan P, const float2* __restrict
 // (times dxi^2/2pi); each CTA adds its sum of v over Omega \ Omega0 into the
 // image's accumulator.
 template <int L>
-__global__ void __launch_bounds__(1024) k_rows_inv(DevPlan P, const float2* __restrict__ X, long long xs,
+__global__ void TAT_ROWS_BOUNDS k_rows_inv(DevPlan P, const float2* __restrict__ X, long long xs,
                                                    float* __restrict__ f, long long fs, float* acc, long long accs,
                                                    int RP, int nt) {
   extern __shared__ float2 sm[];

@@ -307,10 +307,10 @@ tat_status make_fft(tat_plan_s* P, int L, FftDev* f, int* nthreads) {
   }
   f->ptw_len = (int)pt.size();
   TAT_TRY(upload(P, pt, &f->ptw));
-  // Four-step twiddles for L = RA*256 (RA = 2, 4, 8, 16):
+  // Four-step twiddles for L = RA*256 (RA = 2, 4, 8, 16, 32):
   // w_L^(16 a p), w_L^(b p), w_256^(m p) for a, b, m < 16 and p = 1, 2, 4, 8.
   std::vector<float2> ft(192, make_float2(1.f, 0.f));
-  if (L % 256 == 0 && (L / 256 == 2 || L / 256 == 4 || L / 256 == 8 || L / 256 == 16)) {
+  if (L % 256 == 0 && (L / 256 == 2 || L / 256 == 4 || L / 256 == 8 || L / 256 == 16 || L / 256 == 32)) {
     const int pw[4] = {1, 2, 4, 8};
     for (int pi = 0; pi < 4; ++pi)
       for (int i = 0; i < 16; ++i) {
@@ -568,14 +568,14 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
   }
   // Launch shapes.
   LaunchCfg& c = P->cfg;
-  // Lengths RA*256 (RA = 2..16) use the in-place four-step transform, which
+  // Lengths RA*256 (RA = 2..32) use the in-place four-step transform, which
   // needs 256 threads; up to 4 row pairs (1024 threads) per CTA.
-  const bool four_step = d.N == 512 || d.N == 1024 || d.N == 2048 || d.N == 4096;
+  const bool four_step = d.N == 512 || d.N == 1024 || d.N == 2048 || d.N == 4096 || d.N == 8192;
   c.nt_rows = four_step ? std::max(c.nt_N, 256) : c.nt_N;
   // the four-step transform needs groups of at least 64 threads (step B of RA = 4)
   if (d.n_phi == 1024) c.nt_phi = std::max(c.nt_phi, 64);
   if (n_det == 1024) c.nt_det = std::max(c.nt_det, 64);
-  c.rows_pairs = std::max(1, std::min(4, 1024 / c.nt_rows));
+  c.rows_pairs = d.N == 8192 ? 1 : std::max(1, std::min(4, 1024 / c.nt_rows));
   c.strip = 8;
   c.rings_per_cta = rings_per_cta_for(n_phi);
   c.t_tile = time_tile_for(n_det);

@@ -79,8 +79,9 @@ struct Slot {
   size_t off = 0, bytes = 0;          // arena region
   float* in = nullptr;
   float* out = nullptr;
+  float* mid = nullptr;               // A f of a pair request (TAT_OP_PAIR only)
   void* ws = nullptr;
-  size_t in_elems = 0, out_elems = 0;
+  size_t in_elems = 0, out_elems = 0, mid_elems = 0;
   std::map<int, cudaGraphExec_t> graphs;  // batch -> executable graph
   std::vector<long long> pending;
   unsigned long long last_use = 0;
@@ -134,19 +135,25 @@ void fail_now(tat_service_s* S, const std::vector<long long>& ids, tat_status wh
   S->st.completed += (long long)ids.size();
 }
 
-tat_status launch_op(tat_plan_t plan, tat_op op, int b, const float* in, long long in_s, float* out, long long out_s,
-                     void* ws, cudaStream_t st) {
-  switch (op) {
-    case TAT_OP_FORWARD: return tat_forward_batched(plan, b, in, in_s, out, out_s, ws, st);
-    case TAT_OP_ADJOINT: return tat_adjoint_batched(plan, b, in, in_s, out, out_s, ws, st);
-    case TAT_OP_INVERSE: return tat_inverse_batched(plan, b, in, in_s, out, out_s, ws, st);
+tat_status launch_op(const Slot& s, int b) {
+  const long long in_s = (long long)s.in_elems, out_s = (long long)s.out_elems;
+  switch (s.op) {
+    case TAT_OP_FORWARD: return tat_forward_batched(s.plan, b, s.in, in_s, s.out, out_s, s.ws, s.stream);
+    case TAT_OP_ADJOINT: return tat_adjoint_batched(s.plan, b, s.in, in_s, s.out, out_s, s.ws, s.stream);
+    case TAT_OP_INVERSE: return tat_inverse_batched(s.plan, b, s.in, in_s, s.out, out_s, s.ws, s.stream);
+    case TAT_OP_PAIR: {
+      const long long mid_s = (long long)s.mid_elems;
+      const tat_status e = tat_forward_batched(s.plan, b, s.in, in_s, s.mid, mid_s, s.ws, s.stream);
+      if (e != TAT_OK) return e;
+      return tat_adjoint_batched(s.plan, b, s.mid, mid_s, s.out, out_s, s.ws, s.stream);
+    }
   }
   return TAT_ERR_INVALID_ARG;
 }
 
 size_t slot_bytes(const Slot& s, int cap) {
   return align_up(s.in_elems * sizeof(float) * cap) + align_up(s.out_elems * sizeof(float) * cap) +
-         align_up(tat_workspace_size(s.plan, cap));
+         align_up(s.mid_elems * sizeof(float) * cap) + align_up(tat_workspace_size(s.plan, cap));
 }
 
 void drop_graphs(Slot& s) {
@@ -159,7 +166,7 @@ void evict(tat_service_s* S, Slot& s) {
   drop_graphs(s);
   S->arena.release(s.off);
   s.cap = 0;
-  s.in = s.out = nullptr;
+  s.in = s.out = s.mid = nullptr;
   s.ws = nullptr;
   ++S->st.evictions;
 }
@@ -192,6 +199,8 @@ tat_status admit(tat_service_s* S, Slot& s) {
     p += align_up(s.in_elems * sizeof(float) * cap);
     s.out = reinterpret_cast<float*>(p);
     p += align_up(s.out_elems * sizeof(float) * cap);
+    s.mid = s.mid_elems ? reinterpret_cast<float*>(p) : nullptr;
+    p += align_up(s.mid_elems * sizeof(float) * cap);
     s.ws = p;
     return TAT_OK;
   }
@@ -229,16 +238,14 @@ tat_status run_chunk(tat_service_s* S, Slot& s, const std::vector<long long>& id
     if (e != TAT_OK) return e;
     ++S->st.graph_launches;
   } else {
-    tat_status e = launch_op(s.plan, s.op, b, s.in, (long long)s.in_elems, s.out, (long long)s.out_elems, s.ws,
-                             s.stream);
+    tat_status e = launch_op(s, b);
     if (e != TAT_OK) return e;
     if (S->cfg.use_graphs) {
       // capture the same launch for the next chunk of this size (capture runs nothing)
       cudaGraph_t graph = nullptr;
       cudaGraphExec_t exec = nullptr;
       if (cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        const tat_status le = launch_op(s.plan, s.op, b, s.in, (long long)s.in_elems, s.out,
-                                        (long long)s.out_elems, s.ws, s.stream);
+        const tat_status le = launch_op(s, b);
         const cudaError_t ce = cudaStreamEndCapture(s.stream, &graph);
         if (le == TAT_OK && ce == cudaSuccess && graph &&
             cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
@@ -321,7 +328,8 @@ tat_status tat_service_destroy(tat_service_t S) {
 tat_status tat_service_submit(tat_service_t S, const tat_plan_desc* desc, tat_op op, const float* in, float* out,
                               long long* id) {
   if (!S || !desc || !in || !out || !id) return TAT_ERR_INVALID_ARG;
-  if (op != TAT_OP_FORWARD && op != TAT_OP_ADJOINT && op != TAT_OP_INVERSE) return TAT_ERR_INVALID_ARG;
+  if (op != TAT_OP_FORWARD && op != TAT_OP_ADJOINT && op != TAT_OP_INVERSE && op != TAT_OP_PAIR)
+    return TAT_ERR_INVALID_ARG;
   tat_plan_info info;
   const tat_status q = tat_plan_query(desc, &info);
   if (q != TAT_OK) return q;
@@ -333,8 +341,9 @@ tat_status tat_service_submit(tat_service_t S, const tat_plan_desc* desc, tat_op
     slot->key = key;
     slot->op = op;
     const size_t img = (size_t)desc->n * desc->n, dat = (size_t)desc->n_det * desc->n_t;
-    slot->in_elems = op == TAT_OP_FORWARD ? img : dat;
+    slot->in_elems = op == TAT_OP_FORWARD || op == TAT_OP_PAIR ? img : dat;
     slot->out_elems = op == TAT_OP_FORWARD ? dat : img;
+    slot->mid_elems = op == TAT_OP_PAIR ? dat : 0;
   }
   Request r;
   r.id = (long long)S->requests.size();
@@ -367,8 +376,8 @@ tat_status tat_service_flush(tat_service_t S) {
       // tune on zeroed slot buffers at the slot's batch size (the knobs belong to the plan)
       const tat_plan_desc& pd = d;
       const size_t img = (size_t)pd.n * pd.n, dat = (size_t)pd.n_det * pd.n_t;
-      float* fbuf = s.op == TAT_OP_FORWARD ? s.in : s.out;
-      float* gbuf = s.op == TAT_OP_FORWARD ? s.out : s.in;
+      float* fbuf = s.op == TAT_OP_ADJOINT ? s.out : s.in;
+      float* gbuf = s.op == TAT_OP_PAIR ? s.mid : (s.op == TAT_OP_FORWARD ? s.out : s.in);
       cudaMemsetAsync(fbuf, 0, img * sizeof(float) * s.cap, s.stream);
       cudaMemsetAsync(gbuf, 0, dat * sizeof(float) * s.cap, s.stream);
       e = tat_plan_autotune(s.plan, s.cap, fbuf, gbuf, fbuf, s.ws, s.stream, nullptr, nullptr, nullptr);

@@ -50,6 +50,10 @@ CASES = {
     "n64_fold": dict(n=64, n_det=64, n_t=128, support_radius=0.9, n_phi=256),
     "n64_physical": dict(n=64, n_det=128, n_t=128, support_radius=0.9, c=1.5, R=0.8, T=1.6),
     "n64_pad16": dict(n=64, n_det=128, n_t=128, support_radius=0.9, pad_L=16.0),
+    # N = 8192: the four-step transform with a 32-point first step, in full (553 > 512 rows)
+    # and pruned to two terms (440 <= 512 rows)
+    "n553_N8192": dict(n=553, n_det=128, n_t=128, support_radius=0.9, T=6.0),
+    "n440_N8192_pruned": dict(n=440, n_det=128, n_t=128, support_radius=0.9, T=8.0),
 }
 
 _ORACLE_KEYS = {"low_mode_quadrature": "low_mode"}

@@ -1,5 +1,6 @@
 """GPU tests of the mixed-size request runtime (include/tat_service.h) and the
-launch-shape autotuner: results equal the direct batched calls, graphs are
+launch-shape autotuner: results (A, A*, A^-1 and the pair A* A) equal the direct
+batched calls, graphs are
 reused, admission under a tight memory budget evicts and shrinks batches and
 reports out-of-memory for a request that fits at no batch size.
 """
@@ -39,10 +40,10 @@ def _requests(torch, count=12):
     reqs = []
     for i in range(count):
         n, nd, nt = SIZES[i % len(SIZES)]
-        op = ("forward", "adjoint", "inverse")[(i // len(SIZES)) % 3]
-        if op == "forward":
+        op = ("forward", "adjoint", "inverse", "pair")[(i // len(SIZES)) % 4]
+        if op in ("forward", "pair"):
             x = torch.tensor(ellipse_phantom(n, i).astype(np.float32), device="cuda:0")
-            out = torch.empty((nd, nt), device="cuda:0")
+            out = torch.empty((nd, nt) if op == "forward" else (n, n), device="cuda:0")
         else:
             x = torch.tensor(random_sinogram(nd, nt, i).astype(np.float32), device="cuda:0")
             out = torch.empty((n, n), device="cuda:0")
@@ -52,6 +53,8 @@ def _requests(torch, count=12):
 
 def _direct(pkg, torch, n, nd, nt, op, x):
     o = pkg.TatOperator(n, nd, nt, device="cuda:0", support_radius=0.9)
+    if op == "pair":
+        return o.adjoint(o.forward(x)).cpu().numpy()
     return getattr(o, op)(x).cpu().numpy()
 
 
