@@ -476,13 +476,29 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
   float2* buf = sm + g * SL;
   if constexpr (FourStep<L>::on) col_fft_inv<L>(buf, P.fphi, smtw, gt, nt, nt, P.n_phi, nullptr);
   else fft<L, true>(buf, P.fphi, gt, nt, P.n_phi, P.n_phi, nullptr, nullptr, smptw);
-  const int r = rbase + g;
-  if (r <= P.J) {
-    const int q4 = P.n_phi / 4;
-    for (int l = gt; l < P.nh; l += nt) {
+  if constexpr (INV) {
+    // Angle-major output Y[l'][ring] (row length J+1, rings 1..J): the inverse's
+    // Cartesian nodes along a column read neighbouring rings at nearly one angle,
+    // which this layout makes adjacent.  The CTA's rings go out together, so each
+    // angle's run of rings is one contiguous write.
+    __syncthreads();
+    const int q4 = P.n_phi / 4, J1 = P.J + 1, ng = blockDim.x / nt;
+    for (int e = threadIdx.x; e < P.nh * ng; e += blockDim.x) {
+      const int l = e / ng, gg = e - l * ng, rr = rbase + gg;
+      if (rr > P.J) continue;
       int s = l - q4;
       if (s < 0) s += P.n_phi;
-      Yb[(size_t)r * P.nh + l] = buf[xpad<L>(s)];
+      Yb[(size_t)l * J1 + rr] = sm[gg * SL + xpad<L>(s)];
+    }
+  } else {
+    const int r = rbase + g;
+    if (r <= P.J) {
+      const int q4 = P.n_phi / 4;
+      for (int l = gt; l < P.nh; l += nt) {
+        int s = l - q4;
+        if (s < 0) s += P.n_phi;
+        Yb[(size_t)r * P.nh + l] = buf[xpad<L>(s)];
+      }
     }
   }
 }
@@ -701,12 +717,14 @@ __global__ void __launch_bounds__(1024) k_modes_inv(DevPlan P, const float2* __r
   for (int j = threadIdx.x; j < J1; j += blockDim.x) Dm[j] = sm[xpad<L>(j)];
 }
 
-// Polar sample Y[ring j][l'] of the half circle; ring 0 (lambda = 0) is zero for
-// the inverse, and l' = nh (phi = pi/2) is the conjugate of l' = 0 (phi = -pi/2).
+// Polar sample (ring j, angle l') of the half circle from the angle-major
+// Y[l'][j] that k_rings_adj<L, true> writes; ring 0 (lambda = 0) is zero for the
+// inverse, and l' = nh (phi = pi/2) is the conjugate of l' = 0 (phi = -pi/2).
 __device__ __forceinline__ float2 inv_polar(const DevPlan& P, const float2* __restrict__ Yb, int j, int l) {
   if (j == 0) return make_float2(0.f, 0.f);
-  if (l >= P.nh) return cconj(Yb[(size_t)j * P.nh + (l - P.nh)]);
-  return Yb[(size_t)j * P.nh + l];
+  const size_t J1 = (size_t)P.J + 1;
+  if (l >= P.nh) return cconj(Yb[(size_t)(l - P.nh) * J1 + j]);
+  return Yb[(size_t)l * J1 + j];
 }
 
 // vhat at the Cartesian node (c, qs) of the half plane (Algorithm 3, step 5):
