@@ -1215,6 +1215,8 @@ def run_lpd(args, rank, world, local):
                 "data": "synthetic (seeded ellipse phantoms, data from this library's A + 2 % noise)",
                 "config": lpd_config(args.train_steps, args.arc),
                 "comparison_ms_per_step": {"graph": ms, "eager": ms_eager, "operators_only_4K_calls": ms_ops},
+                "operator_launch_shapes": {"ms_pair": net.tuned[0], "strip": net.tuned[1], "row_pairs": net.tuned[2]}
+                if net.tuned else None,
                 "reconstruction_rel_l2_test": {"lpd": err_lpd, "tv_ls": err_tv, "tv_alpha": best_alpha,
                                                "nnls": err_nnls},
                 "training": {"steps": args.train_steps, "seconds": t_train, "loss_curve": losses,

@@ -478,6 +478,17 @@ class TatOperator:
         self.W_Y = (self.info["dt"] * R / c) * (2 * math.pi * R / n_det)
         self._ws = {}
 
+    def autotune(self, batch):
+        """Times the column-strip and row-pair launch shapes on one A + A* of `batch` zero images
+        and keeps the fastest for this plan (tat_plan_autotune); returns (ms, strip, row_pairs)."""
+        torch = self.torch
+        f = torch.zeros((batch, self.n, self.n), dtype=torch.float32, device=self.device)
+        g = torch.zeros((batch, self.n_det, self.n_t), dtype=torch.float32, device=self.device)
+        ws = self.workspace(batch)
+        with torch.cuda.device(self.device):
+            return tat_plan_autotune(self.plan, batch, f.data_ptr(), g.data_ptr(), f.data_ptr(), ws.data_ptr(),
+                                     torch.cuda.current_stream(self.device).cuda_stream)
+
     def workspace(self, batch):
         ws = self._ws.get(batch)
         if ws is None:

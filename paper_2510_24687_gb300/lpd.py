@@ -62,8 +62,11 @@ def init_params(seed=0):
 class LPD:
     """K-iteration learned primal-dual on one TatOperator for batches of `batch` data sets."""
 
-    def __init__(self, op, batch, K=10, params=None, seed=0, lr=1e-3, betas=(0.9, 0.999), eps=1e-8):
+    def __init__(self, op, batch, K=10, params=None, seed=0, lr=1e-3, betas=(0.9, 0.999), eps=1e-8, autotune=True):
         self.op, self.B, self.K = op, batch, K
+        # the operator's launch shapes tuned once for this batch (small images leave the
+        # default column strips with too few CTAs per SM)
+        self.tuned = op.autotune(batch) if autotune else None
         self.lr, self.betas, self.eps = lr, betas, eps
         dev = op.device
         self.dev = dev
