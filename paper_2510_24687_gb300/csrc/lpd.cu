@@ -107,6 +107,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
   unsigned ok;
   asm volatile(
@@ -332,6 +335,245 @@ __global__ void __launch_bounds__(256) k_conv_mid(int B, int H, int W, const __g
         mid_tile<BWD, MASK, OMASK>(sm + s * STAGE, sm + s * STAGE + HALO_SLOT, sm + s * STAGE + OT, wsm, bias, out, b,
                                    y0, x0, H, W);
       });
+}
+
+// ---- 32 -> 32 forward on the 5th-generation tensor cores (tcgen05, accumulators in TMEM)
+//
+// Implicit GEMM per tile of 16 rows x 8 pixels: M = 128 pixels, N = 32 output channels,
+// K = 9 taps x 32 input channels in 18 tcgen05.mma (kind::f16, BF16 operands, FP32
+// accumulation) issued by one thread.  Operands sit in shared memory in the canonical
+// K-major layout without swizzle: 8 x 16-byte core matrices, i.e. 8 consecutive pixels (or
+// output channels) of one 8-channel plane.  The halo of a tile (18 x 10 pixels) arrives by
+// TMA as four 8-channel planes [pixel][16 B], so the A operand of a tap is the plane shifted
+// by the tap's offset: core-matrix rows 16 B apart (consecutive pixels), core-matrix groups
+// 160 B apart (one halo row of 10 pixels), K halves one plane apart.  The accumulator of a
+// tile is 32 TMEM columns; two of them alternate, so the epilogue of tile i-1 (tcgen05.ld,
+// bias, ReLU, BF16, 64 contiguous bytes per pixel) overlaps the MMAs of tile i, and four halo
+// slots rotate, so the halos of tiles i+1..i+3 load meanwhile.  tcgen05.commit signals on an
+// mbarrier when a tile's MMAs have finished reading their halo slot and writing their
+// accumulator.  Every wait is bounded; on a timeout the CTA records it, waits (bounded) for
+// its copies and MMAs in flight, frees its TMEM and returns.
+namespace tc {
+constexpr int TX = 8, TY = 16;             // tile: M = 128 pixels
+constexpr int HX = TX + 2, HY = TY + 2;    // 10 x 18 halo
+constexpr int PLANE = 2944;                // bytes of one 8-channel halo plane (180 x 16 B, rounded up to 128 B)
+constexpr int SLOT = 4 * PLANE;            // one staged halo
+constexpr int NS = 4;                      // halo slots: tiles n+1..n+3 load while tile n computes
+constexpr int HALO_TX = 4 * HX * HY * 16;  // bytes a halo's four copies deliver
+constexpr int WOFF = NS * SLOT;            // weights [tap][plane][co][16 B], 2 KB per tap
+constexpr int BOFF = WOFF + 9 * 2048;      // bias, 32 floats
+constexpr int MOFF = BOFF + 128;           // mbarriers: halo full[NS], empty[NS], accumulator full[2],
+                                           // empty[2]; then the TMEM address
+constexpr int SMEM = 1024 + MOFF + 128;     // alignment slack + what the layout above uses
+constexpr int TMEM_COLS = 64;              // two accumulators of 32 FP32 columns
+// Instruction descriptor (kind::f16): FP32 D, BF16 A and B, both K-major, N = 32, M = 128.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+}  // namespace tc
+
+// Shared-memory matrix descriptor: canonical K-major layout without swizzle, start address,
+// leading byte offset (between the two core matrices along K) and stride byte offset
+// (between core-matrix groups along M or N), all in 16-byte units; version 1.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// 32 consecutive FP32 columns of the warp's 32 TMEM lanes (one lane per thread).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+// FWD: out = relu(conv(in) + b).  BWD: out = conv^T(in) (the data gradient of an already
+// masked gradient `in`: taps flipped, input and output channels swapped), times [omask > 0]
+// with OMASK (the ReLU mask of the layer below).
+//
+// Warp roles (192 threads): warp 0 loads halos (TMA), warp 1 owns the TMEM and issues the
+// MMAs, warps 2-5 run the epilogue (warp w reads TMEM lanes 32 (w mod 4) .. + 31).  They hand
+// tiles over through mbarriers only -- halo full / empty per slot, accumulator full / empty
+// per TMEM buffer -- so no CTA-wide barrier sits inside the tile loop.
+template <bool BWD, bool OMASK>
+__global__ void __launch_bounds__(192, 3) k_conv_mid_tc(int B, int H, int W, const __grid_constant__ CUtensorMap map8,
+                                                        const tat_bf16* __restrict__ w, const float* __restrict__ bias,
+                                                        const tat_bf16* __restrict__ omask,
+                                                        tat_bf16* __restrict__ out) {
+  constexpr int TX = tc::TX, TY = tc::TY, HX = tc::HX, PLANE = tc::PLANE, SLOT = tc::SLOT, WOFF = tc::WOFF;
+  constexpr int BOFF = tc::BOFF, MOFF = tc::MOFF, HALO_TX = tc::HALO_TX, TMEM_COLS = tc::TMEM_COLS, NS = tc::NS;
+  constexpr uint32_t IDESC = tc::IDESC;
+  extern __shared__ unsigned char dsm[];
+  unsigned char* sm = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
+  tat_bf16* wsm = reinterpret_cast<tat_bf16*>(sm + WOFF);
+  float* bsm = reinterpret_cast<float*>(sm + BOFF);
+  uint64_t* hfull = reinterpret_cast<uint64_t*>(sm + MOFF);  // [NS] halo landed
+  uint64_t* hempty = hfull + NS;                              // [NS] halo consumed by the MMAs
+  uint64_t* afull = hempty + NS;                              // [2] accumulator written
+  uint64_t* aempty = afull + 2;                               // [2] accumulator read by the epilogue
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(aempty + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // weights w[tap][co][ci] -> B[tap][k / 8][n][k % 8] with n the output channel of this
+  // GEMM and k its input channel (BWD: n = ci, k = co, tap mirrored)
+  for (int e = tid; e < 9 * C * C; e += blockDim.x) {
+    const int tap = e >> 10, co = (e >> 5) & 31, ci = e & 31;
+    if (BWD) wsm[(8 - tap) * 1024 + (co >> 3) * 256 + ci * 8 + (co & 7)] = w[e];
+    else wsm[tap * 1024 + (ci >> 3) * 256 + co * 8 + (ci & 7)] = w[e];
+  }
+  if (!BWD && tid < C) bsm[tid] = bias[tid];
+  if (tid == 0) {
+    for (int k = 0; k < NS; ++k) {
+      mbar_init(&hfull[k], 1);
+      mbar_init(&hempty[k], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&afull[k], 1);
+      mbar_init(&aempty[k], 128);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // weights: generic writes, read by the MMAs
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+  const uint32_t sbase = smem_u32(sm);
+  const int tilesx = (W + TX - 1) / TX, tilesy = (H + TY - 1) / TY;
+  const long long ntiles = (long long)B * tilesx * tilesy;
+  const int mine = ntiles > blockIdx.x ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x) + 1 : 0;  // tiles of this CTA
+  auto coords = [&](int n, int& b, int& y0, int& x0) {
+    const long long tile = blockIdx.x + (long long)n * gridDim.x;
+    b = (int)(tile / (tilesx * tilesy));
+    const int rr = (int)(tile % (tilesx * tilesy));
+    y0 = (rr / tilesx) * TY;
+    x0 = (rr % tilesx) * TX;
+  };
+  bool ok = true;
+  if (warp == 0) {
+    if (lane == 0) {  // halo loads
+      int issued = 0;
+      for (int n = 0; n < mine && ok; ++n) {
+        const int k = n % NS;
+        if (n >= NS) ok = mbar_wait(&hempty[k], (unsigned)((n / NS + 1) & 1));  // MMAs of tile n - NS done
+        if (!ok) break;
+        int b, y0, x0;
+        coords(n, b, y0, x0);
+        mbar_expect_tx(&hfull[k], HALO_TX);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tma_load_4d(sm + k * SLOT + c * PLANE, &map8, 8 * c, x0 - 1, y0 - 1, b, &hfull[k]);
+        issued = n + 1;
+      }
+      if (!ok) {  // let the copies in flight land (their slots are not reused after this)
+        for (int n = issued - NS > 0 ? issued - NS : 0; n < issued; ++n)
+          mbar_wait(&hfull[n % NS], (unsigned)((n / NS) & 1));
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMAs
+      int committed = 0;
+      for (int n = 0; n < mine && ok; ++n) {
+        const int k = n % NS, a = n & 1;
+        ok = mbar_wait(&hfull[k], (unsigned)((n / NS) & 1));
+        if (ok && n >= 2) ok = mbar_wait(&aempty[a], (unsigned)((n / 2 + 1) & 1));  // tile n-2 read out
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t d = tbase + (uint32_t)(a * 32);
+        const uint32_t abase = sbase + k * SLOT, wbase = sbase + WOFF;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+          for (int kc = 0; kc < 2; ++kc) {
+            const uint64_t ad = umma_desc(abase + 2 * kc * PLANE + (dy * HX + dx) * 16, PLANE, HX * 16);
+            const uint64_t bd = umma_desc(wbase + tap * 2048 + 2 * kc * 512, 512, 128);
+            umma_f16(d, ad, bd, IDESC, (tap | kc) != 0);
+          }
+        }
+        umma_commit(&hempty[k]);  // halo slot free once these MMAs have read it
+        umma_commit(&afull[a]);   // accumulator ready
+        committed = n + 1;
+      }
+      if (!ok && committed > 0)  // the MMAs in flight must finish before the TMEM is freed
+        mbar_wait(&afull[(committed - 1) & 1], (unsigned)(((committed - 1) >> 1) & 1));
+    }
+  } else {  // epilogue: 128 threads, thread m of the tile = TMEM lane m = pixel (m / 8, m % 8)
+    const int quarter = warp & 3;
+    const int m = 32 * quarter + lane;
+    for (int n = 0; n < mine && ok; ++n) {
+      const int a = n & 1;
+      ok = mbar_wait(&afull[a], (unsigned)((n >> 1) & 1));
+      if (__any_sync(0xffffffffu, !ok)) {  // keep the warp together for the warp-wide TMEM load
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      uint32_t r[32];
+      tmem_ld32(tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(a * 32), r);
+      tc_fence_before();
+      mbar_arrive(&aempty[a]);
+      int b, y0, x0;
+      coords(n, b, y0, x0);
+      const int y = y0 + (m >> 3), x = x0 + (m & 7);
+      if (y < H && x < W) {
+        const long long pix = ((long long)b * H + y) * W + x;
+        uint4* dst = reinterpret_cast<uint4*>(out + pix * C);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          unsigned pk[4];
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const int c0 = 8 * q + 2 * kk;
+            float v0 = __uint_as_float(r[c0]), v1 = __uint_as_float(r[c0 + 1]);
+            if (!BWD) {
+              v0 = fmaxf(v0 + bsm[c0], 0.f);
+              v1 = fmaxf(v1 + bsm[c0 + 1], 0.f);
+            }
+            pk[kk] = (unsigned)tobf(v0) | ((unsigned)tobf(v1) << 16);
+          }
+          if (OMASK) {
+            const uint4 mk = reinterpret_cast<const uint4*>(omask + pix * C)[q];
+            pk[0] = relu_masked(pk[0], mk.x);
+            pk[1] = relu_masked(pk[1], mk.y);
+            pk[2] = relu_masked(pk[2], mk.z);
+            pk[3] = relu_masked(pk[3], mk.w);
+          }
+          dst[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+      }
+    }
+  }
+  if (!ok) atomicExch(&g_lpd_timeout, 1);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tbase), "r"(TMEM_COLS) : "memory");
 }
 
 // Dynamic shared memory of k_conv_mid_wgrad: alignment slack, two slots of three halos
@@ -1051,6 +1293,31 @@ bool smem_attr(size_t bytes) {
 
 bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) != 0; }
 
+// Tensor map of a [batch][H][W][32] BF16 activation for the tcgen05 kernel: 8-channel
+// boxes of the 18 x 10 halo, no swizzle (the MMA's canonical K-major layout).
+bool halo8_map(CUtensorMap* m, const tat_bf16* base, int batch, int H, int W) {
+  const EncodeTiled fn = encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)batch};
+  const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+  const cuuint32_t box[4] = {8, (cuuint32_t)tc::HX, (cuuint32_t)tc::HY, 1};
+  const cuuint32_t estride[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<tat_bf16*>(base), dims, strides, box, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <bool BWD, bool OMASK>
+tat_status launch_mid_tc(int batch, int H, int W, const CUtensorMap& m8, const tat_bf16* w, const float* b,
+                         const tat_bf16* omask, tat_bf16* out, cudaStream_t s, const char* what) {
+  constexpr size_t smem = tc::SMEM;
+  if (!smem_attr<k_conv_mid_tc<BWD, OMASK>>(smem)) return TAT_ERR_CUDA;
+  const long long tiles = (long long)batch * ((H + tc::TY - 1) / tc::TY) * ((W + tc::TX - 1) / tc::TX);
+  const int ctas = (int)(tiles < 3 * 152 ? tiles : 3 * 152);  // 3 resident per SM: 3 x 64 TMEM columns
+  k_conv_mid_tc<BWD, OMASK><<<ctas, 192, smem, s>>>(batch, H, W, m8, w, b, omask, out);
+  return launched(what);
+}
+
 template <bool BWD, bool MASK, bool OMASK>
 tat_status launch_mid(int batch, int H, int W, const tat_bf16* in, const tat_bf16* mask, const tat_bf16* omask,
                       const tat_bf16* w, const float* b, tat_bf16* out, cudaStream_t s, const char* what) {
@@ -1165,9 +1432,15 @@ tat_status tat_conv_in_bwd_weights(int batch, int H, int W, int cin, const float
 
 tat_status tat_conv_mid_fwd(int batch, int H, int W, const tat_bf16* h_in, const tat_bf16* w, const float* b,
                             tat_bf16* h_out, tat_stream_t stream) {
-  if (bad_sizes(batch, H, W) || !h_in || !w || !b || !h_out) return TAT_ERR_INVALID_ARG;
-  return launch_mid<false, false, false>(batch, H, W, h_in, nullptr, nullptr, w, b, h_out,
-                                         static_cast<cudaStream_t>(stream), "tat_conv_mid_fwd");
+  if (bad_sizes(batch, H, W) || !h_in || !w || !b || !h_out || misaligned(h_in) || misaligned(h_out))
+    return TAT_ERR_INVALID_ARG;
+  CUtensorMap m8;
+  if (!halo8_map(&m8, h_in, batch, H, W)) {
+    fprintf(stderr, "tat_conv_mid_fwd: tensor map encoding failed\n");
+    return TAT_ERR_CUDA;
+  }
+  return launch_mid_tc<false, false>(batch, H, W, m8, w, b, nullptr, h_out, static_cast<cudaStream_t>(stream),
+                                     "tat_conv_mid_fwd");
 }
 
 tat_status tat_conv_mid_bwd_data(int batch, int H, int W, const tat_bf16* g_out, const tat_bf16* h_out,
@@ -1177,8 +1450,15 @@ tat_status tat_conv_mid_bwd_data(int batch, int H, int W, const tat_bf16* g_out,
   const char* what = "tat_conv_mid_bwd_data";
   if (h_out && h_in) return launch_mid<true, true, true>(batch, H, W, g_out, h_out, h_in, w, nullptr, g_in, s, what);
   if (h_out) return launch_mid<true, true, false>(batch, H, W, g_out, h_out, nullptr, w, nullptr, g_in, s, what);
-  if (h_in) return launch_mid<true, false, true>(batch, H, W, g_out, nullptr, h_in, w, nullptr, g_in, s, what);
-  return launch_mid<true, false, false>(batch, H, W, g_out, nullptr, nullptr, w, nullptr, g_in, s, what);
+  // an already masked gradient: the tcgen05 kernel
+  if (misaligned(g_out) || misaligned(h_in) || misaligned(g_in)) return TAT_ERR_INVALID_ARG;
+  CUtensorMap m8;
+  if (!halo8_map(&m8, g_out, batch, H, W)) {
+    fprintf(stderr, "%s: tensor map encoding failed\n", what);
+    return TAT_ERR_CUDA;
+  }
+  if (h_in) return launch_mid_tc<true, true>(batch, H, W, m8, w, nullptr, h_in, g_in, s, what);
+  return launch_mid_tc<true, false>(batch, H, W, m8, w, nullptr, nullptr, g_in, s, what);
 }
 
 tat_status tat_lpd_check(void) {
