@@ -224,6 +224,20 @@ def time_oracle(sample_ops=2, seed=0):
     return time.perf_counter() - t0
 
 
+def time_oracle_single_thread(timeout_s=180):
+    """Seconds of one oracle application at n = 512 with BLAS and OpenMP held to one thread
+    (a child process, since thread counts are fixed when numpy loads); None if it fails."""
+    import subprocess
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = "import bench; print(bench.time_oracle(1))"
+    try:
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                           timeout=timeout_s)
+        return float(r.stdout.strip().splitlines()[-1]) if r.returncode == 0 else None
+    except (subprocess.TimeoutExpired, ValueError, IndexError):
+        return None
+
+
 def cpu_threads():
     for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         if os.environ.get(var):
@@ -546,7 +560,13 @@ def main():
         ops = 2
         t = time_oracle(ops)
         cpu = {"value": 0.5 * ops / t, "unit": "pairs/s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"one A+A* pair of the n={N_IMG} workload (image seed 0) through the FP64 numpy/scipy oracle"}
+               "sample": f"one A+A* pair of the n={N_IMG} workload (image seed 0) through the FP64 numpy/scipy "
+                         "oracle, its Bessel and stencil tables built inside each call; its matrix products use "
+                         "all cores (BLAS), its FFTs one"}
+        t1 = time_oracle_single_thread()
+        if t1 is not None:
+            cpu["single_thread"] = {"value": 0.5 / t1, "unit": "pairs/s", "cores": 1,
+                                    "sample": "one oracle A (half a pair), BLAS and OpenMP held to one thread"}
 
     if rank == 0:
         line = {"metric": METRIC.replace("n=512", f"n={N_IMG}"), "value": value, "unit": "pairs/s", "n_gpus": world,
