@@ -126,12 +126,17 @@ __global__ void TAT_COLS_BOUNDS_F k_cols_fwd(DevPlan P, const float2* __restrict
   const float2* Xb = X + (size_t)b * xs;
   float2* Yb = Y + (size_t)b * ys;
   const int N = P.N;
+  // the first PolarEntry of each thread's gather is loaded before the column FFT, so that
+  // its latency hides behind the transform
+  PolarEntry pe0{};
 #pragma unroll 1
   for (int cc = 0; cc < ncols; ++cc) {
     float2* buf = (cc & 1) ? slot1 : slot0;
     const int c = c0 + cc;
     const float2* col = Xb + (size_t)c * P.n;  // R[c][0..n): contiguous
     for (int iy = tid; iy < P.n; iy += NT) buf[xpad<L>(iy)] = col[iy];
+    const int e0 = cc > 0 ? P.coloff[c - 1] + tid : 0, e1 = cc > 0 ? P.coloff[c] : 0;
+    if (e0 < e1) pe0 = P.pts[e0];
     __syncthreads();
     // column DFT over the n nonzero rows (the phase e^{i q dxi} of each output
     // row is applied by the gather below)
@@ -139,9 +144,8 @@ __global__ void TAT_COLS_BOUNDS_F k_cols_fwd(DevPlan P, const float2* __restrict
     if (cc > 0) {
       const float2* A = (cc & 1) ? slot0 : slot1;  // column c-1
       const float2* B = buf;                       // column c
-      const int e1 = P.coloff[c];
-      for (int e = P.coloff[c - 1] + tid; e < e1; e += NT) {
-        const PolarEntry pe = P.pts[e];
+      for (int e = e0; e < e1; e += NT) {
+        const PolarEntry pe = e == e0 ? pe0 : P.pts[e];
         const int ra = wrapN(pe.k0, N), rb = wrapN(pe.k0 + 1, N);
         const int qa = xpad<L>(colpos<L>(ra)), qb = xpad<L>(colpos<L>(rb));
         const float a = pe.a, bb = pe.b;
