@@ -238,6 +238,27 @@ def time_oracle_single_thread(timeout_s=180):
         return None
 
 
+def replica_seed0(rank, batch):
+    """First phantom seed of a rank's batch: replicas work on disjoint images."""
+    return rank * batch
+
+
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time (the whole job ends when it does); a no-op on one rank."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, ms):
+    """Whole-job units per second: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / (ms / 1e3)
+
+
 def cpu_threads():
     for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
         if os.environ.get(var):
@@ -443,7 +464,7 @@ def main():
     B = args.batch
     op = pkg.TatOperator(N_IMG, N_DET, N_T, T=T_WIN, support_radius=RSUP, device=dev)
     info = op.info
-    fh = phantom_batch(N_IMG, B, seed0=rank * B).astype(np.float32)
+    fh = phantom_batch(N_IMG, B, seed0=replica_seed0(rank, B)).astype(np.float32)
     f = torch.tensor(fh, device=dev)
     g = torch.empty((B, N_DET, N_T), dtype=torch.float32, device=dev)
     f2 = torch.empty_like(f)
@@ -475,12 +496,8 @@ def main():
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = B * args.steps * world / (ms / 1e3)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    value = job_throughput(B * args.steps, world, ms)
 
     # ---- per-stage timing (same work, events between the five stages of each direction)
     stage_ms = stage_times(pkg, op, B, f, g, f2, ws, stream, max(3, min(args.steps, 10)))
@@ -512,12 +529,8 @@ def main():
         step_e2e()
     e1.record(stream)
     torch.cuda.synchronize()
-    ems = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ems], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ems = float(t.item())
-    e2e = {"value": B * esteps * world / (ems / 1e3), "unit": "pairs/s", "h2d_bytes_per_step": fh.nbytes,
+    ems = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    e2e = {"value": job_throughput(B * esteps, world, ems), "unit": "pairs/s", "h2d_bytes_per_step": fh.nbytes,
            "d2h_bytes_per_step": fh.nbytes, "steps": esteps}
 
     # ---- comparisons on the same batch: the plain per-image path (one A and one A* call per
@@ -641,7 +654,7 @@ def run_inverse(args, rank, world, local):
     B = args.batch
     op = pkg.TatOperator(N_IMG, N_DET, N_T, T=T_WIN, support_radius=RSUP, device=dev)
     info = op.info
-    fh = phantom_batch(N_IMG, B, seed0=rank * B).astype(np.float32)
+    fh = phantom_batch(N_IMG, B, seed0=replica_seed0(rank, B)).astype(np.float32)
     gclean = op.forward(torch.tensor(fh, device=dev)).cpu().numpy()
     gh = np.stack([add_noise(gclean[b], 0.01, 9000 + rank * B + b) for b in range(B)]).astype(np.float32)
     g = torch.tensor(gh, device=dev)
@@ -664,12 +677,7 @@ def run_inverse(args, rank, world, local):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms / reps
+        return max_over_ranks(e0.elapsed_time(e1), world, dev) / reps
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -852,11 +860,8 @@ def run_service(args, rank, world, local):
         lat += [svc.latency(i)[0] for i in ids]
     wall = (time.perf_counter() - t0) / args.steps
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([wall], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        wall = float(t.item())
-    value = SVC_REQ * world / wall
+    wall = max_over_ranks(wall, world, dev)
+    value = job_throughput(SVC_REQ, world, 1e3 * wall)
     st = svc.stats()
 
     # one request at a time through the same runtime (no batching across requests)
@@ -1151,11 +1156,8 @@ def run_lpd(args, rank, world, local):
     ms = timed(lambda: net.train_step(yb, fb, graph=True), args.steps)
     clk = clocks.stop()
     ms_eager = timed(lambda: net.train_step(yb, fb, graph=False), max(3, min(args.steps, 10)))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 1e3 / ms
+    ms = max_over_ranks(ms, world, dev)
+    value = job_throughput(1, world, ms)
 
     # time of the operator calls inside one step: 4K applications of A or A* on the batch
     ws = op.workspace(LPD_B)
@@ -1315,7 +1317,7 @@ def run_solves(args, rank, world, local):
     B = SOLVE_B if args.batch == 32 else args.batch
     op = pkg.TatOperator(SOLVE_N, SOLVE_DET, SOLVE_T, T=T_WIN, support_radius=RSUP, arc_begin=0.0,
                          arc_len=math.pi, device=dev)
-    fh = phantom_batch(SOLVE_N, B, seed0=rank * B).astype(np.float32)
+    fh = phantom_batch(SOLVE_N, B, seed0=replica_seed0(rank, B)).astype(np.float32)
     g_clean = op.forward(torch.tensor(fh, device=dev)).cpu().numpy()
     gh = np.stack([add_noise(g_clean[b], 0.01, 7000 + rank * B + b) for b in range(B)]).astype(np.float32)
     mask = torch.tensor(roi_mask(SOLVE_N, radius=RSUP, upper_half=True), dtype=torch.float32, device=dev)
@@ -1347,13 +1349,9 @@ def run_solves(args, rank, world, local):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    ms = timed(step, args.steps)
+    ms = max_over_ranks(timed(step, args.steps), world, dev)
     clk = clocks.stop()
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = B * world / (ms / 1e3)
+    value = job_throughput(B, world, ms)
 
     # comparisons: eager launches, one image at a time, and the bare A+A* pairs of the same iterations
     ms_eager = timed(lambda: step(graph=False), 2)
