@@ -249,7 +249,8 @@ class LPD:
     def fit(self, f_train, y_train, steps, seed=0, graph=True, log_every=100):
         """Adam on random batches (with replacement, seeded) of the training pairs
         (f_train (N, n, n), y_train (N, n_det, n_t), device tensors); returns
-        [(step, loss)] every `log_every` steps and at the last one."""
+        [(step, loss)] every `log_every` steps and at the last one.  At those points it
+        also reads the convolutions' timeout flag and raises TatError if one was set."""
         gen = torch.Generator().manual_seed(seed)
         curve = []
         for it in range(steps):
@@ -257,4 +258,5 @@ class LPD:
             loss = self.train_step(y_train[idx].contiguous(), f_train[idx].contiguous(), graph=graph)
             if it % log_every == 0 or it == steps - 1:
                 curve.append((it, float(loss.item())))
+                B.tat_lpd_check()  # raises if a convolution gave up waiting for a tile (no results from it)
         return curve
