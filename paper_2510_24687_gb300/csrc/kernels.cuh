@@ -798,9 +798,11 @@ __global__ void TAT_COLS_BOUNDS_I k_cols_inv(DevPlan P, const float2* __restrict
   if (strip == 0 && tid == 0) acc[(size_t)b * accs] = 0.f;
 #pragma unroll 1
   for (int c = c0; c < c1; ++c) {
+    const int qmax = P.inv_qmax[c];  // rows beyond it lie outside the cut-off: zero, no table read
     for (int q = tid; q < N; q += NT) {
       const int qs = q < N / 2 ? q : q - N;
-      buf[xpad<L>(colpos<L>(q))] = cmulc(inv_node(P, Yb, c, qs), __ldg(&P.phase[q]));
+      const float2 v = (qs <= qmax && -qs <= qmax) ? inv_node(P, Yb, c, qs) : make_float2(0.f, 0.f);
+      buf[xpad<L>(colpos<L>(q))] = cmulc(v, __ldg(&P.phase[q]));
     }
     __syncthreads();
     col_fft_inv<L>(buf, P.fN, smtw, tid, NT, nt, P.n, nullptr);

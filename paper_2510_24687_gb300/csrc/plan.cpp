@@ -510,6 +510,7 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
     const int h2 = d.N / 2;
     std::vector<unsigned> jl((size_t)h2 * h2);
     std::vector<float2> ab((size_t)h2 * h2);
+    std::vector<int> qmax(h2, -1);  // u grows with q along a column: the inside rows are q <= qmax
     const double rho = dxi / dlam, acell = n_phi / (2.0 * kPi);
     parallel_for(h2, [&](int c) {
       for (int q = 0; q < h2; ++q) {
@@ -523,6 +524,7 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
           const double jf = std::min(std::floor(u), (double)(d.J - 1));
           j = (unsigned)jf;
           a = std::min(u - jf, 1.0);
+          qmax[c] = q;
         }
         jl[e] = j | ((unsigned)Lf << 16);
         ab[e] = make_float2((float)a, (float)(ph - Lf));
@@ -530,6 +532,7 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
     });
     TAT_TRY(upload(P, jl, &d.inv_jl));
     TAT_TRY(upload(P, ab, &d.inv_ab));
+    TAT_TRY(upload(P, qmax, &d.inv_qmax));
     d.inv_scale = (float)(dxi * dxi / (2.0 * kPi));
     d.inv_ok = n_phi == n_det ? 1 : 0;
   }

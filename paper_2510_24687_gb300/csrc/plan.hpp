@@ -71,6 +71,7 @@ struct DevPlan {
   const unsigned* inv_jl;          // [N/2][N/2] quadrant node (c, q): ring j (low 16 bits, 0xffff: beyond
                                    // the cut-off) and angle cell L = floor(atan2(q, c) n_phi / 2pi) (high)
   const float2* inv_ab;            // [N/2][N/2] (a, b): fractional ring and angle positions
+  const int* inv_qmax;             // [N/2] largest |q| of column c inside the cut-off (-1: none)
   const int2* outrange;            // [n] columns [lo, hi) of each row inside |x| <= R (the disk Omega)
   float inv_scale;                 // dxi^2 / (2 pi)
   float inv_count;                 // nodes of Omega \ Omega0 (0: no constant C)
