@@ -358,7 +358,7 @@ constexpr int TX = 8, TY = 16;             // tile: M = 128 pixels
 constexpr int HX = TX + 2, HY = TY + 2;    // 10 x 18 halo
 constexpr int PLANE = 2944;                // bytes of one 8-channel halo plane (180 x 16 B, rounded up to 128 B)
 constexpr int SLOT = 4 * PLANE;            // one staged halo
-constexpr int NS = 4;                      // halo slots: tiles n+1..n+3 load while tile n computes
+constexpr int NS = 3;                      // halo slots: tiles n+1, n+2 load while tile n computes
 constexpr int HALO_TX = 4 * HX * HY * 16;  // bytes a halo's four copies deliver
 constexpr int WOFF = NS * SLOT;            // weights [tap][plane][co][16 B], 2 KB per tap
 constexpr int BOFF = WOFF + 9 * 2048;      // bias, 32 floats
@@ -416,7 +416,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
 // tiles over through mbarriers only -- halo full / empty per slot, accumulator full / empty
 // per TMEM buffer -- so no CTA-wide barrier sits inside the tile loop.
 template <bool BWD, bool OMASK>
-__global__ void __launch_bounds__(192, 3) k_conv_mid_tc(int B, int H, int W, const __grid_constant__ CUtensorMap map8,
+__global__ void __launch_bounds__(192, 4) k_conv_mid_tc(int B, int H, int W, const __grid_constant__ CUtensorMap map8,
                                                         const tat_bf16* __restrict__ w, const float* __restrict__ bias,
                                                         const tat_bf16* __restrict__ omask,
                                                         tat_bf16* __restrict__ out) {
@@ -1313,7 +1313,7 @@ tat_status launch_mid_tc(int batch, int H, int W, const CUtensorMap& m8, const t
   constexpr size_t smem = tc::SMEM;
   if (!smem_attr<k_conv_mid_tc<BWD, OMASK>>(smem)) return TAT_ERR_CUDA;
   const long long tiles = (long long)batch * ((H + tc::TY - 1) / tc::TY) * ((W + tc::TX - 1) / tc::TX);
-  const int ctas = (int)(tiles < 3 * 152 ? tiles : 3 * 152);  // 3 resident per SM: 3 x 64 TMEM columns
+  const int ctas = (int)(tiles < 4 * 152 ? tiles : 4 * 152);  // 4 resident per SM: 4 x 64 TMEM columns
   k_conv_mid_tc<BWD, OMASK><<<ctas, 192, smem, s>>>(batch, H, W, m8, w, b, omask, out);
   return launched(what);
 }
