@@ -47,7 +47,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-compare", action="store_true", help="pair workload: skip the per-image and cuFFT comparisons")
     p.add_argument("--no-autotune", action="store_true",
-                   help="pair workload: keep the plan's default launch shapes instead of tat_plan_autotune's")
+                   help="keep the plans' default launch shapes instead of tat_plan_autotune's")
     p.add_argument("--size", type=int, default=512,
                    help="pair workload: image size n (n_det = n_t = 2n); 512 is the headline, 256 the batched config")
     p.add_argument("--train-steps", type=int, default=1500, help="lpd workload: training steps before evaluation")
@@ -661,6 +661,7 @@ def run_inverse(args, rank, world, local):
     B = args.batch
     op = pkg.TatOperator(N_IMG, N_DET, N_T, T=T_WIN, support_radius=RSUP, device=dev)
     info = op.info
+    tuned = None if args.no_autotune else op.autotune(B)  # the column strips and row pairs A^-1 shares
     fh = phantom_batch(N_IMG, B, seed0=replica_seed0(rank, B)).astype(np.float32)
     gclean = op.forward(torch.tensor(fh, device=dev)).cpu().numpy()
     gh = np.stack([add_noise(gclean[b], 0.01, 9000 + rank * B + b) for b in range(B)]).astype(np.float32)
@@ -846,7 +847,7 @@ def run_service(args, rank, world, local):
     xs = [torch.tensor(ellipse_phantom(n, 100 * rank + i).astype(np.float32), device=dev) for i, n in enumerate(sizes)]
     outs = [torch.empty((n, n), device=dev) for n in sizes]
     descs = {n: pkg.TatService.desc(n, 2 * n, 2 * n, T=T_WIN, support_radius=RSUP) for n in SVC_SIZES}
-    svc = pkg.TatService(memory_budget=8 << 30, max_batch=32, use_graphs=True)
+    svc = pkg.TatService(memory_budget=8 << 30, max_batch=32, use_graphs=True, autotune=not args.no_autotune)
 
     def round_():
         ids = [svc.submit(descs[n], "pair", x, o) for n, x, o in zip(sizes, xs, outs)]
@@ -1324,6 +1325,7 @@ def run_solves(args, rank, world, local):
     B = SOLVE_B if args.batch == 32 else args.batch
     op = pkg.TatOperator(SOLVE_N, SOLVE_DET, SOLVE_T, T=T_WIN, support_radius=RSUP, arc_begin=0.0,
                          arc_len=math.pi, device=dev)
+    tuned = None if args.no_autotune else op.autotune(B)
     fh = phantom_batch(SOLVE_N, B, seed0=replica_seed0(rank, B)).astype(np.float32)
     g_clean = op.forward(torch.tensor(fh, device=dev)).cpu().numpy()
     gh = np.stack([add_noise(g_clean[b], 0.01, 7000 + rank * B + b) for b in range(B)]).astype(np.float32)
