@@ -21,9 +21,12 @@
  *    for every later launch of that shape;
  *  - an autotuner for the launch shapes that the kernels take at run time.
  *
- * Pointers passed to tat_service_submit are DEVICE pointers owned by the
- * caller; they must stay valid, and the output must not be read, until the
- * request has completed (tat_service_synchronize).  Inputs are copied into the
+ * Pointers passed to tat_service_submit are owned by the caller: device
+ * pointers, or page-locked host pointers (cudaHostAlloc / cudaHostRegister;
+ * the staging copies run with cudaMemcpyDefault), in which case a request's
+ * upload, operator and download all run on its slot's stream.  They must stay
+ * valid, and the output must not be read, until the request has completed
+ * (tat_service_synchronize).  Inputs are copied into the
  * slot on the slot's stream after tat_service_flush, so the caller must not
  * modify them before then either.  A service is used from one host thread;
  * completion times are recorded from CUDA host callbacks.

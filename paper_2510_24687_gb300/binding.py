@@ -560,7 +560,8 @@ class TatService:
 
     ``submit(desc_kw, op, x, out)`` queues op(x) -> out for the problem described by
     ``desc_kw`` (n, n_det, n_t and optional tat_plan_desc fields); x and out are
-    contiguous float32 CUDA tensors that must stay alive until ``synchronize``.
+    contiguous float32 CUDA tensors, or pinned host tensors (then the service uploads and
+    downloads them on the request's slot stream); both must stay alive until ``synchronize``.
     """
 
     OPS = {"forward": TAT_OP_FORWARD, "adjoint": TAT_OP_ADJOINT, "inverse": TAT_OP_INVERSE, "pair": TAT_OP_PAIR}
@@ -585,8 +586,8 @@ class TatService:
 
     def submit(self, desc, op, x, out):
         for t in (x, out):
-            if not (t.is_cuda and t.is_contiguous() and t.dtype.itemsize == 4):
-                raise ValueError("x and out must be contiguous float32 CUDA tensors")
+            if not ((t.is_cuda or t.is_pinned()) and t.is_contiguous() and t.dtype.itemsize == 4):
+                raise ValueError("x and out must be contiguous float32 CUDA or pinned host tensors")
         self._keep.append((x, out))
         return tat_service_submit(self.handle, desc, self.OPS[op], x.data_ptr(), out.data_ptr())
 

@@ -228,7 +228,7 @@ tat_status run_chunk(tat_service_s* S, Slot& s, const std::vector<long long>& id
   for (int i = 0; i < b; ++i) {
     const Request& r = S->requests[(size_t)ids[i]];
     tat_status e = cuda_ok(cudaMemcpyAsync(s.in + (size_t)i * s.in_elems, r.in, s.in_elems * sizeof(float),
-                                           cudaMemcpyDeviceToDevice, s.stream),
+                                           cudaMemcpyDefault, s.stream),
                            "staging copy");
     if (e != TAT_OK) return e;
   }
@@ -260,7 +260,7 @@ tat_status run_chunk(tat_service_s* S, Slot& s, const std::vector<long long>& id
   for (int i = 0; i < b; ++i) {
     const Request& r = S->requests[(size_t)ids[i]];
     tat_status e = cuda_ok(cudaMemcpyAsync(r.out, s.out + (size_t)i * s.out_elems, s.out_elems * sizeof(float),
-                                           cudaMemcpyDeviceToDevice, s.stream),
+                                           cudaMemcpyDefault, s.stream),
                            "result copy");
     if (e != TAT_OK) return e;
   }

@@ -79,6 +79,29 @@ def test_service_matches_direct_calls_and_reuses_graphs(pkg, torch):
     svc.close()
 
 
+def test_pinned_host_buffers(pkg, torch):
+    """Requests with page-locked host inputs and outputs: the service uploads, runs and
+    downloads them on the slot streams, with the results of the device-pointer path."""
+    reqs = _requests(torch)
+    svc = pkg.TatService(memory_budget=2 << 30, max_batch=4)
+    hreqs = []
+    for n, nd, nt, op, x, out in reqs:
+        hx = x.cpu().pin_memory()
+        hout = torch.empty(out.shape, dtype=torch.float32).pin_memory()
+        hreqs.append((n, nd, nt, op, hx, hout))
+    ids_h = [svc.submit(svc.desc(n, nd, nt, support_radius=0.9), op, hx, ho) for n, nd, nt, op, hx, ho in hreqs]
+    ids_d = [svc.submit(svc.desc(n, nd, nt, support_radius=0.9), op, x, out) for n, nd, nt, op, x, out in reqs]
+    svc.flush()
+    svc.synchronize()
+    for (n, nd, nt, op, hx, ho), (_, _, _, _, x, out), ih in zip(hreqs, reqs, ids_h):
+        assert svc.latency(ih)[1] == 0
+        if op == "forward":
+            assert torch.equal(ho, out.cpu())
+        else:
+            assert rel(ho.numpy(), out.cpu().numpy()) <= 1e-6
+    svc.close()
+
+
 def test_admission_evicts_and_shrinks_batches(pkg, torch):
     """A budget that holds one (n = 128, batch 2) slot at a time: slots are evicted between sizes and
     the batch cap is halved; results stay exact."""
