@@ -56,7 +56,11 @@ def dev32(torch, x):
     return torch.as_tensor(np.asarray(x, np.float32)).cuda().contiguous()
 
 
-B_, H_, W_ = 2, 20, 36     # not multiples of the 8 x 16 tiles
+# (2, 20, 36): not multiples of the tiles, one tile per CTA; (2, 200, 264): also ragged, ~850
+# tiles against 456-608 persistent CTAs, so CTAs run several tiles through their TMA slots,
+# mbarrier phases and TMEM accumulators
+LAYER_SIZES = [(2, 20, 36), (2, 200, 264)]
+LAYER_IDS = ["ragged", "multi-tile"]
 
 
 def _stream(torch):
@@ -64,7 +68,9 @@ def _stream(torch):
 
 
 @pytest.mark.parametrize("cin", [2, 3])
-def test_conv_in_forward_backward(pkg, torch, cin):
+@pytest.mark.parametrize("size", LAYER_SIZES, ids=LAYER_IDS)
+def test_conv_in_forward_backward(pkg, torch, cin, size):
+    B_, H_, W_ = size
     import torch.nn.functional as F
     xs = [uniform(10 + c, B_ * H_ * W_).reshape(B_, H_, W_) - 0.3 for c in range(cin)]
     w = 0.3 * gaussian(20, 9 * cin * 32)
@@ -123,7 +129,9 @@ def test_conv_in_forward_backward(pkg, torch, cin):
     pkg.tat_lpd_check()
 
 
-def test_conv_mid_forward_backward(pkg, torch):
+@pytest.mark.parametrize("size", LAYER_SIZES, ids=LAYER_IDS)
+def test_conv_mid_forward_backward(pkg, torch, size):
+    B_, H_, W_ = size
     import torch.nn.functional as F
     hin = np.maximum(gaussian(40, B_ * H_ * W_ * 32), 0).reshape(B_, H_, W_, 32)
     w = 0.08 * gaussian(41, 9 * 32 * 32)
@@ -174,7 +182,9 @@ def test_conv_mid_forward_backward(pkg, torch):
     pkg.tat_lpd_check()     # no TMA tile wait gave up
 
 
-def test_conv_out_forward_backward(pkg, torch):
+@pytest.mark.parametrize("size", LAYER_SIZES, ids=LAYER_IDS)
+def test_conv_out_forward_backward(pkg, torch, size):
+    B_, H_, W_ = size
     import torch.nn.functional as F
     hin = np.maximum(gaussian(50, B_ * H_ * W_ * 32), 0).reshape(B_, H_, W_, 32)
     w = 0.1 * gaussian(51, 9 * 32)
