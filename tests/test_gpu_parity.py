@@ -161,9 +161,11 @@ def test_invalid_arguments(pkg, torch):
 
 
 def test_n256_batch32_sampled(pkg, torch):
-    """Batched workload n=256, 512 detectors x 512 samples, B=32: images 0 and 31 against the oracle."""
+    """Batched workload n=256, 512 detectors x 512 samples, B=32 with the launch shapes the
+    autotuner picks (as the benchmark runs it): images 0 and 31 against the oracle."""
     op, P = make(pkg, torch, dict(n=256, n_det=512, n_t=512, support_radius=0.9))
     B = 32
+    op.autotune(B)
     fs = np.stack([f32(ellipse_phantom(256, s)) for s in range(B)])
     g = op.forward(torch.tensor(fs, dtype=torch.float32, device="cuda:0")).cpu().numpy()
     for s in (0, B - 1):
@@ -179,13 +181,19 @@ def test_n256_batch32_sampled(pkg, torch):
 
 
 def test_headline_n512_full(pkg, torch):
-    """n=512, 1024 detectors x 1024 samples, in the batched launch the benchmark times (B=4 here)."""
+    """n=512, 1024 detectors x 1024 samples, in the launch the benchmark times: B=32 with the
+    autotuned launch shapes; images 0 and 31 of A and two images of A* against the oracle."""
     op, P = make(pkg, torch, dict(n=512, n_det=1024, n_t=1024, support_radius=0.9))
-    B = 4
+    B = 32
+    op.autotune(B)
     fs = np.stack([f32(ellipse_phantom(512, s)) for s in range(B)])
     g = op.forward(torch.tensor(fs, dtype=torch.float32, device="cuda:0")).cpu().numpy()
-    assert rel(g[2], O.forward(P, fs[2])) <= TOL
-    gin = f32(random_sinogram(1024, 1024, 5))
-    gi = torch.tensor(np.stack([gin] * B), dtype=torch.float32, device="cuda:0")
+    for s in (0, B - 1):
+        assert rel(g[s], O.forward(P, fs[s])) <= TOL
+    gins = [f32(random_sinogram(1024, 1024, 5 + s)) for s in (0, 1)]
+    gi = torch.zeros((B, 1024, 1024), dtype=torch.float32, device="cuda:0")
+    gi[1] = torch.tensor(gins[0], device="cuda:0")
+    gi[B - 2] = torch.tensor(gins[1], device="cuda:0")
     fa = op.adjoint(gi).cpu().numpy()
-    assert rel(fa[1], O.adjoint(P, gin)) <= TOL
+    assert rel(fa[1], O.adjoint(P, gins[0])) <= TOL
+    assert rel(fa[B - 2], O.adjoint(P, gins[1])) <= TOL
