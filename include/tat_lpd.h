@@ -103,6 +103,11 @@ tat_status tat_conv_out_bwd(int batch, int H, int W, const float* g_out, const t
  * Synchronises with the device. */
 tat_status tat_lpd_check(void);
 
+/* Test of the give-up path: one thread waits, at most `tries` (1 .. 2^20) times, on an
+ * mbarrier that nothing arrives on, then sets the flag tat_lpd_check reports and writes 1 to
+ * *gave_up (a DEVICE int).  The context stays usable.  Asynchronous on `stream`. */
+tat_status tat_lpd_timeout_probe(int tries, int* gave_up, tat_stream_t stream);
+
 /* Adam step (bias-corrected, step >= 1) on FP32 parameters; w_bf16 (optional)
  * receives the updated parameters rounded to BF16. */
 tat_status tat_adam(long long count, float lr, float beta1, float beta2, float eps, int step, float* param,

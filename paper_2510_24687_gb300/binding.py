@@ -126,6 +126,7 @@ def load() -> ctypes.CDLL:
         "tat_to_bf16": (_I, [_LL, _P, _P, _P]),
         "tat_fill": (_I, [_LL, _F, _P, _P]),
         "tat_lpd_check": (_I, []),
+        "tat_lpd_timeout_probe": (_I, [_I, _P, _P]),
         "tat_mse": (_I, [_LL, _P, _P, _F, _P, _P, _P]),
         "tat_axpby_clamp": (_I, [_LL, _F, _P, _F, _P, _F, _P, _LL, _P, _P]),
         "tat_axpby_clamp_backward": (_I, [_LL, _P, _F, _P, _LL, _P, _F, _P, _F, _P, _P]),
@@ -404,6 +405,10 @@ def tat_conv_out_bwd(batch, H, W, g_out, h, w, mask_relu, g_h, scratch, scratch_
 def tat_adam(count, lr, beta1, beta2, eps, step, param, grad, m, v, w_bf16, stream=0):
     _check(load().tat_adam(count, lr, beta1, beta2, eps, step, param, grad, m, v, w_bf16 or None, stream or None),
            "tat_adam")
+
+
+def tat_lpd_timeout_probe(tries, gave_up_ptr, stream=0):
+    _check(load().tat_lpd_timeout_probe(tries, gave_up_ptr, stream or None), "tat_lpd_timeout_probe")
 
 
 def tat_lpd_check():

@@ -214,6 +214,19 @@ __device__ __forceinline__ bool tile_loop(int B, int H, int W, uint64_t* bar, un
   return true;
 }
 
+// One thread waits, bounded by `tries`, on an mbarrier that nothing arrives on: the wait
+// gives up, records the timeout in the flag tat_lpd_check reads, and returns.  It exercises
+// the give-up path of the convolutions' waits without a stuck copy.
+__global__ void k_wait_probe(int tries, int* gave_up) {
+  __shared__ uint64_t bar;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  bool ok = false;
+  for (int i = 0; i < tries && !ok; ++i) ok = mbar_try_wait(&bar, 0u);
+  if (!ok) atomicExch(&g_lpd_timeout, 1);
+  *gave_up = ok ? 0 : 1;
+}
+
 __device__ __forceinline__ void init_bars(uint64_t* bar) {
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
@@ -1459,6 +1472,12 @@ tat_status tat_conv_mid_bwd_data(int batch, int H, int W, const tat_bf16* g_out,
   }
   if (h_in) return launch_mid_tc<true, true>(batch, H, W, m8, w, nullptr, h_in, g_in, s, what);
   return launch_mid_tc<true, false>(batch, H, W, m8, w, nullptr, nullptr, g_in, s, what);
+}
+
+tat_status tat_lpd_timeout_probe(int tries, int* gave_up, tat_stream_t stream) {
+  if (tries < 1 || tries > (1 << 20) || !gave_up) return TAT_ERR_INVALID_ARG;
+  k_wait_probe<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(tries, gave_up);
+  return launched("tat_lpd_timeout_probe");
 }
 
 tat_status tat_lpd_check(void) {

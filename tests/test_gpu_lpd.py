@@ -300,3 +300,33 @@ def test_trained_lpd_beats_tv_on_limited_view(pkg, torch):
     e_tv = err(solver.tv(y_te, a_best, 100, sigma, tau, s).clone(), f_te)
     print(f"limited view, n=64: LPD {e_lpd:.4f}  TV-LS {e_tv:.4f} (alpha {a_best})")
     assert e_lpd < e_tv
+
+
+def test_bounded_wait_gives_up_and_reports(pkg, torch):
+    """A wait on an mbarrier that nothing arrives on runs out after its try count, sets the
+    flag tat_lpd_check reports as TAT_ERR_TIMEOUT (once: the check clears it), and leaves the
+    context usable: a convolution afterwards runs and matches the one before."""
+    dev = torch.device("cuda:0")
+    pkg.tat_lpd_check()                                   # start from a clear flag
+    B_, H_, W_ = 1, 20, 36
+    h = torch.from_numpy(np.abs(gaussian(60, B_ * H_ * W_ * 32)).astype(np.float32)).to(dev)
+    hb = torch.empty(h.numel(), dtype=torch.int16, device=dev)
+    pkg.tat_to_bf16(h.numel(), h.data_ptr(), hb.data_ptr())
+    w = torch.from_numpy((0.05 * gaussian(61, 9 * 32 * 32)).astype(np.float32)).to(dev)
+    wb = torch.empty(w.numel(), dtype=torch.int16, device=dev)
+    pkg.tat_to_bf16(w.numel(), w.data_ptr(), wb.data_ptr())
+    b = torch.zeros(32, dtype=torch.float32, device=dev)
+    out0, out1 = torch.empty_like(hb), torch.empty_like(hb)
+    pkg.tat_conv_mid_fwd(B_, H_, W_, hb.data_ptr(), wb.data_ptr(), b.data_ptr(), out0.data_ptr())
+    gave_up = torch.zeros(1, dtype=torch.int32, device=dev)
+    pkg.tat_lpd_timeout_probe(256, gave_up.data_ptr())
+    torch.cuda.synchronize()
+    assert int(gave_up.item()) == 1
+    with pytest.raises(pkg.TatError) as err:
+        pkg.tat_lpd_check()
+    assert err.value.status == 5                          # TAT_ERR_TIMEOUT
+    pkg.tat_lpd_check()                                   # cleared by the report
+    pkg.tat_conv_mid_fwd(B_, H_, W_, hb.data_ptr(), wb.data_ptr(), b.data_ptr(), out1.data_ptr())
+    torch.cuda.synchronize()
+    assert torch.equal(out0, out1)
+    pkg.tat_lpd_check()
