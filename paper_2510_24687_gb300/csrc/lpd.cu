@@ -136,6 +136,29 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// Shared-memory tile at `src` to the 4-D box of `map` at (c0, c1, c2, c3) (all >= 0; parts
+// outside the tensor are not written), as one bulk group of the calling thread.
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0, int c1, int c2, int c3) {
+  asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];\n" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+
+// Named barrier 2 over the 128 epilogue threads of the tcgen05 kernel; the _all form also
+// returns whether `v` holds in every one of them.
+__device__ __forceinline__ void epilogue_sync() { asm volatile("bar.sync 2, 128;\n" ::: "memory"); }
+__device__ __forceinline__ bool epilogue_all(bool v) {
+  unsigned r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 2, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((unsigned)v)
+      : "memory");
+  return r != 0;
+}
+
 // g * [h > 0] for the two BF16 values of a word (h > 0: sign clear and not zero).
 __device__ __forceinline__ unsigned relu_masked(unsigned g, unsigned h) {
   const unsigned lo = h & 0xffffu, hi = h >> 16;
@@ -314,6 +337,33 @@ constexpr size_t mid_smem_bytes() {
   return 1024 + 2 * NT * HALO_SLOT + 9 * C * CP * 2 + 2 * sizeof(uint64_t);
 }
 
+// BF16 element k (0..7) of a 16-byte word.
+__device__ __forceinline__ tat_bf16 bf16_of(const uint4& v, int k) {
+  const unsigned word = k < 2 ? v.x : k < 4 ? v.y : k < 6 ? v.z : v.w;
+  return (tat_bf16)((k & 1) ? word >> 16 : word & 0xffffu);
+}
+
+// Stages the 32 -> 32 weights w[tap][co][ci] (16-byte aligned) in shared memory with 16-byte
+// loads, all of a thread's loads in flight before its first store.  Word u of w holds the
+// input channels ci = 8 (u mod 4) .. + 7 of (tap, co) = (u / 128, (u / 4) mod 32); `place`
+// stores it.  Threads t = 0 .. NTHR - 1 of the calling group take part.
+template <int NTHR, class Place>
+__device__ __forceinline__ void stage_mid_weights(const tat_bf16* __restrict__ w, int t, Place place) {
+  constexpr int NV = 9 * C * C / 8, PER = (NV + NTHR - 1) / NTHR;
+  const uint4* w4 = reinterpret_cast<const uint4*>(w);
+  uint4 v[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int u = t + NTHR * i;
+    if (u < NV) v[i] = __ldg(w4 + u);
+  }
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int u = t + NTHR * i;
+    if (u < NV) place(u >> 7, (u >> 2) & 31, u & 3, v[i]);
+  }
+}
+
 template <bool BWD, bool MASK, bool OMASK>
 __global__ void __launch_bounds__(256) k_conv_mid(int B, int H, int W, const __grid_constant__ CUtensorMap map_in,
                                                   const __grid_constant__ CUtensorMap map_mask,
@@ -327,13 +377,15 @@ __global__ void __launch_bounds__(256) k_conv_mid(int B, int H, int W, const __g
   constexpr int STAGE = NT * HALO_SLOT;
   tat_bf16* wsm = reinterpret_cast<tat_bf16*>(sm + 2 * STAGE);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * STAGE + 9 * C * CP * 2);
-  // weights, read in global order (coalesced): wsm[tap][n][k] with n the output
-  // channel of this GEMM and k its input channel
-  for (int e = threadIdx.x; e < 9 * C * C; e += blockDim.x) {
-    const int tap = e / (C * C), r = e % (C * C), co = r / C, ci = r % C;
-    if (BWD) wsm[((8 - tap) * C + ci) * CP + co] = w[e];
-    else wsm[(tap * C + co) * CP + ci] = w[e];
-  }
+  // weights: wsm[tap][n][k] with n the output channel of this GEMM and k its input channel
+  stage_mid_weights<256>(w, threadIdx.x, [&](int tap, int co, int j, const uint4& v) {
+    if (BWD) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) wsm[((8 - tap) * C + 8 * j + k) * CP + co] = bf16_of(v, k);
+    } else {
+      reinterpret_cast<uint4*>(wsm)[(tap * C + co) * (CP / 8) + j] = v;
+    }
+  });
   init_bars(bar);
   __syncthreads();
   tile_loop(
@@ -361,8 +413,10 @@ __global__ void __launch_bounds__(256) k_conv_mid(int B, int H, int W, const __g
 // by the tap's offset: core-matrix rows 16 B apart (consecutive pixels), core-matrix groups
 // 160 B apart (one halo row of 10 pixels), K halves one plane apart.  The accumulator of a
 // tile is 32 TMEM columns; two of them alternate, so the epilogue of tile i-1 (tcgen05.ld,
-// bias, ReLU, BF16, 64 contiguous bytes per pixel) overlaps the MMAs of tile i, and four halo
-// slots rotate, so the halos of tiles i+1..i+3 load meanwhile.  tcgen05.commit signals on an
+// bias, ReLU, BF16 into a shared-memory tile that one bulk tensor store writes out) overlaps
+// the MMAs of tile i, and two halo slots alternate, so the halo of tile i+1 loads meanwhile.
+// The weights are staged by the MMA and epilogue warps while the first halos load.
+// tcgen05.commit signals on an
 // mbarrier when a tile's MMAs have finished reading their halo slot and writing their
 // accumulator.  Every wait is bounded; on a timeout the CTA records it, waits (bounded) for
 // its copies and MMAs in flight, frees its TMEM and returns.
@@ -371,13 +425,15 @@ constexpr int TX = 8, TY = 16;             // tile: M = 128 pixels
 constexpr int HX = TX + 2, HY = TY + 2;    // 10 x 18 halo
 constexpr int PLANE = 2944;                // bytes of one 8-channel halo plane (180 x 16 B, rounded up to 128 B)
 constexpr int SLOT = 4 * PLANE;            // one staged halo
-constexpr int NS = 3;                      // halo slots: tiles n+1, n+2 load while tile n computes
+constexpr int NS = 2;                      // halo slots: tile n+1 loads while tile n computes
 constexpr int HALO_TX = 4 * HX * HY * 16;  // bytes a halo's four copies deliver
 constexpr int WOFF = NS * SLOT;            // weights [tap][plane][co][16 B], 2 KB per tap
 constexpr int BOFF = WOFF + 9 * 2048;      // bias, 32 floats
-constexpr int MOFF = BOFF + 128;           // mbarriers: halo full[NS], empty[NS], accumulator full[2],
+constexpr int OOFF = BOFF + 128;           // output tile [16][8][32] BF16 for the bulk store, 8 KB
+constexpr int MOFF = OOFF + TX * TY * 64;  // mbarriers: halo full[NS], empty[NS], accumulator full[2],
                                            // empty[2]; then the TMEM address
-constexpr int SMEM = 1024 + MOFF + 128;     // alignment slack + what the layout above uses
+constexpr int SMEM = 128 + MOFF + 128;     // alignment slack (128 B for the TMA tiles) + the layout above
+                                           // (49.4 KB: 4 CTAs per SM)
 constexpr int TMEM_COLS = 64;              // two accumulators of 32 FP32 columns
 // Instruction descriptor (kind::f16): FP32 D, BF16 A and B, both K-major, N = 32, M = 128.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
@@ -430,30 +486,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
 // per TMEM buffer -- so no CTA-wide barrier sits inside the tile loop.
 template <bool BWD, bool OMASK>
 __global__ void __launch_bounds__(192, 4) k_conv_mid_tc(int B, int H, int W, const __grid_constant__ CUtensorMap map8,
+                                                        const __grid_constant__ CUtensorMap map_out,
                                                         const tat_bf16* __restrict__ w, const float* __restrict__ bias,
-                                                        const tat_bf16* __restrict__ omask,
-                                                        tat_bf16* __restrict__ out) {
+                                                        const tat_bf16* __restrict__ omask) {
   constexpr int TX = tc::TX, TY = tc::TY, HX = tc::HX, PLANE = tc::PLANE, SLOT = tc::SLOT, WOFF = tc::WOFF;
   constexpr int BOFF = tc::BOFF, MOFF = tc::MOFF, HALO_TX = tc::HALO_TX, TMEM_COLS = tc::TMEM_COLS, NS = tc::NS;
   constexpr uint32_t IDESC = tc::IDESC;
   extern __shared__ unsigned char dsm[];
-  unsigned char* sm = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
+  unsigned char* sm = dsm + ((128u - (smem_u32(dsm) & 127u)) & 127u);
   tat_bf16* wsm = reinterpret_cast<tat_bf16*>(sm + WOFF);
   float* bsm = reinterpret_cast<float*>(sm + BOFF);
+  uint4* osm = reinterpret_cast<uint4*>(sm + tc::OOFF);     // [pixel][4 x 16 B]
   uint64_t* hfull = reinterpret_cast<uint64_t*>(sm + MOFF);  // [NS] halo landed
   uint64_t* hempty = hfull + NS;                              // [NS] halo consumed by the MMAs
   uint64_t* afull = hempty + NS;                              // [2] accumulator written
   uint64_t* aempty = afull + 2;                               // [2] accumulator read by the epilogue
   uint32_t* tslot = reinterpret_cast<uint32_t*>(aempty + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // weights w[tap][co][ci] -> B[tap][k / 8][n][k % 8] with n the output channel of this
-  // GEMM and k its input channel (BWD: n = ci, k = co, tap mirrored)
-  for (int e = tid; e < 9 * C * C; e += blockDim.x) {
-    const int tap = e >> 10, co = (e >> 5) & 31, ci = e & 31;
-    if (BWD) wsm[(8 - tap) * 1024 + (co >> 3) * 256 + ci * 8 + (co & 7)] = w[e];
-    else wsm[tap * 1024 + (ci >> 3) * 256 + co * 8 + (ci & 7)] = w[e];
-  }
-  if (!BWD && tid < C) bsm[tid] = bias[tid];
   if (tid == 0) {
     for (int k = 0; k < NS; ++k) {
       mbar_init(&hfull[k], 1);
@@ -471,11 +520,27 @@ __global__ void __launch_bounds__(192, 4) k_conv_mid_tc(int B, int H, int W, con
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // weights: generic writes, read by the MMAs
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = *tslot;
+  if (warp != 0) {
+    // Warps 1-5 stage the weights w[tap][co][ci] -> B[tap][k / 8][n][k % 8] (n the output
+    // channel of this GEMM, k its input channel; BWD: n = ci, k = co, tap mirrored) and the
+    // bias while warp 0 already loads the first halos; a named barrier among the 160 threads
+    // orders the stores (made visible to the MMAs' async proxy) before the first MMA.
+    stage_mid_weights<160>(w, tid - 32, [&](int tap, int co, int j, const uint4& v) {
+      if (BWD) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) wsm[(8 - tap) * 1024 + (co >> 3) * 256 + (8 * j + k) * 8 + (co & 7)] = bf16_of(v, k);
+      } else {
+        reinterpret_cast<uint4*>(wsm)[tap * 128 + j * 32 + co] = v;
+      }
+    });
+    if (!BWD && tid - 32 < C) bsm[tid - 32] = bias[tid - 32];
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("bar.sync 1, 160;\n" ::: "memory");
+  }
   const uint32_t sbase = smem_u32(sm);
   const int tilesx = (W + TX - 1) / TX, tilesy = (H + TY - 1) / TY;
   const long long ntiles = (long long)B * tilesx * tilesy;
@@ -538,13 +603,11 @@ __global__ void __launch_bounds__(192, 4) k_conv_mid_tc(int B, int H, int W, con
   } else {  // epilogue: 128 threads, thread m of the tile = TMEM lane m = pixel (m / 8, m % 8)
     const int quarter = warp & 3;
     const int m = 32 * quarter + lane;
-    for (int n = 0; n < mine && ok; ++n) {
+    for (int n = 0; n < mine; ++n) {
       const int a = n & 1;
       ok = mbar_wait(&afull[a], (unsigned)((n >> 1) & 1));
-      if (__any_sync(0xffffffffu, !ok)) {  // keep the warp together for the warp-wide TMEM load
-        ok = false;
-        break;
-      }
+      ok = epilogue_all(ok);  // one decision for the four warps, which meet at named barriers below
+      if (!ok) break;
       tc_fence_after();
       uint32_t r[32];
       tmem_ld32(tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(a * 32), r);
@@ -552,34 +615,49 @@ __global__ void __launch_bounds__(192, 4) k_conv_mid_tc(int B, int H, int W, con
       mbar_arrive(&aempty[a]);
       int b, y0, x0;
       coords(n, b, y0, x0);
-      const int y = y0 + (m >> 3), x = x0 + (m & 7);
-      if (y < H && x < W) {
-        const long long pix = ((long long)b * H + y) * W + x;
-        uint4* dst = reinterpret_cast<uint4*>(out + pix * C);
+      uint4 pk[4];  // channels 8q .. 8q+7 of this pixel, BF16
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          unsigned pk[4];
+      for (int q = 0; q < 4; ++q) {
+        unsigned wd[4];
 #pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {
-            const int c0 = 8 * q + 2 * kk;
-            float v0 = __uint_as_float(r[c0]), v1 = __uint_as_float(r[c0 + 1]);
-            if (!BWD) {
-              v0 = fmaxf(v0 + bsm[c0], 0.f);
-              v1 = fmaxf(v1 + bsm[c0 + 1], 0.f);
-            }
-            pk[kk] = (unsigned)tobf(v0) | ((unsigned)tobf(v1) << 16);
+        for (int kk = 0; kk < 4; ++kk) {
+          const int c0 = 8 * q + 2 * kk;
+          float v0 = __uint_as_float(r[c0]), v1 = __uint_as_float(r[c0 + 1]);
+          if (!BWD) {
+            v0 = fmaxf(v0 + bsm[c0], 0.f);
+            v1 = fmaxf(v1 + bsm[c0 + 1], 0.f);
           }
-          if (OMASK) {
-            const uint4 mk = reinterpret_cast<const uint4*>(omask + pix * C)[q];
-            pk[0] = relu_masked(pk[0], mk.x);
-            pk[1] = relu_masked(pk[1], mk.y);
-            pk[2] = relu_masked(pk[2], mk.z);
-            pk[3] = relu_masked(pk[3], mk.w);
+          wd[kk] = (unsigned)tobf(v0) | ((unsigned)tobf(v1) << 16);
+        }
+        pk[q] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+      }
+      if (OMASK) {
+        const int y = y0 + (m >> 3), x = x0 + (m & 7);
+        if (y < H && x < W) {
+          const uint4* mk4 = reinterpret_cast<const uint4*>(omask + (((long long)b * H + y) * W + x) * C);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint4 mk = mk4[q];
+            pk[q] = make_uint4(relu_masked(pk[q].x, mk.x), relu_masked(pk[q].y, mk.y), relu_masked(pk[q].z, mk.z),
+                               relu_masked(pk[q].w, mk.w));
           }
-          dst[q] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
       }
+      // the previous tile's bulk store has finished reading the staging tile
+      if (m == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+      epilogue_sync();
+      // chunk (q + m / 2) mod 4 in step q: the 8 lanes of a 128-byte wavefront write 8
+      // different bank groups
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c = (q + (m >> 1)) & 3;
+        osm[4 * m + c] = c == 0 ? pk[0] : c == 1 ? pk[1] : c == 2 ? pk[2] : pk[3];
+      }
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic writes, read by the bulk store
+      epilogue_sync();
+      if (m == 0) tma_store_4d(&map_out, osm, 0, x0, y0, b);  // pixels outside the image are clipped
     }
+    if (m == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
   }
   if (!ok) atomicExch(&g_lpd_timeout, 1);
   tc_fence_before();
@@ -1320,14 +1398,33 @@ bool halo8_map(CUtensorMap* m, const tat_bf16* base, int batch, int H, int W) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor map of the tcgen05 kernel's output: one 16 x 8-pixel tile of 32 channels per box
+// (the shared-memory staging tile [y][x][32], no swizzle).
+bool tile_out_map(CUtensorMap* m, tat_bf16* base, int batch, int H, int W) {
+  const EncodeTiled fn = encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)batch};
+  const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+  const cuuint32_t box[4] = {(cuuint32_t)C, (cuuint32_t)tc::TX, (cuuint32_t)tc::TY, 1};
+  const cuuint32_t estride[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, base, dims, strides, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <bool BWD, bool OMASK>
 tat_status launch_mid_tc(int batch, int H, int W, const CUtensorMap& m8, const tat_bf16* w, const float* b,
                          const tat_bf16* omask, tat_bf16* out, cudaStream_t s, const char* what) {
   constexpr size_t smem = tc::SMEM;
   if (!smem_attr<k_conv_mid_tc<BWD, OMASK>>(smem)) return TAT_ERR_CUDA;
+  CUtensorMap mo;
+  if (!tile_out_map(&mo, out, batch, H, W)) {
+    fprintf(stderr, "%s: tensor map encoding failed\n", what);
+    return TAT_ERR_CUDA;
+  }
   const long long tiles = (long long)batch * ((H + tc::TY - 1) / tc::TY) * ((W + tc::TX - 1) / tc::TX);
   const int ctas = (int)(tiles < 4 * 152 ? tiles : 4 * 152);  // 4 resident per SM: 4 x 64 TMEM columns
-  k_conv_mid_tc<BWD, OMASK><<<ctas, 192, smem, s>>>(batch, H, W, m8, w, b, omask, out);
+  k_conv_mid_tc<BWD, OMASK><<<ctas, 192, smem, s>>>(batch, H, W, m8, mo, w, b, omask);
   return launched(what);
 }
 
@@ -1445,7 +1542,8 @@ tat_status tat_conv_in_bwd_weights(int batch, int H, int W, int cin, const float
 
 tat_status tat_conv_mid_fwd(int batch, int H, int W, const tat_bf16* h_in, const tat_bf16* w, const float* b,
                             tat_bf16* h_out, tat_stream_t stream) {
-  if (bad_sizes(batch, H, W) || !h_in || !w || !b || !h_out || misaligned(h_in) || misaligned(h_out))
+  if (bad_sizes(batch, H, W) || !h_in || !w || !b || !h_out || misaligned(h_in) || misaligned(h_out) ||
+      misaligned(w))
     return TAT_ERR_INVALID_ARG;
   CUtensorMap m8;
   if (!halo8_map(&m8, h_in, batch, H, W)) {
@@ -1458,7 +1556,7 @@ tat_status tat_conv_mid_fwd(int batch, int H, int W, const tat_bf16* h_in, const
 
 tat_status tat_conv_mid_bwd_data(int batch, int H, int W, const tat_bf16* g_out, const tat_bf16* h_out,
                                  const tat_bf16* w, const tat_bf16* h_in, tat_bf16* g_in, tat_stream_t stream) {
-  if (bad_sizes(batch, H, W) || !g_out || !w || !g_in) return TAT_ERR_INVALID_ARG;
+  if (bad_sizes(batch, H, W) || !g_out || !w || !g_in || misaligned(w)) return TAT_ERR_INVALID_ARG;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   const char* what = "tat_conv_mid_bwd_data";
   if (h_out && h_in) return launch_mid<true, true, true>(batch, H, W, g_out, h_out, h_in, w, nullptr, g_in, s, what);
