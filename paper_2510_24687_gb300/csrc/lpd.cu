@@ -95,6 +95,8 @@ __device__ __forceinline__ void mma_bf16(float* d, const unsigned* a, const unsi
 constexpr int HALO_PIX = (TY + 2) * (TX + 2);  // 180 pixels of 64 bytes
 constexpr int HALO_BYTES = HALO_PIX * C * 2;   // 11 520 bytes per tile
 constexpr int HALO_SLOT = 12288;               // tile slot, a multiple of the 512-byte swizzle period
+constexpr int ZP = 196;  // pitch of per-tap sums over a halo: 192 rows (12 m-tiles) + 4, so that fragment
+                         // stores spread over all banks
 constexpr int kSpinLimit = 1 << 22;            // tries of a bounded mbarrier wait before giving up
 
 __device__ int g_lpd_timeout = 0;  // set when a CTA gave up waiting for a tile
@@ -879,17 +881,18 @@ __global__ void __launch_bounds__(256) k_conv_in_fwd(int B, int H, int W, const 
 
 // Layout of k_conv_in_bwd's dynamic shared memory: alignment slack; two slots of the g
 // halo (and, with MASK, the h halo), a region that afterwards holds the per-warp weight-
-// gradient sums; the flipped weights [9][8][CP]; two BF16 copies of the x halo (the second
-// shifted by one column, so that every pixel pair is a 4-byte word in one of them); two
-// mbarriers.
+// gradient sums; the per-tap sums z[9 CIN][ZP] of the data gradient; two BF16 copies of the
+// x halo (the second shifted by one column, so that every pixel pair is a 4-byte word in one
+// of them); two mbarriers.
 template <int CIN, bool MASK>
 struct InBwdSmem {
   static constexpr int STAGE = (MASK ? 2 : 1) * HALO_SLOT;
   static constexpr int NTW = (9 * CIN + 1 + 7) / 8;  // n-tiles of the weight-gradient GEMM (with the ones column)
+  static constexpr int NTZ = (9 * CIN + 7) / 8;      // n-tiles of the per-tap sums
   static constexpr int RED = 8 * NTW * 8 * C * 4;
   static constexpr int REGION = 2 * STAGE > RED ? 2 * STAGE : RED;
   static constexpr int XCOPY = CIN * XH * XP;
-  static constexpr int WSB = REGION, XS = WSB + 9 * 8 * CP * 2, BAR = XS + 2 * XCOPY * 2;
+  static constexpr int ZS = REGION, XS = ZS + 9 * CIN * ZP * 4, BAR = XS + 2 * XCOPY * 2;
   static constexpr size_t BYTES = 1024 + BAR + 2 * sizeof(uint64_t);
 };
 
@@ -912,15 +915,24 @@ __global__ void __launch_bounds__(256, 2) k_conv_in_bwd(int B, int H, int W, con
   const bool DATA = parts & 1, WGRAD = parts & 2;
   extern __shared__ unsigned char dsm[];
   unsigned char* sm = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
-  tat_bf16* wsb = reinterpret_cast<tat_bf16*>(sm + L::WSB);
+  float* zs = reinterpret_cast<float*>(sm + L::ZS);
   unsigned short* xs = reinterpret_cast<unsigned short*>(sm + L::XS);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L::BAR);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  if (DATA)
-    for (int e = threadIdx.x; e < 9 * 8 * C; e += blockDim.x) {
-      const int tap = e / (8 * C), n = (e / C) % 8, co = e % C;
-      wsb[(tap * 8 + n) * CP + co] = n < CIN ? w[((8 - tap) * CIN + n) * C + co] : (tat_bf16)0;
-    }
+  // B of the per-tap sums: B[k = co][n = tap CIN + c] = w[8 - tap][c][co] (the flipped kernel)
+  unsigned bz[2][L::NTZ][2];
+#pragma unroll
+  for (int kc = 0; kc < 2; ++kc)
+#pragma unroll
+    for (int nt = 0; nt < L::NTZ; ++nt)
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        const int n = 8 * nt + g, co = 16 * kc + 8 * hf + 2 * t;
+        const int tap = n / CIN, c = n % CIN;
+        bz[kc][nt][hf] = DATA && n < KV ? (unsigned)w[((8 - tap) * CIN + c) * C + co] |
+                                              ((unsigned)w[((8 - tap) * CIN + c) * C + co + 1] << 16)
+                                        : 0u;
+      }
   // B of the weight gradient: per n-tile the word offset of the thread's x pair (column n = 8 nt + g)
   int boff[NTW];
   unsigned bconst[NTW];
@@ -971,13 +983,15 @@ __global__ void __launch_bounds__(256, 2) k_conv_in_bwd(int B, int H, int W, con
         const unsigned char* ht = gt + HALO_SLOT;
         const int m = lane >> 3;
         if (DATA) {
-          float acc[4] = {0.f, 0.f, 0.f, 0.f};
+          // per-tap sums z[tap CIN + c](q) = sum_co G'(q)[co] w[8 - tap][c][co] of every halo
+          // pixel q (12 m-tiles of 16; the last one partly past the halo, inside the slot) ...
+          for (int mt = warp; mt < 12; mt += 8) {
+            float acc[L::NTZ][4];
 #pragma unroll
-          for (int tap = 0; tap < 9; ++tap) {
-            const int dy = tap / 3, dx = tap % 3;
-            unsigned bq[4];
-            ldsm_x4(bq, reinterpret_cast<const unsigned char*>(wsb + (tap * 8 + (lane & 7)) * CP + m * 8));
-            const int pa = (warp + dy) * XW + dx + (m & 1) * 8 + (lane & 7);
+            for (int nt = 0; nt < L::NTZ; ++nt)
+#pragma unroll
+              for (int k = 0; k < 4; ++k) acc[nt][k] = 0.f;
+            const int pa = 16 * mt + (m & 1) * 8 + (lane & 7);
 #pragma unroll
             for (int kc = 0; kc < 2; ++kc) {
               unsigned a[4];
@@ -988,22 +1002,36 @@ __global__ void __launch_bounds__(256, 2) k_conv_in_bwd(int B, int H, int W, con
 #pragma unroll
                 for (int j = 0; j < 4; ++j) a[j] = relu_masked(a[j], mk[j]);
               }
-              mma_bf16(acc, a, bq + 2 * kc);
-            }
-          }
-          const int y = y0 + warp;
-          if (t < 2 && y < H) {
 #pragma unroll
-            for (int hf = 0; hf < 2; ++hf) {
-              const int x = x0c + g + 8 * hf;
-              if (x >= W) continue;
-              const long long pix = ((long long)b * H + y) * W + x;
+              for (int nt = 0; nt < L::NTZ; ++nt) mma_bf16(acc[nt], a, bz[kc][nt]);
+            }
+            const int q = 16 * mt + g;
+#pragma unroll
+            for (int nt = 0; nt < L::NTZ; ++nt)
 #pragma unroll
               for (int j = 0; j < 2; ++j) {
-                const int c = 2 * t + j;
-                if (c >= CIN) continue;
+                const int n = 8 * nt + 2 * t + j;
+                if (n < KV) {
+                  zs[n * ZP + q] = acc[nt][j];
+                  zs[n * ZP + q + 8] = acc[nt][2 + j];
+                }
+              }
+          }
+          __syncthreads();
+          // ... then gx_c(p) = sum_tap z[tap CIN + c](p + tap), a 9-point stencil
+          if (threadIdx.x < TY * TX) {
+            const int r = threadIdx.x >> 4, cc = threadIdx.x & 15;
+            const int y = y0 + r, x = x0c + cc;
+            if (y < H && x < W) {
+              const long long pix = ((long long)b * H + y) * W + x;
+#pragma unroll
+              for (int c = 0; c < CIN; ++c) {
                 float* gx = c == 0 ? gx0 : (c == 1 ? gx1 : gx2);
-                if (gx != nullptr) gx[pix] = (((accumulate >> c) & 1) ? gx[pix] : 0.f) + acc[2 * hf + j];
+                if (gx == nullptr) continue;
+                float v = 0.f;
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) v += zs[(tap * CIN + c) * ZP + (r + tap / 3) * XW + cc + tap % 3];
+                gx[pix] = (((accumulate >> c) & 1) ? gx[pix] : 0.f) + v;
               }
             }
           }
@@ -1059,55 +1087,80 @@ __global__ void __launch_bounds__(256, 2) k_conv_in_bwd(int B, int H, int W, con
 }
 
 // Dynamic shared memory of the out-layer kernels: alignment slack, two slots of h halos,
-// [9][8][CP] weights (forward) or the hi / lo x 2-copy halo of g_out (backward), two mbarriers.
-constexpr size_t out_fwd_smem_bytes() { return 1024 + 2 * HALO_SLOT + 9 * 8 * CP * 2 + 2 * sizeof(uint64_t); }
+// the per-tap sums z[9][ZP] (forward) or the hi / lo x 2-copy halo of g_out (backward), two
+// mbarriers.
+constexpr size_t out_fwd_smem_bytes() { return 1024 + 2 * HALO_SLOT + 9 * ZP * 4 + 2 * sizeof(uint64_t); }
 constexpr size_t out_bwd_smem_bytes() { return 1024 + 2 * HALO_SLOT + 4 * XH * XP * 2 + 2 * sizeof(uint64_t); }
 
-// out = residual + b + conv_out(h): the 32 -> 32 forward with N = 8 (weights in column 0).
+// out = residual + b + conv_out(h), in two steps per tile.  First the per-tap channel sums
+// z[tap](q) = sum_ci w[tap][ci] h(q)[ci] of every halo pixel q: a GEMM with M = the halo's
+// pixels (12 m-tiles of 16, the last one partly past the halo, inside the slot), N = 16
+// (taps, 9 used), K = 32 channels, A by ldmatrix from the swizzled halo -- each halo value
+// is read once.  Then out(p) = sum_tap z[tap](p + tap), a 9-point stencil on z in shared
+// memory.
 __global__ void __launch_bounds__(256) k_conv_out_fwd(int B, int H, int W, const __grid_constant__ CUtensorMap map_h,
                                                       const tat_bf16* __restrict__ w, const float* __restrict__ bias,
                                                       const float* residual, float* out) {
   extern __shared__ unsigned char dsm[];
   unsigned char* sm = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
-  tat_bf16* wso = reinterpret_cast<tat_bf16*>(sm + 2 * HALO_SLOT);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * HALO_SLOT + 9 * 8 * CP * 2);
+  float* zs = reinterpret_cast<float*>(sm + 2 * HALO_SLOT);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + 2 * HALO_SLOT + 9 * ZP * 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  for (int e = threadIdx.x; e < 9 * 8 * C; e += blockDim.x) {
-    const int tap = e / (8 * C), n = (e / C) % 8, k = e % C;
-    wso[(tap * 8 + n) * CP + k] = n == 0 ? w[tap * C + k] : (tat_bf16)0;
-  }
+  // B[k = ci][n = tap] fragments of the two k-steps and two n-tiles (taps 9..15 zero)
+  unsigned bq[2][2][2];
+#pragma unroll
+  for (int kc = 0; kc < 2; ++kc)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        const int tap = 8 * nt + g, ci = 16 * kc + 8 * hf + 2 * t;
+        bq[kc][nt][hf] = tap < 9 ? (unsigned)w[tap * C + ci] | ((unsigned)w[tap * C + ci + 1] << 16) : 0u;
+      }
   init_bars(bar);
   __syncthreads();
   const float b0 = bias[0];
+  const int m = lane >> 3;
   tile_loop(
       B, H, W, bar, HALO_BYTES,
       [&](int b, int y0, int x0c, int s) { tma_load_4d(sm + s * HALO_SLOT, &map_h, 0, x0c - 1, y0 - 1, b, &bar[s]); },
       [](int, int, int) {}, [] {},
       [&](int b, int y0, int x0c, int s) {
         const unsigned char* ht = sm + s * HALO_SLOT;
-        const int m = lane >> 3;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-          const int dy = tap / 3, dx = tap % 3;
-          unsigned bq[4];
-          ldsm_x4(bq, reinterpret_cast<const unsigned char*>(wso + (tap * 8 + (lane & 7)) * CP + m * 8));
-          const int pa = (warp + dy) * XW + dx + (m & 1) * 8 + (lane & 7);
+        for (int mt = warp; mt < 12; mt += 8) {
+          float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
           for (int kc = 0; kc < 2; ++kc) {
             unsigned a[4];
-            ldsm_x4(a, swz(ht, pa, 2 * kc + (m >> 1)));
-            mma_bf16(acc, a, bq + 2 * kc);
+            ldsm_x4(a, swz(ht, 16 * mt + (m & 1) * 8 + (lane & 7), 2 * kc + (m >> 1)));
+            mma_bf16(acc[0], a, bq[kc][0]);
+            mma_bf16(acc[1], a, bq[kc][1]);
+          }
+          const int q = 16 * mt + g;
+#pragma unroll
+          for (int nt = 0; nt < 2; ++nt) {
+            const int tap = 8 * nt + 2 * t;
+            if (tap < 9) {
+              zs[tap * ZP + q] = acc[nt][0];
+              zs[tap * ZP + q + 8] = acc[nt][2];
+            }
+            if (tap + 1 < 9) {
+              zs[(tap + 1) * ZP + q] = acc[nt][1];
+              zs[(tap + 1) * ZP + q + 8] = acc[nt][3];
+            }
           }
         }
-        const int y = y0 + warp;
-        if (t != 0 || y >= H) return;
+        __syncthreads();
+        const int r = threadIdx.x >> 4, c = threadIdx.x & 15;  // 256 threads = the 8 x 16 outputs, twice
+        if (threadIdx.x < TY * TX) {
+          const int y = y0 + r, x = x0c + c;
+          if (y < H && x < W) {
+            float v = 0.f;
 #pragma unroll
-        for (int hf = 0; hf < 2; ++hf) {
-          const int x = x0c + g + 8 * hf;
-          if (x >= W) continue;
-          const long long pix = ((long long)b * H + y) * W + x;
-          out[pix] = residual[pix] + b0 + acc[2 * hf];
+            for (int tap = 0; tap < 9; ++tap) v += zs[tap * ZP + (r + tap / 3) * XW + c + tap % 3];
+            const long long pix = ((long long)b * H + y) * W + x;
+            out[pix] = residual[pix] + b0 + v;
+          }
         }
       });
 }
