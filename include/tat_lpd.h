@@ -19,11 +19,14 @@
  * stored in BF16, hidden activations and their gradients stored in BF16),
  * FP32 accumulation, FP32 biases, residual planes, outputs of the out layer,
  * gradients of the FP32 planes and of all weights.  All layers run on the
- * tensor cores (mma.sync m16n8k16, BF16 x BF16 -> FP32, exact products); the
- * FP32 gradient entering the out layer's backward is split into two BF16 terms
- * (hi + lo, 16 significand bits).  Tiles of the hidden activations are staged
- * by TMA, so those pointers (h, h_in, h_out, g_h, g_out of the BF16 layers)
- * must be 16-byte aligned (TAT_ERR_INVALID_ARG otherwise).
+ * tensor cores (BF16 x BF16 -> FP32, exact products): the 32 -> 32 forward and
+ * the data gradient of an already masked gradient on tcgen05 (accumulators in
+ * tensor memory), the others on mma.sync m16n8k16; the FP32 gradient entering
+ * the out layer's backward is split into two BF16 terms (hi + lo, 16
+ * significand bits).  Tiles of the hidden activations are staged by TMA, so
+ * those pointers (h, h_in, h_out, g_h, g_out of the BF16 layers), and the
+ * weights w of the 32 -> 32 layer (read in 16-byte words), must be 16-byte
+ * aligned (TAT_ERR_INVALID_ARG otherwise).
  *
  * Layouts (all DEVICE pointers owned by the caller): planes FP32 [batch][H][W];
  * hidden activations BF16 NHWC [batch][H][W][32] (BF16 as its 16-bit pattern,
@@ -34,8 +37,9 @@
  * pixels write per-CTA partial sums into `scratch` (FP32, at least
  * tat_lpd_scratch_floats(batch, H, W) floats) and then add them in a fixed
  * order: the sums are deterministic.  Calls are asynchronous on `stream`;
- * TAT_ERR_INVALID_ARG for NULL required pointers, non-positive sizes, cin not
- * 2 or 3, or a scratch buffer that is too small.
+ * TAT_ERR_INVALID_ARG for NULL required pointers, non-positive sizes, grids of
+ * batch x H x W >= 2^31 pixels, cin not 2 or 3, or a scratch buffer that is too
+ * small.
  */
 #ifndef TAT_LPD_H_
 #define TAT_LPD_H_

@@ -197,15 +197,16 @@ __device__ __forceinline__ const unsigned char* swz(const unsigned char* tile, i
 template <class Issue, class Prefetch, class Commit, class Body>
 __device__ __forceinline__ bool tile_loop(int B, int H, int W, uint64_t* bar, unsigned bytes, Issue issue,
                                           Prefetch prefetch, Commit commit, Body body) {
-  const int tilesx = (W + TX - 1) / TX, tilesy = (H + TY - 1) / TY;
-  const long long ntiles = (long long)B * tilesx * tilesy;
-  auto coords = [&](long long tile, int& b, int& y0, int& x0) {
-    b = (int)(tile / (tilesx * tilesy));
-    const int rr = (int)(tile % (tilesx * tilesy));
-    y0 = (rr / tilesx) * TY;
-    x0 = (rr % tilesx) * TX;
+  // 32-bit tile arithmetic: the host rejects grids of 2^31 pixels or more
+  const unsigned tilesx = (W + TX - 1) / TX, tpi = tilesx * ((H + TY - 1) / TY);
+  const unsigned ntiles = (unsigned)B * tpi;
+  auto coords = [&](unsigned tile, int& b, int& y0, int& x0) {
+    const unsigned bb = tile / tpi, rr = tile - bb * tpi, ty = rr / tilesx;
+    b = (int)bb;
+    y0 = (int)ty * TY;
+    x0 = (int)(rr - ty * tilesx) * TX;
   };
-  auto start = [&](long long tile, int s) {
+  auto start = [&](unsigned tile, int s) {
     int b, y0, x0;
     coords(tile, b, y0, x0);
     if (bytes != 0 && threadIdx.x == 0) {
@@ -215,14 +216,14 @@ __device__ __forceinline__ bool tile_loop(int B, int H, int W, uint64_t* bar, un
     }
     prefetch(b, y0, x0);
   };
-  if ((long long)blockIdx.x < ntiles) {
+  if (blockIdx.x < ntiles) {
     start(blockIdx.x, 0);
     commit();
   }
   int i = 0;
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
+  for (unsigned tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++i) {
     const int s = i & 1;
-    const long long next = tile + gridDim.x;
+    const unsigned next = tile + gridDim.x;
     if (next < ntiles) start(next, s ^ 1);  // slot s^1 was released by the barrier ending the previous tile
     const bool ok = bytes == 0 || mbar_wait(&bar[s], (unsigned)((i >> 1) & 1));
     if (__syncthreads_or(!ok)) {
@@ -544,15 +545,16 @@ __global__ void __launch_bounds__(192, 4) k_conv_mid_tc(int B, int H, int W, con
     asm volatile("bar.sync 1, 160;\n" ::: "memory");
   }
   const uint32_t sbase = smem_u32(sm);
-  const int tilesx = (W + TX - 1) / TX, tilesy = (H + TY - 1) / TY;
-  const long long ntiles = (long long)B * tilesx * tilesy;
+  // 32-bit tile arithmetic: the host rejects grids of 2^31 pixels or more
+  const unsigned tilesx = (W + TX - 1) / TX, tpi = tilesx * ((H + TY - 1) / TY);
+  const unsigned ntiles = (unsigned)B * tpi;
   const int mine = ntiles > blockIdx.x ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x) + 1 : 0;  // tiles of this CTA
   auto coords = [&](int n, int& b, int& y0, int& x0) {
-    const long long tile = blockIdx.x + (long long)n * gridDim.x;
-    b = (int)(tile / (tilesx * tilesy));
-    const int rr = (int)(tile % (tilesx * tilesy));
-    y0 = (rr / tilesx) * TY;
-    x0 = (rr % tilesx) * TX;
+    const unsigned tile = blockIdx.x + (unsigned)n * gridDim.x, bb = tile / tpi, rr = tile - bb * tpi,
+                   ty = rr / tilesx;
+    b = (int)bb;
+    y0 = (int)ty * TY;
+    x0 = (int)(rr - ty * tilesx) * TX;
   };
   bool ok = true;
   if (warp == 0) {
@@ -1373,7 +1375,9 @@ __global__ void k_mse(long long n, const float* __restrict__ a, const float* __r
   }
 }
 
-bool bad_sizes(int batch, int H, int W) { return batch < 1 || H < 1 || W < 1; }
+bool bad_sizes(int batch, int H, int W) {
+  return batch < 1 || H < 1 || W < 1 || (long long)batch * H * W >= (1LL << 31);  // tiles are counted in 32 bits
+}
 
 // Persistent tensor-core conv: up to 3 CTAs per SM, every CTA stages the
 // weights once and loops over tiles.

@@ -103,6 +103,8 @@ def test_lpd_layers_reject_bad_arguments_before_any_device_work(pkg):
         pkg.tat_conv_out_bwd(1, 8, 16, fake, fake, fake, 0, fake, fake, 1, fake, fake)
     with pytest.raises(bad):
         pkg.tat_conv_in_fwd(1, 8, 16, 4, fake, fake, fake, fake, fake, fake)
+    with pytest.raises(bad):                     # 2^32 pixels: tile indices are 32-bit
+        pkg.tat_conv_out_fwd(1 << 16, 1 << 8, 1 << 8, fake, fake, fake, fake, fake)
     for tries in (0, (1 << 20) + 1):
         with pytest.raises(bad):
             pkg.tat_lpd_timeout_probe(tries, fake)
