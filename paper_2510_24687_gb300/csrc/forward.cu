@@ -18,6 +18,9 @@ tat_status validate_shapes(const tat_plan_s* Pl) {
   const int N = Pl->d.N;
   const bool ct = N == 256 || N == 512 || N == 1024 || N == 2048 || N == 4096 || N == 8192;
   if (ct && N <= 4096 && s.cols_block > 256) return TAT_ERR_UNSUPPORTED;
+  // the Stockham column FFT runs on nt_N threads of the CTA; the four-step one on any multiple of 32
+  const bool four = N == 512 || N == 1024 || N == 2048 || N == 4096 || N == 8192;
+  if (!four && (s.cols_block < Pl->cfg.nt_N || s.cols_block < 256)) return TAT_ERR_UNSUPPORTED;
   if (N == 8192 && s.rows_block > 512) return TAT_ERR_UNSUPPORTED;  // launch bound of the row kernels there
   for (size_t m : smem)
     if (m > mx) return TAT_ERR_UNSUPPORTED;

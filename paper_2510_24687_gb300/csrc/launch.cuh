@@ -30,7 +30,7 @@ inline Shapes shapes(const tat_plan_s* Pl, int batch) {
   // 1-D, strip-major: blockIdx.x = strip * batch + image
   s.cols_grid_f = dim3(((P.ncol - 1 + c.strip - 1) / c.strip) * batch);
   s.cols_grid_a = dim3(((P.ncol + c.strip - 1) / c.strip) * batch);
-  s.cols_block = c.nt_N < 256 ? 256 : c.nt_N;
+  s.cols_block = c.cols_threads;
   s.cols_smem_f = (2 * (size_t)xpad_len(P.N) + kFourStepTw) * sizeof(float2);
   s.cols_smem_a = (2 * (size_t)xpad_len(P.N) + kFourStepTw) * sizeof(float2);
   s.cols_smem_i = ((size_t)xpad_len(P.N) + kFourStepTw) * sizeof(float2);

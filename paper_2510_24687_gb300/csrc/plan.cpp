@@ -580,6 +580,7 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
   if (n_det == 1024) c.nt_det = std::max(c.nt_det, 64);
   c.rows_pairs = d.N == 8192 ? 1 : std::max(1, std::min(4, 1024 / c.nt_rows));
   c.strip = 8;
+  c.cols_threads = std::max(c.nt_N, 256);
   c.rings_per_cta = rings_per_cta_for(n_phi);
   c.t_tile = time_tile_for(n_det);
   // Workspace per image (float2): X holds row spectra (n x N/2) or per-mode

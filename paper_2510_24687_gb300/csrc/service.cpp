@@ -380,7 +380,7 @@ tat_status tat_service_flush(tat_service_t S) {
       float* gbuf = s.op == TAT_OP_PAIR ? s.mid : (s.op == TAT_OP_FORWARD ? s.out : s.in);
       cudaMemsetAsync(fbuf, 0, img * sizeof(float) * s.cap, s.stream);
       cudaMemsetAsync(gbuf, 0, dat * sizeof(float) * s.cap, s.stream);
-      e = tat_plan_autotune(s.plan, s.cap, fbuf, gbuf, fbuf, s.ws, s.stream, nullptr, nullptr, nullptr);
+      e = tat_plan_autotune(s.plan, s.cap, fbuf, gbuf, fbuf, s.ws, s.stream, nullptr, nullptr, nullptr, nullptr);
       drop_graphs(s);
       s.tuned = true;
     }
@@ -437,8 +437,21 @@ tat_status tat_service_get_stats(tat_service_t S, tat_service_stats* out) {
   return TAT_OK;
 }
 
+tat_status tat_plan_set_launch_shape(tat_plan_t plan, int strip, int row_pairs, int cols_threads) {
+  if (!plan || strip < 1 || row_pairs < 1 || cols_threads < 32) return TAT_ERR_INVALID_ARG;
+  const tat::LaunchCfg old = plan->cfg;
+  plan->cfg.strip = strip;
+  plan->cfg.rows_pairs = row_pairs;
+  plan->cfg.cols_threads = cols_threads;
+  if (row_pairs * plan->cfg.nt_rows > 1024 || tat::validate_shapes(plan) != TAT_OK) {
+    plan->cfg = old;
+    return TAT_ERR_UNSUPPORTED;
+  }
+  return TAT_OK;
+}
+
 tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, float* f_out, void* workspace,
-                             tat_stream_t stream, double* ms_best, int* strip_out, int* rp_out) {
+                             tat_stream_t stream, double* ms_best, int* strip_out, int* rp_out, int* cols_threads_out) {
   if (!plan || batch < 1 || !f || !g || !f_out || !workspace) return TAT_ERR_INVALID_ARG;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const tat::LaunchCfg base = plan->cfg;
@@ -451,32 +464,44 @@ tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, flo
   tat::LaunchCfg best = base;
   float best_ms = 1e30f;
   tat_status err = TAT_OK;
-  for (int strip : {2, 4, 8, 16, 32}) {
+  // Times plan->cfg on one pair (after one warm-up pair); keeps it when it is the fastest so far.
+  auto trial = [&]() {
+    if (tat::validate_shapes(plan) != TAT_OK) return;
+    float ms = 0.f;
+    for (int rep = 0; rep < 3 && err == TAT_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      err = tat::launch_forward(plan, batch, f, fs, g, gs, workspace, st);
+      if (err == TAT_OK) err = tat::launch_adjoint(plan, batch, g, gs, f_out, fs, workspace, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) err = TAT_ERR_CUDA;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rep > 0) ms += t;  // first repetition is the warm-up
+    }
+    if (err == TAT_OK && ms / 2.f < best_ms) {
+      best_ms = ms / 2.f;
+      best = plan->cfg;
+    }
+  };
+  for (int strip : {2, 4, 8, 16, 32})
     for (int rp : {1, 2, 4}) {
+      if (err != TAT_OK) break;
       plan->cfg = base;
       plan->cfg.strip = strip;
       plan->cfg.rows_pairs = rp;
-      if (rp * plan->cfg.nt_rows > 1024 || tat::validate_shapes(plan) != TAT_OK) continue;
-      float ms = 0.f;
-      for (int rep = 0; rep < 3 && err == TAT_OK; ++rep) {
-        cudaEventRecord(e0, st);
-        err = tat::launch_forward(plan, batch, f, fs, g, gs, workspace, st);
-        if (err == TAT_OK) err = tat::launch_adjoint(plan, batch, g, gs, f_out, fs, workspace, st);
-        cudaEventRecord(e1, st);
-        if (cudaEventSynchronize(e1) != cudaSuccess) err = TAT_ERR_CUDA;
-        float t = 0.f;
-        cudaEventElapsedTime(&t, e0, e1);
-        if (rep > 0) ms += t;  // first repetition is the warm-up
-      }
-      if (err != TAT_OK) break;
-      ms /= 2.f;
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = plan->cfg;
-      }
+      if (rp * plan->cfg.nt_rows <= 1024) trial();
     }
-    if (err != TAT_OK) break;
-  }
+  // then smaller column CTAs for the chosen strip and row pairs (more of them per SM, where the
+  // four-step column FFT keeps fewer than 256 threads busy), and strips around the chosen one
+  const tat::LaunchCfg first = best;
+  for (int threads : {64, 128})
+    for (int strip : {first.strip / 2, first.strip, first.strip * 2}) {
+      if (err != TAT_OK || strip < 2 || strip > 32 || threads >= first.cols_threads) continue;
+      plan->cfg = first;
+      plan->cfg.cols_threads = threads;
+      plan->cfg.strip = strip;
+      trial();
+    }
   plan->cfg = err == TAT_OK ? best : base;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -484,6 +509,7 @@ tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, flo
   if (ms_best) *ms_best = best_ms;
   if (strip_out) *strip_out = best.strip;
   if (rp_out) *rp_out = best.rows_pairs;
+  if (cols_threads_out) *cols_threads_out = best.cols_threads;
   return TAT_OK;
 }
 
