@@ -409,12 +409,15 @@ __global__ void __launch_bounds__(256) k_conv_mid(int B, int H, int W, const __g
 //
 // Implicit GEMM per tile of 16 rows x 8 pixels: M = 128 pixels, N = 32 output channels,
 // K = 9 taps x 32 input channels in 18 tcgen05.mma (kind::f16, BF16 operands, FP32
-// accumulation) issued by one thread.  Operands sit in shared memory in the canonical
-// K-major layout without swizzle: 8 x 16-byte core matrices, i.e. 8 consecutive pixels (or
-// output channels) of one 8-channel plane.  The halo of a tile (18 x 10 pixels) arrives by
-// TMA as four 8-channel planes [pixel][16 B], so the A operand of a tap is the plane shifted
-// by the tap's offset: core-matrix rows 16 B apart (consecutive pixels), core-matrix groups
-// 160 B apart (one halo row of 10 pixels), K halves one plane apart.  The accumulator of a
+// accumulation) issued by one thread.  The halo of a tile (18 x 10 pixels of 32 channels)
+// arrives by one TMA copy with the 64-byte swizzle: [pixel][64 B], the 16-byte chunks of a
+// pixel permuted by address bits 7-8.  It is the A operand as it lies, in the canonical
+// K-major layout with the same swizzle: a row (pixel) is 64 B = the whole K of one tap, the
+// tap's A is the halo shifted by the tap's offset (start address + 64 B per pixel; the
+// swizzle follows the absolute address, so odd shifts read what the copy wrote), 8-row
+// groups 640 B apart (one halo row of 10 pixels), the second K = 16 step 32 B further.  The
+// weights (B) use the layout without swizzle: 8 x 16-byte core matrices of 8 output channels
+// x 8 input channels.  The accumulator of a
 // tile is 32 TMEM columns; two of them alternate, so the epilogue of tile i-1 (tcgen05.ld,
 // bias, ReLU, BF16 into a shared-memory tile that one bulk tensor store writes out) overlaps
 // the MMAs of tile i, and two halo slots alternate, so the halo of tile i+1 loads meanwhile.
@@ -426,29 +429,36 @@ __global__ void __launch_bounds__(256) k_conv_mid(int B, int H, int W, const __g
 namespace tc {
 constexpr int TX = 8, TY = 16;             // tile: M = 128 pixels
 constexpr int HX = TX + 2, HY = TY + 2;    // 10 x 18 halo
-constexpr int PLANE = 2944;                // bytes of one 8-channel halo plane (180 x 16 B, rounded up to 128 B)
-constexpr int SLOT = 4 * PLANE;            // one staged halo
+constexpr int SLOT = 11776;                // one staged halo [180 pixels][64 B], a multiple of the 512-byte
+                                           // swizzle period
 constexpr int NS = 2;                      // halo slots: tile n+1 loads while tile n computes
-constexpr int HALO_TX = 4 * HX * HY * 16;  // bytes a halo's four copies deliver
+constexpr int HALO_TX = HX * HY * 64;      // bytes of a halo
 constexpr int WOFF = NS * SLOT;            // weights [tap][plane][co][16 B], 2 KB per tap
 constexpr int BOFF = WOFF + 9 * 2048;      // bias, 32 floats
 constexpr int OOFF = BOFF + 128;           // output tile [16][8][32] BF16 for the bulk store, 8 KB
-constexpr int MOFF = OOFF + TX * TY * 64;  // mbarriers: halo full[NS], empty[NS], accumulator full[2],
-                                           // empty[2]; then the TMEM address
-constexpr int SMEM = 128 + MOFF + 128;     // alignment slack (128 B for the TMA tiles) + the layout above
-                                           // (49.4 KB: 4 CTAs per SM)
-constexpr int TMEM_COLS = 64;              // two accumulators of 32 FP32 columns
+constexpr int NACC = 2;                    // accumulators in TMEM: the MMAs run up to NACC - 1 tiles ahead
+constexpr int CTAS = 4;                    // resident CTAs per SM (shared memory, TMEM: CTAS x TMEM_COLS <= 512)
+constexpr int MOFF = OOFF + TX * TY * 64;  // mbarriers: halo full[NS], empty[NS], accumulator full[NACC],
+                                           // empty[NACC]; then the TMEM address
+constexpr int SMEM = 512 + MOFF + 256;     // alignment slack (512 B: the swizzled halos) + the layout above
+                                           // (49.5 KB: 4 CTAs per SM)
+constexpr int TMEM_COLS = 32 * NACC;       // NACC accumulators of 32 FP32 columns (a power of 2 >= 32)
+static_assert(2 * (NS + NACC) * 8 + 4 <= 256, "mbarrier region");
+static_assert(CTAS * TMEM_COLS <= 512, "TMEM columns of the resident CTAs");
 // Instruction descriptor (kind::f16): FP32 D, BF16 A and B, both K-major, N = 32, M = 128.
 constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
 }  // namespace tc
 
 // Shared-memory matrix descriptor: canonical K-major layout without swizzle, start address,
 // leading byte offset (between the two core matrices along K) and stride byte offset
-// (between core-matrix groups along M or N), all in 16-byte units; version 1.
+// (between core-matrix groups along M or N), all in 16-byte units; version 1.  OR-ing
+// kSwizzle64 into it selects the 64-byte-swizzle layout (rows of 64 B, SBO between 8-row
+// groups, LBO unused).
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
          (1ull << 46);
 }
+constexpr uint64_t kSwizzle64 = 4ull << 61;  // layout type field: 64-byte swizzle
 
 __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
   asm volatile(
@@ -488,30 +498,31 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
 // tiles over through mbarriers only -- halo full / empty per slot, accumulator full / empty
 // per TMEM buffer -- so no CTA-wide barrier sits inside the tile loop.
 template <bool BWD, bool OMASK>
-__global__ void __launch_bounds__(192, 4) k_conv_mid_tc(int B, int H, int W, const __grid_constant__ CUtensorMap map8,
+__global__ void __launch_bounds__(192, tc::CTAS) k_conv_mid_tc(int B, int H, int W, const __grid_constant__ CUtensorMap map8,
                                                         const __grid_constant__ CUtensorMap map_out,
                                                         const tat_bf16* __restrict__ w, const float* __restrict__ bias,
                                                         const tat_bf16* __restrict__ omask) {
-  constexpr int TX = tc::TX, TY = tc::TY, HX = tc::HX, PLANE = tc::PLANE, SLOT = tc::SLOT, WOFF = tc::WOFF;
+  constexpr int TX = tc::TX, TY = tc::TY, HX = tc::HX, SLOT = tc::SLOT, WOFF = tc::WOFF;
   constexpr int BOFF = tc::BOFF, MOFF = tc::MOFF, HALO_TX = tc::HALO_TX, TMEM_COLS = tc::TMEM_COLS, NS = tc::NS;
+  constexpr int NACC = tc::NACC;
   constexpr uint32_t IDESC = tc::IDESC;
   extern __shared__ unsigned char dsm[];
-  unsigned char* sm = dsm + ((128u - (smem_u32(dsm) & 127u)) & 127u);
+  unsigned char* sm = dsm + ((512u - (smem_u32(dsm) & 511u)) & 511u);
   tat_bf16* wsm = reinterpret_cast<tat_bf16*>(sm + WOFF);
   float* bsm = reinterpret_cast<float*>(sm + BOFF);
   uint4* osm = reinterpret_cast<uint4*>(sm + tc::OOFF);     // [pixel][4 x 16 B]
   uint64_t* hfull = reinterpret_cast<uint64_t*>(sm + MOFF);  // [NS] halo landed
   uint64_t* hempty = hfull + NS;                              // [NS] halo consumed by the MMAs
-  uint64_t* afull = hempty + NS;                              // [2] accumulator written
-  uint64_t* aempty = afull + 2;                               // [2] accumulator read by the epilogue
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(aempty + 2);
+  uint64_t* afull = hempty + NS;                              // [NACC] accumulator written
+  uint64_t* aempty = afull + NACC;                            // [NACC] accumulator read by the epilogue
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(aempty + NACC);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int k = 0; k < NS; ++k) {
       mbar_init(&hfull[k], 1);
       mbar_init(&hempty[k], 1);
     }
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < NACC; ++k) {
       mbar_init(&afull[k], 1);
       mbar_init(&aempty[k], 128);
     }
@@ -567,8 +578,7 @@ __global__ void __launch_bounds__(192, 4) k_conv_mid_tc(int B, int H, int W, con
         int b, y0, x0;
         coords(n, b, y0, x0);
         mbar_expect_tx(&hfull[k], HALO_TX);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) tma_load_4d(sm + k * SLOT + c * PLANE, &map8, 8 * c, x0 - 1, y0 - 1, b, &hfull[k]);
+        tma_load_4d(sm + k * SLOT, &map8, 0, x0 - 1, y0 - 1, b, &hfull[k]);
         issued = n + 1;
       }
       if (!ok) {  // let the copies in flight land (their slots are not reused after this)
@@ -580,9 +590,9 @@ __global__ void __launch_bounds__(192, 4) k_conv_mid_tc(int B, int H, int W, con
     if (lane == 0) {  // MMAs
       int committed = 0;
       for (int n = 0; n < mine && ok; ++n) {
-        const int k = n % NS, a = n & 1;
+        const int k = n % NS, a = n % NACC;
         ok = mbar_wait(&hfull[k], (unsigned)((n / NS) & 1));
-        if (ok && n >= 2) ok = mbar_wait(&aempty[a], (unsigned)((n / 2 + 1) & 1));  // tile n-2 read out
+        if (ok && n >= NACC) ok = mbar_wait(&aempty[a], (unsigned)((n / NACC + 1) & 1));  // tile n-NACC read out
         if (!ok) break;
         tc_fence_after();
         const uint32_t d = tbase + (uint32_t)(a * 32);
@@ -592,7 +602,7 @@ __global__ void __launch_bounds__(192, 4) k_conv_mid_tc(int B, int H, int W, con
           const int dy = tap / 3, dx = tap % 3;
 #pragma unroll
           for (int kc = 0; kc < 2; ++kc) {
-            const uint64_t ad = umma_desc(abase + 2 * kc * PLANE + (dy * HX + dx) * 16, PLANE, HX * 16);
+            const uint64_t ad = umma_desc(abase + (dy * HX + dx) * 64 + 32 * kc, 16, HX * 64) | kSwizzle64;
             const uint64_t bd = umma_desc(wbase + tap * 2048 + 2 * kc * 512, 512, 128);
             umma_f16(d, ad, bd, IDESC, (tap | kc) != 0);
           }
@@ -602,14 +612,14 @@ __global__ void __launch_bounds__(192, 4) k_conv_mid_tc(int B, int H, int W, con
         committed = n + 1;
       }
       if (!ok && committed > 0)  // the MMAs in flight must finish before the TMEM is freed
-        mbar_wait(&afull[(committed - 1) & 1], (unsigned)(((committed - 1) >> 1) & 1));
+        mbar_wait(&afull[(committed - 1) % NACC], (unsigned)(((committed - 1) / NACC) & 1));
     }
   } else {  // epilogue: 128 threads, thread m of the tile = TMEM lane m = pixel (m / 8, m % 8)
     const int quarter = warp & 3;
     const int m = 32 * quarter + lane;
     for (int n = 0; n < mine; ++n) {
-      const int a = n & 1;
-      ok = mbar_wait(&afull[a], (unsigned)((n >> 1) & 1));
+      const int a = n % NACC;
+      ok = mbar_wait(&afull[a], (unsigned)((n / NACC) & 1));
       ok = epilogue_all(ok);  // one decision for the four warps, which meet at named barriers below
       if (!ok) break;
       tc_fence_after();
@@ -1441,17 +1451,17 @@ bool smem_attr(size_t bytes) {
 
 bool misaligned(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) != 0; }
 
-// Tensor map of a [batch][H][W][32] BF16 activation for the tcgen05 kernel: 8-channel
-// boxes of the 18 x 10 halo, no swizzle (the MMA's canonical K-major layout).
-bool halo8_map(CUtensorMap* m, const tat_bf16* base, int batch, int H, int W) {
+// Tensor map of a [batch][H][W][32] BF16 activation for the tcgen05 kernel: the 18 x 10
+// halo of 32 channels in one box, 64-byte swizzle (the MMA's swizzled K-major layout).
+bool halo_tc_map(CUtensorMap* m, const tat_bf16* base, int batch, int H, int W) {
   const EncodeTiled fn = encoder();
   if (!fn) return false;
   const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)batch};
   const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
-  const cuuint32_t box[4] = {8, (cuuint32_t)tc::HX, (cuuint32_t)tc::HY, 1};
+  const cuuint32_t box[4] = {(cuuint32_t)C, (cuuint32_t)tc::HX, (cuuint32_t)tc::HY, 1};
   const cuuint32_t estride[4] = {1, 1, 1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<tat_bf16*>(base), dims, strides, box, estride,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -1480,7 +1490,7 @@ tat_status launch_mid_tc(int batch, int H, int W, const CUtensorMap& m8, const t
     return TAT_ERR_CUDA;
   }
   const long long tiles = (long long)batch * ((H + tc::TY - 1) / tc::TY) * ((W + tc::TX - 1) / tc::TX);
-  const int ctas = (int)(tiles < 4 * 152 ? tiles : 4 * 152);  // 4 resident per SM: 4 x 64 TMEM columns
+  const int ctas = (int)(tiles < tc::CTAS * 152 ? tiles : tc::CTAS * 152);  // persistent: all resident
   k_conv_mid_tc<BWD, OMASK><<<ctas, 192, smem, s>>>(batch, H, W, m8, mo, w, b, omask);
   return launched(what);
 }
@@ -1603,7 +1613,7 @@ tat_status tat_conv_mid_fwd(int batch, int H, int W, const tat_bf16* h_in, const
       misaligned(w))
     return TAT_ERR_INVALID_ARG;
   CUtensorMap m8;
-  if (!halo8_map(&m8, h_in, batch, H, W)) {
+  if (!halo_tc_map(&m8, h_in, batch, H, W)) {
     fprintf(stderr, "tat_conv_mid_fwd: tensor map encoding failed\n");
     return TAT_ERR_CUDA;
   }
@@ -1621,7 +1631,7 @@ tat_status tat_conv_mid_bwd_data(int batch, int H, int W, const tat_bf16* g_out,
   // an already masked gradient: the tcgen05 kernel
   if (misaligned(g_out) || misaligned(h_in) || misaligned(g_in)) return TAT_ERR_INVALID_ARG;
   CUtensorMap m8;
-  if (!halo8_map(&m8, g_out, batch, H, W)) {
+  if (!halo_tc_map(&m8, g_out, batch, H, W)) {
     fprintf(stderr, "%s: tensor map encoding failed\n", what);
     return TAT_ERR_CUDA;
   }
