@@ -619,6 +619,22 @@ __global__ void __launch_bounds__(192, tc::CTAS) k_conv_mid_tc(int B, int H, int
     const int m = 32 * quarter + lane;
     for (int n = 0; n < mine; ++n) {
       const int a = n % NACC;
+      int b, y0, x0;
+      coords(n, b, y0, x0);
+      // OMASK: the mask of the tile's 16-byte chunks m, m + 128, m + 256, m + 384 (pixel
+      // chunk / 4, part chunk mod 4: a warp reads 512 contiguous bytes per load), issued before
+      // the wait for the accumulator so that their latency overlaps it
+      uint4 mk[4];
+      if (OMASK) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int ch = m + 128 * i, pm = ch >> 2;
+          const int y = y0 + (pm >> 3), x = x0 + (pm & 7);
+          mk[i] = y < H && x < W
+                      ? reinterpret_cast<const uint4*>(omask + (((long long)b * H + y) * W + x) * C)[ch & 3]
+                      : make_uint4(0u, 0u, 0u, 0u);
+        }
+      }
       ok = mbar_wait(&afull[a], (unsigned)((n / NACC) & 1));
       ok = epilogue_all(ok);  // one decision for the four warps, which meet at named barriers below
       if (!ok) break;
@@ -627,8 +643,6 @@ __global__ void __launch_bounds__(192, tc::CTAS) k_conv_mid_tc(int B, int H, int
       tmem_ld32(tbase + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(a * 32), r);
       tc_fence_before();
       mbar_arrive(&aempty[a]);
-      int b, y0, x0;
-      coords(n, b, y0, x0);
       uint4 pk[4];  // channels 8q .. 8q+7 of this pixel, BF16
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -645,18 +659,6 @@ __global__ void __launch_bounds__(192, tc::CTAS) k_conv_mid_tc(int B, int H, int
         }
         pk[q] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
       }
-      if (OMASK) {
-        const int y = y0 + (m >> 3), x = x0 + (m & 7);
-        if (y < H && x < W) {
-          const uint4* mk4 = reinterpret_cast<const uint4*>(omask + (((long long)b * H + y) * W + x) * C);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const uint4 mk = mk4[q];
-            pk[q] = make_uint4(relu_masked(pk[q].x, mk.x), relu_masked(pk[q].y, mk.y), relu_masked(pk[q].z, mk.z),
-                               relu_masked(pk[q].w, mk.w));
-          }
-        }
-      }
       // the previous tile's bulk store has finished reading the staging tile
       if (m == 0) asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
       epilogue_sync();
@@ -667,11 +669,184 @@ __global__ void __launch_bounds__(192, tc::CTAS) k_conv_mid_tc(int B, int H, int
         const int c = (q + (m >> 1)) & 3;
         osm[4 * m + c] = c == 0 ? pk[0] : c == 1 ? pk[1] : c == 2 ? pk[2] : pk[3];
       }
+      if (OMASK) {  // mask the staged tile chunk by chunk, as the mask was read
+        epilogue_sync();
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          uint4& o = osm[m + 128 * i];
+          o = make_uint4(relu_masked(o.x, mk[i].x), relu_masked(o.y, mk[i].y), relu_masked(o.z, mk[i].z),
+                         relu_masked(o.w, mk[i].w));
+        }
+      }
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // generic writes, read by the bulk store
       epilogue_sync();
       if (m == 0) tma_store_4d(&map_out, osm, 0, x0, y0, b);  // pixels outside the image are clipped
     }
     if (m == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+  }
+  if (!ok) atomicExch(&g_lpd_timeout, 1);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tbase), "r"(TMEM_COLS) : "memory");
+}
+
+// ---- 32 -> 32 weight gradient on tcgen05 (an already masked gradient G')
+//
+// dW[tap][co][ci] = sum_p G'(p)[co] in(p + tap)[ci] is a GEMM with K = pixels, whose
+// M = 32 output channels are below the 64 / 128 rows of an MMA; so the M rows stack four
+// copies of G' shifted by j = 0..3 pixels along x (both operands MN-major: a pixel's 32
+// channels are one 64-byte row of the swizzled halo, and the four M atoms are 64 B = one
+// pixel apart).  With B = in shifted by (dy - 1, +1), rows (j, co) of chain dy sum
+// G'(Q)[co] in(Q + (dy - 1, 1 - j))[ci] over Q = P + (0, j), P the tile's pixels: the taps
+// (dy, dx = 2 - j) for j = 0, 1, 2 (j = 3 is not used).  The three dy share A: they are the
+// three N atoms of one MMA (N = 96, atoms one in-box row apart).  So that Q still covers
+// every pixel of the image once, the tile columns start one tile left of the image (x0 = -8;
+// the copies fill zeros outside it).  Per 16 x 8-pixel tile: 8 MMAs of M = 128, N = 96,
+// K = 16, accumulated in TMEM over all tiles of the CTA; warp 0 streams the two halos (G'
+// 16 x 11 pixels, in 18 x 8) by TMA, warp 1 issues the MMAs, warps 2-5 add up db from the G'
+// halo meanwhile (a stage is free once both are done with it) and read the sums out once at
+// the end into the per-CTA partials [tap][co][ci] then [co].  Every wait is bounded.
+namespace wg {
+constexpr int TX = 8, TY = 16;
+constexpr int GX = TX + 3, GY = TY;                   // G' box: pixels x0 .. x0+10, rows y0 .. y0+15
+constexpr int IX = TX, IY = TY + 2;                   // in box: pixels x0+1 .. x0+8, rows y0-1 .. y0+16
+constexpr int GSZ = 11264, ISZ = 9216;                // 176 and 144 pixels of 64 B (multiples of 512 B)
+constexpr int SLOT = GSZ + ISZ;                       // one stage
+constexpr int NS = 4;                                 // stages
+constexpr int MOFF = NS * SLOT;                       // mbarriers full[NS], empty[NS], done; TMEM address
+constexpr int SMEM = 512 + MOFF + 128;
+constexpr int TMEM_COLS = 128;                        // D: columns 32 dy + ci (96 used)
+constexpr int CTAS = 152;                             // one per SM: fewer partial sets to add up
+// kind::f16, FP32 D, BF16 A and B, both MN-major (bits 15, 16), N = 96, M = 128
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((96u >> 3) << 17) |
+                           ((128u >> 4) << 24);
+}  // namespace wg
+
+__global__ void __launch_bounds__(192, 1) k_conv_mid_wgrad_tc(int B, int H, int W,
+                                                              const __grid_constant__ CUtensorMap map_g,
+                                                              const __grid_constant__ CUtensorMap map_in,
+                                                              float* __restrict__ partial) {
+  constexpr int NS = wg::NS, SLOT = wg::SLOT, GSZ = wg::GSZ, TMEM_COLS = wg::TMEM_COLS;
+  extern __shared__ unsigned char dsm[];
+  unsigned char* sm = dsm + ((512u - (smem_u32(dsm) & 511u)) & 511u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + wg::MOFF);
+  uint64_t* empty = full + NS;
+  uint64_t* done = empty + NS;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  __shared__ float dbred[4][C];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int k = 0; k < NS; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], 1 + 128);  // the MMAs' commit and the 128 db threads
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tslot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *tslot;
+  const uint32_t sbase = smem_u32(sm);
+  // tiles: image b, tile row ty, tile column tx with x0 = 8 (tx - 1), tx = 0 .. ceil(W / 8)
+  const unsigned tilesx = (W + wg::TX - 1) / wg::TX + 1, tpi = tilesx * ((H + wg::TY - 1) / wg::TY);
+  const unsigned ntiles = (unsigned)B * tpi;
+  const int mine = ntiles > blockIdx.x ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
+  auto coords = [&](int n, int& b, int& y0, int& x0) {
+    const unsigned tile = blockIdx.x + (unsigned)n * gridDim.x, bb = tile / tpi, rr = tile - bb * tpi,
+                   ty = rr / tilesx;
+    b = (int)bb;
+    y0 = (int)ty * wg::TY;
+    x0 = ((int)(rr - ty * tilesx) - 1) * wg::TX;
+  };
+  bool ok = true;
+  if (warp == 0) {
+    if (lane == 0) {  // halo loads
+      int issued = 0;
+      for (int n = 0; n < mine && ok; ++n) {
+        const int k = n % NS;
+        if (n >= NS) ok = mbar_wait(&empty[k], (unsigned)((n / NS + 1) & 1));  // MMAs of tile n - NS done
+        if (!ok) break;
+        int b, y0, x0;
+        coords(n, b, y0, x0);
+        mbar_expect_tx(&full[k], (wg::GX * wg::GY + wg::IX * wg::IY) * 64);
+        tma_load_4d(sm + k * SLOT, &map_g, 0, x0, y0, b, &full[k]);
+        tma_load_4d(sm + k * SLOT + GSZ, &map_in, 0, x0 + 1, y0 - 1, b, &full[k]);
+        issued = n + 1;
+      }
+      if (!ok)  // let the copies in flight land (their slots are not reused after this)
+        for (int n = issued - NS > 0 ? issued - NS : 0; n < issued; ++n)
+          mbar_wait(&full[n % NS], (unsigned)((n / NS) & 1));
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {  // MMAs
+      for (int n = 0; n < mine && ok; ++n) {
+        const int k = n % NS;
+        ok = mbar_wait(&full[k], (unsigned)((n / NS) & 1));
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t gb = sbase + k * SLOT, ib = gb + GSZ;
+#pragma unroll
+        for (int st = 0; st < wg::TY / 2; ++st) {  // K = 16 pixels = tile rows 2 st, 2 st + 1
+          // A: G' from pixel (2 st, 0) of the G' box; M atoms one pixel apart, 8-row groups one box row apart.
+          // B: in from row 2 st of the in box (rows y0 - 1 ..); N atoms (dy) and 8-row groups one box row apart.
+          const uint64_t ad = umma_desc(gb + 2 * st * wg::GX * 64, 64, wg::GX * 64) | kSwizzle64;
+          const uint64_t bd = umma_desc(ib + 2 * st * wg::IX * 64, wg::IX * 64, wg::IX * 64) | kSwizzle64;
+          umma_f16(tbase, ad, bd, wg::IDESC, (n | st) != 0);
+        }
+        umma_commit(&empty[k]);  // stage free once these MMAs have read it
+      }
+    }
+    if (lane == 0) {
+      umma_commit(done);        // arrives once every MMA issued so far has completed
+      mbar_wait(done, 0u);      // (bounded) none is in flight when the TMEM is freed
+    }
+  } else {
+    // db: thread t = co + 32 r adds G'(ky, kx)[co] over the tile rows ky = 4 r .. 4 r + 3 of every
+    // tile (its own 8 columns; zeros outside the image)
+    const int t = tid - 64, co = t & 31, r4 = t >> 5;
+    float db = 0.f;
+    for (int n = 0; n < mine && ok; ++n) {
+      const int k = n % NS;
+      ok = mbar_wait(&full[k], (unsigned)((n / NS) & 1));
+      if (!ok) break;
+      const unsigned char* gt = sm + k * SLOT;
+#pragma unroll
+      for (int ky = 4 * r4; ky < 4 * r4 + 4; ++ky)
+#pragma unroll
+        for (int kx = 0; kx < 8; ++kx) {
+          const int p = ky * wg::GX + kx;
+          db += bf(*reinterpret_cast<const tat_bf16*>(swz(gt, p, co >> 3) + 2 * (co & 7)));
+        }
+      mbar_arrive(&empty[k]);
+    }
+    dbred[r4][co] = db;
+    // read-out: warp w reads TMEM lanes 32 (w mod 4) .. + 31 = rows (j = w mod 4, co = lane)
+    const int j = warp & 3;
+    const bool fin = mbar_wait(done, 0u);
+    ok = __all_sync(0xffffffffu, fin && ok);
+    tc_fence_after();
+    float* out = partial + (size_t)blockIdx.x * (9 * C * C + C);
+    if (j < 3) {
+#pragma unroll 1
+      for (int dy = 0; dy < 3; ++dy) {
+        uint32_t r[32];
+        tmem_ld32(tbase + ((uint32_t)(32 * j) << 16) + (uint32_t)(32 * dy), r);
+        float* dst = out + ((3 * dy + 2 - j) * C + lane) * C;  // dW[tap = 3 dy + dx][co][ci], dx = 2 - j
+#pragma unroll
+        for (int ci = 0; ci < C; ++ci) dst[ci] = mine > 0 ? __uint_as_float(r[ci]) : 0.f;
+      }
+    }
+    asm volatile("bar.sync 2, 128;\n" ::: "memory");  // dbred complete
+    if (t < C) out[9 * C * C + t] = dbred[0][t] + dbred[1][t] + dbred[2][t] + dbred[3][t];
   }
   if (!ok) atomicExch(&g_lpd_timeout, 1);
   tc_fence_before();
@@ -1552,6 +1727,19 @@ tat_status in_bwd(int batch, int H, int W, const float* x0, const float* x1, con
   return launched("tat_conv_in_bwd");
 }
 
+// Tensor maps of k_conv_mid_wgrad_tc: 32 channels x `bx` x `by` pixels, 64-byte swizzle.
+bool wgrad_tc_map(CUtensorMap* m, const tat_bf16* base, int batch, int H, int W, int bx, int by) {
+  const EncodeTiled fn = encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)batch};
+  const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+  const cuuint32_t box[4] = {(cuuint32_t)C, (cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t estride[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<tat_bf16*>(base), dims, strides, box, estride,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int wgrad_ctas(int batch, int H, int W) {
   const long long tiles = (long long)batch * ((H + TY - 1) / TY) * ((W + TX - 1) / TX);
   return (int)(tiles < kMaxCtas ? tiles : kMaxCtas);
@@ -1673,16 +1861,25 @@ tat_status tat_conv_mid_bwd_weights(int batch, int H, int W, const tat_bf16* h_i
     fprintf(stderr, "tat_conv_mid_bwd_weights: tensor map encoding failed\n");
     return TAT_ERR_CUDA;
   }
+  int ctas_used = ctas;
   if (h_out) {
     if (!smem_attr<k_conv_mid_wgrad<true>>(wgrad_smem_bytes())) return TAT_ERR_CUDA;
     k_conv_mid_wgrad<true><<<ctas, 288, wgrad_smem_bytes(), s>>>(batch, H, W, mi, mg, mh, scratch);
-  } else {
-    if (!smem_attr<k_conv_mid_wgrad<false>>(wgrad_smem_bytes())) return TAT_ERR_CUDA;
-    k_conv_mid_wgrad<false><<<ctas, 288, wgrad_smem_bytes(), s>>>(batch, H, W, mi, mg, mh, scratch);
+  } else {  // an already masked gradient: tcgen05, one CTA per SM
+    CUtensorMap tg, ti;
+    if (!wgrad_tc_map(&tg, g_out, batch, H, W, wg::GX, wg::GY) ||
+        !wgrad_tc_map(&ti, h_in, batch, H, W, wg::IX, wg::IY)) {
+      fprintf(stderr, "tat_conv_mid_bwd_weights: tensor map encoding failed\n");
+      return TAT_ERR_CUDA;
+    }
+    const long long tiles = (long long)batch * ((H + wg::TY - 1) / wg::TY) * ((W + wg::TX - 1) / wg::TX + 1);
+    ctas_used = (int)(tiles < wg::CTAS ? tiles : wg::CTAS);
+    if (!smem_attr<k_conv_mid_wgrad_tc>(wg::SMEM)) return TAT_ERR_CUDA;
+    k_conv_mid_wgrad_tc<<<ctas_used, 192, wg::SMEM, s>>>(batch, H, W, tg, ti, scratch);
   }
   tat_status st = launched("tat_conv_mid_bwd_weights");
   if (st != TAT_OK) return st;
-  k_reduce_partials<<<(nw + 31) / 32, 256, 0, s>>>(ctas, 9 * C * C, C, scratch, gw, gb);
+  k_reduce_partials<<<(nw + 31) / 32, 256, 0, s>>>(ctas_used, 9 * C * C, C, scratch, gw, gb);
   return launched("tat_conv_mid_bwd_weights");
 }
 
