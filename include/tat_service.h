@@ -98,7 +98,8 @@ tat_status tat_service_get_stats(tat_service_t svc, tat_service_stats* stats);
  * 2, 4, 8, 16, 32 half-plane columns per CTA in the column stages and 1, 2, 4
  * row pairs per CTA in the row stages (those within the device limits), then,
  * for the best of those, column CTAs of 64 and 128 threads (instead of 256;
- * four-step column lengths only) with half, the same and twice its strip -- on
+ * four-step column lengths only) with half, the same and twice its strip, and
+ * the best shape with and without programmatic dependent launch of the stages -- on
  * one A then one A* of `batch` images at f (device, batch*n*n floats, output
  * of A* written to f_out) with g (batch*n_det*n_t floats) and the workspace
  * for `batch`, and keeps the fastest for every later call on this plan.  The

@@ -22,28 +22,27 @@ tat_status launch_adjoint(const tat_plan_s* Pl, int batch, const float* g, long 
   dispatch_ang(P.n_det, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_theta_adj<L>>(dev);
-    k_theta_adj<L><<<s.theta_grid, s.theta_block, s.theta_smem, st>>>(P, g, gs, Y, ys, c.t_tile, c.nt_det);
+    ok &= pdl_launch(c.pdl != 0, k_theta_adj<L>, s.theta_grid, s.theta_block, s.theta_smem, st, P, g, gs, Y, ys, c.t_tile, c.nt_det) == cudaSuccess;
     stage_done();
   });
   dispatch_2M(2 * P.M, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_modes_adj<L>>(dev);
-    k_modes_adj<L><<<s.modes_grid, s.modes_block, s.modes_smem, st>>>(P, Y, ys, X, xs, c.nt_2M);
+    ok &= pdl_launch(c.pdl != 0, k_modes_adj<L>, s.modes_grid, s.modes_block, s.modes_smem, st, P, Y, ys, X, xs, c.nt_2M) == cudaSuccess;
     stage_done();
   });
   dispatch_ang(P.n_phi, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_rings_adj<L>>(dev);
-    k_rings_adj<L><<<s.rings_grid, s.rings_block, s.rings_smem, st>>>(P, X, xs, Y, ys, c.rings_per_cta, c.nt_phi,
-                                                                      s.ntiles);
+    ok &= pdl_launch(c.pdl != 0, k_rings_adj<L>, s.rings_grid, s.rings_block, s.rings_smem, st, P, X, xs, Y, ys, c.rings_per_cta, c.nt_phi, s.ntiles) == cudaSuccess;
     stage_done();
   });
   dispatch_N(P.N, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_cols_adj<L>>(dev) && ensure_smem<k_rows_adj<L>>(dev);
-    k_cols_adj<L><<<s.cols_grid_a, s.cols_block, s.cols_smem_a, st>>>(P, Y, ys, X, xs, c.strip, c.nt_N, batch);
+    ok &= pdl_launch(c.pdl != 0, k_cols_adj<L>, s.cols_grid_a, s.cols_block, s.cols_smem_a, st, P, Y, ys, X, xs, c.strip, c.nt_N, batch) == cudaSuccess;
     stage_done();
-    k_rows_adj<L><<<s.rows_grid, s.rows_block, s.rows_smem, st>>>(P, X, xs, f, fs, c.rows_pairs, c.nt_rows);
+    ok &= pdl_launch(c.pdl != 0, k_rows_adj<L>, s.rows_grid, s.rows_block, s.rows_smem, st, P, X, xs, f, fs, c.rows_pairs, c.nt_rows) == cudaSuccess;
     stage_done();
   });
   return check_launch(ok);

@@ -46,28 +46,27 @@ tat_status launch_forward(const tat_plan_s* Pl, int batch, const float* f, long 
   dispatch_N(P.N, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_rows_fwd<L>>(dev) && ensure_smem<k_cols_fwd<L>>(dev);
-    k_rows_fwd<L><<<s.rows_grid, s.rows_block, s.rows_smem, st>>>(P, f, fs, X, xs, c.rows_pairs, c.nt_rows);
+    ok &= pdl_launch(c.pdl != 0, k_rows_fwd<L>, s.rows_grid, s.rows_block, s.rows_smem, st, P, f, fs, X, xs, c.rows_pairs, c.nt_rows) == cudaSuccess;
     stage_done();
-    k_cols_fwd<L><<<s.cols_grid_f, s.cols_block, s.cols_smem_f, st>>>(P, X, xs, Y, ys, c.strip, c.nt_N, batch);
+    ok &= pdl_launch(c.pdl != 0, k_cols_fwd<L>, s.cols_grid_f, s.cols_block, s.cols_smem_f, st, P, X, xs, Y, ys, c.strip, c.nt_N, batch) == cudaSuccess;
     stage_done();
   });
   dispatch_ang(P.n_phi, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_rings_fwd<L>>(dev);
-    k_rings_fwd<L><<<s.rings_grid, s.rings_block, s.rings_smem, st>>>(P, Y, ys, X, xs, c.rings_per_cta, c.nt_phi,
-                                                                      s.ntiles);
+    ok &= pdl_launch(c.pdl != 0, k_rings_fwd<L>, s.rings_grid, s.rings_block, s.rings_smem, st, P, Y, ys, X, xs, c.rings_per_cta, c.nt_phi, s.ntiles) == cudaSuccess;
     stage_done();
   });
   dispatch_2M(2 * P.M, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_modes_fwd<L>>(dev);
-    k_modes_fwd<L><<<s.modes_grid, s.modes_block, s.modes_smem, st>>>(P, X, xs, Y, ys, c.nt_2M);
+    ok &= pdl_launch(c.pdl != 0, k_modes_fwd<L>, s.modes_grid, s.modes_block, s.modes_smem, st, P, X, xs, Y, ys, c.nt_2M) == cudaSuccess;
     stage_done();
   });
   dispatch_ang(P.n_det, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_theta_fwd<L>>(dev);
-    k_theta_fwd<L><<<s.theta_grid, s.theta_block, s.theta_smem, st>>>(P, Y, ys, g, gs, c.t_tile, c.nt_det);
+    ok &= pdl_launch(c.pdl != 0, k_theta_fwd<L>, s.theta_grid, s.theta_block, s.theta_smem, st, P, Y, ys, g, gs, c.t_tile, c.nt_det) == cudaSuccess;
     stage_done();
   });
   return check_launch(ok);

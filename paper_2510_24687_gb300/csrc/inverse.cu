@@ -28,37 +28,34 @@ tat_status launch_inverse(const tat_plan_s* Pl, int batch, const float* g, long 
   dispatch_ang(P.n_det, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_theta_adj<L>>(dev);
-    k_theta_adj<L><<<s.theta_grid, s.theta_block, s.theta_smem, st>>>(P, g, gs, Y, ys, c.t_tile, c.nt_det);
+    ok &= pdl_launch(c.pdl != 0, k_theta_adj<L>, s.theta_grid, s.theta_block, s.theta_smem, st, P, g, gs, Y, ys, c.t_tile, c.nt_det) == cudaSuccess;
     stage_done();
   });
   dispatch_2M(2 * P.M, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_modes_inv<L>>(dev);
-    k_modes_inv<L><<<s.modes_grid, s.modes_block, s.modes_smem, st>>>(P, Y, ys, X, xs, c.nt_2M);
+    ok &= pdl_launch(c.pdl != 0, k_modes_inv<L>, s.modes_grid, s.modes_block, s.modes_smem, st, P, Y, ys, X, xs, c.nt_2M) == cudaSuccess;
     stage_done();
   });
   dispatch_ang(P.n_phi, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_rings_adj<L, true>>(dev);
     const dim3 grid(s.ntiles, batch);
-    k_rings_adj<L, true><<<grid, s.rings_block, s.rings_smem, st>>>(P, X, xs, Y, ys, c.rings_per_cta, c.nt_phi,
-                                                                     s.ntiles);
+    ok &= pdl_launch(c.pdl != 0, k_rings_adj<L, true>, grid, s.rings_block, s.rings_smem, st, P, X, xs, Y, ys, c.rings_per_cta, c.nt_phi, s.ntiles) == cudaSuccess;
     stage_done();
   });
   dispatch_N(P.N, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_cols_inv<L>>(dev) && ensure_smem<k_rows_inv<L>>(dev);
-    k_cols_inv<L><<<s.cols_grid_a, s.cols_block, s.cols_smem_i, st>>>(P, Y, ys, X, xs, c.strip, c.nt_N, batch, acc,
-                                                                      accs);
+    ok &= pdl_launch(c.pdl != 0, k_cols_inv<L>, s.cols_grid_a, s.cols_block, s.cols_smem_i, st, P, Y, ys, X, xs, c.strip, c.nt_N, batch, acc, accs) == cudaSuccess;
     stage_done();
-    k_rows_inv<L><<<s.rows_grid, s.rows_block, s.rows_smem, st>>>(P, X, xs, f, fs, acc, accs, c.rows_pairs,
-                                                                  c.nt_rows);
+    ok &= pdl_launch(c.pdl != 0, k_rows_inv<L>, s.rows_grid, s.rows_block, s.rows_smem, st, P, X, xs, f, fs, acc, accs, c.rows_pairs, c.nt_rows) == cudaSuccess;
     stage_done();
   });
   {
     const long long count = (long long)batch * P.n * P.n;
     const int blocks = (int)std::min<long long>((count + 255) / 256, 152LL * 8);
-    k_inv_finish<<<blocks, 256, 0, st>>>(P, batch, acc, accs, f, fs);
+    ok &= pdl_launch(c.pdl != 0, k_inv_finish, blocks, 256, 0, st, P, batch, acc, accs, f, fs) == cudaSuccess;
     stage_done();
   }
   return check_launch(ok);

@@ -23,6 +23,7 @@
 // are processed; the other halves follow from Hermitian symmetry (f real).
 #pragma once
 
+#include "pdl.cuh"
 #include "fft.cuh"
 #include "plan.hpp"
 
@@ -51,6 +52,7 @@ __device__ __forceinline__ int wrapN(int q, int N) { return q < 0 ? q + N : q; }
 template <int L>
 __global__ void TAT_ROWS_BOUNDS k_rows_fwd(DevPlan P, const float* __restrict__ f, long long fs,
                                                    float2* __restrict__ X, long long xs, int RP, int nt) {
+  TAT_GRID_DEPENDENCY();
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
   const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
@@ -111,6 +113,7 @@ __device__ __forceinline__ void strip_and_image(int batch, int* strip, int* b) {
 template <int L>
 __global__ void TAT_COLS_BOUNDS_F k_cols_fwd(DevPlan P, const float2* __restrict__ X, long long xs,
                                            float2* __restrict__ Y, long long ys, int S, int nt, int batch) {
+  TAT_GRID_DEPENDENCY();
   extern __shared__ float2 sm[];
   int strip, b;
   strip_and_image(batch, &strip, &b);
@@ -173,6 +176,7 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
 template <int L>
 __global__ void __launch_bounds__(1024) k_rings_fwd(DevPlan P, const float2* __restrict__ Y, long long ys, float2* __restrict__ X,
                             long long xs, int /*rings per CTA*/, int nt, int ntiles) {
+  TAT_GRID_DEPENDENCY();
   constexpr int RPC = rings_per_cta_for(L);
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
@@ -242,6 +246,7 @@ __global__ void __launch_bounds__(1024) k_rings_fwd(DevPlan P, const float2* __r
 template <int L>
 __global__ void __launch_bounds__(1024) k_modes_fwd(DevPlan P, const float2* __restrict__ X, long long xs, float2* __restrict__ Y,
                             long long ys, int nt) {
+  TAT_GRID_DEPENDENCY();
   extern __shared__ float2 sm[];
   const int b = blockIdx.y, k = blockIdx.x;
   const int J1 = P.J + 1, L2 = 2 * P.M;
@@ -293,6 +298,7 @@ __device__ __forceinline__ float2 folded_mode(const DevPlan& P, const float2* G,
 template <int L>
 __global__ void __launch_bounds__(1024) k_theta_fwd(DevPlan P, const float2* __restrict__ Y, long long ys, float* __restrict__ g,
                             long long gs, int /*time tile*/, int nt) {
+  TAT_GRID_DEPENDENCY();
   constexpr int TT = time_tile_for(L);
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
@@ -336,6 +342,7 @@ __global__ void __launch_bounds__(1024) k_theta_fwd(DevPlan P, const float2* __r
 template <int L>
 __global__ void __launch_bounds__(1024) k_theta_adj(DevPlan P, const float* __restrict__ g, long long gs, float2* __restrict__ Y,
                             long long ys, int /*time tile*/, int nt) {
+  TAT_GRID_DEPENDENCY();
   constexpr int TT = time_tile_for(L);
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
@@ -383,6 +390,7 @@ __global__ void __launch_bounds__(1024) k_theta_adj(DevPlan P, const float* __re
 template <int L>
 __global__ void __launch_bounds__(1024) k_modes_adj(DevPlan P, const float2* __restrict__ Y, long long ys, float2* __restrict__ X,
                             long long xs, int nt) {
+  TAT_GRID_DEPENDENCY();
   extern __shared__ float2 sm[];
   const int b = blockIdx.y, k = blockIdx.x;
   const int J1 = P.J + 1, L2 = 2 * P.M;
@@ -432,6 +440,7 @@ __global__ void __launch_bounds__(1024) k_modes_adj(DevPlan P, const float2* __r
 template <int L, bool INV = false>
 __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __restrict__ X, long long xs, float2* __restrict__ Y,
                             long long ys, int /*rings per CTA*/, int nt, int ntiles) {
+  TAT_GRID_DEPENDENCY();
   constexpr int RPC = rings_per_cta_for(L);
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
@@ -575,6 +584,7 @@ __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* _
 template <int L>
 __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict__ Y, long long ys,
                                            float2* __restrict__ X, long long xs, int S, int nt, int batch) {
+  TAT_GRID_DEPENDENCY();
   extern __shared__ float2 sm[];
   int strip, b;
   strip_and_image(batch, &strip, &b);
@@ -664,6 +674,7 @@ __device__ __forceinline__ void rows_inverse_dft(const DevPlan& P, const float2*
 template <int L>
 __global__ void TAT_ROWS_BOUNDS k_rows_adj(DevPlan P, const float2* __restrict__ X, long long xs, float* __restrict__ f,
                            long long fs, int RP, int nt) {
+  TAT_GRID_DEPENDENCY();
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
   const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
@@ -699,6 +710,7 @@ __global__ void TAT_ROWS_BOUNDS k_rows_adj(DevPlan P, const float2* __restrict__
 template <int L>
 __global__ void __launch_bounds__(1024) k_modes_inv(DevPlan P, const float2* __restrict__ Y, long long ys,
                                                     float2* __restrict__ X, long long xs, int nt) {
+  TAT_GRID_DEPENDENCY();
   extern __shared__ float2 sm[];
   const int b = blockIdx.y, k = blockIdx.x;
   const int J1 = P.J + 1, L2 = 2 * P.M;
@@ -782,6 +794,7 @@ template <int L>
 __global__ void TAT_COLS_BOUNDS_I k_cols_inv(DevPlan P, const float2* __restrict__ Y, long long ys,
                                            float2* __restrict__ X, long long xs, int S, int nt, int batch,
                                            float* acc, long long accs) {
+  TAT_GRID_DEPENDENCY();
   extern __shared__ float2 sm[];
   int strip, b;
   strip_and_image(batch, &strip, &b);
@@ -819,6 +832,7 @@ template <int L>
 __global__ void TAT_ROWS_BOUNDS k_rows_inv(DevPlan P, const float2* __restrict__ X, long long xs,
                                                    float* __restrict__ f, long long fs, float* acc, long long accs,
                                                    int RP, int nt) {
+  TAT_GRID_DEPENDENCY();
   extern __shared__ float2 sm[];
   const int b = blockIdx.y;
   const int g = threadIdx.x / nt, gt = threadIdx.x % nt;
@@ -858,6 +872,7 @@ __global__ void TAT_ROWS_BOUNDS k_rows_inv(DevPlan P, const float2* __restrict__
 // Step 8: f = Pi_Omega0 (v + C), C = -(sum of v over Omega \ Omega0) / (its node count).
 __global__ void k_inv_finish(DevPlan P, int batch, const float* __restrict__ acc, long long accs, float* f,
                              long long fs) {
+  TAT_GRID_DEPENDENCY();
   const long long nn = (long long)P.n * P.n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn * batch;
        i += (long long)gridDim.x * blockDim.x) {

@@ -24,6 +24,7 @@
 #include <cstdio>
 #include <mutex>
 
+#include "pdl.cuh"
 #include "tat_lpd.h"
 
 namespace {
@@ -61,6 +62,7 @@ int blocks_for(long long n, int threads) {
 // gb[e - nw_w].  A block covers 32 outputs (lanes); its 8 warps split the CTAs.
 __global__ void __launch_bounds__(256) k_reduce_partials(int nctas, int nw_w, int nb, const float* __restrict__ partial,
                                                          float* gw, float* gb) {
+  TAT_GRID_DEPENDENCY();
   __shared__ float red[8][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = nw_w + nb;
@@ -373,6 +375,7 @@ __global__ void __launch_bounds__(256) k_conv_mid(int B, int H, int W, const __g
                                                   const __grid_constant__ CUtensorMap map_omask,
                                                   const tat_bf16* __restrict__ w, const float* __restrict__ bias,
                                                   tat_bf16* __restrict__ out) {
+  TAT_GRID_DEPENDENCY();
   extern __shared__ unsigned char dsm[];
   unsigned char* sm = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);  // 1024-aligned (swizzle period)
   constexpr int NT = 1 + MASK + OMASK;
@@ -502,6 +505,7 @@ __global__ void __launch_bounds__(192, tc::CTAS) k_conv_mid_tc(int B, int H, int
                                                         const __grid_constant__ CUtensorMap map_out,
                                                         const tat_bf16* __restrict__ w, const float* __restrict__ bias,
                                                         const tat_bf16* __restrict__ omask) {
+  TAT_GRID_DEPENDENCY();
   constexpr int TX = tc::TX, TY = tc::TY, HX = tc::HX, SLOT = tc::SLOT, WOFF = tc::WOFF;
   constexpr int BOFF = tc::BOFF, MOFF = tc::MOFF, HALO_TX = tc::HALO_TX, TMEM_COLS = tc::TMEM_COLS, NS = tc::NS;
   constexpr int NACC = tc::NACC;
@@ -728,6 +732,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_mid_wgrad_tc(int B, int H, int 
                                                               const __grid_constant__ CUtensorMap map_g,
                                                               const __grid_constant__ CUtensorMap map_in,
                                                               float* __restrict__ partial) {
+  TAT_GRID_DEPENDENCY();
   constexpr int NS = wg::NS, SLOT = wg::SLOT, GSZ = wg::GSZ, TMEM_COLS = wg::TMEM_COLS;
   extern __shared__ unsigned char dsm[];
   unsigned char* sm = dsm + ((512u - (smem_u32(dsm) & 511u)) & 511u);
@@ -873,6 +878,7 @@ __global__ void __launch_bounds__(288, 2) k_conv_mid_wgrad(int B, int H, int W, 
                                                            const __grid_constant__ CUtensorMap map_g,
                                                            const __grid_constant__ CUtensorMap map_h,
                                                            float* __restrict__ partial) {
+  TAT_GRID_DEPENDENCY();
   constexpr int STAGE = 3 * HALO_SLOT;
   extern __shared__ unsigned char dsm[];
   unsigned char* sm = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
@@ -1001,6 +1007,7 @@ __global__ void __launch_bounds__(256) k_conv_in_fwd(int B, int H, int W, const 
                                                      const float* __restrict__ x1, const float* __restrict__ x2,
                                                      const tat_bf16* __restrict__ w, const float* __restrict__ bias,
                                                      tat_bf16* __restrict__ h) {
+  TAT_GRID_DEPENDENCY();
   constexpr int KV = 9 * CIN;
   __shared__ __align__(16) unsigned short xs[CIN * XH * XW];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -1097,6 +1104,7 @@ __global__ void __launch_bounds__(256, 2) k_conv_in_bwd(int B, int H, int W, con
                                                         const float* __restrict__ x2, const tat_bf16* __restrict__ w,
                                                         float* gx0, float* gx1, float* gx2, int accumulate, int parts,
                                                         float* __restrict__ partial) {
+  TAT_GRID_DEPENDENCY();
   using L = InBwdSmem<CIN, MASK>;
   constexpr int KV = 9 * CIN, NTW = L::NTW, STAGE = L::STAGE, XCOPY = L::XCOPY;
   const bool DATA = parts & 1, WGRAD = parts & 2;
@@ -1288,6 +1296,7 @@ constexpr size_t out_bwd_smem_bytes() { return 1024 + 2 * HALO_SLOT + 4 * XH * X
 __global__ void __launch_bounds__(256) k_conv_out_fwd(int B, int H, int W, const __grid_constant__ CUtensorMap map_h,
                                                       const tat_bf16* __restrict__ w, const float* __restrict__ bias,
                                                       const float* residual, float* out) {
+  TAT_GRID_DEPENDENCY();
   extern __shared__ unsigned char dsm[];
   unsigned char* sm = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
   float* zs = reinterpret_cast<float*>(sm + 2 * HALO_SLOT);
@@ -1361,6 +1370,7 @@ template <bool MASK>
 __global__ void __launch_bounds__(256, 2) k_conv_out_bwd(int B, int H, int W, const __grid_constant__ CUtensorMap map_h,
                                                          const float* __restrict__ gout, const tat_bf16* __restrict__ w,
                                                          tat_bf16* __restrict__ gh, float* __restrict__ partial) {
+  TAT_GRID_DEPENDENCY();
   constexpr int PART = 2 * XH * XP, CPY = XH * XP;  // gs[part][copy][XH][XP]
   extern __shared__ unsigned char dsm[];
   unsigned char* sm = dsm + ((1024u - (smem_u32(dsm) & 1023u)) & 1023u);
@@ -1521,6 +1531,7 @@ __global__ void __launch_bounds__(256, 2) k_conv_out_bwd(int B, int H, int W, co
 
 __global__ void k_adam(long long n, float lr, float b1, float b2, float eps, float c1, float c2, float* p,
                        const float* __restrict__ g, float* m, float* v, tat_bf16* wb) {
+  TAT_GRID_DEPENDENCY();
   GRID_STRIDE(i, n) {
     const float gi = g[i];
     const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -1534,15 +1545,18 @@ __global__ void k_adam(long long n, float lr, float b1, float b2, float eps, flo
 }
 
 __global__ void k_fill(long long n, float value, float* out) {
+  TAT_GRID_DEPENDENCY();
   GRID_STRIDE(i, n) out[i] = value;
 }
 
 __global__ void k_to_bf16(long long n, const float* __restrict__ x, tat_bf16* out) {
+  TAT_GRID_DEPENDENCY();
   GRID_STRIDE(i, n) out[i] = tobf(x[i]);
 }
 
 __global__ void k_mse(long long n, const float* __restrict__ a, const float* __restrict__ b, float scale, float* grad,
                       float* loss) {
+  TAT_GRID_DEPENDENCY();
   float s = 0.f;
   GRID_STRIDE(i, n) {
     const float d = a[i] - b[i];
@@ -1666,7 +1680,7 @@ tat_status launch_mid_tc(int batch, int H, int W, const CUtensorMap& m8, const t
   }
   const long long tiles = (long long)batch * ((H + tc::TY - 1) / tc::TY) * ((W + tc::TX - 1) / tc::TX);
   const int ctas = (int)(tiles < tc::CTAS * 152 ? tiles : tc::CTAS * 152);  // persistent: all resident
-  k_conv_mid_tc<BWD, OMASK><<<ctas, 192, smem, s>>>(batch, H, W, m8, mo, w, b, omask);
+  tat::pdl_launch(true, k_conv_mid_tc<BWD, OMASK>, ctas, 192, smem, s, batch, H, W, m8, mo, w, b, omask);
   return launched(what);
 }
 
@@ -1682,7 +1696,7 @@ tat_status launch_mid(int batch, int H, int W, const tat_bf16* in, const tat_bf1
   }
   constexpr size_t smem = mid_smem_bytes<1 + MASK + OMASK>();
   if (!smem_attr<k_conv_mid<BWD, MASK, OMASK>>(smem)) return TAT_ERR_CUDA;
-  k_conv_mid<BWD, MASK, OMASK><<<mid_ctas(batch, H, W), 256, smem, s>>>(batch, H, W, mi, mm, mo, w, b, out);
+  tat::pdl_launch(true, k_conv_mid<BWD, MASK, OMASK>, mid_ctas(batch, H, W), 256, smem, s, batch, H, W, mi, mm, mo, w, b, out);
   return launched(what);
 }
 
@@ -1698,8 +1712,7 @@ tat_status launch_in_bwd(int batch, int H, int W, const CUtensorMap& mg, const C
                          int accumulate, int parts, float* scratch, int ctas, cudaStream_t s) {
   constexpr size_t smem = InBwdSmem<CIN, MASK>::BYTES;
   if (!smem_attr<k_conv_in_bwd<CIN, MASK>>(smem)) return TAT_ERR_CUDA;
-  k_conv_in_bwd<CIN, MASK><<<ctas, 256, smem, s>>>(batch, H, W, mg, mh, x0, x1, x2, w, gx0, gx1, gx2, accumulate,
-                                                    parts, scratch);
+  tat::pdl_launch(true, k_conv_in_bwd<CIN, MASK>, ctas, 256, smem, s, batch, H, W, mg, mh, x0, x1, x2, w, gx0, gx1, gx2, accumulate, parts, scratch);
   return launched("tat_conv_in_bwd");
 }
 
@@ -1723,7 +1736,7 @@ tat_status in_bwd(int batch, int H, int W, const float* x0, const float* x1, con
         : launch_in_bwd<CIN, false>(batch, H, W, mg, mh, x0, x1, x2, w, gx0, gx1, gx2, accumulate, parts, scratch, ctas,
                                     s);
   if (st != TAT_OK || !wgrad) return st;
-  k_reduce_partials<<<(nw + 31) / 32, 256, 0, s>>>(ctas, 9 * CIN * C, C, scratch, gw, gb);
+  tat::pdl_launch(true, k_reduce_partials, (nw + 31) / 32, 256, 0, s, ctas, 9 * CIN * C, C, scratch, gw, gb);
   return launched("tat_conv_in_bwd");
 }
 
@@ -1760,8 +1773,8 @@ tat_status tat_conv_in_fwd(int batch, int H, int W, int cin, const float* x0, co
     return TAT_ERR_INVALID_ARG;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int ctas = thin_ctas(batch, H, W, 3);
-  if (cin == 2) k_conv_in_fwd<2><<<ctas, 256, 0, s>>>(batch, H, W, x0, x1, nullptr, w, b, h);
-  else k_conv_in_fwd<3><<<ctas, 256, 0, s>>>(batch, H, W, x0, x1, x2, w, b, h);
+  if (cin == 2) tat::pdl_launch(true, k_conv_in_fwd<2>, ctas, 256, 0, s, batch, H, W, x0, x1, nullptr, w, b, h);
+  else tat::pdl_launch(true, k_conv_in_fwd<3>, ctas, 256, 0, s, batch, H, W, x0, x1, x2, w, b, h);
   return launched("tat_conv_in_fwd");
 }
 
@@ -1864,7 +1877,7 @@ tat_status tat_conv_mid_bwd_weights(int batch, int H, int W, const tat_bf16* h_i
   int ctas_used = ctas;
   if (h_out) {
     if (!smem_attr<k_conv_mid_wgrad<true>>(wgrad_smem_bytes())) return TAT_ERR_CUDA;
-    k_conv_mid_wgrad<true><<<ctas, 288, wgrad_smem_bytes(), s>>>(batch, H, W, mi, mg, mh, scratch);
+    tat::pdl_launch(true, k_conv_mid_wgrad<true>, ctas, 288, wgrad_smem_bytes(), s, batch, H, W, mi, mg, mh, scratch);
   } else {  // an already masked gradient: tcgen05, one CTA per SM
     CUtensorMap tg, ti;
     if (!wgrad_tc_map(&tg, g_out, batch, H, W, wg::GX, wg::GY) ||
@@ -1875,11 +1888,11 @@ tat_status tat_conv_mid_bwd_weights(int batch, int H, int W, const tat_bf16* h_i
     const long long tiles = (long long)batch * ((H + wg::TY - 1) / wg::TY) * ((W + wg::TX - 1) / wg::TX + 1);
     ctas_used = (int)(tiles < wg::CTAS ? tiles : wg::CTAS);
     if (!smem_attr<k_conv_mid_wgrad_tc>(wg::SMEM)) return TAT_ERR_CUDA;
-    k_conv_mid_wgrad_tc<<<ctas_used, 192, wg::SMEM, s>>>(batch, H, W, tg, ti, scratch);
+    tat::pdl_launch(true, k_conv_mid_wgrad_tc, ctas_used, 192, wg::SMEM, s, batch, H, W, tg, ti, scratch);
   }
   tat_status st = launched("tat_conv_mid_bwd_weights");
   if (st != TAT_OK) return st;
-  k_reduce_partials<<<(nw + 31) / 32, 256, 0, s>>>(ctas_used, 9 * C * C, C, scratch, gw, gb);
+  tat::pdl_launch(true, k_reduce_partials, (nw + 31) / 32, 256, 0, s, ctas_used, 9 * C * C, C, scratch, gw, gb);
   return launched("tat_conv_mid_bwd_weights");
 }
 
@@ -1892,8 +1905,7 @@ tat_status tat_conv_out_fwd(int batch, int H, int W, const tat_bf16* h, const ta
     return TAT_ERR_CUDA;
   }
   if (!smem_attr<k_conv_out_fwd>(out_fwd_smem_bytes())) return TAT_ERR_CUDA;
-  k_conv_out_fwd<<<thin_ctas(batch, H, W, 3), 256, out_fwd_smem_bytes(), static_cast<cudaStream_t>(stream)>>>(
-      batch, H, W, mh, w, b, residual, out);
+  tat::pdl_launch(true, k_conv_out_fwd, thin_ctas(batch, H, W, 3), 256, out_fwd_smem_bytes(), static_cast<cudaStream_t>(stream), batch, H, W, mh, w, b, residual, out);
   return launched("tat_conv_out_fwd");
 }
 
@@ -1912,14 +1924,14 @@ tat_status tat_conv_out_bwd(int batch, int H, int W, const float* g_out, const t
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (mask_relu) {
     if (!smem_attr<k_conv_out_bwd<true>>(out_bwd_smem_bytes())) return TAT_ERR_CUDA;
-    k_conv_out_bwd<true><<<ctas, 256, out_bwd_smem_bytes(), s>>>(batch, H, W, mh, g_out, w, g_h, scratch);
+    tat::pdl_launch(true, k_conv_out_bwd<true>, ctas, 256, out_bwd_smem_bytes(), s, batch, H, W, mh, g_out, w, g_h, scratch);
   } else {
     if (!smem_attr<k_conv_out_bwd<false>>(out_bwd_smem_bytes())) return TAT_ERR_CUDA;
-    k_conv_out_bwd<false><<<ctas, 256, out_bwd_smem_bytes(), s>>>(batch, H, W, mh, g_out, w, g_h, scratch);
+    tat::pdl_launch(true, k_conv_out_bwd<false>, ctas, 256, out_bwd_smem_bytes(), s, batch, H, W, mh, g_out, w, g_h, scratch);
   }
   tat_status st = launched("tat_conv_out_bwd");
   if (st != TAT_OK) return st;
-  k_reduce_partials<<<(9 * C + 1 + 31) / 32, 256, 0, s>>>(ctas, 9 * C, 1, scratch, gw, gb);
+  tat::pdl_launch(true, k_reduce_partials, (9 * C + 1 + 31) / 32, 256, 0, s, ctas, 9 * C, 1, scratch, gw, gb);
   return launched("tat_conv_out_bwd");
 }
 
@@ -1927,27 +1939,26 @@ tat_status tat_adam(long long count, float lr, float beta1, float beta2, float e
                     const float* grad, float* m, float* v, tat_bf16* w_bf16, tat_stream_t stream) {
   if (count <= 0 || step < 1 || !param || !grad || !m || !v) return TAT_ERR_INVALID_ARG;
   const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
-  k_adam<<<blocks_for(count, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(count, lr, beta1, beta2, eps, c1, c2,
-                                                                                 param, grad, m, v, w_bf16);
+  tat::pdl_launch(true, k_adam, blocks_for(count, 256), 256, 0, static_cast<cudaStream_t>(stream), count, lr, beta1, beta2, eps, c1, c2, param, grad, m, v, w_bf16);
   return launched("tat_adam");
 }
 
 tat_status tat_fill(long long count, float value, float* out, tat_stream_t stream) {
   if (count <= 0 || !out) return TAT_ERR_INVALID_ARG;
-  k_fill<<<blocks_for(count, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(count, value, out);
+  tat::pdl_launch(true, k_fill, blocks_for(count, 256), 256, 0, static_cast<cudaStream_t>(stream), count, value, out);
   return launched("tat_fill");
 }
 
 tat_status tat_to_bf16(long long count, const float* x, tat_bf16* out, tat_stream_t stream) {
   if (count <= 0 || !x || !out) return TAT_ERR_INVALID_ARG;
-  k_to_bf16<<<blocks_for(count, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(count, x, out);
+  tat::pdl_launch(true, k_to_bf16, blocks_for(count, 256), 256, 0, static_cast<cudaStream_t>(stream), count, x, out);
   return launched("tat_to_bf16");
 }
 
 tat_status tat_mse(long long count, const float* a, const float* b, float scale, float* grad, float* loss,
                    tat_stream_t stream) {
   if (count <= 0 || !a || !b || !loss) return TAT_ERR_INVALID_ARG;
-  k_mse<<<blocks_for(count, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(count, a, b, scale, grad, loss);
+  tat::pdl_launch(true, k_mse, blocks_for(count, 256), 256, 0, static_cast<cudaStream_t>(stream), count, a, b, scale, grad, loss);
   return launched("tat_mse");
 }
 

@@ -581,6 +581,7 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
   c.rows_pairs = d.N == 8192 ? 1 : std::max(1, std::min(4, 1024 / c.nt_rows));
   c.strip = 8;
   c.cols_threads = std::max(c.nt_N, 256);
+  c.pdl = d.N <= 2048;  // measured: +13 % pairs/s at N = 1024, B = 8; -2 % at N = 4096, B = 32
   c.rings_per_cta = rings_per_cta_for(n_phi);
   c.t_tile = time_tile_for(n_det);
   // Workspace per image (float2): X holds row spectra (n x N/2) or per-mode

@@ -98,6 +98,7 @@ struct LaunchCfg {
   int nt_N, nt_phi, nt_2M, nt_det;  // threads per FFT of each length
   int nt_rows;        // threads per row transform (the four-step lengths need 256)
   int cols_threads;   // threads per CTA of the column pass (>= nt_N; fewer than 256 only for four-step lengths)
+  int pdl;            // 1: stages launched with programmatic dependent launch (outside graph capture)
 };
 
 }  // namespace tat

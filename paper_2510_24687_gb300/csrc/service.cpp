@@ -502,6 +502,12 @@ tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, flo
       plan->cfg.strip = strip;
       trial();
     }
+  // and the stages with and without programmatic dependent launch
+  if (err == TAT_OK) {
+    plan->cfg = best;
+    plan->cfg.pdl = !best.pdl;
+    trial();
+  }
   plan->cfg = err == TAT_OK ? best : base;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 
+#include "pdl.cuh"
 #include "tat_solvers.h"
 
 namespace {
@@ -57,6 +58,7 @@ __device__ __forceinline__ float div_at(const float* px, const float* py, long l
 __global__ void k_axpby_clamp(long long count, float a, const float* __restrict__ x, float b,
                               const float* __restrict__ y, float lo, const float* __restrict__ mask,
                               long long period, float* out) {
+  TAT_GRID_DEPENDENCY();
   TAT_GRID_STRIDE(i, count) {
     float v = a * x[i];
     if (y != nullptr) v += b * y[i];
@@ -69,6 +71,7 @@ __global__ void k_axpby_clamp(long long count, float a, const float* __restrict_
 __global__ void k_axpby_clamp_backward(long long count, const float* __restrict__ out, float lo,
                                        const float* __restrict__ mask, long long period,
                                        const float* __restrict__ go, float a, float* gx, float b, float* gy) {
+  TAT_GRID_DEPENDENCY();
   TAT_GRID_STRIDE(i, count) {
     float G = out[i] > lo ? go[i] : 0.f;
     if (mask != nullptr) G *= mask[i % period];
@@ -79,6 +82,7 @@ __global__ void k_axpby_clamp_backward(long long count, const float* __restrict_
 
 __global__ void k_pd_dual_data(long long count, float sigma, float inv, const float* __restrict__ Af,
                                const float* __restrict__ g, const float* q_in, float* q_out) {
+  TAT_GRID_DEPENDENCY();
   TAT_GRID_STRIDE(i, count) { q_out[i] = (q_in[i] + sigma * (Af[i] - g[i])) * inv; }
 }
 
@@ -98,6 +102,7 @@ __device__ __forceinline__ Pix pixel(long long i, int n, long long nn) {
 
 __global__ void k_tv_dual(int batch, int n, float ih, float sigma, float bound, const float* __restrict__ fbar,
                           const float* p_in, float* p_out) {
+  TAT_GRID_DEPENDENCY();
   const long long nn = (long long)n * n;
   TAT_GRID_STRIDE(i, nn * batch) {
     const Pix P = pixel(i, n, nn);
@@ -115,6 +120,7 @@ __global__ void k_tv_dual(int batch, int n, float ih, float sigma, float bound, 
 __global__ void k_tv_dual_backward(int batch, int n, float ih, float sigma, float bound,
                                    const float* __restrict__ fbar, const float* __restrict__ p_in,
                                    const float* __restrict__ go, float* gp) {
+  TAT_GRID_DEPENDENCY();
   const long long nn = (long long)n * n;
   TAT_GRID_STRIDE(i, nn * batch) {
     const Pix P = pixel(i, n, nn);
@@ -139,6 +145,7 @@ __global__ void k_tv_dual_backward(int batch, int n, float ih, float sigma, floa
 
 // out = scale * div_h(field) per image (the grad_h^T half of the dual backward).
 __global__ void k_scaled_div(int batch, int n, float ih, float scale, const float* __restrict__ field, float* out) {
+  TAT_GRID_DEPENDENCY();
   const long long nn = (long long)n * n;
   TAT_GRID_STRIDE(i, nn * batch) {
     const Pix P = pixel(i, n, nn);
@@ -150,6 +157,7 @@ __global__ void k_scaled_div(int batch, int n, float ih, float scale, const floa
 __global__ void k_tv_primal(int batch, int n, float ih, float tau, const float* __restrict__ Asq,
                             const float* __restrict__ p, const float* __restrict__ mask, const float* f_in,
                             float* f_out, float* fbar) {
+  TAT_GRID_DEPENDENCY();
   const long long nn = (long long)n * n;
   TAT_GRID_STRIDE(i, nn * batch) {
     const Pix P = pixel(i, n, nn);
@@ -177,6 +185,7 @@ __device__ __forceinline__ float primal_D(const float* f_out, const float* mask,
 __global__ void k_tv_primal_backward(int batch, int n, float ih, float tau, const float* __restrict__ f_out,
                                      const float* __restrict__ mask, const float* __restrict__ gfo,
                                      const float* __restrict__ gfb, float* gf, float* gA, float* gp) {
+  TAT_GRID_DEPENDENCY();
   const long long nn = (long long)n * n;
   TAT_GRID_STRIDE(i, nn * batch) {
     const Pix P = pixel(i, n, nn);
@@ -202,8 +211,7 @@ extern "C" {
 tat_status tat_axpby_clamp(long long count, float a, const float* x, float b, const float* y, float lo,
                            const float* mask, long long mask_period, float* out, tat_stream_t stream) {
   if (count <= 0 || !x || !out || (mask && mask_period <= 0)) return TAT_ERR_INVALID_ARG;
-  k_axpby_clamp<<<blocks_for(count), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
-      count, a, x, b, y, lo, mask, mask ? mask_period : 1, out);
+  tat::pdl_launch(true, k_axpby_clamp, blocks_for(count), kThreads, 0, static_cast<cudaStream_t>(stream), count, a, x, b, y, lo, mask, mask ? mask_period : 1, out);
   return launched("tat_axpby_clamp");
 }
 
@@ -212,16 +220,14 @@ tat_status tat_axpby_clamp_backward(long long count, const float* out, float lo,
                                     float* grad_y, tat_stream_t stream) {
   if (count <= 0 || !out || !grad_out || (mask && mask_period <= 0)) return TAT_ERR_INVALID_ARG;
   if (!grad_x && !grad_y) return TAT_OK;
-  k_axpby_clamp_backward<<<blocks_for(count), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
-      count, out, lo, mask, mask ? mask_period : 1, grad_out, a, grad_x, b, grad_y);
+  tat::pdl_launch(true, k_axpby_clamp_backward, blocks_for(count), kThreads, 0, static_cast<cudaStream_t>(stream), count, out, lo, mask, mask ? mask_period : 1, grad_out, a, grad_x, b, grad_y);
   return launched("tat_axpby_clamp_backward");
 }
 
 tat_status tat_pd_dual_data(long long count, float sigma, const float* Af, const float* g, const float* q_in,
                             float* q_out, tat_stream_t stream) {
   if (count <= 0 || !Af || !g || !q_in || !q_out || !(sigma > 0.f)) return TAT_ERR_INVALID_ARG;
-  k_pd_dual_data<<<blocks_for(count), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
-      count, sigma, 1.f / (1.f + sigma), Af, g, q_in, q_out);
+  tat::pdl_launch(true, k_pd_dual_data, blocks_for(count), kThreads, 0, static_cast<cudaStream_t>(stream), count, sigma, 1.f / (1.f + sigma), Af, g, q_in, q_out);
   return launched("tat_pd_dual_data");
 }
 
@@ -230,8 +236,7 @@ tat_status tat_tv_dual(int batch, int n, float h_eff, float sigma, float bound, 
   if (bad_image_args(batch, n, h_eff) || !(sigma > 0.f) || !(bound > 0.f) || !fbar || !p_in || !p_out)
     return TAT_ERR_INVALID_ARG;
   const long long count = (long long)batch * n * n;
-  k_tv_dual<<<blocks_for(count), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(batch, n, 1.f / h_eff, sigma,
-                                                                                     bound, fbar, p_in, p_out);
+  tat::pdl_launch(true, k_tv_dual, blocks_for(count), kThreads, 0, static_cast<cudaStream_t>(stream), batch, n, 1.f / h_eff, sigma, bound, fbar, p_in, p_out);
   return launched("tat_tv_dual");
 }
 
@@ -243,11 +248,10 @@ tat_status tat_tv_dual_backward(int batch, int n, float h_eff, float sigma, floa
     return TAT_ERR_INVALID_ARG;
   const long long count = (long long)batch * n * n;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  k_tv_dual_backward<<<blocks_for(count), kThreads, 0, s>>>(batch, n, 1.f / h_eff, sigma, bound, fbar, p_in,
-                                                             grad_p_out, grad_p_in);
+  tat::pdl_launch(true, k_tv_dual_backward, blocks_for(count), kThreads, 0, s, batch, n, 1.f / h_eff, sigma, bound, fbar, p_in, grad_p_out, grad_p_in);
   const tat_status st = launched("tat_tv_dual_backward");
   if (st != TAT_OK || !grad_fbar) return st;
-  k_scaled_div<<<blocks_for(count), kThreads, 0, s>>>(batch, n, 1.f / h_eff, -sigma, grad_p_in, grad_fbar);
+  tat::pdl_launch(true, k_scaled_div, blocks_for(count), kThreads, 0, s, batch, n, 1.f / h_eff, -sigma, grad_p_in, grad_fbar);
   return launched("tat_tv_dual_backward");
 }
 
@@ -256,8 +260,7 @@ tat_status tat_tv_primal(int batch, int n, float h_eff, float tau, const float* 
   if (bad_image_args(batch, n, h_eff) || !(tau > 0.f) || !Asq || !p || !f_in || !f_out || !fbar)
     return TAT_ERR_INVALID_ARG;
   const long long count = (long long)batch * n * n;
-  k_tv_primal<<<blocks_for(count), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(batch, n, 1.f / h_eff, tau, Asq,
-                                                                                       p, mask, f_in, f_out, fbar);
+  tat::pdl_launch(true, k_tv_primal, blocks_for(count), kThreads, 0, static_cast<cudaStream_t>(stream), batch, n, 1.f / h_eff, tau, Asq, p, mask, f_in, f_out, fbar);
   return launched("tat_tv_primal");
 }
 
@@ -266,8 +269,7 @@ tat_status tat_tv_primal_backward(int batch, int n, float h_eff, float tau, cons
                                   float* grad_p, tat_stream_t stream) {
   if (bad_image_args(batch, n, h_eff) || !(tau > 0.f) || !f_out) return TAT_ERR_INVALID_ARG;
   const long long count = (long long)batch * n * n;
-  k_tv_primal_backward<<<blocks_for(count), kThreads, 0, static_cast<cudaStream_t>(stream)>>>(
-      batch, n, 1.f / h_eff, tau, f_out, mask, grad_f_out, grad_fbar, grad_f_in, grad_Asq, grad_p);
+  tat::pdl_launch(true, k_tv_primal_backward, blocks_for(count), kThreads, 0, static_cast<cudaStream_t>(stream), batch, n, 1.f / h_eff, tau, f_out, mask, grad_f_out, grad_fbar, grad_f_in, grad_Asq, grad_p);
   return launched("tat_tv_primal_backward");
 }
 
