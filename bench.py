@@ -53,10 +53,11 @@ def parse_args():
     p.add_argument("--train-steps", type=int, default=1500, help="lpd workload: training steps before evaluation")
     p.add_argument("--arc", choices=["full", "half"], default="full",
                    help="lpd workload: detectors on the full circle, or on theta in [0, pi) (limited view)")
-    p.add_argument("--workload", choices=["pair", "solves", "inverse", "service", "lpd"], default="pair",
+    p.add_argument("--workload", choices=["pair", "solves", "inverse", "service", "lpd", "lpd_layers"], default="pair",
                    help="pair: the A+A* throughput line (default); solves: batched NNLS + TV-PDHG "
                         "reconstructions; inverse: the approximate inverse (Algorithm 3); service: 64 mixed-size "
-                        "requests through the batching runtime; lpd: learned primal-dual training")
+                        "requests through the batching runtime; lpd: learned primal-dual training; lpd_layers: "
+                        "rounds of the seven dual-net convolution calls (the profiling driver of the LPD kernels)")
     return p.parse_args()
 
 
@@ -486,6 +487,8 @@ def main():
         return run_service(args, rank, world, local)
     if args.workload == "lpd":
         return run_lpd(args, rank, world, local)
+    if args.workload == "lpd_layers":
+        return run_lpd_layers(args, rank, world, local)
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -1049,11 +1052,10 @@ def lpd_oracle_seconds():
     return (time.perf_counter() - t0) * (LPD_K / 2) * LPD_B
 
 
-def lpd_kernel_roofline(pkg, stream, dev, peaks):
-    """Per-call time of each convolution call of the dual net (B = 8 planes of 256 x 256, the larger
-    of the two nets; each call runs K times per training step), measured live with events on
-    `stream`, and the roofline of the slowest one against the tighter of its ALU (or tensor) and
-    HBM bounds."""
+def lpd_calls(pkg, stream, dev):
+    """The seven convolution calls of the dual net (B = 8 planes of 256 x 256, the larger of the
+    two nets) on seeded random data: name -> (call, algorithmic flops, algorithmic HBM bytes,
+    compute bound, kernels launched)."""
     import torch
     B, H, W, C = LPD_B, LPD_DET, LPD_T, 32
     P = B * H * W
@@ -1085,13 +1087,13 @@ def lpd_kernel_roofline(pkg, stream, dev, peaks):
             4 * P * 27 * C, P * (2 * C + 24), "tensor", "k_conv_in_bwd<3, 0> + k_reduce_partials"),
         "tat_conv_mid_fwd": (
             lambda: pkg.tat_conv_mid_fwd(B, H, W, a(h_in), a(w_mid), a(bias), a(h_out), s),
-            2 * P * 9 * C * C, P * 4 * C, "tensor", "k_conv_mid<0, 0, 0>"),
+            2 * P * 9 * C * C, P * 4 * C, "tensor", "k_conv_mid_tc<0, 0>"),
         "tat_conv_mid_bwd_data (pre-masked, masks its output)": (
             lambda: pkg.tat_conv_mid_bwd_data(B, H, W, a(g_h), 0, a(w_mid), a(h_in), a(g_in), s),
-            2 * P * 9 * C * C, P * 6 * C, "tensor", "k_conv_mid<1, 0, 1>"),
+            2 * P * 9 * C * C, P * 6 * C, "tensor", "k_conv_mid_tc<1, 1>"),
         "tat_conv_mid_bwd_weights (pre-masked)": (
             lambda: pkg.tat_conv_mid_bwd_weights(B, H, W, a(h_in), a(g_h), 0, a(scr), nscr, a(gw), a(gb), s),
-            2 * P * 9 * C * C, P * 4 * C, "tensor", "k_conv_mid_wgrad<0> + k_reduce_partials"),
+            2 * P * 9 * C * C, P * 4 * C, "tensor", "k_conv_mid_wgrad_tc + k_reduce_partials"),
         "tat_conv_out_fwd": (
             lambda: pkg.tat_conv_out_fwd(B, H, W, a(h_out), a(w_out), a(bias), a(x[0]), a(out), s),
             2 * P * 9 * C, P * (2 * C + 8), "tensor", "k_conv_out_fwd"),
@@ -1100,6 +1102,16 @@ def lpd_kernel_roofline(pkg, stream, dev, peaks):
                                          s),
             4 * P * 9 * C, P * (4 + 4 * C), "tensor", "k_conv_out_bwd<1> + k_reduce_partials"),
     }
+    return calls
+
+
+def lpd_kernel_roofline(pkg, stream, dev, peaks):
+    """Per-call time of each convolution call of the dual net (each call runs K times per training
+    step), measured live with events on `stream`, and the roofline of the slowest one against the
+    tighter of its ALU (or tensor) and HBM bounds."""
+    import torch
+    B, H, W = LPD_B, LPD_DET, LPD_T
+    calls = lpd_calls(pkg, stream, dev)
     reps = 20
     times = {}
     for name, (fn, *_rest) in calls.items():
@@ -1128,12 +1140,49 @@ def lpd_kernel_roofline(pkg, stream, dev, peaks):
         r = {"bound": kind, "achieved": flops / t / 1e12, "peak": peak_tc if kind == "tensor" else peak_alu,
              "unit": "TFLOP/s"}
     r["frac"] = r["achieved"] / r["peak"]
-    r.update({"traffic": None, "kernel": dom, "kernels": kernels, "call_us": 1e3 * times[dom],
+    # DRAM bytes of the call's kernels from the committed ncu capture, if taken on the current kernels
+    r.update({"traffic": traffic_for(dom, "lpd_dual_n256_b8", ("lpd.cu", "pdl.cuh"), key="dram_bytes_per_call"),
+              "kernel": dom, "kernels": kernels, "call_us": 1e3 * times[dom],
               "algorithmic": {"flops": flops, "hbm_bytes": nbytes},
               "peak_source": "measured" if peaks else "fallback",
               "call_us_all": {k: round(1e3 * v, 2) for k, v in times.items()},
               "workload": f"dual net, {B} x {H} x {W} pixels, 32 channels"})
     return r
+
+
+def run_lpd_layers(args, rank, world, local):
+    """W + K rounds of the seven dual-net convolution calls, in the order of `lpd_calls` (10
+    kernel launches a round); prints the per-round time.  One device, no replicas: this is the
+    driver for profiling the LPD kernels (e.g. ncu -s 10 -c 10 captures the second round)."""
+    import torch
+    if rank != 0:
+        return
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2510_24687_gb300 as pkg
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    calls = lpd_calls(pkg, stream, dev)
+    for _ in range(args.warmup):
+        for fn, *_rest in calls.values():
+            fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        for fn, *_rest in calls.values():
+            fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pkg.tat_lpd_check()
+    ms = e0.elapsed_time(e1) / max(1, args.steps)
+    print(json.dumps({"metric": "rounds/s of the seven dual-net LPD convolution calls", "value": 1e3 / ms,
+                      "unit": "rounds/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                      "dtype": "bf16", "data": "synthetic (seeded random activations and weights)",
+                      "config": {"workload": "dual net, 8 x 256 x 256 pixels, 32 channels, calls: " +
+                                 ", ".join(calls)}, "gpu_launches": 10 * args.steps}))
 
 
 def run_lpd(args, rank, world, local):
