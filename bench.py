@@ -640,7 +640,7 @@ def main():
                 "config": workload_config(B), "roofline": roofline, "hbm_roofline_pair": hbm,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 10 * args.steps, "comparisons": comparisons,
                 "launch_shapes": ({"autotuned": True, "strip": tuned[1], "row_pairs": tuned[2],
-                                   "cols_threads": tuned[3], "autotune_ms_pair_batch": tuned[0]}
+                                   "cols_threads": tuned[3], "row_threads": tuned[4], "autotune_ms_pair_batch": tuned[0]}
                                   if tuned else {"autotuned": False}),
                 "clocks": clk, "plan": {k: info[k] for k in ("N", "M", "J", "n_phi", "n_low", "n_points")},
                 "kernel_source_hash": kernel_source_hash()}
@@ -1374,7 +1374,7 @@ def run_lpd(args, rank, world, local):
                 "config": lpd_config(args.train_steps, args.arc),
                 "comparison_ms_per_step": {"graph": ms, "eager": ms_eager, "operators_only_4K_calls": ms_ops},
                 "operator_launch_shapes": {"ms_pair": net.tuned[0], "strip": net.tuned[1], "row_pairs": net.tuned[2],
-                                           "cols_threads": net.tuned[3]}
+                                           "cols_threads": net.tuned[3], "row_threads": net.tuned[4]}
                 if net.tuned else None,
                 "reconstruction_rel_l2_test": {"lpd": err_lpd, "tv_ls": err_tv, "tv_alpha": best_alpha,
                                                "nnls": err_nnls},

@@ -98,25 +98,30 @@ tat_status tat_service_get_stats(tat_service_t svc, tat_service_stats* stats);
  * 2, 4, 8, 16, 32 half-plane columns per CTA in the column stages and 1, 2, 4
  * row pairs per CTA in the row stages (those within the device limits), then,
  * for the best of those, column CTAs of 64 and 128 threads (instead of 256;
- * four-step column lengths only) with half, the same and twice its strip, and
- * the best shape with and without programmatic dependent launch of the stages -- on
+ * four-step column lengths only) with half, the same and twice its strip, then
+ * row groups of 64 and 128 threads (instead of 256; lengths N <= 1024) with 1, 2
+ * and 4 times its row pairs, and the best shape with and without programmatic
+ * dependent launch of the stages -- on
  * one A then one A* of `batch` images at f (device, batch*n*n floats, output
  * of A* written to f_out) with g (batch*n_det*n_t floats) and the workspace
  * for `batch`, and keeps the fastest for every later call on this plan.  The
  * shapes only regroup work: results are unchanged (up to the rounding order
  * of the adjoint's shared-memory atomics).  Synchronises `stream`.  *ms_best
  * (optional) receives the chosen shape's time for the pair, *strip,
- * *row_pairs and *cols_threads (optional) the chosen knobs. */
+ * *row_pairs, *cols_threads and *row_threads (optional) the chosen knobs. */
 tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, float* f_out, void* workspace,
-                             tat_stream_t stream, double* ms_best, int* strip, int* row_pairs, int* cols_threads);
+                             tat_stream_t stream, double* ms_best, int* strip, int* row_pairs, int* cols_threads,
+                             int* row_threads);
 
 /* Sets the same knobs directly (for instance to reuse shapes tuned earlier): `strip`
  * columns per column CTA, `row_pairs` per row CTA, `cols_threads` threads per column
- * CTA (a multiple of 32; below 256 only for the four-step column lengths 512 .. 4096).
- * TAT_ERR_UNSUPPORTED, with the plan unchanged, for shapes outside the device or kernel
- * limits.  Results do not depend on the shapes (up to the rounding order of the
- * adjoint's shared-memory atomics).  Host only. */
-tat_status tat_plan_set_launch_shape(tat_plan_t plan, int strip, int row_pairs, int cols_threads);
+ * CTA (a multiple of 32; below 256 only for the four-step column lengths 512 .. 4096),
+ * `row_threads` threads per row pair (a multiple of 32 for the four-step lengths up to
+ * 4096, else the plan's own; 0 keeps the current value).  TAT_ERR_UNSUPPORTED, with the
+ * plan unchanged, for shapes outside the device or kernel limits.  Results do not depend
+ * on the shapes (up to the rounding order of the adjoint's shared-memory atomics).  Host
+ * only. */
+tat_status tat_plan_set_launch_shape(tat_plan_t plan, int strip, int row_pairs, int cols_threads, int row_threads);
 
 #ifdef __cplusplus
 }

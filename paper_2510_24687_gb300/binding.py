@@ -110,8 +110,8 @@ def load() -> ctypes.CDLL:
         "tat_service_latency": (_I, [_P, _LL, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
         "tat_service_get_stats": (_I, [_P, ctypes.POINTER(tat_service_stats)]),
         "tat_plan_autotune": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_I),
-                                   ctypes.POINTER(_I), ctypes.POINTER(_I)]),
-        "tat_plan_set_launch_shape": (_I, [_P, _I, _I, _I]),
+                                   ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+        "tat_plan_set_launch_shape": (_I, [_P, _I, _I, _I, _I]),
         "tat_lpd_scratch_floats": (ctypes.c_size_t, [_I, _I, _I]),
         "tat_conv_in_fwd": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P]),
         "tat_conv_in_bwd_data": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _I, _P]),
@@ -301,17 +301,19 @@ def tat_tv_primal_backward(batch, n, h_eff, tau, f_out_ptr, mask_ptr, grad_f_out
                                          grad_p_ptr or None, stream or None), "tat_tv_primal_backward")
 
 
-def tat_plan_set_launch_shape(plan, strip, row_pairs, cols_threads):
-    _check(load().tat_plan_set_launch_shape(plan, strip, row_pairs, cols_threads), "tat_plan_set_launch_shape")
+def tat_plan_set_launch_shape(plan, strip, row_pairs, cols_threads, row_threads=0):
+    _check(load().tat_plan_set_launch_shape(plan, strip, row_pairs, cols_threads, row_threads),
+           "tat_plan_set_launch_shape")
 
 
 def tat_plan_autotune(plan, batch, f_ptr, g_ptr, f_out_ptr, ws_ptr, stream=0):
     """Times the runtime launch shapes on one A + A* of `batch` images; returns
-    (ms, strip, row_pairs, cols_threads)."""
-    ms, strip, rp, ct = _D(0), _I(0), _I(0), _I(0)
+    (ms, strip, row_pairs, cols_threads, row_threads)."""
+    ms, strip, rp, ct, rt = _D(0), _I(0), _I(0), _I(0), _I(0)
     _check(load().tat_plan_autotune(plan, batch, f_ptr, g_ptr, f_out_ptr, ws_ptr, stream or None, ctypes.byref(ms),
-                                    ctypes.byref(strip), ctypes.byref(rp), ctypes.byref(ct)), "tat_plan_autotune")
-    return ms.value, strip.value, rp.value, ct.value
+                                    ctypes.byref(strip), ctypes.byref(rp), ctypes.byref(ct), ctypes.byref(rt)),
+           "tat_plan_autotune")
+    return ms.value, strip.value, rp.value, ct.value, rt.value
 
 
 def tat_service_config_default() -> tat_service_config:
@@ -492,7 +494,7 @@ class TatOperator:
     def autotune(self, batch):
         """Times the column-strip, row-pair and column-CTA launch shapes on one A + A* of `batch`
         zero images and keeps the fastest for this plan (tat_plan_autotune); returns (ms, strip,
-        row_pairs, cols_threads)."""
+        row_pairs, cols_threads, row_threads)."""
         torch = self.torch
         f = torch.zeros((batch, self.n, self.n), dtype=torch.float32, device=self.device)
         g = torch.zeros((batch, self.n_det, self.n_t), dtype=torch.float32, device=self.device)

@@ -21,6 +21,8 @@ tat_status validate_shapes(const tat_plan_s* Pl) {
   // the Stockham column FFT runs on nt_N threads of the CTA; the four-step one on any multiple of 32
   const bool four = N == 512 || N == 1024 || N == 2048 || N == 4096 || N == 8192;
   if (!four && (s.cols_block < Pl->cfg.nt_N || s.cols_block < 256)) return TAT_ERR_UNSUPPORTED;
+  // a row group runs the Stockham FFT on exactly nt_N threads; the four-step one on any multiple of 32
+  if (four ? Pl->cfg.nt_rows % 32 != 0 : Pl->cfg.nt_rows != Pl->cfg.nt_N) return TAT_ERR_UNSUPPORTED;
   if (N == 8192 && s.rows_block > 512) return TAT_ERR_UNSUPPORTED;  // launch bound of the row kernels there
   for (size_t m : smem)
     if (m > mx) return TAT_ERR_UNSUPPORTED;

@@ -59,23 +59,26 @@ int blocks_for(long long n, int threads) {
 // ------------------------------------------------------------------ weight-gradient partial sums
 
 // out[e] += sum over CTAs of partial[cta][e] (fixed order); e < nw_w goes to gw[e], the rest to
-// gb[e - nw_w].  A block covers 32 outputs (lanes); its 8 warps split the CTAs.
-__global__ void __launch_bounds__(256) k_reduce_partials(int nctas, int nw_w, int nb, const float* __restrict__ partial,
-                                                         float* gw, float* gb) {
+// gb[e - nw_w].  A block covers 32 outputs (lanes); its 32 warps split the CTAs, so that each
+// warp adds about ten partials (the sums are short, latency-bound chains otherwise).
+__global__ void __launch_bounds__(1024) k_reduce_partials(int nctas, int nw_w, int nb, const float* __restrict__ partial,
+                                                          float* gw, float* gb) {
   TAT_GRID_DEPENDENCY();
-  __shared__ float red[8][32];
+  __shared__ float red[32][33];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nw = nw_w + nb;
   const int e = blockIdx.x * 32 + lane;
   float s = 0.f;
-  if (e < nw)
-    for (int c = warp; c < nctas; c += 8) s += partial[(size_t)c * nw + e];
+  if (e < nw) {
+#pragma unroll 4
+    for (int c = warp; c < nctas; c += 32) s += partial[(size_t)c * nw + e];
+  }
   red[warp][lane] = s;
   __syncthreads();
   if (warp == 0 && e < nw) {
     float t = 0.f;
 #pragma unroll
-    for (int w = 0; w < 8; ++w) t += red[w][lane];
+    for (int w = 0; w < 32; ++w) t += red[w][lane];
     if (e < nw_w) gw[e] += t;
     else gb[e - nw_w] += t;
   }
@@ -1736,7 +1739,7 @@ tat_status in_bwd(int batch, int H, int W, const float* x0, const float* x1, con
         : launch_in_bwd<CIN, false>(batch, H, W, mg, mh, x0, x1, x2, w, gx0, gx1, gx2, accumulate, parts, scratch, ctas,
                                     s);
   if (st != TAT_OK || !wgrad) return st;
-  tat::pdl_launch(true, k_reduce_partials, (nw + 31) / 32, 256, 0, s, ctas, 9 * CIN * C, C, scratch, gw, gb);
+  tat::pdl_launch(true, k_reduce_partials, (nw + 31) / 32, 1024, 0, s, ctas, 9 * CIN * C, C, scratch, gw, gb);
   return launched("tat_conv_in_bwd");
 }
 
@@ -1892,7 +1895,7 @@ tat_status tat_conv_mid_bwd_weights(int batch, int H, int W, const tat_bf16* h_i
   }
   tat_status st = launched("tat_conv_mid_bwd_weights");
   if (st != TAT_OK) return st;
-  tat::pdl_launch(true, k_reduce_partials, (nw + 31) / 32, 256, 0, s, ctas_used, 9 * C * C, C, scratch, gw, gb);
+  tat::pdl_launch(true, k_reduce_partials, (nw + 31) / 32, 1024, 0, s, ctas_used, 9 * C * C, C, scratch, gw, gb);
   return launched("tat_conv_mid_bwd_weights");
 }
 
@@ -1931,7 +1934,7 @@ tat_status tat_conv_out_bwd(int batch, int H, int W, const float* g_out, const t
   }
   tat_status st = launched("tat_conv_out_bwd");
   if (st != TAT_OK) return st;
-  tat::pdl_launch(true, k_reduce_partials, (9 * C + 1 + 31) / 32, 256, 0, s, ctas, 9 * C, 1, scratch, gw, gb);
+  tat::pdl_launch(true, k_reduce_partials, (9 * C + 1 + 31) / 32, 1024, 0, s, ctas, 9 * C, 1, scratch, gw, gb);
   return launched("tat_conv_out_bwd");
 }
 

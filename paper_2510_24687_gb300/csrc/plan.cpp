@@ -571,8 +571,9 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
   }
   // Launch shapes.
   LaunchCfg& c = P->cfg;
-  // Lengths RA*256 (RA = 2..32) use the in-place four-step transform, which
-  // needs 256 threads; up to 4 row pairs (1024 threads) per CTA.
+  // Lengths RA*256 (RA = 2..32) use the in-place four-step transform, 256 threads
+  // per row pair by default (any multiple of 32 works); up to 4 row pairs (1024
+  // threads) per CTA.
   const bool four_step = d.N == 512 || d.N == 1024 || d.N == 2048 || d.N == 4096 || d.N == 8192;
   c.nt_rows = four_step ? std::max(c.nt_N, 256) : c.nt_N;
   // the four-step transform needs groups of at least 64 threads (step B of RA = 4)

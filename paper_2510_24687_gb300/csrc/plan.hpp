@@ -96,7 +96,8 @@ struct LaunchCfg {
   int rings_per_cta;  // rings per CTA in the angular pass
   int t_tile;         // time samples per CTA in the theta pass (even)
   int nt_N, nt_phi, nt_2M, nt_det;  // threads per FFT of each length
-  int nt_rows;        // threads per row transform (the four-step lengths need 256)
+  int nt_rows;        // threads per row-pair transform (256 by default for the four-step lengths; 64 or 128
+                      // keep more of them busy in the second pass at N <= 1024)
   int cols_threads;   // threads per CTA of the column pass (>= nt_N; fewer than 256 only for four-step lengths)
   int pdl;            // 1: stages launched with programmatic dependent launch (outside graph capture)
 };

@@ -380,7 +380,8 @@ tat_status tat_service_flush(tat_service_t S) {
       float* gbuf = s.op == TAT_OP_PAIR ? s.mid : (s.op == TAT_OP_FORWARD ? s.out : s.in);
       cudaMemsetAsync(fbuf, 0, img * sizeof(float) * s.cap, s.stream);
       cudaMemsetAsync(gbuf, 0, dat * sizeof(float) * s.cap, s.stream);
-      e = tat_plan_autotune(s.plan, s.cap, fbuf, gbuf, fbuf, s.ws, s.stream, nullptr, nullptr, nullptr, nullptr);
+      e = tat_plan_autotune(s.plan, s.cap, fbuf, gbuf, fbuf, s.ws, s.stream, nullptr, nullptr, nullptr, nullptr,
+                            nullptr);
       drop_graphs(s);
       s.tuned = true;
     }
@@ -437,12 +438,13 @@ tat_status tat_service_get_stats(tat_service_t S, tat_service_stats* out) {
   return TAT_OK;
 }
 
-tat_status tat_plan_set_launch_shape(tat_plan_t plan, int strip, int row_pairs, int cols_threads) {
-  if (!plan || strip < 1 || row_pairs < 1 || cols_threads < 32) return TAT_ERR_INVALID_ARG;
+tat_status tat_plan_set_launch_shape(tat_plan_t plan, int strip, int row_pairs, int cols_threads, int row_threads) {
+  if (!plan || strip < 1 || row_pairs < 1 || cols_threads < 32 || row_threads < 0) return TAT_ERR_INVALID_ARG;
   const tat::LaunchCfg old = plan->cfg;
   plan->cfg.strip = strip;
   plan->cfg.rows_pairs = row_pairs;
   plan->cfg.cols_threads = cols_threads;
+  if (row_threads > 0) plan->cfg.nt_rows = row_threads;
   if (row_pairs * plan->cfg.nt_rows > 1024 || tat::validate_shapes(plan) != TAT_OK) {
     plan->cfg = old;
     return TAT_ERR_UNSUPPORTED;
@@ -451,7 +453,8 @@ tat_status tat_plan_set_launch_shape(tat_plan_t plan, int strip, int row_pairs, 
 }
 
 tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, float* f_out, void* workspace,
-                             tat_stream_t stream, double* ms_best, int* strip_out, int* rp_out, int* cols_threads_out) {
+                             tat_stream_t stream, double* ms_best, int* strip_out, int* rp_out, int* cols_threads_out,
+                             int* row_threads_out) {
   if (!plan || batch < 1 || !f || !g || !f_out || !workspace) return TAT_ERR_INVALID_ARG;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   const tat::LaunchCfg base = plan->cfg;
@@ -502,6 +505,17 @@ tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, flo
       plan->cfg.strip = strip;
       trial();
     }
+  // then fewer threads per row pair (more pairs per CTA) for the four-step lengths up to 1024
+  const tat::LaunchCfg second = best;
+  if (plan->d.N <= 1024)
+    for (int threads : {64, 128})
+      for (int rp : {second.rows_pairs, 2 * second.rows_pairs, 4 * second.rows_pairs}) {
+        if (err != TAT_OK || threads >= second.nt_rows || rp * threads > 1024) continue;
+        plan->cfg = second;
+        plan->cfg.nt_rows = threads;
+        plan->cfg.rows_pairs = rp;
+        trial();
+      }
   // and the stages with and without programmatic dependent launch
   if (err == TAT_OK) {
     plan->cfg = best;
@@ -516,6 +530,7 @@ tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, flo
   if (strip_out) *strip_out = best.strip;
   if (rp_out) *rp_out = best.rows_pairs;
   if (cols_threads_out) *cols_threads_out = best.cols_threads;
+  if (row_threads_out) *row_threads_out = best.nt_rows;
   return TAT_OK;
 }
 

@@ -62,7 +62,7 @@ def test_null_handles_are_rejected(pkg):
     assert lib.tat_adjoint_batched(None, 1, None, 0, None, 0, None, None) == 1
     assert lib.tat_plan_destroy(None) == 1
     assert lib.tat_workspace_size(None, 1) == 0
-    assert lib.tat_plan_set_launch_shape(None, 8, 1, 256) == 1
+    assert lib.tat_plan_set_launch_shape(None, 8, 1, 256, 0) == 1
 
 
 def test_plan_create_without_device_fails_cleanly(pkg):

@@ -260,8 +260,10 @@ def test_lpd_training_reduces_loss_and_graph_matches(pkg, torch):
         lg.append(float(graph.train_step(yd, fd, graph=True).item()))
     assert le[-1] < 0.5 * le[0] and lg[-1] < 0.5 * lg[0]
     # A* sums with shared-memory atomics (reproducible to rounding, not bit for bit), and
-    # training amplifies such differences step by step: the runs agree closely at first
-    assert np.allclose(le[:10], lg[:10], rtol=1e-4, atol=0)
+    # training amplifies such differences step by step: the runs agree closely until the
+    # loss jumps at the seventh step (lr 2e-3 on this tiny problem), where a 1e-6 rounding
+    # difference has been seen to grow to 2e-4 -- also between two eager runs
+    assert np.allclose(le[:6], lg[:6], rtol=1e-4, atol=0)
 
 
 def test_trained_lpd_beats_tv_on_limited_view(pkg, torch):

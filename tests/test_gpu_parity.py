@@ -199,17 +199,19 @@ def test_headline_n512_full(pkg, torch):
     assert rel(fa[B - 2], O.adjoint(P, gins[1])) <= TOL
 
 
-@pytest.mark.parametrize("n,cols_threads,strip", [(128, 64, 4), (128, 128, 16), (256, 64, 2), (256, 128, 8)])
-def test_small_column_ctas(pkg, torch, n, cols_threads, strip):
-    """Column CTAs of 64 and 128 threads (the four-step column FFT of N = 8n on fewer threads
-    than 256) against the oracle, batch 3, and the forward bit-identical to the default shape."""
+@pytest.mark.parametrize("n,cols_threads,strip,row_threads,row_pairs",
+                         [(128, 64, 4, 64, 8), (128, 128, 16, 128, 4), (256, 64, 2, 0, 1), (256, 128, 8, 0, 2)])
+def test_small_column_ctas(pkg, torch, n, cols_threads, strip, row_threads, row_pairs):
+    """Column CTAs of 64 and 128 threads and row groups of 64 and 128 threads (the four-step
+    FFTs of N = 8n on fewer threads than 256) against the oracle, batch 3, and the forward
+    bit-identical to the default shape."""
     op, P = make(pkg, torch, dict(n=n, n_det=2 * n, n_t=2 * n, support_radius=0.9))
     B = 3
     fs = np.stack([f32(ellipse_phantom(n, 40 + s)) for s in range(B)])
     ft = torch.tensor(fs, dtype=torch.float32, device="cuda:0")
     g_default = op.forward(ft).cpu().numpy()
     inv_default = op.inverse(torch.tensor(g_default, device="cuda:0")).cpu().numpy()
-    pkg.tat_plan_set_launch_shape(op.plan, strip, 1, cols_threads)
+    pkg.tat_plan_set_launch_shape(op.plan, strip, row_pairs, cols_threads, row_threads)
     g = op.forward(ft).cpu().numpy()
     assert np.array_equal(g, g_default)
     for s in range(B):

@@ -148,7 +148,8 @@ def test_autotune_keeps_results(pkg, torch):
     f2 = torch.empty_like(f)
     ws = op.workspace(B)
     s = torch.cuda.current_stream().cuda_stream
-    ms, strip, rp, ct = pkg.tat_plan_autotune(op.plan, B, f.data_ptr(), g.data_ptr(), f2.data_ptr(), ws.data_ptr(), s)
-    assert ms > 0 and strip in (2, 4, 8, 16, 32) and rp in (1, 2, 4) and ct in (64, 128, 256)
+    ms, strip, rp, ct, rt = pkg.tat_plan_autotune(op.plan, B, f.data_ptr(), g.data_ptr(), f2.data_ptr(), ws.data_ptr(), s)
+    assert ms > 0 and strip in (2, 4, 8, 16, 32) and rp in (1, 2, 4, 8, 16) and ct in (64, 128, 256)
+    assert rt in (64, 128, 256)
     assert np.array_equal(op.forward(f).cpu().numpy(), g0)
     assert rel(op.adjoint(op.forward(f)).cpu().numpy(), a0) <= 1e-6
