@@ -3,19 +3,20 @@
 // the loss and the Adam step.  See include/tat_lpd.h for layouts and
 // precision.
 //
-// The 32 -> 32 layer is an implicit GEMM on the tensor cores: per CTA an
-// 8 x 16 pixel tile (one warp per image row of 16 pixels = one m16 tile) and
-// K = 9 taps x 32 channels in 18 mma.sync.m16n8k16 steps.  The 10 x 18 x 32
-// input halo of each tile arrives by TMA (a 4-D tensor map over the NHWC
-// activations, zero fill outside the image, 64-byte swizzle, which keeps the
-// fragment loads conflict-free), double-buffered on two mbarriers so that the
-// next tile's halo is in flight while the current one's MMAs run; the CTAs are
-// persistent and stage the 9 x 32 x 32 weights once, rows padded to 40 BF16.
-// Its weight gradient is the GEMM dW[tap] = G'^T In_tap over the pixels, one
-// warp per tap, operands fetched with ldmatrix.trans.  The thin layers (2 or 3
-// planes -> 32, and 32 -> 1) are implicit GEMMs on the same tiles with one
-// dimension of 8 to 27; their backward passes compute the data and the weight
-// gradients in one pass over the tiles.
+// The 32 -> 32 layer runs on the 5th-generation tensor cores (tcgen05, accumulators in
+// TMEM): the forward and the data gradient of an already masked gradient as an implicit
+// GEMM per 16 x 8-pixel tile (k_conv_mid_tc), the weight gradient of an already masked
+// gradient with four pixel-shifted copies of G' stacked in M (k_conv_mid_wgrad_tc).  The
+// variants that read the gradient's ReLU mask themselves run on mma.sync m16n8k16
+// (k_conv_mid, k_conv_mid_wgrad): per CTA an 8 x 16 pixel tile, one warp per image row of
+// 16 pixels, K = 9 taps x 32 channels in 18 steps.  Every halo arrives by TMA (4-D tensor
+// maps over the NHWC activations, zero fill outside the image, 64-byte swizzle); the CTAs
+// are persistent.  The thin layers (2 or 3 planes -> 32, and 32 -> 1) are implicit GEMMs
+// on mma.sync with one dimension of 8 to 27 -- the 32 -> 1 forward and the in layer's data
+// gradient as per-tap channel sums of each halo pixel followed by a 9-point stencil -- and
+// their backward passes compute the data and the weight gradients in one pass over the
+// tiles.  Weight gradients leave per-CTA partial sums that k_reduce_partials adds in a
+// fixed order.
 #include <cuda.h>  // CUtensorMap and its enums (types only; the encoder is looked up at run time)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
