@@ -87,7 +87,9 @@ tat_status tat_conv_mid_fwd(int batch, int H, int W, const tat_bf16* h_in, const
  * pre-activation (h_in being that layer's ReLU output). */
 tat_status tat_conv_mid_bwd_data(int batch, int H, int W, const tat_bf16* g_out, const tat_bf16* h_out,
                                  const tat_bf16* w, const tat_bf16* h_in, tat_bf16* g_in, tat_stream_t stream);
-/* gw += d/dw, gb += d/db of <g_out, h_out> (tensor cores; h_out == NULL as above). */
+/* gw += d/dw, gb += d/db of <g_out, h_out> (tensor cores; h_out == NULL as above: then
+ * on tcgen05, one CTA per SM, with the taps of a kernel row and four pixel shifts stacked
+ * into one MMA; with h_out, on mma.sync). */
 tat_status tat_conv_mid_bwd_weights(int batch, int H, int W, const tat_bf16* h_in, const tat_bf16* g_out,
                                     const tat_bf16* h_out, float* scratch, size_t scratch_floats, float* gw,
                                     float* gb, tat_stream_t stream);
