@@ -182,6 +182,73 @@ def test_centred_gaussian_closed_form():
     assert errs[False] > 10 * errs[True]       # the low-mode quadrature is what makes it accurate
 
 
+# ------------------------------------------------------------ physical units (c, R != 1)
+#
+# Section 2.1 sets R = c = 1 "without loss of generality"; the oracle takes
+# physical (c, R, T) and normalises internally.  These pins state the physical
+# problem on their own: the wave equation p_tt = c^2 Lap p with p(0) = f,
+# p_t(0) = 0 on a grid of n nodes over [-R, R]^2, detectors on |z| = R at
+# t_m = m T/(n_t - 1), and the L2 inner products of Eq. innerProducts in
+# physical units (dx on the plane, arc length R dtheta times dt on the data).
+
+_PHYS = dict(c=1.5, R=0.8, T=1.6)
+
+
+def _gauss_physical(sig, c, R, t):
+    """p(z, t) at |z| = R for f = exp(-|x|^2/sig^2), all in physical units.
+
+    Radial Fourier synthesis of the wave equation: p = int_0^inf lam fhat(lam)
+    J_0(lam R) cos(c lam t) dlam with fhat(lam) = (sig^2/2) exp(-sig^2 lam^2/4).
+    """
+    fn = lambda l: l * (sig ** 2 / 2) * np.exp(-sig ** 2 * l ** 2 / 4) * j0(l * R) * np.cos(c * l * t)
+    return quad(fn, 0, 60 / sig, limit=2000, epsabs=1e-13)[0]
+
+
+def _physical_gaussian_error(P, c, R, T):
+    n, n_t = P.n, P.n_t
+    sig = 0.12 * R
+    x = -R + np.arange(n) * (2 * R / (n - 1))          # physical node positions
+    X, Y = np.meshgrid(x, x)
+    g = O.forward(P, np.exp(-(X ** 2 + Y ** 2) / sig ** 2))
+    t = np.arange(n_t) * (T / (n_t - 1))                # physical sample times
+    ref = np.array([_gauss_physical(sig, c, R, tm) for tm in t])
+    return np.linalg.norm(g - ref[None, :]) / (np.linalg.norm(ref) * math.sqrt(P.n_det))
+
+
+def test_physical_units_centred_gaussian():
+    """A at (c, R, T) = (1.5, 0.8, 1.6) against the closed form written in physical units."""
+    c, R, T = _PHYS["c"], _PHYS["R"], _PHYS["T"]
+    P = O.OraclePlan(64, 128, 128, c=c, R=R, T=T)
+    assert _physical_gaussian_error(P, c, R, T) < 5e-4
+    # A planted mistake in the normalisation, T' = T R / c instead of c T / R
+    # (the same plan with c and R exchanged), is caught.
+    bad = O.OraclePlan(64, 128, 128, c=R, R=c, T=T)
+    assert _physical_gaussian_error(bad, c, R, T) > 1e-1
+
+
+def _physical_dot_gap(P, c, R, T, f, g):
+    """|<A f, g>_Y - <f, A* g>_X| / |<A f, g>_Y| with the physical quadrature weights."""
+    w_x = (2 * R / (P.n - 1)) ** 2                      # dx dy of the node grid on [-R, R]^2
+    w_y = (T / (P.n_t - 1)) * (2 * math.pi * R / P.n_det)   # dt times arc length per detector
+    lhs = w_y * np.sum(O.forward(P, f) * g)
+    rhs = w_x * np.sum(f * O.adjoint(P, g))
+    return abs(lhs - rhs) / abs(lhs)
+
+
+def test_physical_units_dot_product():
+    """<A f, g>_Y = <f, A* g>_X (Eq. innerProducts) with weights written here in physical units."""
+    c, R, T = _PHYS["c"], _PHYS["R"], _PHYS["T"]
+    P = O.OraclePlan(32, 64, 64, c=c, R=R, T=T, support_radius=0.9)
+    f = ellipse_phantom(32, 3)
+    g = random_sinogram(64, 64, 7)
+    assert _physical_dot_gap(P, c, R, T, f, g) <= 1e-12
+    # Planted mistakes in the oracle's weights are caught: W_X without R^2, W_Y without R/c.
+    for attr, wrong in (("W_X", P.h ** 2), ("W_Y", P.dt * (2 * math.pi * R / P.n_det))):
+        bad = O.OraclePlan(32, 64, 64, c=c, R=R, T=T, support_radius=0.9)
+        setattr(bad, attr, wrong)
+        assert _physical_dot_gap(bad, c, R, T, f, g) > 1e-2
+
+
 _CS = [(0.3, -0.2, 0.15, 1.0), (-0.25, 0.35, 0.1, 0.7)]
 
 
