@@ -153,9 +153,12 @@ tat_status tat_inverse_batched(tat_plan_t plan, int batch, const float* g, long 
  * device memory when they need A (a process whose GPU memory is all handed to
  * its own pool, or a loop that cannot afford cudaMalloc's implicit device
  * synchronisation).  The call itself allocates nothing.  Every GPU that loads
- * the library holds the 16 MiB until the process exits.  The first call on
- * each device looks up the buffer's device address (cudaGetSymbolAddress), so
- * make that first call before any stream capture.  All calls on a device
+ * the library holds the 16 MiB until the process exits.  Every call looks up
+ * the buffer's device address on the current device (cudaGetSymbolAddress,
+ * which allocates nothing); the first lookup on a device may load the
+ * library's device code, so make the first call before any stream capture.
+ * f and g must be 4-byte aligned (else TAT_ERR_INVALID_ARG, as for
+ * tat_forward).  All calls on a device
  * share the one buffer: calls that overlap on the GPU (different streams or
  * host threads) race and must be serialised by the caller.  Plans whose
  * scratch exceeds 16 MiB (tat_workspace_size(plan, 1)) are rejected with

@@ -8,8 +8,8 @@
 // For them this entry point runs the same five kernels as tat_forward, using
 // a file-scope buffer of kNoAllocScratchBytes that every GPU loading this
 // library holds until the process exits.  No call here allocates.
+#include <cstdint>
 #include <cstdio>
-#include <mutex>
 
 #include "plan.hpp"
 
@@ -21,25 +21,18 @@ constexpr size_t kNoAllocScratchBytes = 16u << 20;  // 16 MiB: n = 512, 1024 x 1
 // symbol: its device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-
-// Looks up the buffer's device address once per device, with that device current.
-tat_status scratch_address(int device, void** out) {
-  if (device < 0 || device >= kMaxDevices) return TAT_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[device]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      fprintf(stderr, "tat_forward_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
-      cudaGetLastError();
-      return TAT_ERR_CUDA;
-    }
-    g_addr[device] = p;
+// Looks up the buffer's device address on the current device.  Done on every
+// call (cudaGetSymbolAddress allocates nothing), so that a device reset or a
+// new primary context never leaves a stale address behind.
+tat_status scratch_address(void** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    fprintf(stderr, "tat_forward_noalloc: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
+    cudaGetLastError();
+    return TAT_ERR_CUDA;
   }
-  *out = g_addr[device];
+  *out = p;
   return TAT_OK;
 }
 
@@ -47,6 +40,8 @@ tat_status scratch_address(int device, void** out) {
 
 extern "C" tat_status tat_forward_noalloc(tat_plan_t plan, const float* f, float* g, tat_stream_t stream) {
   if (!plan || !f || !g) return TAT_ERR_INVALID_ARG;
+  // the kernels read f and write g as 4-byte floats
+  if (reinterpret_cast<uintptr_t>(f) % 4 || reinterpret_cast<uintptr_t>(g) % 4) return TAT_ERR_INVALID_ARG;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
@@ -60,7 +55,7 @@ extern "C" tat_status tat_forward_noalloc(tat_plan_t plan, const float* f, float
     return TAT_ERR_UNSUPPORTED;
   }
   void* scratch = nullptr;
-  const tat_status s = scratch_address(dev, &scratch);
+  const tat_status s = scratch_address(&scratch);
   if (s != TAT_OK) return s;
   // Every scratch element the five stages read is written earlier in the same
   // call, so nothing needs clearing between calls.
