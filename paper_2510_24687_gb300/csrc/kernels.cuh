@@ -516,67 +516,78 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
   }
 }
 
-// Transposed bilinear weights of the points with stencil column i0 = c into
-// the column buffers of c (weight 1-a) and c+1 (weight a); either may be null.
-// Each warp takes 32 consecutive points.  Points are sorted by stencil row k0,
-// so equal rows form runs of lanes; when a warp holds runs, they are summed
-// with a segmented shuffle scan and only the last lane of each run issues the
-// shared-memory atomics (near the origin up to 64 samples share a cell).
+// Transposed bilinear weights of the points with stencil column i0 = c, added
+// into the column buffers of c (weight 1-a) and c+1 (weight a); either may be
+// null.  The sum is the same on every call, bit for bit: each run of points
+// with one stencil row k0 (the plan's run table) is summed by one lane, in the
+// table's order, into its row-k0 part (weight 1-b) and row-k0+1 part (weight b),
+// and every buffer cell is written by exactly one lane with a plain add --
+// cell k0 by the run with key k0, which first adds the row-k0 part of the run
+// with key k0-1 if there is one, and cell k0+1 by the run with key k0 when no
+// run has key k0+1.  No atomics: the order of every addition is fixed.
+// The conj(phase) of the column transform is applied once per cell.
 template <int L>
 __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* __restrict__ Yb, int c, float2* left,
                                                float2* right, int tid, int NT) {
   const unsigned full = 0xffffffffu;
-  const int lane = tid & 31, warp = tid >> 5, nwarp = NT >> 5;
-  const int e0 = P.coloff[c], e1 = P.coloff[c + 1];
-  for (int base = e0 + warp * 32; base < e1; base += nwarp * 32) {
-    const int e = base + lane;
-    int key = 0x7fffffff;
-    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // left qa, left qb, right qa, right qb (re, im)
-    if (e < e1) {
-      const PolarEntry pe = P.pts[e];
-      const float2 val = Yb[pe.p];
-      key = pe.k0;
-      // conj(phase) of the two stencil rows (transpose of the column phase)
-      const float2 va = cmulc(val, __ldg(&P.phase[wrapN(key, P.N)]));
-      const float2 vb = cmulc(val, __ldg(&P.phase[wrapN(key + 1, P.N)]));
-      const float wl = 1.f - pe.a, wr = pe.a, w0 = 1.f - pe.b, w1 = pe.b;
-      v[0] = wl * w0 * va.x; v[1] = wl * w0 * va.y;
-      v[2] = wl * w1 * vb.x; v[3] = wl * w1 * vb.y;
-      v[4] = wr * w0 * va.x; v[5] = wr * w0 * va.y;
-      v[6] = wr * w1 * vb.x; v[7] = wr * w1 * vb.y;
+  const int lane = tid & 31;
+  const int r0 = P.runoff[c], r1 = P.runoff[c + 1];
+  // warp-uniform loop (NT is a multiple of 32): lane l takes run base + l
+  for (int base = r0 + (tid - lane); base < r1; base += NT) {
+    const int r = base + lane;
+    const bool valid = r < r1;
+    int k = 0, s = 0;
+    float2 la = make_float2(0.f, 0.f), lb = la, ra = la, rb = la;
+    if (valid) {
+      const int2 run = P.runs[r];
+      k = run.y;
+      s = run.x;
+      const int e = P.runs[r + 1].x;
+      for (int i = s; i < e; ++i) {
+        const PolarEntry pe = P.pts[i];
+        const float2 v = Yb[pe.p];
+        const float wl0 = (1.f - pe.a) * (1.f - pe.b), wl1 = (1.f - pe.a) * pe.b;
+        const float wr0 = pe.a * (1.f - pe.b), wr1 = pe.a * pe.b;
+        la.x += wl0 * v.x; la.y += wl0 * v.y;
+        lb.x += wl1 * v.x; lb.y += wl1 * v.y;
+        ra.x += wr0 * v.x; ra.y += wr0 * v.y;
+        rb.x += wr1 * v.x; rb.y += wr1 * v.y;
+      }
     }
-    const int prev = __shfl_up_sync(full, key, 1);
-    const bool head = lane == 0 || prev != key;
-    const unsigned heads = __ballot_sync(full, head);
-    bool emit = key != 0x7fffffff;
-    if (__popc(heads) <= 24) {
-      // segmented inclusive scan; the run's last lane ends up with the run's sum
-      const int seg = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const float t = __shfl_up_sync(full, v[q], o);
-          if (lane - o >= seg) v[q] += t;
-        }
+    // row-k parts of the run with key k-1: from the lane before, or (lane 0) summed again
+    float2 plb, prb;
+    plb.x = __shfl_up_sync(full, lb.x, 1);
+    plb.y = __shfl_up_sync(full, lb.y, 1);
+    prb.x = __shfl_up_sync(full, rb.x, 1);
+    prb.y = __shfl_up_sync(full, rb.y, 1);
+    if (!valid) continue;
+    const int2 prev = r > r0 ? P.runs[r - 1] : make_int2(0, 0);
+    const bool has_prev = r > r0 && prev.y == k - 1;
+    if (has_prev && lane == 0) {
+      plb = make_float2(0.f, 0.f);
+      prb = plb;
+      for (int i = prev.x; i < s; ++i) {
+        const PolarEntry pe = P.pts[i];
+        const float2 v = Yb[pe.p];
+        const float wl1 = (1.f - pe.a) * pe.b, wr1 = pe.a * pe.b;
+        plb.x += wl1 * v.x; plb.y += wl1 * v.y;
+        prb.x += wr1 * v.x; prb.y += wr1 * v.y;
       }
-      const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
-      emit = emit && tail;
     }
-    if (emit) {
-      const int qa = xpad<L>(colpos<L>(wrapN(key, P.N))), qb = xpad<L>(colpos<L>(wrapN(key + 1, P.N)));
-      if (left != nullptr) {
-        atomicAdd(&left[qa].x, v[0]);
-        atomicAdd(&left[qa].y, v[1]);
-        atomicAdd(&left[qb].x, v[2]);
-        atomicAdd(&left[qb].y, v[3]);
-      }
-      if (right != nullptr) {
-        atomicAdd(&right[qa].x, v[4]);
-        atomicAdd(&right[qa].y, v[5]);
-        atomicAdd(&right[qb].x, v[6]);
-        atomicAdd(&right[qb].y, v[7]);
-      }
+    const bool has_next = r + 1 < r1 && P.runs[r + 1].y == k + 1;
+    const int ra_row = wrapN(k, P.N), rb_row = wrapN(k + 1, P.N);
+    const int qa = xpad<L>(colpos<L>(ra_row)), qb = xpad<L>(colpos<L>(rb_row));
+    const float2 pa = __ldg(&P.phase[ra_row]);
+    if (has_prev) {
+      la = cadd(la, plb);
+      ra = cadd(ra, prb);
+    }
+    if (left != nullptr) left[qa] = cadd(left[qa], cmulc(la, pa));
+    if (right != nullptr) right[qa] = cadd(right[qa], cmulc(ra, pa));
+    if (!has_next) {
+      const float2 pb = __ldg(&P.phase[rb_row]);
+      if (left != nullptr) left[qb] = cadd(left[qb], cmulc(lb, pb));
+      if (right != nullptr) right[qb] = cadd(right[qb], cmulc(rb, pb));
     }
   }
 }

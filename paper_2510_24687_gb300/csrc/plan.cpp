@@ -565,8 +565,23 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
       std::sort(sorted.begin() + off[c], sorted.begin() + off[c + 1], [](const PolarEntry& x, const PolarEntry& y) {
         return x.k0 != y.k0 ? x.k0 < y.k0 : x.p < y.p;
       });
+    // Runs of equal stencil row k0 within a column ({first point, k0}), for the
+    // adjoint's deterministic scatter; a sentinel {npts, 0} follows the last run,
+    // so run r ends where run r + 1 starts.
+    std::vector<int2> runs;
+    std::vector<int> runoff(d.ncol + 1, 0);
+    runs.reserve(npts + 1);
+    for (int c = 0; c < d.ncol; ++c) {
+      runoff[c] = (int)runs.size();
+      for (int e = off[c]; e < off[c + 1]; ++e)
+        if (e == off[c] || sorted[e].k0 != sorted[e - 1].k0) runs.push_back(make_int2(e, sorted[e].k0));
+    }
+    runoff[d.ncol] = (int)runs.size();
+    runs.push_back(make_int2(npts, 0));
     TAT_TRY(upload(P, sorted, &d.pts));
     TAT_TRY(upload(P, off, &d.coloff));
+    TAT_TRY(upload(P, runs, &d.runs));
+    TAT_TRY(upload(P, runoff, &d.runoff));
     if (npts != P->info.n_points) return TAT_ERR_INTERNAL;
   }
   // Launch shapes.

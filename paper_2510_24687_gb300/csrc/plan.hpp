@@ -62,6 +62,9 @@ struct DevPlan {
   const float* gamma;              // [n_det] 1 on the arc Gamma, else 0
   const PolarEntry* pts;           // [n_points]
   const int* coloff;               // [ncol+1] points with i0 = c: [coloff[c], coloff[c+1])
+  const int2* runs;                // [n_runs+1] {first point, k0} of each run of equal k0 within a column,
+                                   // column by column; run r ends at runs[r+1].x (a sentinel closes the table)
+  const int* runoff;               // [ncol+1] runs of column c: [runoff[c], runoff[c+1])
   const float* Bt;                 // [(K+1) x (J+1)] dlam*lam_j*J_k(lam_j)/n_phi
   const float* Bh;                 // [2 x n_low]     w_q*dlam*lam_q*J_k(lam_q)/n_phi
   const float* Lcos;               // [n_low x n_t]   cos(lam_q t_m)

@@ -1,7 +1,7 @@
 """GPU tests of the mixed-size request runtime (include/tat_service.h) and the
-launch-shape autotuner: results (A, A*, A^-1 and the pair A* A) equal the direct
-batched calls, graphs are
-reused, admission under a tight memory budget evicts and shrinks batches and
+launch-shape autotuner: results (A, A*, A^-1 and the pair A* A) match the FP64
+oracle at every size served (n = 1024 included) and equal the direct batched
+calls, graphs are reused, admission under a tight memory budget evicts and shrinks batches and
 reports out-of-memory for a request that fits at no batch size.
 """
 import numpy as np
@@ -58,7 +58,21 @@ def _direct(pkg, torch, n, nd, nt, op, x):
     return getattr(o, op)(x).cpu().numpy()
 
 
-def test_service_matches_direct_calls_and_reuses_graphs(pkg, torch):
+def _oracle(n, nd, nt, op, x):
+    """The FP64 oracle's answer to one request (the pair's intermediate A f kept in FP64)."""
+    from oracle import tat_oracle as O
+    P = O.OraclePlan(n, nd, nt, support_radius=0.9)
+    xd = x.cpu().numpy().astype(np.float64)
+    if op == "pair":
+        return O.adjoint(P, O.forward(P, xd))
+    return getattr(O, op)(P, xd)
+
+
+def test_service_matches_oracle_and_direct_calls_and_reuses_graphs(pkg, torch):
+    """Every request of the mixed batch (three sizes, among them 96 x 96 with 192 x 160 data,
+    times A, A*, A^-1 and the pair A* A) against the FP64 oracle at the parity bar 1e-5, and
+    against the direct calls: the forward bit for bit, the rest to 1e-6 (A^-1 and the pair
+    run with the service's batch, whose launch shapes may differ)."""
     svc = pkg.TatService(memory_budget=2 << 30, max_batch=4)
     reqs = _requests(torch)
     for rnd in range(2):
@@ -68,14 +82,37 @@ def test_service_matches_direct_calls_and_reuses_graphs(pkg, torch):
         for rid, (n, nd, nt, op, x, out) in zip(ids, reqs):
             ms, status = svc.latency(rid)
             assert status == 0 and ms > 0
+            got = out.cpu().numpy()
+            if rnd == 0:
+                assert rel(got, _oracle(n, nd, nt, op, x)) <= 1e-5, (n, op)
             ref = _direct(pkg, torch, n, nd, nt, op, x)
             if op == "forward":
-                assert np.array_equal(out.cpu().numpy(), ref)
+                assert np.array_equal(got, ref)
             else:
-                assert rel(out.cpu().numpy(), ref) <= 1e-6
+                assert rel(got, ref) <= 1e-6
     st = svc.stats()
     assert st["requests"] == st["completed"] == 2 * len(reqs)
     assert st["plans"] == len(SIZES) and st["graph_launches"] > 0 and st["evictions"] == 0
+    svc.close()
+
+
+def test_service_n1024_member_matches_oracle(pkg, torch):
+    """The largest member of the mixed-size workload: n = 1024 with 2048 detectors x 2048
+    samples (N = 8192, the 32-point four-step transforms), one A and one A* request through
+    the service against the FP64 oracle at 1e-5."""
+    n, nd, nt = 1024, 2048, 2048
+    svc = pkg.TatService(memory_budget=8 << 30, max_batch=2)
+    f = torch.tensor(ellipse_phantom(n, 7).astype(np.float32), device="cuda:0")
+    g = torch.tensor(random_sinogram(nd, nt, 8).astype(np.float32), device="cuda:0")
+    out_g = torch.empty((nd, nt), device="cuda:0")
+    out_f = torch.empty((n, n), device="cuda:0")
+    d = svc.desc(n, nd, nt, support_radius=0.9)
+    ids = [svc.submit(d, "forward", f, out_g), svc.submit(d, "adjoint", g, out_f)]
+    svc.flush()
+    svc.synchronize()
+    assert all(svc.latency(i)[1] == 0 for i in ids)
+    assert rel(out_g.cpu().numpy(), _oracle(n, nd, nt, "forward", f)) <= 1e-5
+    assert rel(out_f.cpu().numpy(), _oracle(n, nd, nt, "adjoint", g)) <= 1e-5
     svc.close()
 
 
