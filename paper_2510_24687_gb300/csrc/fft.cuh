@@ -387,6 +387,90 @@ __device__ __forceinline__ void fft(float2* buf, const FftDev& f, int tid, int n
   else fft_ct_from<L, INV, 0, 1>(buf, f, tid, nthr, n_in, n_out, pre, post, smptw);
 }
 
+// First pass of a compile-time schedule with its inputs from `load(i)` (global memory,
+// or zero where the caller knows an input vanishes) instead of the shared buffer:
+// the copy into shared memory and the first pass's reads become one step.  Ns = 1, so
+// no twiddles; the outputs go to the buffer at j R + r.
+template <int R, bool INV, class Load>
+__device__ __forceinline__ void fft_pass_load(float2* buf, int L, int tid, int nthr, Load& load) {
+  constexpr int NB = 16 / R;
+  const int nb = L / R;
+  const bool act = tid < nthr;
+  float2 v[NB][R];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = tid + b * nthr;
+    if (act && j < nb) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b][r] = load(j + r * nb);
+      bfly<R, INV>(v[b]);
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = tid + b * nthr;
+    if (act && j < nb) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[spad(j * R + r)] = v[b][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Last pass (Ns R = L) handing each output o < n_out to `store(o, value)` instead of
+// writing it back to the buffer, which it leaves unchanged (no trailing barrier).
+template <int R, bool INV, class Store>
+__device__ __forceinline__ void fft_pass_store(const float2* buf, int L, int tid, int nthr, int n_out, Store& store,
+                                               const float2* ptws) {
+  constexpr int NB = 16 / R;
+  const int nb = L / R;  // = Ns
+  const bool act = tid < nthr;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = tid + b * nthr;
+    if (act && j < nb) {
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = buf[spad(j + r * nb)];
+      float2 w1 = make_float2(1.f, 0.f), w2 = w1, w4 = w1, w8 = w1;
+      pass_tw<R>(ptws, nb, j, w1, w2, w4, w8);
+      apply_twiddles_given<R, INV>(v, w1, w2, w4, w8);
+      bfly<R, INV>(v);
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (j + r * nb < n_out) store(j + r * nb, v[r]);
+    }
+  }
+}
+
+template <int L, bool INV, int S, int NS, class Load, class Store>
+__device__ __forceinline__ void fft_io_from(float2* buf, const FftDev& f, int tid, int nthr, int n_out, Load& load,
+                                            Store& store, const float2* smptw) {
+  constexpr int NP = Sched<L>::npass;
+  if constexpr (S < NP) {
+    constexpr int R = Sched<L>::radix(S);
+    if constexpr (S == 0) {
+      fft_pass_load<R, INV>(buf, L, tid, nthr, load);
+    } else if constexpr (S == NP - 1) {
+      fft_pass_store<R, INV>(buf, L, tid, nthr, n_out, store, smptw + f.ptw_off[S]);
+    } else {
+      fft_pass<R, INV>(buf, L, NS, f.tw, tid, nthr, false, false, 0, 0, nullptr, nullptr, smptw + f.ptw_off[S]);
+    }
+    fft_io_from<L, INV, S + 1, NS * R>(buf, f, tid, nthr, n_out, load, store, smptw);
+  }
+}
+
+// Unnormalised DFT of length L (compile-time schedule of at least two passes) from
+// load(i), i < L, to store(o, X[o]) for o < n_out, with `buf` (xpad_len(L) slots) as
+// the exchange between passes and `smptw` the shared-memory per-pass twiddles (loaded
+// and synchronised by the caller).  Every thread of the CTA must call it.
+template <int L, bool INV, class Load, class Store>
+__device__ __forceinline__ void fft_io(float2* buf, const FftDev& f, int tid, int nthr, int n_out, Load load,
+                                       Store store, const float2* smptw) {
+  static_assert(L > 0 && Sched<L>::npass >= 2, "fft_io needs a compile-time schedule of two or more passes");
+  fft_io_from<L, INV, 0, 1>(buf, f, tid, nthr, n_out, load, store, smptw);
+}
+
 // Copies an FFT's per-pass twiddle tables to shared memory (caller syncs).
 __device__ __forceinline__ void load_pass_tw(float2* dst, const FftDev& f, int tid, int nthr) {
   for (int i = tid; i < f.ptw_len; i += nthr) dst[i] = f.ptw[i];
@@ -549,11 +633,18 @@ __device__ __forceinline__ void col_fft_fwd(float2* buf, const FftDev& f, const 
   }
 }
 
+struct NoMid {
+  __device__ __forceinline__ void operator()() const {}
+};
+
 // Inverse (unnormalised): Z[q] at colpos(q), times conj(pre[q]) -> z[0, n_out) in natural order.
-template <int L>
+// `mid()` runs between the two steps of the four-step transform (before the transform for
+// other lengths): a place to issue global loads whose latency the second step hides.
+template <int L, class Mid = NoMid>
 __device__ __forceinline__ void col_fft_inv(float2* buf, const FftDev& f, const float2* smtw, int tid, int nthr,
-                                            int sthr, int n_out, const float2* __restrict__ pre) {
+                                            int sthr, int n_out, const float2* __restrict__ pre, Mid mid = Mid{}) {
   if constexpr (!FourStep<L>::on) {
+    mid();
     fft<L, true>(buf, f, tid, sthr, f.L, n_out, pre, nullptr);
   } else {
     constexpr int RA = FourStep<L>::RA;
@@ -579,6 +670,7 @@ __device__ __forceinline__ void col_fft_inv(float2* buf, const FftDev& f, const 
       for (int m1 = 0; m1 < 16; ++m1) buf[xpad<L>(base + 16 * m1 + m)] = v[m1];
     }
     __syncthreads();
+    mid();
     for (int n2 = tid; n2 < 256; n2 += nthr) {
       float2 v[RA];
 #pragma unroll

@@ -43,6 +43,7 @@ __device__ __forceinline__ float2 mul_mipow(float2 v, int k) {
 }
 __device__ __forceinline__ int wrapN(int q, int N) { return q < 0 ? q + N : q; }
 
+
 // ------------------------------------------------------------------ forward
 
 // Row kernels: up to 1024 threads (4 row pairs); at L = 8192 one row pair of 512
@@ -130,17 +131,32 @@ __global__ void TAT_COLS_BOUNDS_F k_cols_fwd(DevPlan P, const float2* __restrict
   float2* Yb = Y + (size_t)b * ys;
   const int N = P.N;
   // the first PolarEntry of each thread's gather is loaded before the column FFT, so that
-  // its latency hides behind the transform
+  // its latency hides behind the transform; so is the next column's input (up to two rows
+  // a thread, else it is read when needed)
   PolarEntry pe0{};
+  const bool ahead = P.n <= 2 * NT;
+  float2 nx0 = make_float2(0.f, 0.f), nx1 = nx0;
+  auto load_ahead = [&](int c) {
+    const float2* col = Xb + (size_t)c * P.n;
+    if (tid < P.n) nx0 = col[tid];
+    if (tid + NT < P.n) nx1 = col[tid + NT];
+  };
+  if (ahead) load_ahead(c0);
 #pragma unroll 1
   for (int cc = 0; cc < ncols; ++cc) {
     float2* buf = (cc & 1) ? slot1 : slot0;
     const int c = c0 + cc;
-    const float2* col = Xb + (size_t)c * P.n;  // R[c][0..n): contiguous
-    for (int iy = tid; iy < P.n; iy += NT) buf[xpad<L>(iy)] = col[iy];
+    if (ahead) {
+      if (tid < P.n) buf[xpad<L>(tid)] = nx0;
+      if (tid + NT < P.n) buf[xpad<L>(tid + NT)] = nx1;
+    } else {
+      const float2* col = Xb + (size_t)c * P.n;  // R[c][0..n): contiguous
+      for (int iy = tid; iy < P.n; iy += NT) buf[xpad<L>(iy)] = col[iy];
+    }
     const int e0 = cc > 0 ? P.coloff[c - 1] + tid : 0, e1 = cc > 0 ? P.coloff[c] : 0;
     if (e0 < e1) pe0 = P.pts[e0];
     __syncthreads();
+    if (ahead && cc + 1 < ncols) load_ahead(c + 1);
     // column DFT over the n nonzero rows (the phase e^{i q dxi} of each output
     // row is applied by the gather below)
     col_fft_fwd<L>(buf, P.fN, smtw, tid, NT, nt, P.n, nullptr);
@@ -253,28 +269,53 @@ __global__ void __launch_bounds__(1024) k_modes_fwd(DevPlan P, const float2* __r
   const float2* Cm = X + (size_t)b * xs + (size_t)k * J1;
   float2* smptw = sm + xpad_len(L2);
   load_pass_tw(smptw, P.f2M, threadIdx.x, blockDim.x);
-  for (int j = threadIdx.x; j < L2; j += blockDim.x) {
-    float2 v = make_float2(0.f, 0.f);
-    if (j >= 1 && j <= P.J) v = Cm[j];
-    else if (j >= L2 - P.J) v = Cm[L2 - j];
-    sm[xpad<L>(j)] = v;
-  }
-  __syncthreads();
-  fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, P.n_t, nullptr, nullptr, smptw);
   float2* G = Y + (size_t)b * ys + (size_t)k * P.n_t;
   const bool low = P.low_on && k <= 1;
   const float2* Ch = X + (size_t)b * xs + (size_t)(P.K + 1) * J1 + (size_t)k * P.n_low;
-  for (int m = threadIdx.x; m < P.n_t; m += blockDim.x) {
-    float2 v = cscale(sm[xpad<L>(m)], 0.5f);
-    if (low) {
-      for (int q = 0; q < P.n_low; ++q) {
-        const float c = P.Lcos[(size_t)q * P.n_t + m];
-        const float2 ch = Ch[q];
-        v.x += c * ch.x;
-        v.y += c * ch.y;
+  if constexpr (L > 0) {
+    // the even extension is read straight into the first pass (its zero band is not
+    // touched) and each kept output leaves the last pass straight for global memory
+    const int J = P.J;
+    auto load = [&](int j) -> float2 {
+      if (j >= 1 && j <= J) return Cm[j];
+      if (j >= L2 - J) return Cm[L2 - j];
+      return make_float2(0.f, 0.f);
+    };
+    auto store = [&](int m, float2 x) {
+      float2 v = cscale(x, 0.5f);
+      if (low) {
+        for (int q = 0; q < P.n_low; ++q) {
+          const float c = P.Lcos[(size_t)q * P.n_t + m];
+          const float2 ch = Ch[q];
+          v.x += c * ch.x;
+          v.y += c * ch.y;
+        }
       }
+      G[m] = v;
+    };
+    __syncthreads();  // twiddles
+    fft_io<L, false>(sm, P.f2M, threadIdx.x, nt, P.n_t, load, store, smptw);
+  } else {
+    for (int j = threadIdx.x; j < L2; j += blockDim.x) {
+      float2 v = make_float2(0.f, 0.f);
+      if (j >= 1 && j <= P.J) v = Cm[j];
+      else if (j >= L2 - P.J) v = Cm[L2 - j];
+      sm[xpad<L>(j)] = v;
     }
-    G[m] = v;
+    __syncthreads();
+    fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, P.n_t, nullptr, nullptr, smptw);
+    for (int m = threadIdx.x; m < P.n_t; m += blockDim.x) {
+      float2 v = cscale(sm[xpad<L>(m)], 0.5f);
+      if (low) {
+        for (int q = 0; q < P.n_low; ++q) {
+          const float c = P.Lcos[(size_t)q * P.n_t + m];
+          const float2 ch = Ch[q];
+          v.x += c * ch.x;
+          v.y += c * ch.y;
+        }
+      }
+      G[m] = v;
+    }
   }
 }
 
@@ -311,11 +352,23 @@ __global__ void __launch_bounds__(1024) k_theta_fwd(DevPlan P, const float2* __r
   float2* smtw = smptw + P.fdet.ptw_len;
   load_pass_tw(smptw, P.fdet, threadIdx.x, blockDim.x);
   load_fourstep_tw(smtw, P.fdet.fstw, threadIdx.x, blockDim.x);
+  // 16-byte loads of the time-sample pairs (m1, m2) when the modes are not folded, the tile is
+  // whole and every row starts on a 16-byte boundary
+  const bool vin = P.n_phi == P.n_det && (P.n_t & 1) == 0 && (ys & 1) == 0 && m0 + TT <= P.n_t &&
+                   (reinterpret_cast<uintptr_t>(Y) & 15) == 0;
+#pragma unroll 4
   for (int e = threadIdx.x; e < (nd / 2 + 1) * npair; e += blockDim.x) {
     const int bin = e / npair, p = e % npair;
     const int m1 = m0 + 2 * p, m2 = m1 + 1;
-    float2 x1 = m1 < P.n_t ? folded_mode(P, G, bin, m1) : make_float2(0.f, 0.f);
-    float2 x2 = m2 < P.n_t ? folded_mode(P, G, bin, m2) : make_float2(0.f, 0.f);
+    float2 x1, x2;
+    if (vin) {
+      const float4 v = *reinterpret_cast<const float4*>(G + (size_t)bin * P.n_t + m1);
+      x1 = make_float2(v.x, v.y);
+      x2 = make_float2(v.z, v.w);
+    } else {
+      x1 = m1 < P.n_t ? folded_mode(P, G, bin, m1) : make_float2(0.f, 0.f);
+      x2 = m2 < P.n_t ? folded_mode(P, G, bin, m2) : make_float2(0.f, 0.f);
+    }
     if (bin == 0 || bin == nd / 2) { x1.y = 0.f; x2.y = 0.f; }
     float2* z = sm + p * SL;
     z[xpad<L>(colpos<L>(bin))] = make_float2(x1.x - x2.y, x1.y + x2.x);
@@ -328,6 +381,20 @@ __global__ void __launch_bounds__(1024) k_theta_fwd(DevPlan P, const float2* __r
     else fft<L, true>(sm + gi * SL, P.fdet, gt, nt, P.n_det, P.n_det, nullptr, nullptr, smptw);
   }
   float* gb = g + (size_t)b * gs;
+  if constexpr (TT % 4 == 0) {
+    // 16-byte stores of four time samples (two transforms) per detector when aligned
+    if ((P.n_t & 3) == 0 && (gs & 3) == 0 && m0 + TT <= P.n_t && (reinterpret_cast<uintptr_t>(g) & 15) == 0) {
+      constexpr int Q = TT / 4;
+      for (int e = threadIdx.x; e < nd * Q; e += blockDim.x) {
+        const int d = e / Q, q = e - d * Q;
+        const float gm = P.gamma[d];
+        const float2 z0 = sm[(2 * q) * SL + xpad<L>(d)], z1 = sm[(2 * q + 1) * SL + xpad<L>(d)];
+        *reinterpret_cast<float4*>(gb + (size_t)d * P.n_t + m0 + 4 * q) =
+            make_float4(gm * z0.x, gm * z0.y, gm * z1.x, gm * z1.y);
+      }
+      return;
+    }
+  }
   for (int e = threadIdx.x; e < nd * TT; e += blockDim.x) {
     const int d = e / TT, tt = e % TT;
     const int m = m0 + tt;
@@ -354,12 +421,29 @@ __global__ void __launch_bounds__(1024) k_theta_adj(DevPlan P, const float* __re
   float2* smtw = smptw + P.fdet.ptw_len;
   load_pass_tw(smptw, P.fdet, threadIdx.x, blockDim.x);
   load_fourstep_tw(smtw, P.fdet.fstw, threadIdx.x, blockDim.x);
-  for (int e = threadIdx.x; e < nd * TT; e += blockDim.x) {
-    const int d = e / TT, tt = e % TT;
-    const int m = m0 + tt;
-    const float v = m < P.n_t ? P.gamma[d] * gb[(size_t)d * P.n_t + m] : 0.f;
-    float* z = reinterpret_cast<float*>(sm + (tt >> 1) * SL + xpad<L>(d));
-    z[tt & 1] = v;
+  bool vec = false;
+  if constexpr (TT % 4 == 0)
+    vec = (P.n_t & 3) == 0 && (gs & 3) == 0 && m0 + TT <= P.n_t && (reinterpret_cast<uintptr_t>(g) & 15) == 0;
+  if (vec) {
+    // 16-byte loads: four time samples of one detector, the real and imaginary parts of two
+    // transforms
+    constexpr int Q = TT >= 4 ? TT / 4 : 1;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < nd * Q; e += blockDim.x) {
+      const int d = e / Q, q = e - d * Q;
+      const float4 v = __ldg(reinterpret_cast<const float4*>(gb + (size_t)d * P.n_t + m0) + q);
+      const float gm = P.gamma[d];
+      sm[(2 * q) * SL + xpad<L>(d)] = make_float2(gm * v.x, gm * v.y);
+      sm[(2 * q + 1) * SL + xpad<L>(d)] = make_float2(gm * v.z, gm * v.w);
+    }
+  } else {
+    for (int e = threadIdx.x; e < nd * TT; e += blockDim.x) {
+      const int d = e / TT, tt = e % TT;
+      const int m = m0 + tt;
+      const float v = m < P.n_t ? P.gamma[d] * gb[(size_t)d * P.n_t + m] : 0.f;
+      float* z = reinterpret_cast<float*>(sm + (tt >> 1) * SL + xpad<L>(d));
+      z[tt & 1] = v;
+    }
   }
   __syncthreads();
   {
@@ -368,6 +452,21 @@ __global__ void __launch_bounds__(1024) k_theta_adj(DevPlan P, const float* __re
     else fft<L, false>(sm + gi * SL, P.fdet, gt, nt, P.n_det, P.n_det, nullptr, nullptr, smptw);
   }
   float2* Gp = Y + (size_t)b * ys;
+  if ((P.n_t & 1) == 0 && (ys & 1) == 0 && m0 + TT <= P.n_t && (reinterpret_cast<uintptr_t>(Y) & 15) == 0) {
+    // both time samples of a transform at once: one 16-byte store of two modes' values
+    constexpr int NP = TT / 2;
+    for (int e = threadIdx.x; e < (P.K + 1) * NP; e += blockDim.x) {
+      const int k = e / NP, pp = e - k * NP;
+      const int bin = k % nd;
+      const float2* z = sm + pp * SL;
+      const float2 Z = z[xpad<L>(colpos<L>(bin))];
+      const float2 Zc = cconj(z[xpad<L>(colpos<L>(bin == 0 ? 0 : nd - bin))]);
+      const float2 s2 = cscale(cadd(Z, Zc), 0.5f);
+      const float2 dd = csub(Z, Zc);
+      *reinterpret_cast<float4*>(Gp + (size_t)k * P.n_t + m0 + 2 * pp) = make_float4(s2.x, s2.y, 0.5f * dd.y, -0.5f * dd.x);
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < (P.K + 1) * TT; e += blockDim.x) {
     const int k = e / TT, tt = e % TT;
     const int m = m0 + tt;
@@ -397,21 +496,39 @@ __global__ void __launch_bounds__(1024) k_modes_adj(DevPlan P, const float2* __r
   const float2* Gp = Y + (size_t)b * ys + (size_t)k * P.n_t;
   float2* smptw = sm + xpad_len(L2);
   load_pass_tw(smptw, P.f2M, threadIdx.x, blockDim.x);
-  for (int j = threadIdx.x; j < L2; j += blockDim.x) {
-    float2 v = make_float2(0.f, 0.f);
-    if (j < P.n_t) v = Gp[j];
-    else if (j > L2 - P.n_t) v = Gp[L2 - j];
-    sm[xpad<L>(j)] = v;
-  }
-  __syncthreads();
   const float2 g0 = Gp[0];
-  fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, P.J + 1, nullptr, nullptr, smptw);
   float2* Dm = X + (size_t)b * xs + (size_t)k * J1;
   const bool low = P.low_on && k <= 1;
-  for (int j = threadIdx.x; j < J1; j += blockDim.x) {
-    float2 v = cscale(cadd(sm[xpad<L>(j)], g0), 0.5f);
-    if (low && j < kLowA) v = make_float2(0.f, 0.f);
-    Dm[j] = v;
+  if constexpr (L > 0) {
+    // as in k_modes_fwd: the even extension of the time samples straight into the
+    // first pass, the kept outputs j < J + 1 straight out of the last one
+    const int nt_ = P.n_t;
+    auto load = [&](int j) -> float2 {
+      if (j < nt_) return Gp[j];
+      if (j > L2 - nt_) return Gp[L2 - j];
+      return make_float2(0.f, 0.f);
+    };
+    auto store = [&](int j, float2 x) {
+      float2 v = cscale(cadd(x, g0), 0.5f);
+      if (low && j < kLowA) v = make_float2(0.f, 0.f);
+      Dm[j] = v;
+    };
+    __syncthreads();  // twiddles
+    fft_io<L, false>(sm, P.f2M, threadIdx.x, nt, J1, load, store, smptw);
+  } else {
+    for (int j = threadIdx.x; j < L2; j += blockDim.x) {
+      float2 v = make_float2(0.f, 0.f);
+      if (j < P.n_t) v = Gp[j];
+      else if (j > L2 - P.n_t) v = Gp[L2 - j];
+      sm[xpad<L>(j)] = v;
+    }
+    __syncthreads();
+    fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, P.J + 1, nullptr, nullptr, smptw);
+    for (int j = threadIdx.x; j < J1; j += blockDim.x) {
+      float2 v = cscale(cadd(sm[xpad<L>(j)], g0), 0.5f);
+      if (low && j < kLowA) v = make_float2(0.f, 0.f);
+      Dm[j] = v;
+    }
   }
   if (low) {
     // Dh[k][q] = sum_m cos(lam_q t_m) g'_k(t_m): one warp per low-mode node.
@@ -516,6 +633,54 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
   }
 }
 
+// Explicitly rounded arithmetic for the adjoint's scatter: the compiler may not fuse
+// or reorder these, so every inlined copy of the scatter (and the lane-0 recount of
+// a neighbour's sum) performs the same operations and gives the same bits.
+__device__ __forceinline__ void acc_rn(float2& acc, float w, float2 v) {
+  acc.x = __fmaf_rn(w, v.x, acc.x);
+  acc.y = __fmaf_rn(w, v.y, acc.y);
+}
+__device__ __forceinline__ float2 cadd_rn(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+__device__ __forceinline__ float2 cmulc_rn(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(__fmaf_rn(a.x, b.x, __fmul_rn(a.y, b.y)), __fmaf_rn(a.y, b.x, -__fmul_rn(a.x, b.y)));
+}
+// bilinear weights (1-a)(1-b), (1-a)b, a(1-b), ab
+__device__ __forceinline__ float w_l0(const PolarEntry& e) { return __fmul_rn(__fsub_rn(1.f, e.a), __fsub_rn(1.f, e.b)); }
+__device__ __forceinline__ float w_l1(const PolarEntry& e) { return __fmul_rn(__fsub_rn(1.f, e.a), e.b); }
+__device__ __forceinline__ float w_r0(const PolarEntry& e) { return __fmul_rn(e.a, __fsub_rn(1.f, e.b)); }
+__device__ __forceinline__ float w_r1(const PolarEntry& e) { return __fmul_rn(e.a, e.b); }
+
+// A thread's first run of a column (run runoff[c] + tid), loaded ahead of the column's
+// scatter in three steps -- run record, first point, polar sample -- each issued a
+// phase before it is needed, so that the column transform in between hides the
+// latency of the dependent global loads.
+struct RunAhead {
+  int s = -1, e = 0, k = 0;  // first point, end, key (s < 0: no run for this thread)
+  bool prev = false, next = false;  // runs with keys k-1 / k+1 in the same column
+  PolarEntry pe{};
+  float2 v = make_float2(0.f, 0.f);
+};
+
+__device__ __forceinline__ void run_ahead_record(const DevPlan& P, int c, int tid, RunAhead& q) {
+  q.s = -1;
+  if (c < 0 || c > P.ncol - 2) return;
+  const int r0 = P.runoff[c], r1 = P.runoff[c + 1], r = r0 + tid;
+  if (r >= r1) return;
+  const int2 run = P.runs[r], nx = P.runs[r + 1];
+  const int pk = r > r0 ? P.runs[r - 1].y : 0;
+  q.s = run.x;
+  q.e = nx.x;
+  q.k = run.y;
+  q.prev = r > r0 && pk == run.y - 1;
+  q.next = r + 1 < r1 && nx.y == run.y + 1;
+}
+__device__ __forceinline__ void run_ahead_point(const DevPlan& P, RunAhead& q) {
+  if (q.s >= 0) q.pe = P.pts[q.s];
+}
+__device__ __forceinline__ void run_ahead_sample(const float2* __restrict__ Yb, RunAhead& q) {
+  if (q.s >= 0) q.v = Yb[q.pe.p];
+}
+
 // Transposed bilinear weights of the points with stencil column i0 = c, added
 // into the column buffers of c (weight 1-a) and c+1 (weight a); either may be
 // null.  The sum is the same on every call, bit for bit: each run of points
@@ -525,35 +690,55 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
 // cell k0 by the run with key k0, which first adds the row-k0 part of the run
 // with key k0-1 if there is one, and cell k0+1 by the run with key k0 when no
 // run has key k0+1.  No atomics: the order of every addition is fixed.
-// The conj(phase) of the column transform is applied once per cell.
+// The conj(phase) of the column transform is applied once per cell.  `q` holds
+// this thread's first run of the column, loaded ahead (RunAhead).
 template <int L>
 __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* __restrict__ Yb, int c, float2* left,
-                                               float2* right, int tid, int NT) {
+                                               float2* right, int tid, int NT, const RunAhead& q) {
   const unsigned full = 0xffffffffu;
   const int lane = tid & 31;
   const int r0 = P.runoff[c], r1 = P.runoff[c + 1];
+  bool first = true;
   // warp-uniform loop (NT is a multiple of 32): lane l takes run base + l
   for (int base = r0 + (tid - lane); base < r1; base += NT) {
     const int r = base + lane;
     const bool valid = r < r1;
     int k = 0, s = 0;
+    bool has_prev = false, has_next = false;
     float2 la = make_float2(0.f, 0.f), lb = la, ra = la, rb = la;
+    auto add = [&](const PolarEntry& pe, float2 v) {
+      acc_rn(la, w_l0(pe), v);
+      acc_rn(lb, w_l1(pe), v);
+      acc_rn(ra, w_r0(pe), v);
+      acc_rn(rb, w_r1(pe), v);
+    };
     if (valid) {
-      const int2 run = P.runs[r];
-      k = run.y;
-      s = run.x;
-      const int e = P.runs[r + 1].x;
-      for (int i = s; i < e; ++i) {
-        const PolarEntry pe = P.pts[i];
-        const float2 v = Yb[pe.p];
-        const float wl0 = (1.f - pe.a) * (1.f - pe.b), wl1 = (1.f - pe.a) * pe.b;
-        const float wr0 = pe.a * (1.f - pe.b), wr1 = pe.a * pe.b;
-        la.x += wl0 * v.x; la.y += wl0 * v.y;
-        lb.x += wl1 * v.x; lb.y += wl1 * v.y;
-        ra.x += wr0 * v.x; ra.y += wr0 * v.y;
-        rb.x += wr1 * v.x; rb.y += wr1 * v.y;
+      int e;
+      if (first) {  // r = r0 + tid: the run loaded ahead
+        k = q.k;
+        s = q.s;
+        e = q.e;
+        has_prev = q.prev;
+        has_next = q.next;
+        add(q.pe, q.v);
+        for (int i = s + 1; i < e; ++i) {
+          const PolarEntry pe = P.pts[i];
+          add(pe, Yb[pe.p]);
+        }
+      } else {
+        const int2 run = P.runs[r], nx = P.runs[r + 1];
+        k = run.y;
+        s = run.x;
+        e = nx.x;
+        has_prev = P.runs[r - 1].y == k - 1;  // r > r0 here
+        has_next = r + 1 < r1 && nx.y == k + 1;
+        for (int i = s; i < e; ++i) {
+          const PolarEntry pe = P.pts[i];
+          add(pe, Yb[pe.p]);
+        }
       }
     }
+    first = false;
     // row-k parts of the run with key k-1: from the lane before, or (lane 0) summed again
     float2 plb, prb;
     plb.x = __shfl_up_sync(full, lb.x, 1);
@@ -561,33 +746,29 @@ __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* _
     prb.x = __shfl_up_sync(full, rb.x, 1);
     prb.y = __shfl_up_sync(full, rb.y, 1);
     if (!valid) continue;
-    const int2 prev = r > r0 ? P.runs[r - 1] : make_int2(0, 0);
-    const bool has_prev = r > r0 && prev.y == k - 1;
     if (has_prev && lane == 0) {
       plb = make_float2(0.f, 0.f);
       prb = plb;
-      for (int i = prev.x; i < s; ++i) {
+      for (int i = P.runs[r - 1].x; i < s; ++i) {
         const PolarEntry pe = P.pts[i];
         const float2 v = Yb[pe.p];
-        const float wl1 = (1.f - pe.a) * pe.b, wr1 = pe.a * pe.b;
-        plb.x += wl1 * v.x; plb.y += wl1 * v.y;
-        prb.x += wr1 * v.x; prb.y += wr1 * v.y;
+        acc_rn(plb, w_l1(pe), v);
+        acc_rn(prb, w_r1(pe), v);
       }
     }
-    const bool has_next = r + 1 < r1 && P.runs[r + 1].y == k + 1;
     const int ra_row = wrapN(k, P.N), rb_row = wrapN(k + 1, P.N);
     const int qa = xpad<L>(colpos<L>(ra_row)), qb = xpad<L>(colpos<L>(rb_row));
     const float2 pa = __ldg(&P.phase[ra_row]);
     if (has_prev) {
-      la = cadd(la, plb);
-      ra = cadd(ra, prb);
+      la = cadd_rn(la, plb);
+      ra = cadd_rn(ra, prb);
     }
-    if (left != nullptr) left[qa] = cadd(left[qa], cmulc(la, pa));
-    if (right != nullptr) right[qa] = cadd(right[qa], cmulc(ra, pa));
+    if (left != nullptr) left[qa] = cadd_rn(left[qa], cmulc_rn(la, pa));
+    if (right != nullptr) right[qa] = cadd_rn(right[qa], cmulc_rn(ra, pa));
     if (!has_next) {
       const float2 pb = __ldg(&P.phase[rb_row]);
-      if (left != nullptr) left[qb] = cadd(left[qb], cmulc(lb, pb));
-      if (right != nullptr) right[qb] = cadd(right[qb], cmulc(rb, pb));
+      if (left != nullptr) left[qb] = cadd_rn(left[qb], cmulc_rn(lb, pb));
+      if (right != nullptr) right[qb] = cadd_rn(right[qb], cmulc_rn(rb, pb));
     }
   }
 }
@@ -609,11 +790,18 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
   const float2* Yb = Y + (size_t)b * ys;
   float2* Xb = X + (size_t)b * xs;
   auto slot = [&](int c) { return sm + ((c - c0) & 1) * SL; };
+  RunAhead ahead;  // this thread's first run of the next column to scatter
   {
     float2* first = slot(c0);
+    run_ahead_record(P, c0 - 1, tid, ahead);
     for (int q = tid; q < SL; q += NT) first[q] = make_float2(0.f, 0.f);
+    run_ahead_point(P, ahead);
+    run_ahead_sample(Yb, ahead);
     __syncthreads();
-    if (c0 >= 1) scatter_column<L>(P, Yb, c0 - 1, nullptr, first, tid, NT);  // right side of the previous column
+    if (c0 >= 1) scatter_column<L>(P, Yb, c0 - 1, nullptr, first, tid, NT, ahead);  // right side of the previous column
+    run_ahead_record(P, c0, tid, ahead);
+    run_ahead_point(P, ahead);
+    run_ahead_sample(Yb, ahead);
   }
 #pragma unroll 1
   for (int c = c0; c < c1; ++c) {
@@ -622,7 +810,9 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
     if (nxt != nullptr)
       for (int q = tid; q < SL; q += NT) nxt[q] = make_float2(0.f, 0.f);
     __syncthreads();
-    if (c <= P.ncol - 2) scatter_column<L>(P, Yb, c, cur, nxt, tid, NT);
+    if (c <= P.ncol - 2) scatter_column<L>(P, Yb, c, cur, nxt, tid, NT, ahead);
+    // the next column's first runs: record now, point before the transform, sample half-way
+    run_ahead_record(P, c + 1 < c1 ? c + 1 : -1, tid, ahead);
     __syncthreads();
     if (c == 0) {
       // Column 0 also receives the mirrored samples of the other half circle:
@@ -635,14 +825,15 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
         } else {
           const int pa = xpad<L>(colpos<L>(q)), pb = xpad<L>(colpos<L>(N - q));
           const float2 A = cur[pa], B = cur[pb];
-          cur[pa] = cadd(A, cconj(B));
-          cur[pb] = cadd(B, cconj(A));
+          cur[pa] = cadd_rn(A, cconj(B));
+          cur[pb] = cadd_rn(B, cconj(A));
         }
       }
       __syncthreads();
     }
     // inverse column DFT (conj(phase) already applied by the scatter), first n rows only
-    col_fft_inv<L>(cur, P.fN, smtw, tid, NT, nt, P.n, nullptr);
+    run_ahead_point(P, ahead);
+    col_fft_inv<L>(cur, P.fN, smtw, tid, NT, nt, P.n, nullptr, [&]() { run_ahead_sample(Yb, ahead); });
     float2* col = Xb + (size_t)c * P.n;  // R'[c][0..n): contiguous
     for (int iy = tid; iy < P.n; iy += NT) col[iy] = cur[xpad<L>(iy)];
     __syncthreads();
@@ -728,7 +919,8 @@ __global__ void __launch_bounds__(1024) k_modes_inv(DevPlan P, const float2* __r
   const float2* Gp = Y + (size_t)b * ys + (size_t)k * P.n_t;
   float2* smptw = sm + xpad_len(L2);
   load_pass_tw(smptw, P.f2M, threadIdx.x, blockDim.x);
-  for (int j = threadIdx.x; j < L2; j += blockDim.x) {
+  float2* Dm = X + (size_t)b * xs + (size_t)k * J1;
+  auto load = [&](int j) -> float2 {
     float2 v = make_float2(0.f, 0.f);
     const int m = j <= P.M ? j : L2 - j;
     if (m > 0 && m < P.n_t) {
@@ -736,12 +928,19 @@ __global__ void __launch_bounds__(1024) k_modes_inv(DevPlan P, const float2* __r
       if (m == P.n_t - 1) v = cscale(v, 0.5f);
       if (j > P.M) v = make_float2(-v.x, -v.y);
     }
-    sm[xpad<L>(j)] = v;
+    return v;
+  };
+  if constexpr (L > 0) {
+    // the odd extension straight into the first pass, the kept outputs straight out
+    auto store = [&](int j, float2 x) { Dm[j] = x; };
+    __syncthreads();  // twiddles
+    fft_io<L, false>(sm, P.f2M, threadIdx.x, nt, J1, load, store, smptw);
+  } else {
+    for (int j = threadIdx.x; j < L2; j += blockDim.x) sm[xpad<L>(j)] = load(j);
+    __syncthreads();
+    fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, J1, nullptr, nullptr, smptw);
+    for (int j = threadIdx.x; j < J1; j += blockDim.x) Dm[j] = sm[xpad<L>(j)];
   }
-  __syncthreads();
-  fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, J1, nullptr, nullptr, smptw);
-  float2* Dm = X + (size_t)b * xs + (size_t)k * J1;
-  for (int j = threadIdx.x; j < J1; j += blockDim.x) Dm[j] = sm[xpad<L>(j)];
 }
 
 // Polar sample (ring j, angle l') of the half circle from the angle-major
