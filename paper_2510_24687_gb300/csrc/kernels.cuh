@@ -43,6 +43,17 @@ __device__ __forceinline__ float2 mul_mipow(float2 v, int k) {
 }
 __device__ __forceinline__ int wrapN(int q, int N) { return q < 0 ? q + N : q; }
 
+// The column phase e^{i q dxi} of FFT bin q from the two-level table staged in shared
+// memory (load_phase2): one complex product instead of a global load.
+__device__ __forceinline__ void load_phase2(float2* dst, const DevPlan& P, int tid, int nthr) {
+  for (int i = tid; i < P.ph_lo + 64; i += nthr) dst[i] = P.phase2[i];
+}
+__device__ __forceinline__ float2 phase_at(const float2* t, const DevPlan& P, int q) {
+  const float2 a = t[q >> 6], b = t[P.ph_lo + (q & 63)];
+  float2 v = make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+  if (P.ph_flip && q >= (P.N >> 1)) v = make_float2(-v.x, -v.y);
+  return v;
+}
 
 // ------------------------------------------------------------------ forward
 
@@ -122,8 +133,10 @@ __global__ void TAT_COLS_BOUNDS_F k_cols_fwd(DevPlan P, const float2* __restrict
   float2* slot0 = sm;
   float2* slot1 = sm + SL;
   float2* smtw = sm + 2 * SL;  // four-step twiddles
+  float2* smph = smtw + kFourStepTw;  // two-level phase table
   const int tid = threadIdx.x, NT = blockDim.x;
   load_fourstep_tw(smtw, P.fN.fstw, tid, NT);
+  load_phase2(smph, P, tid, NT);
   const int c0 = strip * S;
   const int c1 = min(c0 + S, P.ncol - 1);  // owned stencil columns i0 in [c0, c1)
   const int ncols = c1 - c0 + 1;           // spectrum columns c0..c1
@@ -170,7 +183,7 @@ __global__ void TAT_COLS_BOUNDS_F k_cols_fwd(DevPlan P, const float2* __restrict
         const float a = pe.a, bb = pe.b;
         const float2 va = cadd(cscale(A[qa], 1.f - a), cscale(B[qa], a));
         const float2 vb = cadd(cscale(A[qb], 1.f - a), cscale(B[qb], a));
-        Yb[pe.p] = cadd(cscale(cmul(va, __ldg(&P.phase[ra])), 1.f - bb), cscale(cmul(vb, __ldg(&P.phase[rb])), bb));
+        Yb[pe.p] = cadd(cscale(cmul(va, phase_at(smph, P, ra)), 1.f - bb), cscale(cmul(vb, phase_at(smph, P, rb)), bb));
       }
     }
     __syncthreads();
@@ -694,7 +707,8 @@ __device__ __forceinline__ void run_ahead_sample(const float2* __restrict__ Yb, 
 // this thread's first run of the column, loaded ahead (RunAhead).
 template <int L>
 __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* __restrict__ Yb, int c, float2* left,
-                                               float2* right, int tid, int NT, const RunAhead& q) {
+                                               float2* right, int tid, int NT, const RunAhead& q,
+                                               const float2* smph) {
   const unsigned full = 0xffffffffu;
   const int lane = tid & 31;
   const int r0 = P.runoff[c], r1 = P.runoff[c + 1];
@@ -758,7 +772,7 @@ __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* _
     }
     const int ra_row = wrapN(k, P.N), rb_row = wrapN(k + 1, P.N);
     const int qa = xpad<L>(colpos<L>(ra_row)), qb = xpad<L>(colpos<L>(rb_row));
-    const float2 pa = __ldg(&P.phase[ra_row]);
+    const float2 pa = phase_at(smph, P, ra_row);
     if (has_prev) {
       la = cadd_rn(la, plb);
       ra = cadd_rn(ra, prb);
@@ -766,7 +780,7 @@ __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* _
     if (left != nullptr) left[qa] = cadd_rn(left[qa], cmulc_rn(la, pa));
     if (right != nullptr) right[qa] = cadd_rn(right[qa], cmulc_rn(ra, pa));
     if (!has_next) {
-      const float2 pb = __ldg(&P.phase[rb_row]);
+      const float2 pb = phase_at(smph, P, rb_row);
       if (left != nullptr) left[qb] = cadd_rn(left[qb], cmulc_rn(lb, pb));
       if (right != nullptr) right[qb] = cadd_rn(right[qb], cmulc_rn(rb, pb));
     }
@@ -784,7 +798,9 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
   const int SL = xpad_len(N);
   const int tid = threadIdx.x, NT = blockDim.x;
   float2* smtw = sm + 2 * SL;  // four-step twiddles
+  float2* smph = smtw + kFourStepTw;  // two-level phase table
   load_fourstep_tw(smtw, P.fN.fstw, tid, NT);
+  load_phase2(smph, P, tid, NT);
   const int c0 = strip * S;
   const int c1 = min(c0 + S, P.ncol);  // owned columns [c0, c1)
   const float2* Yb = Y + (size_t)b * ys;
@@ -798,7 +814,7 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
     run_ahead_point(P, ahead);
     run_ahead_sample(Yb, ahead);
     __syncthreads();
-    if (c0 >= 1) scatter_column<L>(P, Yb, c0 - 1, nullptr, first, tid, NT, ahead);  // right side of the previous column
+    if (c0 >= 1) scatter_column<L>(P, Yb, c0 - 1, nullptr, first, tid, NT, ahead, smph);  // right side of the previous column
     run_ahead_record(P, c0, tid, ahead);
     run_ahead_point(P, ahead);
     run_ahead_sample(Yb, ahead);
@@ -810,7 +826,7 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
     if (nxt != nullptr)
       for (int q = tid; q < SL; q += NT) nxt[q] = make_float2(0.f, 0.f);
     __syncthreads();
-    if (c <= P.ncol - 2) scatter_column<L>(P, Yb, c, cur, nxt, tid, NT, ahead);
+    if (c <= P.ncol - 2) scatter_column<L>(P, Yb, c, cur, nxt, tid, NT, ahead, smph);
     // the next column's first runs: record now, point before the transform, sample half-way
     run_ahead_record(P, c + 1 < c1 ? c + 1 : -1, tid, ahead);
     __syncthreads();

@@ -31,8 +31,8 @@ inline Shapes shapes(const tat_plan_s* Pl, int batch) {
   s.cols_grid_f = dim3(((P.ncol - 1 + c.strip - 1) / c.strip) * batch);
   s.cols_grid_a = dim3(((P.ncol + c.strip - 1) / c.strip) * batch);
   s.cols_block = c.cols_threads;
-  s.cols_smem_f = (2 * (size_t)xpad_len(P.N) + kFourStepTw) * sizeof(float2);
-  s.cols_smem_a = (2 * (size_t)xpad_len(P.N) + kFourStepTw) * sizeof(float2);
+  s.cols_smem_f = (2 * (size_t)xpad_len(P.N) + kFourStepTw + P.ph_lo + 64) * sizeof(float2);
+  s.cols_smem_a = (2 * (size_t)xpad_len(P.N) + kFourStepTw + P.ph_lo + 64) * sizeof(float2);
   s.cols_smem_i = ((size_t)xpad_len(P.N) + kFourStepTw) * sizeof(float2);
   s.ntiles = (P.J + c.rings_per_cta - 1) / c.rings_per_cta;
   s.rings_grid = dim3(s.ntiles + P.n_low, batch);

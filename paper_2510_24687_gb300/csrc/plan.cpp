@@ -401,6 +401,23 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
       ph[q] = make_float2((float)c, (float)s);
     }
     TAT_TRY(upload(P, ph, &d.phase));
+    // Two-level form for the column kernels' shared memory: with q unsigned,
+    // e^{2 pi i q (n-1)/(2N)} = hi[q >> 6] lo[q & 63]; the signed bins q >= N/2 differ
+    // by e^{-i pi (n-1)} = (-1)^(n-1).
+    d.ph_lo = (d.N + 63) / 64;
+    d.ph_flip = (n - 1) & 1;
+    std::vector<float2> ph2(d.ph_lo + 64);
+    for (int a = 0; a < d.ph_lo; ++a) {
+      double c, s;
+      cos_sin_2pi(64LL * a * (n - 1), 2LL * d.N, &c, &s);
+      ph2[a] = make_float2((float)c, (float)s);
+    }
+    for (int b = 0; b < 64; ++b) {
+      double c, s;
+      cos_sin_2pi((long long)b * (n - 1), 2LL * d.N, &c, &s);
+      ph2[d.ph_lo + b] = make_float2((float)c, (float)s);
+    }
+    TAT_TRY(upload(P, ph2, &d.phase2));
   }
   // Support disk Pi_Omega0: node kept iff (2ix-(n-1))^2 + (2iy-(n-1))^2 <= (r (n-1))^2.
   {

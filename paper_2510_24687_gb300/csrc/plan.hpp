@@ -58,6 +58,9 @@ struct DevPlan {
   float adj_scale;                 // (h^2/2pi) * W_Y / W_X
   FftDev fN, fphi, f2M, fdet;
   const float2* phase;             // [N] e^{i q dxi}, q the signed frequency of FFT bin
+  const float2* phase2;            // [ph_lo + 64] two-level form: phase[q] = hi[q >> 6] * lo[q & 63],
+                                   // negated for q >= N/2 when ph_flip (hi at 0, lo at ph_lo)
+  int ph_lo, ph_flip;
   const int2* rowrange;            // [n] support columns [lo, hi) of each image row
   const float* gamma;              // [n_det] 1 on the arc Gamma, else 0
   const PolarEntry* pts;           // [n_points]
