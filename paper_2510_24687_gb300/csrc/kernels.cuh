@@ -55,6 +55,27 @@ __device__ __forceinline__ float2 phase_at(const float2* t, const DevPlan& P, in
   return v;
 }
 
+// 16-byte asynchronous copy global -> shared (cp.async, completion by wait_group: a
+// hardware wait, no spinning).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// The angular stage's per-tile multiplier block (bt_bs floats of a tiled table) copied to
+// shared memory at `dst` (16-byte aligned) with asynchronous copies; the caller waits
+// (cp_async_wait_all + barrier) before reading it.
+__device__ __forceinline__ void stage_multipliers(float* dst, const float* tiled, int tile, int bs) {
+  const float4* src = reinterpret_cast<const float4*>(tiled + (size_t)tile * bs);
+  for (int i = threadIdx.x; i < bs / 4; i += blockDim.x) cp_async16(dst + 4 * i, src + i);
+  cp_async_commit();
+}
+__device__ __forceinline__ float* align16(void* p) {
+  return reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
+}
+
 // ------------------------------------------------------------------ forward
 
 // Row kernels: up to 1024 threads (4 row pairs); at L = 8192 one row pair of 512
@@ -91,6 +112,8 @@ __global__ void TAT_ROWS_BOUNDS k_rows_fwd(DevPlan P, const float* __restrict__ 
   // this CTA are adjacent rows, so consecutive threads write consecutive rows.
   float2* Xb = X + (size_t)b * xs;
   const int pair0 = blockIdx.x * RP;
+  // the two rows of a pair are adjacent in R[q][.]: one 16-byte store when aligned
+  const bool vec = (P.n & 1) == 0 && (xs & 1) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
   for (int e = threadIdx.x; e < P.ncol * RP; e += blockDim.x) {
     const int q = e / RP, gg = e - q * RP;
     const int py1 = 2 * (pair0 + gg);
@@ -103,8 +126,13 @@ __global__ void TAT_ROWS_BOUNDS k_rows_fwd(DevPlan P, const float* __restrict__ 
     const float2 x2 = make_float2(0.5f * dd.y, -0.5f * dd.x);
     const float2 ph = cscale(P.phase[q], P.h2_2pi);
     float2* col = Xb + (size_t)q * P.n;
-    col[py1] = cmul(ph, x1);
-    if (py1 + 1 < P.n) col[py1 + 1] = cmul(ph, x2);
+    const float2 y1 = cmul(ph, x1), y2 = cmul(ph, x2);
+    if (py1 + 1 < P.n && vec) {
+      *reinterpret_cast<float4*>(col + py1) = make_float4(y1.x, y1.y, y2.x, y2.y);  // rows py1, py1 + 1
+    } else {
+      col[py1] = y1;
+      if (py1 + 1 < P.n) col[py1 + 1] = y2;
+    }
   }
 }
 
@@ -244,6 +272,8 @@ __global__ void __launch_bounds__(1024) k_rings_fwd(DevPlan P, const float2* __r
   float2* buf = sm + g * SL;
   float2* smptw = sm + RPC * SL;
   float2* smtw = smptw + P.fphi.ptw_len;
+  float* smB = align16(smtw + kFourStepTw);  // this tile's multipliers [k][g]
+  stage_multipliers(smB, P.Btt, blockIdx.x, P.bt_bs);  // in flight during the loads and the FFTs
   load_pass_tw(smptw, P.fphi, threadIdx.x, blockDim.x);
   load_fourstep_tw(smtw, P.fphi.fstw, threadIdx.x, blockDim.x);
   const int rbase = 1 + blockIdx.x * RPC;
@@ -251,24 +281,28 @@ __global__ void __launch_bounds__(1024) k_rings_fwd(DevPlan P, const float2* __r
   const bool valid = r <= P.J;
   const int q4 = P.n_phi / 4;
   const float2* Fr = Yb + (size_t)r * P.nh;
-  for (int l = gt; l < P.n_phi; l += nt) {
-    float2 v = make_float2(0.f, 0.f);
-    if (valid) {
-      if (l < q4) v = Fr[l + q4];
-      else if (l < 3 * q4) v = cconj(Fr[l - q4]);
-      else v = Fr[l - 3 * q4];
-    }
-    buf[xpad<L>(l)] = v;
+  // Each half-circle sample F(l') is read once (16-byte loads, two samples each) and lands
+  // at l = l' - n_phi/4 (mod n_phi) and, conjugated, at l' + n_phi/4 (F(phi + pi) = conj F(phi)).
+#pragma unroll 4
+  for (int i = gt; i < P.nh / 2; i += nt) {
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) w = *reinterpret_cast<const float4*>(Fr + 2 * i);
+    const int l0 = 2 * i, l1 = l0 + 1;
+    buf[xpad<L>(l0 >= q4 ? l0 - q4 : l0 + 3 * q4)] = make_float2(w.x, w.y);
+    buf[xpad<L>(l0 + q4)] = make_float2(w.x, -w.y);
+    buf[xpad<L>(l1 >= q4 ? l1 - q4 : l1 + 3 * q4)] = make_float2(w.z, w.w);
+    buf[xpad<L>(l1 + q4)] = make_float2(w.z, -w.w);
   }
   __syncthreads();
   if constexpr (FourStep<L>::on) col_fft_fwd<L>(buf, P.fphi, smtw, gt, nt, nt, P.n_phi, nullptr);
   else fft<L, false>(buf, P.fphi, gt, nt, P.n_phi, P.K + 1, nullptr, nullptr, smptw);
+  cp_async_wait_all();
+  __syncthreads();
   for (int e = threadIdx.x; e < (P.K + 1) * RPC; e += blockDim.x) {
     const int k = e / RPC, gg = e % RPC;
     const int rr = rbase + gg;
     if (rr > P.J) continue;
-    const float bt = (P.low_on && k <= 1 && rr < kLowA) ? 0.f : P.Bt[(size_t)k * J1 + rr];
-    Xb[(size_t)k * J1 + rr] = mul_ipow(cscale(sm[gg * SL + xpad<L>(colpos<L>(k))], bt), k);
+    Xb[(size_t)k * J1 + rr] = mul_ipow(cscale(sm[gg * SL + xpad<L>(colpos<L>(k))], smB[e]), k);
   }
 }
 
@@ -595,18 +629,18 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
   const int SL = xpad_len(P.n_phi);
   float2* smptw = sm + RPC * SL;
   float2* smtw = smptw + P.fphi.ptw_len;
+  float* smB = align16(smtw + kFourStepTw);  // this tile's multipliers [k][g]
+  stage_multipliers(smB, INV ? P.Bit : P.Btt, blockIdx.x, P.bt_bs);
   load_pass_tw(smptw, P.fphi, threadIdx.x, blockDim.x);
   load_fourstep_tw(smtw, P.fphi.fstw, threadIdx.x, blockDim.x);
   const int rbase = 1 + blockIdx.x * RPC;
+  cp_async_wait_all();
+  __syncthreads();
   for (int e = threadIdx.x; e < (P.K + 1) * RPC; e += blockDim.x) {
     const int k = e / RPC, gg = e % RPC;
     const int rr = rbase + gg;
     float2 w = make_float2(0.f, 0.f);
-    if constexpr (INV) {
-      if (rr <= P.J) w = mul_mipow(cscale(Xb[(size_t)k * J1 + rr], P.Binv[(size_t)k * J1 + rr]), k + 1);
-    } else if (rr <= P.J && !(P.low_on && k <= 1 && rr < kLowA)) {
-      w = mul_mipow(cscale(Xb[(size_t)k * J1 + rr], P.Bt[(size_t)k * J1 + rr]), k);
-    }
+    if (rr <= P.J) w = mul_mipow(cscale(Xb[(size_t)k * J1 + rr], smB[e]), INV ? k + 1 : k);
     float2* bg = sm + gg * SL;
     bg[xpad<L>(colpos<L>(k))] = w;
     if (k >= 1 && k < P.K) {
@@ -873,13 +907,26 @@ __device__ __forceinline__ void rows_inverse_dft(const DevPlan& P, const float2*
   // H[q] = conj(phase[q]) R'[q] for q < N/2, H[N-q] = conj(H[q]), H[N/2] = 0;
   // consecutive threads read consecutive rows of one column.
   const int pair0 = blockIdx.x * RP;
+  // the two rows of a pair are adjacent in R'[q][.]: one 16-byte load when aligned
+  const bool vec = (P.n & 1) == 0 && (reinterpret_cast<uintptr_t>(Xb) & 15) == 0;
+#pragma unroll 4
   for (int e = threadIdx.x; e < P.ncol * RP; e += blockDim.x) {
     const int q = e / RP, gg = e - q * RP;
     const int py1 = 2 * (pair0 + gg);
     float2* bg = sm + gg * SL;
     const float2* col = Xb + (size_t)q * P.n;
-    float2 h1 = py1 < P.n ? cmulc(col[py1], P.phase[q]) : make_float2(0.f, 0.f);
-    float2 h2 = py1 + 1 < P.n ? cmulc(col[py1 + 1], P.phase[q]) : make_float2(0.f, 0.f);
+    float2 r1 = make_float2(0.f, 0.f), r2 = r1;
+    if (vec && py1 < P.n) {
+      const float4 w = *reinterpret_cast<const float4*>(col + py1);
+      r1 = make_float2(w.x, w.y);
+      r2 = make_float2(w.z, w.w);
+    } else {
+      if (py1 < P.n) r1 = col[py1];
+      if (py1 + 1 < P.n) r2 = col[py1 + 1];
+    }
+    const float2 phq = __ldg(&P.phase[q]);
+    float2 h1 = py1 < P.n ? cmulc(r1, phq) : make_float2(0.f, 0.f);
+    float2 h2 = py1 + 1 < P.n ? cmulc(r2, phq) : make_float2(0.f, 0.f);
     if (q == 0) { h1.y = 0.f; h2.y = 0.f; }
     bg[xpad<L>(colpos<L>(q))] = make_float2(h1.x - h2.y, h1.y + h2.x);
     if (q > 0) bg[xpad<L>(colpos<L>(N - q))] = make_float2(h1.x + h2.y, h2.x - h1.y);  // conj(h1) + i conj(h2)

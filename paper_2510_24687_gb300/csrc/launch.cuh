@@ -37,7 +37,8 @@ inline Shapes shapes(const tat_plan_s* Pl, int batch) {
   s.ntiles = (P.J + c.rings_per_cta - 1) / c.rings_per_cta;
   s.rings_grid = dim3(s.ntiles + P.n_low, batch);
   s.rings_block = c.rings_per_cta * c.nt_phi;
-  s.rings_smem = ((size_t)c.rings_per_cta * xpad_len(P.n_phi) + P.fphi.ptw_len + kFourStepTw) * sizeof(float2);
+  s.rings_smem = ((size_t)c.rings_per_cta * xpad_len(P.n_phi) + P.fphi.ptw_len + kFourStepTw) * sizeof(float2) +
+                 ((size_t)P.bt_bs + 4) * sizeof(float);  // + the tile's multiplier block, 16-byte aligned
   if (s.rings_smem < 96 * sizeof(float)) s.rings_smem = 96 * sizeof(float);
   s.modes_grid = dim3(P.K + 1, batch);
   s.modes_block = c.nt_2M;

@@ -497,6 +497,26 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
         Bi[(size_t)k * (d.J + 1) + j] = (float)(dJ * dt / n_det);
       }
     TAT_TRY(upload(P, Bi, &d.Binv));
+    // The same multipliers by ring tile, so that each CTA of the angular stage copies its
+    // block with 16-byte asynchronous copies: [tile][k][g], ring 1 + tile*rpc + g.
+    {
+      const int rpc = rings_per_cta_for(n_phi);
+      const int ntiles = (d.J + rpc - 1) / rpc;
+      d.bt_bs = ((d.K + 1) * rpc + 3) / 4 * 4;
+      std::vector<float> tt((size_t)std::max(ntiles, 1) * d.bt_bs, 0.0f), ti(tt.size(), 0.0f);
+      for (int t = 0; t < ntiles; ++t)
+        for (int k = 0; k <= d.K; ++k)
+          for (int g = 0; g < rpc; ++g) {
+            const int rr = 1 + t * rpc + g;
+            if (rr > d.J) continue;
+            const size_t o = (size_t)t * d.bt_bs + (size_t)k * rpc + g;
+            const bool low_zero = low_on && k <= 1 && rr < kLowA;
+            tt[o] = low_zero ? 0.0f : Bt[(size_t)k * (d.J + 1) + rr];
+            ti[o] = Bi[(size_t)k * (d.J + 1) + rr];
+          }
+      TAT_TRY(upload(P, tt, &d.Btt));
+      TAT_TRY(upload(P, ti, &d.Bit));
+    }
     std::vector<float> Bh(2 * std::max(d.n_low, 1), 0.0f), Lc((size_t)std::max(d.n_low, 1) * n_t, 0.0f);
     for (int q = 0; q < d.n_low; ++q) {
       const int r = d.J + 1 + q;

@@ -69,6 +69,12 @@ struct DevPlan {
                                    // column by column; run r ends at runs[r+1].x (a sentinel closes the table)
   const int* runoff;               // [ncol+1] runs of column c: [runoff[c], runoff[c+1])
   const float* Bt;                 // [(K+1) x (J+1)] dlam*lam_j*J_k(lam_j)/n_phi
+  const float* Btt;                // Bt by ring tile: [tile][k][g], ring 1 + tile*rpc + g, g < rpc
+                                   // (rpc = rings_per_cta_for(n_phi)); each tile padded to bt_bs floats
+                                   // (a multiple of 4); zero for rings > J and, with the low-mode rule,
+                                   // for k <= 1 and rings < kLowA
+  const float* Bit;                // Binv in the same tiled layout (no low-mode zeros)
+  int bt_bs;                       // floats per tile block
   const float* Bh;                 // [2 x n_low]     w_q*dlam*lam_q*J_k(lam_q)/n_phi
   const float* Lcos;               // [n_low x n_t]   cos(lam_q t_m)
   const float2* cs_half;           // [nh] (cos phi, sin phi) of the half-circle angles
