@@ -1052,6 +1052,24 @@ def run_service(args, rank, world, local):
     value = job_throughput(SVC_REQ, world, 1e3 * wall)
     st = svc.stats()
 
+    # the same rounds with one graph per (size, operation) on each size's own stream instead of
+    # one graph launch for the whole flush
+    per_slot = pkg.TatService(memory_budget=8 << 30, max_batch=32, use_graphs=True, one_graph=False)
+    for _ in range(2):
+        for n, x, o in zip(sizes, xs, outs):
+            per_slot.submit(descs[n], "pair", x, o)
+        per_slot.flush()
+        per_slot.synchronize()
+    torch.cuda.synchronize()
+    t5 = time.perf_counter()
+    for _ in range(args.steps):
+        for n, x, o in zip(sizes, xs, outs):
+            per_slot.submit(descs[n], "pair", x, o)
+        per_slot.flush()
+        per_slot.synchronize()
+    per_slot_wall = (time.perf_counter() - t5) / args.steps
+    per_slot.close()
+
     # one request at a time through the same runtime (no batching across requests)
     solo = pkg.TatService(memory_budget=2 << 30, max_batch=1, use_graphs=True)
     for n, x, o in zip(sizes, xs, outs):
@@ -1091,6 +1109,58 @@ def run_service(args, rank, world, local):
         plain_lat.append(1e3 * (time.perf_counter() - t4))
     plain_wall = time.perf_counter() - t3
 
+    # latency under load: requests of the same mix arrive as a Poisson process at a stated
+    # fraction of the measured batch throughput; a host loop submits each when it arrives and
+    # flushes whatever has arrived (no waiting to fill a batch), then sleeps until the next
+    # arrival.  Latency runs from the arrival time to the completion callback (host clocks).
+    # The plain per-request path under the same arrivals is a FIFO queue of synchronous direct
+    # calls, each taking the service time measured for its size above.
+    plain_ms_by_size = {}
+    for n_, l_ in zip(sizes, plain_lat):
+        plain_ms_by_size.setdefault(n_, []).append(l_)
+    plain_ms_by_size = {k: float(np.median(v)) for k, v in plain_ms_by_size.items()}
+
+    def poisson_run(load, n_req, seed):
+        rng = np.random.default_rng(seed)
+        rate = load * value / world                      # requests per second on this GPU
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        order = [sizes[i % len(sizes)] for i in range(n_req)]
+        slots = [(xs[i % len(sizes)], outs[i % len(sizes)]) for i in range(n_req)]
+        ids, t_sub = [], []
+        torch.cuda.synchronize()
+        t_start = time.perf_counter()
+        i = 0
+        while i < n_req:
+            now = time.perf_counter() - t_start
+            while i < n_req and arrivals[i] <= now:
+                t_sub.append(time.perf_counter() - t_start)
+                ids.append(svc.submit(descs[order[i]], "pair", slots[i][0], slots[i][1]))
+                i += 1
+            svc.flush()
+            if i < n_req:
+                wait = arrivals[i] - (time.perf_counter() - t_start)
+                if wait > 0:
+                    time.sleep(wait)
+        svc.synchronize()
+        lat_ = np.array([(t_sub[k] - arrivals[k]) * 1e3 + svc.latency(ids[k])[0] for k in range(n_req)])
+        # the same arrivals through the plain path: one synchronous request at a time, FIFO
+        free_at, plat = 0.0, []
+        for k in range(n_req):
+            start = max(free_at, arrivals[k])
+            free_at = start + plain_ms_by_size[order[k]] / 1e3
+            plat.append((free_at - arrivals[k]) * 1e3)
+        return lat_, np.array(plat), n_req / (arrivals[-1])
+
+    under_load = {}
+    for load in (0.5, 0.8):
+        poisson_run(load, 128, 11)                       # warm: graphs for the batch sizes that occur
+        lat_l, plat_l, offered = poisson_run(load, 512, 12)
+        under_load[f"load_{load:.1f}"] = {
+            "offered_requests_per_s": offered,
+            "p50_ms": float(np.percentile(lat_l, 50)), "p99_ms": float(np.percentile(lat_l, 99)),
+            "plain_path_p50_ms": float(np.percentile(plat_l, 50)),
+            "plain_path_p99_ms": float(np.percentile(plat_l, 99)), "requests": 512}
+
     # end to end: the requests carry pinned host inputs and outputs; the service uploads,
     # computes and downloads each on its slot's stream, inside the timed region
     pins = [x.cpu().pin_memory() for x in xs]
@@ -1123,7 +1193,17 @@ def run_service(args, rank, world, local):
                 "config": service_config(sizes),
                 "latency_ms": {"p50": float(np.percentile(lat_np, 50)), "p99": float(np.percentile(lat_np, 99)),
                                "max": float(lat_np.max()), "samples": int(lat_np.size),
-                               "timing": "host clock, submission to completion callback"},
+                               "timing": "host clock, submission to completion callback; all 64 requests "
+                                         "queued at once, so p50 ~ p99 ~ the batch time"},
+                "latency_under_load": dict(under_load, arrivals="Poisson at the stated fraction of the measured "
+                                           "throughput, the request mix of the workload; each request submitted "
+                                           "on arrival and flushed at once; latency from arrival to completion "
+                                           "(host clocks); the plain path is a FIFO queue of synchronous direct "
+                                           "calls with the measured per-size service times"),
+                "flush": "one CUDA graph launch per flush: every size's batch a parallel branch",
+                "graph_per_slot": {"requests_per_s": SVC_REQ / per_slot_wall,
+                                   "what": "the same rounds with one graph per (size, operation), each on its "
+                                           "size's own stream"},
                 "one_at_a_time": {"requests_per_s": SVC_REQ / solo_wall,
                                   "p50_ms": float(np.percentile(solo_lat, 50)),
                                   "p99_ms": float(np.percentile(solo_lat, 99)),

@@ -53,6 +53,12 @@ typedef struct {
   int max_batch;        /* images per launch and per (problem, operation) pair, >= 1 */
   int use_graphs;       /* 1: capture and replay one CUDA graph per (problem, operation, batch) */
   int autotune;         /* 1: run tat_plan_autotune on each new plan at its slot's batch size */
+  int one_graph;        /* 1 (with use_graphs): a flush whose composition (sizes, operations and
+                           batch counts) has been flushed before runs the first batch of every size
+                           in one CUDA graph, the sizes as parallel branches, launched once (the
+                           graph is captured on the composition's second flush and cached); other
+                           flushes, and all with 0, use one graph per (problem, operation, batch)
+                           on the slot's own stream */
 } tat_service_config;
 
 typedef struct {
@@ -60,6 +66,7 @@ typedef struct {
   long long completed;  /* completed (including failed) */
   long long launches;   /* batched operator launches */
   long long graph_launches;
+  long long flush_graphs;   /* single-graph flushes (one_graph): one graph launch for all sizes */
   long long evictions;  /* slots evicted to admit others */
   int plans;            /* plans in the cache */
   int slots;            /* slots resident now */
@@ -67,7 +74,7 @@ typedef struct {
   size_t peak_bytes;    /* most arena bytes held by slots at once */
 } tat_service_stats;
 
-/* Defaults: 8 GiB budget, max_batch 32, graphs on, autotune off. */
+/* Defaults: 8 GiB budget, max_batch 32, graphs on, autotune off, one graph per flush. */
 tat_status tat_service_config_default(tat_service_config* cfg);
 
 /* Creates a service on the current device and allocates its arena.
@@ -97,31 +104,40 @@ tat_status tat_service_get_stats(tat_service_t svc, tat_service_stats* stats);
 /* Times the launch shapes the kernels take at run time -- column strips of
  * 2, 4, 8, 16, 32 half-plane columns per CTA in the column stages and 1, 2, 4
  * row pairs per CTA in the row stages (those within the device limits), then,
- * for the best of those, column CTAs of 64 and 128 threads (instead of 256;
- * four-step column lengths only) with half, the same and twice its strip, then
+ * for the best of those, column CTAs of 64, 128 and 384 threads (instead of 256; 64 and
+ * 128 for the four-step column lengths only) with half, the same and twice its strip, then
  * row groups of 64 and 128 threads (instead of 256; lengths N <= 1024) with 1, 2
- * and 4 times its row pairs, and the best shape with and without programmatic
- * dependent launch of the stages -- on
+ * and 4 times its row pairs, the best shape with and without programmatic
+ * dependent launch of the stages, and the other pass order of the length-2M FFT of
+ * the cosine and sine stages (tat_plan_set_fft_order) -- on
  * one A then one A* of `batch` images at f (device, batch*n*n floats, output
  * of A* written to f_out) with g (batch*n_det*n_t floats) and the workspace
  * for `batch`, and keeps the fastest for every later call on this plan.  The
- * shapes only regroup work: results are unchanged (up to the rounding order
- * of the adjoint's shared-memory atomics).  Synchronises `stream`.  *ms_best
+ * shapes only regroup work: A* is unchanged bit for bit, A and A^-1 up to the
+ * rounding of the FFT pass order.  Synchronises `stream`.  *ms_best
  * (optional) receives the chosen shape's time for the pair, *strip,
- * *row_pairs, *cols_threads and *row_threads (optional) the chosen knobs. */
+ * *row_pairs, *cols_threads and *row_threads (optional) the chosen knobs
+ * (tat_plan_get_fft_order reports the chosen pass order). */
 tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, float* f_out, void* workspace,
                              tat_stream_t stream, double* ms_best, int* strip, int* row_pairs, int* cols_threads,
                              int* row_threads);
 
 /* Sets the same knobs directly (for instance to reuse shapes tuned earlier): `strip`
  * columns per column CTA, `row_pairs` per row CTA, `cols_threads` threads per column
- * CTA (a multiple of 32; below 256 only for the four-step column lengths 512 .. 4096),
+ * CTA (a multiple of 32, at most 384 for the column lengths up to 4096 with a
+ * compile-time schedule; below 256 only for the four-step column lengths 512 .. 4096),
  * `row_threads` threads per row pair (a multiple of 32 for the four-step lengths up to
  * 4096, else the plan's own; 0 keeps the current value).  TAT_ERR_UNSUPPORTED, with the
  * plan unchanged, for shapes outside the device or kernel limits.  Results do not depend
- * on the shapes (up to the rounding order of the adjoint's shared-memory atomics).  Host
- * only. */
+ * on the shapes (A* bit for bit: its scatter adds in a fixed order).  Host only. */
 tat_status tat_plan_set_launch_shape(tat_plan_t plan, int strip, int row_pairs, int cols_threads, int row_threads);
+
+/* Pass order of the length-2M FFT inside the cosine (A, A*) and sine (A^-1) stages: 0 runs
+ * the radix-3 passes first, 1 the same passes in reverse (the tail radix first).  The
+ * results agree to rounding.  tat_plan_autotune tries both and keeps the faster; these set
+ * and read the order directly.  TAT_ERR_INVALID_ARG for an order other than 0 or 1. */
+tat_status tat_plan_set_fft_order(tat_plan_t plan, int order);
+tat_status tat_plan_get_fft_order(tat_plan_t plan, int* order);
 
 #ifdef __cplusplus
 }

@@ -47,12 +47,13 @@ class tat_plan_info(ctypes.Structure):
 
 class tat_service_config(ctypes.Structure):
     _fields_ = [("memory_budget", ctypes.c_size_t), ("max_batch", ctypes.c_int), ("use_graphs", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("one_graph", ctypes.c_int)]
 
 
 class tat_service_stats(ctypes.Structure):
     _fields_ = [("requests", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("launches", ctypes.c_longlong),
-                ("graph_launches", ctypes.c_longlong), ("evictions", ctypes.c_longlong), ("plans", ctypes.c_int),
+                ("graph_launches", ctypes.c_longlong), ("flush_graphs", ctypes.c_longlong),
+                ("evictions", ctypes.c_longlong), ("plans", ctypes.c_int),
                 ("slots", ctypes.c_int), ("arena_bytes", ctypes.c_size_t), ("peak_bytes", ctypes.c_size_t)]
 
     def as_dict(self):
@@ -112,6 +113,8 @@ def load() -> ctypes.CDLL:
         "tat_plan_autotune": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(_D), ctypes.POINTER(_I),
                                    ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
         "tat_plan_set_launch_shape": (_I, [_P, _I, _I, _I, _I]),
+        "tat_plan_set_fft_order": (_I, [_P, _I]),
+        "tat_plan_get_fft_order": (_I, [_P, ctypes.POINTER(_I)]),
         "tat_lpd_scratch_floats": (ctypes.c_size_t, [_I, _I, _I]),
         "tat_conv_in_fwd": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P]),
         "tat_conv_in_bwd_data": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _I, _P]),
@@ -304,6 +307,17 @@ def tat_tv_primal_backward(batch, n, h_eff, tau, f_out_ptr, mask_ptr, grad_f_out
 def tat_plan_set_launch_shape(plan, strip, row_pairs, cols_threads, row_threads=0):
     _check(load().tat_plan_set_launch_shape(plan, strip, row_pairs, cols_threads, row_threads),
            "tat_plan_set_launch_shape")
+
+
+def tat_plan_set_fft_order(plan, order):
+    """Pass order (0 or 1) of the length-2M FFT of the cosine and sine stages."""
+    _check(load().tat_plan_set_fft_order(plan, order), "tat_plan_set_fft_order")
+
+
+def tat_plan_get_fft_order(plan):
+    o = _I()
+    _check(load().tat_plan_get_fft_order(plan, ctypes.byref(o)), "tat_plan_get_fft_order")
+    return o.value
 
 
 def tat_plan_autotune(plan, batch, f_ptr, g_ptr, f_out_ptr, ws_ptr, stream=0):
@@ -580,7 +594,7 @@ class TatService:
 
     OPS = {"forward": TAT_OP_FORWARD, "adjoint": TAT_OP_ADJOINT, "inverse": TAT_OP_INVERSE, "pair": TAT_OP_PAIR}
 
-    def __init__(self, memory_budget=None, max_batch=None, use_graphs=True, autotune=False):
+    def __init__(self, memory_budget=None, max_batch=None, use_graphs=True, autotune=False, one_graph=True):
         cfg = tat_service_config_default()
         if memory_budget is not None:
             cfg.memory_budget = int(memory_budget)
@@ -588,6 +602,7 @@ class TatService:
             cfg.max_batch = int(max_batch)
         cfg.use_graphs = 1 if use_graphs else 0
         cfg.autotune = 1 if autotune else 0
+        cfg.one_graph = 1 if one_graph else 0
         self.handle = tat_service_create(cfg)
         self._keep = []
 

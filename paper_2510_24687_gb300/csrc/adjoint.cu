@@ -27,8 +27,11 @@ tat_status launch_adjoint(const tat_plan_s* Pl, int batch, const float* g, long 
   });
   dispatch_2M(2 * P.M, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
-    ok &= ensure_smem<k_modes_adj<L>>(dev);
-    ok &= pdl_launch(c.pdl != 0, k_modes_adj<L>, s.modes_grid, s.modes_block, s.modes_smem, st, P, Y, ys, X, xs, c.nt_2M) == cudaSuccess;
+    dispatch_order(L > 0 ? c.order_2M : 0, [&](auto Vc) {
+      constexpr int V = decltype(Vc)::value;
+      ok &= ensure_smem<k_modes_adj<L, V>>(dev);
+      ok &= pdl_launch(c.pdl != 0, k_modes_adj<L, V>, s.modes_grid, s.modes_block, s.modes_smem, st, P, Y, ys, X, xs, c.nt_2M) == cudaSuccess;
+    });
     stage_done();
   });
   dispatch_ang(P.n_phi, [&](auto Lc) {

@@ -262,11 +262,14 @@ __device__ __forceinline__ void pass_tw(const float2* t, int Ns, int k, float2& 
   }
 }
 
+// keep_mod > 0: the next pass is the last, with Ns = keep_mod, and keeps only its outputs
+// below n_out, which read exactly the values at o with o mod keep_mod < n_out: the others
+// are not written.
 template <int R, bool INV>
 __device__ __forceinline__ void fft_pass(float2* buf, int L, int Ns, const float2* __restrict__ tw, int tid,
                                          int nthr, bool first, bool last, int n_in, int n_out,
                                          const float2* __restrict__ pre, const float2* __restrict__ post,
-                                         const float2* ptws = nullptr) {
+                                         const float2* ptws = nullptr, int keep_mod = 0) {
   constexpr int NB = 16 / R;
   const int nb = L / R;
   const int tws = L / (Ns * R);
@@ -311,6 +314,8 @@ __device__ __forceinline__ void fft_pass(float2* buf, int L, int Ns, const float
         const int o = base + r * Ns;
         if (last) {
           if (o < n_out) buf[spad(o)] = post != nullptr ? cmul(v[b][r], __ldg(&post[o])) : v[b][r];
+        } else if (keep_mod > 0) {
+          if (o % keep_mod < n_out) buf[spad(o)] = v[b][r];
         } else {
           buf[spad(o)] = v[b][r];
         }
@@ -322,8 +327,10 @@ __device__ __forceinline__ void fft_pass(float2* buf, int L, int Ns, const float
 
 // Radix schedule of a length L = 2^k 3^m: all radix-3 passes, then radix-16
 // passes, then the remainder of k mod 4 as 8*4 (one 16 fewer), 4 or 8, or a
-// single 2 for k = 1.  The plan builder uses the same rule.
-template <int L>
+// single 2 for k = 1 (order V = 0); order V = 1 runs the same passes in reverse
+// (the tail radix first, the radix-3 passes last).  The plan builder uses the
+// same rule (fft_schedule), and the autotuner picks the order per plan.
+template <int L, int V = 0>
 struct Sched {
   __host__ __device__ static constexpr int pow3(int x) { return x % 3 == 0 ? 1 + pow3(x / 3) : 0; }
   __host__ __device__ static constexpr int strip3(int x) { return x % 3 == 0 ? strip3(x / 3) : x; }
@@ -334,23 +341,24 @@ struct Sched {
   static constexpr int n16 = (rem == 1 && n16full >= 1) ? n16full - 1 : n16full;
   static constexpr int ntail = rem == 0 ? 0 : (rem == 1 && n16full >= 1) ? 2 : 1;
   static constexpr int npass = n3 + n16 + ntail;
-  __host__ __device__ static constexpr int radix(int s) {
+  __host__ __device__ static constexpr int radix0(int s) {
     return s < n3 ? 3
          : s < n3 + n16 ? 16
          : rem == 1 ? (n16full >= 1 ? (s == n3 + n16 ? 8 : 4) : 2)
          : rem == 2 ? 4
          : 8;
   }
+  __host__ __device__ static constexpr int radix(int s) { return V == 0 ? radix0(s) : radix0(npass - 1 - s); }
 };
 
-template <int L, bool INV, int S, int NS>
+template <int L, bool INV, int S, int NS, int V = 0>
 __device__ __forceinline__ void fft_ct_from(float2* buf, const FftDev& f, int tid, int nthr, int n_in, int n_out,
                                             const float2* pre, const float2* post, const float2* smptw) {
-  if constexpr (S < Sched<L>::npass) {
-    constexpr int R = Sched<L>::radix(S);
-    fft_pass<R, INV>(buf, L, NS, f.tw, tid, nthr, S == 0, S == Sched<L>::npass - 1, n_in, n_out, pre, post,
+  if constexpr (S < Sched<L, V>::npass) {
+    constexpr int R = Sched<L, V>::radix(S);
+    fft_pass<R, INV>(buf, L, NS, f.tw, tid, nthr, S == 0, S == Sched<L, V>::npass - 1, n_in, n_out, pre, post,
                      smptw != nullptr && S > 0 ? smptw + f.ptw_off[S] : nullptr);
-    fft_ct_from<L, INV, S + 1, NS * R>(buf, f, tid, nthr, n_in, n_out, pre, post, smptw);
+    fft_ct_from<L, INV, S + 1, NS * R, V>(buf, f, tid, nthr, n_in, n_out, pre, post, smptw);
   }
 }
 
@@ -376,15 +384,15 @@ __device__ __forceinline__ void fft_run(float2* buf, const FftDev& f, int tid, i
   }
 }
 
-// L > 0: compile-time schedule (must equal f.L); L == 0: runtime schedule.
-// Reads buf[0, n_in), writes buf[0, n_out); every thread of the CTA must call it.
-// `smptw`: shared-memory copy of f.ptw (null: twiddles from the global table).
-template <int L, bool INV>
+// L > 0: compile-time schedule of order V (must equal f's schedule); L == 0: runtime
+// schedule read from f.  Reads buf[0, n_in), writes buf[0, n_out); every thread of the
+// CTA must call it.  `smptw`: shared-memory copy of f.ptw (null: global twiddle table).
+template <int L, bool INV, int V = 0>
 __device__ __forceinline__ void fft(float2* buf, const FftDev& f, int tid, int nthr, int n_in, int n_out,
                                     const float2* pre = nullptr, const float2* post = nullptr,
                                     const float2* smptw = nullptr) {
   if constexpr (L == 0) fft_run<INV>(buf, f, tid, nthr, n_in, n_out, pre, post, smptw);
-  else fft_ct_from<L, INV, 0, 1>(buf, f, tid, nthr, n_in, n_out, pre, post, smptw);
+  else fft_ct_from<L, INV, 0, 1, V>(buf, f, tid, nthr, n_in, n_out, pre, post, smptw);
 }
 
 // First pass of a compile-time schedule with its inputs from `load(i)` (global memory,
@@ -418,7 +426,9 @@ __device__ __forceinline__ void fft_pass_load(float2* buf, int L, int tid, int n
 }
 
 // Last pass (Ns R = L) handing each output o < n_out to `store(o, value)` instead of
-// writing it back to the buffer, which it leaves unchanged (no trailing barrier).
+// writing it back to the buffer, which it leaves unchanged (no trailing barrier).  The
+// outputs of butterfly j are j + r L/R, so butterflies j >= n_out are skipped whole
+// (with the radix-3 pass last and n_out = L/6, half of them).
 template <int R, bool INV, class Store>
 __device__ __forceinline__ void fft_pass_store(const float2* buf, int L, int tid, int nthr, int n_out, Store& store,
                                                const float2* ptws) {
@@ -428,7 +438,7 @@ __device__ __forceinline__ void fft_pass_store(const float2* buf, int L, int tid
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const int j = tid + b * nthr;
-    if (act && j < nb) {
+    if (act && j < nb && j < n_out) {
       float2 v[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) v[r] = buf[spad(j + r * nb)];
@@ -443,20 +453,23 @@ __device__ __forceinline__ void fft_pass_store(const float2* buf, int L, int tid
   }
 }
 
-template <int L, bool INV, int S, int NS, class Load, class Store>
+template <int L, bool INV, int V, int S, int NS, class Load, class Store>
 __device__ __forceinline__ void fft_io_from(float2* buf, const FftDev& f, int tid, int nthr, int n_out, Load& load,
                                             Store& store, const float2* smptw) {
-  constexpr int NP = Sched<L>::npass;
+  constexpr int NP = Sched<L, V>::npass;
   if constexpr (S < NP) {
-    constexpr int R = Sched<L>::radix(S);
+    constexpr int R = Sched<L, V>::radix(S);
     if constexpr (S == 0) {
       fft_pass_load<R, INV>(buf, L, tid, nthr, load);
     } else if constexpr (S == NP - 1) {
       fft_pass_store<R, INV>(buf, L, tid, nthr, n_out, store, smptw + f.ptw_off[S]);
     } else {
-      fft_pass<R, INV>(buf, L, NS, f.tw, tid, nthr, false, false, 0, 0, nullptr, nullptr, smptw + f.ptw_off[S]);
+      // the pass before the last writes only what the kept outputs of the last one read
+      constexpr int keep = S == NP - 2 ? L / Sched<L, V>::radix(NP - 1) : 0;
+      fft_pass<R, INV>(buf, L, NS, f.tw, tid, nthr, false, false, 0, keep > 0 ? n_out : 0, nullptr, nullptr,
+                       smptw + f.ptw_off[S], keep < n_out ? 0 : keep);
     }
-    fft_io_from<L, INV, S + 1, NS * R>(buf, f, tid, nthr, n_out, load, store, smptw);
+    fft_io_from<L, INV, V, S + 1, NS * R>(buf, f, tid, nthr, n_out, load, store, smptw);
   }
 }
 
@@ -464,11 +477,11 @@ __device__ __forceinline__ void fft_io_from(float2* buf, const FftDev& f, int ti
 // load(i), i < L, to store(o, X[o]) for o < n_out, with `buf` (xpad_len(L) slots) as
 // the exchange between passes and `smptw` the shared-memory per-pass twiddles (loaded
 // and synchronised by the caller).  Every thread of the CTA must call it.
-template <int L, bool INV, class Load, class Store>
+template <int L, bool INV, int V = 0, class Load, class Store>
 __device__ __forceinline__ void fft_io(float2* buf, const FftDev& f, int tid, int nthr, int n_out, Load load,
                                        Store store, const float2* smptw) {
-  static_assert(L > 0 && Sched<L>::npass >= 2, "fft_io needs a compile-time schedule of two or more passes");
-  fft_io_from<L, INV, 0, 1>(buf, f, tid, nthr, n_out, load, store, smptw);
+  static_assert(L > 0 && Sched<L, V>::npass >= 2, "fft_io needs a compile-time schedule of two or more passes");
+  fft_io_from<L, INV, V, 0, 1>(buf, f, tid, nthr, n_out, load, store, smptw);
 }
 
 // Copies an FFT's per-pass twiddle tables to shared memory (caller syncs).

@@ -17,7 +17,7 @@ tat_status validate_shapes(const tat_plan_s* Pl) {
   if (s.cols_block > 512) return TAT_ERR_UNSUPPORTED;  // launch bound of the column kernels
   const int N = Pl->d.N;
   const bool ct = N == 256 || N == 512 || N == 1024 || N == 2048 || N == 4096 || N == 8192;
-  if (ct && N <= 4096 && s.cols_block > 256) return TAT_ERR_UNSUPPORTED;
+  if (ct && N <= 4096 && s.cols_block > 384) return TAT_ERR_UNSUPPORTED;
   // the Stockham column FFT runs on nt_N threads of the CTA; the four-step one on any multiple of 32
   const bool four = N == 512 || N == 1024 || N == 2048 || N == 4096 || N == 8192;
   if (!four && (s.cols_block < Pl->cfg.nt_N || s.cols_block < 256)) return TAT_ERR_UNSUPPORTED;
@@ -61,8 +61,11 @@ tat_status launch_forward(const tat_plan_s* Pl, int batch, const float* f, long 
   });
   dispatch_2M(2 * P.M, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
-    ok &= ensure_smem<k_modes_fwd<L>>(dev);
-    ok &= pdl_launch(c.pdl != 0, k_modes_fwd<L>, s.modes_grid, s.modes_block, s.modes_smem, st, P, X, xs, Y, ys, c.nt_2M) == cudaSuccess;
+    dispatch_order(L > 0 ? c.order_2M : 0, [&](auto Vc) {
+      constexpr int V = decltype(Vc)::value;
+      ok &= ensure_smem<k_modes_fwd<L, V>>(dev);
+      ok &= pdl_launch(c.pdl != 0, k_modes_fwd<L, V>, s.modes_grid, s.modes_block, s.modes_smem, st, P, X, xs, Y, ys, c.nt_2M) == cudaSuccess;
+    });
     stage_done();
   });
   dispatch_ang(P.n_det, [&](auto Lc) {

@@ -33,8 +33,11 @@ tat_status launch_inverse(const tat_plan_s* Pl, int batch, const float* g, long 
   });
   dispatch_2M(2 * P.M, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
-    ok &= ensure_smem<k_modes_inv<L>>(dev);
-    ok &= pdl_launch(c.pdl != 0, k_modes_inv<L>, s.modes_grid, s.modes_block, s.modes_smem, st, P, Y, ys, X, xs, c.nt_2M) == cudaSuccess;
+    dispatch_order(L > 0 ? c.order_2M : 0, [&](auto Vc) {
+      constexpr int V = decltype(Vc)::value;
+      ok &= ensure_smem<k_modes_inv<L, V>>(dev);
+      ok &= pdl_launch(c.pdl != 0, k_modes_inv<L, V>, s.modes_grid, s.modes_block, s.modes_smem, st, P, Y, ys, X, xs, c.nt_2M) == cudaSuccess;
+    });
     stage_done();
   });
   dispatch_ang(P.n_phi, [&](auto Lc) {
@@ -47,7 +50,7 @@ tat_status launch_inverse(const tat_plan_s* Pl, int batch, const float* g, long 
   dispatch_N(P.N, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_cols_inv<L>>(dev) && ensure_smem<k_rows_inv<L>>(dev);
-    ok &= pdl_launch(c.pdl != 0, k_cols_inv<L>, s.cols_grid_a, s.cols_block, s.cols_smem_i, st, P, Y, ys, X, xs, c.strip, c.nt_N, batch, acc, accs) == cudaSuccess;
+    ok &= pdl_launch(c.pdl != 0, k_cols_inv<L>, s.cols_grid_a, s.cols_block_i, s.cols_smem_i, st, P, Y, ys, X, xs, c.strip, c.nt_N, batch, acc, accs) == cudaSuccess;
     stage_done();
     ok &= pdl_launch(c.pdl != 0, k_rows_inv<L>, s.rows_grid, s.rows_block, s.rows_smem, st, P, X, xs, f, fs, acc, accs, c.rows_pairs, c.nt_rows) == cudaSuccess;
     stage_done();

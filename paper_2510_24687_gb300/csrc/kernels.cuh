@@ -136,11 +136,12 @@ __global__ void TAT_ROWS_BOUNDS k_rows_fwd(DevPlan P, const float* __restrict__ 
   }
 }
 
-// Column kernels: 256 threads for the compile-time lengths up to 4096 (512
-// otherwise), with 3 CTAs per SM for the forward and 2 for the adjoint, whose
-// scatter needs more registers (best of both settings measured on GB300, n = 512).
-#define TAT_COLS_BOUNDS_F __launch_bounds__((L > 0 && L <= 4096) ? 256 : 512, (L > 0 && L <= 4096) ? 3 : 1)
-#define TAT_COLS_BOUNDS_A __launch_bounds__((L > 0 && L <= 4096) ? 256 : 512, (L > 0 && L <= 4096) ? 3 : 1)
+// Column kernels: up to 384 threads for the compile-time lengths up to 4096 (512
+// otherwise), compiled for two 384-thread CTAs per SM -- the same 80-register budget as
+// three CTAs of 256 threads, which is the default shape; 384 lets one pass of the
+// adjoint's scatter cover a column's runs (about 370 on average at n = 512).
+#define TAT_COLS_BOUNDS_F __launch_bounds__((L > 0 && L <= 4096) ? 384 : 512, (L > 0 && L <= 4096) ? 2 : 1)
+#define TAT_COLS_BOUNDS_A __launch_bounds__((L > 0 && L <= 4096) ? 384 : 512, (L > 0 && L <= 4096) ? 2 : 1)
 
 // Column strips are launched strip-major (all images' strip 0 first): the
 // strips near q_x = 0 hold up to 7x the average number of polar samples, so
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(1024) k_rings_fwd(DevPlan P, const float2* __r
   }
 }
 
-template <int L>
+template <int L, int V = 0>
 __global__ void __launch_bounds__(1024) k_modes_fwd(DevPlan P, const float2* __restrict__ X, long long xs, float2* __restrict__ Y,
                             long long ys, int nt) {
   TAT_GRID_DEPENDENCY();
@@ -341,7 +342,7 @@ __global__ void __launch_bounds__(1024) k_modes_fwd(DevPlan P, const float2* __r
       G[m] = v;
     };
     __syncthreads();  // twiddles
-    fft_io<L, false>(sm, P.f2M, threadIdx.x, nt, P.n_t, load, store, smptw);
+    fft_io<L, false, V>(sm, P.f2M, threadIdx.x, nt, P.n_t, load, store, smptw);
   } else {
     for (int j = threadIdx.x; j < L2; j += blockDim.x) {
       float2 v = make_float2(0.f, 0.f);
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(1024) k_modes_fwd(DevPlan P, const float2* __r
       sm[xpad<L>(j)] = v;
     }
     __syncthreads();
-    fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, P.n_t, nullptr, nullptr, smptw);
+    fft<L, false, V>(sm, P.f2M, threadIdx.x, nt, L2, P.n_t, nullptr, nullptr, smptw);
     for (int m = threadIdx.x; m < P.n_t; m += blockDim.x) {
       float2 v = cscale(sm[xpad<L>(m)], 0.5f);
       if (low) {
@@ -533,7 +534,7 @@ __global__ void __launch_bounds__(1024) k_theta_adj(DevPlan P, const float* __re
   }
 }
 
-template <int L>
+template <int L, int V = 0>
 __global__ void __launch_bounds__(1024) k_modes_adj(DevPlan P, const float2* __restrict__ Y, long long ys, float2* __restrict__ X,
                             long long xs, int nt) {
   TAT_GRID_DEPENDENCY();
@@ -561,7 +562,7 @@ __global__ void __launch_bounds__(1024) k_modes_adj(DevPlan P, const float2* __r
       Dm[j] = v;
     };
     __syncthreads();  // twiddles
-    fft_io<L, false>(sm, P.f2M, threadIdx.x, nt, J1, load, store, smptw);
+    fft_io<L, false, V>(sm, P.f2M, threadIdx.x, nt, J1, load, store, smptw);
   } else {
     for (int j = threadIdx.x; j < L2; j += blockDim.x) {
       float2 v = make_float2(0.f, 0.f);
@@ -570,7 +571,7 @@ __global__ void __launch_bounds__(1024) k_modes_adj(DevPlan P, const float2* __r
       sm[xpad<L>(j)] = v;
     }
     __syncthreads();
-    fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, P.J + 1, nullptr, nullptr, smptw);
+    fft<L, false, V>(sm, P.f2M, threadIdx.x, nt, L2, P.J + 1, nullptr, nullptr, smptw);
     for (int j = threadIdx.x; j < J1; j += blockDim.x) {
       float2 v = cscale(cadd(sm[xpad<L>(j)], g0), 0.5f);
       if (low && j < kLowA) v = make_float2(0.f, 0.f);
@@ -629,18 +630,17 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
   const int SL = xpad_len(P.n_phi);
   float2* smptw = sm + RPC * SL;
   float2* smtw = smptw + P.fphi.ptw_len;
-  float* smB = align16(smtw + kFourStepTw);  // this tile's multipliers [k][g]
-  stage_multipliers(smB, INV ? P.Bit : P.Btt, blockIdx.x, P.bt_bs);
   load_pass_tw(smptw, P.fphi, threadIdx.x, blockDim.x);
   load_fourstep_tw(smtw, P.fphi.fstw, threadIdx.x, blockDim.x);
   const int rbase = 1 + blockIdx.x * RPC;
-  cp_async_wait_all();
-  __syncthreads();
+  // the multipliers come first here, so they are read straight from this tile's contiguous
+  // block of the tiled table, together with the coefficients
+  const float* Bb = (INV ? P.Bit : P.Btt) + (size_t)blockIdx.x * P.bt_bs;
   for (int e = threadIdx.x; e < (P.K + 1) * RPC; e += blockDim.x) {
     const int k = e / RPC, gg = e % RPC;
     const int rr = rbase + gg;
     float2 w = make_float2(0.f, 0.f);
-    if (rr <= P.J) w = mul_mipow(cscale(Xb[(size_t)k * J1 + rr], smB[e]), INV ? k + 1 : k);
+    if (rr <= P.J) w = mul_mipow(cscale(Xb[(size_t)k * J1 + rr], __ldg(Bb + e)), INV ? k + 1 : k);
     float2* bg = sm + gg * SL;
     bg[xpad<L>(colpos<L>(k))] = w;
     if (k >= 1 && k < P.K) {
@@ -972,7 +972,7 @@ __global__ void TAT_ROWS_BOUNDS k_rows_adj(DevPlan P, const float2* __restrict__
 // extension of the trapezoid-weighted samples (weight 1/2 at t = T; t = 0 drops
 // out) gives FFT_j = -2i sum_m w_m sin(lam_j t_m) g'_k(t_m).  The factor i/2 and
 // the -2 of Eq. Four_coef_v make the ring multiplier (-i)^(k+1) J'_k dt/n_det.
-template <int L>
+template <int L, int V = 0>
 __global__ void __launch_bounds__(1024) k_modes_inv(DevPlan P, const float2* __restrict__ Y, long long ys,
                                                     float2* __restrict__ X, long long xs, int nt) {
   TAT_GRID_DEPENDENCY();
@@ -997,11 +997,11 @@ __global__ void __launch_bounds__(1024) k_modes_inv(DevPlan P, const float2* __r
     // the odd extension straight into the first pass, the kept outputs straight out
     auto store = [&](int j, float2 x) { Dm[j] = x; };
     __syncthreads();  // twiddles
-    fft_io<L, false>(sm, P.f2M, threadIdx.x, nt, J1, load, store, smptw);
+    fft_io<L, false, V>(sm, P.f2M, threadIdx.x, nt, J1, load, store, smptw);
   } else {
     for (int j = threadIdx.x; j < L2; j += blockDim.x) sm[xpad<L>(j)] = load(j);
     __syncthreads();
-    fft<L, false>(sm, P.f2M, threadIdx.x, nt, L2, J1, nullptr, nullptr, smptw);
+    fft<L, false, V>(sm, P.f2M, threadIdx.x, nt, L2, J1, nullptr, nullptr, smptw);
     for (int j = threadIdx.x; j < J1; j += blockDim.x) Dm[j] = sm[xpad<L>(j)];
   }
 }

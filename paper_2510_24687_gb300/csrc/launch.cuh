@@ -14,7 +14,7 @@ namespace {
 
 struct Shapes {
   dim3 rows_grid, cols_grid_f, cols_grid_a, rings_grid, modes_grid, theta_grid;
-  int rows_block, cols_block, rings_block, modes_block, theta_block;
+  int rows_block, cols_block, cols_block_i, rings_block, modes_block, theta_block;
   size_t rows_smem, cols_smem_f, cols_smem_a, cols_smem_i, rings_smem, modes_smem, theta_smem;
   int ntiles;
 };
@@ -31,6 +31,9 @@ inline Shapes shapes(const tat_plan_s* Pl, int batch) {
   s.cols_grid_f = dim3(((P.ncol - 1 + c.strip - 1) / c.strip) * batch);
   s.cols_grid_a = dim3(((P.ncol + c.strip - 1) / c.strip) * batch);
   s.cols_block = c.cols_threads;
+  // the inverse's column kernel is compiled for at most 256 threads at these lengths
+  const bool ct_le4096 = P.N == 256 || P.N == 512 || P.N == 1024 || P.N == 2048 || P.N == 4096;
+  s.cols_block_i = ct_le4096 ? std::min(c.cols_threads, 256) : c.cols_threads;
   s.cols_smem_f = (2 * (size_t)xpad_len(P.N) + kFourStepTw + P.ph_lo + 64) * sizeof(float2);
   s.cols_smem_a = (2 * (size_t)xpad_len(P.N) + kFourStepTw + P.ph_lo + 64) * sizeof(float2);
   s.cols_smem_i = ((size_t)xpad_len(P.N) + kFourStepTw) * sizeof(float2);
@@ -77,6 +80,12 @@ inline void dispatch_ang(int L, F&& f) {
     case 4096: f(IC<4096>{}); break;
     default: f(IC<0>{}); break;
   }
+}
+// Pass order of the length-2M transform (compile-time V of the cosine/sine kernels).
+template <class F>
+inline void dispatch_order(int order, F&& f) {
+  if (order == 1) f(IC<1>{});
+  else f(IC<0>{});
 }
 template <class F>
 inline void dispatch_2M(int L, F&& f) {

@@ -73,7 +73,7 @@ void parallel_for(int count, F&& fn) {
 // Radix schedule: radix-3 passes, radix-16 passes, then the remainder of
 // log2 mod 4 as 8*4 (one 16 fewer), 4 or 8 (or one 2 for a length-2 factor);
 // the device code uses the same rule.
-int fft_schedule(int L, int* radix) {
+int fft_schedule(int L, int* radix, int order = 0) {
   int r = L, np = 0;
   while (r % 3 == 0) { radix[np++] = 3; r /= 3; }
   int k = 0;
@@ -90,6 +90,7 @@ int fft_schedule(int L, int* radix) {
   } else if (rem == 3) {
     radix[np++] = 8;
   }
+  if (order == 1) std::reverse(radix, radix + np);  // the same passes, tail radix first
   return np;
 }
 
@@ -266,9 +267,9 @@ tat_status upload(tat_plan_s* P, const std::vector<T>& h, const T** out) {
   return TAT_OK;
 }
 
-tat_status make_fft(tat_plan_s* P, int L, FftDev* f, int* nthreads) {
+tat_status make_fft(tat_plan_s* P, int L, FftDev* f, int* nthreads, int order = 0) {
   f->L = L;
-  f->npass = fft_schedule(L, f->radix);
+  f->npass = fft_schedule(L, f->radix, order);
   if (f->npass < 0 || f->npass > kMaxPass) return TAT_ERR_UNSUPPORTED;
   std::vector<float2> tw(L);
   for (int k = 0; k < L; ++k) {
@@ -387,7 +388,12 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
   // FFT lengths: N (rows/columns), n_phi (rings), 2M (cosine transform), n_det (detectors).
   TAT_TRY(make_fft(P, d.N, &d.fN, &P->cfg.nt_N));
   TAT_TRY(make_fft(P, n_phi, &d.fphi, &P->cfg.nt_phi));
-  TAT_TRY(make_fft(P, 2 * d.M, &d.f2M, &P->cfg.nt_2M));
+  // the cosine/sine transforms' FFT in both pass orders (the autotuner picks one per plan)
+  TAT_TRY(make_fft(P, 2 * d.M, &P->f2M_v[0], &P->nt_2M_v[0], 0));
+  TAT_TRY(make_fft(P, 2 * d.M, &P->f2M_v[1], &P->nt_2M_v[1], 1));
+  d.f2M = P->f2M_v[0];
+  P->cfg.nt_2M = P->nt_2M_v[0];
+  P->cfg.order_2M = 0;
   TAT_TRY(make_fft(P, n_det, &d.fdet, &P->cfg.nt_det));
 
   // Phase e^{-i xi_q x_0} = e^{i q dxi} (x_0 = -1) of every FFT bin, q signed:

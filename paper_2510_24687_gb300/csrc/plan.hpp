@@ -112,6 +112,7 @@ struct LaunchCfg {
                       // keep more of them busy in the second pass at N <= 1024)
   int cols_threads;   // threads per CTA of the column pass (>= nt_N; fewer than 256 only for four-step lengths)
   int pdl;            // 1: stages launched with programmatic dependent launch (outside graph capture)
+  int order_2M;       // pass order of the length-2M FFT of the cosine/sine stages (Sched V: 0 or 1)
 };
 
 }  // namespace tat
@@ -125,6 +126,8 @@ struct tat_plan_s {
   // sizes of the per-image workspace regions, in float2 elements
   size_t ws_x;  // row spectra / per-mode coefficients
   size_t ws_y;  // polar samples / time modes
+  tat::FftDev f2M_v[2];  // the length-2M FFT in pass orders 0 and 1; d.f2M is f2M_v[cfg.order_2M]
+  int nt_2M_v[2];
   std::vector<void*> allocations;  // device memory owned by the plan
 };
 

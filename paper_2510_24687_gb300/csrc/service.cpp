@@ -21,6 +21,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr size_t kAlign = 256;
+constexpr size_t kMaxCompositions = 4096;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 tat_status cuda_ok(cudaError_t e, const char* what) {
@@ -83,6 +84,8 @@ struct Slot {
   void* ws = nullptr;
   size_t in_elems = 0, out_elems = 0, mid_elems = 0;
   std::map<int, cudaGraphExec_t> graphs;  // batch -> executable graph
+  cudaStream_t branch = nullptr;      // captured into the single-graph flush (never runs work itself)
+  cudaEvent_t staged = nullptr;       // inputs of the chunk in the single graph are on the device
   std::vector<long long> pending;
   unsigned long long last_use = 0;
   bool tuned = false;
@@ -105,6 +108,15 @@ struct tat_service_s {
   std::mutex mu;                            // guards request completion fields
   unsigned long long tick = 0;
   tat_service_stats st{};
+  // single-graph flushes: the launch stream, its completion event and the executable graphs
+  // by composition (slot keys and batch sizes); dropped whenever a slot's buffers change
+  cudaStream_t launch = nullptr;
+  cudaEvent_t launched = nullptr;
+  std::map<std::string, cudaGraphExec_t> flush_graphs;
+  // how often each composition has been flushed: a composition gets its single graph on its
+  // second flush, so that a stream of ever-new compositions (random arrivals) never pays a
+  // capture and instantiation per flush (bounded: cleared past kMaxCompositions entries)
+  std::map<std::string, int> seen;
 };
 
 namespace {
@@ -135,21 +147,22 @@ void fail_now(tat_service_s* S, const std::vector<long long>& ids, tat_status wh
   S->st.completed += (long long)ids.size();
 }
 
-tat_status launch_op(const Slot& s, int b) {
+tat_status launch_op(const Slot& s, int b, cudaStream_t st) {
   const long long in_s = (long long)s.in_elems, out_s = (long long)s.out_elems;
   switch (s.op) {
-    case TAT_OP_FORWARD: return tat_forward_batched(s.plan, b, s.in, in_s, s.out, out_s, s.ws, s.stream);
-    case TAT_OP_ADJOINT: return tat_adjoint_batched(s.plan, b, s.in, in_s, s.out, out_s, s.ws, s.stream);
-    case TAT_OP_INVERSE: return tat_inverse_batched(s.plan, b, s.in, in_s, s.out, out_s, s.ws, s.stream);
+    case TAT_OP_FORWARD: return tat_forward_batched(s.plan, b, s.in, in_s, s.out, out_s, s.ws, st);
+    case TAT_OP_ADJOINT: return tat_adjoint_batched(s.plan, b, s.in, in_s, s.out, out_s, s.ws, st);
+    case TAT_OP_INVERSE: return tat_inverse_batched(s.plan, b, s.in, in_s, s.out, out_s, s.ws, st);
     case TAT_OP_PAIR: {
       const long long mid_s = (long long)s.mid_elems;
-      const tat_status e = tat_forward_batched(s.plan, b, s.in, in_s, s.mid, mid_s, s.ws, s.stream);
+      const tat_status e = tat_forward_batched(s.plan, b, s.in, in_s, s.mid, mid_s, s.ws, st);
       if (e != TAT_OK) return e;
-      return tat_adjoint_batched(s.plan, b, s.mid, mid_s, s.out, out_s, s.ws, s.stream);
+      return tat_adjoint_batched(s.plan, b, s.mid, mid_s, s.out, out_s, s.ws, st);
     }
   }
   return TAT_ERR_INVALID_ARG;
 }
+tat_status launch_op(const Slot& s, int b) { return launch_op(s, b, s.stream); }
 
 size_t slot_bytes(const Slot& s, int cap) {
   return align_up(s.in_elems * sizeof(float) * cap) + align_up(s.out_elems * sizeof(float) * cap) +
@@ -161,9 +174,16 @@ void drop_graphs(Slot& s) {
   s.graphs.clear();
 }
 
+void drop_flush_graphs(tat_service_s* S) {
+  for (auto& g : S->flush_graphs) cudaGraphExecDestroy(g.second);
+  S->flush_graphs.clear();
+}
+
 void evict(tat_service_s* S, Slot& s) {
   cudaStreamSynchronize(s.stream);
+  if (S->launch) cudaStreamSynchronize(S->launch);
   drop_graphs(s);
+  drop_flush_graphs(S);
   S->arena.release(s.off);
   s.cap = 0;
   s.in = s.out = s.mid = nullptr;
@@ -191,6 +211,7 @@ tat_status admit(tat_service_s* S, Slot& s) {
       ok = S->arena.alloc(need, &off);
     }
     if (!ok) continue;
+    drop_flush_graphs(S);  // the composition graphs hold the old buffer addresses
     s.off = off;
     s.bytes = need;
     s.cap = cap;
@@ -273,6 +294,110 @@ tat_status run_chunk(tat_service_s* S, Slot& s, const std::vector<long long>& id
   return TAT_OK;
 }
 
+// The first chunk of every ready slot as ONE launch: each slot's inputs are staged on its
+// own stream, then one CUDA graph -- a parallel branch per slot (size), captured once per
+// composition of slots and batch sizes and cached -- runs on the service's launch stream
+// after all of them, and each slot copies its results out on its own stream after it.
+// `launched` is set once the graph is on the launch stream: after that the chunks are
+// this call's to finish or fail, never to be run again by the caller.
+tat_status run_flush_graph(tat_service_s* S, const std::vector<Slot*>& ready,
+                           const std::vector<std::vector<long long>>& chunk, bool* launched) {
+  *launched = false;
+  std::string key;
+  for (size_t i = 0; i < ready.size(); ++i) {
+    key += ready[i]->key;
+    key += '#' + std::to_string(chunk[i].size()) + ';';
+  }
+  if (!S->flush_graphs.count(key)) {
+    if (S->seen.size() > kMaxCompositions) S->seen.clear();
+    if (++S->seen[key] < 2) return TAT_ERR_UNSUPPORTED;  // first sight: the per-slot path runs it
+  }
+  tat_status e = TAT_OK;
+  if (!S->launch) e = cuda_ok(cudaStreamCreateWithFlags(&S->launch, cudaStreamNonBlocking), "launch stream");
+  if (e == TAT_OK && !S->launched)
+    e = cuda_ok(cudaEventCreateWithFlags(&S->launched, cudaEventDisableTiming), "launch event");
+  for (size_t i = 0; i < ready.size() && e == TAT_OK; ++i) {
+    Slot& s = *ready[i];
+    if (!s.branch) e = cuda_ok(cudaStreamCreateWithFlags(&s.branch, cudaStreamNonBlocking), "branch stream");
+    if (e == TAT_OK && !s.staged)
+      e = cuda_ok(cudaEventCreateWithFlags(&s.staged, cudaEventDisableTiming), "staging event");
+    for (size_t k = 0; k < chunk[i].size() && e == TAT_OK; ++k) {
+      const Request& r = S->requests[(size_t)chunk[i][k]];
+      e = cuda_ok(cudaMemcpyAsync(s.in + k * s.in_elems, r.in, s.in_elems * sizeof(float), cudaMemcpyDefault,
+                                  s.stream),
+                  "staging copy");
+    }
+    if (e == TAT_OK) e = cuda_ok(cudaEventRecord(s.staged, s.stream), "staging event");
+    if (e == TAT_OK) e = cuda_ok(cudaStreamWaitEvent(S->launch, s.staged, 0), "launch wait");
+  }
+  if (e != TAT_OK) return e;
+  auto it = S->flush_graphs.find(key);
+  if (it == S->flush_graphs.end()) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join(ready.size(), nullptr);
+    bool ok = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess;
+    for (auto& j : join) ok = ok && cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess;
+    if (ok && cudaStreamBeginCapture(S->launch, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      tat_status le = cudaEventRecord(fork, S->launch) == cudaSuccess ? TAT_OK : TAT_ERR_CUDA;
+      for (size_t i = 0; i < ready.size() && le == TAT_OK; ++i) {
+        Slot& s = *ready[i];
+        if (cudaStreamWaitEvent(s.branch, fork, 0) != cudaSuccess) le = TAT_ERR_CUDA;
+        if (le == TAT_OK) le = launch_op(s, (int)chunk[i].size(), s.branch);
+        if (le == TAT_OK && cudaEventRecord(join[i], s.branch) != cudaSuccess) le = TAT_ERR_CUDA;
+        if (le == TAT_OK && cudaStreamWaitEvent(S->launch, join[i], 0) != cudaSuccess) le = TAT_ERR_CUDA;
+      }
+      const cudaError_t ce = cudaStreamEndCapture(S->launch, &graph);
+      ok = le == TAT_OK && ce == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    } else {
+      ok = false;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (fork) cudaEventDestroy(fork);
+    for (auto& j : join)
+      if (j) cudaEventDestroy(j);
+    cudaGetLastError();
+    if (!ok) {
+      if (exec) cudaGraphExecDestroy(exec);
+      return TAT_ERR_CUDA;
+    }
+    it = S->flush_graphs.emplace(key, exec).first;
+  }
+  e = cuda_ok(cudaGraphLaunch(it->second, S->launch), "flush graph launch");
+  if (e != TAT_OK) return e;
+  *launched = true;
+  ++S->st.flush_graphs;
+  S->st.launches += (long long)ready.size();
+  const tat_status le = cuda_ok(cudaEventRecord(S->launched, S->launch), "launch event");
+  tat_status first = TAT_OK;
+  for (size_t i = 0; i < ready.size(); ++i) {
+    Slot& s = *ready[i];
+    e = le;
+    if (e == TAT_OK) e = cuda_ok(cudaStreamWaitEvent(s.stream, S->launched, 0), "result wait");
+    for (size_t k = 0; k < chunk[i].size() && e == TAT_OK; ++k) {
+      const Request& r = S->requests[(size_t)chunk[i][k]];
+      e = cuda_ok(cudaMemcpyAsync(r.out, s.out + k * s.out_elems, s.out_elems * sizeof(float), cudaMemcpyDefault,
+                                  s.stream),
+                  "result copy");
+    }
+    if (e == TAT_OK) {
+      Completion* c = new Completion{S, chunk[i]};
+      const cudaError_t ce = cudaLaunchHostFunc(s.stream, on_complete, c);
+      if (ce != cudaSuccess) {
+        delete c;
+        e = cuda_ok(ce, "host callback");
+      }
+    }
+    if (e != TAT_OK) {  // this slot's requests fail; the other slots still complete
+      cudaStreamSynchronize(s.stream);
+      fail_now(S, chunk[i], e);
+      if (first == TAT_OK) first = e;
+    }
+  }
+  return first;
+}
+
 }  // namespace
 
 extern "C" {
@@ -283,6 +408,7 @@ tat_status tat_service_config_default(tat_service_config* cfg) {
   cfg->max_batch = 32;
   cfg->use_graphs = 1;
   cfg->autotune = 0;
+  cfg->one_graph = 1;
   return TAT_OK;
 }
 
@@ -313,12 +439,18 @@ tat_status tat_service_create(tat_service_t* svc, const tat_service_config* cfg)
 
 tat_status tat_service_destroy(tat_service_t S) {
   if (!S) return TAT_ERR_INVALID_ARG;
+  if (S->launch) cudaStreamSynchronize(S->launch);
+  drop_flush_graphs(S);
   for (auto& kv : S->slots) {
     Slot& s = *kv.second;
     if (s.stream) cudaStreamSynchronize(s.stream);
     drop_graphs(s);
     if (s.stream) cudaStreamDestroy(s.stream);
+    if (s.branch) cudaStreamDestroy(s.branch);
+    if (s.staged) cudaEventDestroy(s.staged);
   }
+  if (S->launch) cudaStreamDestroy(S->launch);
+  if (S->launched) cudaEventDestroy(S->launched);
   for (auto& kv : S->plans) tat_plan_destroy(kv.second);
   cudaFree(S->arena.base);
   delete S;
@@ -360,9 +492,45 @@ tat_status tat_service_submit(tat_service_t S, const tat_plan_desc* desc, tat_op
   return TAT_OK;
 }
 
+namespace {
+// Runs the pending requests of the prepared slots `ready` and clears them: with one_graph,
+// the first chunk of every slot as one graph launch; the rest (and everything, without it)
+// chunk by chunk on the slots' own streams.
+void run_ready(tat_service_t S, std::vector<Slot*>& ready, tat_status* first_error) {
+  size_t skip_first = 0;
+  if (S->cfg.one_graph && S->cfg.use_graphs && !ready.empty()) {
+    std::vector<std::vector<long long>> chunk(ready.size());
+    for (size_t i = 0; i < ready.size(); ++i) {
+      Slot& s = *ready[i];
+      const size_t j = std::min(s.pending.size(), (size_t)s.cap);
+      chunk[i].assign(s.pending.begin(), s.pending.begin() + (long)j);
+    }
+    bool launched = false;
+    const tat_status e = run_flush_graph(S, ready, chunk, &launched);
+    if (launched) skip_first = 1;
+    if (e != TAT_OK && launched && *first_error == TAT_OK) *first_error = e;
+  }
+  for (Slot* sp : ready) {
+    Slot& s = *sp;
+    for (size_t i = skip_first * (size_t)s.cap; i < s.pending.size(); i += (size_t)s.cap) {
+      const size_t j = std::min(s.pending.size(), i + (size_t)s.cap);
+      std::vector<long long> ids(s.pending.begin() + (long)i, s.pending.begin() + (long)j);
+      const tat_status e = run_chunk(S, s, ids);
+      if (e != TAT_OK) {
+        fail_now(S, ids, e);
+        if (*first_error == TAT_OK) *first_error = e;
+      }
+    }
+    s.pending.clear();
+  }
+  ready.clear();
+}
+}  // namespace
+
 tat_status tat_service_flush(tat_service_t S) {
   if (!S) return TAT_ERR_INVALID_ARG;
   tat_status first_error = TAT_OK;
+  std::vector<Slot*> ready;  // slots with pending requests, plan and buffers in place
   for (auto& kv : S->slots) {
     Slot& s = *kv.second;
     if (s.pending.empty()) continue;
@@ -372,6 +540,12 @@ tat_status tat_service_flush(tat_service_t S) {
     tat_status e = s.plan ? TAT_OK : ensure_plan(S, d, &s.plan);
     if (e == TAT_OK && !s.stream) e = cuda_ok(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking), "stream");
     if (e == TAT_OK) e = admit(S, s);
+    if (e == TAT_ERR_OOM && !ready.empty()) {
+      // the slots prepared so far hold the memory: run them now (they become evictable once
+      // their requests are issued) and admit this one after them
+      run_ready(S, ready, &first_error);
+      e = admit(S, s);
+    }
     if (e == TAT_OK && S->cfg.autotune && !s.tuned && s.op != TAT_OP_INVERSE) {
       // tune on zeroed slot buffers at the slot's batch size (the knobs belong to the plan)
       const tat_plan_desc& pd = d;
@@ -383,6 +557,7 @@ tat_status tat_service_flush(tat_service_t S) {
       e = tat_plan_autotune(s.plan, s.cap, fbuf, gbuf, fbuf, s.ws, s.stream, nullptr, nullptr, nullptr, nullptr,
                             nullptr);
       drop_graphs(s);
+      drop_flush_graphs(S);
       s.tuned = true;
     }
     if (e != TAT_OK) {
@@ -391,17 +566,9 @@ tat_status tat_service_flush(tat_service_t S) {
       if (first_error == TAT_OK) first_error = e;
       continue;
     }
-    for (size_t i = 0; i < s.pending.size(); i += (size_t)s.cap) {
-      const size_t j = std::min(s.pending.size(), i + (size_t)s.cap);
-      std::vector<long long> ids(s.pending.begin() + (long)i, s.pending.begin() + (long)j);
-      e = run_chunk(S, s, ids);
-      if (e != TAT_OK) {
-        fail_now(S, ids, e);
-        if (first_error == TAT_OK) first_error = e;
-      }
-    }
-    s.pending.clear();
+    ready.push_back(&s);
   }
+  run_ready(S, ready, &first_error);
   S->st.slots = 0;
   for (auto& kv : S->slots) S->st.slots += kv.second->cap > 0 ? 1 : 0;
   S->st.peak_bytes = S->arena.peak;
@@ -411,6 +578,7 @@ tat_status tat_service_flush(tat_service_t S) {
 tat_status tat_service_synchronize(tat_service_t S) {
   if (!S) return TAT_ERR_INVALID_ARG;
   tat_status r = TAT_OK;
+  if (S->launch) r = cuda_ok(cudaStreamSynchronize(S->launch), "synchronize");
   for (auto& kv : S->slots)
     if (kv.second->stream) {
       const tat_status e = cuda_ok(cudaStreamSynchronize(kv.second->stream), "synchronize");
@@ -449,6 +617,36 @@ tat_status tat_plan_set_launch_shape(tat_plan_t plan, int strip, int row_pairs, 
     plan->cfg = old;
     return TAT_ERR_UNSUPPORTED;
   }
+  return TAT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// Selects the pass order of the length-2M transform: its tables and thread count with it.
+void apply_order_2M(tat_plan_t plan, int order) {
+  plan->cfg.order_2M = order;
+  plan->cfg.nt_2M = plan->nt_2M_v[order];
+  plan->d.f2M = plan->f2M_v[order];
+}
+}  // namespace
+
+extern "C" {
+
+tat_status tat_plan_set_fft_order(tat_plan_t plan, int order) {
+  if (!plan || (order != 0 && order != 1)) return TAT_ERR_INVALID_ARG;
+  const int old = plan->cfg.order_2M;
+  apply_order_2M(plan, order);
+  if (tat::validate_shapes(plan) != TAT_OK) {
+    apply_order_2M(plan, old);
+    return TAT_ERR_UNSUPPORTED;
+  }
+  return TAT_OK;
+}
+
+tat_status tat_plan_get_fft_order(tat_plan_t plan, int* order) {
+  if (!plan || !order) return TAT_ERR_INVALID_ARG;
+  *order = plan->cfg.order_2M;
   return TAT_OK;
 }
 
@@ -497,9 +695,9 @@ tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, flo
   // then smaller column CTAs for the chosen strip and row pairs (more of them per SM, where the
   // four-step column FFT keeps fewer than 256 threads busy), and strips around the chosen one
   const tat::LaunchCfg first = best;
-  for (int threads : {64, 128})
+  for (int threads : {64, 128, 384})
     for (int strip : {first.strip / 2, first.strip, first.strip * 2}) {
-      if (err != TAT_OK || strip < 2 || strip > 32 || threads >= first.cols_threads) continue;
+      if (err != TAT_OK || strip < 2 || strip > 32 || threads == first.cols_threads) continue;
       plan->cfg = first;
       plan->cfg.cols_threads = threads;
       plan->cfg.strip = strip;
@@ -522,7 +720,15 @@ tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, flo
     plan->cfg.pdl = !best.pdl;
     trial();
   }
+  // and the other pass order of the cosine/sine stages' length-2M FFT (radix-3 passes first
+  // or last), which moves the zero band of the extension and the kept outputs between passes
+  if (err == TAT_OK) {
+    plan->cfg = best;
+    apply_order_2M(plan, 1 - best.order_2M);
+    trial();
+  }
   plan->cfg = err == TAT_OK ? best : base;
+  apply_order_2M(plan, plan->cfg.order_2M);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (err != TAT_OK) return err;

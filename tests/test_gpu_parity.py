@@ -233,3 +233,29 @@ def test_small_column_ctas(pkg, torch, n, cols_threads, strip, row_threads, row_
     assert np.array_equal(fa, fa_default)   # each run of the scatter is summed the same way in any CTA shape
     inv = op.inverse(torch.tensor(g_default, device="cuda:0")).cpu().numpy()   # the inverse's column stage too
     assert rel(inv, inv_default) <= 1e-6
+
+
+@pytest.mark.parametrize("n", [64, 256])
+def test_fft_pass_order_variant(pkg, torch, n):
+    """The other pass order of the length-2M FFT in the cosine and sine stages (the autotuner's
+    FFT choice): A, A* and A^-1 against the oracle at the parity bar, and against order 0."""
+    op, P = make(pkg, torch, dict(n=n, n_det=2 * n, n_t=2 * n, support_radius=0.9))
+    B = 2
+    fs = np.stack([f32(ellipse_phantom(n, 70 + s)) for s in range(B)])
+    gs = np.stack([f32(random_sinogram(2 * n, 2 * n, 80 + s)) for s in range(B)])
+    ft = torch.tensor(fs, dtype=torch.float32, device="cuda:0")
+    gt = torch.tensor(gs, dtype=torch.float32, device="cuda:0")
+    ref = {name: getattr(op, name)(x).cpu().numpy() for name, x in (("forward", ft), ("adjoint", gt), ("inverse", gt))}
+    assert pkg.tat_plan_get_fft_order(op.plan) == 0
+    pkg.tat_plan_set_fft_order(op.plan, 1)
+    assert pkg.tat_plan_get_fft_order(op.plan) == 1
+    out = {name: getattr(op, name)(x).cpu().numpy() for name, x in (("forward", ft), ("adjoint", gt), ("inverse", gt))}
+    for s_ in range(B):
+        assert rel(out["forward"][s_], O.forward(P, fs[s_])) <= TOL
+        assert rel(out["adjoint"][s_], O.adjoint(P, gs[s_])) <= TOL
+    assert rel(out["inverse"][0], O.inverse(P, gs[0])) <= TOL
+    for name in out:
+        assert rel(out[name], ref[name]) <= 1e-6
+    with pytest.raises(pkg.TatError):
+        pkg.tat_plan_set_fft_order(op.plan, 2)
+    pkg.tat_plan_set_fft_order(op.plan, 0)
