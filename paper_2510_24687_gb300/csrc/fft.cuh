@@ -649,13 +649,19 @@ __device__ __forceinline__ void col_fft_fwd(float2* buf, const FftDev& f, const 
 struct NoMid {
   __device__ __forceinline__ void operator()() const {}
 };
+// The barrier among the threads that run a transform: the whole CTA by default; a named
+// barrier of one warp group in a warp-specialised kernel.
+struct CtaBar {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
 
 // Inverse (unnormalised): Z[q] at colpos(q), times conj(pre[q]) -> z[0, n_out) in natural order.
 // `mid()` runs between the two steps of the four-step transform (before the transform for
 // other lengths): a place to issue global loads whose latency the second step hides.
-template <int L, class Mid = NoMid>
+template <int L, class Mid = NoMid, class Bar = CtaBar>
 __device__ __forceinline__ void col_fft_inv(float2* buf, const FftDev& f, const float2* smtw, int tid, int nthr,
-                                            int sthr, int n_out, const float2* __restrict__ pre, Mid mid = Mid{}) {
+                                            int sthr, int n_out, const float2* __restrict__ pre, Mid mid = Mid{},
+                                            Bar bar = Bar{}) {
   if constexpr (!FourStep<L>::on) {
     mid();
     fft<L, true>(buf, f, tid, sthr, f.L, n_out, pre, nullptr);
@@ -682,7 +688,7 @@ __device__ __forceinline__ void col_fft_inv(float2* buf, const FftDev& f, const 
 #pragma unroll
       for (int m1 = 0; m1 < 16; ++m1) buf[xpad<L>(base + 16 * m1 + m)] = v[m1];
     }
-    __syncthreads();
+    bar();
     mid();
     for (int n2 = tid; n2 < 256; n2 += nthr) {
       float2 v[RA];
@@ -707,7 +713,7 @@ __device__ __forceinline__ void col_fft_inv(float2* buf, const FftDev& f, const 
           if (256 * n1 + n2 < n_out) buf[xpad<L>(256 * n1 + n2)] = v[n1];
       }
     }
-    __syncthreads();
+    bar();
   }
 }
 

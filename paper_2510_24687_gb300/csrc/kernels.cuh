@@ -708,10 +708,11 @@ struct RunAhead {
   float2 v = make_float2(0.f, 0.f);
 };
 
-__device__ __forceinline__ void run_ahead_record(const DevPlan& P, int c, int tid, RunAhead& q) {
+// (run runoff[c] + tid + off: off = i * NT for the thread's run of scatter batch i)
+__device__ __forceinline__ void run_ahead_record(const DevPlan& P, int c, int tid, RunAhead& q, int off = 0) {
   q.s = -1;
   if (c < 0 || c > P.ncol - 2) return;
-  const int r0 = P.runoff[c], r1 = P.runoff[c + 1], r = r0 + tid;
+  const int r0 = P.runoff[c], r1 = P.runoff[c + 1], r = r0 + tid + off;
   if (r >= r1) return;
   const int2 run = P.runs[r], nx = P.runs[r + 1];
   const int pk = r > r0 ? P.runs[r - 1].y : 0;
@@ -737,18 +738,21 @@ __device__ __forceinline__ void run_ahead_sample(const float2* __restrict__ Yb, 
 // cell k0 by the run with key k0, which first adds the row-k0 part of the run
 // with key k0-1 if there is one, and cell k0+1 by the run with key k0 when no
 // run has key k0+1.  No atomics: the order of every addition is fixed.
-// The conj(phase) of the column transform is applied once per cell.  `q` holds
-// this thread's first run of the column, loaded ahead (RunAhead).
-template <int L>
+// The conj(phase) of the column transform is applied once per cell.  `qa[i]`,
+// i < NA, hold this thread's runs of the column's first NA batches (run
+// runoff[c] + tid + i * NT), loaded ahead (RunAhead).
+template <int L, int NA = 1>
 __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* __restrict__ Yb, int c, float2* left,
-                                               float2* right, int tid, int NT, const RunAhead& q,
+                                               float2* right, int tid, int NT, const RunAhead* qa,
                                                const float2* smph) {
   const unsigned full = 0xffffffffu;
   const int lane = tid & 31;
   const int r0 = P.runoff[c], r1 = P.runoff[c + 1];
-  bool first = true;
+  int batch = 0;
   // warp-uniform loop (NT is a multiple of 32): lane l takes run base + l
-  for (int base = r0 + (tid - lane); base < r1; base += NT) {
+  for (int base = r0 + (tid - lane); base < r1; base += NT, ++batch) {
+    const bool first = batch < NA;
+    const RunAhead& q = qa[first ? batch : 0];
     const int r = base + lane;
     const bool valid = r < r1;
     int k = 0, s = 0;
@@ -762,7 +766,7 @@ __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* _
     };
     if (valid) {
       int e;
-      if (first) {  // r = r0 + tid: the run loaded ahead
+      if (first) {  // r = r0 + tid + batch * NT: a run loaded ahead
         k = q.k;
         s = q.s;
         e = q.e;
@@ -786,7 +790,6 @@ __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* _
         }
       }
     }
-    first = false;
     // row-k parts of the run with key k-1: from the lane before, or (lane 0) summed again
     float2 plb, prb;
     plb.x = __shfl_up_sync(full, lb.x, 1);
@@ -848,7 +851,7 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
     run_ahead_point(P, ahead);
     run_ahead_sample(Yb, ahead);
     __syncthreads();
-    if (c0 >= 1) scatter_column<L>(P, Yb, c0 - 1, nullptr, first, tid, NT, ahead, smph);  // right side of the previous column
+    if (c0 >= 1) scatter_column<L>(P, Yb, c0 - 1, nullptr, first, tid, NT, &ahead, smph);  // right side of the previous column
     run_ahead_record(P, c0, tid, ahead);
     run_ahead_point(P, ahead);
     run_ahead_sample(Yb, ahead);
@@ -860,7 +863,7 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
     if (nxt != nullptr)
       for (int q = tid; q < SL; q += NT) nxt[q] = make_float2(0.f, 0.f);
     __syncthreads();
-    if (c <= P.ncol - 2) scatter_column<L>(P, Yb, c, cur, nxt, tid, NT, ahead, smph);
+    if (c <= P.ncol - 2) scatter_column<L>(P, Yb, c, cur, nxt, tid, NT, &ahead, smph);
     // the next column's first runs: record now, point before the transform, sample half-way
     run_ahead_record(P, c + 1 < c1 ? c + 1 : -1, tid, ahead);
     __syncthreads();
@@ -887,6 +890,103 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
     float2* col = Xb + (size_t)c * P.n;  // R'[c][0..n): contiguous
     for (int iy = tid; iy < P.n; iy += NT) col[iy] = cur[xpad<L>(iy)];
     __syncthreads();
+  }
+}
+
+// Named barrier among `n` threads (a multiple of 32) of one warp group.
+__device__ __forceinline__ void group_bar(int id, int n) { asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
+
+// The adjoint column stage with its two kinds of work on separate warps.  Warps 0-7
+// (256 threads) run the column transforms, warps 8-11 (128 threads) the scatter, one
+// column apart: in step t the scatter fills column c0 + t - 1 (and the right-hand part of
+// the next column) while the transform group runs column c0 + t - 2, so the scatter's
+// dependent global loads overlap the transform's shared-memory work.  Three column
+// buffers rotate (the one being transformed, the one being scattered into, its right-hand
+// neighbour); each group synchronises internally with its own named barrier (1: transform,
+// 2: scatter) and both meet at the CTA barrier that ends every step.  Same arithmetic, in
+// the same order, as k_cols_adj: the results are identical bit for bit.  Compile-time
+// four-step lengths up to 4096 only.
+constexpr int kWsFftThreads = 256, kWsScatterThreads = 128;
+constexpr int kWsAhead = 3;  // scatter batches of 128 runs loaded ahead (about 370 runs a column at n = 512)
+
+template <int L>
+__global__ void __launch_bounds__(kWsFftThreads + kWsScatterThreads, 2)
+    k_cols_adj_ws(DevPlan P, const float2* __restrict__ Y, long long ys, float2* __restrict__ X, long long xs, int S,
+                  int batch) {
+  static_assert(FourStep<L>::on && L <= 4096, "warp-specialised adjoint column stage: four-step lengths <= 4096");
+  TAT_GRID_DEPENDENCY();
+  extern __shared__ float2 sm[];
+  int strip, b;
+  strip_and_image(batch, &strip, &b);
+  const int N = P.N;
+  const int SL = xpad_len(N);
+  const int tid = threadIdx.x;
+  float2* smtw = sm + 3 * SL;          // four-step twiddles
+  float2* smph = smtw + kFourStepTw;   // two-level phase table
+  load_fourstep_tw(smtw, P.fN.fstw, tid, blockDim.x);
+  load_phase2(smph, P, tid, blockDim.x);
+  const int c0 = strip * S;
+  const int c1 = min(c0 + S, P.ncol);  // owned columns [c0, c1)
+  const float2* Yb = Y + (size_t)b * ys;
+  float2* Xb = X + (size_t)b * xs;
+  auto buf = [&](int c) { return sm + ((c - c0 + 3) % 3) * SL; };  // c >= c0 - 1
+  const bool fft_group = tid < kWsFftThreads;
+  const int gt = fft_group ? tid : tid - kWsFftThreads;  // index within the group
+  RunAhead ahead[kWsAhead];  // scatter group: its runs of the column it scatters next
+  if (!fft_group)
+    for (int i = 0; i < kWsAhead; ++i) {
+      run_ahead_record(P, c0 - 1, gt, ahead[i], i * kWsScatterThreads);
+      run_ahead_point(P, ahead[i]);
+      run_ahead_sample(Yb, ahead[i]);
+    }
+  __syncthreads();  // tables
+  const int nsteps = (c1 - c0) + 2;
+#pragma unroll 1
+  for (int t = 0; t < nsteps; ++t) {
+    if (!fft_group) {
+      const int cs = c0 + t - 1;  // column scattered in this step
+      if (cs < c1) {
+        float2* right = cs + 1 < c1 ? buf(cs + 1) : nullptr;  // zeroed here: its buffer last held column cs - 2
+        float2* left = cs >= c0 ? buf(cs) : nullptr;           // holds cs - 1's right-hand part already
+        if (right != nullptr)
+          for (int q = gt; q < SL; q += kWsScatterThreads) right[q] = make_float2(0.f, 0.f);
+        group_bar(2, kWsScatterThreads);
+        if (cs >= 0 && cs <= P.ncol - 2)
+          scatter_column<L, kWsAhead>(P, Yb, cs, left, right, gt, kWsScatterThreads, ahead, smph);
+        // the next column's runs, while the transform group finishes this step
+        for (int i = 0; i < kWsAhead; ++i) {
+          run_ahead_record(P, cs + 1 < c1 ? cs + 1 : -1, gt, ahead[i], i * kWsScatterThreads);
+          run_ahead_point(P, ahead[i]);
+          run_ahead_sample(Yb, ahead[i]);
+        }
+      }
+    } else {
+      const int cf = c0 + t - 2;  // column transformed in this step
+      if (cf >= c0 && cf < c1) {
+        float2* cur = buf(cf);
+        auto bar1 = [] { group_bar(1, kWsFftThreads); };
+        if (cf == 0) {
+          // column 0 also receives the mirrored samples of the other half circle
+          for (int q = gt; q < N / 2; q += kWsFftThreads) {
+            if (q == 0) {
+              const int p0 = xpad<L>(colpos<L>(0));
+              const float2 v = cur[p0];
+              cur[p0] = make_float2(2.f * v.x, 0.f);
+            } else {
+              const int pa = xpad<L>(colpos<L>(q)), pb = xpad<L>(colpos<L>(N - q));
+              const float2 A = cur[pa], B = cur[pb];
+              cur[pa] = cadd_rn(A, cconj(B));
+              cur[pb] = cadd_rn(B, cconj(A));
+            }
+          }
+          bar1();
+        }
+        col_fft_inv<L>(cur, P.fN, smtw, gt, kWsFftThreads, kWsFftThreads, P.n, nullptr, NoMid{}, bar1);
+        float2* col = Xb + (size_t)cf * P.n;
+        for (int iy = gt; iy < P.n; iy += kWsFftThreads) col[iy] = cur[xpad<L>(iy)];
+      }
+    }
+    __syncthreads();  // end of the step: both groups
   }
 }
 

@@ -110,7 +110,13 @@ struct tat_service_s {
   tat_service_stats st{};
   // single-graph flushes: the launch stream, its completion event and the executable graphs
   // by composition (slot keys and batch sizes); dropped whenever a slot's buffers change
-  cudaStream_t launch = nullptr;
+  // (a small pool, used in turn: consecutive flushes must not queue behind one another --
+  // each slot's own stream already orders that slot's work from flush to flush)
+  static constexpr int kLaunchStreams = 4;
+  cudaStream_t launch_pool[kLaunchStreams] = {};
+  cudaEvent_t launched_pool[kLaunchStreams] = {};
+  int next_launch = 0;
+  cudaStream_t launch = nullptr;  // the pool entry of the current flush
   cudaEvent_t launched = nullptr;
   std::map<std::string, cudaGraphExec_t> flush_graphs;
   // how often each composition has been flushed: a composition gets its single graph on its
@@ -179,9 +185,14 @@ void drop_flush_graphs(tat_service_s* S) {
   S->flush_graphs.clear();
 }
 
+void sync_launch_pool(tat_service_s* S) {
+  for (cudaStream_t st : S->launch_pool)
+    if (st) cudaStreamSynchronize(st);
+}
+
 void evict(tat_service_s* S, Slot& s) {
   cudaStreamSynchronize(s.stream);
-  if (S->launch) cudaStreamSynchronize(S->launch);
+  sync_launch_pool(S);
   drop_graphs(s);
   drop_flush_graphs(S);
   S->arena.release(s.off);
@@ -313,9 +324,14 @@ tat_status run_flush_graph(tat_service_s* S, const std::vector<Slot*>& ready,
     if (++S->seen[key] < 2) return TAT_ERR_UNSUPPORTED;  // first sight: the per-slot path runs it
   }
   tat_status e = TAT_OK;
-  if (!S->launch) e = cuda_ok(cudaStreamCreateWithFlags(&S->launch, cudaStreamNonBlocking), "launch stream");
-  if (e == TAT_OK && !S->launched)
-    e = cuda_ok(cudaEventCreateWithFlags(&S->launched, cudaEventDisableTiming), "launch event");
+  const int li = S->next_launch;
+  S->next_launch = (li + 1) % tat_service_s::kLaunchStreams;
+  if (!S->launch_pool[li])
+    e = cuda_ok(cudaStreamCreateWithFlags(&S->launch_pool[li], cudaStreamNonBlocking), "launch stream");
+  if (e == TAT_OK && !S->launched_pool[li])
+    e = cuda_ok(cudaEventCreateWithFlags(&S->launched_pool[li], cudaEventDisableTiming), "launch event");
+  S->launch = S->launch_pool[li];
+  S->launched = S->launched_pool[li];
   for (size_t i = 0; i < ready.size() && e == TAT_OK; ++i) {
     Slot& s = *ready[i];
     if (!s.branch) e = cuda_ok(cudaStreamCreateWithFlags(&s.branch, cudaStreamNonBlocking), "branch stream");
@@ -439,7 +455,7 @@ tat_status tat_service_create(tat_service_t* svc, const tat_service_config* cfg)
 
 tat_status tat_service_destroy(tat_service_t S) {
   if (!S) return TAT_ERR_INVALID_ARG;
-  if (S->launch) cudaStreamSynchronize(S->launch);
+  sync_launch_pool(S);
   drop_flush_graphs(S);
   for (auto& kv : S->slots) {
     Slot& s = *kv.second;
@@ -449,8 +465,10 @@ tat_status tat_service_destroy(tat_service_t S) {
     if (s.branch) cudaStreamDestroy(s.branch);
     if (s.staged) cudaEventDestroy(s.staged);
   }
-  if (S->launch) cudaStreamDestroy(S->launch);
-  if (S->launched) cudaEventDestroy(S->launched);
+  for (int i = 0; i < tat_service_s::kLaunchStreams; ++i) {
+    if (S->launch_pool[i]) cudaStreamDestroy(S->launch_pool[i]);
+    if (S->launched_pool[i]) cudaEventDestroy(S->launched_pool[i]);
+  }
   for (auto& kv : S->plans) tat_plan_destroy(kv.second);
   cudaFree(S->arena.base);
   delete S;
@@ -498,7 +516,8 @@ namespace {
 // chunk by chunk on the slots' own streams.
 void run_ready(tat_service_t S, std::vector<Slot*>& ready, tat_status* first_error) {
   size_t skip_first = 0;
-  if (S->cfg.one_graph && S->cfg.use_graphs && !ready.empty()) {
+  // (a flush of one slot is one graph launch on that slot's stream anyway)
+  if (S->cfg.one_graph && S->cfg.use_graphs && ready.size() >= 2) {
     std::vector<std::vector<long long>> chunk(ready.size());
     for (size_t i = 0; i < ready.size(); ++i) {
       Slot& s = *ready[i];
@@ -578,7 +597,8 @@ tat_status tat_service_flush(tat_service_t S) {
 tat_status tat_service_synchronize(tat_service_t S) {
   if (!S) return TAT_ERR_INVALID_ARG;
   tat_status r = TAT_OK;
-  if (S->launch) r = cuda_ok(cudaStreamSynchronize(S->launch), "synchronize");
+  for (cudaStream_t st : S->launch_pool)
+    if (st && r == TAT_OK) r = cuda_ok(cudaStreamSynchronize(st), "synchronize");
   for (auto& kv : S->slots)
     if (kv.second->stream) {
       const tat_status e = cuda_ok(cudaStreamSynchronize(kv.second->stream), "synchronize");
@@ -647,6 +667,23 @@ tat_status tat_plan_set_fft_order(tat_plan_t plan, int order) {
 tat_status tat_plan_get_fft_order(tat_plan_t plan, int* order) {
   if (!plan || !order) return TAT_ERR_INVALID_ARG;
   *order = plan->cfg.order_2M;
+  return TAT_OK;
+}
+
+tat_status tat_plan_set_adjoint_ws(tat_plan_t plan, int on) {
+  if (!plan || (on != 0 && on != 1)) return TAT_ERR_INVALID_ARG;
+  const int old = plan->cfg.cols_adj_ws;
+  plan->cfg.cols_adj_ws = on;
+  if (tat::validate_shapes(plan) != TAT_OK) {
+    plan->cfg.cols_adj_ws = old;
+    return TAT_ERR_UNSUPPORTED;
+  }
+  return TAT_OK;
+}
+
+tat_status tat_plan_get_adjoint_ws(tat_plan_t plan, int* on) {
+  if (!plan || !on) return TAT_ERR_INVALID_ARG;
+  *on = plan->cfg.cols_adj_ws;
   return TAT_OK;
 }
 
@@ -726,6 +763,17 @@ tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, flo
     plan->cfg = best;
     apply_order_2M(plan, 1 - best.order_2M);
     trial();
+  }
+  // and the adjoint column stage on separate scatter and transform warps, with half, the same
+  // and twice the chosen strip (where the kernel exists: four-step lengths up to 4096)
+  const tat::LaunchCfg third = best;
+  for (int strip : {third.strip / 2, third.strip, third.strip * 2}) {
+    if (err != TAT_OK || strip < 2 || strip > 32) continue;
+    plan->cfg = third;
+    apply_order_2M(plan, third.order_2M);
+    plan->cfg.cols_adj_ws = 1 - third.cols_adj_ws;
+    plan->cfg.strip = strip;
+    trial();  // skipped when validate_shapes rejects the variant
   }
   plan->cfg = err == TAT_OK ? best : base;
   apply_order_2M(plan, plan->cfg.order_2M);
