@@ -108,9 +108,8 @@ tat_status tat_service_get_stats(tat_service_t svc, tat_service_stats* stats);
  * 128 for the four-step column lengths only) with half, the same and twice its strip, then
  * row groups of 64 and 128 threads (instead of 256; lengths N <= 1024) with 1, 2
  * and 4 times its row pairs, the best shape with and without programmatic
- * dependent launch of the stages, the other pass order of the length-2M FFT of
- * the cosine and sine stages (tat_plan_set_fft_order), and the adjoint column stage
- * on separate scatter and transform warps (tat_plan_set_adjoint_ws) -- on
+ * dependent launch of the stages, and the other pass order of the length-2M FFT of
+ * the cosine and sine stages (tat_plan_set_fft_order) -- on
  * one A then one A* of `batch` images at f (device, batch*n*n floats, output
  * of A* written to f_out) with g (batch*n_det*n_t floats) and the workspace
  * for `batch`, and keeps the fastest for every later call on this plan.  The
@@ -139,15 +138,6 @@ tat_status tat_plan_set_launch_shape(tat_plan_t plan, int strip, int row_pairs, 
  * and read the order directly.  TAT_ERR_INVALID_ARG for an order other than 0 or 1. */
 tat_status tat_plan_set_fft_order(tat_plan_t plan, int order);
 tat_status tat_plan_get_fft_order(tat_plan_t plan, int* order);
-
-/* 1: the adjoint's column stage runs on separate warp groups -- 4 warps scatter the next
- * column while 8 warps transform the current one (three rotating column buffers, 384
- * threads and about 107 KB of shared memory a CTA at N = 4096); 0: every warp does both in
- * turn.  The same arithmetic in the same order: A* is identical bit for bit.  Four-step
- * column lengths N = 512 .. 4096 only (TAT_ERR_UNSUPPORTED otherwise, plan unchanged);
- * tat_plan_autotune tries both. */
-tat_status tat_plan_set_adjoint_ws(tat_plan_t plan, int on);
-tat_status tat_plan_get_adjoint_ws(tat_plan_t plan, int* on);
 
 #ifdef __cplusplus
 }

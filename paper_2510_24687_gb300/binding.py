@@ -115,8 +115,6 @@ def load() -> ctypes.CDLL:
         "tat_plan_set_launch_shape": (_I, [_P, _I, _I, _I, _I]),
         "tat_plan_set_fft_order": (_I, [_P, _I]),
         "tat_plan_get_fft_order": (_I, [_P, ctypes.POINTER(_I)]),
-        "tat_plan_set_adjoint_ws": (_I, [_P, _I]),
-        "tat_plan_get_adjoint_ws": (_I, [_P, ctypes.POINTER(_I)]),
         "tat_lpd_scratch_floats": (ctypes.c_size_t, [_I, _I, _I]),
         "tat_conv_in_fwd": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P]),
         "tat_conv_in_bwd_data": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _I, _P]),
@@ -319,17 +317,6 @@ def tat_plan_set_fft_order(plan, order):
 def tat_plan_get_fft_order(plan):
     o = _I()
     _check(load().tat_plan_get_fft_order(plan, ctypes.byref(o)), "tat_plan_get_fft_order")
-    return o.value
-
-
-def tat_plan_set_adjoint_ws(plan, on):
-    """1: the adjoint column stage on separate scatter and transform warps (same results)."""
-    _check(load().tat_plan_set_adjoint_ws(plan, int(on)), "tat_plan_set_adjoint_ws")
-
-
-def tat_plan_get_adjoint_ws(plan):
-    o = _I()
-    _check(load().tat_plan_get_adjoint_ws(plan, ctypes.byref(o)), "tat_plan_get_adjoint_ws")
     return o.value
 
 

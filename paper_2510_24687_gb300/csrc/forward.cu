@@ -26,8 +26,6 @@ tat_status validate_shapes(const tat_plan_s* Pl) {
   if (N == 8192 && s.rows_block > 512) return TAT_ERR_UNSUPPORTED;  // launch bound of the row kernels there
   for (size_t m : smem)
     if (m > mx) return TAT_ERR_UNSUPPORTED;
-  // the warp-specialised adjoint column stage: four-step lengths up to 4096 only
-  if (Pl->cfg.cols_adj_ws && (!four || N > 4096 || s.cols_smem_ws > mx)) return TAT_ERR_UNSUPPORTED;
   if (Pl->cfg.t_tile % 2 || Pl->cfg.strip < 1 || Pl->cfg.rings_per_cta < 1) return TAT_ERR_INVALID_ARG;
   return TAT_OK;
 }

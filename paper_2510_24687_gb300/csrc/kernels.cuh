@@ -893,103 +893,6 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
   }
 }
 
-// Named barrier among `n` threads (a multiple of 32) of one warp group.
-__device__ __forceinline__ void group_bar(int id, int n) { asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory"); }
-
-// The adjoint column stage with its two kinds of work on separate warps.  Warps 0-7
-// (256 threads) run the column transforms, warps 8-11 (128 threads) the scatter, one
-// column apart: in step t the scatter fills column c0 + t - 1 (and the right-hand part of
-// the next column) while the transform group runs column c0 + t - 2, so the scatter's
-// dependent global loads overlap the transform's shared-memory work.  Three column
-// buffers rotate (the one being transformed, the one being scattered into, its right-hand
-// neighbour); each group synchronises internally with its own named barrier (1: transform,
-// 2: scatter) and both meet at the CTA barrier that ends every step.  Same arithmetic, in
-// the same order, as k_cols_adj: the results are identical bit for bit.  Compile-time
-// four-step lengths up to 4096 only.
-constexpr int kWsFftThreads = 256, kWsScatterThreads = 128;
-constexpr int kWsAhead = 3;  // scatter batches of 128 runs loaded ahead (about 370 runs a column at n = 512)
-
-template <int L>
-__global__ void __launch_bounds__(kWsFftThreads + kWsScatterThreads, 2)
-    k_cols_adj_ws(DevPlan P, const float2* __restrict__ Y, long long ys, float2* __restrict__ X, long long xs, int S,
-                  int batch) {
-  static_assert(FourStep<L>::on && L <= 4096, "warp-specialised adjoint column stage: four-step lengths <= 4096");
-  TAT_GRID_DEPENDENCY();
-  extern __shared__ float2 sm[];
-  int strip, b;
-  strip_and_image(batch, &strip, &b);
-  const int N = P.N;
-  const int SL = xpad_len(N);
-  const int tid = threadIdx.x;
-  float2* smtw = sm + 3 * SL;          // four-step twiddles
-  float2* smph = smtw + kFourStepTw;   // two-level phase table
-  load_fourstep_tw(smtw, P.fN.fstw, tid, blockDim.x);
-  load_phase2(smph, P, tid, blockDim.x);
-  const int c0 = strip * S;
-  const int c1 = min(c0 + S, P.ncol);  // owned columns [c0, c1)
-  const float2* Yb = Y + (size_t)b * ys;
-  float2* Xb = X + (size_t)b * xs;
-  auto buf = [&](int c) { return sm + ((c - c0 + 3) % 3) * SL; };  // c >= c0 - 1
-  const bool fft_group = tid < kWsFftThreads;
-  const int gt = fft_group ? tid : tid - kWsFftThreads;  // index within the group
-  RunAhead ahead[kWsAhead];  // scatter group: its runs of the column it scatters next
-  if (!fft_group)
-    for (int i = 0; i < kWsAhead; ++i) {
-      run_ahead_record(P, c0 - 1, gt, ahead[i], i * kWsScatterThreads);
-      run_ahead_point(P, ahead[i]);
-      run_ahead_sample(Yb, ahead[i]);
-    }
-  __syncthreads();  // tables
-  const int nsteps = (c1 - c0) + 2;
-#pragma unroll 1
-  for (int t = 0; t < nsteps; ++t) {
-    if (!fft_group) {
-      const int cs = c0 + t - 1;  // column scattered in this step
-      if (cs < c1) {
-        float2* right = cs + 1 < c1 ? buf(cs + 1) : nullptr;  // zeroed here: its buffer last held column cs - 2
-        float2* left = cs >= c0 ? buf(cs) : nullptr;           // holds cs - 1's right-hand part already
-        if (right != nullptr)
-          for (int q = gt; q < SL; q += kWsScatterThreads) right[q] = make_float2(0.f, 0.f);
-        group_bar(2, kWsScatterThreads);
-        if (cs >= 0 && cs <= P.ncol - 2)
-          scatter_column<L, kWsAhead>(P, Yb, cs, left, right, gt, kWsScatterThreads, ahead, smph);
-        // the next column's runs, while the transform group finishes this step
-        for (int i = 0; i < kWsAhead; ++i) {
-          run_ahead_record(P, cs + 1 < c1 ? cs + 1 : -1, gt, ahead[i], i * kWsScatterThreads);
-          run_ahead_point(P, ahead[i]);
-          run_ahead_sample(Yb, ahead[i]);
-        }
-      }
-    } else {
-      const int cf = c0 + t - 2;  // column transformed in this step
-      if (cf >= c0 && cf < c1) {
-        float2* cur = buf(cf);
-        auto bar1 = [] { group_bar(1, kWsFftThreads); };
-        if (cf == 0) {
-          // column 0 also receives the mirrored samples of the other half circle
-          for (int q = gt; q < N / 2; q += kWsFftThreads) {
-            if (q == 0) {
-              const int p0 = xpad<L>(colpos<L>(0));
-              const float2 v = cur[p0];
-              cur[p0] = make_float2(2.f * v.x, 0.f);
-            } else {
-              const int pa = xpad<L>(colpos<L>(q)), pb = xpad<L>(colpos<L>(N - q));
-              const float2 A = cur[pa], B = cur[pb];
-              cur[pa] = cadd_rn(A, cconj(B));
-              cur[pb] = cadd_rn(B, cconj(A));
-            }
-          }
-          bar1();
-        }
-        col_fft_inv<L>(cur, P.fN, smtw, gt, kWsFftThreads, kWsFftThreads, P.n, nullptr, NoMid{}, bar1);
-        float2* col = Xb + (size_t)cf * P.n;
-        for (int iy = gt; iy < P.n; iy += kWsFftThreads) col[iy] = cur[xpad<L>(iy)];
-      }
-    }
-    __syncthreads();  // end of the step: both groups
-  }
-}
-
 // Row stage of A* and A^{-1}: rebuilds the Hermitian row spectra of this CTA's
 // RP row pairs from the column-major R'[q][iy] and runs the inverse row DFTs;
 // row pair g of the CTA ends in sm + g * xpad_len(N), rows 2*pair and 2*pair+1

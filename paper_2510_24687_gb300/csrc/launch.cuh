@@ -15,7 +15,7 @@ namespace {
 struct Shapes {
   dim3 rows_grid, cols_grid_f, cols_grid_a, rings_grid, modes_grid, theta_grid;
   int rows_block, cols_block, cols_block_i, rings_block, modes_block, theta_block;
-  size_t rows_smem, cols_smem_f, cols_smem_a, cols_smem_i, cols_smem_ws, rings_smem, modes_smem, theta_smem;
+  size_t rows_smem, cols_smem_f, cols_smem_a, cols_smem_i, rings_smem, modes_smem, theta_smem;
   int ntiles;
 };
 
@@ -37,7 +37,6 @@ inline Shapes shapes(const tat_plan_s* Pl, int batch) {
   s.cols_smem_f = (2 * (size_t)xpad_len(P.N) + kFourStepTw + P.ph_lo + 64) * sizeof(float2);
   s.cols_smem_a = (2 * (size_t)xpad_len(P.N) + kFourStepTw + P.ph_lo + 64) * sizeof(float2);
   s.cols_smem_i = ((size_t)xpad_len(P.N) + kFourStepTw) * sizeof(float2);
-  s.cols_smem_ws = (3 * (size_t)xpad_len(P.N) + kFourStepTw + P.ph_lo + 64) * sizeof(float2);
   s.ntiles = (P.J + c.rings_per_cta - 1) / c.rings_per_cta;
   s.rings_grid = dim3(s.ntiles + P.n_low, batch);
   s.rings_block = c.rings_per_cta * c.nt_phi;

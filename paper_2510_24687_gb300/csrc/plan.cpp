@@ -394,7 +394,6 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
   d.f2M = P->f2M_v[0];
   P->cfg.nt_2M = P->nt_2M_v[0];
   P->cfg.order_2M = 0;
-  P->cfg.cols_adj_ws = 0;
   TAT_TRY(make_fft(P, n_det, &d.fdet, &P->cfg.nt_det));
 
   // Phase e^{-i xi_q x_0} = e^{i q dxi} (x_0 = -1) of every FFT bin, q signed:

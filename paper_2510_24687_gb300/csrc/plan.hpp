@@ -113,7 +113,6 @@ struct LaunchCfg {
   int cols_threads;   // threads per CTA of the column pass (>= nt_N; fewer than 256 only for four-step lengths)
   int pdl;            // 1: stages launched with programmatic dependent launch (outside graph capture)
   int order_2M;       // pass order of the length-2M FFT of the cosine/sine stages (Sched V: 0 or 1)
-  int cols_adj_ws;    // 1: the adjoint column stage on separate scatter and transform warps (k_cols_adj_ws)
 };
 
 }  // namespace tat

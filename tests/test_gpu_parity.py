@@ -260,23 +260,3 @@ def test_fft_pass_order_variant(pkg, torch, n):
         pkg.tat_plan_set_fft_order(op.plan, 2)
     pkg.tat_plan_set_fft_order(op.plan, 0)
 
-
-@pytest.mark.parametrize("n,strip", [(64, 8), (128, 4), (256, 16), (512, 16)])
-def test_adjoint_warp_specialised_columns(pkg, torch, n, strip):
-    """The adjoint column stage on separate scatter and transform warps gives A* bit for bit
-    (same arithmetic, same order), at several sizes and strip widths, ragged last strips
-    included."""
-    op, P = make(pkg, torch, dict(n=n, n_det=2 * n, n_t=2 * n, support_radius=0.9))
-    B = 2
-    gs = np.stack([f32(random_sinogram(2 * n, 2 * n, 90 + s)) for s in range(B)])
-    gt = torch.tensor(gs, dtype=torch.float32, device="cuda:0")
-    pkg.tat_plan_set_launch_shape(op.plan, strip, 2, 256, 0)
-    ref = op.adjoint(gt).cpu().numpy()
-    assert pkg.tat_plan_get_adjoint_ws(op.plan) == 0
-    pkg.tat_plan_set_adjoint_ws(op.plan, 1)
-    assert pkg.tat_plan_get_adjoint_ws(op.plan) == 1
-    out = op.adjoint(gt).cpu().numpy()
-    assert np.array_equal(out, ref)
-    if n <= 256:
-        assert rel(out[0], O.adjoint(P, gs[0])) <= TOL
-    pkg.tat_plan_set_adjoint_ws(op.plan, 0)
