@@ -64,7 +64,7 @@ def parse_args():
 
 # ------------------------------------------------------------------ helpers
 
-OPERATOR_SOURCES = ("fft.cuh", "kernels.cuh", "launch.cuh", "pdl.cuh", "plan.cpp", "plan.hpp", "forward.cu",
+OPERATOR_SOURCES = ("fft.cuh", "kernels.cuh", "colsplit.cuh", "launch.cuh", "pdl.cuh", "plan.cpp", "plan.hpp", "forward.cu",
                     "adjoint.cu", "inverse.cu")
 
 
@@ -654,8 +654,9 @@ def main():
     B = args.batch
     op = pkg.TatOperator(N_IMG, N_DET, N_T, T=T_WIN, support_radius=RSUP, device=dev)
     info = op.info
-    # the library's autotuner picks the column-strip width and row pairs for this batch once,
-    # before any timing (results unchanged up to the adjoint's atomic rounding order)
+    # the library's autotuner picks the launch shapes, the FFT pass order and the column
+    # transform for this batch once, before any timing (results unchanged up to the rounding
+    # of the pass order and column transform it picks)
     tuned = None if args.no_autotune else op.autotune(B)
     fh = phantom_batch(N_IMG, B, seed0=replica_seed0(rank, B)).astype(np.float32)
     f = torch.tensor(fh, device=dev)
@@ -771,9 +772,11 @@ def main():
                 "data": "synthetic (seeded random-ellipse phantoms; the paper's phantoms are not published)",
                 "config": workload_config(B), "roofline": roofline, "hbm_roofline_pair": hbm,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 10 * args.steps, "comparisons": comparisons,
-                "launch_shapes": ({"autotuned": True, "strip": tuned[1], "row_pairs": tuned[2],
-                                   "cols_threads": tuned[3], "row_threads": tuned[4], "autotune_ms_pair_batch": tuned[0]}
-                                  if tuned else {"autotuned": False}),
+                "launch_shapes": dict(({"autotuned": True, "strip": tuned[1], "row_pairs": tuned[2],
+                                        "cols_threads": tuned[3], "row_threads": tuned[4],
+                                        "autotune_ms_pair_batch": tuned[0]} if tuned else {"autotuned": False}),
+                                      column_split=pkg.tat_plan_get_column_split(op.plan),
+                                      fft_order=pkg.tat_plan_get_fft_order(op.plan)),
                 "clocks": clk, "plan": {k: info[k] for k in ("N", "M", "J", "n_phi", "n_low", "n_points")},
                 "kernel_source_hash": kernel_source_hash()}
         print(json.dumps(line), flush=True)

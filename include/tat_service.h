@@ -108,13 +108,14 @@ tat_status tat_service_get_stats(tat_service_t svc, tat_service_stats* stats);
  * 128 for the four-step column lengths only) with half, the same and twice its strip, then
  * row groups of 64 and 128 threads (instead of 256; lengths N <= 1024) with 1, 2
  * and 4 times its row pairs, the best shape with and without programmatic
- * dependent launch of the stages, and the other pass order of the length-2M FFT of
- * the cosine and sine stages (tat_plan_set_fft_order) -- on
+ * dependent launch of the stages, the other pass order of the length-2M FFT of
+ * the cosine and sine stages (tat_plan_set_fft_order) and the other column transform
+ * at N = 4096 (tat_plan_set_column_split) -- on
  * one A then one A* of `batch` images at f (device, batch*n*n floats, output
  * of A* written to f_out) with g (batch*n_det*n_t floats) and the workspace
  * for `batch`, and keeps the fastest for every later call on this plan.  The
  * shapes only regroup work: A* is unchanged bit for bit, A and A^-1 up to the
- * rounding of the FFT pass order.  Synchronises `stream`.  *ms_best
+ * rounding of the FFT pass order (and both up to that of the column transform).  Synchronises `stream`.  *ms_best
  * (optional) receives the chosen shape's time for the pair, *strip,
  * *row_pairs, *cols_threads and *row_threads (optional) the chosen knobs
  * (tat_plan_get_fft_order reports the chosen pass order). */
@@ -138,6 +139,17 @@ tat_status tat_plan_set_launch_shape(tat_plan_t plan, int strip, int row_pairs, 
  * and read the order directly.  TAT_ERR_INVALID_ARG for an order other than 0 or 1. */
 tat_status tat_plan_set_fft_order(tat_plan_t plan, int order);
 tat_status tat_plan_get_fft_order(tat_plan_t plan, int* order);
+
+/* Column transform of the column stages of A and A* (Algorithm 1 step 2 and its transpose)
+ * at N = 4096 with n <= 512: 1 splits each length-4096 column DFT into eight 512-point
+ * DFTs, one per warp of a 256-thread CTA (the column's rows are zero from n on, so bin
+ * q = k1 + 8 k2 takes only the 512-point DFT k2 of the rows twiddled by w_N^(m k1));
+ * 0 runs the four-step transform in CTA-wide passes.  The plan's default is 1 wherever it
+ * applies; tat_plan_autotune tries both.  The results agree to rounding (each variant is
+ * deterministic bit for bit on its own).  Elsewhere the setting is kept and has no effect.
+ * TAT_ERR_INVALID_ARG for a value other than 0 or 1. */
+tat_status tat_plan_set_column_split(tat_plan_t plan, int on);
+tat_status tat_plan_get_column_split(tat_plan_t plan, int* on);
 
 #ifdef __cplusplus
 }

@@ -27,6 +27,7 @@ from .autograd import A, Astar  # noqa: E402
 from .solvers import TatSolver, nnls_unrolled, pdhg_steps, power_norm_sq, tv_unrolled  # noqa: E402
 from .binding import tat_debug_inverse_batched_timed, tat_inverse, tat_inverse_batched  # noqa: E402
 from .binding import (TatService, tat_plan_autotune, tat_plan_get_fft_order, tat_plan_set_fft_order,  # noqa: E402
+                      tat_plan_get_column_split, tat_plan_set_column_split,
                       tat_plan_set_launch_shape, tat_service_config_default, tat_service_create,
                       tat_service_destroy, tat_service_flush, tat_service_get_stats, tat_service_latency,
                       tat_service_submit, tat_service_synchronize)
@@ -35,7 +36,7 @@ from .binding import (tat_axpby_clamp, tat_axpby_clamp_backward, tat_pd_dual_dat
 
 __all__ += ["lpd", "tat_adam", "tat_conv_in_bwd", "tat_conv_in_bwd_data", "tat_conv_in_bwd_weights", "tat_conv_in_fwd",
             "tat_conv_mid_bwd_data", "tat_conv_mid_bwd_weights", "tat_conv_mid_fwd", "tat_conv_out_bwd",
-            "tat_conv_out_fwd", "tat_fill", "tat_lpd_check", "tat_lpd_scratch_floats", "tat_lpd_timeout_probe", "tat_mse", "tat_to_bf16", "TatService", "tat_plan_autotune", "tat_plan_get_fft_order", "tat_plan_set_fft_order", "tat_plan_set_launch_shape", "tat_service_config_default", "tat_service_create",
+            "tat_conv_out_fwd", "tat_fill", "tat_lpd_check", "tat_lpd_scratch_floats", "tat_lpd_timeout_probe", "tat_mse", "tat_to_bf16", "TatService", "tat_plan_autotune", "tat_plan_get_fft_order", "tat_plan_set_fft_order", "tat_plan_get_column_split", "tat_plan_set_column_split", "tat_plan_set_launch_shape", "tat_service_config_default", "tat_service_create",
             "tat_service_destroy", "tat_service_flush", "tat_service_get_stats", "tat_service_latency",
             "tat_service_submit", "tat_service_synchronize", "tat_inverse", "tat_inverse_batched", "tat_debug_inverse_batched_timed", "autograd", "solvers", "A", "Astar", "TatSolver", "nnls_unrolled", "pdhg_steps", "power_norm_sq",
             "tv_unrolled", "tat_axpby_clamp", "tat_axpby_clamp_backward", "tat_pd_dual_data", "tat_tv_dual",

@@ -115,6 +115,8 @@ def load() -> ctypes.CDLL:
         "tat_plan_set_launch_shape": (_I, [_P, _I, _I, _I, _I]),
         "tat_plan_set_fft_order": (_I, [_P, _I]),
         "tat_plan_get_fft_order": (_I, [_P, ctypes.POINTER(_I)]),
+        "tat_plan_set_column_split": (_I, [_P, _I]),
+        "tat_plan_get_column_split": (_I, [_P, ctypes.POINTER(_I)]),
         "tat_lpd_scratch_floats": (ctypes.c_size_t, [_I, _I, _I]),
         "tat_conv_in_fwd": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _P]),
         "tat_conv_in_bwd_data": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P, _P, _I, _P]),
@@ -317,6 +319,17 @@ def tat_plan_set_fft_order(plan, order):
 def tat_plan_get_fft_order(plan):
     o = _I()
     _check(load().tat_plan_get_fft_order(plan, ctypes.byref(o)), "tat_plan_get_fft_order")
+    return o.value
+
+
+def tat_plan_set_column_split(plan, on):
+    """Column transform at N = 4096 (n <= 512): 1 eight warp-level 512-point DFTs, 0 four-step."""
+    _check(load().tat_plan_set_column_split(plan, int(on)), "tat_plan_set_column_split")
+
+
+def tat_plan_get_column_split(plan):
+    o = _I()
+    _check(load().tat_plan_get_column_split(plan, ctypes.byref(o)), "tat_plan_get_column_split")
     return o.value
 
 

@@ -43,7 +43,16 @@ tat_status launch_adjoint(const tat_plan_s* Pl, int batch, const float* g, long 
   dispatch_N(P.N, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_cols_adj<L>>(dev) && ensure_smem<k_rows_adj<L>>(dev);
-    ok &= pdl_launch(c.pdl != 0, k_cols_adj<L>, s.cols_grid_a, s.cols_block, s.cols_smem_a, st, P, Y, ys, X, xs, c.strip, c.nt_N, batch) == cudaSuccess;
+    if constexpr (split_length(L)) {
+      if (s.cols_split) {
+        ok &= ensure_smem<k_cols_adj_split<L>>(dev);
+        ok &= pdl_launch(c.pdl != 0, k_cols_adj_split<L>, s.cols_grid_a, s.cols_block, s.cols_smem_a, st, P, Y, ys, X, xs, c.strip, batch) == cudaSuccess;
+      } else {
+        ok &= pdl_launch(c.pdl != 0, k_cols_adj<L>, s.cols_grid_a, s.cols_block, s.cols_smem_a, st, P, Y, ys, X, xs, c.strip, c.nt_N, batch) == cudaSuccess;
+      }
+    } else {
+      ok &= pdl_launch(c.pdl != 0, k_cols_adj<L>, s.cols_grid_a, s.cols_block, s.cols_smem_a, st, P, Y, ys, X, xs, c.strip, c.nt_N, batch) == cudaSuccess;
+    }
     stage_done();
     ok &= pdl_launch(c.pdl != 0, k_rows_adj<L>, s.rows_grid, s.rows_block, s.rows_smem, st, P, X, xs, f, fs, c.rows_pairs, c.nt_rows) == cudaSuccess;
     stage_done();

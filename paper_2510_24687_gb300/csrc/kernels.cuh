@@ -18,7 +18,9 @@
 //   k_theta_fwd  steps 6-7: per time sample, inverse DFT over the modes
 //                (Eq. FourSerForg; two time samples per complex FFT), arc mask
 //                -> g[d][m]
-// Adjoint: the same five kernels transposed, in reverse order.  Only the
+// Adjoint: the same five kernels transposed, in reverse order; between its angular
+// and column stages the polar samples lie in the order of the plan's point table
+// (column, then row of the bilinear stencil), which the scatter walks.  Only the
 // half plane q_x >= 0 of the spectrum and the half circle phi in [-pi/2, pi/2)
 // are processed; the other halves follow from Hermitian symmetry (f real).
 #pragma once
@@ -623,7 +625,7 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
     for (int l = threadIdx.x; l < P.nh; l += blockDim.x) {
       const float2 cs = P.cs_half[l];
       const float2 e = cs, ec = cconj(cs);
-      Yb[(size_t)r * P.nh + l] = cadd(c0, cadd(cmul(c1, e), cmul(cm, ec)));
+      Yb[__ldg(&P.pinv[(size_t)r * P.nh + l])] = cadd(c0, cadd(cmul(c1, e), cmul(cm, ec)));
     }
     return;
   }
@@ -674,7 +676,7 @@ __global__ void __launch_bounds__(1024) k_rings_adj(DevPlan P, const float2* __r
       for (int l = gt; l < P.nh; l += nt) {
         int s = l - q4;
         if (s < 0) s += P.n_phi;
-        Yb[(size_t)r * P.nh + l] = buf[xpad<L>(s)];
+        Yb[__ldg(&P.pinv[(size_t)r * P.nh + l])] = buf[xpad<L>(s)];
       }
     }
   }
@@ -698,9 +700,10 @@ __device__ __forceinline__ float w_r0(const PolarEntry& e) { return __fmul_rn(e.
 __device__ __forceinline__ float w_r1(const PolarEntry& e) { return __fmul_rn(e.a, e.b); }
 
 // A thread's first run of a column (run runoff[c] + tid), loaded ahead of the column's
-// scatter in three steps -- run record, first point, polar sample -- each issued a
-// phase before it is needed, so that the column transform in between hides the
-// latency of the dependent global loads.
+// scatter in two steps -- run record, then its first point and polar sample (the
+// samples lie in the order of the point table, so both come from the run's first
+// index) -- each issued a phase before it is needed, so that the column transform in
+// between hides the latency of the dependent global loads.
 struct RunAhead {
   int s = -1, e = 0, k = 0;  // first point, end, key (s < 0: no run for this thread)
   bool prev = false, next = false;  // runs with keys k-1 / k+1 in the same column
@@ -722,11 +725,11 @@ __device__ __forceinline__ void run_ahead_record(const DevPlan& P, int c, int ti
   q.prev = r > r0 && pk == run.y - 1;
   q.next = r + 1 < r1 && nx.y == run.y + 1;
 }
-__device__ __forceinline__ void run_ahead_point(const DevPlan& P, RunAhead& q) {
-  if (q.s >= 0) q.pe = P.pts[q.s];
-}
-__device__ __forceinline__ void run_ahead_sample(const float2* __restrict__ Yb, RunAhead& q) {
-  if (q.s >= 0) q.v = Yb[q.pe.p];
+__device__ __forceinline__ void run_ahead_point(const DevPlan& P, const float2* __restrict__ Yb, RunAhead& q) {
+  if (q.s >= 0) {
+    q.pe = P.pts[q.s];
+    q.v = Yb[q.s];
+  }
 }
 
 // Transposed bilinear weights of the points with stencil column i0 = c, added
@@ -741,10 +744,16 @@ __device__ __forceinline__ void run_ahead_sample(const float2* __restrict__ Yb, 
 // The conj(phase) of the column transform is applied once per cell.  `qa[i]`,
 // i < NA, hold this thread's runs of the column's first NA batches (run
 // runoff[c] + tid + i * NT), loaded ahead (RunAhead).
-template <int L, int NA = 1>
+// Buffer slot of column bin q in the four-step column layout (padded, permuted).
+template <int L>
+struct ColSlot {
+  __device__ __forceinline__ int operator()(int q) const { return xpad<L>(colpos<L>(q)); }
+};
+
+template <int L, int NA = 1, class Slot = ColSlot<L>>
 __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* __restrict__ Yb, int c, float2* left,
                                                float2* right, int tid, int NT, const RunAhead* qa,
-                                               const float2* smph) {
+                                               const float2* smph, Slot slot = Slot{}) {
   const unsigned full = 0xffffffffu;
   const int lane = tid & 31;
   const int r0 = P.runoff[c], r1 = P.runoff[c + 1];
@@ -773,10 +782,7 @@ __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* _
         has_prev = q.prev;
         has_next = q.next;
         add(q.pe, q.v);
-        for (int i = s + 1; i < e; ++i) {
-          const PolarEntry pe = P.pts[i];
-          add(pe, Yb[pe.p]);
-        }
+        for (int i = s + 1; i < e; ++i) add(P.pts[i], Yb[i]);
       } else {
         const int2 run = P.runs[r], nx = P.runs[r + 1];
         k = run.y;
@@ -784,10 +790,7 @@ __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* _
         e = nx.x;
         has_prev = P.runs[r - 1].y == k - 1;  // r > r0 here
         has_next = r + 1 < r1 && nx.y == k + 1;
-        for (int i = s; i < e; ++i) {
-          const PolarEntry pe = P.pts[i];
-          add(pe, Yb[pe.p]);
-        }
+        for (int i = s; i < e; ++i) add(P.pts[i], Yb[i]);
       }
     }
     // row-k parts of the run with key k-1: from the lane before, or (lane 0) summed again
@@ -802,13 +805,13 @@ __device__ __forceinline__ void scatter_column(const DevPlan& P, const float2* _
       prb = plb;
       for (int i = P.runs[r - 1].x; i < s; ++i) {
         const PolarEntry pe = P.pts[i];
-        const float2 v = Yb[pe.p];
+        const float2 v = Yb[i];
         acc_rn(plb, w_l1(pe), v);
         acc_rn(prb, w_r1(pe), v);
       }
     }
     const int ra_row = wrapN(k, P.N), rb_row = wrapN(k + 1, P.N);
-    const int qa = xpad<L>(colpos<L>(ra_row)), qb = xpad<L>(colpos<L>(rb_row));
+    const int qa = slot(ra_row), qb = slot(rb_row);
     const float2 pa = phase_at(smph, P, ra_row);
     if (has_prev) {
       la = cadd_rn(la, plb);
@@ -848,13 +851,11 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
     float2* first = slot(c0);
     run_ahead_record(P, c0 - 1, tid, ahead);
     for (int q = tid; q < SL; q += NT) first[q] = make_float2(0.f, 0.f);
-    run_ahead_point(P, ahead);
-    run_ahead_sample(Yb, ahead);
+    run_ahead_point(P, Yb, ahead);
     __syncthreads();
     if (c0 >= 1) scatter_column<L>(P, Yb, c0 - 1, nullptr, first, tid, NT, &ahead, smph);  // right side of the previous column
     run_ahead_record(P, c0, tid, ahead);
-    run_ahead_point(P, ahead);
-    run_ahead_sample(Yb, ahead);
+    run_ahead_point(P, Yb, ahead);
   }
 #pragma unroll 1
   for (int c = c0; c < c1; ++c) {
@@ -864,7 +865,7 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
       for (int q = tid; q < SL; q += NT) nxt[q] = make_float2(0.f, 0.f);
     __syncthreads();
     if (c <= P.ncol - 2) scatter_column<L>(P, Yb, c, cur, nxt, tid, NT, &ahead, smph);
-    // the next column's first runs: record now, point before the transform, sample half-way
+    // the next column's first runs: record now, point and sample before the transform
     run_ahead_record(P, c + 1 < c1 ? c + 1 : -1, tid, ahead);
     __syncthreads();
     if (c == 0) {
@@ -885,8 +886,8 @@ __global__ void TAT_COLS_BOUNDS_A k_cols_adj(DevPlan P, const float2* __restrict
       __syncthreads();
     }
     // inverse column DFT (conj(phase) already applied by the scatter), first n rows only
-    run_ahead_point(P, ahead);
-    col_fft_inv<L>(cur, P.fN, smtw, tid, NT, nt, P.n, nullptr, [&]() { run_ahead_sample(Yb, ahead); });
+    run_ahead_point(P, Yb, ahead);
+    col_fft_inv<L>(cur, P.fN, smtw, tid, NT, nt, P.n, nullptr);
     float2* col = Xb + (size_t)c * P.n;  // R'[c][0..n): contiguous
     for (int iy = tid; iy < P.n; iy += NT) col[iy] = cur[xpad<L>(iy)];
     __syncthreads();

@@ -621,6 +621,11 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
     }
     runoff[d.ncol] = (int)runs.size();
     runs.push_back(make_int2(npts, 0));
+    std::vector<int> pinv((size_t)d.n_rings * d.nh, -1);
+    for (int e = 0; e < npts; ++e) pinv[sorted[e].p] = e;
+    for (size_t p = d.nh; p < pinv.size(); ++p)
+      if (pinv[p] < 0) return TAT_ERR_INTERNAL;  // every sample of rings >= 1 has exactly one point
+    TAT_TRY(upload(P, pinv, &d.pinv));
     TAT_TRY(upload(P, sorted, &d.pts));
     TAT_TRY(upload(P, off, &d.coloff));
     TAT_TRY(upload(P, runs, &d.runs));
@@ -640,6 +645,7 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
   c.rows_pairs = d.N == 8192 ? 1 : std::max(1, std::min(4, 1024 / c.nt_rows));
   c.strip = 8;
   c.cols_threads = std::max(c.nt_N, 256);
+  c.cols_split = (d.N == 4096 && n <= 512) ? 1 : 0;
   c.pdl = d.N <= 2048;  // measured: +13 % pairs/s at N = 1024, B = 8; -2 % at N = 4096, B = 32
   c.rings_per_cta = rings_per_cta_for(n_phi);
   c.t_tile = time_tile_for(n_det);

@@ -68,6 +68,9 @@ struct DevPlan {
   const int2* runs;                // [n_runs+1] {first point, k0} of each run of equal k0 within a column,
                                    // column by column; run r ends at runs[r+1].x (a sentinel closes the table)
   const int* runoff;               // [ncol+1] runs of column c: [runoff[c], runoff[c+1])
+  const int* pinv;                 // [n_rings x nh] index in pts of polar slot p (-1 for ring 0, which
+                                   // has no point): A*'s angular stage writes its polar samples in the
+                                   // order of pts, so the scatter reads them contiguously
   const float* Bt;                 // [(K+1) x (J+1)] dlam*lam_j*J_k(lam_j)/n_phi
   const float* Btt;                // Bt by ring tile: [tile][k][g], ring 1 + tile*rpc + g, g < rpc
                                    // (rpc = rings_per_cta_for(n_phi)); each tile padded to bt_bs floats
@@ -113,6 +116,8 @@ struct LaunchCfg {
   int cols_threads;   // threads per CTA of the column pass (>= nt_N; fewer than 256 only for four-step lengths)
   int pdl;            // 1: stages launched with programmatic dependent launch (outside graph capture)
   int order_2M;       // pass order of the length-2M FFT of the cosine/sine stages (Sched V: 0 or 1)
+  int cols_split;     // 1: at N = 4096 (n <= 512) the column stages split each column transform over
+                      // the eight warps of a 256-thread CTA (colsplit.cuh); 0: the four-step transform
 };
 
 }  // namespace tat

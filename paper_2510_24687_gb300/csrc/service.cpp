@@ -670,6 +670,23 @@ tat_status tat_plan_get_fft_order(tat_plan_t plan, int* order) {
   return TAT_OK;
 }
 
+tat_status tat_plan_set_column_split(tat_plan_t plan, int on) {
+  if (!plan || (on != 0 && on != 1)) return TAT_ERR_INVALID_ARG;
+  const int old = plan->cfg.cols_split;
+  plan->cfg.cols_split = on;
+  if (tat::validate_shapes(plan) != TAT_OK) {
+    plan->cfg.cols_split = old;
+    return TAT_ERR_UNSUPPORTED;
+  }
+  return TAT_OK;
+}
+
+tat_status tat_plan_get_column_split(tat_plan_t plan, int* on) {
+  if (!plan || !on) return TAT_ERR_INVALID_ARG;
+  *on = plan->cfg.cols_split;
+  return TAT_OK;
+}
+
 tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, float* f_out, void* workspace,
                              tat_stream_t stream, double* ms_best, int* strip_out, int* rp_out, int* cols_threads_out,
                              int* row_threads_out) {
@@ -746,6 +763,19 @@ tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, flo
     plan->cfg = best;
     apply_order_2M(plan, 1 - best.order_2M);
     trial();
+  }
+  // and the other column transform where both exist (N = 4096, n <= 512), with the best
+  // strip among its neighbours
+  if (err == TAT_OK && plan->d.N == 4096 && plan->d.n <= 512) {
+    const tat::LaunchCfg third = best;
+    for (int strip : {third.strip / 2, third.strip, third.strip * 2}) {
+      if (err != TAT_OK || strip < 2 || strip > 32) continue;
+      plan->cfg = third;
+      apply_order_2M(plan, third.order_2M);
+      plan->cfg.cols_split = 1 - third.cols_split;
+      plan->cfg.strip = strip;
+      trial();
+    }
   }
   plan->cfg = err == TAT_OK ? best : base;
   apply_order_2M(plan, plan->cfg.order_2M);

@@ -65,6 +65,8 @@ def test_null_handles_are_rejected(pkg):
     assert lib.tat_plan_set_launch_shape(None, 8, 1, 256, 0) == 1
     assert lib.tat_plan_set_fft_order(None, 0) == 1
     assert lib.tat_plan_get_fft_order(None, None) == 1
+    assert lib.tat_plan_set_column_split(None, 1) == 1
+    assert lib.tat_plan_get_column_split(None, None) == 1
 
 
 def test_plan_create_without_device_fails_cleanly(pkg):

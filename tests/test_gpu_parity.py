@@ -54,6 +54,12 @@ CASES = {
     # and pruned to two terms (440 <= 512 rows)
     "n553_N8192": dict(n=553, n_det=128, n_t=128, support_radius=0.9, T=6.0),
     "n440_N8192_pruned": dict(n=440, n_det=128, n_t=128, support_radius=0.9, T=8.0),
+    # N = 4096: the column stages on the warp-split transform (n <= 512 rows; 220 rows leave
+    # the upper half of every warp's inputs zero) and, with 586 rows (a smaller padding), on
+    # the four-step one
+    "n500_N4096_split": dict(n=500, n_det=128, n_t=128, support_radius=0.9),
+    "n220_N4096_split": dict(n=220, n_det=128, n_t=128, support_radius=0.9, T=8.0),
+    "n586_N4096_fourstep": dict(n=586, n_det=128, n_t=128, support_radius=0.9, pad_L=7.0),
 }
 
 _ORACLE_KEYS = {"low_mode_quadrature": "low_mode"}
@@ -87,6 +93,36 @@ def test_adjoint_parity(pkg, torch, name):
     ref = O.adjoint(P, gin)
     assert f.shape == (P.n, P.n)
     assert rel(f, ref) <= TOL
+
+
+@pytest.mark.parametrize("name", ["n500_N4096_split", "n220_N4096_split"])
+def test_column_split_variants(pkg, torch, name):
+    """At N = 4096 with at most 512 rows the column stages run on the warp-split transform
+    (the default) or on the four-step one: both against the oracle and each other, batch 3,
+    and the split A* the same bits on repeated calls and for other column strips."""
+    op, P = make(pkg, torch, CASES[name])
+    assert op.info["N"] == 4096
+    assert pkg.tat_plan_get_column_split(op.plan) == 1
+    B = 3
+    fs = np.stack([f32(ellipse_phantom(P.n, 70 + s)) for s in range(B)])
+    gs = np.stack([f32(random_sinogram(P.n_det, P.n_t, 80 + s)) for s in range(B)])
+    ft = torch.tensor(fs, dtype=torch.float32, device="cuda:0")
+    gt = torch.tensor(gs, dtype=torch.float32, device="cuda:0")
+    g_split, fa_split = op.forward(ft).cpu().numpy(), op.adjoint(gt).cpu().numpy()
+    assert np.array_equal(op.adjoint(gt).cpu().numpy(), fa_split)
+    pkg.tat_plan_set_launch_shape(op.plan, 3, 2, 256, 0)       # strips of 3 columns
+    assert np.array_equal(op.adjoint(gt).cpu().numpy(), fa_split)
+    assert np.array_equal(op.forward(ft).cpu().numpy(), g_split)
+    pkg.tat_plan_set_column_split(op.plan, 0)
+    assert pkg.tat_plan_get_column_split(op.plan) == 0
+    g_four, fa_four = op.forward(ft).cpu().numpy(), op.adjoint(gt).cpu().numpy()
+    for s in (0, B - 1):
+        assert rel(g_split[s], O.forward(P, fs[s])) <= TOL
+        assert rel(fa_split[s], O.adjoint(P, gs[s])) <= TOL
+        assert rel(g_four[s], g_split[s].astype(np.float64)) <= 1e-6
+        assert rel(fa_four[s], fa_split[s].astype(np.float64)) <= 1e-6
+    with pytest.raises(pkg.TatError):
+        pkg.tat_plan_set_column_split(op.plan, 2)
 
 
 def test_plan_matches_oracle_grid(pkg, torch):
