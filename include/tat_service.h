@@ -109,8 +109,8 @@ tat_status tat_service_get_stats(tat_service_t svc, tat_service_stats* stats);
  * row groups of 64 and 128 threads (instead of 256; lengths N <= 1024) with 1, 2
  * and 4 times its row pairs, the best shape with and without programmatic
  * dependent launch of the stages, the other pass order of the length-2M FFT of
- * the cosine and sine stages (tat_plan_set_fft_order) and the other column transform
- * at N = 4096 (tat_plan_set_column_split) -- on
+ * the cosine and sine stages (tat_plan_set_fft_order) and the other column transforms
+ * (tat_plan_set_column_split, where the split one applies) -- on
  * one A then one A* of `batch` images at f (device, batch*n*n floats, output
  * of A* written to f_out) with g (batch*n_det*n_t floats) and the workspace
  * for `batch`, and keeps the fastest for every later call on this plan.  The
@@ -141,15 +141,18 @@ tat_status tat_plan_set_fft_order(tat_plan_t plan, int order);
 tat_status tat_plan_get_fft_order(tat_plan_t plan, int* order);
 
 /* Column transform of the column stages of A and A* (Algorithm 1 step 2 and its transpose)
- * at N = 4096 with n <= 512: 1 splits each length-4096 column DFT into eight 512-point
- * DFTs, one per warp of a 256-thread CTA (the column's rows are zero from n on, so bin
- * q = k1 + 8 k2 takes only the 512-point DFT k2 of the rows twiddled by w_N^(m k1));
- * 0 runs the four-step transform in CTA-wide passes.  The plan's default is 1 wherever it
- * applies; tat_plan_autotune tries both.  The results agree to rounding (each variant is
- * deterministic bit for bit on its own).  Elsewhere the setting is kept and has no effect.
- * TAT_ERR_INVALID_ARG for a value other than 0 or 1. */
-tat_status tat_plan_set_column_split(tat_plan_t plan, int on);
-tat_status tat_plan_get_column_split(tat_plan_t plan, int* on);
+ * at N = 512 RB (RB = 1, 2, 4, 8, 16) with n <= 512 (n <= 1024 at N = 8192).  The split
+ * transform divides each length-N column DFT into RB 512-point DFTs, one per warp of a CTA
+ * of RB warps (the column's rows are zero from n on, so bin q = k1 + RB k2 takes only the
+ * 512-point DFT k2 of the rows twiddled by w_N^(m k1), at N = 8192 with the rows m + 512
+ * folded onto m); the other runs the four-step transform in CTA-wide passes.  `mask` bit 0
+ * selects the split transform for the forward's column stage, bit 1 for the adjoint's
+ * (0 .. 3).  Plan defaults: 3 at N = 1024 .. 4096, 1 at N = 512, 2 at N = 8192, 0 where the
+ * split transform does not apply (there the setting is kept and has no effect);
+ * tat_plan_autotune tries the other values.  The transforms agree to rounding (each is
+ * deterministic bit for bit on its own).  TAT_ERR_INVALID_ARG outside 0 .. 3. */
+tat_status tat_plan_set_column_split(tat_plan_t plan, int mask);
+tat_status tat_plan_get_column_split(tat_plan_t plan, int* mask);
 
 #ifdef __cplusplus
 }

@@ -322,9 +322,10 @@ def tat_plan_get_fft_order(plan):
     return o.value
 
 
-def tat_plan_set_column_split(plan, on):
-    """Column transform at N = 4096 (n <= 512): 1 eight warp-level 512-point DFTs, 0 four-step."""
-    _check(load().tat_plan_set_column_split(plan, int(on)), "tat_plan_set_column_split")
+def tat_plan_set_column_split(plan, mask):
+    """Column transforms at N = 512 RB: bit 0 (forward) / bit 1 (adjoint) set: RB warp-level
+    512-point DFTs; clear: the four-step transform."""
+    _check(load().tat_plan_set_column_split(plan, int(mask)), "tat_plan_set_column_split")
 
 
 def tat_plan_get_column_split(plan):

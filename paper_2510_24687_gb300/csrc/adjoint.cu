@@ -44,9 +44,9 @@ tat_status launch_adjoint(const tat_plan_s* Pl, int batch, const float* g, long 
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_cols_adj<L>>(dev) && ensure_smem<k_rows_adj<L>>(dev);
     if constexpr (split_length(L)) {
-      if (s.cols_split) {
+      if (s.cols_split_a) {
         ok &= ensure_smem<k_cols_adj_split<L>>(dev);
-        ok &= pdl_launch(c.pdl != 0, k_cols_adj_split<L>, s.cols_grid_a, s.cols_block, s.cols_smem_a, st, P, Y, ys, X, xs, c.strip, batch) == cudaSuccess;
+        ok &= pdl_launch(c.pdl != 0, k_cols_adj_split<L>, s.cols_grid_a, s.cols_block_split, s.cols_smem_a, st, P, Y, ys, X, xs, c.strip, batch) == cudaSuccess;
       } else {
         ok &= pdl_launch(c.pdl != 0, k_cols_adj<L>, s.cols_grid_a, s.cols_block, s.cols_smem_a, st, P, Y, ys, X, xs, c.strip, c.nt_N, batch) == cudaSuccess;
       }

@@ -51,9 +51,9 @@ tat_status launch_forward(const tat_plan_s* Pl, int batch, const float* f, long 
     ok &= pdl_launch(c.pdl != 0, k_rows_fwd<L>, s.rows_grid, s.rows_block, s.rows_smem, st, P, f, fs, X, xs, c.rows_pairs, c.nt_rows) == cudaSuccess;
     stage_done();
     if constexpr (split_length(L)) {
-      if (s.cols_split) {
+      if (s.cols_split_f) {
         ok &= ensure_smem<k_cols_fwd_split<L>>(dev);
-        ok &= pdl_launch(c.pdl != 0, k_cols_fwd_split<L>, s.cols_grid_f, s.cols_block, s.cols_smem_f, st, P, X, xs, Y, ys, c.strip, batch) == cudaSuccess;
+        ok &= pdl_launch(c.pdl != 0, k_cols_fwd_split<L>, s.cols_grid_f, s.cols_block_split, s.cols_smem_f, st, P, X, xs, Y, ys, c.strip, batch) == cudaSuccess;
       } else {
         ok &= pdl_launch(c.pdl != 0, k_cols_fwd<L>, s.cols_grid_f, s.cols_block, s.cols_smem_f, st, P, X, xs, Y, ys, c.strip, c.nt_N, batch) == cudaSuccess;
       }

@@ -18,7 +18,8 @@ struct Shapes {
   int rows_block, cols_block, cols_block_i, rings_block, modes_block, theta_block;
   size_t rows_smem, cols_smem_f, cols_smem_a, cols_smem_i, rings_smem, modes_smem, theta_smem;
   int ntiles;
-  bool cols_split;  // the N = 4096 column stages on the warp-split transform
+  bool cols_split_f, cols_split_a;  // the forward / adjoint column stage on the warp-split transform
+  int cols_block_split;              // CTA size of the split column kernels: one warp per 512 points
 };
 
 inline Shapes shapes(const tat_plan_s* Pl, int batch) {
@@ -39,11 +40,12 @@ inline Shapes shapes(const tat_plan_s* Pl, int batch) {
   s.cols_smem_f = (2 * (size_t)xpad_len(P.N) + kFourStepTw + P.ph_lo + 64) * sizeof(float2);
   s.cols_smem_a = (2 * (size_t)xpad_len(P.N) + kFourStepTw + P.ph_lo + 64) * sizeof(float2);
   s.cols_smem_i = ((size_t)xpad_len(P.N) + kFourStepTw) * sizeof(float2);
-  s.cols_split = c.cols_split != 0 && split_length(P.N) && P.n <= 512;
-  if (s.cols_split) {
-    s.cols_block = 256;  // eight warps, one 512-point transform each
-    s.cols_smem_f = s.cols_smem_a = split_cols_smem(P.ph_lo + 64);
-  }
+  const bool split_ok = split_length(P.N) && P.n <= split_max_rows(P.N);
+  s.cols_split_f = split_ok && (c.cols_split & 1);
+  s.cols_split_a = split_ok && (c.cols_split & 2);
+  s.cols_block_split = 32 * (P.N / 512);
+  if (s.cols_split_f) s.cols_smem_f = split_cols_smem(P.N, P.ph_lo + 64);
+  if (s.cols_split_a) s.cols_smem_a = split_cols_smem(P.N, P.ph_lo + 64);
   s.ntiles = (P.J + c.rings_per_cta - 1) / c.rings_per_cta;
   s.rings_grid = dim3(s.ntiles + P.n_low, batch);
   s.rings_block = c.rings_per_cta * c.nt_phi;

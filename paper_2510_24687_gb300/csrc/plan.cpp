@@ -645,7 +645,12 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
   c.rows_pairs = d.N == 8192 ? 1 : std::max(1, std::min(4, 1024 / c.nt_rows));
   c.strip = 8;
   c.cols_threads = std::max(c.nt_N, 256);
-  c.cols_split = (d.N == 4096 && n <= 512) ? 1 : 0;
+  // measured at the benchmark sizes: both stages gain at N = 1024 .. 4096; at N = 512 only the
+  // forward, at N = 8192 only the adjoint (the autotuner tries every combination)
+  if ((d.N == 512 || d.N == 1024 || d.N == 2048 || d.N == 4096 || d.N == 8192) && n <= (d.N == 8192 ? 1024 : 512))
+    c.cols_split = d.N == 512 ? 1 : d.N == 8192 ? 2 : 3;
+  else
+    c.cols_split = 0;
   c.pdl = d.N <= 2048;  // measured: +13 % pairs/s at N = 1024, B = 8; -2 % at N = 4096, B = 32
   c.rings_per_cta = rings_per_cta_for(n_phi);
   c.t_tile = time_tile_for(n_det);

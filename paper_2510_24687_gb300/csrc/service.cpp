@@ -670,10 +670,10 @@ tat_status tat_plan_get_fft_order(tat_plan_t plan, int* order) {
   return TAT_OK;
 }
 
-tat_status tat_plan_set_column_split(tat_plan_t plan, int on) {
-  if (!plan || (on != 0 && on != 1)) return TAT_ERR_INVALID_ARG;
+tat_status tat_plan_set_column_split(tat_plan_t plan, int mask) {
+  if (!plan || mask < 0 || mask > 3) return TAT_ERR_INVALID_ARG;
   const int old = plan->cfg.cols_split;
-  plan->cfg.cols_split = on;
+  plan->cfg.cols_split = mask;
   if (tat::validate_shapes(plan) != TAT_OK) {
     plan->cfg.cols_split = old;
     return TAT_ERR_UNSUPPORTED;
@@ -681,9 +681,9 @@ tat_status tat_plan_set_column_split(tat_plan_t plan, int on) {
   return TAT_OK;
 }
 
-tat_status tat_plan_get_column_split(tat_plan_t plan, int* on) {
-  if (!plan || !on) return TAT_ERR_INVALID_ARG;
-  *on = plan->cfg.cols_split;
+tat_status tat_plan_get_column_split(tat_plan_t plan, int* mask) {
+  if (!plan || !mask) return TAT_ERR_INVALID_ARG;
+  *mask = plan->cfg.cols_split;
   return TAT_OK;
 }
 
@@ -764,18 +764,22 @@ tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, flo
     apply_order_2M(plan, 1 - best.order_2M);
     trial();
   }
-  // and the other column transform where both exist (N = 4096, n <= 512), with the best
-  // strip among its neighbours
-  if (err == TAT_OK && plan->d.N == 4096 && plan->d.n <= 512) {
+  // and the other column transform where both exist (N = 512 .. 8192 with few enough rows),
+  // with the best strip among its neighbours
+  const int N = plan->d.N;
+  const bool split_ok = (N == 512 || N == 1024 || N == 2048 || N == 4096 || N == 8192) &&
+                        plan->d.n <= (N == 8192 ? 1024 : 512);
+  if (err == TAT_OK && split_ok) {
     const tat::LaunchCfg third = best;
-    for (int strip : {third.strip / 2, third.strip, third.strip * 2}) {
-      if (err != TAT_OK || strip < 2 || strip > 32) continue;
-      plan->cfg = third;
-      apply_order_2M(plan, third.order_2M);
-      plan->cfg.cols_split = 1 - third.cols_split;
-      plan->cfg.strip = strip;
-      trial();
-    }
+    for (int split = 0; split < 4; ++split)
+      for (int strip : {third.strip / 2, third.strip, third.strip * 2}) {
+        if (err != TAT_OK || split == third.cols_split || strip < 2 || strip > 32) continue;
+        plan->cfg = third;
+        apply_order_2M(plan, third.order_2M);
+        plan->cfg.cols_split = split;
+        plan->cfg.strip = strip;
+        trial();
+      }
   }
   plan->cfg = err == TAT_OK ? best : base;
   apply_order_2M(plan, plan->cfg.order_2M);

@@ -57,6 +57,8 @@ CASES = {
     # N = 4096: the column stages on the warp-split transform (n <= 512 rows; 220 rows leave
     # the upper half of every warp's inputs zero) and, with 586 rows (a smaller padding), on
     # the four-step one
+    "n128_N1024": dict(n=128, n_det=128, n_t=128, support_radius=0.9),
+    "n255_N2048": dict(n=255, n_det=128, n_t=128, support_radius=0.9),
     "n500_N4096_split": dict(n=500, n_det=128, n_t=128, support_radius=0.9),
     "n220_N4096_split": dict(n=220, n_det=128, n_t=128, support_radius=0.9, T=8.0),
     "n586_N4096_fourstep": dict(n=586, n_det=128, n_t=128, support_radius=0.9, pad_L=7.0),
@@ -95,34 +97,44 @@ def test_adjoint_parity(pkg, torch, name):
     assert rel(f, ref) <= TOL
 
 
-@pytest.mark.parametrize("name", ["n500_N4096_split", "n220_N4096_split"])
+@pytest.mark.parametrize("name", ["n64", "n128_N1024", "n255_N2048", "n500_N4096_split", "n220_N4096_split",
+                                  "n553_N8192", "n440_N8192_pruned"])
 def test_column_split_variants(pkg, torch, name):
-    """At N = 4096 with at most 512 rows the column stages run on the warp-split transform
-    (the default) or on the four-step one: both against the oracle and each other, batch 3,
-    and the split A* the same bits on repeated calls and for other column strips."""
+    """At N = 512 RB (RB = 1 .. 16) with at most 512 rows (1024 at N = 8192) either column
+    stage runs on the warp-split transform or on the four-step one (a bit each in the
+    plan's mask): both against the oracle and each other, batch 3; each stage's result
+    depends only on its own bit, bit for bit; the split A* the same bits on repeated calls
+    and for other column strips."""
     op, P = make(pkg, torch, CASES[name])
-    assert op.info["N"] == 4096
-    assert pkg.tat_plan_get_column_split(op.plan) == 1
+    N = op.info["N"]
+    assert pkg.tat_plan_get_column_split(op.plan) == {512: 1, 8192: 2}.get(N, 3)
     B = 3
     fs = np.stack([f32(ellipse_phantom(P.n, 70 + s)) for s in range(B)])
     gs = np.stack([f32(random_sinogram(P.n_det, P.n_t, 80 + s)) for s in range(B)])
     ft = torch.tensor(fs, dtype=torch.float32, device="cuda:0")
     gt = torch.tensor(gs, dtype=torch.float32, device="cuda:0")
-    g_split, fa_split = op.forward(ft).cpu().numpy(), op.adjoint(gt).cpu().numpy()
+    out = {}
+    for mask in (3, 0, 1, 2):
+        pkg.tat_plan_set_column_split(op.plan, mask)
+        assert pkg.tat_plan_get_column_split(op.plan) == mask
+        out[mask] = (op.forward(ft).cpu().numpy(), op.adjoint(gt).cpu().numpy())
+    g_split, fa_split = out[3]
+    g_four, fa_four = out[0]
+    assert np.array_equal(out[1][0], g_split) and np.array_equal(out[1][1], fa_four)
+    assert np.array_equal(out[2][0], g_four) and np.array_equal(out[2][1], fa_split)
+    pkg.tat_plan_set_column_split(op.plan, 3)
     assert np.array_equal(op.adjoint(gt).cpu().numpy(), fa_split)
-    pkg.tat_plan_set_launch_shape(op.plan, 3, 2, 256, 0)       # strips of 3 columns
+    big = N == 8192                                             # one row pair, 512-thread CTAs there
+    pkg.tat_plan_set_launch_shape(op.plan, 3, 1 if big else 2, 512 if big else 256, 0)   # strips of 3 columns
     assert np.array_equal(op.adjoint(gt).cpu().numpy(), fa_split)
     assert np.array_equal(op.forward(ft).cpu().numpy(), g_split)
-    pkg.tat_plan_set_column_split(op.plan, 0)
-    assert pkg.tat_plan_get_column_split(op.plan) == 0
-    g_four, fa_four = op.forward(ft).cpu().numpy(), op.adjoint(gt).cpu().numpy()
     for s in (0, B - 1):
         assert rel(g_split[s], O.forward(P, fs[s])) <= TOL
         assert rel(fa_split[s], O.adjoint(P, gs[s])) <= TOL
         assert rel(g_four[s], g_split[s].astype(np.float64)) <= 1e-6
         assert rel(fa_four[s], fa_split[s].astype(np.float64)) <= 1e-6
     with pytest.raises(pkg.TatError):
-        pkg.tat_plan_set_column_split(op.plan, 2)
+        pkg.tat_plan_set_column_split(op.plan, 4)
 
 
 def test_plan_matches_oracle_grid(pkg, torch):
@@ -250,6 +262,7 @@ def test_small_column_ctas(pkg, torch, n, cols_threads, strip, row_threads, row_
     FFTs of N = 8n on fewer threads than 256) against the oracle, batch 3, and the forward
     bit-identical to the default shape."""
     op, P = make(pkg, torch, dict(n=n, n_det=2 * n, n_t=2 * n, support_radius=0.9))
+    pkg.tat_plan_set_column_split(op.plan, 0)   # the four-step column transform, whose CTA size varies
     B = 3
     fs = np.stack([f32(ellipse_phantom(n, 40 + s)) for s in range(B)])
     ft = torch.tensor(fs, dtype=torch.float32, device="cuda:0")

@@ -198,11 +198,13 @@ def test_autotune_keeps_results(pkg, torch):
     assert rt in (64, 128, 256)
     order = pkg.tat_plan_get_fft_order(op.plan)
     assert order in (0, 1)
+    split = pkg.tat_plan_get_column_split(op.plan)
+    assert split in (0, 1, 2, 3)
     g1 = op.forward(f).cpu().numpy()
-    if order == 0:
+    if order == 0 and split & 1:
         assert np.array_equal(g1, g0)     # launch shapes only regroup work
     else:
-        assert rel(g1, g0) <= 1e-6        # the other FFT pass order rounds differently
+        assert rel(g1, g0) <= 1e-6        # another FFT pass order or column transform rounds differently
     assert rel(op.adjoint(op.forward(f)).cpu().numpy(), a0) <= 1e-6
     # at a fixed pass order A* does not depend on the launch shapes, bit for bit
     gfix = torch.tensor(g0, device="cuda:0")
