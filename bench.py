@@ -248,15 +248,30 @@ def alu_peak():
     return _ALU_PEAK
 
 
-def alu_roofline(stage_ms, flops, workload):
+def kernel_names(pkg, op):
+    """The kernel of each stage under the plan's column-transform mask (bit 0: A's column
+    stage on the warp-split transform, bit 1: A*'s), where that transform applies."""
+    names = dict(KERNEL_NAMES)
+    N, n = op.info["N"], op.n
+    if N in (512, 1024, 2048, 4096, 8192) and n <= (1024 if N == 8192 else 512):
+        mask = pkg.tat_plan_get_column_split(op.plan)
+        if mask & 1:
+            names["cols_fwd"] = "k_cols_fwd_split"
+        if mask & 2:
+            names["cols_adj"] = "k_cols_adj_split"
+    return names
+
+
+def alu_roofline(stage_ms, flops, workload, names=None):
     """FP32-ALU roofline of the dominant stage (the stages are FFT/shared-memory kernels, not HBM-bound)."""
+    names = names or KERNEL_NAMES
     dom = max(stage_ms, key=stage_ms.get)
     peak_alu, peak_src = alu_peak()
     achieved = flops[dom] / (stage_ms[dom] / 1e3) / 1e12
-    return {"bound": "alu", "kernel": KERNEL_NAMES[dom], "achieved": achieved, "peak": peak_alu,
-            "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": traffic_for(KERNEL_NAMES[dom], workload),
+    return {"bound": "alu", "kernel": names[dom], "achieved": achieved, "peak": peak_alu,
+            "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": traffic_for(names[dom], workload),
             # the unit that bounds these kernels: L1/shared-memory throughput in % of its peak (ncu)
-            "l1tex_throughput_pct": traffic_for(KERNEL_NAMES[dom], workload, key="l1tex_throughput_pct"),
+            "l1tex_throughput_pct": traffic_for(names[dom], workload, key="l1tex_throughput_pct"),
             "peak_source": peak_src,
             "flops_per_launch": flops[dom],
             "flop_count": "pruned transforms: see stage_flops",
@@ -697,7 +712,7 @@ def main():
 
     # ---- per-stage timing (same work, events between the five stages of each direction)
     stage_ms = stage_times(pkg, op, B, f, g, f2, ws, stream, max(3, min(args.steps, 10)))
-    roofline = alu_roofline(stage_ms, stage_flops(info, B), f"pair_n{N_IMG}_b{B}")
+    roofline = alu_roofline(stage_ms, stage_flops(info, B), f"pair_n{N_IMG}_b{B}", kernel_names(pkg, op))
     peaks = measured_peaks()
     hbm_peak = peaks["hbm_gbs"] if peaks else 6800.0
     pair_bytes = 2 * (4 * N_IMG * N_IMG + 4 * N_DET * N_T)
@@ -994,7 +1009,7 @@ def service_roofline(pkg, sizes, stream, dev):
     x2 = torch.empty_like(x)
     stage_times(pkg, op, B, x, y, x2, ws, stream, 2)
     ms = stage_times(pkg, op, B, x, y, x2, ws, stream, 5)
-    r = alu_roofline(ms, stage_flops(op.info, B, n, 2 * n, 2 * n), f"service_n{n}_b{B}")
+    r = alu_roofline(ms, stage_flops(op.info, B, n, 2 * n, 2 * n), f"service_n{n}_b{B}", kernel_names(pkg, op))
     r["group"] = f"{B} requests of n={n} (n_det=n_t={2 * n}) in one batched A and A*"
     return r
 
@@ -1750,7 +1765,8 @@ def run_solves(args, rank, world, local):
              "peak_source": "measured" if peaks else "fallback", "ms": ms_primal,
              "note": "fused element-wise step; algorithmic bytes = f, A*q, p (2 planes), mask, f_out, fbar per pixel"}
     stage_ms = stage_times(pkg, op, B, xbuf, ybuf, x_tmp2, ws, stream, 5)
-    roofline = alu_roofline(stage_ms, stage_flops(op.info, B, SOLVE_N, SOLVE_DET, SOLVE_T), "solves_n256_b16")
+    roofline = alu_roofline(stage_ms, stage_flops(op.info, B, SOLVE_N, SOLVE_DET, SOLVE_T), "solves_n256_b16",
+                            kernel_names(pkg, op))
 
     # end to end: sinograms from pinned host memory, reconstructions back to pinned memory
     g_pin = torch.from_numpy(gh).pin_memory()

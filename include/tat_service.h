@@ -146,11 +146,12 @@ tat_status tat_plan_get_fft_order(tat_plan_t plan, int* order);
  * of RB warps (the column's rows are zero from n on, so bin q = k1 + RB k2 takes only the
  * 512-point DFT k2 of the rows twiddled by w_N^(m k1), at N = 8192 with the rows m + 512
  * folded onto m); the other runs the four-step transform in CTA-wide passes.  `mask` bit 0
- * selects the split transform for the forward's column stage, bit 1 for the adjoint's
- * (0 .. 3).  Plan defaults: 3 at N = 1024 .. 4096, 1 at N = 512, 2 at N = 8192, 0 where the
- * split transform does not apply (there the setting is kept and has no effect);
- * tat_plan_autotune tries the other values.  The transforms agree to rounding (each is
- * deterministic bit for bit on its own).  TAT_ERR_INVALID_ARG outside 0 .. 3. */
+ * selects the split transform for the column stage of A, bit 1 for that of A* (0 .. 3;
+ * A^-1's column stage keeps the four-step transform).  Plan defaults: 3 at
+ * N = 1024 .. 4096, 1 at N = 512, 2 at N = 8192, 0 where the split transform does not
+ * apply (there the setting is kept and has no effect); tat_plan_autotune tries the other
+ * values.  The transforms agree to rounding (each is deterministic bit for bit on its
+ * own).  TAT_ERR_INVALID_ARG outside 0 .. 3. */
 tat_status tat_plan_set_column_split(tat_plan_t plan, int mask);
 tat_status tat_plan_get_column_split(tat_plan_t plan, int* mask);
 

@@ -116,7 +116,7 @@ struct LaunchCfg {
   int cols_threads;   // threads per CTA of the column pass (>= nt_N; fewer than 256 only for four-step lengths)
   int pdl;            // 1: stages launched with programmatic dependent launch (outside graph capture)
   int order_2M;       // pass order of the length-2M FFT of the cosine/sine stages (Sched V: 0 or 1)
-  int cols_split;     // bit 0 (forward) / bit 1 (adjoint): that column stage splits each column
+  int cols_split;     // bit 0 (A) / bit 1 (A*): that column stage splits each column
                       // transform of length N = 512 RB over the RB warps of a CTA (colsplit.cuh;
                       // RB = 1 .. 16, n <= 512, or 1024 at RB = 16); a clear bit: the four-step one
 };

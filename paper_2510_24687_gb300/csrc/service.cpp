@@ -730,11 +730,17 @@ tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, flo
       if (rp * plan->cfg.nt_rows <= 1024) trial();
     }
   // then smaller column CTAs for the chosen strip and row pairs (more of them per SM, where the
-  // four-step column FFT keeps fewer than 256 threads busy), and strips around the chosen one
+  // four-step column FFT keeps fewer than 256 threads busy), and strips around the chosen one;
+  // not when both column stages of the pair run the split transform, whose CTA size is fixed
+  // (the knob would change nothing the pair times, only A^-1's four-step column stage)
   const tat::LaunchCfg first = best;
+  const int N = plan->d.N;
+  const bool split_ok = (N == 512 || N == 1024 || N == 2048 || N == 4096 || N == 8192) &&
+                        plan->d.n <= (N == 8192 ? 1024 : 512);
+  const bool pair_split = split_ok && (first.cols_split & 3) == 3;
   for (int threads : {64, 128, 384})
     for (int strip : {first.strip / 2, first.strip, first.strip * 2}) {
-      if (err != TAT_OK || strip < 2 || strip > 32 || threads == first.cols_threads) continue;
+      if (err != TAT_OK || pair_split || strip < 2 || strip > 32 || threads == first.cols_threads) continue;
       plan->cfg = first;
       plan->cfg.cols_threads = threads;
       plan->cfg.strip = strip;
@@ -764,11 +770,8 @@ tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, flo
     apply_order_2M(plan, 1 - best.order_2M);
     trial();
   }
-  // and the other column transform where both exist (N = 512 .. 8192 with few enough rows),
+  // and the other column transforms where both exist (N = 512 .. 8192 with few enough rows),
   // with the best strip among its neighbours
-  const int N = plan->d.N;
-  const bool split_ok = (N == 512 || N == 1024 || N == 2048 || N == 4096 || N == 8192) &&
-                        plan->d.n <= (N == 8192 ? 1024 : 512);
   if (err == TAT_OK && split_ok) {
     const tat::LaunchCfg third = best;
     for (int split = 0; split < 4; ++split)
