@@ -169,7 +169,7 @@ __device__ __forceinline__ void split_load_column(float2* v, const float2* __res
 // transforms of columns c0..c1 and the bilinear gather of the polar samples whose
 // stencil column lies in [c0, c1).  Each warp loads all n rows of the next column into
 // its registers (the RB warps read the same rows; L1 serves the repeats) while the CTA
-// gathers, so the transform starts from registers.
+// waits at the barrier and gathers, so the transform starts from registers.
 template <int L>
 __global__ void TAT_SPLIT_BOUNDS k_cols_fwd_split(DevPlan P, const float2* __restrict__ X, long long xs,
                                                   float2* __restrict__ Y, long long ys, int S, int batch) {
@@ -211,8 +211,10 @@ __global__ void TAT_SPLIT_BOUNDS k_cols_fwd_split(DevPlan P, const float2* __res
     split_dft_fwd(v, reg, tgw, t, lane);
 #pragma unroll
     for (int i = 0; i < 16; ++i) reg[lane + 32 * i] = v[i];
-    __syncthreads();
+    // the next column's rows (global memory only) are requested before the barrier, so that
+    // their latency overlaps the wait for the other warps' transforms
     if (cc + 1 < ncols) split_load_column<RB>(v, Xb + (size_t)(c + 1) * n, n, lane, w16);
+    __syncthreads();
     if (cc > 0) {
       const float2* A = (cc & 1) ? slot0 : slot1;  // column c-1
       const float2* B = buf;                       // column c

@@ -94,15 +94,21 @@ struct DevPlan {
 };
 
 // Tile shapes fixed at compile time per FFT length (index arithmetic by
-// shifts); the host uses the same functions for the launch shapes.  Lengths
-// with a compile-time schedule below 4096 take 8 rings / 16 time samples per
-// CTA; 4096 takes 2 / 4 and runtime lengths (L = 0) 1 / 2, so that a CTA never
-// exceeds 1024 threads.
+// shifts); the host uses the same functions for the launch shapes.  Rings per CTA
+// in the angular stages: 4 at n_phi = 256, 1024, 2048, 8 at the other compile-time
+// lengths below 4096, 2 at 4096, 1 for runtime lengths; time samples per CTA in the
+// theta stages: 8 at n_det = 1024, 2048, 16 at the other compile-time lengths below
+// 4096, 4 at 4096, 2 for runtime lengths (so that a CTA never exceeds 1024 threads).
+// The smaller tiles were measured faster there (more CTAs in flight per SM).
 __host__ __device__ constexpr bool ct_angular_length(int L) {
   return L == 64 || L == 128 || L == 256 || L == 512 || L == 1024 || L == 2048;
 }
-__host__ __device__ constexpr int rings_per_cta_for(int L) { return ct_angular_length(L) ? 8 : L == 4096 ? 2 : 1; }
-__host__ __device__ constexpr int time_tile_for(int L) { return ct_angular_length(L) ? 16 : L == 4096 ? 4 : 2; }
+__host__ __device__ constexpr int rings_per_cta_for(int L) {
+  return (L == 256 || L == 1024 || L == 2048) ? 4 : ct_angular_length(L) ? 8 : L == 4096 ? 2 : 1;
+}
+__host__ __device__ constexpr int time_tile_for(int L) {
+  return (L == 1024 || L == 2048) ? 8 : ct_angular_length(L) ? 16 : L == 4096 ? 4 : 2;
+}
 
 // Launch shapes (host-side knobs; chosen per plan).
 struct LaunchCfg {
