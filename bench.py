@@ -907,7 +907,7 @@ def run_inverse(args, rank, world, local):
     peak_alu, peak_src = alu_peak()
     achieved = flops[dom] / (stage_ms[dom] / 1e3) / 1e12
     kname = {"theta_inv": "k_theta_adj", "modes_inv": "k_modes_inv", "rings_inv": "k_rings_adj<INV>",
-             "cols_inv": "k_cols_inv", "rows_inv": "k_rows_inv", "finish_inv": "k_inv_finish"}
+             "cols_inv": "k_cols_inv", "rows_inv": "k_rows_inv", "finish_inv": "k_inv_sum + k_inv_finish"}
     roofline = {"bound": "alu", "kernel": kname[dom], "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
                 "frac": achieved / peak_alu, "traffic": traffic_for(kname[dom], "inverse_n512_b32"),
                 "peak_source": peak_src,
@@ -945,7 +945,7 @@ def run_inverse(args, rank, world, local):
                 "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded random-ellipse phantoms, g = A f + 1 % noise)",
                 "config": inverse_config(B), "roofline": roofline, "hbm_roofline": hbm, "cpu_baseline": cpu,
-                "e2e": e2e, "gpu_launches": 6 * args.steps, "clocks": clk,
+                "e2e": e2e, "gpu_launches": 7 * args.steps, "clocks": clk,
                 "kernel_source_hash": kernel_source_hash()}
         print(json.dumps(line), flush=True)
     if world > 1:

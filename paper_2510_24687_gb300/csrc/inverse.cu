@@ -15,7 +15,8 @@ tat_status launch_inverse(const tat_plan_s* Pl, int batch, const float* g, long 
   float2* X = static_cast<float2*>(ws);
   float2* Y = X + (size_t)batch * Pl->ws_x;
   const long long xs = (long long)Pl->ws_x, ys = (long long)Pl->ws_y;
-  // the per-image accumulator of C: element 0 of the image's Y region, as a float
+  // the per-image sum for C: element 0 of the image's Y region, as a float, and the row CTAs'
+  // partial sums after it (the polar samples there are consumed by the column stage)
   float* acc = reinterpret_cast<float*>(Y);
   const long long accs = 2 * ys;
   const int dev = Pl->device;
@@ -50,7 +51,7 @@ tat_status launch_inverse(const tat_plan_s* Pl, int batch, const float* g, long 
   dispatch_N(P.N, [&](auto Lc) {
     constexpr int L = decltype(Lc)::value;
     ok &= ensure_smem<k_cols_inv<L>>(dev) && ensure_smem<k_rows_inv<L>>(dev);
-    ok &= pdl_launch(c.pdl != 0, k_cols_inv<L>, s.cols_grid_a, s.cols_block_i, s.cols_smem_i, st, P, Y, ys, X, xs, c.strip, c.nt_N, batch, acc, accs) == cudaSuccess;
+    ok &= pdl_launch(c.pdl != 0, k_cols_inv<L>, s.cols_grid_i, s.cols_block_i, s.cols_smem_i, st, P, Y, ys, X, xs, s.strip_i, c.nt_N, batch) == cudaSuccess;
     stage_done();
     ok &= pdl_launch(c.pdl != 0, k_rows_inv<L>, s.rows_grid, s.rows_block, s.rows_smem, st, P, X, xs, f, fs, acc, accs, c.rows_pairs, c.nt_rows) == cudaSuccess;
     stage_done();
@@ -58,6 +59,7 @@ tat_status launch_inverse(const tat_plan_s* Pl, int batch, const float* g, long 
   {
     const long long count = (long long)batch * P.n * P.n;
     const int blocks = (int)std::min<long long>((count + 255) / 256, 152LL * 8);
+    ok &= pdl_launch(c.pdl != 0, k_inv_sum, batch, 256, 0, st, (int)s.rows_grid.x, acc, accs) == cudaSuccess;
     ok &= pdl_launch(c.pdl != 0, k_inv_finish, blocks, 256, 0, st, P, batch, acc, accs, f, fs) == cudaSuccess;
     stage_done();
   }

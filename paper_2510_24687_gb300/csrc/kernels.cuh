@@ -1062,15 +1062,12 @@ __device__ __forceinline__ float2 inv_node(const DevPlan& P, const float2* __res
 
 // Steps 5-6 (columns): per strip of half-plane columns, vhat on the whole
 // column (times conj(e^{i q dxi}), the x_0 = -1 phase of the inverse DFT), the
-// inverse column DFT, first n rows kept -> X = V'[c][iy].  The strip-0 CTA of
-// each image also clears the image's accumulator of the constant C (`acc`, in
-// element 0 of the image's Y region: ring 0, which this kernel never reads).
+// inverse column DFT, first n rows kept -> X = V'[c][iy].
 #define TAT_COLS_BOUNDS_I __launch_bounds__((L > 0 && L <= 4096) ? 256 : 512, (L > 0 && L <= 4096) ? 4 : 1)
 
 template <int L>
 __global__ void TAT_COLS_BOUNDS_I k_cols_inv(DevPlan P, const float2* __restrict__ Y, long long ys,
-                                           float2* __restrict__ X, long long xs, int S, int nt, int batch,
-                                           float* acc, long long accs) {
+                                           float2* __restrict__ X, long long xs, int S, int nt, int batch) {
   TAT_GRID_DEPENDENCY();
   extern __shared__ float2 sm[];
   int strip, b;
@@ -1085,7 +1082,6 @@ __global__ void TAT_COLS_BOUNDS_I k_cols_inv(DevPlan P, const float2* __restrict
   const int c1 = min(c0 + S, P.ncol);
   const float2* Yb = Y + (size_t)b * ys;
   float2* Xb = X + (size_t)b * xs;
-  if (strip == 0 && tid == 0) acc[(size_t)b * accs] = 0.f;
 #pragma unroll 1
   for (int c = c0; c < c1; ++c) {
     const int qmax = P.inv_qmax[c];  // rows beyond it lie outside the cut-off: zero, no table read
@@ -1143,7 +1139,25 @@ __global__ void TAT_ROWS_BOUNDS k_rows_inv(DevPlan P, const float2* __restrict__
     if ((threadIdx.x & (2 * st - 1)) == 0 && threadIdx.x + st < blockDim.x) red[threadIdx.x] += red[threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0 && red[0] != 0.f) atomicAdd(acc + (size_t)b * accs, red[0]);
+  if (threadIdx.x == 0) acc[(size_t)b * accs + 1 + blockIdx.x] = red[0];  // this CTA's partial sum
+}
+
+// The sum over Omega \ Omega0 of each image from its row CTAs' `nblk` partial sums (slots
+// 1..nblk after the accumulator), in a fixed order -- each thread a fixed set of slots,
+// then a fixed tree -- so that A^-1 gives the same bits on every call; one CTA per image.
+__global__ void k_inv_sum(int nblk, float* acc, long long accs) {
+  TAT_GRID_DEPENDENCY();
+  __shared__ float red[256];
+  float* a = acc + (size_t)blockIdx.x * accs;
+  float s = 0.f;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += a[1 + i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+    if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a[0] = red[0];
 }
 
 // Step 8: f = Pi_Omega0 (v + C), C = -(sum of v over Omega \ Omega0) / (its node count).

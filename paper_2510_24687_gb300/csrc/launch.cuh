@@ -14,7 +14,8 @@ namespace tat {
 namespace {
 
 struct Shapes {
-  dim3 rows_grid, cols_grid_f, cols_grid_a, rings_grid, modes_grid, theta_grid;
+  dim3 rows_grid, cols_grid_f, cols_grid_a, cols_grid_i, rings_grid, modes_grid, theta_grid;
+  int strip_i;  // columns per CTA of A^-1's column stage
   int rows_block, cols_block, cols_block_i, rings_block, modes_block, theta_block;
   size_t rows_smem, cols_smem_f, cols_smem_a, cols_smem_i, rings_smem, modes_smem, theta_smem;
   int ntiles;
@@ -33,6 +34,10 @@ inline Shapes shapes(const tat_plan_s* Pl, int batch) {
   // 1-D, strip-major: blockIdx.x = strip * batch + image
   s.cols_grid_f = dim3(((P.ncol - 1 + c.strip - 1) / c.strip) * batch);
   s.cols_grid_a = dim3(((P.ncol + c.strip - 1) / c.strip) * batch);
+  // A^-1's gather-bound column stage is fastest with short strips (measured at n = 256, 512:
+  // 8 columns ahead of 16 and 32), whatever the pair's tuned strip
+  s.strip_i = std::min(c.strip, 8);
+  s.cols_grid_i = dim3(((P.ncol + s.strip_i - 1) / s.strip_i) * batch);
   s.cols_block = c.cols_threads;
   // the inverse's column kernel is compiled for at most 256 threads at these lengths
   const bool ct_le4096 = P.N == 256 || P.N == 512 || P.N == 1024 || P.N == 2048 || P.N == 4096;

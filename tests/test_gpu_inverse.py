@@ -90,6 +90,17 @@ def test_left_inverse_on_device(pkg, torch):
     assert rel(fr, f.astype(np.float64)) < 3e-3
 
 
+def test_inverse_repeats_bit_for_bit(pkg, torch):
+    """Repeated A^-1 calls give the same bits: the constant C is summed from per-CTA partial
+    sums in a fixed order (no atomics), at a size with many row CTAs."""
+    op, P = make(pkg, dict(n=500, n_det=128, n_t=128, support_radius=0.9))
+    g = np.stack([f32(random_sinogram(128, 128, 70 + s)) for s in range(2)]).astype(np.float32)
+    gt = torch.tensor(g, device="cuda:0")
+    a = op.inverse(gt).cpu().numpy()
+    assert np.array_equal(op.inverse(gt).cpu().numpy(), a)
+    assert rel(a[1], O.inverse(P, g[1].astype(np.float64))) <= TOL
+
+
 def test_inverse_batched_matches_single(pkg, torch):
     op, P = make(pkg, CASES["n64"])
     gs = np.stack([f32(random_sinogram(P.n_det, P.n_t, 20 + b)) for b in range(3)]).astype(np.float32)
