@@ -1604,7 +1604,8 @@ def run_lpd(args, rank, world, local):
                 "config": lpd_config(args.train_steps, args.arc),
                 "comparison_ms_per_step": {"graph": ms, "eager": ms_eager, "operators_only_4K_calls": ms_ops},
                 "operator_launch_shapes": {"ms_pair": net.tuned[0], "strip": net.tuned[1], "row_pairs": net.tuned[2],
-                                           "cols_threads": net.tuned[3], "row_threads": net.tuned[4]}
+                                           "cols_threads": net.tuned[3], "row_threads": net.tuned[4],
+                                           "column_split": pkg.tat_plan_get_column_split(net.op.plan)}
                 if net.tuned else None,
                 "reconstruction_rel_l2_test": {"lpd": err_lpd, "tv_ls": err_tv, "tv_alpha": best_alpha,
                                                "nnls": err_nnls},

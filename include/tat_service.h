@@ -110,7 +110,9 @@ tat_status tat_service_get_stats(tat_service_t svc, tat_service_stats* stats);
  * and 4 times its row pairs, the best shape with and without programmatic
  * dependent launch of the stages, the other pass order of the length-2M FFT of
  * the cosine and sine stages (tat_plan_set_fft_order) and the other column transforms
- * (tat_plan_set_column_split, where the split one applies) -- on
+ * (tat_plan_set_column_split, where the split one applies; with half, the same and twice
+ * the strip and, where a column stage then runs the four-step transform, column CTAs of
+ * 64, 128, 256 and 384 threads) -- on
  * one A then one A* of `batch` images at f (device, batch*n*n floats, output
  * of A* written to f_out) with g (batch*n_det*n_t floats) and the workspace
  * for `batch`, and keeps the fastest for every later call on this plan.  The

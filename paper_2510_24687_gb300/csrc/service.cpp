@@ -771,18 +771,22 @@ tat_status tat_plan_autotune(tat_plan_t plan, int batch, float* f, float* g, flo
     trial();
   }
   // and the other column transforms where both exist (N = 512 .. 8192 with few enough rows),
-  // with the best strip among its neighbours
+  // with the best strip among its neighbours and, where a column stage then runs the
+  // four-step transform, each of the column CTA sizes
   if (err == TAT_OK && split_ok) {
     const tat::LaunchCfg third = best;
     for (int split = 0; split < 4; ++split)
-      for (int strip : {third.strip / 2, third.strip, third.strip * 2}) {
-        if (err != TAT_OK || split == third.cols_split || strip < 2 || strip > 32) continue;
-        plan->cfg = third;
-        apply_order_2M(plan, third.order_2M);
-        plan->cfg.cols_split = split;
-        plan->cfg.strip = strip;
-        trial();
-      }
+      for (int strip : {third.strip / 2, third.strip, third.strip * 2})
+        for (int threads : {64, 128, 256, 384}) {
+          if (err != TAT_OK || split == third.cols_split || strip < 2 || strip > 32) continue;
+          if (split == 3 ? threads != third.cols_threads : threads == 384 && N <= 1024) continue;
+          plan->cfg = third;
+          apply_order_2M(plan, third.order_2M);
+          plan->cfg.cols_split = split;
+          plan->cfg.strip = strip;
+          plan->cfg.cols_threads = threads;
+          trial();  // skips shapes the kernels do not take
+        }
   }
   plan->cfg = err == TAT_OK ? best : base;
   apply_order_2M(plan, plan->cfg.order_2M);
