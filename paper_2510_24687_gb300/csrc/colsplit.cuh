@@ -31,7 +31,7 @@
 namespace tat {
 namespace {
 
-constexpr int kSplitRegion = 544;  // slots per warp region (32 rows of 17)
+constexpr int kSplitRegion = kSplitRegionSlots;  // slots per warp region (32 rows of 17)
 
 __host__ __device__ constexpr bool split_length(int L) {
   return L == 512 || L == 1024 || L == 2048 || L == 4096 || L == 8192;
@@ -182,22 +182,19 @@ __global__ void TAT_SPLIT_BOUNDS k_cols_fwd_split(DevPlan P, const float2* __res
   float2* slot0 = sm;
   float2* slot1 = sm + CS;
   float2* tg = sm + 2 * CS;
-  float2* smph = tg + 32 * RB;
   const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, k1 = tid >> 5;
   const int c0 = strip * S;
   const int c1 = min(c0 + S, P.ncol - 1);  // owned stencil columns i0 in [c0, c1)
   const int ncols = c1 - c0 + 1;           // spectrum columns c0..c1
   const float2* Xb = X + (size_t)b * xs;
   float2* Yb = Y + (size_t)b * ys;
-  const int N = P.N, n = P.n;
+  const int n = P.n;
   const float2 w16 = RB == 16 ? unit_root<16, false>(k1) : make_float2(1.f, 0.f);
   float2 v[16];
   split_load_column<RB>(v, Xb + (size_t)c0 * n, n, lane, w16);
   load_split_tg<RB>(tg, P.fN.tw, tid, NT);
-  load_phase2(smph, P, tid, NT);
   const SplitTw t = split_twiddles<RB>(P.fN.tw, k1, lane);
   const float2* tgw = tg + 32 * k1 + 16 * (lane >> 4);
-  const SplitSlot<RB> pos;
   __syncthreads();
 #pragma unroll 1
   for (int cc = 0; cc < ncols; ++cc) {
@@ -205,8 +202,8 @@ __global__ void TAT_SPLIT_BOUNDS k_cols_fwd_split(DevPlan P, const float2* __res
     const int c = c0 + cc;
     // the first polar entry of this thread's gather, loaded before the transform
     const int e0 = cc > 0 ? P.coloff[c - 1] + tid : 0, e1 = cc > 0 ? P.coloff[c] : 0;
-    PolarEntry pe0{};
-    if (e0 < e1) pe0 = P.pts[e0];
+    PolarEntrySplit pe0{};
+    if (e0 < e1) pe0 = P.pts_split[e0];
     float2* reg = buf + k1 * kSplitRegion;
     split_dft_fwd(v, reg, tgw, t, lane);
 #pragma unroll
@@ -218,14 +215,14 @@ __global__ void TAT_SPLIT_BOUNDS k_cols_fwd_split(DevPlan P, const float2* __res
     if (cc > 0) {
       const float2* A = (cc & 1) ? slot0 : slot1;  // column c-1
       const float2* B = buf;                       // column c
+      // the stencil rows' slots and phase-weighted row weights come precomputed with the point
       for (int e = e0; e < e1; e += NT) {
-        const PolarEntry pe = e == e0 ? pe0 : P.pts[e];
-        const int ra = wrapN(pe.k0, N), rb = wrapN(pe.k0 + 1, N);
-        const int qa = pos(ra), qb = pos(rb);
-        const float a = pe.a, bb = pe.b;
+        const PolarEntrySplit pe = e == e0 ? pe0 : P.pts_split[e];
+        const int qa = (int)(pe.slots & 0xffffu), qb = (int)(pe.slots >> 16);
+        const float a = pe.a;
         const float2 va = cadd(cscale(A[qa], 1.f - a), cscale(B[qa], a));
         const float2 vb = cadd(cscale(A[qb], 1.f - a), cscale(B[qb], a));
-        Yb[pe.p] = cadd(cscale(cmul(va, phase_at(smph, P, ra)), 1.f - bb), cscale(cmul(vb, phase_at(smph, P, rb)), bb));
+        Yb[pe.p] = cadd(cmul(va, pe.alpha), cmul(vb, pe.beta));
       }
     }
     __syncthreads();

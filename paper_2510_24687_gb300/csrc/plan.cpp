@@ -627,6 +627,30 @@ tat_status build_plan(const tat_plan_desc& D, tat_plan_s* P) {
       if (pinv[p] < 0) return TAT_ERR_INTERNAL;  // every sample of rings >= 1 has exactly one point
     TAT_TRY(upload(P, pinv, &d.pinv));
     TAT_TRY(upload(P, sorted, &d.pts));
+    // the split forward column stage's copy of the table (N = 512 RB, few enough rows)
+    const bool split_ok = (d.N == 512 || d.N == 1024 || d.N == 2048 || d.N == 4096 || d.N == 8192) &&
+                          n <= (d.N == 8192 ? 1024 : 512);
+    if (split_ok) {
+      const int RB = d.N / 512;
+      auto slot = [&](long long q) { return (unsigned)((q % RB) * kSplitRegionSlots + q / RB); };
+      std::vector<PolarEntrySplit> ps(npts);
+      for (int e = 0; e < npts; ++e) {
+        const PolarEntry& s = sorted[e];
+        const long long k0 = s.k0, k1 = s.k0 + 1;  // signed rows; |k| < N/2
+        double c0, s0, c1, s1;
+        cos_sin_2pi(k0 * (n - 1), 2LL * d.N, &c0, &s0);
+        cos_sin_2pi(k1 * (n - 1), 2LL * d.N, &c1, &s1);
+        const double b = s.b;
+        PolarEntrySplit& t = ps[e];
+        t.p = s.p;
+        t.slots = slot(k0 < 0 ? k0 + d.N : k0) | (slot(k1 < 0 ? k1 + d.N : k1) << 16);
+        t.a = s.a;
+        t.pad = 0.f;
+        t.alpha = make_float2((float)((1.0 - b) * c0), (float)((1.0 - b) * s0));
+        t.beta = make_float2((float)(b * c1), (float)(b * s1));
+      }
+      TAT_TRY(upload(P, ps, &d.pts_split));
+    }
     TAT_TRY(upload(P, off, &d.coloff));
     TAT_TRY(upload(P, runs, &d.runs));
     TAT_TRY(upload(P, runoff, &d.runoff));

@@ -47,6 +47,21 @@ struct PolarEntry {
   float b;
 };
 
+// Slots per warp region of a split column buffer (colsplit.cuh): 32 rows of 17.
+constexpr int kSplitRegionSlots = 544;
+
+// The same polar sample for the forward column stage on the split transform, with what the
+// gather needs precomputed on the host: the buffer slots of its stencil rows k0 and k0 + 1
+// in the split layout, and the phase-weighted row weights (FP64-built, rounded once).
+struct PolarEntrySplit {
+  int p;           // polar slot
+  unsigned slots;  // slot of row k0 (low 16 bits) and of row k0 + 1 (high 16 bits)
+  float a;         // weight of the second stencil column
+  float pad;
+  float2 alpha;    // (1 - b) e^{i k0 dxi}
+  float2 beta;     // b e^{i (k0 + 1) dxi}
+};
+
 // Everything a kernel needs, passed by value.
 struct DevPlan {
   int n, n_det, n_t;
@@ -64,6 +79,8 @@ struct DevPlan {
   const int2* rowrange;            // [n] support columns [lo, hi) of each image row
   const float* gamma;              // [n_det] 1 on the arc Gamma, else 0
   const PolarEntry* pts;           // [n_points]
+  const PolarEntrySplit* pts_split;  // [n_points] the same points for the split forward column stage
+                                     // (null where the split transform does not apply)
   const int* coloff;               // [ncol+1] points with i0 = c: [coloff[c], coloff[c+1])
   const int2* runs;                // [n_runs+1] {first point, k0} of each run of equal k0 within a column,
                                    // column by column; run r ends at runs[r+1].x (a sentinel closes the table)
