@@ -25,6 +25,9 @@
 namespace tat {
 
 __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+// spad(i + r s) = spad(i) + r spad(s) for i >= 0 when s is a multiple of 16: the padded
+// slots of a butterfly's strided elements then sit at a constant step (immediate offsets).
+__device__ __forceinline__ bool spad_linear(int s) { return (s & 15) == 0; }
 __host__ __device__ __forceinline__ int spad_len(int L) { return L + (L >> 4) + 1; }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -275,19 +278,22 @@ __device__ __forceinline__ void fft_pass(float2* buf, int L, int Ns, const float
   const int tws = L / (Ns * R);
   const bool act = tid < nthr;
   float2 v[NB][R];
+  const bool lin_in = spad_linear(nb), lin_out = spad_linear(Ns);
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const int j = tid + b * nthr;
     if (act && j < nb) {
+      const int sj = spad(j);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int idx = j + r * nb;
+        const int slot = lin_in ? sj + r * spad(nb) : spad(idx);
         if (first) {
-          float2 x = idx < n_in ? buf[spad(idx)] : make_float2(0.f, 0.f);
+          float2 x = idx < n_in ? buf[slot] : make_float2(0.f, 0.f);
           if (pre != nullptr && idx < n_in) x = cmulc(x, __ldg(&pre[idx]));
           v[b][r] = x;
         } else {
-          v[b][r] = buf[spad(idx)];
+          v[b][r] = buf[slot];
         }
       }
       if (Ns > 1) {
@@ -309,15 +315,17 @@ __device__ __forceinline__ void fft_pass(float2* buf, int L, int Ns, const float
     if (act && j < nb) {
       const int k = j % Ns;
       const int base = (j - k) * R + k;
+      const int sb = spad(base);
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int o = base + r * Ns;
+        const int slot = lin_out ? sb + r * spad(Ns) : spad(o);
         if (last) {
-          if (o < n_out) buf[spad(o)] = post != nullptr ? cmul(v[b][r], __ldg(&post[o])) : v[b][r];
+          if (o < n_out) buf[slot] = post != nullptr ? cmul(v[b][r], __ldg(&post[o])) : v[b][r];
         } else if (keep_mod > 0) {
-          if (o % keep_mod < n_out) buf[spad(o)] = v[b][r];
+          if (o % keep_mod < n_out) buf[slot] = v[b][r];
         } else {
-          buf[spad(o)] = v[b][r];
+          buf[slot] = v[b][r];
         }
       }
     }
@@ -440,8 +448,9 @@ __device__ __forceinline__ void fft_pass_store(const float2* buf, int L, int tid
     const int j = tid + b * nthr;
     if (act && j < nb && j < n_out) {
       float2 v[R];
+      const int sj = spad(j);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = buf[spad(j + r * nb)];
+      for (int r = 0; r < R; ++r) v[r] = buf[spad_linear(nb) ? sj + r * spad(nb) : spad(j + r * nb)];
       float2 w1 = make_float2(1.f, 0.f), w2 = w1, w4 = w1, w8 = w1;
       pass_tw<R>(ptws, nb, j, w1, w2, w4, w8);
       apply_twiddles_given<R, INV>(v, w1, w2, w4, w8);
